@@ -1,0 +1,222 @@
+/*
+ * qsim.h -- C ABI of the GB300 state-vector library (sm_103a).
+ *
+ * The library applies parameterised gates to 2^n-amplitude complex state
+ * vectors on one GPU and computes the reversible-adjoint gradient, following
+ * the register / instruction-set statement of Yao.jl (arXiv 1912.10877):
+ * Sec. "Instructions on Quantum Registers" (instruct!, measure, measure!),
+ * Sec. "Representing Quantum Circuits" (apply! of a chain), Sec. "Forward
+ * Mode" (expect of sums of Pauli strings), Sec. "Reverse Mode" (expect',
+ * Eqs. apply-back and outer-product) and Sec. "Batched Quantum Registers".
+ *
+ * Conventions shared by every entry point
+ *  - Qubit order is little-endian: qubit loc l (0-based) is bit l of the basis
+ *    index; the paper's 1-based qubit q is loc q-1.
+ *  - A k-qubit gate on locs (l_0, ..., l_{k-1}) has matrix index bit j <->
+ *    qubit l_j; matrices are row-major 2^k x 2^k with interleaved (re, im)
+ *    doubles and are always passed in FP64 (the library rounds them once to
+ *    FP32 for complex64 states).
+ *  - Controls: ctrl value 1 = control on |1>, 0 = inverse control on |0>.
+ *  - Amplitudes are interleaved (re, im): QS_C64 = 2 x float per amplitude,
+ *    QS_C128 = 2 x double.  A batch of registers is stored back to back,
+ *    register r at element offset offsets[r] (offsets are prefix sums of
+ *    2^{n_r}); each register is contiguous.
+ *  - Pointers named dev_* are device pointers; host_* are host pointers.
+ *    Every call is asynchronous on the state's stream except those that write
+ *    host outputs, which synchronise that stream before returning.
+ *  - Every entry point returns QS_OK (0) or a negative status; no exception
+ *    crosses the ABI.  qs_last_error() gives a message for the calling thread.
+ *  - Handles are not thread-safe; use one handle per host thread or serialise.
+ */
+#ifndef QSIM_H
+#define QSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define QS_OK 0
+#define QS_EINVAL (-1)        /* bad argument: size, loc, duplicate qubit, null pointer */
+#define QS_ENOMEM (-2)        /* device or host allocation failed */
+#define QS_EDEVICE (-3)       /* a CUDA call or kernel failed */
+#define QS_ETIMEDOUT (-4)     /* a bounded device-side wait gave up */
+#define QS_EUNSUPPORTED (-5)  /* valid request this build does not implement */
+
+/* amplitude types */
+#define QS_C64 0   /* complex64: FP32 math and accumulation for gate application */
+#define QS_C128 1  /* complex128: FP64 */
+
+#define QS_MAXK 5        /* largest gate arity (targets) */
+#define QS_MAXQ 40       /* largest register (qubits) */
+
+/* gate kinds (App. "Builtin Block Types"; R_S(theta) = exp(-i S theta / 2),
+ * Sec. "Forward Mode"; shift(theta) = diag(1, e^{i theta}), listing
+ * "inspecting gates"; phase(theta) = e^{i theta} on the target) */
+enum qs_gate_kind {
+  QS_GATE_I = 0, QS_GATE_X, QS_GATE_Y, QS_GATE_Z, QS_GATE_H, QS_GATE_S, QS_GATE_SDG,
+  QS_GATE_T, QS_GATE_TDG, QS_GATE_RX, QS_GATE_RY, QS_GATE_RZ, QS_GATE_SHIFT,
+  QS_GATE_PHASE, QS_GATE_SWAP, QS_GATE_ROT, QS_GATE_MATRIX
+};
+
+/* One entry of a flat gate list (the paper's put / control / chain blocks,
+ * flattened).  QS_GATE_ROT is exp(-i theta/2 * sigma_{paulis[0]} (x) ...) on
+ * locs; QS_GATE_MATRIX reads 2^k x 2^k entries at mat_offset of the matrix
+ * pool given to qs_circuit_create. */
+typedef struct qs_gate_desc {
+  int32_t kind;              /* enum qs_gate_kind */
+  int32_t nlocs;             /* k, 1..QS_MAXK (SWAP: 2) */
+  int32_t locs[QS_MAXK];     /* target qubits */
+  int32_t paulis[QS_MAXK];   /* ROT: 1 = X, 2 = Y, 3 = Z per target */
+  int32_t param;             /* index into the parameter vector, -1 = use theta */
+  int32_t reserved;
+  uint64_t ctrl_mask;        /* bit q set: qubit q is a control */
+  uint64_t ctrl_vals;        /* bit q: required value of control q */
+  int64_t mat_offset;        /* MATRIX: offset in complex entries into the pool */
+  double theta;              /* fixed angle when param < 0 */
+} qs_gate_desc;
+
+/* One Pauli string with a real coefficient: qubit q carries X if only bit q of
+ * x_mask is set, Z if only bit q of z_mask is set, Y if both. */
+typedef struct qs_pauli_term {
+  double coeff;
+  uint64_t x_mask;
+  uint64_t z_mask;
+} qs_pauli_term;
+
+typedef struct qs_state qs_state;
+typedef struct qs_circuit qs_circuit;
+typedef struct qs_observable qs_observable;
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* qs_last_error(void);
+
+/* ---------------------------------------------------------------- states */
+
+/* Bytes of amplitude storage for nreg registers of nqubits[r] qubits. */
+int qs_state_bytes(int nreg, const int32_t* host_nqubits, int dtype, size_t* out_bytes);
+
+/* A register (nbatch = 1) or a uniform batch of nbatch registers of nqubits
+ * qubits (Sec. "Batched Quantum Registers").  dev_buf, if not NULL, must hold
+ * qs_state_bytes() bytes, 256-byte aligned, and stays owned by the caller for
+ * the life of the handle; if NULL the library allocates and frees it.  The
+ * amplitudes are NOT initialised: call qs_state_reset or qs_state_upload.
+ * stream is a cudaStream_t (NULL = legacy default stream). */
+int qs_state_create(int nqubits, int dtype, int nbatch, void* dev_buf, void* stream,
+                    qs_state** out);
+
+/* A batch of nreg registers of uneven sizes host_nqubits[r] (1..QS_MAXQ). */
+int qs_batch_create(int nreg, const int32_t* host_nqubits, int dtype, void* dev_buf,
+                    void* stream, qs_state** out);
+
+int qs_state_destroy(qs_state* s);
+int qs_state_set_stream(qs_state* s, void* stream);
+
+/* Device pointer of the amplitudes, total bytes, and element offsets of the
+ * registers (host_offsets may be NULL; else it receives nreg + 1 values). */
+int qs_state_data(const qs_state* s, void** dev_ptr, size_t* bytes, int64_t* host_offsets);
+
+/* |x_r> on every register r: host_basis[r] is the basis index (NULL = |0...0>). */
+int qs_state_reset(qs_state* s, const uint64_t* host_basis);
+
+/* Copy all amplitudes from / to host memory (pageable or pinned), in the
+ * state's dtype and layout.  Both synchronise the stream. */
+int qs_state_upload(qs_state* s, const void* host_amps);
+int qs_state_download(const qs_state* s, void* host_amps);
+
+/* ---------------------------------------------------------------- gates */
+
+/* instruct!(reg, U, locs, ctrl_locs, ctrl_vals) on every register of s
+ * (Sec. "Instructions on Quantum Registers"; the general multi-control,
+ * multi-qubit, arbitrary-location instruction of Sec. "Performance").
+ * host_mat: 2^k x 2^k row-major interleaved complex doubles (not checked for
+ * unitarity).  locs and ctrl_locs must be distinct and < every register's n.
+ * The library picks a diagonal, permutation or dense kernel from the matrix's
+ * non-zero pattern (App. "Matrix Types"). */
+int qs_apply_gate(qs_state* s, const double* host_mat, int k, const int32_t* host_locs,
+                  int nctrl, const int32_t* host_ctrl_locs, const int32_t* host_ctrl_vals);
+
+/* The same for a named gate (enum qs_gate_kind other than MATRIX) at angle
+ * theta; host_paulis is read only for QS_GATE_ROT. */
+int qs_apply_named(qs_state* s, int kind, int k, const int32_t* host_locs,
+                   const int32_t* host_paulis, int nctrl, const int32_t* host_ctrl_locs,
+                   const int32_t* host_ctrl_vals, double theta);
+
+/* ---------------------------------------------------------------- circuits */
+
+/* Immutable gate list of nqubits qubits with nparams parameters.
+ * host_mats: pool of interleaved complex doubles for MATRIX gates (may be
+ * NULL if none), nmat complex entries.  Everything is copied. */
+int qs_circuit_create(int nqubits, const qs_gate_desc* host_gates, int ngates,
+                      const double* host_mats, int64_t nmat, int nparams, qs_circuit** out);
+int qs_circuit_destroy(qs_circuit* c);
+int qs_circuit_info(const qs_circuit* c, int* nqubits, int* ngates, int* nparams);
+
+/* apply!(reg, chain): gates in list order on every register of s (Sec.
+ * "Representing Quantum Circuits").  host_params: nparams doubles shared by
+ * all registers, or nbatch * nparams (register-major) if per_register != 0. */
+int qs_apply_circuit(qs_state* s, const qs_circuit* c, const double* host_params,
+                     int per_register);
+
+/* As qs_apply_circuit on a single register, also saving forward checkpoints:
+ * after gate index g (0-based) with (g + 1) % ckpt_every == 0 and g + 1 <
+ * ngates, the state is copied to slot (g + 1) / ckpt_every - 1 of dev_ckpts,
+ * which must hold qs_checkpoint_count() states of the state's dtype. */
+int qs_checkpoint_count(const qs_circuit* c, int ckpt_every, int* count);
+int qs_apply_circuit_ckpt(qs_state* s, const qs_circuit* c, const double* host_params,
+                          int ckpt_every, void* dev_ckpts);
+
+/* ---------------------------------------------------------------- observables */
+
+/* O = sum_t coeff_t P_t (Sec. "Forward Mode", expect; Listing "Heisenberg
+ * Hamiltonian" for sums of Pauli strings).  Strings must be Hermitian as
+ * given (any X/Y/Z pattern is). */
+int qs_observable_create(const qs_pauli_term* host_terms, int nterms, qs_observable** out);
+int qs_observable_destroy(qs_observable* o);
+
+/* <psi_r|O|psi_r> for every register r into host_out[nreg] (FP64 reduction). */
+int qs_expect(qs_state* s, const qs_observable* o, double* host_out);
+
+/* ---------------------------------------------------------------- gradient */
+
+/* Device bytes of the work buffer qs_backward needs for an n-qubit register
+ * (two complex128 states: psi and its adjoint lambda). */
+int qs_backward_work_bytes(int nqubits, size_t* out_bytes);
+
+/* expect'(O, reg => circuit) (Sec. "Reverse Mode"): s holds the circuit's
+ * OUTPUT state psi_N of a single register (left unchanged).  With lambda =
+ * O psi_N, gates are walked backwards; a gate U = exp(-i theta c H) adds
+ * 2 c Im<lambda|H|psi> to host_grad[param] (rotations c = 1/2, H = Pauli;
+ * shift c = -1, H = P1; phase c = -1, H = 1; H includes the control
+ * projector), then psi <- U^dag psi and lambda <- U^dag lambda (Eq.
+ * apply-back), in FP64 in dev_work.  If ckpt_every > 0, dev_ckpts holds the
+ * checkpoints written by qs_apply_circuit_ckpt and psi restarts from them
+ * (bounding uncompute drift).  host_grad receives nparams doubles (shared
+ * parameters add up); host_loss, if not NULL, receives <psi_N|O|psi_N>. */
+int qs_backward(qs_state* s, const qs_circuit* c, const double* host_params,
+                const qs_observable* o, int ckpt_every, const void* dev_ckpts, void* dev_work,
+                double* host_grad, double* host_loss);
+
+/* ---------------------------------------------------------------- measurement */
+
+/* measure / measure! on all qubits (Sec. "Instructions on Quantum
+ * Registers"), nshots samples per register from |psi|^2 using the caller's
+ * uniform numbers host_u[nreg][nshots] in [0, 1) into host_out[nreg][nshots].
+ * Deterministic contract: p_i = re*re + im*im (separately rounded FP64
+ * multiply and add; complex64 amplitudes are promoted exactly); level-0
+ * blocks of 1024 consecutive p_i and level-1 blocks of 1024 level-0 sums are
+ * left folds; total T is the left fold of the level-1 sums; for t = u * T
+ * each level walks its values from the carried prefix, takes the first
+ * value whose running sum exceeds t (else the last positive value, else the
+ * last) and carries its exclusive prefix down.  collapse != 0 (requires
+ * nshots == 1) projects each register onto its sample and renormalises. */
+int qs_measure(qs_state* s, const double* host_u, int nshots, int64_t* host_out, int collapse);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QSIM_H */

@@ -1,0 +1,198 @@
+// adjoint.cu -- reversible-adjoint backward pass (sm_103a), Sec. "Reverse Mode".
+//
+// With lambda = dL/dpsi* (Wirtinger) = O psi_N, gates are walked from last to
+// first.  With psi and lambda the states right after gate k, a gate
+// U = exp(-i theta c H) contributes dL/dtheta = 2 c Im<lambda|H|psi> (H includes
+// the control projector), and then both states are uncomputed,
+// psi <- U^dag psi, lambda <- U^dag lambda (Eq. apply-back); the outer product
+// of Eq. outer-product is never formed, only its contraction with H.
+//
+// Parameterised gates run one fused pass per gate: each thread loads the
+// psi and lambda 2^k-tuples, adds Im sum_m conj(l_m) (G x)_m to its FP64
+// partial, applies U^dag to both tuples and stores them.  Block partials land
+// in scratch memory and one block folds them pairwise into grad[param] in
+// stream order.  The uncompute runs in FP64 (complex128 work buffers) whatever
+// the forward precision; checkpoints taken during the forward replace psi at
+// segment boundaries so that uncompute drift cannot accumulate across segments.
+#include <cstring>
+
+#include "common.cuh"
+
+namespace qs {
+
+int expect_raw(const void* data, int dtype, int n, int nreg, const qs_observable* o, qs_state* ws_owner,
+               double* host_out);
+int apply_observable_c128(const double2* psi, double2* lam, int n, const qs_observable* o, cudaStream_t st);
+int promote_to_c128(const void* in, int dtype, double2* out, uint64_t dim, cudaStream_t st);
+
+constexpr int kAdjThreads = 256;
+constexpr int kAdjMaxBlocks = 1216;  // 8 per SM on 152 SMs
+
+template <int K>
+struct AdjMat {
+  double2 g[1 << (2 * K)];   // generator H on the targets
+  double2 ud[1 << (2 * K)];  // U^dagger on the targets
+  uint64_t off[1 << K];
+};
+
+template <int K>
+__global__ void __launch_bounds__(kAdjThreads)
+k_adjoint_param(double2* __restrict__ psi, double2* __restrict__ lam, uint64_t nitems, IdxSpec s,
+                const __grid_constant__ AdjMat<K> M, double* __restrict__ partials) {
+  constexpr int D = 1 << K;
+  double acc = 0.0;
+  for (uint64_t it = (uint64_t)blockIdx.x * kAdjThreads + threadIdx.x; it < nitems;
+       it += (uint64_t)gridDim.x * kAdjThreads) {
+    const uint64_t base = item_index(it, s);
+    double2 x[D], l[D];
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      x[m] = psi[base + M.off[m]];
+      l[m] = lam[base + M.off[m]];
+    }
+    // Im sum_m conj(l_m) (G x)_m
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      double2 gx = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int j = 0; j < D; ++j) gx = cfma(M.g[m * D + j], x[j], gx);
+      acc += l[m].x * gx.y - l[m].y * gx.x;
+    }
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      double2 px = make_double2(0.0, 0.0), pl = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        px = cfma(M.ud[m * D + j], x[j], px);
+        pl = cfma(M.ud[m * D + j], l[j], pl);
+      }
+      psi[base + M.off[m]] = px;
+      lam[base + M.off[m]] = pl;
+    }
+  }
+  __shared__ double red[kAdjThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < kAdjThreads / 32; ++w) v += red[w];
+    partials[blockIdx.x] = v;
+  }
+}
+
+// grad[param] += scale * (pairwise fold of partials[0..n))
+__global__ void k_fold_into(const double* __restrict__ partials, int n, double scale, double* __restrict__ grad,
+                            int param) {
+  __shared__ double buf[2048];
+  for (int i = threadIdx.x; i < 2048; i += blockDim.x) buf[i] = i < n ? partials[i] : 0.0;
+  __syncthreads();
+  for (int w = 1024; w > 0; w >>= 1) {
+    for (int i = threadIdx.x; i < w; i += blockDim.x) buf[i] += buf[i + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) grad[param] += scale * buf[0];
+}
+
+template <int K>
+static int launch_adjoint_param(double2* psi, double2* lam, int n, const qs_gate_desc& g,
+                                const std::vector<cd>& G, const std::vector<cd>& Ud, double* partials,
+                                double* dgrad, double cfac, cudaStream_t st) {
+  AdjMat<K> M;
+  memset(&M, 0, sizeof(M));
+  constexpr int D = 1 << K;
+  uint64_t locmask = 0;
+  for (int j = 0; j < K; ++j) locmask |= 1ull << g.locs[j];
+  for (int m = 0; m < D; ++m) {
+    uint64_t o = 0;
+    for (int j = 0; j < K; ++j)
+      if ((m >> j) & 1) o |= 1ull << g.locs[j];
+    M.off[m] = o;
+  }
+  for (int i = 0; i < D * D; ++i) {
+    M.g[i] = make_double2(G[i].real(), G[i].imag());
+    M.ud[i] = make_double2(Ud[i].real(), Ud[i].imag());
+  }
+  IdxSpec s;
+  QS_TRY(make_idx(n, locmask | g.ctrl_mask, g.ctrl_vals & g.ctrl_mask, &s));
+  const uint64_t items = 1ull << s.item_log2;
+  const int nblk = (int)std::min<uint64_t>(kAdjMaxBlocks, std::max<uint64_t>(1, (items + kAdjThreads * 4 - 1) / (kAdjThreads * 4)));
+  k_adjoint_param<K><<<nblk, kAdjThreads, 0, st>>>(psi, lam, items, s, M, partials);
+  QS_LAUNCHED();
+  k_fold_into<<<1, 256, 0, st>>>(partials, nblk, 2.0 * cfac, dgrad, g.param);
+  QS_LAUNCHED();
+  return QS_OK;
+}
+
+// generator H (on the targets) and factor c with U = exp(-i theta c H)
+static int generator(const qs_gate_desc& g, std::vector<cd>& G, double* cfac) {
+  const int D = 1 << g.nlocs;
+  G.assign(D * D, cd(0, 0));
+  switch (g.kind) {
+    case QS_GATE_RX: G[1] = 1; G[2] = 1; *cfac = 0.5; return QS_OK;
+    case QS_GATE_RY: G[1] = cd(0, -1); G[2] = cd(0, 1); *cfac = 0.5; return QS_OK;
+    case QS_GATE_RZ: G[0] = 1; G[3] = -1; *cfac = 0.5; return QS_OK;
+    case QS_GATE_SHIFT: G[3] = 1; *cfac = -1.0; return QS_OK;
+    case QS_GATE_PHASE: G[0] = 1; G[3] = 1; *cfac = -1.0; return QS_OK;
+    case QS_GATE_ROT:
+      pauli_string(g.nlocs, g.paulis, G);
+      *cfac = 0.5;
+      return QS_OK;
+  }
+  return fail(QS_EUNSUPPORTED, "gate kind %d has no parameter gradient", g.kind);
+}
+
+int backward(qs_state* s, const qs_circuit* c, const double* params, const qs_observable* o, int ckpt_every,
+             const void* ckpts, void* work, double* host_grad, double* host_loss) {
+  if (s->nreg != 1) return fail(QS_EUNSUPPORTED, "qs_backward takes a single register");
+  const int n = s->nq[0];
+  if (n != c->nqubits) return fail(QS_EINVAL, "circuit has %d qubits, state %d", c->nqubits, n);
+  if (ckpt_every < 0 || (ckpt_every > 0 && !ckpts)) return fail(QS_EINVAL, "bad checkpoint arguments");
+  if (!work) return fail(QS_EINVAL, "work buffer is NULL");
+  cudaStream_t st = s->stream;
+  const uint64_t dim = 1ull << n;
+  double2* psi = (double2*)work;
+  double2* lam = psi + dim;
+  const int np = std::max(1, c->nparams);
+  if (host_loss) QS_TRY(expect_raw(s->data, s->dtype, n, 1, o, s, host_loss));
+  // scratch: grad[np] | partials[kAdjMaxBlocks]
+  QS_TRY(ensure_ws(s, s->ws, sizeof(double) * (np + kAdjMaxBlocks) + 256));
+  double* dgrad = (double*)s->ws.ptr;
+  double* partials = dgrad + np;
+  QS_CUDA(cudaMemsetAsync(dgrad, 0, sizeof(double) * np, st));
+  QS_TRY(promote_to_c128(s->data, s->dtype, psi, dim, st));
+  QS_TRY(apply_observable_c128(psi, lam, n, o, st));
+  const size_t ab = amp_bytes(s->dtype);
+  std::vector<cd> U, G;
+  for (int k = (int)c->gates.size() - 1; k >= 0; --k) {
+    const qs_gate_desc& g = c->gates[k];
+    if (ckpt_every > 0 && (k + 1) % ckpt_every == 0 && k + 1 < (int)c->gates.size()) {
+      const int slot = (k + 1) / ckpt_every - 1;
+      QS_TRY(promote_to_c128((const char*)ckpts + ab * dim * slot, s->dtype, psi, dim, st));
+    }
+    QS_TRY(gate_matrix(c, g, params, U));
+    dagger(U, g.nlocs);
+    if (g.param >= 0 && g.kind != QS_GATE_MATRIX) {
+      double cfac = 0;
+      QS_TRY(generator(g, G, &cfac));
+      int rc;
+      switch (g.nlocs) {
+        case 1: rc = launch_adjoint_param<1>(psi, lam, n, g, G, U, partials, dgrad, cfac, st); break;
+        case 2: rc = launch_adjoint_param<2>(psi, lam, n, g, G, U, partials, dgrad, cfac, st); break;
+        case 3: rc = launch_adjoint_param<3>(psi, lam, n, g, G, U, partials, dgrad, cfac, st); break;
+        default: rc = fail(QS_EUNSUPPORTED, "parameterised gate on %d targets", g.nlocs);
+      }
+      QS_TRY(rc);
+    } else {
+      Plan p;
+      QS_TRY(plan_gate(U.data(), g.nlocs, g.locs, g.ctrl_mask, g.ctrl_vals, &p));
+      QS_TRY(launch_plan_on(psi, QS_C128, n, 1, dim, p, s));
+      QS_TRY(launch_plan_on(lam, QS_C128, n, 1, dim, p, s));
+    }
+  }
+  QS_CUDA(cudaMemcpyAsync(host_grad, dgrad, sizeof(double) * c->nparams, cudaMemcpyDeviceToHost, st));
+  QS_CUDA(cudaStreamSynchronize(st));
+  return QS_OK;
+}
+
+}  // namespace qs

@@ -1,0 +1,212 @@
+// common.cuh -- internal types and device helpers of the sm_103a state-vector
+// library.  Included only by this library's .cu files.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/qsim.h"
+
+namespace qs {
+
+using cd = std::complex<double>;
+
+// ------------------------------------------------------------------ errors
+
+void set_error(const char* fmt, ...);
+int fail(int code, const char* fmt, ...);
+
+#define QS_CUDA(call)                                                                 \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return ::qs::fail(QS_EDEVICE, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),  \
+                        __FILE__, __LINE__);                                          \
+  } while (0)
+
+#define QS_LAUNCHED()                                                                 \
+  do {                                                                                \
+    cudaError_t e_ = cudaGetLastError();                                              \
+    if (e_ != cudaSuccess)                                                            \
+      return ::qs::fail(QS_EDEVICE, "kernel launch: %s (%s:%d)", cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                          \
+  } while (0)
+
+#define QS_TRY(expr)              \
+  do {                            \
+    int rc_ = (expr);             \
+    if (rc_ != QS_OK) return rc_; \
+  } while (0)
+
+// ------------------------------------------------------------------ index spec
+//
+// A launch walks "items": item = r * 2^item_log2 + j, register r, local index
+// j over the free bits.  The amplitude index of item j inside its register is
+// deposit(j): zeros inserted at the fixed bit positions (ascending), then the
+// fixed bits' required values OR'ed in.
+
+constexpr int kMaxFix = 48;
+
+struct IdxSpec {
+  int nfix;
+  int item_log2;              // items per register = 2^item_log2
+  uint64_t set_bits;          // required values of the fixed bits
+  uint64_t reg_stride;        // amplitudes per register
+  uint8_t fix[kMaxFix];       // fixed bit positions, ascending
+};
+
+__device__ __forceinline__ uint64_t deposit(uint64_t j, const IdxSpec& s) {
+  for (int q = 0; q < s.nfix; ++q) {
+    const int p = s.fix[q];
+    const uint64_t lo = j & ((1ull << p) - 1ull);
+    j = ((j >> p) << (p + 1)) | lo;
+  }
+  return j | s.set_bits;
+}
+
+__device__ __forceinline__ uint64_t item_index(uint64_t item, const IdxSpec& s) {
+  const uint64_t r = item >> s.item_log2;
+  const uint64_t j = item & ((1ull << s.item_log2) - 1ull);
+  return r * s.reg_stride + deposit(j, s);
+}
+
+// Builds an IdxSpec over a register of n qubits with the given fixed-bit mask.
+int make_idx(int n, uint64_t fixed_mask, uint64_t set_bits, IdxSpec* out);
+
+// ------------------------------------------------------------------ complex math
+
+template <typename R> struct C2;
+template <> struct C2<float> { using T = float2; };
+template <> struct C2<double> { using T = double2; };
+
+template <typename R> using c2_t = typename C2<R>::T;
+
+template <typename T> __device__ __forceinline__ T cmk(decltype(T::x) a, decltype(T::x) b) {
+  T r; r.x = a; r.y = b; return r;
+}
+
+// acc + a * b (complex), FMA-contracted
+template <typename T> __device__ __forceinline__ T cfma(T a, T b, T acc) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+  return acc;
+}
+template <typename T> __device__ __forceinline__ T cmul(T a, T b) {
+  T r;
+  r.x = fma(a.x, b.x, -a.y * b.y);
+  r.y = fma(a.x, b.y, a.y * b.x);
+  return r;
+}
+
+// two consecutive amplitudes (bit 0 = 0, 1) as one vector access
+__device__ __forceinline__ void ld_pair(const float2* p, float2& a0, float2& a1) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a0 = make_float2(v.x, v.y);
+  a1 = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void st_pair(float2* p, float2 a0, float2 a1) {
+  *reinterpret_cast<float4*>(p) = make_float4(a0.x, a0.y, a1.x, a1.y);
+}
+__device__ __forceinline__ void ld_pair(const double2* p, double2& a0, double2& a1) {
+  a0 = p[0];
+  a1 = p[1];
+}
+__device__ __forceinline__ void st_pair(double2* p, double2 a0, double2 a1) {
+  p[0] = a0;
+  p[1] = a1;
+}
+
+// ------------------------------------------------------------------ host-side objects
+
+struct Workspace {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace qs
+
+struct qs_state {
+  int dtype = QS_C64;
+  int nreg = 0;
+  bool uniform = true;               // every register has the same n
+  std::vector<int> nq;               // qubits per register
+  std::vector<int64_t> off;          // element offsets, nreg + 1
+  void* data = nullptr;              // device amplitudes
+  size_t bytes = 0;
+  bool owns = false;
+  cudaStream_t stream = nullptr;
+  qs::Workspace ws;                  // reduction scratch, grown on demand
+};
+
+struct qs_circuit {
+  int nqubits = 0;
+  int nparams = 0;
+  std::vector<qs_gate_desc> gates;
+  std::vector<qs::cd> mats;
+};
+
+struct qs_observable {
+  std::vector<qs_pauli_term> terms;
+};
+
+namespace qs {
+
+// grow a workspace (stream-ordered free of the old buffer is not needed: we
+// synchronise the stream before replacing it)
+int ensure_ws(qs_state* s, Workspace& w, size_t bytes);
+
+size_t amp_bytes(int dtype);
+
+// ------------------------------------------------------------------ gate plans
+
+enum OpClass {
+  OP_NOP = 0,
+  OP_DIAG1,     // amplitude *= (bit t ? d1 : d0) over the fixed-bit subspace (t < 0: d0)
+  OP_SWAP1,     // a <-> b (pure X)
+  OP_PERM1,     // a' = u01 b, b' = u10 a
+  OP_DENSE1,    // [a'; b'] = U [a; b]
+  OP_DIAGK,     // amplitude *= d[m], m = gathered target bits
+  OP_PERMK,     // y[m] = v[m] x[perm[m]]
+  OP_DENSEK     // y = U x over 2^k tuples
+};
+
+struct Plan {
+  OpClass op = OP_NOP;
+  int k = 0;
+  int locs[QS_MAXK] = {0};
+  uint64_t ctrl_mask = 0, ctrl_vals = 0;
+  // 1-qubit forms
+  int t = -1;                       // target (DIAG1: -1 = uniform factor)
+  uint64_t mask = 0, vals = 0;      // fixed subspace for DIAG1
+  cd d0 = 1, d1 = 1;
+  cd u[4];
+  // k-qubit forms (row-major 2^k x 2^k; perm / diag tables)
+  std::vector<cd> U;
+  int perm[1 << QS_MAXK];
+  cd pv[1 << QS_MAXK];
+};
+
+// classify a 2^k x 2^k matrix with controls into a kernel plan
+int plan_gate(const cd* U, int k, const int* locs, uint64_t ctrl_mask, uint64_t ctrl_vals, Plan* p);
+
+// launch a plan on every register of s (uniform: one launch; uneven: per register)
+int launch_plan(qs_state* s, const Plan& p);
+// launch a plan on an explicit single-register buffer (used by the adjoint)
+int launch_plan_on(void* data, int dtype, int n, int nreg, int64_t reg_stride, const Plan& p,
+                   qs_state* owner);
+
+// gate matrices (FP64, row-major), generators and daggers
+int named_matrix(int kind, int k, const int32_t* paulis, double theta, std::vector<cd>& U);
+int gate_matrix(const qs_circuit* c, const qs_gate_desc& g, const double* params, std::vector<cd>& U);
+void dagger(std::vector<cd>& U, int k);
+void pauli_string(int k, const int32_t* paulis, std::vector<cd>& S);
+int validate_gate(int n, int k, const int32_t* locs, uint64_t ctrl_mask);
+
+}  // namespace qs

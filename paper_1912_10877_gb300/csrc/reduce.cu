@@ -1,0 +1,415 @@
+// reduce.cu -- expectation values, lambda = O psi, measurement sampling, reset
+// and collapse (sm_103a).
+//
+// expect (Sec. "Forward Mode"): O = sum_t c_t P_t with P_t a Pauli string.
+// For a basis state, P|i> = i^{nY} (-1)^{popc(i & z)} |i ^ x>, so
+// <psi|P|psi> = sum_i ph(i) conj(psi_{i^x}) psi_i.  Terms are grouped by their
+// x mask; one streaming pass per group reads each amplitude (or each pair
+// (i, i^x) once, counting it twice) and accumulates every term of the group in
+// FP64.  Per-block partial sums go to scratch memory and a second kernel folds
+// them in a fixed order, so results are reproducible run to run.
+//
+// measure (Sec. "Instructions on Quantum Registers"): the deterministic
+// contract of qsim.h -- FP64 probabilities with separately rounded multiply
+// and add, left folds over level-0 blocks of 1024 probabilities and level-1
+// blocks of 1024 level-0 sums, and a three-level walk per shot.
+#include <cmath>
+#include <cstring>
+#include <map>
+
+#include "common.cuh"
+
+namespace qs {
+
+constexpr int kRedThreads = 256;
+constexpr int kGroupTerms = 16;   // terms of one x-mask group handled per launch
+constexpr int kObsChunk = 64;     // terms per lambda = O psi launch
+
+struct TermGroup {
+  int nt;
+  int item_log2;
+  int h;                 // highest bit of x (-1 if x == 0)
+  uint64_t x;
+  uint64_t z[kGroupTerms];
+  int ny[kGroupTerms];   // number of Y factors mod 4
+};
+
+__device__ __forceinline__ double2 ld_amp(const float2* p, uint64_t i) {
+  const float2 v = p[i];
+  return make_double2((double)v.x, (double)v.y);
+}
+__device__ __forceinline__ double2 ld_amp(const double2* p, uint64_t i) { return p[i]; }
+
+__device__ __forceinline__ double term_value(int ny, double s, double zr, double zi) {
+  switch (ny & 3) {
+    case 0: return s * zr;
+    case 1: return -s * zi;
+    case 2: return -s * zr;
+    default: return s * zi;
+  }
+}
+
+// grid (blocks_per_reg, nreg); partials[(reg * nt_total + term_base + t) * nblk + block]
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+k_expect_group(const T* __restrict__ psi, uint64_t reg_stride, TermGroup g, double* __restrict__ partials,
+               int nt_total, int term_base) {
+  const int nblk = gridDim.x;
+  const uint64_t r = blockIdx.y;
+  const T* p = psi + r * reg_stride;
+  const uint64_t items = 1ull << g.item_log2;
+  double acc[kGroupTerms];
+#pragma unroll
+  for (int t = 0; t < kGroupTerms; ++t) acc[t] = 0.0;
+  for (uint64_t j = (uint64_t)blockIdx.x * kRedThreads + threadIdx.x; j < items;
+       j += (uint64_t)nblk * kRedThreads) {
+    uint64_t i = j;
+    if (g.h >= 0) i = ((j >> g.h) << (g.h + 1)) | (j & ((1ull << g.h) - 1ull));
+    const double2 a = ld_amp(p, i);
+    double zr, zi;
+    if (g.h >= 0) {
+      const double2 b = ld_amp(p, i ^ g.x);
+      zr = b.x * a.x + b.y * a.y;
+      zi = b.x * a.y - b.y * a.x;
+    } else {
+      zr = a.x * a.x + a.y * a.y;
+      zi = 0.0;
+    }
+#pragma unroll
+    for (int t = 0; t < kGroupTerms; ++t) {
+      if (t < g.nt) {
+        const double s = (__popcll(i & g.z[t]) & 1) ? -1.0 : 1.0;
+        acc[t] += term_value(g.ny[t], s, zr, zi);
+      }
+    }
+  }
+  __shared__ double red[kRedThreads / 32][kGroupTerms];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < kGroupTerms; ++t) {
+    double v = acc[t];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][t] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < g.nt) {
+    double v = 0.0;
+    for (int w = 0; w < kRedThreads / 32; ++w) v += red[w][threadIdx.x];
+    const double f = g.h >= 0 ? 2.0 : 1.0;
+    partials[((r * nt_total) + term_base + threadIdx.x) * nblk + blockIdx.x] = f * v;
+  }
+}
+
+// one thread per register: fold block partials per term (pairwise in place
+// would need scratch; a left fold over <= a few thousand FP64 partials is
+// exact enough and deterministic), then sum c_t * v_t in term order.
+__global__ void k_expect_final(const double* __restrict__ partials, int nblk, int nt_total,
+                               const double* __restrict__ coeff, int nreg, double* __restrict__ out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nreg) return;
+  double total = 0.0;
+  for (int t = 0; t < nt_total; ++t) {
+    const double* q = partials + ((size_t)r * nt_total + t) * nblk;
+    double v = 0.0;
+    for (int b = 0; b < nblk; ++b) v += q[b];
+    total += coeff[t] * v;
+  }
+  out[r] = total;
+}
+
+struct ObsChunk {
+  int nt;
+  uint64_t x[kObsChunk];
+  uint64_t z[kObsChunk];
+  int ny[kObsChunk];
+  double c[kObsChunk];
+};
+
+// lam (+)= sum_t c_t P_t psi, FP64 (complex128 buffers), one amplitude per thread
+__global__ void __launch_bounds__(256)
+k_apply_obs(const double2* __restrict__ psi, double2* __restrict__ lam, uint64_t dim, int accumulate,
+            const __grid_constant__ ObsChunk o) {
+  const uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x;
+  if (i >= dim) return;
+  double2 acc = accumulate ? lam[i] : make_double2(0.0, 0.0);
+  for (int t = 0; t < o.nt; ++t) {
+    const uint64_t j = i ^ o.x[t];          // (P psi)_i = ph(j) psi_j, j = i ^ x
+    const double2 v = psi[j];
+    const double s = (__popcll(j & o.z[t]) & 1) ? -o.c[t] : o.c[t];
+    double re, im;
+    switch (o.ny[t] & 3) {
+      case 0: re = v.x; im = v.y; break;
+      case 1: re = -v.y; im = v.x; break;   // * i
+      case 2: re = -v.x; im = -v.y; break;  // * -1
+      default: re = v.y; im = -v.x; break;  // * -i
+    }
+    acc.x += s * re;
+    acc.y += s * im;
+  }
+  lam[i] = acc;
+}
+
+// ------------------------------------------------------------------ host side
+
+static int grouped(const qs_observable* o, std::vector<std::pair<uint64_t, std::vector<int>>>& groups) {
+  std::map<uint64_t, std::vector<int>> m;
+  for (int t = 0; t < (int)o->terms.size(); ++t) m[o->terms[t].x_mask].push_back(t);
+  groups.assign(m.begin(), m.end());
+  return QS_OK;
+}
+
+// expectation of registers stored at `data` (uniform: nreg x 2^n, else one register)
+int expect_raw(const void* data, int dtype, int n, int nreg, const qs_observable* o, qs_state* ws_owner,
+               double* host_out) {
+  cudaStream_t st = ws_owner->stream;
+  const int nt_total = (int)o->terms.size();
+  for (const auto& t : o->terms) {
+    if (n < 64 && ((t.x_mask | t.z_mask) >> n)) return fail(QS_EINVAL, "observable acts on a qubit >= n=%d", n);
+  }
+  std::vector<std::pair<uint64_t, std::vector<int>>> groups;
+  grouped(o, groups);
+  const uint64_t dim = 1ull << n;
+  int nblk = (int)std::min<uint64_t>(std::max<uint64_t>(1, dim / (kRedThreads * 8)),
+                                     std::max(1, 1216 / std::max(1, nreg)));
+  const size_t part_bytes = sizeof(double) * (size_t)nreg * std::max(1, nt_total) * nblk;
+  const size_t coeff_off = (part_bytes + 255) / 256 * 256;
+  const size_t out_off = coeff_off + (sizeof(double) * std::max(1, nt_total) + 255) / 256 * 256;
+  QS_TRY(ensure_ws(ws_owner, ws_owner->ws, out_off + sizeof(double) * nreg));
+  double* partials = (double*)ws_owner->ws.ptr;
+  double* dcoeff = (double*)((char*)ws_owner->ws.ptr + coeff_off);
+  double* dev_out = (double*)((char*)ws_owner->ws.ptr + out_off);
+  // coefficients in the global term order of the partials layout below
+  std::vector<double> coeff;
+  std::vector<int> order;
+  for (auto& g : groups)
+    for (int t : g.second) { order.push_back(t); coeff.push_back(o->terms[t].coeff); }
+  if (nt_total > 0)
+    QS_CUDA(cudaMemcpyAsync(dcoeff, coeff.data(), sizeof(double) * nt_total, cudaMemcpyHostToDevice, st));
+  int base = 0;
+  for (auto& g : groups) {
+    const auto& ids = g.second;
+    for (size_t c0 = 0; c0 < ids.size(); c0 += kGroupTerms) {
+      TermGroup tg;
+      memset(&tg, 0, sizeof(tg));
+      tg.x = g.first;
+      tg.h = g.first ? 63 - __builtin_clzll(g.first) : -1;
+      tg.item_log2 = g.first ? n - 1 : n;
+      tg.nt = (int)std::min<size_t>(kGroupTerms, ids.size() - c0);
+      for (int t = 0; t < tg.nt; ++t) {
+        const auto& term = o->terms[ids[c0 + t]];
+        tg.z[t] = term.z_mask;
+        tg.ny[t] = __builtin_popcountll(term.x_mask & term.z_mask) & 3;
+      }
+      dim3 grid(nblk, nreg);
+      if (dtype == QS_C64)
+        k_expect_group<float2><<<grid, kRedThreads, 0, st>>>((const float2*)data, dim, tg, partials, nt_total, base);
+      else
+        k_expect_group<double2><<<grid, kRedThreads, 0, st>>>((const double2*)data, dim, tg, partials, nt_total, base);
+      QS_LAUNCHED();
+      base += tg.nt;
+    }
+  }
+  if (nt_total == 0) {
+    QS_CUDA(cudaMemsetAsync(dev_out, 0, sizeof(double) * nreg, st));
+  } else {
+    k_expect_final<<<(nreg + 127) / 128, 128, 0, st>>>(partials, nblk, nt_total, dcoeff, nreg, dev_out);
+    QS_LAUNCHED();
+  }
+  QS_CUDA(cudaMemcpyAsync(host_out, dev_out, sizeof(double) * nreg, cudaMemcpyDeviceToHost, st));
+  QS_CUDA(cudaStreamSynchronize(st));
+  return QS_OK;
+}
+
+int apply_observable_c128(const double2* psi, double2* lam, int n, const qs_observable* o, cudaStream_t st) {
+  const uint64_t dim = 1ull << n;
+  const int nt = (int)o->terms.size();
+  if (nt == 0) {
+    QS_CUDA(cudaMemsetAsync(lam, 0, sizeof(double2) * dim, st));
+    return QS_OK;
+  }
+  for (int c0 = 0; c0 < nt; c0 += kObsChunk) {
+    ObsChunk ch;
+    memset(&ch, 0, sizeof(ch));
+    ch.nt = std::min(kObsChunk, nt - c0);
+    for (int t = 0; t < ch.nt; ++t) {
+      const auto& term = o->terms[c0 + t];
+      ch.x[t] = term.x_mask;
+      ch.z[t] = term.z_mask;
+      ch.ny[t] = __builtin_popcountll(term.x_mask & term.z_mask) & 3;
+      ch.c[t] = term.coeff;
+    }
+    k_apply_obs<<<(unsigned)((dim + 255) / 256), 256, 0, st>>>(psi, lam, dim, c0 > 0, ch);
+    QS_LAUNCHED();
+  }
+  return QS_OK;
+}
+
+// ------------------------------------------------------------------ sampling
+
+constexpr int kF = 1024;
+
+template <typename T>
+__device__ __forceinline__ double prob(const T* p, uint64_t i) {
+  const double2 a = ld_amp(p, i);
+  return __dadd_rn(__dmul_rn(a.x, a.x), __dmul_rn(a.y, a.y));
+}
+
+template <typename T>
+__global__ void k_level0(const T* __restrict__ psi, uint64_t dim, uint64_t nb0, double* __restrict__ s0) {
+  const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb0) return;
+  const uint64_t lo = b * kF, hi = lo + kF < dim ? lo + kF : dim;
+  double a = prob(psi, lo);
+  for (uint64_t i = lo + 1; i < hi; ++i) a = __dadd_rn(a, prob(psi, i));
+  s0[b] = a;
+}
+
+__global__ void k_level1(const double* __restrict__ s0, uint64_t nb0, uint64_t nb1, double* __restrict__ s1) {
+  const uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nb1) return;
+  const uint64_t lo = c * kF, hi = lo + kF < nb0 ? lo + kF : nb0;
+  double a = s0[lo];
+  for (uint64_t b = lo + 1; b < hi; ++b) a = __dadd_rn(a, s0[b]);
+  s1[c] = a;
+}
+
+// the walk of the contract: first j whose running sum exceeds t, else the last
+// positive value, else the last; acc carries the exclusive prefix
+template <typename F>
+__device__ uint64_t walk(F value, uint64_t len, double t, double& acc) {
+  double a = acc, a_last = acc;
+  int64_t last = -1;
+  for (uint64_t j = 0; j < len; ++j) {
+    const double v = value(j);
+    const double nxt = __dadd_rn(a, v);
+    if (nxt > t) { acc = a; return j; }
+    if (v > 0.0) { last = (int64_t)j; a_last = a; }
+    a = nxt;
+  }
+  if (last >= 0) { acc = a_last; return (uint64_t)last; }
+  return len - 1;
+}
+
+template <typename T>
+__global__ void k_sample(const T* __restrict__ psi, uint64_t dim, const double* __restrict__ s0, uint64_t nb0,
+                         const double* __restrict__ s1, uint64_t nb1, const double* __restrict__ u, int nshots,
+                         int64_t* __restrict__ out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nshots) return;
+  double total = s1[0];
+  for (uint64_t c = 1; c < nb1; ++c) total = __dadd_rn(total, s1[c]);
+  const double t = __dmul_rn(u[s], total);
+  double acc = 0.0;
+  const uint64_t c = walk([&](uint64_t j) { return s1[j]; }, nb1, t, acc);
+  const uint64_t b0 = c * kF, b1 = b0 + kF < nb0 ? b0 + kF : nb0;
+  const uint64_t b = b0 + walk([&](uint64_t j) { return s0[b0 + j]; }, b1 - b0, t, acc);
+  const uint64_t i0 = b * kF, i1 = i0 + kF < dim ? i0 + kF : dim;
+  out[s] = (int64_t)(i0 + walk([&](uint64_t j) { return prob(psi, i0 + j); }, i1 - i0, t, acc));
+}
+
+template <typename T>
+__global__ void k_collapse_scale(T* psi, int64_t x, double2* keep) {
+  const double2 a = ld_amp(psi, (uint64_t)x);
+  const double r = sqrt(a.x * a.x + a.y * a.y);
+  *keep = r > 0.0 ? make_double2(a.x / r, a.y / r) : make_double2(1.0, 0.0);
+}
+
+__device__ __forceinline__ void st_amp(float2* p, uint64_t i, double2 v) { p[i] = make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ void st_amp(double2* p, uint64_t i, double2 v) { p[i] = v; }
+
+template <typename T>
+__global__ void k_collapse_write(T* psi, uint64_t dim, int64_t x, const double2* keep) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= dim) return;
+  st_amp(psi, i, i == (uint64_t)x ? *keep : make_double2(0.0, 0.0));
+}
+
+// one register at `data` with 2^n amplitudes
+int measure_one(void* data, int dtype, int n, const double* host_u, int nshots, int64_t* host_out,
+                int collapse, qs_state* owner) {
+  cudaStream_t st = owner->stream;
+  const uint64_t dim = 1ull << n;
+  const uint64_t nb0 = (dim + kF - 1) / kF, nb1 = (nb0 + kF - 1) / kF;
+  const size_t need = sizeof(double) * (nb0 + nb1) + sizeof(double) * nshots + sizeof(int64_t) * nshots + 64;
+  QS_TRY(ensure_ws(owner, owner->ws, need + 256));
+  char* w = (char*)owner->ws.ptr;
+  double* s0 = (double*)w;
+  double* s1 = s0 + nb0;
+  double* du = s1 + nb1;
+  int64_t* dout = (int64_t*)(du + nshots);
+  double2* keep = (double2*)(((uintptr_t)(dout + nshots) + 15) & ~(uintptr_t)15);
+  QS_CUDA(cudaMemcpyAsync(du, host_u, sizeof(double) * nshots, cudaMemcpyHostToDevice, st));
+  if (dtype == QS_C64) {
+    k_level0<float2><<<(unsigned)((nb0 + 127) / 128), 128, 0, st>>>((const float2*)data, dim, nb0, s0);
+  } else {
+    k_level0<double2><<<(unsigned)((nb0 + 127) / 128), 128, 0, st>>>((const double2*)data, dim, nb0, s0);
+  }
+  QS_LAUNCHED();
+  k_level1<<<(unsigned)((nb1 + 127) / 128), 128, 0, st>>>(s0, nb0, nb1, s1);
+  QS_LAUNCHED();
+  if (dtype == QS_C64)
+    k_sample<float2><<<(nshots + 127) / 128, 128, 0, st>>>((const float2*)data, dim, s0, nb0, s1, nb1, du, nshots, dout);
+  else
+    k_sample<double2><<<(nshots + 127) / 128, 128, 0, st>>>((const double2*)data, dim, s0, nb0, s1, nb1, du, nshots, dout);
+  QS_LAUNCHED();
+  QS_CUDA(cudaMemcpyAsync(host_out, dout, sizeof(int64_t) * nshots, cudaMemcpyDeviceToHost, st));
+  QS_CUDA(cudaStreamSynchronize(st));
+  if (collapse) {
+    const int64_t x = host_out[0];
+    if (dtype == QS_C64) {
+      k_collapse_scale<float2><<<1, 1, 0, st>>>((float2*)data, x, keep);
+      k_collapse_write<float2><<<(unsigned)((dim + 255) / 256), 256, 0, st>>>((float2*)data, dim, x, keep);
+    } else {
+      k_collapse_scale<double2><<<1, 1, 0, st>>>((double2*)data, x, keep);
+      k_collapse_write<double2><<<(unsigned)((dim + 255) / 256), 256, 0, st>>>((double2*)data, dim, x, keep);
+    }
+    QS_LAUNCHED();
+    QS_CUDA(cudaStreamSynchronize(st));
+  }
+  return QS_OK;
+}
+
+// ------------------------------------------------------------------ reset / promote
+
+__global__ void k_set_ones(char* data, int dtype, const int64_t* __restrict__ pos, int count) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= count) return;
+  if (dtype == QS_C64) ((float2*)data)[pos[r]] = make_float2(1.f, 0.f);
+  else ((double2*)data)[pos[r]] = make_double2(1.0, 0.0);
+}
+
+int reset_basis(qs_state* s, const uint64_t* host_basis) {
+  cudaStream_t st = s->stream;
+  std::vector<int64_t> pos(s->nreg);
+  for (int r = 0; r < s->nreg; ++r) {
+    const uint64_t x = host_basis ? host_basis[r] : 0;
+    if (s->nq[r] < 64 && (x >> s->nq[r])) return fail(QS_EINVAL, "basis index %llu out of range for register %d",
+                                                     (unsigned long long)x, r);
+    pos[r] = s->off[r] + (int64_t)x;
+  }
+  QS_TRY(ensure_ws(s, s->ws, sizeof(int64_t) * s->nreg));
+  QS_CUDA(cudaMemsetAsync(s->data, 0, s->bytes, st));
+  QS_CUDA(cudaMemcpyAsync(s->ws.ptr, pos.data(), sizeof(int64_t) * s->nreg, cudaMemcpyHostToDevice, st));
+  k_set_ones<<<(s->nreg + 127) / 128, 128, 0, st>>>((char*)s->data, s->dtype, (const int64_t*)s->ws.ptr, s->nreg);
+  QS_LAUNCHED();
+  return QS_OK;
+}
+
+__global__ void k_promote(const float2* __restrict__ in, double2* __restrict__ out, uint64_t dim) {
+  const uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x;
+  if (i >= dim) return;
+  const float2 v = in[i];
+  out[i] = make_double2((double)v.x, (double)v.y);
+}
+
+int promote_to_c128(const void* in, int dtype, double2* out, uint64_t dim, cudaStream_t st) {
+  if (dtype == QS_C128) {
+    QS_CUDA(cudaMemcpyAsync(out, in, sizeof(double2) * dim, cudaMemcpyDeviceToDevice, st));
+    return QS_OK;
+  }
+  k_promote<<<(unsigned)((dim + 255) / 256), 256, 0, st>>>((const float2*)in, out, dim);
+  QS_LAUNCHED();
+  return QS_OK;
+}
+
+}  // namespace qs

@@ -1,0 +1,280 @@
+"""Python binding of the GB300 state-vector library (include/qsim.h).
+
+PyTorch provides device memory and streams only; every step of the simulation
+runs in libqsim.so's CUDA kernels.  Gate lists use the ``workloads.Gate``
+record (name, locs, ctrl_locs, ctrl_vals, param, theta, paulis, matrix); this
+module only marshals them into ``qs_gate_desc`` arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+_TORCH_DTYPE = {N.QS_C64: torch.complex64, N.QS_C128: torch.complex128}
+_NP_DTYPE = {N.QS_C64: np.complex64, N.QS_C128: np.complex128}
+
+
+def _dtype_code(dtype) -> int:
+    if dtype in (N.QS_C64, torch.complex64, np.complex64, "c64", "complex64"):
+        return N.QS_C64
+    if dtype in (N.QS_C128, torch.complex128, np.complex128, "c128", "complex128"):
+        return N.QS_C128
+    raise ValueError(f"unsupported dtype {dtype}")
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class State:
+    """A register or a batch of registers in device memory owned by a torch tensor."""
+
+    def __init__(self, nqubits, dtype=torch.complex64, nbatch: int = 1, device="cuda", stream=None):
+        L = N.lib()
+        self.dtype_code = _dtype_code(dtype)
+        if isinstance(nqubits, (list, tuple, np.ndarray)):
+            counts = [int(x) for x in nqubits]
+        else:
+            counts = [int(nqubits)] * int(nbatch)
+        self.counts = counts
+        self.nreg = len(counts)
+        self.uniform = len(set(counts)) == 1
+        self.device = torch.device(device)
+        if self.device.type != "cuda":
+            raise ValueError("State lives on a CUDA device")
+        total = sum(1 << c for c in counts)
+        self.buffer = torch.empty(total, dtype=_TORCH_DTYPE[self.dtype_code], device=self.device)
+        self.stream = stream
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            N.check(L.qs_batch_create(self.nreg, N.i32(counts), self.dtype_code,
+                                      ctypes.c_void_p(self.buffer.data_ptr()), _stream_ptr(stream),
+                                      ctypes.byref(h)))
+        self.handle = h
+        self.offsets = np.cumsum([0] + [1 << c for c in counts])
+
+    # -- lifetime -----------------------------------------------------------
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            N.lib().qs_state_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nqubits(self) -> int:
+        if not self.uniform:
+            raise ValueError("uneven batch: use .counts")
+        return self.counts[0]
+
+    def sync_stream(self, stream=None):
+        N.check(N.lib().qs_state_set_stream(self.handle, _stream_ptr(stream)))
+        self.stream = stream
+
+    # -- data -----------------------------------------------------------------
+    def register(self, r: int) -> torch.Tensor:
+        return self.buffer[int(self.offsets[r]):int(self.offsets[r + 1])]
+
+    def tensor(self) -> torch.Tensor:
+        """[nbatch, 2^n] view (uniform batches) of the amplitudes."""
+        return self.buffer.view(self.nreg, -1)
+
+    def reset(self, basis=None):
+        if basis is None:
+            N.check(N.lib().qs_state_reset(self.handle, None))
+        else:
+            b = np.ascontiguousarray(np.broadcast_to(np.asarray(basis, dtype=np.uint64), (self.nreg,)))
+            N.check(N.lib().qs_state_reset(self.handle, b.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+        return self
+
+    def upload(self, amps: np.ndarray):
+        a = np.ascontiguousarray(np.ravel(amps), dtype=_NP_DTYPE[self.dtype_code])
+        if a.size != int(self.offsets[-1]):
+            raise ValueError("amplitude count does not match the state")
+        N.check(N.lib().qs_state_upload(self.handle, a.ctypes.data))
+        return self
+
+    def numpy(self) -> np.ndarray:
+        out = np.empty(int(self.offsets[-1]), dtype=_NP_DTYPE[self.dtype_code])
+        N.check(N.lib().qs_state_download(self.handle, out.ctypes.data))
+        return out
+
+    # -- instructions ---------------------------------------------------------
+    def apply(self, g, params=None):
+        """instruct! one gate record (workloads.Gate)."""
+        cl = N.i32(g.ctrl_locs)
+        cv = N.i32(g.ctrl_vals)
+        locs = N.i32(g.locs)
+        if g.name == "MATRIX":
+            m = np.ascontiguousarray(g.matrix, dtype=np.complex128).view(np.float64)
+            N.check(N.lib().qs_apply_gate(self.handle, N.dptr(m), len(g.locs), locs,
+                                          len(g.ctrl_locs), cl, cv))
+        else:
+            theta = 0.0
+            if g.param is not None:
+                theta = float(params[g.param])
+            elif g.theta is not None:
+                theta = float(g.theta)
+            paulis = N.i32([N.PAULI_CODE[p] for p in g.paulis] if g.paulis else [])
+            N.check(N.lib().qs_apply_named(self.handle, N.GATE_KIND[g.name], len(g.locs), locs, paulis,
+                                           len(g.ctrl_locs), cl, cv, theta))
+        return self
+
+    def apply_matrix(self, U, locs, ctrl_locs=(), ctrl_vals=()):
+        m = np.ascontiguousarray(U, dtype=np.complex128).view(np.float64)
+        N.check(N.lib().qs_apply_gate(self.handle, N.dptr(m), len(locs), N.i32(locs), len(ctrl_locs),
+                                      N.i32(ctrl_locs), N.i32(ctrl_vals or [1] * len(ctrl_locs))))
+        return self
+
+    def apply_circuit(self, circuit: "Circuit", params=None, per_register=False):
+        p = _params_array(params, circuit.nparams * (self.nreg if per_register else 1))
+        N.check(N.lib().qs_apply_circuit(self.handle, circuit.handle, N.dptr(p), 1 if per_register else 0))
+        return self
+
+    def expect(self, obs: "Observable") -> np.ndarray:
+        out = np.zeros(self.nreg)
+        N.check(N.lib().qs_expect(self.handle, obs.handle, N.dptr(out)))
+        return out
+
+    def measure(self, u, collapse=False) -> np.ndarray:
+        """Sample basis indices with the given uniforms [nreg][nshots] in [0, 1)."""
+        u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(self.nreg, -1))
+        out = np.zeros(u.shape, dtype=np.int64)
+        N.check(N.lib().qs_measure(self.handle, N.dptr(u), u.shape[1],
+                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 1 if collapse else 0))
+        return out
+
+
+def _params_array(params, count):
+    if count == 0:
+        return np.zeros(1)
+    p = np.ascontiguousarray(np.ravel(np.asarray(params, dtype=np.float64)))
+    if p.size != count:
+        raise ValueError(f"expected {count} parameters, got {p.size}")
+    return p
+
+
+class Circuit:
+    """Immutable flat gate list (qs_circuit)."""
+
+    def __init__(self, gates, nqubits: int, nparams: int | None = None):
+        L = N.lib()
+        if nparams is None:
+            nparams = 1 + max([g.param for g in gates if g.param is not None], default=-1)
+        arr = (N.GateDesc * max(1, len(gates)))()
+        pool = []
+        off = 0
+        for i, g in enumerate(gates):
+            d = arr[i]
+            d.kind = N.GATE_KIND[g.name]
+            d.nlocs = len(g.locs)
+            for j, l in enumerate(g.locs):
+                d.locs[j] = l
+            if g.paulis:
+                for j, p in enumerate(g.paulis):
+                    d.paulis[j] = N.PAULI_CODE[p]
+            d.param = -1 if g.param is None else int(g.param)
+            d.theta = 0.0 if g.theta is None else float(g.theta)
+            cm = cv = 0
+            for l, v in zip(g.ctrl_locs, g.ctrl_vals):
+                cm |= 1 << l
+                if v:
+                    cv |= 1 << l
+            d.ctrl_mask, d.ctrl_vals = cm, cv
+            if g.name == "MATRIX":
+                m = np.ascontiguousarray(g.matrix, dtype=np.complex128).ravel()
+                d.mat_offset = off
+                pool.append(m)
+                off += m.size
+        mats = np.concatenate(pool) if pool else np.zeros(1, np.complex128)
+        mv = mats.view(np.float64)
+        h = ctypes.c_void_p()
+        N.check(L.qs_circuit_create(int(nqubits), arr, len(gates), N.dptr(mv), off, int(nparams), ctypes.byref(h)))
+        self.handle = h
+        self.nqubits = int(nqubits)
+        self.nparams = int(nparams)
+        self.ngates = len(gates)
+        self.gates = list(gates)
+
+    def checkpoint_count(self, every: int) -> int:
+        c = ctypes.c_int()
+        N.check(N.lib().qs_checkpoint_count(self.handle, int(every), ctypes.byref(c)))
+        return c.value
+
+    def __del__(self):
+        try:
+            if self.handle.value:
+                N.lib().qs_circuit_destroy(self.handle)
+                self.handle = ctypes.c_void_p()
+        except Exception:
+            pass
+
+
+class Observable:
+    """sum_t coeff_t P_t from terms [(coeff, ((loc, 'X'|'Y'|'Z'), ...)), ...]."""
+
+    def __init__(self, terms):
+        arr = (N.PauliTerm * max(1, len(terms)))()
+        for i, (c, ops) in enumerate(terms):
+            x = z = 0
+            for l, p in ops:
+                if p in ("X", "Y"):
+                    x |= 1 << int(l)
+                if p in ("Z", "Y"):
+                    z |= 1 << int(l)
+            arr[i].coeff, arr[i].x_mask, arr[i].z_mask = float(c), x, z
+        h = ctypes.c_void_p()
+        N.check(N.lib().qs_observable_create(arr, len(terms), ctypes.byref(h)))
+        self.handle = h
+        self.terms = list(terms)
+
+    def __del__(self):
+        try:
+            if self.handle.value:
+                N.lib().qs_observable_destroy(self.handle)
+                self.handle = ctypes.c_void_p()
+        except Exception:
+            pass
+
+
+def backward_work(nqubits: int, device="cuda") -> torch.Tensor:
+    b = ctypes.c_size_t()
+    N.check(N.lib().qs_backward_work_bytes(int(nqubits), ctypes.byref(b)))
+    return torch.empty(b.value, dtype=torch.uint8, device=device)
+
+
+def checkpoint_buffer(state: State, circuit: Circuit, every: int) -> torch.Tensor | None:
+    cnt = circuit.checkpoint_count(every)
+    if every <= 0 or cnt == 0:
+        return None
+    return torch.empty((cnt, state.buffer.numel()), dtype=state.buffer.dtype, device=state.buffer.device)
+
+
+def apply_circuit_ckpt(state: State, circuit: Circuit, params, every: int, ckpts: torch.Tensor | None):
+    p = _params_array(params, circuit.nparams)
+    ptr = ctypes.c_void_p(ckpts.data_ptr()) if ckpts is not None else None
+    N.check(N.lib().qs_apply_circuit_ckpt(state.handle, circuit.handle, N.dptr(p), int(every), ptr))
+    return state
+
+
+def backward(state: State, circuit: Circuit, params, obs: Observable, ckpt_every: int = 0,
+             ckpts: torch.Tensor | None = None, work: torch.Tensor | None = None):
+    """expect'(O, reg => circuit): (loss, grad) from the circuit's output state (left unchanged)."""
+    p = _params_array(params, circuit.nparams)
+    if work is None:
+        work = backward_work(state.nqubits, state.device)
+    grad = np.zeros(max(1, circuit.nparams))
+    loss = np.zeros(1)
+    ck = ctypes.c_void_p(ckpts.data_ptr()) if ckpts is not None else None
+    N.check(N.lib().qs_backward(state.handle, circuit.handle, N.dptr(p), obs.handle, int(ckpt_every), ck,
+                                ctypes.c_void_p(work.data_ptr()), N.dptr(grad), N.dptr(loss)))
+    return float(loss[0]), grad[:circuit.nparams]

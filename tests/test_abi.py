@@ -1,0 +1,112 @@
+"""CPU checks of the C ABI: the library loads, exports every entry point the
+header declares, its struct layouts match the binding, and host-only argument
+validation reports errors (no GPU needed, no kernel is launched)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "qsim.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(qs_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1912_10877_gb300 import build as B
+    B.build()
+    from paper_1912_10877_gb300 import _native as N
+    return N.lib()
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 20
+    from paper_1912_10877_gb300 import _native as N
+    for name in names:
+        assert hasattr(L, name), f"{name} not exported"
+        assert name in N.SIGNATURES, f"{name} has no binding signature"
+
+
+def test_struct_layout_matches_binding(tmp_path):
+    from paper_1912_10877_gb300 import _native as N
+    prog = tmp_path / "layout.c"
+    prog.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "qsim.h"\n'
+        "int main(void){\n"
+        ' printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(qs_gate_desc), offsetof(qs_gate_desc, param),'
+        " offsetof(qs_gate_desc, ctrl_mask), offsetof(qs_gate_desc, mat_offset), offsetof(qs_gate_desc, theta),"
+        " sizeof(qs_pauli_term));\n return 0; }\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    G = N.GateDesc
+    want = [ctypes.sizeof(G), G.param.offset, G.ctrl_mask.offset, G.mat_offset.offset, G.theta.offset,
+            ctypes.sizeof(N.PauliTerm)]
+    assert got == want
+
+
+def _circuit(L, gates, n, nparams=0):
+    from paper_1912_10877_gb300 import _native as N
+    arr = (N.GateDesc * max(1, len(gates)))(*gates)
+    h = ctypes.c_void_p()
+    rc = L.qs_circuit_create(n, arr, len(gates), None, 0, nparams, ctypes.byref(h))
+    return rc, h
+
+
+def test_host_validation_errors(L):
+    from paper_1912_10877_gb300 import _native as N
+    g = N.GateDesc()
+    g.kind, g.nlocs, g.param = N.GATE_KIND["X"], 1, -1
+    g.locs[0] = 3
+    rc, h = _circuit(L, [g], 3)  # loc 3 on a 3-qubit circuit
+    assert rc == N.QS_EINVAL and b"out of range" in L.qs_last_error()
+    g.locs[0] = 1
+    g.ctrl_mask = 1 << 1  # control equals target
+    rc, h = _circuit(L, [g], 3)
+    assert rc == N.QS_EINVAL and b"control" in L.qs_last_error()
+    g.ctrl_mask = 0
+    g.kind, g.param = N.GATE_KIND["H"], 0  # H takes no parameter
+    rc, h = _circuit(L, [g], 3, nparams=1)
+    assert rc == N.QS_EINVAL
+    g.kind = N.GATE_KIND["RX"]
+    rc, h = _circuit(L, [g], 3, nparams=1)
+    assert rc == N.QS_OK
+    cnt = ctypes.c_int()
+    assert L.qs_checkpoint_count(h, 1, ctypes.byref(cnt)) == 0 and cnt.value == 0
+    assert L.qs_circuit_destroy(h) == 0
+    b = ctypes.c_size_t()
+    assert L.qs_backward_work_bytes(20, ctypes.byref(b)) == 0 and b.value == 2 * 16 * (1 << 20)
+    nq = (ctypes.c_int32 * 3)(10, 12, 11)
+    assert L.qs_state_bytes(3, nq, N.QS_C64, ctypes.byref(b)) == 0 and b.value == 8 * (1024 + 4096 + 2048)
+    assert L.qs_state_bytes(1, (ctypes.c_int32 * 1)(0), N.QS_C64, ctypes.byref(b)) == N.QS_EINVAL
+    assert L.qs_state_bytes(1, nq, 7, ctypes.byref(b)) == N.QS_EINVAL
+
+
+def test_observable_handle_roundtrip(L):
+    from paper_1912_10877_gb300 import _native as N
+    terms = (N.PauliTerm * 2)()
+    terms[0].coeff, terms[0].z_mask = 1.0, 0b11
+    terms[1].coeff, terms[1].x_mask = 0.5, 0b1
+    h = ctypes.c_void_p()
+    assert L.qs_observable_create(terms, 2, ctypes.byref(h)) == 0
+    assert L.qs_observable_destroy(h) == 0
+    assert L.qs_observable_create(None, 2, ctypes.byref(h)) == N.QS_EINVAL
+
+
+def test_package_has_no_cpu_fallback():
+    # the product package never imports the oracle
+    pkg = os.path.join(ROOT, "paper_1912_10877_gb300")
+    for fn in os.listdir(pkg):
+        if fn.endswith(".py"):
+            src = open(os.path.join(pkg, fn)).read()
+            assert "import oracle" not in src and "from oracle" not in src, fn
