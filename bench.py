@@ -1,0 +1,406 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 state-vector hot path.
+
+Headline: single-gate HBM throughput at n = 25 qubits (2^25 amplitudes,
+complex64, Haar-random state from seed 0).  Suite: X, H, T, Rx(0.7) on every
+qubit, CNOT on (0,1), (11,12), (23,24), Toffoli on (0,1->2), (22,23->24); each
+gate applied 100 times.  One step = 100 rounds of the 105-gate suite (10,500
+single-gate launches; a gate's repetitions are interleaved with the rest of the
+suite so a small touched set never stays in L2).  value = algorithmic bytes /
+device time, where a gate's algorithmic bytes are read + write of every 32-byte
+sector holding at least one amplitude the gate changes.
+
+Extra keys: the same sweep in complex128, the roofline of the dominant kernel
+(live CUDA events per launch), clocks sampled during the timed region, e2e
+through host buffers, and the FP64 oracle timed on the host cores.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+N_QUBITS = 25
+REPS = 100
+SEED = 0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ byte model
+
+def touched_mask(g) -> int:
+    """Bits whose value is fixed for every amplitude the gate changes."""
+    m = 0
+    for c in g.ctrl_locs:
+        m |= 1 << c
+    if g.name in ("T", "TDG", "S", "SDG", "Z", "SHIFT"):  # diagonal with one non-unit entry
+        m |= 1 << g.locs[0]
+    return m
+
+
+def gate_bytes(g, n: int, amp_bytes: int) -> int:
+    """Read + write of every 32-byte sector holding at least one changed amplitude."""
+    per_sector = 32 // amp_bytes
+    low = per_sector.bit_length() - 1   # bits inside a sector
+    hi_fixed = bin(touched_mask(g) >> low).count("1")
+    sectors = 1 << (n - low - hi_fixed)
+    return 2 * 32 * sectors
+
+
+def kernel_class(g) -> str:
+    if g.name in ("X",):
+        return "swap1"
+    if g.name in ("T", "TDG", "S", "SDG", "Z", "SHIFT", "RZ"):
+        return "diag1"
+    return "dense1"
+
+
+# ------------------------------------------------------------------ clocks
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons, pw = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                pw.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ GPU sweep
+
+class Sweep:
+    """Pre-marshalled single-gate launches through the C ABI (qs_apply_named)."""
+
+    def __init__(self, st, suite):
+        from paper_1912_10877_gb300 import _native as N
+        self.N = N
+        self.L = N.lib()
+        self.h = st.handle
+        self.calls = []
+        for label, g in suite:
+            self.calls.append((N.GATE_KIND[g.name], len(g.locs), N.i32(g.locs), N.i32([]),
+                               len(g.ctrl_locs), N.i32(g.ctrl_locs), N.i32(g.ctrl_vals),
+                               float(g.theta or 0.0)))
+
+    def round(self, events=None, base=0):
+        f = self.L.qs_apply_named
+        h = self.h
+        for i, c in enumerate(self.calls):
+            rc = f(h, *c)
+            if rc:
+                self.N.check(rc)
+            if events is not None:
+                events[base + i].record()
+
+
+def run_sweep(dtype_name: str, steps: int, warmup: int, dev, with_events: bool):
+    import torch
+    from paper_1912_10877_gb300 import qsim
+    tdt = torch.complex64 if dtype_name == "c64" else torch.complex128
+    amp = 8 if dtype_name == "c64" else 16
+    n = N_QUBITS
+    suite = W.single_gate_suite(n)
+    psi = W.haar_state(n, SEED)
+    st = qsim.State(n, dtype=tdt)
+    st.upload(psi)
+    sw = Sweep(st, suite)
+    bytes_round = sum(gate_bytes(g, n, amp) for _, g in suite)
+    for _ in range(warmup):
+        for _ in range(REPS):
+            sw.round()
+    torch.cuda.synchronize()
+    nl = len(suite)
+    events = None
+    if with_events:
+        events = [torch.cuda.Event(enable_timing=True) for _ in range(REPS * nl + 1)]
+    per_class_t = {}
+    per_class_b = {}
+    t_total = 0.0
+    for s in range(steps):
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        start.record()
+        if events is not None:
+            events[0].record()
+        for r in range(REPS):
+            sw.round(events, 1 + r * nl)
+        end.record()
+        torch.cuda.synchronize()
+        t_total += start.elapsed_time(end) / 1e3
+        if events is not None:
+            for r in range(REPS):
+                for i, (_, g) in enumerate(suite):
+                    k = 1 + r * nl + i
+                    dt = events[k - 1].elapsed_time(events[k]) / 1e3
+                    c = kernel_class(g)
+                    per_class_t[c] = per_class_t.get(c, 0.0) + dt
+                    per_class_b[c] = per_class_b.get(c, 0) + gate_bytes(g, n, amp)
+    total_bytes = bytes_round * REPS * steps
+    res = {"seconds": t_total, "bytes": total_bytes, "gbs": total_bytes / t_total / 1e9,
+           "launches": nl * REPS * steps, "per_class": {}}
+    for c in per_class_t:
+        res["per_class"][c] = {"seconds": per_class_t[c], "gbs": per_class_b[c] / per_class_t[c] / 1e9,
+                               "launches": None}
+    res["state"] = st
+    res["psi"] = psi
+    res["sweep"] = sw
+    res["bytes_round"] = bytes_round
+    return res
+
+
+def run_e2e(res, steps: int):
+    """Same sweep through host buffers: pinned H2D of the input, the sweep, D2H of the result."""
+    import torch
+    from paper_1912_10877_gb300 import _native as N
+    st, sw = res["state"], res["sweep"]
+    host_in = torch.from_numpy(res["psi"].astype(np.complex64 if st.dtype_code == N.QS_C64 else np.complex128))
+    host_in = host_in.pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    L = N.lib()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        N.check(L.qs_state_upload(st.handle, ctypes.c_void_p(host_in.data_ptr())))
+        for _ in range(REPS):
+            sw.round()
+        N.check(L.qs_state_download(st.handle, ctypes.c_void_p(host_out.data_ptr())))
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    nb = host_in.numel() * host_in.element_size()
+    return {"value": res["bytes_round"] * REPS * steps / dt / 1e9, "unit": "GB/s",
+            "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
+
+
+def traffic_for(kernel: str):
+    """Per-launch DRAM bytes from a committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        entry = t[kernel]
+        src = open(os.path.join(ROOT, "paper_1912_10877_gb300", "csrc", entry["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest() != entry["sha256"]:
+            return None
+        return entry["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ CPU baseline (oracle)
+
+def oracle_baseline(budget_s: float = 15.0):
+    """The FP64 oracle, as it stands, applying suite gates to the n = 25 state on the host cores.
+    Sample: gates of the suite in order, one application each, until ~budget_s of CPU work."""
+    import oracle
+    n = N_QUBITS
+    suite = W.single_gate_suite(n)
+    psi = W.haar_state(n, SEED)
+    order = list(range(0, len(suite), 7)) + [i for i in range(len(suite)) if i % 7]
+    t0 = time.perf_counter()
+    nbytes = 0
+    done = 0
+    for i in order:
+        _, g = suite[i]
+        psi = oracle.apply_circuit(psi, n, [g])
+        nbytes += gate_bytes(g, n, 16)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": nbytes / dt / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} single-gate applications of the n=25 suite in FP64 (complex128 byte model), "
+                      f"{dt:.1f} s on {cores} OpenMP threads"}, dt
+
+
+# ------------------------------------------------------------------ main
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def main():
+    global REPS
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-c128", action="store_true")
+    ap.add_argument("--no-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--reps", type=int, default=REPS, help="repetitions per gate (profiling runs use 1)")
+    args = ap.parse_args()
+    REPS = args.reps
+    world, rank, local = dist_setup(args)
+    hbm_peak, peak_kind = peaks()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        import oracle
+        oracle.build()
+        vals = []
+        for _ in range(args.warmup):
+            oracle_baseline(budget_s=2.0)
+        t_all = 0.0
+        last = None
+        for _ in range(args.steps):
+            last, dt = oracle_baseline(budget_s=10.0)
+            vals.append(last["value"])
+            t_all += dt
+        v = float(np.mean(vals))
+        line = {"impl": "reference", "metric": "gate HBM GB/s at n=25 (single-gate suite)", "value": v,
+                "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * t_all / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "single-gate suite, n=25, Haar state seed 0, 100 reps/gate",
+                           "l2": "n/a (host)"},
+                "cpu_baseline": {"value": v, "unit": "GB/s", "cores": last["cores"], "kind": "oracle",
+                                 "sample": last["sample"]},
+                "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1912_10877_gb300 import lib
+    lib()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # --- headline: complex64 sweep with live per-launch events
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    c64 = run_sweep("c64", args.steps, args.warmup, local, with_events=True)
+    clk = clocks.stop()
+    barrier()
+    t = c64["seconds"]
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    value = c64["bytes"] * world / t / 1e9
+    e2e = None if args.no_e2e else run_e2e(c64, max(1, args.steps))
+    if world > 1 and e2e:
+        e2e["value"] *= world
+    # dominant kernel: largest share of device time
+    pc = c64["per_class"]
+    dom = max(pc, key=lambda c: pc[c]["seconds"])
+    kname = {"dense1": "k_gate1<float, OP_DENSE1>", "swap1": "k_gate1<float, OP_SWAP1>",
+             "diag1": "k_diag1<float>"}[dom]
+    achieved = pc[dom]["gbs"]
+    roof = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
+            "peak_kind": f"{peak_kind} (copy GB/s)", "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+            "traffic": traffic_for(dom + "_c64"),
+            "per_class_gbs": {c: round(v["gbs"], 1) for c, v in pc.items()},
+            "per_class_share": {c: round(v["seconds"] / sum(x["seconds"] for x in pc.values()), 4)
+                                for c, v in pc.items()}}
+    del c64
+    extra = {}
+    if not args.no_c128:
+        c128 = run_sweep("c128", max(1, args.steps // 3), max(1, args.warmup // 3), local, with_events=True)
+        extra["c128_sweep"] = {"value": round(c128["gbs"], 1), "unit": "GB/s", "steps": max(1, args.steps // 3),
+                               "per_class_gbs": {c: round(v["gbs"], 1) for c, v in c128["per_class"].items()},
+                               "note": "complex128 FP64 arithmetic; dense 2x2 is FP64-ALU bound on GB300"}
+        del c128
+    launches = REPS * len(W.single_gate_suite(N_QUBITS)) * args.steps
+    line = {"metric": "gate HBM GB/s at n=25 (single-gate suite, complex64)", "value": round(value, 1),
+            "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * t / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64 (f32)", "data": "synthetic",
+            "config": {"workload": "single-gate suite: X,H,T,Rx(0.7) on each of 25 qubits, 3 CNOT, 2 Toffoli; "
+                                   "100 reps each; Haar state n=25 seed 0",
+                       "n": N_QUBITS, "reps": REPS, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (256 MiB state); reps interleaved across the suite"},
+            "roofline": roof, "clocks": clk, "e2e": e2e, "gpu_launches": launches}
+    line.update(extra)
+    if rank == 0 and not args.no_baseline and world == 1:
+        cb, _ = oracle_baseline(budget_s=15.0)
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
