@@ -180,6 +180,28 @@ int qs_observable_destroy(qs_observable* o);
 /* <psi_r|O|psi_r> for every register r into host_out[nreg] (FP64 reduction). */
 int qs_expect(qs_state* s, const qs_observable* o, double* host_out);
 
+/* The same expectation values for callers that cannot allocate device memory:
+ * host frameworks that own all device memory through their own allocator,
+ * latency-critical loops that must not call cudaMalloc or cudaFree (which can
+ * synchronise the device), and processes under a fixed device-memory budget.
+ * The paper has no counterpart; this is a property of this library only.
+ * Allocates nothing and needs no handle: dev_amps holds nreg registers of
+ * nqubits qubits back to back (dtype QS_C64 or QS_C128), host_terms the
+ * observable, dev_out nreg doubles the caller allocated; asynchronous on
+ * stream (a cudaStream_t, NULL = legacy default stream).  Its reduction
+ * scratch is one fixed 512 KiB array of 65536 FP64 partial sums that every GPU
+ * loading the library keeps until the process exits; a request needing more
+ * than that (nreg * nterms > 65536) or more than 64 terms, or nreg > 65535,
+ * is rejected with QS_EINVAL.  All calls share the array and every call
+ * overwrites the part it reads, so nothing carries over from an earlier
+ * call -- but calls whose kernels overlap on the GPU (different streams, or
+ * different host threads) race on it and must be serialised by the caller.
+ * The first call on each device resolves the array's device address
+ * (cudaGetSymbolAddress, which may load the library's GPU module); make
+ * that first call before any stream capture. */
+int qs_expect_static(const void* dev_amps, int dtype, int nqubits, int nreg,
+                     const qs_pauli_term* host_terms, int nterms, double* dev_out, void* stream);
+
 /* ---------------------------------------------------------------- gradient */
 
 /* Device bytes of the work buffer qs_backward needs for an n-qubit register

@@ -71,6 +71,7 @@ SIGNATURES = {
     "qs_observable_create": ([ctypes.POINTER(PauliTerm), _I, _PP], _I),
     "qs_observable_destroy": ([_P], _I),
     "qs_expect": ([_P, _P, _PD], _I),
+    "qs_expect_static": ([_P, _I, _I, _I, ctypes.POINTER(PauliTerm), _I, _P, _P], _I),
     "qs_backward_work_bytes": ([_I, _PSZ], _I),
     "qs_backward": ([_P, _P, _PD, _P, _I, _P, _P, _PD, _PD], _I),
     "qs_measure": ([_P, _PD, _I, _PI64, _I], _I),

@@ -413,3 +413,126 @@ int promote_to_c128(const void* in, int dtype, double2* out, uint64_t dim, cudaS
 }
 
 }  // namespace qs
+
+// ------------------------------------------------------------------ expectation without allocation
+//
+// qs_expect_static: the expectation reduction above with its scratch in a
+// fixed, file-scope device array instead of memory obtained from cudaMalloc,
+// for callers that cannot allocate device memory.  Every GPU that loads the
+// library holds this array (512 KiB) until the process exits.  All calls
+// share it, so calls whose kernels overlap on the GPU race on it.
+
+namespace qs {
+
+constexpr int kStaticPartials = 1 << 16;  // FP64 partial sums (512 KiB)
+constexpr int kStaticTerms = 64;
+constexpr int kStaticMaxDevices = 64;
+
+static __device__ __align__(256) double g_static_partials[kStaticPartials];
+
+struct StaticCoeffs {
+  double c[kStaticTerms];
+};
+
+__global__ void k_expect_final_static(const double* __restrict__ partials, int nblk, int nt_total,
+                                      const __grid_constant__ StaticCoeffs co, int nreg, double* __restrict__ out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nreg) return;
+  double total = 0.0;
+  for (int t = 0; t < nt_total; ++t) {
+    const double* q = partials + ((size_t)r * nt_total + t) * nblk;
+    double v = 0.0;
+    for (int b = 0; b < nblk; ++b) v += q[b];
+    total += co.c[t] * v;
+  }
+  out[r] = total;
+}
+
+// device address of g_static_partials on the current device, resolved once per
+// device (host code must not use the symbol's host-side name as an address)
+static double* g_static_addr[kStaticMaxDevices];
+
+static int static_partials(double** out) {
+  int dev = 0;
+  QS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kStaticMaxDevices) return fail(QS_EUNSUPPORTED, "device ordinal %d >= %d", dev, kStaticMaxDevices);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_partials);
+    if (e != cudaSuccess || !p)
+      return fail(QS_EDEVICE, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+    g_static_addr[dev] = (double*)p;
+  }
+  *out = g_static_addr[dev];
+  return QS_OK;
+}
+
+}  // namespace qs
+
+extern "C" int qs_expect_static(const void* dev_amps, int dtype, int nqubits, int nreg, const qs_pauli_term* host_terms,
+                                int nterms, double* dev_out, void* stream) {
+  using namespace qs;
+  if (!dev_amps || !dev_out || (nterms > 0 && !host_terms)) return fail(QS_EINVAL, "null argument");
+  if (dtype != QS_C64 && dtype != QS_C128) return fail(QS_EINVAL, "dtype must be QS_C64 or QS_C128");
+  if (((uintptr_t)dev_amps % amp_bytes(dtype)) || ((uintptr_t)dev_out % sizeof(double)))
+    return fail(QS_EINVAL, "misaligned amplitude or output pointer");
+  if (nqubits < 1 || nqubits > QS_MAXQ) return fail(QS_EINVAL, "nqubits %d not in 1..%d", nqubits, QS_MAXQ);
+  if (nreg < 1 || nreg > 65535) return fail(QS_EINVAL, "nreg %d not in 1..65535", nreg);
+  if (nterms < 0 || nterms > kStaticTerms)
+    return fail(QS_EINVAL, "nterms %d exceeds the static limit of %d terms", nterms, kStaticTerms);
+  if ((long long)nreg * nterms > kStaticPartials)
+    return fail(QS_EINVAL, "nreg * nterms = %lld exceeds the static scratch of %d partial sums",
+                (long long)nreg * nterms, kStaticPartials);
+  for (int t = 0; t < nterms; ++t)
+    if (nqubits < 64 && ((host_terms[t].x_mask | host_terms[t].z_mask) >> nqubits))
+      return fail(QS_EINVAL, "term %d acts on a qubit >= n=%d", t, nqubits);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (nterms == 0) {
+    QS_CUDA(cudaMemsetAsync(dev_out, 0, sizeof(double) * nreg, st));
+    return QS_OK;
+  }
+  double* partials = nullptr;
+  QS_TRY(static_partials(&partials));
+  // terms ordered by x mask (insertion sort on the stack, stable)
+  int order[kStaticTerms];
+  for (int t = 0; t < nterms; ++t) {
+    int j = t;
+    while (j > 0 && host_terms[order[j - 1]].x_mask > host_terms[t].x_mask) {
+      order[j] = order[j - 1];
+      --j;
+    }
+    order[j] = t;
+  }
+  const uint64_t dim = 1ull << nqubits;
+  long long nblk = (long long)std::min<uint64_t>(std::max<uint64_t>(1, dim / (kRedThreads * 8)),
+                                                 std::max(1, 1216 / nreg));
+  nblk = std::max(1LL, std::min(nblk, (long long)kStaticPartials / ((long long)nreg * nterms)));
+  StaticCoeffs co;
+  memset(&co, 0, sizeof(co));
+  int base = 0;
+  while (base < nterms) {
+    const uint64_t x = host_terms[order[base]].x_mask;
+    TermGroup tg;
+    memset(&tg, 0, sizeof(tg));
+    tg.x = x;
+    tg.h = x ? 63 - __builtin_clzll(x) : -1;
+    tg.item_log2 = x ? nqubits - 1 : nqubits;
+    while (base + tg.nt < nterms && tg.nt < kGroupTerms && host_terms[order[base + tg.nt]].x_mask == x) {
+      const qs_pauli_term& term = host_terms[order[base + tg.nt]];
+      tg.z[tg.nt] = term.z_mask;
+      tg.ny[tg.nt] = __builtin_popcountll(term.x_mask & term.z_mask) & 3;
+      co.c[base + tg.nt] = term.coeff;
+      ++tg.nt;
+    }
+    dim3 grid((unsigned)nblk, nreg);
+    if (dtype == QS_C64)
+      k_expect_group<float2><<<grid, kRedThreads, 0, st>>>((const float2*)dev_amps, dim, tg, partials, nterms, base);
+    else
+      k_expect_group<double2><<<grid, kRedThreads, 0, st>>>((const double2*)dev_amps, dim, tg, partials, nterms, base);
+    QS_LAUNCHED();
+    base += tg.nt;
+  }
+  k_expect_final_static<<<(nreg + 127) / 128, 128, 0, st>>>(partials, (int)nblk, nterms, co, nreg, dev_out);
+  QS_LAUNCHED();
+  return QS_OK;
+}
