@@ -250,6 +250,65 @@ def traffic_for(kernel: str):
         return None
 
 
+# ------------------------------------------------------------------ batched registers (fwd + grad)
+
+BATCH_NREG, BATCH_LO, BATCH_HI, BATCH_DEPTH = 1024, 10, 18, 20
+
+
+def batch_workload():
+    counts = W.batch_qubit_counts(BATCH_NREG, BATCH_LO, BATCH_HI, seed=0)
+    specs = W.batch_variational(counts, BATCH_DEPTH, seed=0)
+    return counts, specs
+
+
+def run_batch_leg(steps: int, warmup: int, compare: bool = True):
+    """1024 registers, n ~ U{10..18}, Rz Rx Rz + CNOT ladder x 20 layers each, <sum Z_i Z_{i+1}>:
+    forward + reversible gradient of every register in ONE persistent launch (complex64).
+    Comparator: the unfused gate-by-gate complex128 path (one kernel per gate per register,
+    per-gate FP64 adjoint), all 1024 registers, same GPU."""
+    import torch
+    from paper_1912_10877_gb300 import qsim
+    counts, specs = batch_workload()
+    circs = [qsim.Circuit(g, int(n)) for n, (g, _) in zip(counts, specs)]
+    obs = [qsim.Observable(W.zz_chain(int(n))) for n in counts]
+    prog = qsim.BatchProgram(circs, obs)
+    st = qsim.State([int(n) for n in counts], dtype=torch.complex64)
+    params = torch.tensor(np.concatenate([p for _, p in specs]), dtype=torch.float64, device="cuda")
+    loss = torch.empty(BATCH_NREG, dtype=torch.float64, device="cuda")
+    grad = torch.empty(prog.nparams, dtype=torch.float64, device="cuda")
+    for _ in range(warmup):
+        prog.run(st, params, grad=True, loss=loss, grad_out=grad)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        prog.run(st, params, grad=True, loss=loss, grad_out=grad)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / steps
+    res = {"metric": "batched fwd+grad circuits/s", "value": round(BATCH_NREG / t, 1), "unit": "circuits/s",
+           "ms_per_batch": round(1e3 * t, 3), "dtype": "c64 (f32 gates and uncompute; f64 reductions above warp level)",
+           "config": {"workload": f"{BATCH_NREG} registers, n ~ U{{{BATCH_LO}..{BATCH_HI}}} seed 0, Rz.Rx.Rz + "
+                                  f"CNOT ladder x {BATCH_DEPTH} layers, <sum Z_i Z_i+1> (open)",
+                      "total_amplitudes": int(sum(1 << int(n) for n in counts)), "launches_per_batch": 2}}
+    if compare:
+        # gate-by-gate complex128: one launch per gate per register, FP64 adjoint per gate
+        rs = np.random.default_rng(0)
+        t0 = time.perf_counter()
+        for r, (n, (g, p)) in enumerate(zip(counts, specs)):
+            s128 = qsim.State(int(n), dtype=torch.complex128)
+            s128.reset()
+            s128.apply_circuit(circs[r], p, fused=False)
+            qsim.backward(s128, circs[r], p, obs[r])
+        torch.cuda.synchronize()
+        tg = time.perf_counter() - t0
+        res["gate_by_gate_c128"] = {"value": round(BATCH_NREG / tg, 2), "unit": "circuits/s",
+                                    "seconds": round(tg, 3), "registers": BATCH_NREG}
+        res["vs_gate_by_gate_c128"] = round(tg / t, 1)
+        del rs
+    return res
+
+
 # ------------------------------------------------------------------ CPU baseline (oracle)
 
 def oracle_baseline(budget_s: float = 15.0):
@@ -296,6 +355,8 @@ def main():
     ap.add_argument("--no-c128", action="store_true")
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--reps", type=int, default=REPS, help="repetitions per gate (profiling runs use 1)")
     args = ap.parse_args()
     REPS = args.reps
@@ -380,6 +441,8 @@ def main():
                                "per_class_gbs": {c: round(v["gbs"], 1) for c, v in c128["per_class"].items()},
                                "note": "complex128 FP64 arithmetic; dense 2x2 is FP64-ALU bound on GB300"}
         del c128
+    if not args.no_batch:
+        extra["batched"] = run_batch_leg(max(1, args.steps), max(1, args.warmup), compare=not args.no_compare)
     launches = REPS * len(W.single_gate_suite(N_QUBITS)) * args.steps
     line = {"metric": "gate HBM GB/s at n=25 (single-gate suite, complex64)", "value": round(value, 1),
             "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

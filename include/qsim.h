@@ -157,9 +157,13 @@ int qs_circuit_info(const qs_circuit* c, int* nqubits, int* ngates, int* nparams
 
 /* apply!(reg, chain): gates in list order on every register of s (Sec.
  * "Representing Quantum Circuits").  host_params: nparams doubles shared by
- * all registers, or nbatch * nparams (register-major) if per_register != 0. */
-int qs_apply_circuit(qs_state* s, const qs_circuit* c, const double* host_params,
-                     int per_register);
+ * all registers, or nbatch * nparams (register-major) with
+ * QS_APPLY_PER_REGISTER.  By default consecutive single-qubit gates on one
+ * qubit (no gate on that qubit in between) are multiplied on the host and
+ * applied as one pass; QS_APPLY_UNFUSED launches one kernel per gate. */
+#define QS_APPLY_PER_REGISTER 1
+#define QS_APPLY_UNFUSED 2
+int qs_apply_circuit(qs_state* s, const qs_circuit* c, const double* host_params, int flags);
 
 /* As qs_apply_circuit on a single register, also saving forward checkpoints:
  * after gate index g (0-based) with (g + 1) % ckpt_every == 0 and g + 1 <
@@ -221,6 +225,43 @@ int qs_backward_work_bytes(int nqubits, size_t* out_bytes);
 int qs_backward(qs_state* s, const qs_circuit* c, const double* host_params,
                 const qs_observable* o, int ckpt_every, const void* dev_ckpts, void* dev_work,
                 double* host_grad, double* host_loss);
+
+/* ---------------------------------------------------------------- batched registers */
+
+/* A batch of registers of uneven sizes, each with its own circuit, parameter
+ * vector and observable, run forward (and optionally through the reversible
+ * backward pass) in ONE persistent launch (Sec. "Batched Quantum Registers";
+ * Sec. "Reverse Mode").  complex64 states, FP32 gate arithmetic and
+ * uncompute, FP64 accumulation of losses and gradients above the warp level.
+ * Restrictions: every gate has one target (controls allowed; X, Y, Z, H, S,
+ * SDG, T, TDG, RX, RY, RZ, SHIFT, PHASE, 1-qubit MATRIX), each register has
+ * 5..30 qubits and at most 2048 parameters, observables are diagonal (sums
+ * of Z strings).  circuits[r]->nqubits is register r's size.  Each circuit is
+ * scheduled into fused passes over tiles of tile_qubits qubits (0 = 13) and
+ * 5-qubit register phases; the program holds device tables and the backward
+ * work buffers (two complex64 copies of every register larger than a tile). */
+typedef struct qs_batch_program qs_batch_program;
+
+#define QS_BATCH_RESET 1  /* start every register from |0...0> (else from the state's content) */
+#define QS_BATCH_GRAD 2   /* also run the backward pass and write gradients */
+
+int qs_batch_program_create(int nreg, const qs_circuit* const* circuits,
+                            const qs_observable* const* observables, int tile_qubits,
+                            qs_batch_program** out);
+int qs_batch_program_destroy(qs_batch_program* p);
+
+/* Register count, total parameters, parameter offsets (nreg + 1, host) and
+ * amplitude offsets (nreg + 1, host) of the program (NULL outputs skipped). */
+int qs_batch_program_info(const qs_batch_program* p, int* nreg, int64_t* nparams_total,
+                          int64_t* host_param_offsets, int64_t* host_amp_offsets);
+
+/* One persistent launch on s's stream (s: a qs_batch_create state of the
+ * same register sizes, QS_C64).  dev_params: the registers' parameter
+ * vectors back to back (device, FP64); dev_loss[nreg] receives <O_r>;
+ * with QS_BATCH_GRAD, dev_grad (same layout as dev_params) receives the
+ * gradients.  The final states psi_N are left in s. */
+int qs_batch_run(qs_state* s, const qs_batch_program* p, const double* dev_params, double* dev_loss,
+                 double* dev_grad, int flags);
 
 /* ---------------------------------------------------------------- measurement */
 

@@ -5,5 +5,5 @@ include/qsim.h); this package is the thin binding.  Importing a submodule that
 needs the library raises if it has not been built.
 """
 from ._native import QsimError, lib  # noqa: F401
-from .qsim import (Circuit, Observable, State, apply_circuit_ckpt, backward,  # noqa: F401
+from .qsim import (BatchProgram, Circuit, Observable, State, apply_circuit_ckpt, backward,  # noqa: F401
                    backward_work, checkpoint_buffer)

@@ -14,6 +14,8 @@ LIB_PATH = os.path.join(HERE, "libqsim.so")
 QS_OK, QS_EINVAL, QS_ENOMEM, QS_EDEVICE, QS_ETIMEDOUT, QS_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 QS_C64, QS_C128 = 0, 1
 QS_MAXK = 5
+QS_BATCH_RESET, QS_BATCH_GRAD = 1, 2
+QS_APPLY_PER_REGISTER, QS_APPLY_UNFUSED = 1, 2
 
 GATE_KIND = {"I": 0, "X": 1, "Y": 2, "Z": 3, "H": 4, "S": 5, "SDG": 6, "T": 7, "TDG": 8,
              "RX": 9, "RY": 10, "RZ": 11, "SHIFT": 12, "PHASE": 13, "SWAP": 14, "ROT": 15,
@@ -75,6 +77,10 @@ SIGNATURES = {
     "qs_backward_work_bytes": ([_I, _PSZ], _I),
     "qs_backward": ([_P, _P, _PD, _P, _I, _P, _P, _PD, _PD], _I),
     "qs_measure": ([_P, _PD, _I, _PI64, _I], _I),
+    "qs_batch_program_create": ([_I, _PP, _PP, _I, _PP], _I),
+    "qs_batch_program_destroy": ([_P], _I),
+    "qs_batch_program_info": ([_P, ctypes.POINTER(_I), _PI64, _PI64, _PI64], _I),
+    "qs_batch_run": ([_P, _P, _P, _P, _P, _I], _I),
 }
 
 _lib = None

@@ -134,12 +134,14 @@ struct Fuser {
   }
 };
 
-static int apply_circuit_impl(qs_state* s, const qs_circuit* c, const double* params, int per_register,
+static int apply_circuit_impl(qs_state* s, const qs_circuit* c, const double* params, int flags,
                               int ckpt_every, void* ckpts) {
   if (!s || !c) return fail(QS_EINVAL, "null handle");
   if (c->nparams > 0 && !params) return fail(QS_EINVAL, "params is NULL");
   if (min_n(s) < c->nqubits) return fail(QS_EINVAL, "circuit has %d qubits, register only %d", c->nqubits, min_n(s));
   const int ng = (int)c->gates.size();
+  const bool per_register = (flags & QS_APPLY_PER_REGISTER) != 0;
+  const bool unfused = (flags & QS_APPLY_UNFUSED) != 0 || ckpt_every > 0;
   std::vector<cd> U;
   if (per_register && s->nreg > 1) {
     if (!s->uniform) return fail(QS_EUNSUPPORTED, "per-register parameters on an uneven batch");
@@ -153,7 +155,8 @@ static int apply_circuit_impl(qs_state* s, const qs_circuit* c, const double* pa
       view.data = (char*)s->data + ab * s->off[r];
       view.owns = false;
       view.ws = Workspace();
-      int rc = apply_circuit_impl(&view, c, params + (size_t)r * c->nparams, 0, 0, nullptr);
+      int rc = apply_circuit_impl(&view, c, params + (size_t)r * c->nparams, flags & ~QS_APPLY_PER_REGISTER, 0,
+                                  nullptr);
       if (rc) return rc;
     }
     return QS_OK;
@@ -165,7 +168,7 @@ static int apply_circuit_impl(qs_state* s, const qs_circuit* c, const double* pa
     QS_TRY(gate_matrix(c, g, params, U));
     uint64_t locmask = 0;
     for (int j = 0; j < g.nlocs; ++j) locmask |= 1ull << g.locs[j];
-    if (g.nlocs == 1 && g.ctrl_mask == 0 && ckpt_every == 0) {
+    if (g.nlocs == 1 && g.ctrl_mask == 0 && !unfused) {
       fz.push(g.locs[0], U);
     } else {
       QS_TRY(fz.flush_mask(locmask | g.ctrl_mask));
@@ -348,8 +351,8 @@ int qs_circuit_info(const qs_circuit* c, int* nq, int* ng, int* np) {
   return QS_OK;
 }
 
-int qs_apply_circuit(qs_state* s, const qs_circuit* c, const double* params, int per_register) {
-  return apply_circuit_impl(s, c, params, per_register, 0, nullptr);
+int qs_apply_circuit(qs_state* s, const qs_circuit* c, const double* params, int flags) {
+  return apply_circuit_impl(s, c, params, flags, 0, nullptr);
 }
 
 int qs_checkpoint_count(const qs_circuit* c, int every, int* count) {

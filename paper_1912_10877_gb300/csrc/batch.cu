@@ -1,0 +1,945 @@
+// batch.cu -- batched registers of uneven sizes in one persistent launch
+// (Sec. "Batched Quantum Registers"; forward, expectation and reversible
+// adjoint of Sec. "Reverse Mode"), complex64.
+//
+// Every register has its own circuit, parameters and diagonal observable.  The
+// host schedules each circuit into fused tile passes (tiles.cuh); a persistent
+// grid of 512-thread CTAs takes registers from an atomic counter in
+// decreasing-cost order.  A register of n <= 13 qubits lives in shared memory
+// for the whole forward, expectation and backward (its lambda too); a larger
+// register streams 2^13-amplitude tiles through L2 / HBM once per pass.
+// Inside a tile each phase keeps 16 amplitudes per thread in registers.
+//
+// Backward (Eq. apply-back): the passes and phases run in reverse; for each
+// gate, in reverse order, a thread adds Im sum conj(lambda) (G psi) over its
+// pairs (FP32 over <= 8 pairs, then FP32 warp shuffles, FP64 from the warp
+// level up) and uncomputes psi and lambda with U^dagger in FP32, using the
+// structured Rx / Ry / diagonal forms of the inverse rotations.  The
+// register's gradient lives in shared memory (FP64) and is written once.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "tiles.cuh"
+
+namespace qs {
+
+constexpr int kMaxRegParams = 2048;
+constexpr int kMaxPhaseOps = 64;
+constexpr int kBatchTile = kMaxTileBits;
+
+struct GSpec {           // one circuit gate of one register
+  int32_t kind;
+  int32_t param;         // global index into params (-1: theta)
+  double theta;
+  double2 mat[4];        // MATRIX gates (1 target)
+};
+
+struct FMem {            // members of a fused forward op (applied in order)
+  int32_t count;
+  int32_t g[4];          // global GSpec indices
+};
+
+struct BReg {
+  int32_t n, m, npass, pass0;
+  int32_t nparam, nterm, term0, pad;
+  int64_t amp_off;       // elements into the batch state
+  int64_t work_off;      // elements into psi/lambda work buffers (n > 13), -1 otherwise
+  int64_t param_off;     // into params / grad
+  double cost;
+};
+
+struct BTerm {
+  double coeff;
+  uint64_t z;
+};
+
+struct BArgs {
+  float2* state;
+  float2* wpsi;          // backward work copies of psi (n > 13)
+  float2* wlam;          // lambda (n > 13)
+  const BReg* regs;
+  const int32_t* order;
+  const TPass* passes;
+  const TPhase* phases;
+  const TOp* fops;
+  const TOp* bops;
+  const BTerm* terms;
+  double* loss;
+  double* grad;
+  int* counter;
+  int nreg;
+  int flags;
+};
+
+enum { BF_RESET = 1, BF_GRAD = 2 };
+
+// ------------------------------------------------------------------ device: ops on 16 amplitudes
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmaf(float2 a, float2 b, float2 c) {  // a*b + c
+  c.x = fmaf(a.x, b.x, c.x);
+  c.x = fmaf(-a.y, b.y, c.x);
+  c.y = fmaf(a.x, b.y, c.y);
+  c.y = fmaf(a.y, b.x, c.y);
+  return c;
+}
+__device__ __forceinline__ float imcj(float2 p, float2 q) { return fmaf(p.x, q.y, -p.y * q.x); }  // Im(conj(p) q)
+__device__ __forceinline__ float recj(float2 p, float2 q) { return fmaf(p.x, q.x, p.y * q.y); }   // Re(conj(p) q)
+
+// (a, b) <- U (a, b) for the structured kinds; U row-major in u0..u3
+template <int KIND>
+__device__ __forceinline__ void pair_apply(float2& a, float2& b, float2 u0, float2 u1, float2 u2, float2 u3) {
+  if (KIND == TK_SWAP) {
+    const float2 t = a; a = b; b = t;
+  } else if (KIND == TK_DIAG) {
+    a = cmulf(a, u0);
+    b = cmulf(b, u3);
+  } else if (KIND == TK_RX) {  // [[c, i s], [i s, c]] (c = u0.x, s = u1.y)
+    const float c = u0.x, s = u1.y;
+    const float2 na = make_float2(fmaf(c, a.x, -s * b.y), fmaf(c, a.y, s * b.x));
+    const float2 nb = make_float2(fmaf(c, b.x, -s * a.y), fmaf(c, b.y, s * a.x));
+    a = na; b = nb;
+  } else if (KIND == TK_RY) {  // real [[c, u1], [u2, c]]
+    const float c = u0.x, p = u1.x, q = u2.x;
+    const float2 na = make_float2(fmaf(c, a.x, p * b.x), fmaf(c, a.y, p * b.y));
+    const float2 nb = make_float2(fmaf(q, a.x, c * b.x), fmaf(q, a.y, c * b.y));
+    a = na; b = nb;
+  } else {
+    const float2 na = cmaf(u1, b, cmulf(u0, a));
+    const float2 nb = cmaf(u3, b, cmulf(u2, a));
+    a = na; b = nb;
+  }
+}
+
+template <int T, int KIND, bool CTRL>
+__device__ __forceinline__ void op_fwd(float2 (&x)[16], const TOp& op) {
+  const int cm = op.cmask, cv = op.cval;
+  const float2 u0 = op.u[0], u1 = op.u[1], u2 = op.u[2], u3 = op.u[3];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j & (1 << T)) continue;
+    if (CTRL && (j & cm) != cv) continue;
+    pair_apply<KIND>(x[j], x[j | (1 << T)], u0, u1, u2, u3);
+  }
+}
+
+template <int T>
+__device__ __forceinline__ void op_fwd_k(float2 (&x)[16], const TOp& op) {
+  if (op.kind == TK_SWAP) op_fwd<T, TK_SWAP, true>(x, op);
+  else if (op.cmask == 0) {
+    if (op.kind == TK_DIAG) op_fwd<T, TK_DIAG, false>(x, op);
+    else op_fwd<T, TK_DENSE, false>(x, op);
+  } else {
+    if (op.kind == TK_DIAG) op_fwd<T, TK_DIAG, true>(x, op);
+    else op_fwd<T, TK_DENSE, true>(x, op);
+  }
+}
+
+__device__ __forceinline__ void apply_fwd(float2 (&x)[16], const TOp& op) {
+  switch (op.t) {
+    case 0: op_fwd_k<0>(x, op); break;
+    case 1: op_fwd_k<1>(x, op); break;
+    case 2: op_fwd_k<2>(x, op); break;
+    default: op_fwd_k<3>(x, op); break;
+  }
+}
+
+// Backward op: first this thread's share of Im<lambda|G|psi> over its pairs
+// (GK 0: none; 1: diagonal generator diag(g0, g3); 2: X; 3: Y), then
+// psi <- U^dag psi and lambda <- U^dag lambda.
+template <int T, int KIND, int GK, bool CTRL>
+__device__ __forceinline__ float op_bwd(float2 (&x)[16], float2 (&l)[16], const TOp& op, float g0, float g3) {
+  const int cm = op.cmask, cv = op.cval;
+  const float2 u0 = op.u[0], u1 = op.u[1], u2 = op.u[2], u3 = op.u[3];
+  float acc = 0.f;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j & (1 << T)) continue;
+    if (CTRL && (j & cm) != cv) continue;
+    const int k = j | (1 << T);
+    if (GK == 1) acc += fmaf(g0, imcj(l[j], x[j]), g3 * imcj(l[k], x[k]));
+    if (GK == 2) acc += imcj(l[j], x[k]) + imcj(l[k], x[j]);
+    if (GK == 3) acc += recj(l[k], x[j]) - recj(l[j], x[k]);
+    pair_apply<KIND>(x[j], x[k], u0, u1, u2, u3);
+    pair_apply<KIND>(l[j], l[k], u0, u1, u2, u3);
+  }
+  return acc;
+}
+
+template <int T, bool CTRL>
+__device__ __forceinline__ float op_bwd_c(float2 (&x)[16], float2 (&l)[16], const TOp& op) {
+  switch (op.gen) {
+    case GEN_X: return op_bwd<T, TK_RX, 2, CTRL>(x, l, op, 0.f, 0.f);
+    case GEN_Y: return op_bwd<T, TK_RY, 3, CTRL>(x, l, op, 0.f, 0.f);
+    case GEN_Z: return op_bwd<T, TK_DIAG, 1, CTRL>(x, l, op, 1.f, -1.f);
+    case GEN_P1: return op_bwd<T, TK_DIAG, 1, CTRL>(x, l, op, 0.f, 1.f);
+    default: return op_bwd<T, TK_DIAG, 1, CTRL>(x, l, op, 1.f, 1.f);  // GEN_I
+  }
+}
+
+template <int T>
+__device__ __forceinline__ float op_bwd_t(float2 (&x)[16], float2 (&l)[16], const TOp& op) {
+  if (op.gen == GEN_NONE) {
+    if (op.kind == TK_SWAP) return op_bwd<T, TK_SWAP, 0, true>(x, l, op, 0.f, 0.f);
+    if (op.kind == TK_DIAG) return op_bwd<T, TK_DIAG, 0, true>(x, l, op, 0.f, 0.f);
+    return op_bwd<T, TK_DENSE, 0, true>(x, l, op, 0.f, 0.f);
+  }
+  return op.cmask ? op_bwd_c<T, true>(x, l, op) : op_bwd_c<T, false>(x, l, op);
+}
+
+__device__ __forceinline__ float apply_bwd(float2 (&x)[16], float2 (&l)[16], const TOp& op) {
+  switch (op.t) {
+    case 0: return op_bwd_t<0>(x, l, op);
+    case 1: return op_bwd_t<1>(x, l, op);
+    case 2: return op_bwd_t<2>(x, l, op);
+    default: return op_bwd_t<3>(x, l, op);
+  }
+}
+
+// ------------------------------------------------------------------ device: the persistent kernel
+
+constexpr int kWarps = kTileThreads / 32;
+
+struct BShared {
+  double grad[kMaxRegParams];
+  float red[kMaxPhaseOps * kWarps];
+  double lred[kWarps];
+  uint32_t rowoff[1 << (kMaxTileBits - kRowBits)];  // register offset of each 32-amplitude tile row (current pass)
+  int reg;
+};
+
+// Tile rows: tile-local bits 0..4 are register qubits 0..4 (planner seed), so a
+// row of 32 amplitudes is contiguous (256 bytes).  rowoff[] holds the register
+// offset of every row of the current pass; tile_base() the offset of a tile.
+__device__ void set_rows(BShared& S, const TPass& p, int m) {
+  for (uint32_t row = threadIdx.x; row < (1u << (m - kRowBits)); row += blockDim.x) {
+    uint32_t o = 0;
+    for (int k = kRowBits; k < m; ++k) o |= ((row >> (k - kRowBits)) & 1u) << p.tbits[k];
+    S.rowoff[row] = o;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ uint64_t tile_base(uint64_t tile, const TPass& p, int g) {
+  uint64_t o = 0;
+  for (int k = 0; k < g; ++k) o |= ((tile >> k) & 1ull) << p.gbits[k];
+  return o;
+}
+
+// Stage one or two tiles (2^m amplitudes each) between global and shared
+// memory.  Each thread issues up to 8 16-byte loads per tile before any shared
+// store (4096 loads of one tile in flight per CTA).
+constexpr int kLdChunk = 8;
+
+template <bool TWO>
+__device__ __noinline__ void load_tiles(float2* sm0, const float2* src0, float2* sm1, const float2* src1,
+                                        const BShared& S, int m) {
+  const uint32_t nq = 1u << (m - 1);  // float4 per tile
+  constexpr int C = TWO ? kLdChunk / 2 : kLdChunk;
+  for (uint32_t q0 = 0; q0 < nq; q0 += C * kTileThreads) {
+    float4 v0[C], v1[C];
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      const uint32_t q = q0 + threadIdx.x + k * kTileThreads;
+      if (q < nq) {
+        const uint32_t off = S.rowoff[q >> 4] + 2 * (q & 15);
+        v0[k] = *reinterpret_cast<const float4*>(src0 + off);
+        if (TWO) v1[k] = *reinterpret_cast<const float4*>(src1 + off);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      const uint32_t q = q0 + threadIdx.x + k * kTileThreads;
+      if (q < nq) {
+        const uint32_t l = 2 * q;
+        sm0[swz(l)] = make_float2(v0[k].x, v0[k].y);
+        sm0[swz(l + 1)] = make_float2(v0[k].z, v0[k].w);
+        if (TWO) {
+          sm1[swz(l)] = make_float2(v1[k].x, v1[k].y);
+          sm1[swz(l + 1)] = make_float2(v1[k].z, v1[k].w);
+        }
+      }
+    }
+  }
+}
+
+template <bool TWO>
+__device__ __noinline__ void store_tiles(const float2* sm0, float2* dst0, const float2* sm1, float2* dst1,
+                                         const BShared& S, int m) {
+  const uint32_t nq = 1u << (m - 1);
+  for (uint32_t q = threadIdx.x; q < nq; q += kTileThreads) {
+    const uint32_t off = S.rowoff[q >> 4] + 2 * (q & 15);
+    const uint32_t l = 2 * q;
+    const float2 a = sm0[swz(l)], b = sm0[swz(l + 1)];
+    *reinterpret_cast<float4*>(dst0 + off) = make_float4(a.x, a.y, b.x, b.y);
+    if (TWO) {
+      const float2 c = sm1[swz(l)], d = sm1[swz(l + 1)];
+      *reinterpret_cast<float4*>(dst1 + off) = make_float4(c.x, c.y, d.x, d.y);
+    }
+  }
+}
+
+__device__ __forceinline__ void load_tile(float2* sm, const float2* src, const BShared& S, int m) {
+  load_tiles<false>(sm, src, nullptr, nullptr, S, m);
+}
+__device__ __forceinline__ void store_tile(const float2* sm, float2* dst, const BShared& S, int m) {
+  store_tiles<false>(sm, dst, nullptr, nullptr, S, m);
+}
+
+__device__ __forceinline__ uint32_t phase_base(uint32_t tid, const TPhase& ph, int nthreadbits) {
+  uint32_t b = 0;
+  for (int k = 0; k < nthreadbits; ++k) b |= ((tid >> k) & 1u) << ph.tpos[k];
+  return b;
+}
+
+__device__ __noinline__ void run_phase_fwd(float2* sm, const TPhase* php, const TOp* fops, int m) {
+  const TPhase ph = *php;
+  const int ntb = m - kRB;
+  if (threadIdx.x < (1u << ntb)) {
+    const uint32_t base = phase_base(threadIdx.x, ph, ntb);
+    uint32_t off[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      uint32_t o = base;
+#pragma unroll
+      for (int k = 0; k < kRB; ++k)
+        if ((j >> k) & 1) o |= 1u << ph.rpos[k];
+      off[j] = swz(o);
+    }
+    float2 x[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) x[j] = sm[off[j]];
+    TOp nxt = fops[ph.fop0];
+    for (int o = 0; o < ph.nfop; ++o) {
+      const TOp cur = nxt;
+      if (o + 1 < ph.nfop) nxt = fops[ph.fop0 + o + 1];
+      apply_fwd(x, cur);
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) sm[off[j]] = x[j];
+  }
+  __syncthreads();
+}
+
+__device__ __noinline__ void run_phase_bwd(float2* sx, float2* sl, const TPhase* php, const TOp* bops, int m,
+                                           BShared& S) {
+  const TPhase ph = *php;
+  const int ntb = m - kRB;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool active = threadIdx.x < (1u << ntb);
+  float2 x[16], l[16];
+  uint32_t off[16];
+  {
+    const uint32_t base = active ? phase_base(threadIdx.x, ph, ntb) : 0u;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      uint32_t o = base;
+#pragma unroll
+      for (int k = 0; k < kRB; ++k)
+        if ((j >> k) & 1) o |= 1u << ph.rpos[k];
+      off[j] = swz(o);
+    }
+  }
+  if (active) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      x[j] = sx[off[j]];
+      l[j] = sl[off[j]];
+    }
+  }
+  TOp nxt = bops[ph.bop0 + ph.nbop - 1];
+  for (int o = ph.nbop - 1; o >= 0; --o) {
+    const TOp op = nxt;
+    if (o > 0) nxt = bops[ph.bop0 + o - 1];
+    float part = 0.f;
+    if (active) part = apply_bwd(x, l, op);
+    if (op.gen != GEN_NONE) {
+      for (int s = 16; s > 0; s >>= 1) part += __shfl_xor_sync(0xffffffffu, part, s);
+      if (lane == 0) S.red[o * kWarps + warp] = part;
+    }
+  }
+  if (active) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      sx[off[j]] = x[j];
+      sl[off[j]] = l[j];
+    }
+  }
+  __syncthreads();
+  // fold the warp partials of every parameterised op in FP64; ops whose
+  // parameter is unique in the phase in parallel, the others by one thread
+  const int nw = (int)(blockDim.x / 32);
+  const int o = threadIdx.x;
+  if (o < ph.nbop) {
+    const TOp& op = bops[ph.bop0 + o];
+    if (op.gen != GEN_NONE && !op.shared) {
+      double v = 0.0;
+      for (int w = 0; w < nw; ++w) v += (double)S.red[o * kWarps + w];
+      S.grad[op.param] += (double)op.cfac2 * v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < ph.nbop; ++q) {
+      const TOp& op = bops[ph.bop0 + q];
+      if (op.gen == GEN_NONE || !op.shared) continue;
+      double v = 0.0;
+      for (int w = 0; w < nw; ++w) v += (double)S.red[q * kWarps + w];
+      S.grad[op.param] += (double)op.cfac2 * v;
+    }
+  }
+  __syncthreads();
+}
+
+// loss partial and lambda = w psi for the diagonal observable, over a tile in smem
+__device__ double expect_tile(float2* sx, float2* sl, uint64_t tbase, const BShared& S, int m, const BTerm* terms,
+                              int nterm) {
+  const uint32_t cnt = 1u << m;
+  double acc = 0.0;
+  for (uint32_t l = threadIdx.x; l < cnt; l += blockDim.x) {
+    const uint64_t gi = tbase + S.rowoff[l >> kRowBits] + (l & 31u);
+    double w = 0.0;
+    for (int t = 0; t < nterm; ++t) w += (__popcll(gi & terms[t].z) & 1) ? -terms[t].coeff : terms[t].coeff;
+    const float2 a = sx[swz(l)];
+    acc += w * ((double)a.x * a.x + (double)a.y * a.y);
+    const float wf = (float)w;
+    sl[swz(l)] = make_float2(wf * a.x, wf * a.y);
+  }
+  return acc;
+}
+
+__device__ void block_loss(double e, BShared& S, double* out) {
+  for (int s = 16; s > 0; s >>= 1) e += __shfl_xor_sync(0xffffffffu, e, s);
+  if ((threadIdx.x & 31) == 0) S.lred[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) v += S.lred[w];
+    *out = v;
+  }
+}
+
+__global__ void __launch_bounds__(kTileThreads, 1) k_batch(BArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  BShared& S = *reinterpret_cast<BShared*>(smraw);
+  float2* sx = reinterpret_cast<float2*>(smraw + ((sizeof(BShared) + 255) & ~size_t(255)));
+  float2* sl = sx + (1 << kMaxTileBits);
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) S.reg = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int ri = S.reg;
+    __syncthreads();
+    if (ri >= a.nreg) break;
+    const int reg = a.order[ri];
+    const BReg R = a.regs[reg];
+    const int n = R.n, m = R.m, g = n - m;
+    const bool grad = (a.flags & BF_GRAD) != 0;
+    for (int i = tid; i < R.nparam; i += blockDim.x) S.grad[i] = 0.0;
+    float2* st = a.state + R.amp_off;
+    const uint64_t ntile = 1ull << g;
+    const TPass* P = a.passes + R.pass0;
+    if (g == 0) {
+      // ---- whole register in shared memory
+      set_rows(S, P[0], m);
+      if (a.flags & BF_RESET) {
+        for (uint32_t l = tid; l < (1u << m); l += blockDim.x) sx[swz(l)] = make_float2(l == 0 ? 1.f : 0.f, 0.f);
+      } else {
+        load_tile(sx, st, S, m);
+      }
+      __syncthreads();
+      for (int pi = 0; pi < R.npass; ++pi)
+        for (int f = 0; f < P[pi].nphase; ++f) run_phase_fwd(sx, a.phases + P[pi].phase0 + f, a.fops, m);
+      store_tile(sx, st, S, m);  // psi_N
+      block_loss(expect_tile(sx, sl, 0, S, m, a.terms + R.term0, R.nterm), S, a.loss + reg);
+      __syncthreads();
+      if (grad) {
+        for (int pi = R.npass - 1; pi >= 0; --pi)
+          for (int f = P[pi].nphase - 1; f >= 0; --f)
+            run_phase_bwd(sx, sl, a.phases + P[pi].phase0 + f, a.bops, m, S);
+      }
+    } else {
+      // ---- tiles streamed through global memory
+      if (a.flags & BF_RESET) {
+        for (uint64_t i = tid; i < (1ull << n); i += blockDim.x) st[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
+        __syncthreads();
+      }
+      for (int pi = 0; pi < R.npass; ++pi) {
+        const TPass& p = P[pi];
+        set_rows(S, p, m);
+        for (uint64_t t = 0; t < ntile; ++t) {
+          const uint64_t tb = tile_base(t, p, g);
+          load_tile(sx, st + tb, S, m);
+          __syncthreads();
+          for (int f = 0; f < p.nphase; ++f) run_phase_fwd(sx, a.phases + p.phase0 + f, a.fops, m);
+          store_tile(sx, st + tb, S, m);
+          __syncthreads();
+        }
+      }
+      // expectation, lambda = O psi, and the work copy of psi for the uncompute
+      double e = 0.0;
+      float2* wp = a.wpsi + R.work_off;
+      float2* wl = a.wlam + R.work_off;
+      const TPass& p0 = P[0];
+      set_rows(S, p0, m);
+      for (uint64_t t = 0; t < ntile; ++t) {
+        const uint64_t tb = tile_base(t, p0, g);
+        load_tile(sx, st + tb, S, m);
+        __syncthreads();
+        e += expect_tile(sx, sl, tb, S, m, a.terms + R.term0, R.nterm);
+        __syncthreads();
+        if (grad) store_tiles<true>(sx, wp + tb, sl, wl + tb, S, m);
+        __syncthreads();
+      }
+      block_loss(e, S, a.loss + reg);
+      __syncthreads();
+      if (grad) {
+        for (int pi = R.npass - 1; pi >= 0; --pi) {
+          const TPass& p = P[pi];
+          set_rows(S, p, m);
+          for (uint64_t t = 0; t < ntile; ++t) {
+            const uint64_t tb = tile_base(t, p, g);
+            load_tiles<true>(sx, wp + tb, sl, wl + tb, S, m);
+            __syncthreads();
+            for (int f = p.nphase - 1; f >= 0; --f) run_phase_bwd(sx, sl, a.phases + p.phase0 + f, a.bops, m, S);
+            store_tiles<true>(sx, wp + tb, sl, wl + tb, S, m);
+            __syncthreads();
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (grad)
+      for (int i = tid; i < R.nparam; i += blockDim.x) a.grad[R.param_off + i] = S.grad[i];
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ device: matrices from parameters
+
+struct PrepArgs {
+  const GSpec* gspec;
+  const FMem* fmem;
+  const int32_t* bgate;
+  TOp* fops;
+  TOp* bops;
+  const double* params;
+  int nfop, nbop;
+};
+
+__device__ void gate_mat(const GSpec& gs, const double* params, double2 (&U)[4]) {
+  const double th = gs.param >= 0 ? params[gs.param] : gs.theta;
+  double s, c;
+  sincos(th * 0.5, &s, &c);
+  const double h = 0.70710678118654752440;
+  auto set = [&](double a0, double a1, double b0, double b1, double c0, double c1, double d0, double d1) {
+    U[0] = make_double2(a0, a1); U[1] = make_double2(b0, b1); U[2] = make_double2(c0, c1); U[3] = make_double2(d0, d1);
+  };
+  switch (gs.kind) {
+    case QS_GATE_X: set(0, 0, 1, 0, 1, 0, 0, 0); break;
+    case QS_GATE_Y: set(0, 0, 0, -1, 0, 1, 0, 0); break;
+    case QS_GATE_Z: set(1, 0, 0, 0, 0, 0, -1, 0); break;
+    case QS_GATE_H: set(h, 0, h, 0, h, 0, -h, 0); break;
+    case QS_GATE_S: set(1, 0, 0, 0, 0, 0, 0, 1); break;
+    case QS_GATE_SDG: set(1, 0, 0, 0, 0, 0, 0, -1); break;
+    case QS_GATE_T: set(1, 0, 0, 0, 0, 0, h, h); break;
+    case QS_GATE_TDG: set(1, 0, 0, 0, 0, 0, h, -h); break;
+    case QS_GATE_RX: set(c, 0, 0, -s, 0, -s, c, 0); break;
+    case QS_GATE_RY: set(c, 0, -s, 0, s, 0, c, 0); break;
+    case QS_GATE_RZ: set(c, -s, 0, 0, 0, 0, c, s); break;
+    case QS_GATE_SHIFT: { double s2, c2; sincos(th, &s2, &c2); set(1, 0, 0, 0, 0, 0, c2, s2); break; }
+    case QS_GATE_PHASE: { double s2, c2; sincos(th, &s2, &c2); set(c2, s2, 0, 0, 0, 0, c2, s2); break; }
+    case QS_GATE_MATRIX: U[0] = gs.mat[0]; U[1] = gs.mat[1]; U[2] = gs.mat[2]; U[3] = gs.mat[3]; break;
+    default: set(1, 0, 0, 0, 0, 0, 1, 0); break;
+  }
+}
+
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+__global__ void k_batch_prep(PrepArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.nfop) {
+    const FMem& fm = a.fmem[i];
+    double2 A[4] = {make_double2(1, 0), make_double2(0, 0), make_double2(0, 0), make_double2(1, 0)};
+    for (int k = 0; k < fm.count; ++k) {
+      double2 U[4];
+      gate_mat(a.gspec[fm.g[k]], a.params, U);
+      const double2 C0 = zadd(zmul(U[0], A[0]), zmul(U[1], A[2]));
+      const double2 C1 = zadd(zmul(U[0], A[1]), zmul(U[1], A[3]));
+      const double2 C2 = zadd(zmul(U[2], A[0]), zmul(U[3], A[2]));
+      const double2 C3 = zadd(zmul(U[2], A[1]), zmul(U[3], A[3]));
+      A[0] = C0; A[1] = C1; A[2] = C2; A[3] = C3;
+    }
+    for (int k = 0; k < 4; ++k) a.fops[i].u[k] = make_float2((float)A[k].x, (float)A[k].y);
+  } else if (i < a.nfop + a.nbop) {
+    const int j = i - a.nfop;
+    double2 U[4];
+    gate_mat(a.gspec[a.bgate[j]], a.params, U);
+    // U^dagger
+    a.bops[j].u[0] = make_float2((float)U[0].x, (float)-U[0].y);
+    a.bops[j].u[1] = make_float2((float)U[2].x, (float)-U[2].y);
+    a.bops[j].u[2] = make_float2((float)U[1].x, (float)-U[1].y);
+    a.bops[j].u[3] = make_float2((float)U[3].x, (float)-U[3].y);
+  }
+}
+
+}  // namespace qs
+
+// ------------------------------------------------------------------ host: the program object
+
+struct qs_batch_program {
+  int nreg = 0;
+  std::vector<int> nq;
+  std::vector<int64_t> param_off;    // nreg + 1
+  std::vector<int64_t> amp_off;      // nreg + 1
+  int64_t work_elems = 0;
+  // device tables
+  qs::BReg* regs = nullptr;
+  int32_t* order = nullptr;
+  qs::TPass* passes = nullptr;
+  qs::TPhase* phases = nullptr;
+  qs::TOp* fops = nullptr;
+  qs::TOp* bops = nullptr;
+  qs::BTerm* terms = nullptr;
+  qs::GSpec* gspec = nullptr;
+  qs::FMem* fmem = nullptr;
+  int32_t* bgate = nullptr;
+  int* counter = nullptr;
+  float2* wpsi = nullptr;
+  float2* wlam = nullptr;
+  int nfop = 0, nbop = 0;
+  int64_t npass = 0, nphase = 0;
+  int blocks = 0;
+  size_t smem = 0;
+};
+
+namespace qs {
+
+static bool diag_kind(int k) {
+  return k == QS_GATE_Z || k == QS_GATE_S || k == QS_GATE_SDG || k == QS_GATE_T || k == QS_GATE_TDG ||
+         k == QS_GATE_RZ || k == QS_GATE_SHIFT || k == QS_GATE_PHASE || k == QS_GATE_I;
+}
+
+static int gen_of(int kind, float* cfac2) {
+  switch (kind) {
+    case QS_GATE_RX: *cfac2 = 1.f; return GEN_X;
+    case QS_GATE_RY: *cfac2 = 1.f; return GEN_Y;
+    case QS_GATE_RZ: *cfac2 = 1.f; return GEN_Z;
+    case QS_GATE_SHIFT: *cfac2 = -2.f; return GEN_P1;
+    case QS_GATE_PHASE: *cfac2 = -2.f; return GEN_I;
+  }
+  *cfac2 = 0.f;
+  return GEN_NONE;
+}
+
+template <typename T>
+static int upload(T** dst, const std::vector<T>& v) {
+  const size_t bytes = sizeof(T) * std::max<size_t>(1, v.size());
+  if (cudaMalloc((void**)dst, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *dst = nullptr;
+    return fail(QS_ENOMEM, "cudaMalloc of %zu program bytes failed", bytes);
+  }
+  if (!v.empty()) QS_CUDA(cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  return QS_OK;
+}
+
+static void free_program(qs_batch_program* p) {
+  if (!p) return;
+  void* ptrs[] = {p->regs, p->order, p->passes, p->phases, p->fops, p->bops, p->terms,
+                  p->gspec, p->fmem, p->bgate, p->counter, p->wpsi, p->wlam};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete p;
+}
+
+static int build_program(int nreg, const qs_circuit* const* circs, const qs_observable* const* obs, int tile_qubits,
+                         qs_batch_program* P) {
+  const int M = tile_qubits > 0 ? tile_qubits : kBatchTile;
+  if (M < kRB || M > kBatchTile) return fail(QS_EINVAL, "tile_qubits must be in %d..%d", kRB, kBatchTile);
+  std::vector<BReg> regs(nreg);
+  std::vector<TPass> passes;
+  std::vector<TPhase> phases;
+  std::vector<TOp> fops, bops;
+  std::vector<BTerm> terms;
+  std::vector<GSpec> gspec;
+  std::vector<FMem> fmem;
+  std::vector<int32_t> bgate;
+  P->nreg = nreg;
+  P->nq.resize(nreg);
+  P->param_off.assign(nreg + 1, 0);
+  P->amp_off.assign(nreg + 1, 0);
+  int64_t work = 0;
+  for (int r = 0; r < nreg; ++r) {
+    const qs_circuit* c = circs[r];
+    const qs_observable* o = obs[r];
+    if (!c || !o) return fail(QS_EINVAL, "register %d: null circuit or observable", r);
+    const int n = c->nqubits;
+    if (n < kRowBits || n > 30) return fail(QS_EUNSUPPORTED, "register %d: batched registers take 5..30 qubits", r);
+    if (c->nparams > kMaxRegParams) return fail(QS_EUNSUPPORTED, "register %d: more than %d parameters", r, kMaxRegParams);
+    P->nq[r] = n;
+    P->param_off[r + 1] = P->param_off[r] + c->nparams;
+    P->amp_off[r + 1] = P->amp_off[r] + (1ll << n);
+    const int m = std::min(n, M);
+    std::vector<HostPass> hp;
+    QS_TRY(plan_passes(c, n, m, kMaxPhaseOps, hp));
+    BReg& R = regs[r];
+    memset(&R, 0, sizeof(R));
+    R.n = n;
+    R.m = m;
+    R.npass = (int)hp.size();
+    R.pass0 = (int)passes.size();
+    R.nparam = c->nparams;
+    R.amp_off = P->amp_off[r];
+    R.param_off = P->param_off[r];
+    R.work_off = n > m ? work : -1;
+    if (n > m) work += 1ll << n;
+    // observable: diagonal Pauli strings only
+    R.term0 = (int)terms.size();
+    for (const auto& t : o->terms) {
+      if (t.x_mask) return fail(QS_EUNSUPPORTED, "register %d: batched observables must be diagonal (Z strings)", r);
+      if (n < 64 && (t.z_mask >> n)) return fail(QS_EINVAL, "register %d: observable qubit out of range", r);
+      terms.push_back({t.coeff, t.z_mask});
+    }
+    R.nterm = (int)o->terms.size();
+    // gate specs of this register
+    const int g0 = (int)gspec.size();
+    for (const auto& g : c->gates) {
+      GSpec s;
+      memset(&s, 0, sizeof(s));
+      s.kind = g.kind;
+      s.param = g.param >= 0 ? (int)(P->param_off[r] + g.param) : -1;
+      s.theta = g.theta;
+      if (g.kind == QS_GATE_MATRIX) {
+        if (g.nlocs != 1) return fail(QS_EUNSUPPORTED, "register %d: multi-qubit matrices in a batch", r);
+        for (int k = 0; k < 4; ++k) s.mat[k] = make_double2(c->mats[g.mat_offset + k].real(), c->mats[g.mat_offset + k].imag());
+      }
+      if (g.kind == QS_GATE_ROT || g.kind == QS_GATE_SWAP)
+        return fail(QS_EUNSUPPORTED, "register %d: ROT / SWAP gates in a batch", r);
+      gspec.push_back(s);
+    }
+    double cost = 0;
+    for (const HostPass& p : hp) {
+      TPass tp;
+      memset(&tp, 0, sizeof(tp));
+      for (int k = 0; k < m; ++k) tp.tbits[k] = (uint8_t)p.tbits[k];
+      int ng = 0;
+      for (int qb = 0; qb < n; ++qb)
+        if (std::find(p.tbits.begin(), p.tbits.end(), qb) == p.tbits.end()) tp.gbits[ng++] = (uint8_t)qb;
+      tp.phase0 = (int)phases.size();
+      tp.nphase = (int)p.phases.size();
+      for (const HostPhase& ph : p.phases) {
+        TPhase t;
+        phase_positions(p, ph, &t);
+        // register qubit -> phase bit index
+        auto pbit = [&](int qb) {
+          for (int k = 0; k < kRB; ++k)
+            if (ph.rbits[k] == qb) return k;
+          return -1;
+        };
+        t.bop0 = (int)bops.size();
+        t.fop0 = (int)fops.size();
+        std::vector<int> last(kRB, -1);  // forward op index (in fops) open for fusion per phase bit
+        for (int gi : ph.gates) {
+          const qs_gate_desc& g = c->gates[gi];
+          const int tb = pbit(g.locs[0]);
+          uint8_t cm = 0, cv = 0;
+          for (int qb = 0; qb < n; ++qb)
+            if ((g.ctrl_mask >> qb) & 1ull) {
+              const int k = pbit(qb);
+              cm |= (uint8_t)(1 << k);
+              if ((g.ctrl_vals >> qb) & 1ull) cv |= (uint8_t)(1 << k);
+            }
+          // backward op: one per gate
+          TOp b;
+          memset(&b, 0, sizeof(b));
+          b.t = (uint8_t)tb;
+          b.cmask = cm;
+          b.cval = cv;
+          b.param = g.param;
+          b.gen = g.param >= 0 ? (uint8_t)gen_of(g.kind, &b.cfac2) : GEN_NONE;
+          // uncompute kind: the generator picks the structured form (Rx / Ry / diagonal)
+          if (b.gen == GEN_X) b.kind = TK_RX;
+          else if (b.gen == GEN_Y) b.kind = TK_RY;
+          else if (b.gen != GEN_NONE) b.kind = TK_DIAG;
+          else b.kind = g.kind == QS_GATE_X ? TK_SWAP : diag_kind(g.kind) ? TK_DIAG : TK_DENSE;
+          if (g.param >= 0 && b.gen == GEN_NONE)
+            return fail(QS_EUNSUPPORTED, "register %d gate %d: kind %d has no batched gradient", r, gi, g.kind);
+          for (int q = t.bop0; q < (int)bops.size(); ++q)
+            if (bops[q].gen != GEN_NONE && b.gen != GEN_NONE && bops[q].param == b.param) {
+              bops[q].shared = 1;
+              b.shared = 1;
+            }
+          bops.push_back(b);
+          bgate.push_back(g0 + gi);
+          // forward op: fuse consecutive uncontrolled gates on one target
+          const bool fusable = cm == 0 && g.kind != QS_GATE_X;
+          if (fusable && last[tb] >= 0 && fmem[last[tb]].count < 4) {
+            FMem& fm = fmem[last[tb]];
+            fm.g[fm.count++] = g0 + gi;
+            if (!diag_kind(g.kind)) fops[last[tb]].kind = TK_DENSE;
+          } else {
+            TOp f;
+            memset(&f, 0, sizeof(f));
+            f.kind = g.kind == QS_GATE_X ? TK_SWAP : diag_kind(g.kind) ? TK_DIAG : TK_DENSE;
+            f.t = (uint8_t)tb;
+            f.cmask = cm;
+            f.cval = cv;
+            f.param = -1;
+            FMem fm;
+            memset(&fm, 0, sizeof(fm));
+            fm.count = 1;
+            fm.g[0] = g0 + gi;
+            fops.push_back(f);
+            fmem.push_back(fm);
+            // any gate on this target (or using it as control) closes fusion on the touched bits
+            for (int k = 0; k < kRB; ++k)
+              if ((cm >> k) & 1) last[k] = -1;
+            last[tb] = fusable ? (int)fops.size() - 1 : -1;
+          }
+          // a controlled gate closes fusion on its control bits and target
+          if (cm) {
+            for (int k = 0; k < kRB; ++k)
+              if ((cm >> k) & 1) last[k] = -1;
+            last[tb] = -1;
+          }
+        }
+        t.nbop = (int)bops.size() - t.bop0;
+        t.nfop = (int)fops.size() - t.fop0;
+        if (t.nbop > kMaxPhaseOps) return fail(QS_EUNSUPPORTED, "phase with %d ops", t.nbop);
+        phases.push_back(t);
+        cost += (double)(1ll << n) * (1 + 0.02 * t.nbop);
+      }
+      passes.push_back(tp);
+    }
+    R.cost = cost;
+  }
+  // decreasing cost order
+  std::vector<int32_t> order(nreg);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return regs[a].cost > regs[b].cost; });
+  P->nfop = (int)fops.size();
+  P->nbop = (int)bops.size();
+  P->npass = (int64_t)passes.size();
+  P->nphase = (int64_t)phases.size();
+  P->work_elems = work;
+  QS_TRY(upload(&P->regs, regs));
+  QS_TRY(upload(&P->order, order));
+  QS_TRY(upload(&P->passes, passes));
+  QS_TRY(upload(&P->phases, phases));
+  QS_TRY(upload(&P->fops, fops));
+  QS_TRY(upload(&P->bops, bops));
+  QS_TRY(upload(&P->terms, terms));
+  QS_TRY(upload(&P->gspec, gspec));
+  QS_TRY(upload(&P->fmem, fmem));
+  QS_TRY(upload(&P->bgate, bgate));
+  QS_TRY(upload(&P->counter, std::vector<int>(1, 0)));
+  if (work > 0) {
+    if (cudaMalloc(&P->wpsi, sizeof(float2) * work) != cudaSuccess ||
+        cudaMalloc(&P->wlam, sizeof(float2) * work) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(QS_ENOMEM, "cudaMalloc of the backward work buffers failed");
+    }
+  }
+  P->smem = ((sizeof(BShared) + 255) & ~size_t(255)) + 2 * sizeof(float2) * (1 << kBatchTile);
+  QS_CUDA(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smem));
+  int dev = 0, sms = 0, per_sm = 0;
+  QS_CUDA(cudaGetDevice(&dev));
+  QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  QS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kTileThreads, P->smem));
+  if (per_sm < 1) return fail(QS_EDEVICE, "batched kernel does not fit on an SM");
+  P->blocks = std::min(nreg, sms * per_sm);
+  return QS_OK;
+}
+
+}  // namespace qs
+
+using namespace qs;
+
+extern "C" {
+
+int qs_batch_program_create(int nreg, const qs_circuit* const* circuits, const qs_observable* const* observables,
+                            int tile_qubits, qs_batch_program** out) {
+  if (!out || nreg < 1 || !circuits || !observables) return fail(QS_EINVAL, "bad arguments");
+  *out = nullptr;
+  qs_batch_program* P = new qs_batch_program();
+  const int rc = build_program(nreg, circuits, observables, tile_qubits, P);
+  if (rc != QS_OK) {
+    const std::string msg = qs_last_error();
+    free_program(P);
+    return fail(rc, "%s", msg.c_str());
+  }
+  *out = P;
+  return QS_OK;
+}
+
+int qs_batch_program_destroy(qs_batch_program* p) {
+  free_program(p);
+  return QS_OK;
+}
+
+int qs_batch_program_info(const qs_batch_program* p, int* nreg, int64_t* nparams_total, int64_t* host_param_offsets,
+                          int64_t* host_amp_offsets) {
+  if (!p) return fail(QS_EINVAL, "null program");
+  if (nreg) *nreg = p->nreg;
+  if (nparams_total) *nparams_total = p->param_off[p->nreg];
+  if (host_param_offsets) std::copy(p->param_off.begin(), p->param_off.end(), host_param_offsets);
+  if (host_amp_offsets) std::copy(p->amp_off.begin(), p->amp_off.end(), host_amp_offsets);
+  return QS_OK;
+}
+
+int qs_batch_run(qs_state* s, const qs_batch_program* p, const double* dev_params, double* dev_loss,
+                 double* dev_grad, int flags) {
+  if (!s || !p || !dev_loss) return fail(QS_EINVAL, "null argument");
+  if (s->dtype != QS_C64) return fail(QS_EUNSUPPORTED, "the batched engine runs complex64 states");
+  if (s->nreg != p->nreg) return fail(QS_EINVAL, "state has %d registers, program %d", s->nreg, p->nreg);
+  for (int r = 0; r < s->nreg; ++r)
+    if (s->nq[r] != p->nq[r]) return fail(QS_EINVAL, "register %d: %d qubits in the state, %d in the program", r, s->nq[r], p->nq[r]);
+  if (p->param_off[p->nreg] > 0 && !dev_params) return fail(QS_EINVAL, "params is NULL");
+  const bool grad = (flags & QS_BATCH_GRAD) != 0;
+  if (grad && !dev_grad) return fail(QS_EINVAL, "grad is NULL");
+  cudaStream_t st = s->stream;
+  PrepArgs pa;
+  pa.gspec = p->gspec;
+  pa.fmem = p->fmem;
+  pa.bgate = p->bgate;
+  pa.fops = p->fops;
+  pa.bops = p->bops;
+  pa.params = dev_params;
+  pa.nfop = p->nfop;
+  pa.nbop = p->nbop;
+  const int tot = p->nfop + p->nbop;
+  if (tot > 0) {
+    k_batch_prep<<<(tot + 255) / 256, 256, 0, st>>>(pa);
+    QS_LAUNCHED();
+  }
+  QS_CUDA(cudaMemsetAsync(p->counter, 0, sizeof(int), st));
+  BArgs a;
+  a.state = (float2*)s->data;
+  a.wpsi = p->wpsi;
+  a.wlam = p->wlam;
+  a.regs = p->regs;
+  a.order = p->order;
+  a.passes = p->passes;
+  a.phases = p->phases;
+  a.fops = p->fops;
+  a.bops = p->bops;
+  a.terms = p->terms;
+  a.loss = dev_loss;
+  a.grad = dev_grad;
+  a.counter = p->counter;
+  a.nreg = p->nreg;
+  a.flags = ((flags & QS_BATCH_RESET) ? BF_RESET : 0) | (grad ? BF_GRAD : 0);
+  k_batch<<<p->blocks, kTileThreads, p->smem, st>>>(a);
+  QS_LAUNCHED();
+  return QS_OK;
+}
+
+}  // extern "C"

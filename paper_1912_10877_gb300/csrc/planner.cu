@@ -1,0 +1,110 @@
+// planner.cu -- host-side scheduling of a gate list into fused tile passes and
+// register phases (see tiles.cuh).  Gates move earlier only past gates that
+// share no qubit with them, so the schedule applies the same operator.
+#include <algorithm>
+#include <cstring>
+
+#include "tiles.cuh"
+
+namespace qs {
+
+static uint64_t qubits_of(const qs_gate_desc& g) {
+  uint64_t q = g.ctrl_mask;
+  for (int j = 0; j < g.nlocs; ++j) q |= 1ull << g.locs[j];
+  return q;
+}
+
+// greedy scan: take gates (in order) whose qubits fit in `set` grown up to
+// `cap` bits, skipping (and blocking the qubits of) gates that do not fit or
+// depend on a skipped gate; at most `limit` gates are taken
+static void scan(const std::vector<int>& rem, const std::vector<uint64_t>& q, uint64_t& set, int cap, size_t limit,
+                 std::vector<int>& taken, std::vector<int>& left) {
+  uint64_t blocked = 0;
+  for (int gi : rem) {
+    const uint64_t g = q[gi];
+    if ((g & blocked) || taken.size() >= limit) {
+      blocked |= g;
+      left.push_back(gi);
+      continue;
+    }
+    const uint64_t u = set | g;
+    if (__builtin_popcountll(u) <= cap) {
+      set = u;
+      taken.push_back(gi);
+    } else {
+      blocked |= g;
+      left.push_back(gi);
+    }
+  }
+}
+
+static std::vector<int> bits_of(uint64_t m) {
+  std::vector<int> v;
+  for (int q = 0; q < 64; ++q)
+    if ((m >> q) & 1ull) v.push_back(q);
+  return v;
+}
+
+int plan_passes(const qs_circuit* c, int n, int m, int max_phase_ops, std::vector<HostPass>& out) {
+  out.clear();
+  if (m < kRowBits || m > n || m > kMaxTileBits)
+    return fail(QS_EINVAL, "tile of %d qubits for a register of %d", m, n);
+  const int G = (int)c->gates.size();
+  std::vector<uint64_t> q(G);
+  for (int i = 0; i < G; ++i) {
+    const qs_gate_desc& g = c->gates[i];
+    if (g.nlocs != 1)
+      return fail(QS_EUNSUPPORTED, "gate %d: the fused tile engine takes single-target gates (kind %d, %d targets)",
+                  i, g.kind, g.nlocs);
+    q[i] = qubits_of(g);
+    if (__builtin_popcountll(q[i]) > kRB)
+      return fail(QS_EUNSUPPORTED, "gate %d touches more than %d qubits", i, kRB);
+  }
+  const uint64_t seed = (1ull << kRowBits) - 1ull;  // register qubits 0..4: contiguous tile rows
+  std::vector<int> rem(G);
+  for (int i = 0; i < G; ++i) rem[i] = i;
+  while (!rem.empty()) {
+    uint64_t B = seed;
+    std::vector<int> taken, left;
+    scan(rem, q, B, m, (size_t)-1, taken, left);
+    if (taken.empty()) return fail(QS_EUNSUPPORTED, "no gate fits a %d-qubit tile", m);
+    for (int b = 0; __builtin_popcountll(B) < m && b < n; ++b) B |= 1ull << b;  // pad with low qubits
+    HostPass P;
+    P.tbits = bits_of(B);
+    std::vector<int> prem = taken;
+    while (!prem.empty()) {
+      uint64_t R = 0;
+      std::vector<int> pt, pl;
+      scan(prem, q, R, kRB, (size_t)max_phase_ops, pt, pl);
+      for (int b : P.tbits) {
+        if (__builtin_popcountll(R) >= kRB) break;
+        R |= 1ull << b;
+      }
+      HostPhase ph;
+      std::vector<int> rb = bits_of(R);
+      for (int k = 0; k < kRB; ++k) ph.rbits[k] = rb[k];
+      ph.gates = pt;
+      P.phases.push_back(ph);
+      prem.swap(pl);
+    }
+    out.push_back(std::move(P));
+    rem.swap(left);
+  }
+  return QS_OK;
+}
+
+void phase_positions(const HostPass& p, const HostPhase& ph, TPhase* out) {
+  memset(out, 0, sizeof(*out));
+  const int m = (int)p.tbits.size();
+  int nt = 0, nr = 0;
+  for (int l = 0; l < m; ++l) {
+    const int qb = p.tbits[l];
+    bool inR = false;
+    for (int k = 0; k < kRB; ++k)
+      if (ph.rbits[k] == qb) inR = true;
+    if (inR) out->rpos[nr++] = (uint8_t)l;
+    else out->tpos[nt++] = (uint8_t)l;
+  }
+}
+
+}  // namespace qs

@@ -1,0 +1,78 @@
+// tiles.cuh -- fused-pass representation shared by the batched engine and the
+// single-register fused path (sm_103a).
+//
+// A circuit is scheduled into PASSES.  A pass owns a set B of m register
+// qubits (its tile bits): the state is cut into 2^(n-m) tiles of 2^m
+// amplitudes that differ only in those bits, each tile is staged in shared
+// memory, and every gate of the pass touches only qubits of B.  A pass is cut
+// into PHASES: a phase owns 4 of the tile's bits (its register bits R); each
+// of the 2^(m-4) threads holds the 16 amplitudes of the tile that differ only
+// in R in registers, applies the phase's gates there, and writes them back.
+// The planner keeps gate order valid by moving a gate earlier only past gates
+// that share no qubit with it.
+#pragma once
+
+#include "common.cuh"
+
+namespace qs {
+
+constexpr int kRB = 4;             // register bits per phase (16 amplitudes per thread)
+constexpr int kRowBits = 5;        // tile rows: 32 consecutive amplitudes (register qubits 0..4)
+constexpr int kMaxTileBits = 13;
+constexpr int kTileThreads = 1 << (kMaxTileBits - kRB);  // 512
+
+// one gate inside a phase (targets and controls are phase-local bit indices 0..3)
+struct TOp {
+  uint8_t kind;   // TK_*
+  uint8_t t;      // target bit (0..3)
+  uint8_t cmask;  // control bits (0..3)
+  uint8_t cval;   // required control values
+  uint8_t gen;    // backward ops: generator code (GEN_*), 0 = no parameter
+  uint8_t shared; // backward ops: the parameter also appears in another op of the phase
+  uint8_t pad[2];
+  int32_t param;  // register-local parameter index, -1 = none
+  float cfac2;    // 2 c for U = exp(-i theta c H)
+  float2 u[4];    // forward: U; backward: U^dagger (row-major 2x2)
+};
+
+// TK_RX: u0 = u3 = c (real), u1 = u2 = i s; TK_RY: u0 = u3 = c, u1 = -s, u2 = s
+enum { TK_DENSE = 0, TK_SWAP = 1, TK_DIAG = 2, TK_RX = 3, TK_RY = 4 };
+enum { GEN_NONE = 0, GEN_X = 1, GEN_Y = 2, GEN_Z = 3, GEN_P1 = 4, GEN_I = 5 };
+
+struct TPhase {
+  uint8_t rpos[kRB];        // tile-local positions of the register bits (ascending)
+  uint8_t tpos[12];         // tile-local positions of the thread bits (ascending)
+  int32_t fop0, nfop;       // forward ops (fused), applied in order
+  int32_t bop0, nbop;       // backward ops (unfused), applied in reverse order
+};
+
+struct TPass {
+  uint8_t tbits[16];        // register qubits of tile-local bits 0..m-1 (ascending)
+  uint8_t gbits[32];        // register qubits of the tile-id bits (ascending)
+  int32_t phase0, nphase;
+};
+
+struct HostPhase {
+  int rbits[kRB];           // register qubits of the phase (ascending)
+  std::vector<int> gates;   // circuit gate indices in forward order
+};
+
+struct HostPass {
+  std::vector<int> tbits;   // register qubits of the tile (ascending)
+  std::vector<HostPhase> phases;
+};
+
+// Greedy commutation-aware scheduling: passes of m qubits (always containing
+// register qubits 0..4, so tile rows are contiguous), phases of exactly kRB of
+// the pass's qubits.  Gates must be single-target (controls allowed) with all
+// qubits inside a phase.  Returns QS_OK or QS_EUNSUPPORTED.
+int plan_passes(const qs_circuit* c, int n, int m, int max_phase_ops, std::vector<HostPass>& out);
+
+// tile-local positions of a phase's register bits and thread bits
+void phase_positions(const HostPass& p, const HostPhase& ph, TPhase* out);
+
+// swizzled shared-memory slot of tile-local amplitude l (spreads the 8-byte
+// accesses of a half-warp over all banks for the phase patterns used here)
+__device__ __forceinline__ uint32_t swz(uint32_t l) { return l ^ ((l >> 5) & 15u); }
+
+}  // namespace qs

@@ -135,9 +135,10 @@ class State:
                                       N.i32(ctrl_locs), N.i32(ctrl_vals or [1] * len(ctrl_locs))))
         return self
 
-    def apply_circuit(self, circuit: "Circuit", params=None, per_register=False):
+    def apply_circuit(self, circuit: "Circuit", params=None, per_register=False, fused=True):
         p = _params_array(params, circuit.nparams * (self.nreg if per_register else 1))
-        N.check(N.lib().qs_apply_circuit(self.handle, circuit.handle, N.dptr(p), 1 if per_register else 0))
+        flags = (N.QS_APPLY_PER_REGISTER if per_register else 0) | (0 if fused else N.QS_APPLY_UNFUSED)
+        N.check(N.lib().qs_apply_circuit(self.handle, circuit.handle, N.dptr(p), flags))
         return self
 
     def expect(self, obs: "Observable") -> np.ndarray:
@@ -278,3 +279,56 @@ def backward(state: State, circuit: Circuit, params, obs: Observable, ckpt_every
     N.check(N.lib().qs_backward(state.handle, circuit.handle, N.dptr(p), obs.handle, int(ckpt_every), ck,
                                 ctypes.c_void_p(work.data_ptr()), N.dptr(grad), N.dptr(loss)))
     return float(loss[0]), grad[:circuit.nparams]
+
+
+class BatchProgram:
+    """Per-register circuits and diagonal observables of a batch of uneven registers,
+    scheduled once into fused tile passes (qs_batch_program)."""
+
+    def __init__(self, circuits, observables, tile_qubits: int = 0):
+        L = N.lib()
+        nreg = len(circuits)
+        if len(observables) != nreg:
+            raise ValueError("one observable per register")
+        ch = (ctypes.c_void_p * nreg)(*[c.handle.value for c in circuits])
+        oh = (ctypes.c_void_p * nreg)(*[o.handle.value for o in observables])
+        h = ctypes.c_void_p()
+        N.check(L.qs_batch_program_create(nreg, ctypes.cast(ch, ctypes.POINTER(ctypes.c_void_p)),
+                                          ctypes.cast(oh, ctypes.POINTER(ctypes.c_void_p)), int(tile_qubits),
+                                          ctypes.byref(h)))
+        self.handle = h
+        self.nreg = nreg
+        self.counts = [c.nqubits for c in circuits]
+        tot = ctypes.c_int64()
+        po = np.zeros(nreg + 1, np.int64)
+        ao = np.zeros(nreg + 1, np.int64)
+        N.check(L.qs_batch_program_info(h, None, ctypes.byref(tot), po.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                        ao.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        self.nparams = int(tot.value)
+        self.param_offsets = po
+        self.amp_offsets = ao
+        self._keep = (circuits, observables)
+
+    def run(self, state: State, params: torch.Tensor, grad: bool = True, reset: bool = True,
+            loss: torch.Tensor | None = None, grad_out: torch.Tensor | None = None):
+        """One persistent launch: forward (+ backward).  params: flat float64 CUDA tensor."""
+        if params.dtype != torch.float64 or not params.is_cuda or params.numel() != self.nparams:
+            raise ValueError("params must be a float64 CUDA tensor of nparams entries")
+        params = params.contiguous()
+        if loss is None:
+            loss = torch.empty(self.nreg, dtype=torch.float64, device=params.device)
+        if grad and grad_out is None:
+            grad_out = torch.empty(self.nparams, dtype=torch.float64, device=params.device)
+        flags = (N.QS_BATCH_RESET if reset else 0) | (N.QS_BATCH_GRAD if grad else 0)
+        N.check(N.lib().qs_batch_run(state.handle, self.handle, ctypes.c_void_p(params.data_ptr()),
+                                     ctypes.c_void_p(loss.data_ptr()),
+                                     ctypes.c_void_p(grad_out.data_ptr() if grad else 0), flags))
+        return loss, grad_out
+
+    def __del__(self):
+        try:
+            if self.handle.value:
+                N.lib().qs_batch_program_destroy(self.handle)
+                self.handle = ctypes.c_void_p()
+        except Exception:
+            pass

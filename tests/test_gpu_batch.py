@@ -1,0 +1,107 @@
+"""Batched uneven registers in one persistent launch (complex64) against the FP64
+oracle: final states (2e-5 absolute), losses (1e-5) and gradients (max abs error
+relative to the largest oracle gradient entry, 1e-4: FP32 forward and uncompute)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1912_10877_gb300 import qsim
+    return qsim
+
+
+def mixed_circuit(n, seed):
+    rs = np.random.default_rng(seed)
+    gates, params = W.variational(n, 2, "ring", seed=seed)
+    p = len(params)
+    extra = []
+    for i in range(12):
+        t = int(rs.integers(n))
+        c = int((t + 1 + rs.integers(n - 1)) % n)
+        kind = ["RY", "SHIFT", "PHASE", "RX", "RZ", "Y", "H", "S", "TDG", "MATRIX", "Z", "X"][i]
+        if kind == "MATRIX":
+            extra.append(W.Gate("MATRIX", (t,), matrix=W.haar_su2(seed + i)))
+        elif kind in ("RY", "SHIFT", "PHASE", "RX", "RZ"):
+            extra.append(W.Gate(kind, (t,), (c,), (int(rs.integers(2)),), param=p))
+            p += 1
+        else:
+            extra.append(W.Gate(kind, (t,), (c,) if i % 2 else (), (1,) if i % 2 else ()))
+    params = np.concatenate([params, rs.uniform(0, 2 * np.pi, p - len(params))])
+    return gates + extra + gates[: 3 * n], params
+
+
+def run_case(qs, specs, tile=0):
+    circs, obs, plist, terms_l, gl = [], [], [], [], []
+    for n, gates, params, terms in specs:
+        circs.append(qs.Circuit(gates, n, nparams=len(params)))
+        obs.append(qs.Observable(terms))
+        plist.append(params)
+        terms_l.append(terms)
+        gl.append(gates)
+    prog = qs.BatchProgram(circs, obs, tile_qubits=tile)
+    st = qs.State([s[0] for s in specs], dtype=torch.complex64)
+    p = torch.tensor(np.concatenate(plist), dtype=torch.float64, device="cuda")
+    loss, grad = prog.run(st, p, grad=True, reset=True)
+    torch.cuda.synchronize()
+    out = st.numpy()
+    loss = loss.cpu().numpy()
+    grad = grad.cpu().numpy()
+    for r, (n, gates, params, terms) in enumerate(specs):
+        ref_psi = oracle.apply_circuit(oracle.zero_state(n), n, gates, params)
+        got = out[int(st.offsets[r]):int(st.offsets[r + 1])]
+        assert np.max(np.abs(got - ref_psi)) < 2e-5, ("state", r, n)
+        rl, rg = oracle.gradient(oracle.zero_state(n), n, gates, params, terms)
+        assert abs(loss[r] - rl) < 1e-5, ("loss", r, n, loss[r], rl)
+        g = grad[prog.param_offsets[r]:prog.param_offsets[r + 1]]
+        assert np.max(np.abs(g - rg)) / max(1e-12, np.max(np.abs(rg))) < 1e-4, ("grad", r, n)
+
+
+def test_batch_variational_uneven_sizes(qs):
+    specs = []
+    for r, n in enumerate([5, 13, 7, 14, 9, 15, 10, 6]):
+        gates, params = W.variational(n, 3, "ladder", seed=100 + r)
+        specs.append((n, gates, params, W.zz_chain(n)))
+    run_case(qs, specs)
+
+
+def test_batch_streamed_tiles_small_tile(qs):
+    # tiles of 8 qubits: registers of 9..12 qubits take the streamed path
+    specs = []
+    for r, n in enumerate([9, 12, 8, 11]):
+        gates, params = W.variational(n, 2, "ring", seed=r)
+        specs.append((n, gates, params, W.zz_chain(n) + [(0.5, ((0, "Z"),))]))
+    run_case(qs, specs, tile=8)
+
+
+def test_batch_mixed_gate_kinds(qs):
+    specs = []
+    for r, n in enumerate([6, 11, 14]):
+        gates, params = mixed_circuit(n, r)
+        specs.append((n, gates, params, W.zz_chain(n, periodic=True)))
+    run_case(qs, specs)
+    specs = [(n, *mixed_circuit(n, 7), W.zz_chain(n)) for n in (9, 10)]
+    run_case(qs, specs, tile=7)
+
+
+def test_batch_forward_only_and_rejects(qs):
+    n = 8
+    gates, params = W.variational(n, 2, "ladder", seed=3)
+    prog = qs.BatchProgram([qs.Circuit(gates, n)], [qs.Observable(W.zz_chain(n))])
+    st = qs.State([n], dtype=torch.complex64)
+    loss, g = prog.run(st, torch.tensor(params, dtype=torch.float64, device="cuda"), grad=False)
+    ref = oracle.expect(oracle.apply_circuit(oracle.zero_state(n), n, gates, params), n, W.zz_chain(n))
+    assert g is None and abs(loss.item() - ref) < 1e-5
+    from paper_1912_10877_gb300 import QsimError
+    with pytest.raises(QsimError):  # non-diagonal observable
+        qs.BatchProgram([qs.Circuit(gates, n)], [qs.Observable([(1.0, ((0, "X"),))])])
+    with pytest.raises(QsimError):  # two-target gate
+        qs.BatchProgram([qs.Circuit([W.Gate("SWAP", (0, 1))], n)], [qs.Observable(W.zz_chain(n))])
