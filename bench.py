@@ -309,6 +309,105 @@ def run_batch_leg(steps: int, warmup: int, compare: bool = True):
     return res
 
 
+# ------------------------------------------------------------------ differentiation and large registers
+
+def run_diff_leg(steps: int, warmup: int):
+    """n = 20, 100 layers of Rz Rx Rz on every qubit + CNOT ring (8000 gates, 6000 angles),
+    transverse-field Ising loss.  (a) complex64 forward with checkpoints every 10 layers and
+    the FP64 reversible uncompute (qs_backward); (b) the tile engine: fused forward and the
+    FP32 tiled backward (qs_backward_tiled)."""
+    import torch
+    from paper_1912_10877_gb300 import qsim
+    n, depth = 20, 100
+    gates, params = W.variational(n, depth, "ring", seed=0)
+    circ = qsim.Circuit(gates, n)
+    obs = qsim.Observable(W.tfim(n))
+    every = 10 * 4 * n
+    st = qsim.State(n, dtype=torch.complex64)
+    ck = qsim.checkpoint_buffer(st, circ, every)
+    work = qsim.backward_work(n)
+
+    def fp64_path():
+        st.reset()
+        qsim.apply_circuit_ckpt(st, circ, params, every, ck)
+        return qsim.backward(st, circ, params, obs, every, ck, work)
+
+    def tiled_path():
+        st.reset()
+        st.apply_circuit(circ, params, tiles=True)
+        return qsim.backward_tiled(st, circ, params, obs)
+
+    out = {}
+    for name, fn in (("fp64_uncompute_ckpt10", fp64_path), ("tiled_fp32", tiled_path)):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            fn()
+        torch.cuda.synchronize()
+        out[name] = round((time.perf_counter() - t0) / steps, 4)
+    return {"metric": "fwd+grad seconds (n=20, 8000 gates, 6000 angles)", "unit": "s",
+            "value": out["fp64_uncompute_ckpt10"], "tiled_fp32_value": out["tiled_fp32"],
+            "passes": qsim.schedule_info(circ)[0], "higher_is_better": False,
+            "config": {"workload": "n=20, 100 x (Rz Rx Rz per qubit + CNOT ring), <sum ZZ + sum X>, seed 0",
+                       "checkpoints": f"every {every} gates (10 layers)"}}
+
+
+def run_large_leg(steps: int, warmup: int):
+    """n = 32 (32 GiB complex64): QFT with swap network on a seeded basis state, depth-20
+    brickwork of Rz + Haar SU(2) + CZ, reversible gradient of <Z_1> w.r.t. the 640 angles,
+    all on the tile engine (one HBM round trip of the state per pass)."""
+    import torch
+    from paper_1912_10877_gb300 import qsim
+    n, depth = 32, 20
+    x = W.random_basis(n, seed=0)
+    qc = qsim.Circuit(W.qft(n, swaps=True), n)
+    bgates, bparams = W.brickwork(n, depth, seed=0)
+    bc = qsim.Circuit(bgates, n, nparams=len(bparams))
+    obs = qsim.Observable(W.z_on(0))
+    st = qsim.State(n, dtype=torch.complex64)
+    b = ctypes.c_size_t()
+    from paper_1912_10877_gb300 import _native as Nn
+    Nn.check(Nn.lib().qs_backward_tiled_work_bytes(n, ctypes.byref(b)))
+    work = torch.empty(b.value, dtype=torch.uint8, device="cuda")
+    qp, bp = qsim.schedule_info(qc)[0], qsim.schedule_info(bc)[0]
+
+    def fwd():
+        st.reset([x])
+        st.apply_circuit(qc, tiles=True)
+        st.apply_circuit(bc, bparams, tiles=True)
+
+    for _ in range(warmup):
+        fwd()
+        qsim.backward_tiled(st, bc, bparams, obs, work=work)
+    torch.cuda.synchronize()
+    tf = tb = 0.0
+    for _ in range(steps):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        fwd()
+        e1.record()
+        qsim.backward_tiled(st, bc, bparams, obs, work=work)
+        e2.record()
+        torch.cuda.synchronize()
+        tf += e0.elapsed_time(e1) / 1e3
+        tb += e1.elapsed_time(e2) / 1e3
+    tf /= steps
+    tb /= steps
+    S = 8 << n
+    fwd_bytes = (qp + bp) * 2 * S          # every pass reads and writes the state once
+    bwd_bytes = bp * 4 * S                 # psi and lambda
+    return {"metric": "n=32 QFT + depth-20 brickwork forward and <Z_1> gradient", "unit": "s",
+            "value": round(tf + tb, 4), "forward_s": round(tf, 4), "backward_s": round(tb, 4),
+            "passes": {"qft": qp, "brickwork": bp},
+            "gates": {"qft": len(W.qft(n, swaps=True)), "brickwork": len(bgates)},
+            "forward_gbs": round(fwd_bytes / tf / 1e9, 1), "backward_gbs": round(bwd_bytes / tb / 1e9, 1),
+            "higher_is_better": False,
+            "config": {"workload": "n=32 c64, QFT+swaps on basis state (seed 0), brickwork depth 20 (seed 0), "
+                                   "grad of <Z_1> wrt 640 angles", "state_gib": 32}}
+
+
 # ------------------------------------------------------------------ CPU baseline (oracle)
 
 def oracle_baseline(budget_s: float = 15.0):
@@ -357,6 +456,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--reps", type=int, default=REPS, help="repetitions per gate (profiling runs use 1)")
     args = ap.parse_args()
     REPS = args.reps
@@ -443,6 +543,9 @@ def main():
         del c128
     if not args.no_batch:
         extra["batched"] = run_batch_leg(max(1, args.steps), max(1, args.warmup), compare=not args.no_compare)
+    if not args.no_large:
+        extra["differentiation"] = run_diff_leg(1, 1)
+        extra["large"] = run_large_leg(1, 1)
     launches = REPS * len(W.single_gate_suite(N_QUBITS)) * args.steps
     line = {"metric": "gate HBM GB/s at n=25 (single-gate suite, complex64)", "value": round(value, 1),
             "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

@@ -155,14 +155,32 @@ int qs_circuit_create(int nqubits, const qs_gate_desc* host_gates, int ngates,
 int qs_circuit_destroy(qs_circuit* c);
 int qs_circuit_info(const qs_circuit* c, int* nqubits, int* ngates, int* nparams);
 
+/* Passes and phases of the circuit's tile-engine schedule for tiles of
+ * tile_qubits qubits (0 = 13); builds and caches the schedule (device
+ * tables) if needed.  QS_EUNSUPPORTED if the circuit does not fit the engine. */
+int qs_circuit_schedule_info(const qs_circuit* c, int tile_qubits, int* npasses, int* nphases);
+
 /* apply!(reg, chain): gates in list order on every register of s (Sec.
  * "Representing Quantum Circuits").  host_params: nparams doubles shared by
  * all registers, or nbatch * nparams (register-major) with
  * QS_APPLY_PER_REGISTER.  By default consecutive single-qubit gates on one
  * qubit (no gate on that qubit in between) are multiplied on the host and
- * applied as one pass; QS_APPLY_UNFUSED launches one kernel per gate. */
+ * applied as one pass; QS_APPLY_UNFUSED launches one kernel per gate.
+ * complex64 registers of the circuit's size with at least 256 tiles of 2^13
+ * amplitudes (n >= 21, or batches) run the tile engine instead: the gate
+ * list is scheduled into passes over 13-qubit tiles (gates move earlier only
+ * past gates on other qubits), one HBM round trip of the state per pass, with
+ * every gate of a pass applied in shared memory / registers.  It takes
+ * single-target gates with up to 3 controls plus SWAPs (as three CNOTs);
+ * other circuits use the per-gate path.  QS_APPLY_TILES forces the tile
+ * engine (QS_EUNSUPPORTED if the circuit does not fit) and
+ * QS_APPLY_TILE_QUBITS(m) sets the tile size (5..13).  A circuit keeps its
+ * schedule and a parameter buffer between calls, so applies of one circuit
+ * must not overlap on different streams. */
 #define QS_APPLY_PER_REGISTER 1
 #define QS_APPLY_UNFUSED 2
+#define QS_APPLY_TILES 4
+#define QS_APPLY_TILE_QUBITS(m) ((m) << 8)
 int qs_apply_circuit(qs_state* s, const qs_circuit* c, const double* host_params, int flags);
 
 /* As qs_apply_circuit on a single register, also saving forward checkpoints:
@@ -262,6 +280,23 @@ int qs_batch_program_info(const qs_batch_program* p, int* nreg, int64_t* nparams
  * gradients.  The final states psi_N are left in s. */
 int qs_batch_run(qs_state* s, const qs_batch_program* p, const double* dev_params, double* dev_loss,
                  double* dev_grad, int flags);
+
+/* Device bytes of the work buffer of qs_backward_tiled (two complex64
+ * copies: psi and lambda). */
+int qs_backward_tiled_work_bytes(int nqubits, size_t* out_bytes);
+
+/* expect'(O, reg => circuit) for large complex64 registers (Sec. "Reverse
+ * Mode", Eq. apply-back): the same walk as qs_backward on the tile engine's
+ * schedule (passes in reverse, gates in reverse inside each phase), with the
+ * uncompute of psi and lambda in FP32 in dev_work and every gradient
+ * contribution accumulated in FP64 from the warp level up (per-CTA partials
+ * folded in CTA order, so the result is reproducible).  s holds psi_N (left
+ * unchanged); tile_qubits 0 = 13.  Gates and parameter kinds as for the tile
+ * engine of qs_apply_circuit (QS_EUNSUPPORTED otherwise); at most 64
+ * observable terms and about 11000 parameters. */
+int qs_backward_tiled(qs_state* s, const qs_circuit* c, const double* host_params,
+                      const qs_observable* o, int tile_qubits, void* dev_work, double* host_grad,
+                      double* host_loss);
 
 /* ---------------------------------------------------------------- measurement */
 

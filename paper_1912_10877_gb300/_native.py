@@ -15,7 +15,7 @@ QS_OK, QS_EINVAL, QS_ENOMEM, QS_EDEVICE, QS_ETIMEDOUT, QS_EUNSUPPORTED = 0, -1, 
 QS_C64, QS_C128 = 0, 1
 QS_MAXK = 5
 QS_BATCH_RESET, QS_BATCH_GRAD = 1, 2
-QS_APPLY_PER_REGISTER, QS_APPLY_UNFUSED = 1, 2
+QS_APPLY_PER_REGISTER, QS_APPLY_UNFUSED, QS_APPLY_TILES = 1, 2, 4
 
 GATE_KIND = {"I": 0, "X": 1, "Y": 2, "Z": 3, "H": 4, "S": 5, "SDG": 6, "T": 7, "TDG": 8,
              "RX": 9, "RY": 10, "RZ": 11, "SHIFT": 12, "PHASE": 13, "SWAP": 14, "ROT": 15,
@@ -67,6 +67,7 @@ SIGNATURES = {
     "qs_circuit_create": ([_I, ctypes.POINTER(GateDesc), _I, _PD, ctypes.c_int64, _I, _PP], _I),
     "qs_circuit_destroy": ([_P], _I),
     "qs_circuit_info": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "qs_circuit_schedule_info": ([_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "qs_apply_circuit": ([_P, _P, _PD, _I], _I),
     "qs_checkpoint_count": ([_P, _I, ctypes.POINTER(_I)], _I),
     "qs_apply_circuit_ckpt": ([_P, _P, _PD, _I, _P], _I),
@@ -76,6 +77,8 @@ SIGNATURES = {
     "qs_expect_static": ([_P, _I, _I, _I, ctypes.POINTER(PauliTerm), _I, _P, _P], _I),
     "qs_backward_work_bytes": ([_I, _PSZ], _I),
     "qs_backward": ([_P, _P, _PD, _P, _I, _P, _P, _PD, _PD], _I),
+    "qs_backward_tiled_work_bytes": ([_I, _PSZ], _I),
+    "qs_backward_tiled": ([_P, _P, _PD, _P, _I, _P, _PD, _PD], _I),
     "qs_measure": ([_P, _PD, _I, _PI64, _I], _I),
     "qs_batch_program_create": ([_I, _PP, _PP, _I, _PP], _I),
     "qs_batch_program_destroy": ([_P], _I),

@@ -161,6 +161,19 @@ static int apply_circuit_impl(qs_state* s, const qs_circuit* c, const double* pa
     }
     return QS_OK;
   }
+  // tile engine: whole circuit in fused passes when it has enough tiles to fill the GPU
+  const int tile = (flags >> 8) & 0xff;
+  const bool force_tiles = (flags & QS_APPLY_TILES) != 0;
+  if (!unfused && s->dtype == QS_C64 && s->uniform && s->nq[0] == c->nqubits) {
+    const int m = std::min(s->nq[0], tile > 0 ? tile : 13);
+    const uint64_t tiles = (uint64_t)s->nreg << (s->nq[0] - m);
+    if (force_tiles || tiles >= 256) {
+      const int rc = fused_forward(s, c, params, tile);
+      if (rc == QS_OK || rc != QS_EUNSUPPORTED || force_tiles) return rc;
+    }
+  } else if (force_tiles) {
+    return fail(QS_EUNSUPPORTED, "the tile engine runs uniform complex64 registers of the circuit's size");
+  }
   Fuser fz(s, c->nqubits);
   const size_t ab = amp_bytes(s->dtype);
   for (int k = 0; k < ng; ++k) {
@@ -339,6 +352,7 @@ int qs_circuit_create(int nqubits, const qs_gate_desc* gates, int ngates, const 
 }
 
 int qs_circuit_destroy(qs_circuit* c) {
+  if (c && c->fused) free_fused(c->fused);
   delete c;
   return QS_OK;
 }
@@ -349,6 +363,12 @@ int qs_circuit_info(const qs_circuit* c, int* nq, int* ng, int* np) {
   if (ng) *ng = (int)c->gates.size();
   if (np) *np = c->nparams;
   return QS_OK;
+}
+
+int qs_circuit_schedule_info(const qs_circuit* c, int tile_qubits, int* npasses, int* nphases) {
+  if (!c) return fail(QS_EINVAL, "null circuit");
+  if (tile_qubits < 0 || tile_qubits > 13) return fail(QS_EINVAL, "tile_qubits must be 0 or 9..13");
+  return schedule_info(c, tile_qubits, npasses, nphases);
 }
 
 int qs_apply_circuit(qs_state* s, const qs_circuit* c, const double* params, int flags) {
@@ -402,6 +422,20 @@ int qs_backward(qs_state* s, const qs_circuit* c, const double* params, const qs
   if (!s || !c || !o || !grad) return fail(QS_EINVAL, "null argument");
   if (c->nparams > 0 && !params) return fail(QS_EINVAL, "params is NULL");
   return backward(s, c, params, o, ckpt_every, ckpts, work, grad, loss);
+}
+
+int qs_backward_tiled_work_bytes(int nqubits, size_t* out) {
+  if (!out || nqubits < 1 || nqubits > QS_MAXQ) return fail(QS_EINVAL, "bad arguments");
+  *out = (size_t)2 * 8 * ((size_t)1 << nqubits);
+  return QS_OK;
+}
+
+int qs_backward_tiled(qs_state* s, const qs_circuit* c, const double* params, const qs_observable* o,
+                      int tile_qubits, void* work, double* grad, double* loss) {
+  if (!s || !c || !o || (!grad && c->nparams > 0)) return fail(QS_EINVAL, "null argument");
+  if (c->nparams > 0 && !params) return fail(QS_EINVAL, "params is NULL");
+  if (tile_qubits < 0 || tile_qubits > 13) return fail(QS_EINVAL, "tile_qubits must be 0 or 9..13");
+  return fused_backward(s, c, params, o, work, grad, loss, tile_qubits);
 }
 
 int qs_measure(qs_state* s, const double* u, int nshots, int64_t* out, int collapse) {

@@ -65,6 +65,7 @@ struct BArgs {
   const TPhase* phases;
   const TOp* fops;
   const TOp* bops;
+  const float2* dtab;    // TK_DIAG16 factor tables
   const BTerm* terms;
   double* loss;
   double* grad;
@@ -215,11 +216,11 @@ struct BShared {
 // Tile rows: tile-local bits 0..4 are register qubits 0..4 (planner seed), so a
 // row of 32 amplitudes is contiguous (256 bytes).  rowoff[] holds the register
 // offset of every row of the current pass; tile_base() the offset of a tile.
-__device__ void set_rows(BShared& S, const TPass& p, int m) {
+__device__ void set_rows(uint32_t* rowoff, const TPass& p, int m) {
   for (uint32_t row = threadIdx.x; row < (1u << (m - kRowBits)); row += blockDim.x) {
     uint32_t o = 0;
     for (int k = kRowBits; k < m; ++k) o |= ((row >> (k - kRowBits)) & 1u) << p.tbits[k];
-    S.rowoff[row] = o;
+    rowoff[row] = o;
   }
   __syncthreads();
 }
@@ -237,7 +238,7 @@ constexpr int kLdChunk = 8;
 
 template <bool TWO>
 __device__ __noinline__ void load_tiles(float2* sm0, const float2* src0, float2* sm1, const float2* src1,
-                                        const BShared& S, int m) {
+                                        const uint32_t* rowoff, int m) {
   const uint32_t nq = 1u << (m - 1);  // float4 per tile
   constexpr int C = TWO ? kLdChunk / 2 : kLdChunk;
   for (uint32_t q0 = 0; q0 < nq; q0 += C * kTileThreads) {
@@ -246,7 +247,7 @@ __device__ __noinline__ void load_tiles(float2* sm0, const float2* src0, float2*
     for (int k = 0; k < C; ++k) {
       const uint32_t q = q0 + threadIdx.x + k * kTileThreads;
       if (q < nq) {
-        const uint32_t off = S.rowoff[q >> 4] + 2 * (q & 15);
+        const uint32_t off = rowoff[q >> 4] + 2 * (q & 15);
         v0[k] = *reinterpret_cast<const float4*>(src0 + off);
         if (TWO) v1[k] = *reinterpret_cast<const float4*>(src1 + off);
       }
@@ -269,10 +270,10 @@ __device__ __noinline__ void load_tiles(float2* sm0, const float2* src0, float2*
 
 template <bool TWO>
 __device__ __noinline__ void store_tiles(const float2* sm0, float2* dst0, const float2* sm1, float2* dst1,
-                                         const BShared& S, int m) {
+                                         const uint32_t* rowoff, int m) {
   const uint32_t nq = 1u << (m - 1);
   for (uint32_t q = threadIdx.x; q < nq; q += kTileThreads) {
-    const uint32_t off = S.rowoff[q >> 4] + 2 * (q & 15);
+    const uint32_t off = rowoff[q >> 4] + 2 * (q & 15);
     const uint32_t l = 2 * q;
     const float2 a = sm0[swz(l)], b = sm0[swz(l + 1)];
     *reinterpret_cast<float4*>(dst0 + off) = make_float4(a.x, a.y, b.x, b.y);
@@ -283,11 +284,11 @@ __device__ __noinline__ void store_tiles(const float2* sm0, float2* dst0, const 
   }
 }
 
-__device__ __forceinline__ void load_tile(float2* sm, const float2* src, const BShared& S, int m) {
-  load_tiles<false>(sm, src, nullptr, nullptr, S, m);
+__device__ __forceinline__ void load_tile(float2* sm, const float2* src, const uint32_t* rowoff, int m) {
+  load_tiles<false>(sm, src, nullptr, nullptr, rowoff, m);
 }
-__device__ __forceinline__ void store_tile(const float2* sm, float2* dst, const BShared& S, int m) {
-  store_tiles<false>(sm, dst, nullptr, nullptr, S, m);
+__device__ __forceinline__ void store_tile(const float2* sm, float2* dst, const uint32_t* rowoff, int m) {
+  store_tiles<false>(sm, dst, nullptr, nullptr, rowoff, m);
 }
 
 __device__ __forceinline__ uint32_t phase_base(uint32_t tid, const TPhase& ph, int nthreadbits) {
@@ -296,37 +297,34 @@ __device__ __forceinline__ uint32_t phase_base(uint32_t tid, const TPhase& ph, i
   return b;
 }
 
-__device__ __noinline__ void run_phase_fwd(float2* sm, const TPhase* php, const TOp* fops, int m) {
+__device__ __noinline__ void run_phase_fwd(float2* sm, const TPhase* php, const TOp* fops, const float2* dtab, int m) {
   const TPhase ph = *php;
   const int ntb = m - kRB;
   if (threadIdx.x < (1u << ntb)) {
-    const uint32_t base = phase_base(threadIdx.x, ph, ntb);
-    uint32_t off[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      uint32_t o = base;
-#pragma unroll
-      for (int k = 0; k < kRB; ++k)
-        if ((j >> k) & 1) o |= 1u << ph.rpos[k];
-      off[j] = swz(o);
-    }
+    const uint32_t sb = swz(phase_base(threadIdx.x, ph, ntb));
     float2 x[16];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) x[j] = sm[off[j]];
+    for (int j = 0; j < 16; ++j) x[j] = sm[sb ^ ph.sroff[j]];
     TOp nxt = fops[ph.fop0];
     for (int o = 0; o < ph.nfop; ++o) {
       const TOp cur = nxt;
       if (o + 1 < ph.nfop) nxt = fops[ph.fop0 + o + 1];
-      apply_fwd(x, cur);
+      if (cur.kind == TK_DIAG16) {
+        const float2* t = dtab + 16 * cur.param;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) x[j] = cmulf(x[j], t[j]);
+      } else {
+        apply_fwd(x, cur);
+      }
     }
 #pragma unroll
-    for (int j = 0; j < 16; ++j) sm[off[j]] = x[j];
+    for (int j = 0; j < 16; ++j) sm[sb ^ ph.sroff[j]] = x[j];
   }
   __syncthreads();
 }
 
 __device__ __noinline__ void run_phase_bwd(float2* sx, float2* sl, const TPhase* php, const TOp* bops, int m,
-                                           BShared& S) {
+                                           float* red, double* gacc) {
   const TPhase ph = *php;
   const int ntb = m - kRB;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -334,15 +332,9 @@ __device__ __noinline__ void run_phase_bwd(float2* sx, float2* sl, const TPhase*
   float2 x[16], l[16];
   uint32_t off[16];
   {
-    const uint32_t base = active ? phase_base(threadIdx.x, ph, ntb) : 0u;
+    const uint32_t sb = active ? swz(phase_base(threadIdx.x, ph, ntb)) : 0u;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      uint32_t o = base;
-#pragma unroll
-      for (int k = 0; k < kRB; ++k)
-        if ((j >> k) & 1) o |= 1u << ph.rpos[k];
-      off[j] = swz(o);
-    }
+    for (int j = 0; j < 16; ++j) off[j] = sb ^ ph.sroff[j];
   }
   if (active) {
 #pragma unroll
@@ -359,7 +351,7 @@ __device__ __noinline__ void run_phase_bwd(float2* sx, float2* sl, const TPhase*
     if (active) part = apply_bwd(x, l, op);
     if (op.gen != GEN_NONE) {
       for (int s = 16; s > 0; s >>= 1) part += __shfl_xor_sync(0xffffffffu, part, s);
-      if (lane == 0) S.red[o * kWarps + warp] = part;
+      if (lane == 0) red[o * kWarps + warp] = part;
     }
   }
   if (active) {
@@ -378,8 +370,8 @@ __device__ __noinline__ void run_phase_bwd(float2* sx, float2* sl, const TPhase*
     const TOp& op = bops[ph.bop0 + o];
     if (op.gen != GEN_NONE && !op.shared) {
       double v = 0.0;
-      for (int w = 0; w < nw; ++w) v += (double)S.red[o * kWarps + w];
-      S.grad[op.param] += (double)op.cfac2 * v;
+      for (int w = 0; w < nw; ++w) v += (double)red[o * kWarps + w];
+      gacc[op.param] += (double)op.cfac2 * v;
     }
   }
   __syncthreads();
@@ -388,20 +380,20 @@ __device__ __noinline__ void run_phase_bwd(float2* sx, float2* sl, const TPhase*
       const TOp& op = bops[ph.bop0 + q];
       if (op.gen == GEN_NONE || !op.shared) continue;
       double v = 0.0;
-      for (int w = 0; w < nw; ++w) v += (double)S.red[q * kWarps + w];
-      S.grad[op.param] += (double)op.cfac2 * v;
+      for (int w = 0; w < nw; ++w) v += (double)red[q * kWarps + w];
+      gacc[op.param] += (double)op.cfac2 * v;
     }
   }
   __syncthreads();
 }
 
 // loss partial and lambda = w psi for the diagonal observable, over a tile in smem
-__device__ double expect_tile(float2* sx, float2* sl, uint64_t tbase, const BShared& S, int m, const BTerm* terms,
-                              int nterm) {
+__device__ double expect_tile(float2* sx, float2* sl, uint64_t tbase, const uint32_t* rowoff, int m,
+                              const BTerm* terms, int nterm) {
   const uint32_t cnt = 1u << m;
   double acc = 0.0;
   for (uint32_t l = threadIdx.x; l < cnt; l += blockDim.x) {
-    const uint64_t gi = tbase + S.rowoff[l >> kRowBits] + (l & 31u);
+    const uint64_t gi = tbase + rowoff[l >> kRowBits] + (l & 31u);
     double w = 0.0;
     for (int t = 0; t < nterm; ++t) w += (__popcll(gi & terms[t].z) & 1) ? -terms[t].coeff : terms[t].coeff;
     const float2 a = sx[swz(l)];
@@ -445,22 +437,22 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(BArgs a) {
     const TPass* P = a.passes + R.pass0;
     if (g == 0) {
       // ---- whole register in shared memory
-      set_rows(S, P[0], m);
+      set_rows(S.rowoff, P[0], m);
       if (a.flags & BF_RESET) {
         for (uint32_t l = tid; l < (1u << m); l += blockDim.x) sx[swz(l)] = make_float2(l == 0 ? 1.f : 0.f, 0.f);
       } else {
-        load_tile(sx, st, S, m);
+        load_tile(sx, st, S.rowoff, m);
       }
       __syncthreads();
       for (int pi = 0; pi < R.npass; ++pi)
-        for (int f = 0; f < P[pi].nphase; ++f) run_phase_fwd(sx, a.phases + P[pi].phase0 + f, a.fops, m);
-      store_tile(sx, st, S, m);  // psi_N
-      block_loss(expect_tile(sx, sl, 0, S, m, a.terms + R.term0, R.nterm), S, a.loss + reg);
+        for (int f = 0; f < P[pi].nphase; ++f) run_phase_fwd(sx, a.phases + P[pi].phase0 + f, a.fops, a.dtab, m);
+      store_tile(sx, st, S.rowoff, m);  // psi_N
+      block_loss(expect_tile(sx, sl, 0, S.rowoff, m, a.terms + R.term0, R.nterm), S, a.loss + reg);
       __syncthreads();
       if (grad) {
         for (int pi = R.npass - 1; pi >= 0; --pi)
           for (int f = P[pi].nphase - 1; f >= 0; --f)
-            run_phase_bwd(sx, sl, a.phases + P[pi].phase0 + f, a.bops, m, S);
+            run_phase_bwd(sx, sl, a.phases + P[pi].phase0 + f, a.bops, m, S.red, S.grad);
       }
     } else {
       // ---- tiles streamed through global memory
@@ -470,13 +462,13 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(BArgs a) {
       }
       for (int pi = 0; pi < R.npass; ++pi) {
         const TPass& p = P[pi];
-        set_rows(S, p, m);
+        set_rows(S.rowoff, p, m);
         for (uint64_t t = 0; t < ntile; ++t) {
           const uint64_t tb = tile_base(t, p, g);
-          load_tile(sx, st + tb, S, m);
+          load_tile(sx, st + tb, S.rowoff, m);
           __syncthreads();
-          for (int f = 0; f < p.nphase; ++f) run_phase_fwd(sx, a.phases + p.phase0 + f, a.fops, m);
-          store_tile(sx, st + tb, S, m);
+          for (int f = 0; f < p.nphase; ++f) run_phase_fwd(sx, a.phases + p.phase0 + f, a.fops, a.dtab, m);
+          store_tile(sx, st + tb, S.rowoff, m);
           __syncthreads();
         }
       }
@@ -485,14 +477,14 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(BArgs a) {
       float2* wp = a.wpsi + R.work_off;
       float2* wl = a.wlam + R.work_off;
       const TPass& p0 = P[0];
-      set_rows(S, p0, m);
+      set_rows(S.rowoff, p0, m);
       for (uint64_t t = 0; t < ntile; ++t) {
         const uint64_t tb = tile_base(t, p0, g);
-        load_tile(sx, st + tb, S, m);
+        load_tile(sx, st + tb, S.rowoff, m);
         __syncthreads();
-        e += expect_tile(sx, sl, tb, S, m, a.terms + R.term0, R.nterm);
+        e += expect_tile(sx, sl, tb, S.rowoff, m, a.terms + R.term0, R.nterm);
         __syncthreads();
-        if (grad) store_tiles<true>(sx, wp + tb, sl, wl + tb, S, m);
+        if (grad) store_tiles<true>(sx, wp + tb, sl, wl + tb, S.rowoff, m);
         __syncthreads();
       }
       block_loss(e, S, a.loss + reg);
@@ -500,13 +492,13 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(BArgs a) {
       if (grad) {
         for (int pi = R.npass - 1; pi >= 0; --pi) {
           const TPass& p = P[pi];
-          set_rows(S, p, m);
+          set_rows(S.rowoff, p, m);
           for (uint64_t t = 0; t < ntile; ++t) {
             const uint64_t tb = tile_base(t, p, g);
-            load_tiles<true>(sx, wp + tb, sl, wl + tb, S, m);
+            load_tiles<true>(sx, wp + tb, sl, wl + tb, S.rowoff, m);
             __syncthreads();
-            for (int f = p.nphase - 1; f >= 0; --f) run_phase_bwd(sx, sl, a.phases + p.phase0 + f, a.bops, m, S);
-            store_tiles<true>(sx, wp + tb, sl, wl + tb, S, m);
+            for (int f = p.nphase - 1; f >= 0; --f) run_phase_bwd(sx, sl, a.phases + p.phase0 + f, a.bops, m, S.red, S.grad);
+            store_tiles<true>(sx, wp + tb, sl, wl + tb, S.rowoff, m);
             __syncthreads();
           }
         }
@@ -519,16 +511,140 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(BArgs a) {
   }
 }
 
+
+// ------------------------------------------------------------------ device: fused forward passes of large registers
+
+struct FArgs {
+  float2* state;
+  const TPass* pass;
+  const TPhase* phases;
+  const TOp* fops;
+  const float2* dtab;
+  int m, g;
+  uint64_t ntile;          // tiles per register
+  uint64_t reg_stride;     // amplitudes per register
+  int nreg;
+};
+
+// One pass over every register of a uniform batch: CTA-strided over tiles,
+// each tile staged in shared memory once and run through all phases of the pass.
+__global__ void __launch_bounds__(kTileThreads, 2) k_fused_pass(FArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  uint32_t* rowoff = reinterpret_cast<uint32_t*>(smraw);
+  float2* sx = reinterpret_cast<float2*>(smraw + sizeof(uint32_t) * (1 << (kMaxTileBits - kRowBits)));
+  const TPass& p = *a.pass;
+  set_rows(rowoff, p, a.m);
+  const uint64_t total = a.ntile * (uint64_t)a.nreg;
+  for (uint64_t t = blockIdx.x; t < total; t += gridDim.x) {
+    const uint64_t r = t / a.ntile, tl = t - r * a.ntile;
+    float2* base = a.state + r * a.reg_stride + tile_base(tl, p, a.g);
+    load_tile(sx, base, rowoff, a.m);
+    __syncthreads();
+    for (int f = 0; f < p.nphase; ++f) run_phase_fwd(sx, a.phases + p.phase0 + f, a.fops, a.dtab, a.m);
+    store_tile(sx, base, rowoff, a.m);
+    __syncthreads();
+  }
+}
+
+
+// One backward pass over a single large register (complex64 psi and lambda
+// work copies): CTA-strided over tiles; every CTA accumulates the pass's
+// gradient contributions in its own FP64 shared-memory slots and writes them
+// to partials[blockIdx.x][param]; k_fold_partials sums the CTAs in order.
+struct FBArgs {
+  float2* wpsi;
+  float2* wlam;
+  const TPass* pass;
+  const TPhase* phases;
+  const TOp* bops;
+  int m, g, nparam;
+  uint64_t ntile;
+  double* partials;      // [gridDim.x][nparam]
+};
+
+__global__ void __launch_bounds__(kTileThreads, 1) k_fused_bwd_pass(FBArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  uint32_t* rowoff = reinterpret_cast<uint32_t*>(smraw);
+  float* red = reinterpret_cast<float*>(rowoff + (1 << (kMaxTileBits - kRowBits)));
+  double* gacc = reinterpret_cast<double*>(red + kMaxPhaseOps * kWarps);
+  float2* sx = reinterpret_cast<float2*>(gacc + ((a.nparam + 1) & ~1));
+  float2* sl = sx + (1 << a.m);
+  const TPass& p = *a.pass;
+  for (int i = threadIdx.x; i < a.nparam; i += blockDim.x) gacc[i] = 0.0;
+  set_rows(rowoff, p, a.m);
+  for (uint64_t t = blockIdx.x; t < a.ntile; t += gridDim.x) {
+    const uint64_t tb = tile_base(t, p, a.g);
+    load_tiles<true>(sx, a.wpsi + tb, sl, a.wlam + tb, rowoff, a.m);
+    __syncthreads();
+    for (int f = p.nphase - 1; f >= 0; --f) run_phase_bwd(sx, sl, a.phases + p.phase0 + f, a.bops, a.m, red, gacc);
+    store_tiles<true>(sx, a.wpsi + tb, sl, a.wlam + tb, rowoff, a.m);
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < a.nparam; i += blockDim.x) a.partials[(size_t)blockIdx.x * a.nparam + i] = gacc[i];
+}
+
+__global__ void k_fold_partials(const double* __restrict__ partials, int nblk, int nparam, double* __restrict__ grad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nparam) return;
+  double v = 0.0;
+  for (int b = 0; b < nblk; ++b) v += partials[(size_t)b * nparam + i];
+  grad[i] += v;
+}
+
+// lambda = O psi for complex64 work copies (FP32 arithmetic, FP64 coefficients)
+struct ObsC64 {
+  int nt;
+  uint64_t x[64];
+  uint64_t z[64];
+  int ny[64];
+  float c[64];
+};
+
+__global__ void __launch_bounds__(256) k_apply_obs_c64(const float2* __restrict__ psi, float2* __restrict__ lam,
+                                                       uint64_t dim, int accumulate, const __grid_constant__ ObsC64 o) {
+  const uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x;
+  if (i >= dim) return;
+  float2 acc = accumulate ? lam[i] : make_float2(0.f, 0.f);
+  for (int t = 0; t < o.nt; ++t) {
+    const uint64_t j = i ^ o.x[t];
+    const float2 v = psi[j];
+    const float s = (__popcll(j & o.z[t]) & 1) ? -o.c[t] : o.c[t];
+    float re, im;
+    switch (o.ny[t] & 3) {
+      case 0: re = v.x; im = v.y; break;
+      case 1: re = -v.y; im = v.x; break;
+      case 2: re = -v.x; im = -v.y; break;
+      default: re = v.y; im = -v.x; break;
+    }
+    acc.x = fmaf(s, re, acc.x);
+    acc.y = fmaf(s, im, acc.y);
+  }
+  lam[i] = acc;
+}
+
 // ------------------------------------------------------------------ device: matrices from parameters
+
+// member of a TK_DIAG16 table: a diagonal gate on the phase bits
+struct DMem {
+  int32_t g;                 // global GSpec index
+  uint8_t tb, cm, cv, pad;   // phase-local target bit, control mask and values
+};
+
+struct DRef {
+  int32_t mem0, count;       // members in dmem[]
+};
 
 struct PrepArgs {
   const GSpec* gspec;
   const FMem* fmem;
   const int32_t* bgate;
+  const DMem* dmem;
+  const DRef* dref;
   TOp* fops;
   TOp* bops;
+  float2* dtab;
   const double* params;
-  int nfop, nbop;
+  int nfop, nbop, ndiag;
 };
 
 __device__ void gate_mat(const GSpec& gs, const double* params, double2 (&U)[4]) {
@@ -587,6 +703,20 @@ __global__ void k_batch_prep(PrepArgs a) {
     a.bops[j].u[1] = make_float2((float)U[2].x, (float)-U[2].y);
     a.bops[j].u[2] = make_float2((float)U[1].x, (float)-U[1].y);
     a.bops[j].u[3] = make_float2((float)U[3].x, (float)-U[3].y);
+  } else if (i < a.nfop + a.nbop + a.ndiag) {
+    // product of the member gates' diagonals on the 16 phase amplitudes
+    const int d = i - a.nfop - a.nbop;
+    double2 f[16];
+    for (int j = 0; j < 16; ++j) f[j] = make_double2(1.0, 0.0);
+    const DRef r = a.dref[d];
+    for (int k = 0; k < r.count; ++k) {
+      const DMem mb = a.dmem[r.mem0 + k];
+      double2 U[4];
+      gate_mat(a.gspec[mb.g], a.params, U);
+      for (int j = 0; j < 16; ++j)
+        if ((j & mb.cm) == mb.cv) f[j] = zmul(f[j], ((j >> mb.tb) & 1) ? U[3] : U[0]);
+    }
+    for (int j = 0; j < 16; ++j) a.dtab[16 * d + j] = make_float2((float)f[j].x, (float)f[j].y);
   }
 }
 
@@ -611,6 +741,10 @@ struct qs_batch_program {
   qs::GSpec* gspec = nullptr;
   qs::FMem* fmem = nullptr;
   int32_t* bgate = nullptr;
+  qs::DMem* dmem = nullptr;
+  qs::DRef* dref = nullptr;
+  float2* dtab = nullptr;
+  int ndiag = 0;
   int* counter = nullptr;
   float2* wpsi = nullptr;
   float2* wlam = nullptr;
@@ -618,6 +752,12 @@ struct qs_batch_program {
   int64_t npass = 0, nphase = 0;
   int blocks = 0;
   size_t smem = 0;
+  // single-register fused forward (no observable, no backward): host copies of
+  // the pass table and a device parameter buffer
+  bool fused_only = false;
+  std::vector<qs::TPass> host_passes;
+  double* dparams = nullptr;
+  int64_t dparams_n = 0;
 };
 
 namespace qs {
@@ -653,8 +793,8 @@ static int upload(T** dst, const std::vector<T>& v) {
 
 static void free_program(qs_batch_program* p) {
   if (!p) return;
-  void* ptrs[] = {p->regs, p->order, p->passes, p->phases, p->fops, p->bops, p->terms,
-                  p->gspec, p->fmem, p->bgate, p->counter, p->wpsi, p->wlam};
+  void* ptrs[] = {p->regs, p->order, p->passes, p->phases, p->fops, p->bops, p->terms, p->gspec, p->fmem,
+                  p->bgate, p->dmem, p->dref, p->dtab, p->counter, p->wpsi, p->wlam, p->dparams};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p;
@@ -663,7 +803,9 @@ static void free_program(qs_batch_program* p) {
 static int build_program(int nreg, const qs_circuit* const* circs, const qs_observable* const* obs, int tile_qubits,
                          qs_batch_program* P) {
   const int M = tile_qubits > 0 ? tile_qubits : kBatchTile;
-  if (M < kRB || M > kBatchTile) return fail(QS_EINVAL, "tile_qubits must be in %d..%d", kRB, kBatchTile);
+  // a tile holds register qubits 0..4 plus room for any gate (target and 3 controls)
+  if (M < kRowBits + kRB || M > kBatchTile)
+    return fail(QS_EINVAL, "tile_qubits must be in %d..%d", kRowBits + kRB, kBatchTile);
   std::vector<BReg> regs(nreg);
   std::vector<TPass> passes;
   std::vector<TPhase> phases;
@@ -672,6 +814,8 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
   std::vector<GSpec> gspec;
   std::vector<FMem> fmem;
   std::vector<int32_t> bgate;
+  std::vector<DMem> dmems;
+  std::vector<DRef> drefs;
   P->nreg = nreg;
   P->nq.resize(nreg);
   P->param_off.assign(nreg + 1, 0);
@@ -679,11 +823,13 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
   int64_t work = 0;
   for (int r = 0; r < nreg; ++r) {
     const qs_circuit* c = circs[r];
-    const qs_observable* o = obs[r];
-    if (!c || !o) return fail(QS_EINVAL, "register %d: null circuit or observable", r);
+    const qs_observable* o = obs ? obs[r] : nullptr;
+    if (!c || (!o && !P->fused_only)) return fail(QS_EINVAL, "register %d: null circuit or observable", r);
     const int n = c->nqubits;
-    if (n < kRowBits || n > 30) return fail(QS_EUNSUPPORTED, "register %d: batched registers take 5..30 qubits", r);
-    if (c->nparams > kMaxRegParams) return fail(QS_EUNSUPPORTED, "register %d: more than %d parameters", r, kMaxRegParams);
+    if (n < kRowBits || n > (P->fused_only ? 32 : 30))
+      return fail(QS_EUNSUPPORTED, "register %d: %d qubits outside the tile engine's range", r, n);
+    if (!P->fused_only && c->nparams > kMaxRegParams)
+      return fail(QS_EUNSUPPORTED, "register %d: more than %d parameters", r, kMaxRegParams);
     P->nq[r] = n;
     P->param_off[r + 1] = P->param_off[r] + c->nparams;
     P->amp_off[r + 1] = P->amp_off[r] + (1ll << n);
@@ -699,16 +845,18 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
     R.nparam = c->nparams;
     R.amp_off = P->amp_off[r];
     R.param_off = P->param_off[r];
-    R.work_off = n > m ? work : -1;
-    if (n > m) work += 1ll << n;
+    R.work_off = (n > m && !P->fused_only) ? work : -1;
+    if (n > m && !P->fused_only) work += 1ll << n;
     // observable: diagonal Pauli strings only
     R.term0 = (int)terms.size();
-    for (const auto& t : o->terms) {
-      if (t.x_mask) return fail(QS_EUNSUPPORTED, "register %d: batched observables must be diagonal (Z strings)", r);
-      if (n < 64 && (t.z_mask >> n)) return fail(QS_EINVAL, "register %d: observable qubit out of range", r);
-      terms.push_back({t.coeff, t.z_mask});
+    if (o) {
+      for (const auto& t : o->terms) {
+        if (t.x_mask) return fail(QS_EUNSUPPORTED, "register %d: batched observables must be diagonal (Z strings)", r);
+        if (n < 64 && (t.z_mask >> n)) return fail(QS_EINVAL, "register %d: observable qubit out of range", r);
+        terms.push_back({t.coeff, t.z_mask});
+      }
     }
-    R.nterm = (int)o->terms.size();
+    R.nterm = o ? (int)o->terms.size() : 0;
     // gate specs of this register
     const int g0 = (int)gspec.size();
     for (const auto& g : c->gates) {
@@ -747,6 +895,8 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
         t.bop0 = (int)bops.size();
         t.fop0 = (int)fops.size();
         std::vector<int> last(kRB, -1);  // forward op index (in fops) open for fusion per phase bit
+        int dg = -1;                     // open TK_DIAG16 table of this phase
+        uint8_t nondiag = 0;             // phase bits touched by non-diagonal gates since it opened
         for (int gi : ph.gates) {
           const qs_gate_desc& g = c->gates[gi];
           const int tb = pbit(g.locs[0]);
@@ -779,12 +929,39 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
             }
           bops.push_back(b);
           bgate.push_back(g0 + gi);
-          // forward op: fuse consecutive uncontrolled gates on one target
+          // forward op: consecutive uncontrolled gates on one target fuse into one 2x2;
+          // controlled diagonal gates (CZ, controlled phases) join the phase's open
+          // 16-entry diagonal table unless a non-diagonal op since it opened shares a
+          // qubit with them (diagonal gates commute with each other)
           const bool fusable = cm == 0 && g.kind != QS_GATE_X;
+          const uint8_t gbits = (uint8_t)(cm | (1u << tb));
+          if (!diag_kind(g.kind)) nondiag |= gbits;
           if (fusable && last[tb] >= 0 && fmem[last[tb]].count < 4) {
             FMem& fm = fmem[last[tb]];
             fm.g[fm.count++] = g0 + gi;
             if (!diag_kind(g.kind)) fops[last[tb]].kind = TK_DENSE;
+          } else if (cm != 0 && diag_kind(g.kind)) {
+            if (dg < 0 || (gbits & nondiag)) {
+              TOp f;
+              memset(&f, 0, sizeof(f));
+              f.kind = TK_DIAG16;
+              f.param = (int)drefs.size();
+              FMem fm;
+              memset(&fm, 0, sizeof(fm));
+              fops.push_back(f);
+              fmem.push_back(fm);
+              drefs.push_back({(int32_t)dmems.size(), 0});
+              dg = (int)drefs.size() - 1;
+              nondiag = 0;
+            }
+            DMem mb;
+            memset(&mb, 0, sizeof(mb));
+            mb.g = g0 + gi;
+            mb.tb = (uint8_t)tb;
+            mb.cm = cm;
+            mb.cv = cv;
+            dmems.push_back(mb);
+            drefs[dg].count++;
           } else {
             TOp f;
             memset(&f, 0, sizeof(f));
@@ -840,6 +1017,10 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
   QS_TRY(upload(&P->gspec, gspec));
   QS_TRY(upload(&P->fmem, fmem));
   QS_TRY(upload(&P->bgate, bgate));
+  QS_TRY(upload(&P->dmem, dmems));
+  QS_TRY(upload(&P->dref, drefs));
+  P->ndiag = (int)drefs.size();
+  QS_TRY(upload(&P->dtab, std::vector<float2>(16 * std::max<size_t>(1, drefs.size()))));
   QS_TRY(upload(&P->counter, std::vector<int>(1, 0)));
   if (work > 0) {
     if (cudaMalloc(&P->wpsi, sizeof(float2) * work) != cudaSuccess ||
@@ -847,6 +1028,18 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
       cudaGetLastError();
       return fail(QS_ENOMEM, "cudaMalloc of the backward work buffers failed");
     }
+  }
+  P->host_passes = passes;
+  if (P->fused_only) {
+    P->smem = sizeof(uint32_t) * (1 << (kMaxTileBits - kRowBits)) + sizeof(float2) * (1 << kBatchTile);
+    QS_CUDA(cudaFuncSetAttribute(k_fused_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smem));
+    int dev = 0, sms = 0, per_sm = 0;
+    QS_CUDA(cudaGetDevice(&dev));
+    QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    QS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_pass, kTileThreads, P->smem));
+    if (per_sm < 1) return fail(QS_EDEVICE, "fused pass kernel does not fit on an SM");
+    P->blocks = sms * per_sm;
+    return QS_OK;
   }
   P->smem = ((sizeof(BShared) + 255) & ~size_t(255)) + 2 * sizeof(float2) * (1 << kBatchTile);
   QS_CUDA(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smem));
@@ -856,6 +1049,236 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
   QS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kTileThreads, P->smem));
   if (per_sm < 1) return fail(QS_EDEVICE, "batched kernel does not fit on an SM");
   P->blocks = std::min(nreg, sms * per_sm);
+  return QS_OK;
+}
+
+// matrices of the forward ops, U^dagger of the backward ops (when `bwd`) and the
+// diagonal tables from the current parameters, on the device
+static int launch_prep(const qs_batch_program* P, const double* dev_params, bool bwd, cudaStream_t st) {
+  PrepArgs pa;
+  pa.gspec = P->gspec;
+  pa.fmem = P->fmem;
+  pa.bgate = P->bgate;
+  pa.dmem = P->dmem;
+  pa.dref = P->dref;
+  pa.fops = P->fops;
+  pa.bops = P->bops;
+  pa.dtab = P->dtab;
+  pa.params = dev_params;
+  pa.nfop = P->nfop;
+  pa.nbop = bwd ? P->nbop : 0;
+  pa.ndiag = P->ndiag;
+  const int tot = pa.nfop + pa.nbop + pa.ndiag;
+  if (tot > 0) {
+    k_batch_prep<<<(tot + 255) / 256, 256, 0, st>>>(pa);
+    QS_LAUNCHED();
+  }
+  return QS_OK;
+}
+
+// ------------------------------------------------------------------ host: fused forward of one circuit
+
+// SWAP(a, b) = CX(a->b) CX(b->a) CX(a->b), each also carrying the SWAP's own controls
+static void expand_swaps(const qs_circuit* c, qs_circuit* out) {
+  out->nqubits = c->nqubits;
+  out->nparams = c->nparams;
+  out->mats = c->mats;
+  out->gates.clear();
+  for (const qs_gate_desc& g : c->gates) {
+    if (g.kind != QS_GATE_SWAP) {
+      out->gates.push_back(g);
+      continue;
+    }
+    const int a = g.locs[0], b = g.locs[1];
+    for (int k = 0; k < 3; ++k) {
+      qs_gate_desc x;
+      memset(&x, 0, sizeof(x));
+      x.kind = QS_GATE_X;
+      x.nlocs = 1;
+      x.param = -1;
+      const int t = (k == 1) ? a : b, ctl = (k == 1) ? b : a;
+      x.locs[0] = t;
+      x.ctrl_mask = g.ctrl_mask | (1ull << ctl);
+      x.ctrl_vals = (g.ctrl_vals & g.ctrl_mask) | (1ull << ctl);
+      out->gates.push_back(x);
+    }
+  }
+}
+
+// the circuit's tile-engine schedule for tiles of M qubits, built once and cached
+static int ensure_schedule(const qs_circuit* c, int M) {
+  if (c->fused && c->fused_tile == M) return QS_OK;
+  if (c->fused) {
+    free_program(c->fused);
+    c->fused = nullptr;
+  }
+  qs_circuit tmp;
+  expand_swaps(c, &tmp);
+  const qs_circuit* cp = &tmp;
+  qs_batch_program* P = new qs_batch_program();
+  P->fused_only = true;
+  const int rc = build_program(1, &cp, nullptr, M, P);
+  if (rc != QS_OK) {
+    const std::string msg = qs_last_error();
+    free_program(P);
+    return fail(rc, "%s", msg.c_str());
+  }
+  c->fused = P;
+  c->fused_tile = M;
+  return QS_OK;
+}
+
+// Applies circuit c to the (uniform, complex64) registers of s with the tile
+// engine: one launch of k_fused_pass per pass.  Returns QS_EUNSUPPORTED (with
+// nothing launched) when the circuit does not fit the engine.
+int fused_forward(qs_state* s, const qs_circuit* c, const double* host_params, int tile_qubits) {
+  if (s->dtype != QS_C64 || !s->uniform || s->nq[0] != c->nqubits)
+    return fail(QS_EUNSUPPORTED, "the tile engine runs uniform complex64 registers of the circuit's size");
+  const int n = s->nq[0];
+  const int M = tile_qubits > 0 ? tile_qubits : kBatchTile;
+  QS_TRY(ensure_schedule(c, M));
+  qs_batch_program* P = c->fused;
+  cudaStream_t st = s->stream;
+  if (c->nparams > 0) {
+    if (P->dparams_n < c->nparams) {
+      if (P->dparams) cudaFree(P->dparams);
+      P->dparams = nullptr;
+      P->dparams_n = 0;
+      if (cudaMalloc(&P->dparams, sizeof(double) * c->nparams) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(QS_ENOMEM, "cudaMalloc of the parameter buffer failed");
+      }
+      P->dparams_n = c->nparams;
+    }
+    QS_CUDA(cudaMemcpyAsync(P->dparams, host_params, sizeof(double) * c->nparams, cudaMemcpyHostToDevice, st));
+  }
+  QS_TRY(launch_prep(P, P->dparams, false, st));
+  const int m = std::min(n, M), g = n - m;
+  FArgs a;
+  a.state = (float2*)s->data;
+  a.phases = P->phases;
+  a.fops = P->fops;
+  a.dtab = P->dtab;
+  a.m = m;
+  a.g = g;
+  a.ntile = 1ull << g;
+  a.reg_stride = 1ull << n;
+  a.nreg = s->nreg;
+  const uint64_t tiles = a.ntile * (uint64_t)s->nreg;
+  const unsigned grid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)P->blocks);
+  for (int64_t pi = 0; pi < P->npass; ++pi) {
+    a.pass = P->passes + pi;
+    k_fused_pass<<<grid, kTileThreads, P->smem, st>>>(a);
+    QS_LAUNCHED();
+  }
+  return QS_OK;
+}
+
+void free_fused(qs_batch_program* p) { free_program(p); }
+
+int schedule_info(const qs_circuit* c, int tile_qubits, int* npasses, int* nphases) {
+  QS_TRY(ensure_schedule(c, tile_qubits > 0 ? tile_qubits : kBatchTile));
+  if (npasses) *npasses = (int)c->fused->npass;
+  if (nphases) *nphases = (int)c->fused->nphase;
+  return QS_OK;
+}
+
+int expect_raw(const void* data, int dtype, int n, int nreg, const qs_observable* o, qs_state* ws_owner,
+               double* host_out);
+
+// Reversible gradient of one complex64 register with the tile engine: psi_N and
+// lambda = O psi_N are copied into dev_work (2 x 2^n complex64), then the
+// schedule's passes run backwards (FP32 uncompute, FP64 accumulation of the
+// per-CTA gradient partials, folded in CTA order).
+int fused_backward(qs_state* s, const qs_circuit* c, const double* host_params, const qs_observable* o,
+                   void* dev_work, double* host_grad, double* host_loss, int tile_qubits) {
+  if (s->dtype != QS_C64 || s->nreg != 1 || s->nq[0] != c->nqubits)
+    return fail(QS_EUNSUPPORTED, "the tiled backward takes one complex64 register of the circuit's size");
+  if (!dev_work) return fail(QS_EINVAL, "work buffer is NULL");
+  const int n = s->nq[0];
+  const int M = tile_qubits > 0 ? tile_qubits : kBatchTile;
+  const int m = std::min(n, M), g = n - m;
+  for (const auto& t : o->terms)
+    if (n < 64 && ((t.x_mask | t.z_mask) >> n)) return fail(QS_EINVAL, "observable acts on a qubit >= n=%d", n);
+  if (o->terms.size() > 64) return fail(QS_EUNSUPPORTED, "the tiled backward takes at most 64 observable terms");
+  // schedule (shared with the fused forward) and parameter-dependent matrices
+  QS_TRY(ensure_schedule(c, M));
+  qs_batch_program* P = c->fused;
+  cudaStream_t st = s->stream;
+  const int np = c->nparams;
+  const size_t smem = sizeof(uint32_t) * (1 << (kMaxTileBits - kRowBits)) + sizeof(float) * kMaxPhaseOps * kWarps +
+                      sizeof(double) * ((np + 1) & ~1) + 2 * sizeof(float2) * (1ull << m);
+  if (smem > 227 * 1024) return fail(QS_EUNSUPPORTED, "%d parameters do not fit the tiled backward's shared memory", np);
+  if (host_loss) QS_TRY(expect_raw(s->data, QS_C64, n, 1, o, s, host_loss));
+  if (np > 0) {
+    if (P->dparams_n < np) {
+      if (P->dparams) cudaFree(P->dparams);
+      P->dparams = nullptr;
+      P->dparams_n = 0;
+      if (cudaMalloc(&P->dparams, sizeof(double) * np) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(QS_ENOMEM, "cudaMalloc of the parameter buffer failed");
+      }
+      P->dparams_n = np;
+    }
+    QS_CUDA(cudaMemcpyAsync(P->dparams, host_params, sizeof(double) * np, cudaMemcpyHostToDevice, st));
+  }
+  QS_TRY(launch_prep(P, P->dparams, true, st));
+  // psi and lambda work copies
+  const uint64_t dim = 1ull << n;
+  float2* wpsi = (float2*)dev_work;
+  float2* wlam = wpsi + dim;
+  QS_CUDA(cudaMemcpyAsync(wpsi, s->data, sizeof(float2) * dim, cudaMemcpyDeviceToDevice, st));
+  if (o->terms.empty()) {
+    QS_CUDA(cudaMemsetAsync(wlam, 0, sizeof(float2) * dim, st));
+  } else {
+    ObsC64 ob;
+    memset(&ob, 0, sizeof(ob));
+    ob.nt = (int)o->terms.size();
+    for (int t = 0; t < ob.nt; ++t) {
+      ob.x[t] = o->terms[t].x_mask;
+      ob.z[t] = o->terms[t].z_mask;
+      ob.ny[t] = __builtin_popcountll(o->terms[t].x_mask & o->terms[t].z_mask) & 3;
+      ob.c[t] = (float)o->terms[t].coeff;
+    }
+    k_apply_obs_c64<<<(unsigned)((dim + 255) / 256), 256, 0, st>>>(wpsi, wlam, dim, 0, ob);
+    QS_LAUNCHED();
+  }
+  // per-CTA partials and the gradient accumulator in the state's scratch
+  QS_CUDA(cudaFuncSetAttribute(k_fused_bwd_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int dev = 0, sms = 0, per_sm = 0;
+  QS_CUDA(cudaGetDevice(&dev));
+  QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  QS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_bwd_pass, kTileThreads, smem));
+  if (per_sm < 1) return fail(QS_EDEVICE, "tiled backward kernel does not fit on an SM");
+  const uint64_t ntile = 1ull << g;
+  const int grid = (int)std::min<uint64_t>(ntile, (uint64_t)sms * per_sm);
+  const size_t npad = (size_t)std::max(1, np);
+  QS_TRY(ensure_ws(s, s->ws, sizeof(double) * (npad + (size_t)grid * npad)));
+  double* dgrad = (double*)s->ws.ptr;
+  double* partials = dgrad + npad;
+  QS_CUDA(cudaMemsetAsync(dgrad, 0, sizeof(double) * npad, st));
+  FBArgs a;
+  a.wpsi = wpsi;
+  a.wlam = wlam;
+  a.phases = P->phases;
+  a.bops = P->bops;
+  a.m = m;
+  a.g = g;
+  a.nparam = np;
+  a.ntile = ntile;
+  a.partials = partials;
+  for (int64_t pi = P->npass - 1; pi >= 0; --pi) {
+    a.pass = P->passes + pi;
+    k_fused_bwd_pass<<<grid, kTileThreads, smem, st>>>(a);
+    QS_LAUNCHED();
+    if (np > 0) {
+      k_fold_partials<<<(np + 255) / 256, 256, 0, st>>>(partials, grid, np, dgrad);
+      QS_LAUNCHED();
+    }
+  }
+  if (np > 0) QS_CUDA(cudaMemcpyAsync(host_grad, dgrad, sizeof(double) * np, cudaMemcpyDeviceToHost, st));
+  QS_CUDA(cudaStreamSynchronize(st));
   return QS_OK;
 }
 
@@ -906,23 +1329,11 @@ int qs_batch_run(qs_state* s, const qs_batch_program* p, const double* dev_param
   const bool grad = (flags & QS_BATCH_GRAD) != 0;
   if (grad && !dev_grad) return fail(QS_EINVAL, "grad is NULL");
   cudaStream_t st = s->stream;
-  PrepArgs pa;
-  pa.gspec = p->gspec;
-  pa.fmem = p->fmem;
-  pa.bgate = p->bgate;
-  pa.fops = p->fops;
-  pa.bops = p->bops;
-  pa.params = dev_params;
-  pa.nfop = p->nfop;
-  pa.nbop = p->nbop;
-  const int tot = p->nfop + p->nbop;
-  if (tot > 0) {
-    k_batch_prep<<<(tot + 255) / 256, 256, 0, st>>>(pa);
-    QS_LAUNCHED();
-  }
+  QS_TRY(launch_prep(p, dev_params, true, st));
   QS_CUDA(cudaMemsetAsync(p->counter, 0, sizeof(int), st));
   BArgs a;
   a.state = (float2*)s->data;
+  a.dtab = p->dtab;
   a.wpsi = p->wpsi;
   a.wlam = p->wlam;
   a.regs = p->regs;

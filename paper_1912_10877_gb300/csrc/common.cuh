@@ -150,6 +150,9 @@ struct qs_circuit {
   int nparams = 0;
   std::vector<qs_gate_desc> gates;
   std::vector<qs::cd> mats;
+  // tile-engine schedule of this circuit (built on first fused apply)
+  mutable qs_batch_program* fused = nullptr;
+  mutable int fused_tile = 0;
 };
 
 struct qs_observable {
@@ -208,5 +211,12 @@ int gate_matrix(const qs_circuit* c, const qs_gate_desc& g, const double* params
 void dagger(std::vector<cd>& U, int k);
 void pauli_string(int k, const int32_t* paulis, std::vector<cd>& S);
 int validate_gate(int n, int k, const int32_t* locs, uint64_t ctrl_mask);
+
+// tile-engine forward of a whole circuit (batch.cu); QS_EUNSUPPORTED if it does not fit
+int fused_forward(qs_state* s, const qs_circuit* c, const double* host_params, int tile_qubits);
+int fused_backward(qs_state* s, const qs_circuit* c, const double* host_params, const qs_observable* o,
+                   void* dev_work, double* host_grad, double* host_loss, int tile_qubits);
+void free_fused(qs_batch_program* p);
+int schedule_info(const qs_circuit* c, int tile_qubits, int* npasses, int* nphases);
 
 }  // namespace qs

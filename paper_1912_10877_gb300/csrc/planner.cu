@@ -105,6 +105,12 @@ void phase_positions(const HostPass& p, const HostPhase& ph, TPhase* out) {
     if (inR) out->rpos[nr++] = (uint8_t)l;
     else out->tpos[nt++] = (uint8_t)l;
   }
+  for (int j = 0; j < (1 << kRB); ++j) {
+    uint32_t r = 0;
+    for (int k = 0; k < kRB; ++k)
+      if ((j >> k) & 1) r |= 1u << out->rpos[k];
+    out->sroff[j] = (uint16_t)swz(r);
+  }
 }
 
 }  // namespace qs

@@ -35,13 +35,16 @@ struct TOp {
   float2 u[4];    // forward: U; backward: U^dagger (row-major 2x2)
 };
 
-// TK_RX: u0 = u3 = c (real), u1 = u2 = i s; TK_RY: u0 = u3 = c, u1 = -s, u2 = s
-enum { TK_DENSE = 0, TK_SWAP = 1, TK_DIAG = 2, TK_RX = 3, TK_RY = 4 };
+// TK_RX: u0 = u3 = c (real), u1 = u2 = i s; TK_RY: u0 = u3 = c, u1 = -s, u2 = s;
+// TK_DIAG16 (forward only): amplitude j of the phase *= table[param][j], the
+// product of consecutive diagonal gates of the phase (they commute)
+enum { TK_DENSE = 0, TK_SWAP = 1, TK_DIAG = 2, TK_RX = 3, TK_RY = 4, TK_DIAG16 = 5 };
 enum { GEN_NONE = 0, GEN_X = 1, GEN_Y = 2, GEN_Z = 3, GEN_P1 = 4, GEN_I = 5 };
 
 struct TPhase {
   uint8_t rpos[kRB];        // tile-local positions of the register bits (ascending)
   uint8_t tpos[12];         // tile-local positions of the thread bits (ascending)
+  uint16_t sroff[1 << kRB]; // swz(register offset of amplitude j): slot = swz(base) ^ sroff[j]
   int32_t fop0, nfop;       // forward ops (fused), applied in order
   int32_t bop0, nbop;       // backward ops (unfused), applied in reverse order
 };
@@ -72,7 +75,8 @@ int plan_passes(const qs_circuit* c, int n, int m, int max_phase_ops, std::vecto
 void phase_positions(const HostPass& p, const HostPhase& ph, TPhase* out);
 
 // swizzled shared-memory slot of tile-local amplitude l (spreads the 8-byte
-// accesses of a half-warp over all banks for the phase patterns used here)
-__device__ __forceinline__ uint32_t swz(uint32_t l) { return l ^ ((l >> 5) & 15u); }
+// accesses of a half-warp over all banks for the phase patterns used here).
+// It is linear over XOR, so swz(base | r) = swz(base) ^ swz(r) for disjoint bits.
+__host__ __device__ __forceinline__ uint32_t swz(uint32_t l) { return l ^ ((l >> 5) & 15u); }
 
 }  // namespace qs

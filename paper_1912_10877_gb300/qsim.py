@@ -135,9 +135,13 @@ class State:
                                       N.i32(ctrl_locs), N.i32(ctrl_vals or [1] * len(ctrl_locs))))
         return self
 
-    def apply_circuit(self, circuit: "Circuit", params=None, per_register=False, fused=True):
+    def apply_circuit(self, circuit: "Circuit", params=None, per_register=False, fused=True, tiles=False,
+                      tile_qubits=0):
+        """apply!(reg, chain).  fused=False: one launch per gate; tiles=True: force the
+        tile engine (fused passes over 2^tile_qubits-amplitude tiles)."""
         p = _params_array(params, circuit.nparams * (self.nreg if per_register else 1))
         flags = (N.QS_APPLY_PER_REGISTER if per_register else 0) | (0 if fused else N.QS_APPLY_UNFUSED)
+        flags |= (N.QS_APPLY_TILES if tiles else 0) | (int(tile_qubits) << 8)
         N.check(N.lib().qs_apply_circuit(self.handle, circuit.handle, N.dptr(p), flags))
         return self
 
@@ -332,3 +336,26 @@ class BatchProgram:
                 self.handle = ctypes.c_void_p()
         except Exception:
             pass
+
+
+def backward_tiled(state: State, circuit: Circuit, params, obs: Observable, tile_qubits: int = 0,
+                   work: torch.Tensor | None = None):
+    """expect' for a large complex64 register on the tile engine (FP32 uncompute,
+    FP64 gradient accumulation): (loss, grad); the state is left unchanged."""
+    p = _params_array(params, circuit.nparams)
+    if work is None:
+        b = ctypes.c_size_t()
+        N.check(N.lib().qs_backward_tiled_work_bytes(state.nqubits, ctypes.byref(b)))
+        work = torch.empty(b.value, dtype=torch.uint8, device=state.device)
+    grad = np.zeros(max(1, circuit.nparams))
+    loss = np.zeros(1)
+    N.check(N.lib().qs_backward_tiled(state.handle, circuit.handle, N.dptr(p), obs.handle, int(tile_qubits),
+                                      ctypes.c_void_p(work.data_ptr()), N.dptr(grad), N.dptr(loss)))
+    return float(loss[0]), grad[:circuit.nparams]
+
+
+def schedule_info(circuit: Circuit, tile_qubits: int = 0):
+    """(passes, phases) of the circuit's tile-engine schedule."""
+    p, f = ctypes.c_int(), ctypes.c_int()
+    N.check(N.lib().qs_circuit_schedule_info(circuit.handle, int(tile_qubits), ctypes.byref(p), ctypes.byref(f)))
+    return p.value, f.value

@@ -74,12 +74,12 @@ def test_batch_variational_uneven_sizes(qs):
 
 
 def test_batch_streamed_tiles_small_tile(qs):
-    # tiles of 8 qubits: registers of 9..12 qubits take the streamed path
+    # tiles of 9 qubits: registers of 10..13 qubits take the streamed path
     specs = []
-    for r, n in enumerate([9, 12, 8, 11]):
+    for r, n in enumerate([10, 13, 9, 12]):
         gates, params = W.variational(n, 2, "ring", seed=r)
         specs.append((n, gates, params, W.zz_chain(n) + [(0.5, ((0, "Z"),))]))
-    run_case(qs, specs, tile=8)
+    run_case(qs, specs, tile=9)
 
 
 def test_batch_mixed_gate_kinds(qs):
@@ -88,8 +88,8 @@ def test_batch_mixed_gate_kinds(qs):
         gates, params = mixed_circuit(n, r)
         specs.append((n, gates, params, W.zz_chain(n, periodic=True)))
     run_case(qs, specs)
-    specs = [(n, *mixed_circuit(n, 7), W.zz_chain(n)) for n in (9, 10)]
-    run_case(qs, specs, tile=7)
+    specs = [(n, *mixed_circuit(n, 7), W.zz_chain(n)) for n in (10, 11)]
+    run_case(qs, specs, tile=9)
 
 
 def test_batch_forward_only_and_rejects(qs):

@@ -1,0 +1,136 @@
+"""The larger workloads at their full sizes.
+
+- differentiation: n = 20, 100 layers of Rz Rx Rz + CNOT ring (8000 gates, 6000
+  angles), transverse-field Ising loss; complex64 forward with checkpoints every
+  10 layers and the FP64 uncompute, against the oracle's adjoint gradient at the
+  same size; the same circuit shape at n = 10 against parameter shift and finite
+  differences on the oracle.
+- large: n = 32 (32 GiB) QFT with swap network on a seeded basis state, then a
+  depth-20 brickwork of Rz + Haar SU(2) gates and CZs, and the reversible gradient
+  of <Z_1> on the tile engine: QFT amplitudes against the closed form at sampled
+  indices, norm, light-cone zeros of the gradient; the same pipeline at n = 22
+  element by element against the oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1912_10877_gb300 import qsim
+    return qsim
+
+
+def diff_gradient(qs, n, depth, dtype, every):
+    gates, params = W.variational(n, depth, "ring", seed=0)
+    terms = W.tfim(n)
+    circ = qs.Circuit(gates, n)
+    obs = qs.Observable(terms)
+    st = qs.State(n, dtype=dtype)
+    st.reset()
+    ck = qs.checkpoint_buffer(st, circ, every)
+    qs.apply_circuit_ckpt(st, circ, params, every, ck)
+    loss, grad = qs.backward(st, circ, params, obs, every, ck)
+    return gates, params, terms, loss, grad
+
+
+def test_differentiation_n10_against_shift_and_fd(qs):
+    n, depth = 10, 100
+    gates, params, terms, loss, grad = diff_gradient(qs, n, depth, torch.complex128, 10 * (4 * n))
+    rl, rg = oracle.gradient(oracle.zero_state(n), n, gates, params, terms)
+    assert abs(loss - rl) < 1e-10
+    assert np.max(np.abs(grad - rg)) / np.max(np.abs(rg)) < 1e-6
+    idx = list(range(0, len(params), 397))
+    sub_gates = gates
+    shift = {}
+    for i in idx:
+        pp, pm = params.copy(), params.copy()
+        pp[i] += math.pi / 2
+        pm[i] -= math.pi / 2
+        shift[i] = 0.5 * (oracle.loss(oracle.zero_state(n), n, sub_gates, pp, terms)
+                          - oracle.loss(oracle.zero_state(n), n, sub_gates, pm, terms))
+    fd = oracle.fd_gradient(oracle.zero_state(n), n, gates, params, terms, h=1e-5, which=idx)
+    scale = np.max(np.abs(rg))
+    for i in idx:
+        assert abs(grad[i] - shift[i]) / scale < 1e-6
+        assert abs(grad[i] - fd[i]) / scale < 1e-6
+
+
+def test_differentiation_n20_full_size(qs, record_property):
+    n, depth = 20, 100
+    gates, params, terms, loss, grad = diff_gradient(qs, n, depth, torch.complex64, 10 * (4 * n))
+    rl, rg = oracle.gradient(oracle.zero_state(n), n, gates, params, terms)
+    err = float(np.max(np.abs(grad - rg)) / np.max(np.abs(rg)))
+    record_property("grad_rel_err_c64_forward_fp64_uncompute", err)
+    record_property("loss_abs_err", abs(loss - rl))
+    print(f"n=20 differentiation: |dloss|={abs(loss - rl):.3e} grad max rel err={err:.3e}")
+    assert abs(loss - rl) < 1e-4
+    assert err < 1e-4
+
+
+def large_pipeline(qs, n, depth, seed=0):
+    x = W.random_basis(n, seed=seed)
+    qft = W.qft(n, swaps=True)
+    bgates, bparams = W.brickwork(n, depth, seed=seed)
+    st = qs.State(n, dtype=torch.complex64)
+    st.reset([x])
+    st.apply_circuit(qs.Circuit(qft, n), tiles=True)
+    bcirc = qs.Circuit(bgates, n, nparams=len(bparams))
+    st.apply_circuit(bcirc, bparams, tiles=True)
+    loss, grad = qs.backward_tiled(st, bcirc, bparams, qs.Observable(W.z_on(0)))
+    return x, qft, bgates, bparams, st, loss, grad
+
+
+def test_large_pipeline_n22_against_oracle(qs):
+    n = 22
+    x, qft, bgates, bparams, st, loss, grad = large_pipeline(qs, n, 20)
+    psi0 = oracle.apply_circuit(oracle.basis_state(n, x), n, qft)
+    psiN = oracle.apply_circuit(psi0, n, bgates, bparams)
+    assert np.max(np.abs(st.numpy() - psiN)) < 2e-5
+    rl, rg = oracle.gradient(psi0, n, bgates, bparams, W.z_on(0))
+    assert abs(loss - rl) < 1e-5
+    assert np.max(np.abs(grad - rg)) / np.max(np.abs(rg)) < 1e-4
+
+
+def test_large_pipeline_n32_properties(qs):
+    n = 32
+    x = W.random_basis(n, seed=0)
+    st = qs.State(n, dtype=torch.complex64)
+    st.reset([x])
+    st.apply_circuit(qs.Circuit(W.qft(n, swaps=True), n), tiles=True)
+    N = 1 << n
+    ks = np.concatenate([np.arange(8), W.rng(1).integers(0, N, 56)]).astype(np.int64)
+    got = st.buffer[torch.as_tensor(ks, device="cuda")].cpu().numpy().astype(np.complex128)
+    # little-endian QFT with the swap network: |x> -> sum_k e^{2 pi i rev(x) rev(k) / N} |k> / sqrt(N)
+    # (rev = n-bit reversal; the oracle pins qft(n)|v> = sqrt(N) IFFT(rev(v)) and the swaps reverse again)
+    def rev(v):
+        return int(format(int(v), "0%db" % n)[::-1], 2)
+    want = np.array([np.exp(2j * np.pi * ((rev(x) * rev(k)) % N) / N) for k in ks]) / math.sqrt(N)
+    assert np.max(np.abs(got - want)) * math.sqrt(N) < 1e-3
+    bgates, bparams = W.brickwork(n, 20, seed=0)
+    bcirc = qs.Circuit(bgates, n, nparams=len(bparams))
+    st.apply_circuit(bcirc, bparams, tiles=True)
+    nrm = float(torch.sum(torch.abs(st.buffer.to(torch.complex128)) ** 2).item())
+    assert abs(nrm - 1.0) < 1e-4
+    loss, grad = qs.backward_tiled(st, bcirc, bparams, qs.Observable(W.z_on(0)))
+    assert -1.0 <= loss <= 1.0 and np.all(np.isfinite(grad))
+    # light cone: an angle on qubit q in layer l can only reach qubit 0 through the
+    # CZs of the later layers, at most one qubit per layer
+    g = grad.reshape(20, n)
+    gmax = float(np.max(np.abs(g)))
+    assert gmax > 1e-3
+    for layer in range(20):
+        later = 20 - layer - 1
+        for q in range(n):
+            if q > later + 1:
+                assert abs(g[layer, q]) < 1e-4 * gmax, (layer, q, g[layer, q])
