@@ -297,19 +297,46 @@ __device__ __forceinline__ uint32_t phase_base(uint32_t tid, const TPhase& ph, i
   return b;
 }
 
-__device__ __noinline__ void run_phase_fwd(float2* sm, const TPhase* php, const TOp* fops, const float2* dtab, int m) {
+// global register index bits of this thread's amplitudes outside the phase
+__device__ __forceinline__ uint32_t thread_global(uint32_t tid, const TPhase& ph, int nthreadbits, uint32_t tbase) {
+  uint32_t b = tbase;
+  for (int k = 0; k < nthreadbits; ++k) b |= ((tid >> k) & 1u) << ph.tq[k];
+  return b;
+}
+
+// out-of-phase diagonal gate with phase-local controls: x_j *= f where (j & cm) == cv
+__device__ __forceinline__ void diag_masked(float2 (&x)[16], float2 f, int cm, int cv) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    if ((j & cm) == cv) x[j] = cmulf(x[j], f);
+}
+
+__device__ __noinline__ void run_phase_fwd(float2* sm, const TPhase* php, const TOp* fops, const float2* dtab, int m,
+                                           uint32_t tbase) {
   const TPhase ph = *php;
   const int ntb = m - kRB;
   if (threadIdx.x < (1u << ntb)) {
     const uint32_t sb = swz(phase_base(threadIdx.x, ph, ntb));
+    const uint32_t gb = thread_global(threadIdx.x, ph, ntb, tbase);
     float2 x[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) x[j] = sm[sb ^ ph.sroff[j]];
-    TOp nxt = fops[ph.fop0];
+    // factors of out-of-phase diagonal gates without phase-local controls are
+    // scalars for this thread: they commute with the phase and are applied once
+    float2 pend = make_float2(1.f, 0.f);
+    bool has_pend = false;
     for (int o = 0; o < ph.nfop; ++o) {
-      const TOp cur = nxt;
-      if (o + 1 < ph.nfop) nxt = fops[ph.fop0 + o + 1];
-      if (cur.kind == TK_DIAG16) {
+      const TOp& cur = fops[ph.fop0 + o];
+      if ((gb & cur.tmask) != cur.tval) continue;
+      if (cur.kind == TK_DIAGOUT) {
+        const float2 f = ((gb >> cur.t) & 1u) ? cur.u[3] : cur.u[0];
+        if (cur.cmask == 0) {
+          pend = cmulf(pend, f);
+          has_pend = true;
+        } else {
+          diag_masked(x, f, cur.cmask, cur.cval);
+        }
+      } else if (cur.kind == TK_DIAG16) {
         const float2* t = dtab + 16 * cur.param;
 #pragma unroll
         for (int j = 0; j < 16; ++j) x[j] = cmulf(x[j], t[j]);
@@ -317,20 +344,49 @@ __device__ __noinline__ void run_phase_fwd(float2* sm, const TPhase* php, const 
         apply_fwd(x, cur);
       }
     }
+    if (has_pend) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) x[j] = cmulf(x[j], pend);
+    }
 #pragma unroll
     for (int j = 0; j < 16; ++j) sm[sb ^ ph.sroff[j]] = x[j];
   }
   __syncthreads();
 }
 
+// backward of an out-of-phase diagonal gate: the generator is diagonal on the
+// target (Z, P1 or 1), whose value is fixed for this thread
+__device__ __forceinline__ float diagout_bwd(float2 (&x)[16], float2 (&l)[16], const TOp& op, uint32_t gb) {
+  const bool b = (gb >> op.t) & 1u;
+  const float2 d = b ? op.u[3] : op.u[0];
+  float gsign = 0.f;
+  switch (op.gen) {
+    case GEN_Z: gsign = b ? -1.f : 1.f; break;
+    case GEN_P1: gsign = b ? 1.f : 0.f; break;
+    case GEN_I: gsign = 1.f; break;
+    default: break;
+  }
+  const int cm = op.cmask, cv = op.cval;
+  float acc = 0.f;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if ((j & cm) != cv) continue;
+    acc += imcj(l[j], x[j]);
+    x[j] = cmulf(x[j], d);
+    l[j] = cmulf(l[j], d);
+  }
+  return gsign * acc;
+}
+
 __device__ __noinline__ void run_phase_bwd(float2* sx, float2* sl, const TPhase* php, const TOp* bops, int m,
-                                           float* red, double* gacc) {
+                                           float* red, double* gacc, uint32_t tbase) {
   const TPhase ph = *php;
   const int ntb = m - kRB;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool active = threadIdx.x < (1u << ntb);
   float2 x[16], l[16];
   uint32_t off[16];
+  const uint32_t gb = active ? thread_global(threadIdx.x, ph, ntb, tbase) : 0u;
   {
     const uint32_t sb = active ? swz(phase_base(threadIdx.x, ph, ntb)) : 0u;
 #pragma unroll
@@ -343,12 +399,11 @@ __device__ __noinline__ void run_phase_bwd(float2* sx, float2* sl, const TPhase*
       l[j] = sl[off[j]];
     }
   }
-  TOp nxt = bops[ph.bop0 + ph.nbop - 1];
   for (int o = ph.nbop - 1; o >= 0; --o) {
-    const TOp op = nxt;
-    if (o > 0) nxt = bops[ph.bop0 + o - 1];
+    const TOp& op = bops[ph.bop0 + o];
     float part = 0.f;
-    if (active) part = apply_bwd(x, l, op);
+    if (active && (gb & op.tmask) == op.tval)
+      part = op.kind == TK_DIAGOUT ? diagout_bwd(x, l, op, gb) : apply_bwd(x, l, op);
     if (op.gen != GEN_NONE) {
       for (int s = 16; s > 0; s >>= 1) part += __shfl_xor_sync(0xffffffffu, part, s);
       if (lane == 0) red[o * kWarps + warp] = part;
@@ -445,14 +500,14 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(BArgs a) {
       }
       __syncthreads();
       for (int pi = 0; pi < R.npass; ++pi)
-        for (int f = 0; f < P[pi].nphase; ++f) run_phase_fwd(sx, a.phases + P[pi].phase0 + f, a.fops, a.dtab, m);
+        for (int f = 0; f < P[pi].nphase; ++f) run_phase_fwd(sx, a.phases + P[pi].phase0 + f, a.fops, a.dtab, m, 0u);
       store_tile(sx, st, S.rowoff, m);  // psi_N
       block_loss(expect_tile(sx, sl, 0, S.rowoff, m, a.terms + R.term0, R.nterm), S, a.loss + reg);
       __syncthreads();
       if (grad) {
         for (int pi = R.npass - 1; pi >= 0; --pi)
           for (int f = P[pi].nphase - 1; f >= 0; --f)
-            run_phase_bwd(sx, sl, a.phases + P[pi].phase0 + f, a.bops, m, S.red, S.grad);
+            run_phase_bwd(sx, sl, a.phases + P[pi].phase0 + f, a.bops, m, S.red, S.grad, 0u);
       }
     } else {
       // ---- tiles streamed through global memory
@@ -467,7 +522,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(BArgs a) {
           const uint64_t tb = tile_base(t, p, g);
           load_tile(sx, st + tb, S.rowoff, m);
           __syncthreads();
-          for (int f = 0; f < p.nphase; ++f) run_phase_fwd(sx, a.phases + p.phase0 + f, a.fops, a.dtab, m);
+          for (int f = 0; f < p.nphase; ++f) run_phase_fwd(sx, a.phases + p.phase0 + f, a.fops, a.dtab, m, (uint32_t)tb);
           store_tile(sx, st + tb, S.rowoff, m);
           __syncthreads();
         }
@@ -497,7 +552,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(BArgs a) {
             const uint64_t tb = tile_base(t, p, g);
             load_tiles<true>(sx, wp + tb, sl, wl + tb, S.rowoff, m);
             __syncthreads();
-            for (int f = p.nphase - 1; f >= 0; --f) run_phase_bwd(sx, sl, a.phases + p.phase0 + f, a.bops, m, S.red, S.grad);
+            for (int f = p.nphase - 1; f >= 0; --f)
+              run_phase_bwd(sx, sl, a.phases + p.phase0 + f, a.bops, m, S.red, S.grad, (uint32_t)tb);
             store_tiles<true>(sx, wp + tb, sl, wl + tb, S.rowoff, m);
             __syncthreads();
           }
@@ -528,7 +584,7 @@ struct FArgs {
 
 // One pass over every register of a uniform batch: CTA-strided over tiles,
 // each tile staged in shared memory once and run through all phases of the pass.
-__global__ void __launch_bounds__(kTileThreads, 2) k_fused_pass(FArgs a) {
+__global__ void __launch_bounds__(kTileThreads, 1) k_fused_pass(FArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   uint32_t* rowoff = reinterpret_cast<uint32_t*>(smraw);
   float2* sx = reinterpret_cast<float2*>(smraw + sizeof(uint32_t) * (1 << (kMaxTileBits - kRowBits)));
@@ -537,10 +593,11 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_fused_pass(FArgs a) {
   const uint64_t total = a.ntile * (uint64_t)a.nreg;
   for (uint64_t t = blockIdx.x; t < total; t += gridDim.x) {
     const uint64_t r = t / a.ntile, tl = t - r * a.ntile;
-    float2* base = a.state + r * a.reg_stride + tile_base(tl, p, a.g);
+    const uint64_t tb = tile_base(tl, p, a.g);
+    float2* base = a.state + r * a.reg_stride + tb;
     load_tile(sx, base, rowoff, a.m);
     __syncthreads();
-    for (int f = 0; f < p.nphase; ++f) run_phase_fwd(sx, a.phases + p.phase0 + f, a.fops, a.dtab, a.m);
+    for (int f = 0; f < p.nphase; ++f) run_phase_fwd(sx, a.phases + p.phase0 + f, a.fops, a.dtab, a.m, (uint32_t)tb);
     store_tile(sx, base, rowoff, a.m);
     __syncthreads();
   }
@@ -576,7 +633,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_fused_bwd_pass(FBArgs a) {
     const uint64_t tb = tile_base(t, p, a.g);
     load_tiles<true>(sx, a.wpsi + tb, sl, a.wlam + tb, rowoff, a.m);
     __syncthreads();
-    for (int f = p.nphase - 1; f >= 0; --f) run_phase_bwd(sx, sl, a.phases + p.phase0 + f, a.bops, a.m, red, gacc);
+    for (int f = p.nphase - 1; f >= 0; --f)
+      run_phase_bwd(sx, sl, a.phases + p.phase0 + f, a.bops, a.m, red, gacc, (uint32_t)tb);
     store_tiles<true>(sx, a.wpsi + tb, sl, a.wlam + tb, rowoff, a.m);
     __syncthreads();
   }
@@ -899,27 +957,38 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
         uint8_t nondiag = 0;             // phase bits touched by non-diagonal gates since it opened
         for (int gi : ph.gates) {
           const qs_gate_desc& g = c->gates[gi];
-          const int tb = pbit(g.locs[0]);
-          uint8_t cm = 0, cv = 0;
+          const bool diag = gate_is_diagonal(c, g);
+          const int tb = pbit(g.locs[0]);  // -1: target outside the phase (diagonal gates only)
+          uint8_t cm = 0, cv = 0;          // controls inside the phase
+          uint32_t tmask = 0, tval = 0;    // controls outside the phase (register qubits)
           for (int qb = 0; qb < n; ++qb)
             if ((g.ctrl_mask >> qb) & 1ull) {
               const int k = pbit(qb);
-              cm |= (uint8_t)(1 << k);
-              if ((g.ctrl_vals >> qb) & 1ull) cv |= (uint8_t)(1 << k);
+              const bool v = (g.ctrl_vals >> qb) & 1ull;
+              if (k >= 0) {
+                cm |= (uint8_t)(1 << k);
+                if (v) cv |= (uint8_t)(1 << k);
+              } else {
+                tmask |= 1u << qb;
+                if (v) tval |= 1u << qb;
+              }
             }
           // backward op: one per gate
           TOp b;
           memset(&b, 0, sizeof(b));
-          b.t = (uint8_t)tb;
+          b.t = (uint8_t)(tb >= 0 ? tb : g.locs[0]);
           b.cmask = cm;
           b.cval = cv;
+          b.tmask = tmask;
+          b.tval = tval;
           b.param = g.param;
           b.gen = g.param >= 0 ? (uint8_t)gen_of(g.kind, &b.cfac2) : GEN_NONE;
           // uncompute kind: the generator picks the structured form (Rx / Ry / diagonal)
-          if (b.gen == GEN_X) b.kind = TK_RX;
+          if (tb < 0) b.kind = TK_DIAGOUT;
+          else if (b.gen == GEN_X) b.kind = TK_RX;
           else if (b.gen == GEN_Y) b.kind = TK_RY;
           else if (b.gen != GEN_NONE) b.kind = TK_DIAG;
-          else b.kind = g.kind == QS_GATE_X ? TK_SWAP : diag_kind(g.kind) ? TK_DIAG : TK_DENSE;
+          else b.kind = g.kind == QS_GATE_X ? TK_SWAP : diag ? TK_DIAG : TK_DENSE;
           if (g.param >= 0 && b.gen == GEN_NONE)
             return fail(QS_EUNSUPPORTED, "register %d gate %d: kind %d has no batched gradient", r, gi, g.kind);
           for (int q = t.bop0; q < (int)bops.size(); ++q)
@@ -929,25 +998,44 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
             }
           bops.push_back(b);
           bgate.push_back(g0 + gi);
-          // forward op: consecutive uncontrolled gates on one target fuse into one 2x2;
-          // controlled diagonal gates (CZ, controlled phases) join the phase's open
-          // 16-entry diagonal table unless a non-diagonal op since it opened shares a
-          // qubit with them (diagonal gates commute with each other)
-          const bool fusable = cm == 0 && g.kind != QS_GATE_X;
+          // forward op.  A diagonal gate with its target outside the phase is a
+          // per-thread factor.  Consecutive uncontrolled gates on one target fuse
+          // into one 2x2; controlled diagonal gates inside the phase join its open
+          // 16-entry table unless a non-diagonal op since the table opened shares a
+          // qubit with them (diagonal gates commute with each other).
+          TOp f;
+          memset(&f, 0, sizeof(f));
+          f.cmask = cm;
+          f.cval = cv;
+          f.tmask = tmask;
+          f.tval = tval;
+          f.param = -1;
+          FMem fm;
+          memset(&fm, 0, sizeof(fm));
+          fm.count = 1;
+          fm.g[0] = g0 + gi;
+          if (tb < 0) {
+            f.kind = TK_DIAGOUT;
+            f.t = (uint8_t)g.locs[0];
+            fops.push_back(f);
+            fmem.push_back(fm);
+            for (int k = 0; k < kRB; ++k)
+              if ((cm >> k) & 1) last[k] = -1;
+            continue;
+          }
+          const bool fusable = cm == 0 && tmask == 0 && g.kind != QS_GATE_X;
           const uint8_t gbits = (uint8_t)(cm | (1u << tb));
-          if (!diag_kind(g.kind)) nondiag |= gbits;
+          if (!diag) nondiag |= gbits;
           if (fusable && last[tb] >= 0 && fmem[last[tb]].count < 4) {
-            FMem& fm = fmem[last[tb]];
-            fm.g[fm.count++] = g0 + gi;
-            if (!diag_kind(g.kind)) fops[last[tb]].kind = TK_DENSE;
-          } else if (cm != 0 && diag_kind(g.kind)) {
+            FMem& fmo = fmem[last[tb]];
+            fmo.g[fmo.count++] = g0 + gi;
+            if (!diag) fops[last[tb]].kind = TK_DENSE;
+          } else if (diag && cm != 0 && tmask == 0) {
             if (dg < 0 || (gbits & nondiag)) {
-              TOp f;
-              memset(&f, 0, sizeof(f));
               f.kind = TK_DIAG16;
+              f.cmask = f.cval = 0;
               f.param = (int)drefs.size();
-              FMem fm;
-              memset(&fm, 0, sizeof(fm));
+              fm.count = 0;
               fops.push_back(f);
               fmem.push_back(fm);
               drefs.push_back({(int32_t)dmems.size(), 0});
@@ -963,26 +1051,14 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
             dmems.push_back(mb);
             drefs[dg].count++;
           } else {
-            TOp f;
-            memset(&f, 0, sizeof(f));
-            f.kind = g.kind == QS_GATE_X ? TK_SWAP : diag_kind(g.kind) ? TK_DIAG : TK_DENSE;
+            f.kind = g.kind == QS_GATE_X ? TK_SWAP : diag ? TK_DIAG : TK_DENSE;
             f.t = (uint8_t)tb;
-            f.cmask = cm;
-            f.cval = cv;
-            f.param = -1;
-            FMem fm;
-            memset(&fm, 0, sizeof(fm));
-            fm.count = 1;
-            fm.g[0] = g0 + gi;
             fops.push_back(f);
             fmem.push_back(fm);
-            // any gate on this target (or using it as control) closes fusion on the touched bits
-            for (int k = 0; k < kRB; ++k)
-              if ((cm >> k) & 1) last[k] = -1;
             last[tb] = fusable ? (int)fops.size() - 1 : -1;
           }
-          // a controlled gate closes fusion on its control bits and target
-          if (cm) {
+          // a controlled gate closes fusion on its target and its phase-local controls
+          if (cm || tmask) {
             for (int k = 0; k < kRB; ++k)
               if ((cm >> k) & 1) last[k] = -1;
             last[tb] = -1;

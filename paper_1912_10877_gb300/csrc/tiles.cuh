@@ -4,12 +4,15 @@
 // A circuit is scheduled into PASSES.  A pass owns a set B of m register
 // qubits (its tile bits): the state is cut into 2^(n-m) tiles of 2^m
 // amplitudes that differ only in those bits, each tile is staged in shared
-// memory, and every gate of the pass touches only qubits of B.  A pass is cut
-// into PHASES: a phase owns 4 of the tile's bits (its register bits R); each
-// of the 2^(m-4) threads holds the 16 amplitudes of the tile that differ only
-// in R in registers, applies the phase's gates there, and writes them back.
-// The planner keeps gate order valid by moving a gate earlier only past gates
-// that share no qubit with it.
+// memory, and every non-diagonal gate of the pass has its target in B.  A pass
+// is cut into PHASES: a phase owns 4 of the tile's bits (its register bits R);
+// each of the 2^(m-4) threads holds the 16 amplitudes of the tile that differ
+// only in R in registers, applies the phase's gates there, and writes them
+// back.  A thread knows the global index of its amplitudes, so a gate's
+// controls outside R become a per-thread predicate, and a diagonal gate whose
+// target is outside R becomes a per-thread factor.  The planner keeps gate
+// order valid by moving a gate earlier only past gates that share no qubit
+// with it.
 #pragma once
 
 #include "common.cuh"
@@ -21,29 +24,37 @@ constexpr int kRowBits = 5;        // tile rows: 32 consecutive amplitudes (regi
 constexpr int kMaxTileBits = 13;
 constexpr int kTileThreads = 1 << (kMaxTileBits - kRB);  // 512
 
-// one gate inside a phase (targets and controls are phase-local bit indices 0..3)
+// one gate inside a phase.  t, cmask and cval are phase-local (bits 0..3 of the
+// register index j); the gate's other controls are register qubits outside the
+// phase, tested per thread on its global base index: (base & tmask) == tval.
 struct TOp {
   uint8_t kind;   // TK_*
-  uint8_t t;      // target bit (0..3)
-  uint8_t cmask;  // control bits (0..3)
-  uint8_t cval;   // required control values
+  uint8_t t;      // target: phase bit (0..3), or the register qubit for TK_DIAGOUT
+  uint8_t cmask;  // phase-local control bits
+  uint8_t cval;   // their required values
   uint8_t gen;    // backward ops: generator code (GEN_*), 0 = no parameter
   uint8_t shared; // backward ops: the parameter also appears in another op of the phase
   uint8_t pad[2];
-  int32_t param;  // register-local parameter index, -1 = none
+  int32_t param;  // register-local parameter index (forward TK_DIAG16: table index), -1 = none
   float cfac2;    // 2 c for U = exp(-i theta c H)
+  uint32_t tmask; // controls outside the phase (register qubit bits)
+  uint32_t tval;
+  uint32_t pad2;
   float2 u[4];    // forward: U; backward: U^dagger (row-major 2x2)
 };
 
 // TK_RX: u0 = u3 = c (real), u1 = u2 = i s; TK_RY: u0 = u3 = c, u1 = -s, u2 = s;
 // TK_DIAG16 (forward only): amplitude j of the phase *= table[param][j], the
-// product of consecutive diagonal gates of the phase (they commute)
-enum { TK_DENSE = 0, TK_SWAP = 1, TK_DIAG = 2, TK_RX = 3, TK_RY = 4, TK_DIAG16 = 5 };
+// product of consecutive diagonal gates inside the phase (they commute);
+// TK_DIAGOUT: diagonal gate whose target qubit is outside the phase: every
+// amplitude of the thread takes the factor u0 or u3 by that qubit's value
+enum { TK_DENSE = 0, TK_SWAP = 1, TK_DIAG = 2, TK_RX = 3, TK_RY = 4, TK_DIAG16 = 5, TK_DIAGOUT = 6 };
 enum { GEN_NONE = 0, GEN_X = 1, GEN_Y = 2, GEN_Z = 3, GEN_P1 = 4, GEN_I = 5 };
 
 struct TPhase {
   uint8_t rpos[kRB];        // tile-local positions of the register bits (ascending)
   uint8_t tpos[12];         // tile-local positions of the thread bits (ascending)
+  uint8_t tq[12];           // register qubits of the thread bits
   uint16_t sroff[1 << kRB]; // swz(register offset of amplitude j): slot = swz(base) ^ sroff[j]
   int32_t fop0, nfop;       // forward ops (fused), applied in order
   int32_t bop0, nbop;       // backward ops (unfused), applied in reverse order
@@ -67,9 +78,13 @@ struct HostPass {
 
 // Greedy commutation-aware scheduling: passes of m qubits (always containing
 // register qubits 0..4, so tile rows are contiguous), phases of exactly kRB of
-// the pass's qubits.  Gates must be single-target (controls allowed) with all
-// qubits inside a phase.  Returns QS_OK or QS_EUNSUPPORTED.
+// the pass's qubits.  Gates must be single-target; a non-diagonal gate's target
+// lies in its phase, its controls and diagonal gates may be anywhere.  Returns
+// QS_OK or QS_EUNSUPPORTED.
 int plan_passes(const qs_circuit* c, int n, int m, int max_phase_ops, std::vector<HostPass>& out);
+
+// diagonal gates (fit in any phase: they only multiply amplitudes)
+bool gate_is_diagonal(const qs_circuit* c, const qs_gate_desc& g);
 
 // tile-local positions of a phase's register bits and thread bits
 void phase_positions(const HostPass& p, const HostPhase& ph, TPhase* out);
