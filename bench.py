@@ -524,8 +524,8 @@ def main():
     # dominant kernel: largest share of device time
     pc = c64["per_class"]
     dom = max(pc, key=lambda c: pc[c]["seconds"])
-    kname = {"dense1": "k_gate1<float, OP_DENSE1>", "swap1": "k_gate1<float, OP_SWAP1>",
-             "diag1": "k_diag1<float>"}[dom]
+    kname = {"dense1": "k_gate1<float, 4, *> (OP_DENSE1: H, Rx)", "swap1": "k_gate1<float, 2, *> (OP_SWAP1: X, CNOT, Toffoli)",
+             "diag1": "k_diag1<float> (T: touched half only)"}[dom]
     achieved = pc[dom]["gbs"]
     roof = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
             "peak_kind": f"{peak_kind} (copy GB/s)", "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
