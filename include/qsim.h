@@ -127,6 +127,23 @@ int qs_state_reset(qs_state* s, const uint64_t* host_basis);
 int qs_state_upload(qs_state* s, const void* host_amps);
 int qs_state_download(const qs_state* s, void* host_amps);
 
+/* Wait for every operation queued on the state's stream.  Returns
+ * QS_ETIMEDOUT if, since the last call, a tensor-core kernel's bounded wait
+ * for its own MMA completion gave up (its tile was then left unwritten); the
+ * word is device-wide and is cleared by this call.  Other errors as
+ * QS_EDEVICE. */
+int qs_state_sync(qs_state* s);
+
+/* ---------------------------------------------------------------- options */
+
+/* Process-wide switches (not thread-safe against concurrent launches).
+ * QS_OPT_TENSOR_CORES (default 1): dense 4- and 5-qubit gates on complex64
+ * states run on the tensor cores (complex product as a real 3xTF32 GEMM,
+ * FP32 accuracy); 0 selects the CUDA-core kernel for them. */
+#define QS_OPT_TENSOR_CORES 1
+int qs_set_option(int option, int value);
+int qs_get_option(int option, int* value);
+
 /* ---------------------------------------------------------------- gates */
 
 /* instruct!(reg, U, locs, ctrl_locs, ctrl_vals) on every register of s
@@ -135,7 +152,8 @@ int qs_state_download(const qs_state* s, void* host_amps);
  * host_mat: 2^k x 2^k row-major interleaved complex doubles (not checked for
  * unitarity).  locs and ctrl_locs must be distinct and < every register's n.
  * The library picks a diagonal, permutation or dense kernel from the matrix's
- * non-zero pattern (App. "Matrix Types"). */
+ * non-zero pattern (App. "Matrix Types"); dense k = 4, 5 on complex64 states
+ * run on the tensor cores unless QS_OPT_TENSOR_CORES is 0 (targets < 32). */
 int qs_apply_gate(qs_state* s, const double* host_mat, int k, const int32_t* host_locs,
                   int nctrl, const int32_t* host_ctrl_locs, const int32_t* host_ctrl_vals);
 

@@ -16,6 +16,7 @@ QS_C64, QS_C128 = 0, 1
 QS_MAXK = 5
 QS_BATCH_RESET, QS_BATCH_GRAD = 1, 2
 QS_APPLY_PER_REGISTER, QS_APPLY_UNFUSED, QS_APPLY_TILES = 1, 2, 4
+QS_OPT_TENSOR_CORES = 1
 
 GATE_KIND = {"I": 0, "X": 1, "Y": 2, "Z": 3, "H": 4, "S": 5, "SDG": 6, "T": 7, "TDG": 8,
              "RX": 9, "RY": 10, "RZ": 11, "SHIFT": 12, "PHASE": 13, "SWAP": 14, "ROT": 15,
@@ -62,6 +63,9 @@ SIGNATURES = {
     "qs_state_reset": ([_P, _PU64], _I),
     "qs_state_upload": ([_P, _P], _I),
     "qs_state_download": ([_P, _P], _I),
+    "qs_state_sync": ([_P], _I),
+    "qs_set_option": ([_I, _I], _I),
+    "qs_get_option": ([_I, ctypes.POINTER(_I)], _I),
     "qs_apply_gate": ([_P, _PD, _I, _PI32, _I, _PI32, _PI32], _I),
     "qs_apply_named": ([_P, _I, _I, _PI32, _PI32, _I, _PI32, _PI32, _D], _I),
     "qs_circuit_create": ([_I, ctypes.POINTER(GateDesc), _I, _PD, ctypes.c_int64, _I, _PP], _I),

@@ -273,6 +273,27 @@ int qs_state_download(const qs_state* s, void* host) {
   return QS_OK;
 }
 
+int qs_state_sync(qs_state* s) {
+  if (!s) return fail(QS_EINVAL, "null state");
+  QS_CUDA(cudaStreamSynchronize(s->stream));
+  return tc_status_take();
+}
+
+int qs_set_option(int option, int value) {
+  switch (option) {
+    case QS_OPT_TENSOR_CORES: set_tensor_cores(value); return QS_OK;
+  }
+  return fail(QS_EINVAL, "unknown option %d", option);
+}
+
+int qs_get_option(int option, int* value) {
+  if (!value) return fail(QS_EINVAL, "null argument");
+  switch (option) {
+    case QS_OPT_TENSOR_CORES: *value = tensor_cores_enabled(); return QS_OK;
+  }
+  return fail(QS_EINVAL, "unknown option %d", option);
+}
+
 static int ctrl_masks(int nctrl, const int32_t* cl, const int32_t* cv, uint64_t* mask, uint64_t* vals) {
   *mask = *vals = 0;
   if (nctrl < 0 || (nctrl > 0 && !cl)) return fail(QS_EINVAL, "bad control arguments");

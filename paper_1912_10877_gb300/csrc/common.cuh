@@ -212,6 +212,13 @@ void dagger(std::vector<cd>& U, int k);
 void pauli_string(int k, const int32_t* paulis, std::vector<cd>& S);
 int validate_gate(int n, int k, const int32_t* locs, uint64_t ctrl_mask);
 
+// dense 4- and 5-qubit blocks of complex64 states on the tensor cores (tc_block.cu)
+void set_tensor_cores(int on);
+int tensor_cores_enabled();
+bool use_block_tc(int dtype, const Plan& p);
+int launch_block_tc(float2* psi, int n, int nreg, const Plan& p, cudaStream_t st);
+int tc_status_take();  // QS_ETIMEDOUT (and clears it) if a tensor-core wait gave up
+
 // tile-engine forward of a whole circuit (batch.cu); QS_EUNSUPPORTED if it does not fit
 int fused_forward(qs_state* s, const qs_circuit* c, const double* host_params, int tile_qubits);
 int fused_backward(qs_state* s, const qs_circuit* c, const double* host_params, const qs_observable* o,

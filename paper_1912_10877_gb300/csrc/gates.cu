@@ -282,6 +282,7 @@ int launch_plan_on(void* data, int dtype, int n, int nreg, int64_t reg_stride, c
                    qs_state* owner) {
   (void)reg_stride;
   cudaStream_t st = owner ? owner->stream : nullptr;
+  if (use_block_tc(dtype, p)) return launch_block_tc((float2*)data, n, nreg, p, st);
   if (dtype == QS_C64) return launch_typed<float>((float2*)data, n, nreg, p, st);
   return launch_typed<double>((double2*)data, n, nreg, p, st);
 }

@@ -80,6 +80,10 @@ class State:
         N.check(N.lib().qs_state_set_stream(self.handle, _stream_ptr(stream)))
         self.stream = stream
 
+    def sync(self):
+        """Waits for the state's stream; raises if a tensor-core wait gave up."""
+        N.check(N.lib().qs_state_sync(self.handle))
+
     # -- data -----------------------------------------------------------------
     def register(self, r: int) -> torch.Tensor:
         return self.buffer[int(self.offsets[r]):int(self.offsets[r + 1])]
@@ -359,3 +363,14 @@ def schedule_info(circuit: Circuit, tile_qubits: int = 0):
     p, f = ctypes.c_int(), ctypes.c_int()
     N.check(N.lib().qs_circuit_schedule_info(circuit.handle, int(tile_qubits), ctypes.byref(p), ctypes.byref(f)))
     return p.value, f.value
+
+
+def set_tensor_cores(on: bool) -> None:
+    """Dense 4- and 5-qubit complex64 gates on the tensor cores (default) or the CUDA cores."""
+    N.check(N.lib().qs_set_option(N.QS_OPT_TENSOR_CORES, 1 if on else 0))
+
+
+def tensor_cores() -> bool:
+    v = ctypes.c_int(0)
+    N.check(N.lib().qs_get_option(N.QS_OPT_TENSOR_CORES, ctypes.byref(v)))
+    return bool(v.value)

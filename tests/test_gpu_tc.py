@@ -1,0 +1,160 @@
+"""GPU parity of dense 4- and 5-qubit blocks on the tensor cores (complex64,
+complex product as a 3xTF32 real GEMM): against the FP64 oracle element by
+element for low, high, permuted and mixed target sets, with controls, uniform
+and uneven batches and ragged tile tails; at n = 25 on sampled tuples; and
+against the CUDA-core kernel of the same gate.  Tolerance: 2e-5 absolute on
+amplitudes of a normalised state."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def qs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1912_10877_gb300 import qsim
+    qsim.set_tensor_cores(True)
+    yield qsim
+    qsim.set_tensor_cores(True)
+
+
+def rand_unitary(k, rs):
+    d = 1 << k
+    a = rs.standard_normal((d, d)) + 1j * rs.standard_normal((d, d))
+    q, r = np.linalg.qr(a)
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+def apply_gpu(qs, psi, n, gate, nbatch=1):
+    st = qs.State(n, dtype=torch.complex64, nbatch=nbatch)
+    st.upload(np.tile(psi, nbatch))
+    st.apply(gate)
+    st.sync()
+    return st.numpy().reshape(nbatch, -1)
+
+
+def placements(n, k, rs):
+    yield tuple(range(k))                                   # lowest qubits, ascending
+    yield tuple(int(x) for x in rs.permutation(k))          # lowest qubits, permuted
+    yield tuple(range(n - k, n))[::-1]                      # highest qubits
+    yield (1,) + tuple(range(n - k + 1, n))                 # one low, rest high
+    yield (0, 1) + tuple(int(x) for x in rs.choice(np.arange(3, n), k - 2, replace=False))
+    for _ in range(3):
+        yield tuple(int(x) for x in rs.choice(n, k, replace=False))
+
+
+@pytest.mark.parametrize("k", [4, 5])
+def test_block_every_placement_with_controls(qs, k):
+    n = 11
+    rs = np.random.default_rng(40 + k)
+    psi = W.haar_state(n, seed=k)
+    for locs in placements(n, k, rs):
+        U = rand_unitary(k, rs)
+        free = [q for q in range(n) if q not in locs]
+        for nc in (0, 1, 2):
+            cl = tuple(int(x) for x in rs.choice(free, nc, replace=False))
+            cv = tuple(int(x) for x in rs.integers(0, 2, nc))
+            g = W.Gate("MATRIX", locs, cl, cv, matrix=U)
+            got = apply_gpu(qs, psi, n, g)[0]
+            want = oracle.apply_circuit(psi, n, [g])
+            assert np.max(np.abs(got - want)) < TOL, (locs, cl, cv)
+
+
+@pytest.mark.parametrize("k", [4, 5])
+def test_block_ragged_tiles_and_batches(qs, k):
+    rs = np.random.default_rng(7 + k)
+    U = rand_unitary(k, rs)
+    # one tuple per register, a few tuples, a partial 128-tuple tile, several tiles + tail
+    for n, nbatch in ((k, 1), (k, 3), (k + 1, 5), (k + 3, 3), (k + 8, 3)):
+        psi = W.haar_state(n, seed=n)
+        locs = tuple(int(x) for x in rs.permutation(n)[:k])
+        g = W.Gate("MATRIX", locs, matrix=U)
+        got = apply_gpu(qs, psi, n, g, nbatch=nbatch)
+        want = oracle.apply_circuit(psi, n, [g])
+        for r in range(nbatch):
+            assert np.max(np.abs(got[r] - want)) < TOL, (n, nbatch, r)
+    # a control that leaves exactly one tuple per register
+    n = k + 1
+    psi = W.haar_state(n, seed=99)
+    g = W.Gate("MATRIX", tuple(range(1, n)), (0,), (1,), matrix=U)
+    got = apply_gpu(qs, psi, n, g, nbatch=2)
+    want = oracle.apply_circuit(psi, n, [g])
+    assert np.max(np.abs(got - want[None, :])) < TOL
+    # uneven registers
+    counts = [k, k + 4, k + 1, k + 9, k + 2]
+    st = qs.State(counts, dtype=torch.complex64)
+    inputs = [W.haar_state(c, seed=300 + c) for c in counts]
+    st.upload(np.concatenate(inputs))
+    g = W.Gate("MATRIX", tuple(range(k))[::-1], matrix=U)
+    st.apply(g)
+    st.sync()
+    out = st.numpy()
+    for r, c in enumerate(counts):
+        seg = out[int(st.offsets[r]):int(st.offsets[r + 1])]
+        assert np.max(np.abs(seg - oracle.apply_circuit(inputs[r], c, [g]))) < TOL, r
+
+
+@pytest.mark.parametrize("k", [4, 5])
+def test_block_tensor_and_cuda_cores_agree(qs, k):
+    n = 14
+    rs = np.random.default_rng(5 * k)
+    psi = W.haar_state(n, seed=21)
+    gates = [W.Gate("MATRIX", tuple(int(x) for x in rs.permutation(n)[:k]), matrix=rand_unitary(k, rs))
+             for _ in range(4)]
+    want = oracle.apply_circuit(psi, n, gates)
+    outs = {}
+    for on in (True, False):
+        qs.set_tensor_cores(on)
+        assert qs.tensor_cores() == on
+        st = qs.State(n, dtype=torch.complex64)
+        st.upload(psi)
+        for g in gates:
+            st.apply(g)
+        st.sync()
+        outs[on] = st.numpy()
+    qs.set_tensor_cores(True)
+    for on in (True, False):
+        assert np.max(np.abs(outs[on] - want)) < TOL, on
+    assert np.max(np.abs(outs[True] - outs[False])) < 2 * TOL
+
+
+def member_offsets(locs):
+    k = len(locs)
+    return np.array([sum(1 << locs[j] for j in range(k) if (m >> j) & 1) for m in range(1 << k)],
+                    dtype=np.int64)
+
+
+@pytest.mark.parametrize("locs", [(0, 1, 2, 3, 4), (24, 20, 22, 23, 21), (2, 7, 13, 19, 24), (9, 1, 0, 17)])
+def test_block_full_size_n25_sampled(qs, locs):
+    # n = 25 complex64, the single-gate workload's size; sampled tuples against the
+    # oracle applied to the tuple as a k-qubit register (gate bit j <-> locs[j])
+    n, k = 25, len(locs)
+    rs = np.random.default_rng(sum(locs))
+    U = rand_unitary(k, rs)
+    psi = W.haar_state(n, seed=25).astype(np.complex64)
+    st = qs.State(n, dtype=torch.complex64)
+    st.upload(psi)
+    st.apply(W.Gate("MATRIX", locs, matrix=U))
+    st.sync()
+    out = st.numpy()
+    offs = member_offsets(locs)
+    lmask = int(offs[-1])
+    small = W.Gate("MATRIX", tuple(range(k)), matrix=U)
+    bases = rs.integers(0, 1 << n, 3000) & ~lmask
+    bases = np.concatenate([bases, [0, ((1 << n) - 1) & ~lmask]])
+    worst = 0.0
+    for b in bases:
+        x = psi[b + offs].astype(np.complex128)
+        y = oracle.apply_circuit(x, k, [small])
+        worst = max(worst, float(np.max(np.abs(out[b + offs] - y))))
+    assert worst < TOL, worst
+    # the whole state stays normalised (unitary block)
+    assert abs(np.linalg.norm(out.astype(np.complex128)) - 1.0) < 1e-4
