@@ -137,9 +137,11 @@ int qs_state_sync(qs_state* s);
 /* ---------------------------------------------------------------- options */
 
 /* Process-wide switches (not thread-safe against concurrent launches).
- * QS_OPT_TENSOR_CORES (default 1): dense 4- and 5-qubit gates on complex64
- * states run on the tensor cores (complex product as a real 3xTF32 GEMM,
- * FP32 accuracy); 0 selects the CUDA-core kernel for them. */
+ * QS_OPT_TENSOR_CORES: which kernel applies dense 4- and 5-qubit gates to
+ * complex64 states.  2: always the tensor cores (complex product as a real
+ * 3xTF32 GEMM, FP32 accuracy); 0: always the CUDA cores; 1 (default): the
+ * tensor cores for the target placements where they measured faster (5-qubit
+ * blocks unless every target is at qubit 5 or above, 4-qubit blocks on qubit 0). */
 #define QS_OPT_TENSOR_CORES 1
 int qs_set_option(int option, int value);
 int qs_get_option(int option, int* value);
@@ -153,7 +155,7 @@ int qs_get_option(int option, int* value);
  * unitarity).  locs and ctrl_locs must be distinct and < every register's n.
  * The library picks a diagonal, permutation or dense kernel from the matrix's
  * non-zero pattern (App. "Matrix Types"); dense k = 4, 5 on complex64 states
- * run on the tensor cores unless QS_OPT_TENSOR_CORES is 0 (targets < 32). */
+ * may run on the tensor cores (QS_OPT_TENSOR_CORES; targets < 32). */
 int qs_apply_gate(qs_state* s, const double* host_mat, int k, const int32_t* host_locs,
                   int nctrl, const int32_t* host_ctrl_locs, const int32_t* host_ctrl_vals);
 

@@ -2,47 +2,59 @@
 // cores (tcgen05, sm_103a), complex64.
 //
 // The general multi-qubit instruction (Sec. "Performance") applies a 2^k x 2^k
-// matrix to every 2^k-tuple of amplitudes.  For a dense block this is a complex
-// matrix product; with D = 2^k and W = 2D it becomes one real GEMM per 128
-// tuples:
-//   A (M = 128 tuples x K = W): row t = [Re x_0 .. Re x_{D-1}, Im x_0 .. Im x_{D-1}]
-//   B (N = W outputs x K = W):  the real form of the matrix,
-//       Re y_r = sum_c Re U_rc Re x_c - Im U_rc Im x_c
-//       Im y_r = sum_c Im U_rc Re x_c + Re U_rc Im x_c
-//   D = A B^T (M x N, FP32) in tensor memory.
+// matrix U to every 2^k-tuple of amplitudes.  For a dense block this is a
+// complex matrix product; with D = 2^k and W = 2D it becomes one real GEMM per
+// 128 tuples, with real and imaginary parts interleaved as they are in memory:
+//   A (M = 128 tuples x K = W): row t = [Re x_0, Im x_0, Re x_1, Im x_1, ...]
+//   B (N = W x K = W), the real form of U:
+//       B[2r][2c] = Re U_rc   B[2r][2c+1] = -Im U_rc
+//       B[2r+1][2c] = Im U_rc B[2r+1][2c+1] = Re U_rc
+//   C = A B^T (M x N, FP32) in tensor memory: row t = [Re y_0, Im y_0, ...].
 // FP32 accuracy comes from the 3xTF32 split: v = hi + lo with hi = v with its
 // low 13 mantissa bits cleared (exact in TF32) and lo = v - hi (exact in FP32),
-// and D = A_hi B_hi + A_hi B_lo + A_lo B_hi; the omitted lo*lo term is below
+// and C = A_hi B_hi + A_hi B_lo + A_lo B_hi; the omitted lo*lo term is below
 // 2^-20 of each product.
 //
-// Per tile of 128 tuples a CTA of 128 threads
-//   1. computes the base index of each tuple (thread t: tuple t),
-//   2. gathers the 128 x D amplitudes with consecutive threads on consecutive
-//      addresses (targets that are the lowest qubits vary fastest, then the
-//      tuple), splits them and stores A_hi, A_lo in shared memory,
-//   3. has one thread issue the W/8 x 3 tcgen05.mma (kind::tf32, K = 8 each),
-//      committed to an mbarrier,
-//   4. reads its own row of D back with tcgen05.ld (warp w owns TMEM lanes
-//      32w..32w+31) and stages it in shared memory over the consumed A,
-//   5. scatters the tile back in the gather's order.
+// One persistent CTA per SM, warp-specialised, tiles of 128 tuples:
+//   warps 0-15  load a tile with 16-byte accesses (the loads of the tile
+//               two ahead are in flight while the current one is split into
+//               A_hi / A_lo in one of two shared-memory stages),
+//   warp 20     issues the W/8 x 3 tcgen05.mma (kind::tf32, K = 8 each) into
+//               one of two TMEM accumulators and commits them to mbarriers,
+//   warps 16-19 read the accumulator rows back with tcgen05.ld (warp w owns
+//               TMEM lanes 32 (w mod 4) ..) and store them to global memory
+//               (through a shared-memory staging tile where a row is a run of
+//               adjacent amplitudes, so that the stores stay coalesced).
 // Operands use the canonical K-major 128-byte-swizzle layout: 8-row atoms of
 // 128-byte rows, 16-byte chunk c of row r stored at chunk c ^ (r mod 8), and
 // the K extent split into 128-byte column blocks stored one after another.
-// Every wait on the mbarrier is bounded in polls and in time; a wait that
-// gives up sets a device status word that qs_state_sync reports.
+// Every mbarrier wait is bounded in polls and in time; a wait that gives up
+// raises a CTA-wide abort flag, sets a device status word that qs_state_sync
+// reports, and every role leaves its loop; the MMA warp waits (bounded) for
+// its last commit before the TMEM is freed.
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "common.cuh"
 
 namespace qs {
 
-constexpr int kTcThreads = 128;                     // one thread per tuple row
-constexpr int kTcRows = 128;                        // M of the MMA
+constexpr int kTcRows = 128;                        // M of the MMA: tuples per tile
+constexpr int kTcLoadWarps = 16, kTcEpiWarps = 4;
+constexpr int kTcLoaders = kTcLoadWarps * 32;       // 512
+constexpr int kTcEpiWarp0 = kTcLoadWarps;           // warps 16..19 (TMEM lane quarters 0..3)
+constexpr int kTcMmaWarp = kTcLoadWarps + kTcEpiWarps;  // warp 20
+constexpr int kTcThreads = (kTcMmaWarp + 1) * 32;   // 672
 constexpr uint32_t kTcSpinLimit = 1u << 24;         // mbarrier polls before giving up
 constexpr uint64_t kTcTimeLimitNs = 2000000000ull;  // and at most 2 s of wall time
 
-__device__ int g_tc_status;  // 0 = fine; 1 = an MMA completion wait gave up
+// how a loader thread's 16-byte (or 8-byte) unit maps onto the tile
+enum { TC_PAIR_MEMBERS = 0,  // target qubit 0: members (2q, 2q+1) of one tuple are adjacent
+       TC_PAIR_TUPLES = 1,   // qubit 0 free: tuples (2p, 2p+1) of one member are adjacent
+       TC_SCALAR = 2 };      // qubit 0 is a control (or one tuple per register): 8-byte units
+
+__device__ int g_tc_status;  // 0 = fine; 1 = an MMA pipeline wait gave up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -89,28 +101,56 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
                : "memory");
 }
 
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(mbar) : "memory");
+}
+
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
 
-// bounded wait for completion of the mbarrier phase with the given parity
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  const uint64_t t0 = global_ns();
+// bounded wait for completion of the mbarrier phase with the given parity;
+// gives up (and raises *abort) after the poll or time limit, or when another
+// role has raised *abort.  Each try_wait may suspend the thread until the
+// phase completes (hint: at most 1 ms), so polls are few.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int* abort) {
+  uint64_t t0 = 0;
   for (uint32_t it = 0; it < kTcSpinLimit; ++it) {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
-        : "r"(mbar), "r"(parity)
+        : "r"(mbar), "r"(parity), "r"(1000000u)
         : "memory");
     if (ok) return true;
-    if ((it & 255u) == 255u && global_ns() - t0 > kTcTimeLimitNs) return false;
+    if (*abort) return false;
+    const uint64_t now = global_ns();
+    if (it == 0) t0 = now;
+    else if (now - t0 > kTcTimeLimitNs) break;
   }
+  *abort = 1;
   return false;
 }
+
+// named barrier over `n` threads, OR-reducing a predicate
+__device__ __forceinline__ bool bar_or(int id, int n, bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\t"
+      "bar.red.or.pred po, %2, %3, pi;\n\tselp.u32 %0, 1, 0, po;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)p), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
 // 32 lanes x 32 consecutive 32-bit TMEM columns: thread i of the warp gets lane (base lane + i)
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
@@ -131,13 +171,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 template <int K>
 struct TcArgs {
   float2* psi;
-  uint64_t ntuples;          // tuples per register
+  uint64_t total;            // tuples over all registers
   uint64_t reg_stride;       // amplitudes per register
-  uint64_t total;            // ntuples * registers
-  IdxSpec s;                 // tuple base index inside a register (targets and controls fixed)
+  int lg;                    // log2(tuples per register)
   int lowbits;               // targets 0..lowbits-1 are register qubits 0..lowbits-1
+  IdxSpec s;                 // tuple base index inside a register (targets and controls fixed)
   uint32_t off[1 << K];      // amplitude offsets of a tuple's members (targets ascending)
-  float b[2 << K][2 << K];   // real form of the matrix, [output][input]
+  float b[2 << K][2 << K];   // real form of the matrix, [output column][input column]
 };
 
 template <int K>
@@ -145,157 +185,338 @@ struct TcSmem {
   static constexpr int D = 1 << K, W = 2 * D;
   static constexpr uint32_t A_BYTES = kTcRows * W * 4;
   static constexpr uint32_t B_BYTES = W * W * 4;
-  // offsets from a 1024-aligned base: A_hi, A_lo, B_hi, B_lo, tuple bases,
-  // member offsets, mbarrier, TMEM slot
-  static constexpr uint32_t A_HI = 0, A_LO = A_BYTES, B_HI = 2 * A_BYTES, B_LO = B_HI + B_BYTES;
-  static constexpr uint32_t BASES = B_LO + B_BYTES;
-  static constexpr uint32_t OFFS = BASES + kTcRows * 8;
-  static constexpr uint32_t MBAR = OFFS + D * 4;
-  static constexpr uint32_t TSLOT = MBAR + 8;
-  static constexpr uint32_t BYTES = TSLOT + 8 + 1024;  // + alignment slack
-  // outputs staged after the MMA has read A: float2 [128][D + 1] over A_hi..A_lo
-  static_assert(kTcRows * (D + 1) * 8 <= 2 * A_BYTES, "output staging fits in the A operands");
+  // offsets from a 1024-aligned base
+  static constexpr uint32_t A0 = 0;                        // stage s: hi at A0 + 2s A_BYTES, lo after it
+  static constexpr uint32_t B_HI = 4 * A_BYTES, B_LO = B_HI + B_BYTES;
+  static constexpr uint32_t ROWOFF = B_LO + B_BYTES;       // P[t]: row t's index relative to its tile
+  static constexpr uint32_t DTAB = ROWOFF + kTcRows * 8;   // deposit of tuple-index byte c (bits 7+8c..)
+  static constexpr uint32_t OFFS = DTAB + 4 * 256 * 8;
+  static constexpr uint32_t MBAR = OFFS + D * 4;           // full[2], empty[2], tfull[2], tempty[2], fin
+  static constexpr uint32_t FLAGS = MBAR + 9 * 8;          // TMEM address, abort flag
+  // epilogue staging when a row holds runs of >= 4 adjacent amplitudes:
+  // float2 [128][D + 2] (the row stride is an odd number of 16-byte chunks,
+  // so rows written by consecutive threads fall in distinct banks)
+  static constexpr int SROW = D + 2;
+  static constexpr uint32_t STAGE = (FLAGS + 16 + 15) & ~15u;
+  static constexpr uint32_t BYTES = STAGE + kTcRows * SROW * 8 + 1024;  // + alignment slack
+  __host__ __device__ static constexpr uint32_t a_hi(int s) { return A0 + (uint32_t)s * 2 * A_BYTES; }
 };
 
+// Amplitude index of tuple t0 + t (t0 a multiple of 128, t < 128) is
+// tile_base(t0) + P[t]: the register and tuple bits of t0 and of t are disjoint
+// (tuples per register and 128 are powers of two), and deposit is a bit scatter.
+__device__ __forceinline__ uint64_t deposit_nb(uint64_t j, const IdxSpec& s) { return deposit(j, s) & ~s.set_bits; }
+
+// deposit of the tuple-index bits 7.. of t0 through per-byte tables
+// (dtab[c][v] = deposit of v << (7 + 8c)); indices up to 2^39 tuples
 template <int K>
-__global__ void __launch_bounds__(kTcThreads) k_block_tc(const __grid_constant__ TcArgs<K> a) {
+__device__ __forceinline__ uint64_t tile_base(uint64_t t0, const TcArgs<K>& a, const uint64_t* dtab) {
+  uint64_t b = (t0 >> a.lg) * a.reg_stride + a.s.set_bits;
+  if (a.lg > 7) {
+    const uint64_t j = (t0 & ((1ull << a.lg) - 1ull)) >> 7;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) b |= dtab[c * 256 + (int)((j >> (8 * c)) & 255u)];
+  }
+  return b;
+}
+
+template <int K>
+__device__ __forceinline__ uint64_t row_offset(int t, const TcArgs<K>& a) {
+  if (a.lg >= 7) return deposit_nb((uint64_t)t, a.s);
+  return (uint64_t)(t >> a.lg) * a.reg_stride + deposit_nb((uint64_t)t & ((1ull << a.lg) - 1ull), a.s);
+}
+
+template <int K, int MODE>
+__global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constant__ TcArgs<K> a) {
   using L = TcSmem<K>;
   constexpr int D = L::D, W = L::W;
+  constexpr uint32_t A_BYTES = L::A_BYTES;
+  // units (16 bytes: two amplitudes; 8 bytes in TC_SCALAR) per tile and per loader thread
+  constexpr int NU = MODE == TC_SCALAR ? kTcRows * D : kTcRows * D / 2;
+  constexpr int UT = NU / kTcLoaders;
+  static_assert(UT * kTcLoaders == NU && UT <= 8, "tile splits evenly over the loaders");
+  using VT = typename std::conditional<MODE == TC_SCALAR, float2, float4>::type;
+
   extern __shared__ unsigned char sm_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)sm_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* s_base = reinterpret_cast<uint64_t*>(sm + L::BASES);
+  uint64_t* s_P = reinterpret_cast<uint64_t*>(sm + L::ROWOFF);
   uint32_t* s_off = reinterpret_cast<uint32_t*>(sm + L::OFFS);
-  float2* s_out = reinterpret_cast<float2*>(sm + L::A_HI);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + L::MBAR);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::TSLOT);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int lb = a.lowbits;
-  const uint32_t lowmask = (1u << lb) - 1u;
+  const uint32_t mb0 = smem_u32(sm + L::MBAR);
+  auto full = [&](int s) { return mb0 + 8u * (uint32_t)s; };
+  auto empty = [&](int s) { return mb0 + 16u + 8u * (uint32_t)s; };
+  auto tfull = [&](int s) { return mb0 + 32u + 8u * (uint32_t)s; };
+  auto tempty = [&](int s) { return mb0 + 48u + 8u * (uint32_t)s; };
+  const uint32_t fin = mb0 + 64u;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::FLAGS);
+  volatile int* abort = reinterpret_cast<volatile int*>(sm + L::FLAGS + 4);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  // the matrix (hi / lo) and the member offsets once per CTA
-  if (tid < D) s_off[tid] = a.off[tid];
+  // ---- setup: the matrix (hi / lo), member and row offsets, barriers, TMEM
   for (int e = tid; e < W * W; e += kTcThreads) {
     const int n = e / W, kk = e % W;
     const float v = a.b[n][kk], h = tf32_hi(v);
     *reinterpret_cast<float*>(sm + L::B_HI + sw128_off(n, kk, W)) = h;
     *reinterpret_cast<float*>(sm + L::B_LO + sw128_off(n, kk, W)) = v - h;
   }
+  if (tid < D) s_off[tid] = a.off[tid];
+  if (tid < kTcRows) s_P[tid] = row_offset(tid, a);
+  uint64_t* s_dtab = reinterpret_cast<uint64_t*>(sm + L::DTAB);
+  for (int e = tid; e < 4 * 256; e += kTcThreads) {
+    const int c = e >> 8, sh = 7 + 8 * c;
+    const uint64_t v = (uint64_t)(e & 255) << sh;
+    s_dtab[e] = (sh < a.lg) ? deposit_nb(v & ((1ull << a.lg) - 1ull), a.s) : 0;
+  }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(full(s), kTcLoaders);
+      mbar_init(empty(s), 1);
+      mbar_init(tfull(s), 1);
+      mbar_init(tempty(s), kTcEpiWarps * 32);
+    }
+    mbar_init(fin, 1);
+    *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == kTcMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"((uint32_t)W));
+                 "r"((uint32_t)(2 * W)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
+  // B written by the generic proxy is read by the tensor core
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
-  const uint32_t mb = smem_u32(mbar);
-  const uint32_t a_hi = smem_u32(sm + L::A_HI), a_lo = smem_u32(sm + L::A_LO);
-  const uint32_t b_hi = smem_u32(sm + L::B_HI), b_lo = smem_u32(sm + L::B_LO);
-  uint32_t parity = 0;
-  bool failed = false;
+  const uint64_t stride_tiles = (uint64_t)gridDim.x;
+  auto tile_row0 = [&](int i) { return ((uint64_t)blockIdx.x + (uint64_t)i * stride_tiles) * kTcRows; };
+  auto tile_rows = [&](uint64_t t0) {
+    return a.total - t0 < (uint64_t)kTcRows ? (int)(a.total - t0) : kTcRows;
+  };
 
-  for (uint64_t t0 = (uint64_t)blockIdx.x * kTcRows; t0 < a.total; t0 += (uint64_t)gridDim.x * kTcRows) {
-    {  // 1. tuple bases
-      const uint64_t t = t0 + tid;
-      uint64_t b = 0;
-      if (t < a.total) {
-        const uint64_t r = t / a.ntuples, j = t - r * a.ntuples;
-        b = r * a.reg_stride + deposit(j, a.s);
-      }
-      s_base[tid] = b;
-    }
-    __syncthreads();
-    const int rows = a.total - t0 < (uint64_t)kTcRows ? (int)(a.total - t0) : kTcRows;
-    // 2. gather: element e -> m_lo = e mod 2^lb, t = (e >> lb) mod 128, m_hi = e >> (lb + 7)
-    {
-      float2 v[D];
+  if (warp < kTcLoadWarps) {
+    // ================================================================ loaders
+    // Every loader thread owns the same UT units of every tile: their global
+    // offsets (relative to the tile base) and shared-memory slots are computed
+    // once.  Threads run independently: the stage mbarriers are the only sync.
+    const int lt = tid;
+    const int lb = a.lowbits;
+    uint64_t goff[UT];
+    uint32_t soff[UT];
+    uint32_t trows = 0;  // the units' rows, 8 bits each (UT <= 4)
+    int tmax = 0;
 #pragma unroll
-      for (int i = 0; i < D; ++i) {
-        const uint32_t e = (uint32_t)tid + (uint32_t)i * kTcThreads;
-        const int t = (int)((e >> lb) & (kTcRows - 1));
-        const uint32_t m = (e & lowmask) | ((e >> (lb + 7)) << lb);
-        v[i] = t < rows ? a.psi[s_base[t] + s_off[m]] : make_float2(0.f, 0.f);
+    for (int k = 0; k < UT; ++k) {
+      const int u = lt + k * kTcLoaders;
+      int t, m;
+      if (MODE == TC_PAIR_MEMBERS) {
+        const int hb = lb - 1;
+        t = (u >> hb) & (kTcRows - 1);
+        m = 2 * ((u & ((1 << hb) - 1)) | ((u >> (hb + 7)) << hb));
+      } else if (MODE == TC_PAIR_TUPLES) {
+        t = 2 * (u & (kTcRows / 2 - 1));
+        m = u >> 6;
+      } else {
+        t = u & (kTcRows - 1);
+        m = u >> 7;
       }
-#pragma unroll
-      for (int i = 0; i < D; ++i) {
-        const uint32_t e = (uint32_t)tid + (uint32_t)i * kTcThreads;
-        const int t = (int)((e >> lb) & (kTcRows - 1));
-        const int m = (int)((e & lowmask) | ((e >> (lb + 7)) << lb));
-        const float hr = tf32_hi(v[i].x), hm = tf32_hi(v[i].y);
-        *reinterpret_cast<float*>(sm + L::A_HI + sw128_off(t, m, kTcRows)) = hr;
-        *reinterpret_cast<float*>(sm + L::A_LO + sw128_off(t, m, kTcRows)) = v[i].x - hr;
-        *reinterpret_cast<float*>(sm + L::A_HI + sw128_off(t, D + m, kTcRows)) = hm;
-        *reinterpret_cast<float*>(sm + L::A_LO + sw128_off(t, D + m, kTcRows)) = v[i].y - hm;
-      }
+      goff[k] = s_P[t] + s_off[m];
+      soff[k] = sw128_off(t, 2 * m, kTcRows);  // PAIR_TUPLES: row t + 1 is at sw128_off(t + 1, 2m)
+      if (UT <= 4) trows |= (uint32_t)t << (8 * k);
+      tmax = max(tmax, MODE == TC_PAIR_TUPLES ? t + 1 : t);
     }
-    // generic-proxy stores -> visible to the tensor core (async proxy)
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    // 3. one thread issues the MMA chain
-    if (tid == 0) {
+    VT v0[UT], v1[UT], v2[UT];
+    auto load = [&](uint64_t t0, VT* v) {
+      const uint64_t tb = tile_base(t0, a, s_dtab);
+      const int rows = tile_rows(t0);
+      if (tmax < rows) {
+#pragma unroll
+        for (int k = 0; k < UT; ++k) v[k] = *reinterpret_cast<const VT*>(a.psi + tb + goff[k]);
+      } else {  // the last, partial tile
+#pragma unroll
+        for (int k = 0; k < UT; ++k) {
+          // UT > 4 only in TC_SCALAR, where every unit of a thread is in row lt mod 128
+          const int t = UT <= 4 ? (int)((trows >> (8 * k)) & 255u) : (lt & (kTcRows - 1));
+          v[k] = t < rows ? *reinterpret_cast<const VT*>(a.psi + tb + goff[k]) : VT{};
+        }
+      }
+    };
+    auto split_store = [&](const VT* v, int s) {
+      unsigned char* ah = sm + L::a_hi(s);
+      unsigned char* al = ah + A_BYTES;
+#pragma unroll
+      for (int k = 0; k < UT; ++k) {
+        if (MODE == TC_PAIR_MEMBERS) {
+          const float4 x = *reinterpret_cast<const float4*>(&v[k]);
+          const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+          *reinterpret_cast<float4*>(ah + soff[k]) = h;  // columns 2m..2m+3: one 16-byte chunk
+          *reinterpret_cast<float4*>(al + soff[k]) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+        } else if (MODE == TC_PAIR_TUPLES) {
+          const float4 x = *reinterpret_cast<const float4*>(&v[k]);
+          const float2 h0 = make_float2(tf32_hi(x.x), tf32_hi(x.y)), h1 = make_float2(tf32_hi(x.z), tf32_hi(x.w));
+          // row t + 1 of the same column: next 128-byte row, chunk index ^ 1 when t is even
+          const uint32_t o0 = soff[k], o1 = (o0 + 128u) ^ 16u;
+          *reinterpret_cast<float2*>(ah + o0) = h0;
+          *reinterpret_cast<float2*>(al + o0) = make_float2(x.x - h0.x, x.y - h0.y);
+          *reinterpret_cast<float2*>(ah + o1) = h1;
+          *reinterpret_cast<float2*>(al + o1) = make_float2(x.z - h1.x, x.w - h1.y);
+        } else {
+          const float2 x = *reinterpret_cast<const float2*>(&v[k]);
+          const float2 h = make_float2(tf32_hi(x.x), tf32_hi(x.y));
+          *reinterpret_cast<float2*>(ah + soff[k]) = h;
+          *reinterpret_cast<float2*>(al + soff[k]) = make_float2(x.x - h.x, x.y - h.y);
+        }
+      }
+    };
+    // tile i is split from one of three register buffers while the loads of
+    // tile i + 2 are in flight in another (the loop body is unrolled over the
+    // rotation, so no register copies wait on loads)
+    auto step = [&](int i, const VT* vc, VT* vp) -> bool {
+      if (tile_row0(i) >= a.total) return false;
+      const int s = i & 1;
+      const uint64_t tn = tile_row0(i + 2);
+      if (tn < a.total) load(tn, vp);
+      // the stage is free once the MMAs that read it two tiles ago have completed
+      if (!mbar_wait(empty(s), ((i >> 1) & 1) ^ 1, abort)) return false;
+      split_store(vc, s);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(full(s));
+      return true;
+    };
+    if (tile_row0(0) < a.total) load(tile_row0(0), v0);
+    if (tile_row0(1) < a.total) load(tile_row0(1), v1);
+    for (int i = 0;; i += 3) {
+      if (!step(i, v0, v2)) break;
+      if (!step(i + 1, v1, v0)) break;
+      if (!step(i + 2, v2, v1)) break;
+    }
+  } else if (warp < kTcMmaWarp) {
+    // ================================================================ epilogue
+    const int q = warp - kTcEpiWarp0;  // TMEM lane quarter
+    const int t = q * 32 + lane;       // this thread's row of every tile
+    const uint64_t myP = s_P[t];
+    const bool staged = MODE == TC_PAIR_MEMBERS && a.lowbits >= 2;
+    float2* stage = reinterpret_cast<float2*>(sm + L::STAGE);
+    for (int i = 0; tile_row0(i) < a.total; ++i) {
+      const int s = i & 1;
+      const uint64_t t0 = tile_row0(i);
+      const int rows = tile_rows(t0);
+      const bool valid = t < rows;
+      const uint64_t tb = tile_base(t0, a, s_dtab);
+      const uint64_t base = tb + myP;
+      // the four epilogue warps agree on giving up (they share named barrier 2)
+      if (bar_or(2, kTcEpiWarps * 32, !mbar_wait(tfull(s), (i >> 1) & 1, abort))) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      constexpr uint32_t idesc = tf32_idesc(W);
+      // 32 columns (16 amplitudes) at a time; the accumulator is released after the last chunk
 #pragma unroll
-      for (int ks = 0; ks < W / 8; ++ks) {
-        const uint32_t koff = (uint32_t)(ks & 3) * 32u;  // 8 tf32 = 32 bytes inside a 128-byte block
-        const uint32_t ablk = (uint32_t)(ks >> 2) * (uint32_t)(kTcRows * 128);
-        const uint32_t bblk = (uint32_t)(ks >> 2) * (uint32_t)(W * 128);
-        const uint64_t dah = sw128_desc(a_hi + ablk + koff), dal = sw128_desc(a_lo + ablk + koff);
-        const uint64_t dbh = sw128_desc(b_hi + bblk + koff), dbl = sw128_desc(b_lo + bblk + koff);
-        mma_tf32(tmem, dah, dbh, idesc, ks > 0 ? 1u : 0u);
-        mma_tf32(tmem, dah, dbl, idesc, 1u);
-        mma_tf32(tmem, dal, dbh, idesc, 1u);
+      for (int c = 0; c < W; c += 32) {
+        float y[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(s * W + c), y);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (c + 32 == W) {
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          mbar_arrive(tempty(s));
+        }
+        const int m0 = c / 2;
+        if (staged) {
+          // stage the row; it leaves in coalesced runs below
+#pragma unroll
+          for (int m = 0; m < 16; m += 2)
+            *reinterpret_cast<float4*>(stage + t * L::SROW + m0 + m) =
+                make_float4(y[2 * m], y[2 * m + 1], y[2 * m + 2], y[2 * m + 3]);
+        } else if (valid) {
+          // consecutive rows hold adjacent amplitudes (or pairs): coalesced stores
+          if (MODE == TC_PAIR_MEMBERS) {
+#pragma unroll
+            for (int m = 0; m < 16; m += 2)
+              *reinterpret_cast<float4*>(a.psi + base + s_off[m0 + m]) =
+                  make_float4(y[2 * m], y[2 * m + 1], y[2 * m + 2], y[2 * m + 3]);
+          } else {
+#pragma unroll
+            for (int m = 0; m < 16; ++m) a.psi[base + s_off[m0 + m]] = make_float2(y[2 * m], y[2 * m + 1]);
+          }
+        }
       }
-      mma_commit(mb);
-    }
-    // 4. bounded wait, then this thread's row of D
-    const bool ok = mbar_wait(mb, parity);
-    parity ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (__syncthreads_or(ok ? 0 : 1)) {
-      failed = true;
-      break;
-    }
-    {
-      float y[W];
-#pragma unroll
-      for (int c = 0; c < W; c += 32) tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, y + c);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      // the MMA has finished reading A: stage the outputs over it, row stride D + 1 (bank spread)
-#pragma unroll
-      for (int m = 0; m < D; ++m) s_out[tid * (D + 1) + m] = make_float2(y[m], y[D + m]);
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    // 5. scatter in the gather's order
+      if (staged) {
+        bar_sync(2, kTcEpiWarps * 32);
+        const int hb = a.lowbits - 1;
 #pragma unroll 4
-    for (int i = 0; i < D; ++i) {
-      const uint32_t e = (uint32_t)tid + (uint32_t)i * kTcThreads;
-      const int t = (int)((e >> lb) & (kTcRows - 1));
-      const uint32_t m = (e & lowmask) | ((e >> (lb + 7)) << lb);
-      if (t < rows) a.psi[s_base[t] + s_off[m]] = s_out[t * (D + 1) + m];
+        for (int k = 0; k < D / 2; ++k) {
+          const int u = t + k * kTcEpiWarps * 32;
+          const int qq = (u & ((1 << hb) - 1)) | ((u >> (hb + 7)) << hb);
+          const int tt = (u >> hb) & (kTcRows - 1);
+          if (tt < rows)
+            *reinterpret_cast<float4*>(a.psi + tb + s_P[tt] + s_off[2 * qq]) =
+                *reinterpret_cast<const float4*>(stage + tt * L::SROW + 2 * qq);
+        }
+        bar_sync(2, kTcEpiWarps * 32);  // the staging buffer is free for the next tile
+      }
     }
-    __syncthreads();  // A, the staged outputs and the tuple bases are free for the next tile
+    __syncwarp();
+  } else {
+    // ================================================================ MMA issue
+    if (lane == 0) {
+      constexpr uint32_t idesc = tf32_idesc(W);
+      const uint32_t b_hi = smem_u32(sm + L::B_HI), b_lo = smem_u32(sm + L::B_LO);
+      bool issued = false;
+      for (int i = 0; tile_row0(i) < a.total; ++i) {
+        const int s = i & 1;
+        const uint32_t ph = (uint32_t)(i >> 1) & 1u;
+        if (!mbar_wait(full(s), ph, abort)) break;
+        if (!mbar_wait(tempty(s), ph ^ 1u, abort)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a_hi = smem_u32(sm + L::a_hi(s)), a_lo = a_hi + A_BYTES;
+        const uint32_t d = tmem + (uint32_t)(s * W);
+#pragma unroll
+        for (int ks = 0; ks < W / 8; ++ks) {
+          const uint32_t koff = (uint32_t)(ks & 3) * 32u;  // 8 tf32 = 32 bytes inside a 128-byte block
+          const uint32_t ablk = (uint32_t)(ks >> 2) * (uint32_t)(kTcRows * 128);
+          const uint32_t bblk = (uint32_t)(ks >> 2) * (uint32_t)(W * 128);
+          const uint64_t dah = sw128_desc(a_hi + ablk + koff), dal = sw128_desc(a_lo + ablk + koff);
+          const uint64_t dbh = sw128_desc(b_hi + bblk + koff), dbl = sw128_desc(b_lo + bblk + koff);
+          mma_tf32(d, dah, dbh, idesc, ks > 0 ? 1u : 0u);
+          mma_tf32(d, dah, dbl, idesc, 1u);
+          mma_tf32(d, dal, dbh, idesc, 1u);
+        }
+        mma_commit(empty(s));
+        mma_commit(tfull(s));
+        issued = true;
+      }
+      // every MMA issued above has completed once this commit arrives
+      if (issued) {
+        mma_commit(fin);
+        volatile int never = 0;
+        mbar_wait(fin, 0, &never);
+      }
+    }
+    __syncwarp();
   }
-  if (failed) {
-    if (tid == 0) atomicExch(&g_tc_status, 1);
-    // one more bounded wait for the MMA still in flight before its TMEM is freed
-    mbar_wait(mb, parity ^ 1u);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)W));
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (tid == 0 && *abort) atomicExch(&g_tc_status, 1);
+  if (warp == kTcMmaWarp)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * W)));
+}
+
+template <int K, int MODE>
+static int launch_tc_mode(const TcArgs<K>& a, cudaStream_t st) {
+  using L = TcSmem<K>;
+  const size_t smem = L::BYTES;
+  int dev = 0, sms = 0;
+  QS_CUDA(cudaGetDevice(&dev));
+  QS_CUDA(cudaFuncSetAttribute(k_block_tc<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const uint64_t tiles = (a.total + kTcRows - 1) / kTcRows;
+  const unsigned grid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)sms);
+  k_block_tc<K, MODE><<<grid, kTcThreads, smem, st>>>(a);
+  QS_LAUNCHED();
+  return QS_OK;
 }
 
 template <int K>
 static int launch_tc_t(float2* psi, int n, int nreg, const Plan& p, cudaStream_t st) {
-  using L = TcSmem<K>;
-  constexpr int D = L::D;
+  constexpr int D = 1 << K;
   TcArgs<K> a;
   memset(&a, 0, sizeof(a));
   // targets in ascending qubit order; the matrix's row and column bits follow
@@ -323,40 +544,43 @@ static int launch_tc_t(float2* psi, int n, int nreg, const Plan& p, cudaStream_t
     for (int c = 0; c < D; ++c) {
       const cd u = p.U[orig(r) * D + orig(c)];
       const float ur = (float)u.real(), ui = (float)u.imag();
-      a.b[r][c] = ur;
-      a.b[r][D + c] = -ui;
-      a.b[D + r][c] = ui;
-      a.b[D + r][D + c] = ur;
+      a.b[2 * r][2 * c] = ur;
+      a.b[2 * r][2 * c + 1] = -ui;
+      a.b[2 * r + 1][2 * c] = ui;
+      a.b[2 * r + 1][2 * c + 1] = ur;
     }
   QS_TRY(make_idx(n, locmask | p.ctrl_mask, p.ctrl_vals, &a.s));
   a.psi = psi;
-  a.ntuples = 1ull << a.s.item_log2;
+  a.lg = a.s.item_log2;
   a.reg_stride = 1ull << n;
-  a.total = a.ntuples * (uint64_t)nreg;
+  a.total = (1ull << a.lg) * (uint64_t)nreg;
   if (a.total == 0) return QS_OK;
-  const size_t smem = L::BYTES;
-  int dev = 0, sms = 0, per_sm = 0;
-  QS_CUDA(cudaGetDevice(&dev));
-  QS_CUDA(cudaFuncSetAttribute(k_block_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  QS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_block_tc<K>, kTcThreads, smem));
-  if (per_sm < 1) return fail(QS_EDEVICE, "tensor-core block kernel does not fit on an SM");
-  // every resident CTA holds W = 2D TMEM columns; an SM has 512
-  per_sm = std::min(per_sm, 512 / (2 * D));
-  const uint64_t tiles = (a.total + kTcRows - 1) / kTcRows;
-  const unsigned grid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)sms * per_sm);
-  k_block_tc<K><<<grid, kTcThreads, smem, st>>>(a);
-  QS_LAUNCHED();
-  return QS_OK;
+  if (a.lowbits >= 1) return launch_tc_mode<K, TC_PAIR_MEMBERS>(a, st);
+  if (!(p.ctrl_mask & 1ull) && a.lg >= 1) return launch_tc_mode<K, TC_PAIR_TUPLES>(a, st);
+  return launch_tc_mode<K, TC_SCALAR>(a, st);
 }
 
 static int g_tc_enabled = 1;
 
-void set_tensor_cores(int on) { g_tc_enabled = on ? 1 : 0; }
+void set_tensor_cores(int mode) { g_tc_enabled = mode < 0 ? 0 : (mode > 2 ? 2 : mode); }
 int tensor_cores_enabled() { return g_tc_enabled; }
 
+// 0: never; 2: always (complex64 dense k = 4, 5); 1 (default): where the
+// tensor-core kernel measured faster than the CUDA-core one on GB300 at n = 25:
+// k = 5 unless qubit 0 is free and no target is below qubit 5 (those tuples are
+// gathered with fully coalesced pairs by the CUDA-core kernel), and k = 4 when
+// qubit 0 is a target.
 bool use_block_tc(int dtype, const Plan& p) {
-  return g_tc_enabled && dtype == QS_C64 && p.op == OP_DENSEK && (p.k == 4 || p.k == 5);
+  if (!g_tc_enabled || dtype != QS_C64 || p.op != OP_DENSEK || (p.k != 4 && p.k != 5)) return false;
+  if (g_tc_enabled == 2) return true;
+  int lo = 64;
+  bool q0 = false;
+  for (int j = 0; j < p.k; ++j) {
+    lo = std::min(lo, p.locs[j]);
+    q0 = q0 || p.locs[j] == 0;
+  }
+  if (p.k == 4) return q0;
+  return q0 || lo < 5 || (p.ctrl_mask & 1ull);
 }
 
 int launch_block_tc(float2* psi, int n, int nreg, const Plan& p, cudaStream_t st) {

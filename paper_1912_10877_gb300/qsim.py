@@ -365,12 +365,14 @@ def schedule_info(circuit: Circuit, tile_qubits: int = 0):
     return p.value, f.value
 
 
-def set_tensor_cores(on: bool) -> None:
-    """Dense 4- and 5-qubit complex64 gates on the tensor cores (default) or the CUDA cores."""
-    N.check(N.lib().qs_set_option(N.QS_OPT_TENSOR_CORES, 1 if on else 0))
+def set_tensor_cores(mode) -> None:
+    """Kernel for dense 4- and 5-qubit complex64 gates: True or 2 = always the tensor
+    cores, False or 0 = the CUDA cores, 1 = per target placement (default)."""
+    m = 2 if mode is True else (0 if mode is False else int(mode))
+    N.check(N.lib().qs_set_option(N.QS_OPT_TENSOR_CORES, m))
 
 
-def tensor_cores() -> bool:
+def tensor_cores() -> int:
     v = ctypes.c_int(0)
     N.check(N.lib().qs_get_option(N.QS_OPT_TENSOR_CORES, ctypes.byref(v)))
-    return bool(v.value)
+    return v.value

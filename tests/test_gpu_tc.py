@@ -21,9 +21,9 @@ def qs():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1912_10877_gb300 import qsim
-    qsim.set_tensor_cores(True)
+    qsim.set_tensor_cores(2)  # always the tensor cores in this file
     yield qsim
-    qsim.set_tensor_cores(True)
+    qsim.set_tensor_cores(1)
 
 
 def rand_unitary(k, rs):
@@ -112,15 +112,15 @@ def test_block_tensor_and_cuda_cores_agree(qs, k):
     want = oracle.apply_circuit(psi, n, gates)
     outs = {}
     for on in (True, False):
-        qs.set_tensor_cores(on)
-        assert qs.tensor_cores() == on
+        qs.set_tensor_cores(2 if on else 0)
+        assert qs.tensor_cores() == (2 if on else 0)
         st = qs.State(n, dtype=torch.complex64)
         st.upload(psi)
         for g in gates:
             st.apply(g)
         st.sync()
         outs[on] = st.numpy()
-    qs.set_tensor_cores(True)
+    qs.set_tensor_cores(2)
     for on in (True, False):
         assert np.max(np.abs(outs[on] - want)) < TOL, on
     assert np.max(np.abs(outs[True] - outs[False])) < 2 * TOL
