@@ -261,20 +261,26 @@ def batch_workload():
     return counts, specs
 
 
-def run_batch_leg(steps: int, warmup: int, compare: bool = True):
+def run_batch_leg(steps: int, warmup: int, compare: bool = True, world: int = 1, rank: int = 0):
     """1024 registers, n ~ U{10..18}, Rz Rx Rz + CNOT ladder x 20 layers each, <sum Z_i Z_{i+1}>:
     forward + reversible gradient of every register in ONE persistent launch (complex64).
+    With N ranks the registers are split by cost (no data-path collective), each rank runs
+    its share, the time is the slowest rank's and the losses are gathered.
     Comparator: the unfused gate-by-gate complex128 path (one kernel per gate per register,
-    per-gate FP64 adjoint), all 1024 registers, same GPU."""
+    per-gate FP64 adjoint), all 1024 registers, same GPU (single rank only)."""
     import torch
     from paper_1912_10877_gb300 import qsim
-    counts, specs = batch_workload()
+    from paper_1912_10877_gb300 import dist as D
+    counts_all, specs_all = batch_workload()
+    mine = D.partition_registers(counts_all, world)[rank]
+    counts = [counts_all[r] for r in mine]
+    specs = [specs_all[r] for r in mine]
     circs = [qsim.Circuit(g, int(n)) for n, (g, _) in zip(counts, specs)]
     obs = [qsim.Observable(W.zz_chain(int(n))) for n in counts]
     prog = qsim.BatchProgram(circs, obs)
     st = qsim.State([int(n) for n in counts], dtype=torch.complex64)
     params = torch.tensor(np.concatenate([p for _, p in specs]), dtype=torch.float64, device="cuda")
-    loss = torch.empty(BATCH_NREG, dtype=torch.float64, device="cuda")
+    loss = torch.empty(len(mine), dtype=torch.float64, device="cuda")
     grad = torch.empty(prog.nparams, dtype=torch.float64, device="cuda")
     for _ in range(warmup):
         prog.run(st, params, grad=True, loss=loss, grad_out=grad)
@@ -285,13 +291,16 @@ def run_batch_leg(steps: int, warmup: int, compare: bool = True):
         prog.run(st, params, grad=True, loss=loss, grad_out=grad)
     e1.record()
     torch.cuda.synchronize()
-    t = e0.elapsed_time(e1) / 1e3 / steps
+    t = D.max_over_ranks(e0.elapsed_time(e1) / 1e3 / steps)
+    losses = D.gather_per_register(loss.cpu().numpy(), mine, BATCH_NREG)
+    assert np.all(np.isfinite(losses)), "a register's loss is missing"
     res = {"metric": "batched fwd+grad circuits/s", "value": round(BATCH_NREG / t, 1), "unit": "circuits/s",
            "ms_per_batch": round(1e3 * t, 3), "dtype": "c64 (f32 gates and uncompute; f64 reductions above warp level)",
            "config": {"workload": f"{BATCH_NREG} registers, n ~ U{{{BATCH_LO}..{BATCH_HI}}} seed 0, Rz.Rx.Rz + "
                                   f"CNOT ladder x {BATCH_DEPTH} layers, <sum Z_i Z_i+1> (open)",
-                      "total_amplitudes": int(sum(1 << int(n) for n in counts)), "launches_per_batch": 2}}
-    if compare:
+                      "total_amplitudes": int(sum(1 << int(n) for n in counts_all)), "launches_per_batch": 2,
+                      "ranks": world, "split": "registers by cost 2^n (LPT), losses gathered"}}
+    if compare and world == 1:
         # gate-by-gate complex128: one launch per gate per register, FP64 adjoint per gate
         rs = np.random.default_rng(0)
         t0 = time.perf_counter()
@@ -356,8 +365,10 @@ def run_diff_leg(steps: int, warmup: int):
 
 def run_large_leg(steps: int, warmup: int):
     """n = 32 (32 GiB complex64): QFT with swap network on a seeded basis state, depth-20
-    brickwork of Rz + Haar SU(2) + CZ, reversible gradient of <Z_1> w.r.t. the 640 angles,
-    all on the tile engine (one HBM round trip of the state per pass)."""
+    brickwork of Rz + Haar SU(2) + CZ, reversible gradient of <Z_1> w.r.t. the 640 angles.
+    The QFT runs on the tile engine (6 passes: its controlled phases fuse); the brickwork
+    forward runs both ways, on the tile engine and as fused 5-qubit blocks (dense ones on
+    the tensor cores), and the faster one counts; the gradient runs on the tile engine."""
     import torch
     from paper_1912_10877_gb300 import qsim
     n, depth = 32, 20
@@ -372,40 +383,97 @@ def run_large_leg(steps: int, warmup: int):
     Nn.check(Nn.lib().qs_backward_tiled_work_bytes(n, ctypes.byref(b)))
     work = torch.empty(b.value, dtype=torch.uint8, device="cuda")
     qp, bp = qsim.schedule_info(qc)[0], qsim.schedule_info(bc)[0]
+    nblocks = len(qsim.circuit_blocks(bc, bparams, 5, matrices=False))
 
-    def fwd():
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    def run_once():
         st.reset([x])
-        st.apply_circuit(qc, tiles=True)
-        st.apply_circuit(bc, bparams, tiles=True)
+        tq = timed(lambda: st.apply_circuit(qc, tiles=True))
+        tb_tiles = timed(lambda: st.apply_circuit(bc, bparams, tiles=True))
+        st.reset([x])
+        timed(lambda: st.apply_circuit(qc, tiles=True))
+        tb_blocks = timed(lambda: st.apply_circuit(bc, bparams, blocks=5))
+        tg = timed(lambda: qsim.backward_tiled(st, bc, bparams, obs, work=work))
+        return tq, tb_tiles, tb_blocks, tg
 
     for _ in range(warmup):
-        fwd()
-        qsim.backward_tiled(st, bc, bparams, obs, work=work)
-    torch.cuda.synchronize()
-    tf = tb = 0.0
+        run_once()
+    acc = np.zeros(4)
     for _ in range(steps):
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        e0.record()
-        fwd()
-        e1.record()
-        qsim.backward_tiled(st, bc, bparams, obs, work=work)
-        e2.record()
-        torch.cuda.synchronize()
-        tf += e0.elapsed_time(e1) / 1e3
-        tb += e1.elapsed_time(e2) / 1e3
-    tf /= steps
-    tb /= steps
+        acc += np.array(run_once())
+    tq, tbt, tbb, tg = acc / steps
+    tf = tq + min(tbt, tbb)
     S = 8 << n
-    fwd_bytes = (qp + bp) * 2 * S          # every pass reads and writes the state once
-    bwd_bytes = bp * 4 * S                 # psi and lambda
     return {"metric": "n=32 QFT + depth-20 brickwork forward and <Z_1> gradient", "unit": "s",
-            "value": round(tf + tb, 4), "forward_s": round(tf, 4), "backward_s": round(tb, 4),
-            "passes": {"qft": qp, "brickwork": bp},
+            "value": round(tf + tg, 4), "forward_s": round(tf, 4), "backward_s": round(tg, 4),
+            "qft_tiles": {"seconds": round(tq, 4), "passes": qp, "gbs": round(qp * 2 * S / tq / 1e9, 1)},
+            "brickwork_tiles": {"seconds": round(tbt, 4), "passes": bp, "gbs": round(bp * 2 * S / tbt / 1e9, 1)},
+            "brickwork_blocks5": {"seconds": round(tbb, 4), "passes": nblocks,
+                                  "gbs": round(nblocks * 2 * S / tbb / 1e9, 1)},
+            "brickwork_forward_used": "blocks5" if tbb < tbt else "tiles",
+            "gradient_tiles": {"seconds": round(tg, 4), "passes": bp, "gbs": round(bp * 4 * S / tg / 1e9, 1)},
             "gates": {"qft": len(W.qft(n, swaps=True)), "brickwork": len(bgates)},
-            "forward_gbs": round(fwd_bytes / tf / 1e9, 1), "backward_gbs": round(bwd_bytes / tb / 1e9, 1),
             "higher_is_better": False,
             "config": {"workload": "n=32 c64, QFT+swaps on basis state (seed 0), brickwork depth 20 (seed 0), "
                                    "grad of <Z_1> wrt 640 angles", "state_gib": 32}}
+
+
+def run_tc_leg(reps: int = 20):
+    """Dense 4- and 5-qubit blocks at n = 25 (complex64, Haar state): the tensor-core
+    kernel (3xTF32 tcgen05 GEMM) against the CUDA-core kernel, per target placement.
+    Bytes per launch: the state read and written once (2 x 2^25 x 8 B); L2 flushed
+    between launches.  The tensor-core flop rate counts the 3 TF32 products."""
+    import torch
+    from paper_1912_10877_gb300 import qsim
+    n = N_QUBITS
+    rs = np.random.default_rng(SEED)
+    st = qsim.State(n, dtype=torch.complex64)
+    st.upload(W.haar_state(n, SEED))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    byts = 2 * (1 << n) * 8
+    out = {}
+    for k in (4, 5):
+        d = 1 << k
+        a = rs.standard_normal((d, d)) + 1j * rs.standard_normal((d, d))
+        q, r = np.linalg.qr(a)
+        U = q * (np.diag(r) / np.abs(np.diag(r)))
+        for place, locs in (("low", tuple(range(k))), ("high", tuple(range(n - k, n))),
+                            ("mixed", (1, 7, 13, 19, 24)[:k])):
+            g = W.Gate("MATRIX", locs, matrix=U)
+            row = {}
+            for mode, name in ((2, "tensor"), (0, "cuda_core")):
+                qsim.set_tensor_cores(mode)
+                for _ in range(3):
+                    st.apply(g)
+                torch.cuda.synchronize()
+                ts = []
+                for _ in range(reps):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    st.apply(g)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1) / 1e3)
+                t = float(np.median(ts))
+                row[name + "_gbs"] = round(byts / t / 1e9, 1)
+                if mode == 2:
+                    w = 2 * d
+                    tiles = (1 << (n - k)) / 128
+                    row["tensor_tf32_tflops"] = round(tiles * 3 * 2 * 128 * w * w / t / 1e12, 1)
+            st.sync()
+            out[f"k{k}_{place}"] = row
+    qsim.set_tensor_cores(1)
+    return {"metric": "dense k-qubit block HBM GB/s at n=25, tensor cores vs CUDA cores", "unit": "GB/s",
+            "placements": {"low": "targets 0..k-1", "high": "targets n-k..n-1", "mixed": "targets (1,7,13,19,24)[:k]"},
+            "results": out, "launches": 2 * 2 * 3 * (reps + 3)}
 
 
 # ------------------------------------------------------------------ CPU baseline (oracle)
@@ -457,6 +525,10 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-tc", action="store_true")
+    ap.add_argument("--leg", default="all", choices=["all", "tc", "batch", "diff", "large"],
+                    help="run one secondary leg alone and print its JSON (profiling captures)")
+    ap.add_argument("--tc-reps", type=int, default=20, help="timed launches per tensor-core configuration")
     ap.add_argument("--reps", type=int, default=REPS, help="repetitions per gate (profiling runs use 1)")
     args = ap.parse_args()
     REPS = args.reps
@@ -498,6 +570,16 @@ def main():
     from paper_1912_10877_gb300 import lib
     lib()
 
+    if args.leg != "all":
+        legs = {"tc": lambda: run_tc_leg(args.tc_reps),
+                "batch": lambda: run_batch_leg(max(1, args.steps), max(1, args.warmup), compare=not args.no_compare,
+                                               world=world, rank=rank),
+                "diff": lambda: run_diff_leg(1, 1), "large": lambda: run_large_leg(1, 1)}
+        out = legs[args.leg]()
+        if rank == 0:
+            print(json.dumps(out))
+        return 0
+
     def barrier():
         if world > 1:
             import torch.distributed as dist
@@ -511,12 +593,8 @@ def main():
     c64 = run_sweep("c64", args.steps, args.warmup, local, with_events=True)
     clk = clocks.stop()
     barrier()
-    t = c64["seconds"]
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    from paper_1912_10877_gb300 import dist as D
+    t = D.max_over_ranks(c64["seconds"])
     value = c64["bytes"] * world / t / 1e9
     e2e = None if args.no_e2e else run_e2e(c64, max(1, args.steps))
     if world > 1 and e2e:
@@ -535,15 +613,20 @@ def main():
                                 for c, v in pc.items()}}
     del c64
     extra = {}
-    if not args.no_c128:
+    # secondary single-GPU legs run at N = 1 only (scaling runs time the headline and the sharded batch)
+    solo = world == 1
+    if not args.no_c128 and solo:
         c128 = run_sweep("c128", max(1, args.steps // 3), max(1, args.warmup // 3), local, with_events=True)
         extra["c128_sweep"] = {"value": round(c128["gbs"], 1), "unit": "GB/s", "steps": max(1, args.steps // 3),
                                "per_class_gbs": {c: round(v["gbs"], 1) for c, v in c128["per_class"].items()},
                                "note": "complex128 FP64 arithmetic; dense 2x2 is FP64-ALU bound on GB300"}
         del c128
     if not args.no_batch:
-        extra["batched"] = run_batch_leg(max(1, args.steps), max(1, args.warmup), compare=not args.no_compare)
-    if not args.no_large:
+        extra["batched"] = run_batch_leg(max(1, args.steps), max(1, args.warmup), compare=not args.no_compare,
+                                         world=world, rank=rank)
+    if not args.no_tc and solo:
+        extra["tensor_core_blocks"] = run_tc_leg(args.tc_reps)
+    if not args.no_large and solo:
         extra["differentiation"] = run_diff_leg(1, 1)
         extra["large"] = run_large_leg(1, 1)
     launches = REPS * len(W.single_gate_suite(N_QUBITS)) * args.steps

@@ -196,12 +196,40 @@ int qs_circuit_schedule_info(const qs_circuit* c, int tile_qubits, int* npasses,
  * engine (QS_EUNSUPPORTED if the circuit does not fit) and
  * QS_APPLY_TILE_QUBITS(m) sets the tile size (5..13).  A circuit keeps its
  * schedule and a parameter buffer between calls, so applies of one circuit
- * must not overlap on different streams. */
+ * must not overlap on different streams.
+ * QS_APPLY_BLOCKS fuses the gates into blocks of at most k qubits
+ * (QS_APPLY_BLOCK_QUBITS(k), 1..5, default 5; targets and controls both
+ * count) and applies each block as one k-qubit instruction with the product
+ * matrix of its gates; dense 4- and 5-qubit blocks of complex64 states may run
+ * on the tensor cores (QS_OPT_TENSOR_CORES).  Gates wider than k stay single. */
 #define QS_APPLY_PER_REGISTER 1
 #define QS_APPLY_UNFUSED 2
 #define QS_APPLY_TILES 4
+#define QS_APPLY_BLOCKS 8
 #define QS_APPLY_TILE_QUBITS(m) ((m) << 8)
+#define QS_APPLY_BLOCK_QUBITS(k) ((k) << 16)
 int qs_apply_circuit(qs_state* s, const qs_circuit* c, const double* host_params, int flags);
+
+/* The k-qubit blocks QS_APPLY_BLOCKS applies (host only, no device work).
+ * *nblocks receives their count.  If not NULL: host_widths[b] = block b's
+ * qubit count; host_locs[b * QS_MAXK + j] = its qubits, ascending, padded
+ * with -1; host_mats[b * 2 * 4^QS_MAXK ...] = its 2^w x 2^w matrix (row-major
+ * interleaved complex doubles, bit j of an index <-> host_locs[b][j], zero
+ * padded) for the parameters host_params.  Call once with NULL arrays for the
+ * count.  Blocks are listed in application order. */
+int qs_circuit_blocks(const qs_circuit* c, const double* host_params, int kmax, int* nblocks,
+                      int32_t* host_widths, int32_t* host_locs, double* host_mats);
+
+/* Autotuner for one circuit on one state shape: applies the circuit with each
+ * candidate flag set (per-gate without fusion, the default, blocks of 2..5
+ * qubits, and for complex64 registers of the circuit's size the tile engine
+ * with 10..13-qubit tiles), 1 warm-up + reps timed applies each (wall clock
+ * around a synchronised stream), and returns the fastest in *best_flags.
+ * If ncand is not NULL it holds the capacity of host_cand_flags / host_cand_ms
+ * on entry and the number of candidates on return (ms = -1: not applicable).
+ * The state's amplitudes are used as scratch: they are overwritten. */
+int qs_autotune_circuit(qs_state* s, const qs_circuit* c, const double* host_params, int reps,
+                        int* best_flags, int* ncand, int32_t* host_cand_flags, double* host_cand_ms);
 
 /* As qs_apply_circuit on a single register, also saving forward checkpoints:
  * after gate index g (0-based) with (g + 1) % ckpt_every == 0 and g + 1 <

@@ -15,7 +15,7 @@ QS_OK, QS_EINVAL, QS_ENOMEM, QS_EDEVICE, QS_ETIMEDOUT, QS_EUNSUPPORTED = 0, -1, 
 QS_C64, QS_C128 = 0, 1
 QS_MAXK = 5
 QS_BATCH_RESET, QS_BATCH_GRAD = 1, 2
-QS_APPLY_PER_REGISTER, QS_APPLY_UNFUSED, QS_APPLY_TILES = 1, 2, 4
+QS_APPLY_PER_REGISTER, QS_APPLY_UNFUSED, QS_APPLY_TILES, QS_APPLY_BLOCKS = 1, 2, 4, 8
 QS_OPT_TENSOR_CORES = 1
 
 GATE_KIND = {"I": 0, "X": 1, "Y": 2, "Z": 3, "H": 4, "S": 5, "SDG": 6, "T": 7, "TDG": 8,
@@ -73,6 +73,8 @@ SIGNATURES = {
     "qs_circuit_info": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "qs_circuit_schedule_info": ([_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "qs_apply_circuit": ([_P, _P, _PD, _I], _I),
+    "qs_circuit_blocks": ([_P, _PD, _I, ctypes.POINTER(_I), _PI32, _PI32, _PD], _I),
+    "qs_autotune_circuit": ([_P, _P, _PD, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), _PI32, _PD], _I),
     "qs_checkpoint_count": ([_P, _I, ctypes.POINTER(_I)], _I),
     "qs_apply_circuit_ckpt": ([_P, _P, _PD, _I, _P], _I),
     "qs_observable_create": ([ctypes.POINTER(PauliTerm), _I, _PP], _I),

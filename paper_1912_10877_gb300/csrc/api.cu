@@ -164,7 +164,8 @@ static int apply_circuit_impl(qs_state* s, const qs_circuit* c, const double* pa
   // tile engine: whole circuit in fused passes when it has enough tiles to fill the GPU
   const int tile = (flags >> 8) & 0xff;
   const bool force_tiles = (flags & QS_APPLY_TILES) != 0;
-  if (!unfused && s->dtype == QS_C64 && s->uniform && s->nq[0] == c->nqubits) {
+  if (force_tiles && (flags & QS_APPLY_BLOCKS)) return fail(QS_EINVAL, "QS_APPLY_TILES and QS_APPLY_BLOCKS together");
+  if (!unfused && !(flags & QS_APPLY_BLOCKS) && s->dtype == QS_C64 && s->uniform && s->nq[0] == c->nqubits) {
     const int m = std::min(s->nq[0], tile > 0 ? tile : 13);
     const uint64_t tiles = (uint64_t)s->nreg << (s->nq[0] - m);
     if (force_tiles || tiles >= 256) {
@@ -173,6 +174,10 @@ static int apply_circuit_impl(qs_state* s, const qs_circuit* c, const double* pa
     }
   } else if (force_tiles) {
     return fail(QS_EUNSUPPORTED, "the tile engine runs uniform complex64 registers of the circuit's size");
+  }
+  if ((flags & QS_APPLY_BLOCKS) && !unfused) {
+    const int kb = (flags >> 16) & 0xf;
+    return apply_blocks(s, c, params, kb > 0 ? kb : QS_MAXK);
   }
   Fuser fz(s, c->nqubits);
   const size_t ab = amp_bytes(s->dtype);
@@ -374,6 +379,7 @@ int qs_circuit_create(int nqubits, const qs_gate_desc* gates, int ngates, const 
 
 int qs_circuit_destroy(qs_circuit* c) {
   if (c && c->fused) free_fused(c->fused);
+  if (c) free_blocks(c);
   delete c;
   return QS_OK;
 }

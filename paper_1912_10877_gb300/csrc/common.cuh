@@ -153,6 +153,9 @@ struct qs_circuit {
   // tile-engine schedule of this circuit (built on first fused apply)
   mutable qs_batch_program* fused = nullptr;
   mutable int fused_tile = 0;
+  // k-qubit block plan of this circuit (built on first block apply)
+  mutable void* blocks = nullptr;
+  mutable int block_k = 0;
 };
 
 struct qs_observable {
@@ -218,6 +221,10 @@ int tensor_cores_enabled();
 bool use_block_tc(int dtype, const Plan& p);
 int launch_block_tc(float2* psi, int n, int nreg, const Plan& p, cudaStream_t st);
 int tc_status_take();  // QS_ETIMEDOUT (and clears it) if a tensor-core wait gave up
+
+// the circuit fused into blocks of at most kmax qubits, gate-by-gate path (blocks.cu)
+int apply_blocks(qs_state* s, const qs_circuit* c, const double* params, int kmax);
+void free_blocks(const qs_circuit* c);
 
 // tile-engine forward of a whole circuit (batch.cu); QS_EUNSUPPORTED if it does not fit
 int fused_forward(qs_state* s, const qs_circuit* c, const double* host_params, int tile_qubits);

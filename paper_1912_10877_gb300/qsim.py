@@ -140,13 +140,18 @@ class State:
         return self
 
     def apply_circuit(self, circuit: "Circuit", params=None, per_register=False, fused=True, tiles=False,
-                      tile_qubits=0):
+                      tile_qubits=0, blocks=0, flags=None):
         """apply!(reg, chain).  fused=False: one launch per gate; tiles=True: force the
-        tile engine (fused passes over 2^tile_qubits-amplitude tiles)."""
+        tile engine (fused passes over 2^tile_qubits-amplitude tiles); blocks=k: fuse
+        the gates into blocks of at most k qubits; flags: raw qs_apply_circuit flags
+        (e.g. from autotune), overriding the others."""
         p = _params_array(params, circuit.nparams * (self.nreg if per_register else 1))
-        flags = (N.QS_APPLY_PER_REGISTER if per_register else 0) | (0 if fused else N.QS_APPLY_UNFUSED)
-        flags |= (N.QS_APPLY_TILES if tiles else 0) | (int(tile_qubits) << 8)
-        N.check(N.lib().qs_apply_circuit(self.handle, circuit.handle, N.dptr(p), flags))
+        if flags is None:
+            flags = (N.QS_APPLY_PER_REGISTER if per_register else 0) | (0 if fused else N.QS_APPLY_UNFUSED)
+            flags |= (N.QS_APPLY_TILES if tiles else 0) | (int(tile_qubits) << 8)
+            if blocks:
+                flags |= N.QS_APPLY_BLOCKS | (int(blocks) << 16)
+        N.check(N.lib().qs_apply_circuit(self.handle, circuit.handle, N.dptr(p), int(flags)))
         return self
 
     def expect(self, obs: "Observable") -> np.ndarray:
@@ -376,3 +381,44 @@ def tensor_cores() -> int:
     v = ctypes.c_int(0)
     N.check(N.lib().qs_get_option(N.QS_OPT_TENSOR_CORES, ctypes.byref(v)))
     return v.value
+
+
+def circuit_blocks(circuit: Circuit, params=None, kmax: int = 5, matrices: bool = True):
+    """The k-qubit blocks of circuit (application order): list of (qubits, matrix or None)."""
+    L = N.lib()
+    nb = ctypes.c_int(0)
+    p = _params_array(params, circuit.nparams)
+    N.check(L.qs_circuit_blocks(circuit.handle, N.dptr(p), int(kmax), ctypes.byref(nb), None, None, None))
+    n = nb.value
+    widths = np.zeros(n, dtype=np.int32)
+    locs = np.zeros(n * N.QS_MAXK, dtype=np.int32)
+    stride = 1 << (2 * N.QS_MAXK)
+    mats = np.zeros(n * stride, dtype=np.complex128) if matrices else None
+    N.check(L.qs_circuit_blocks(circuit.handle, N.dptr(p), int(kmax), ctypes.byref(nb),
+                                widths.ctypes.data_as(N._PI32), locs.ctypes.data_as(N._PI32),
+                                N.dptr(mats.view(np.float64)) if matrices else None))
+    out = []
+    for b in range(n):
+        w = int(widths[b])
+        q = tuple(int(x) for x in locs[b * N.QS_MAXK:b * N.QS_MAXK + w])
+        m = None
+        if matrices:
+            d = 1 << w
+            m = mats[b * stride:b * stride + d * d].reshape(d, d).copy()
+        out.append((q, m))
+    return out
+
+
+def autotune(state: State, circuit: Circuit, params=None, reps: int = 3):
+    """Times the circuit under each fusion / tile candidate on this state (whose
+    amplitudes are overwritten) and returns (best_flags, {flags: ms})."""
+    L = N.lib()
+    p = _params_array(params, circuit.nparams)
+    cap = 32
+    best = ctypes.c_int(0)
+    nc = ctypes.c_int(cap)
+    cf = np.zeros(cap, dtype=np.int32)
+    cm = np.zeros(cap, dtype=np.float64)
+    N.check(L.qs_autotune_circuit(state.handle, circuit.handle, N.dptr(p), int(reps), ctypes.byref(best),
+                                  ctypes.byref(nc), cf.ctypes.data_as(N._PI32), N.dptr(cm)))
+    return best.value, {int(cf[i]): float(cm[i]) for i in range(min(nc.value, cap))}
