@@ -425,6 +425,52 @@ def run_large_leg(steps: int, warmup: int):
                                    "grad of <Z_1> wrt 640 angles", "state_gib": 32}}
 
 
+def run_tiles_leg(n: int = 26, reps: int = 3):
+    """Tile engine at n = 26 (complex64, 512 MiB): QFT + swaps on a basis state and a
+    depth-20 brickwork, forward passes and the brickwork's reversible gradient of <Z_1>;
+    per-pass HBM GB/s (each pass reads and writes the state once; the gradient moves
+    psi and lambda).  Also the brickwork as 5-qubit blocks.  For profiling captures."""
+    import torch
+    from paper_1912_10877_gb300 import qsim
+    x = W.random_basis(n, seed=0)
+    qc = qsim.Circuit(W.qft(n, swaps=True), n)
+    bgates, bparams = W.brickwork(n, 20, seed=0)
+    bc = qsim.Circuit(bgates, n, nparams=len(bparams))
+    obs = qsim.Observable(W.z_on(0))
+    st = qsim.State(n, dtype=torch.complex64)
+    b = ctypes.c_size_t()
+    from paper_1912_10877_gb300 import _native as Nn
+    Nn.check(Nn.lib().qs_backward_tiled_work_bytes(n, ctypes.byref(b)))
+    work = torch.empty(b.value, dtype=torch.uint8, device="cuda")
+    qp, bp = qsim.schedule_info(qc)[0], qsim.schedule_info(bc)[0]
+    nblocks = len(qsim.circuit_blocks(bc, bparams, 5, matrices=False))
+    S = 8 << n
+
+    def timed(fn):
+        ts = []
+        for _ in range(reps):
+            st.reset([x])
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return float(np.median(ts))
+
+    tq = timed(lambda: st.apply_circuit(qc, tiles=True))
+    tb = timed(lambda: st.apply_circuit(bc, bparams, tiles=True))
+    tk = timed(lambda: st.apply_circuit(bc, bparams, blocks=5))
+    tg = timed(lambda: qsim.backward_tiled(st, bc, bparams, obs, work=work))
+    return {"metric": f"tile engine per-pass HBM GB/s at n={n}", "unit": "GB/s",
+            "qft": {"passes": qp, "seconds": round(tq, 5), "gbs": round(qp * 2 * S / tq / 1e9, 1)},
+            "brickwork": {"passes": bp, "seconds": round(tb, 5), "gbs": round(bp * 2 * S / tb / 1e9, 1)},
+            "brickwork_blocks5": {"passes": nblocks, "seconds": round(tk, 5), "gbs": round(nblocks * 2 * S / tk / 1e9, 1)},
+            "brickwork_gradient": {"passes": bp, "seconds": round(tg, 5), "gbs": round(bp * 4 * S / tg / 1e9, 1),
+                                   "note": "timed on the reset state (the timing, not the values, matters here)"}}
+
+
 def run_tc_leg(reps: int = 20):
     """Dense 4- and 5-qubit blocks at n = 25 (complex64, Haar state): the tensor-core
     kernel (3xTF32 tcgen05 GEMM) against the CUDA-core kernel, per target placement.
@@ -526,7 +572,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-tc", action="store_true")
-    ap.add_argument("--leg", default="all", choices=["all", "tc", "batch", "diff", "large"],
+    ap.add_argument("--leg", default="all", choices=["all", "tc", "batch", "diff", "large", "tiles"],
                     help="run one secondary leg alone and print its JSON (profiling captures)")
     ap.add_argument("--tc-reps", type=int, default=20, help="timed launches per tensor-core configuration")
     ap.add_argument("--reps", type=int, default=REPS, help="repetitions per gate (profiling runs use 1)")
@@ -574,7 +620,8 @@ def main():
         legs = {"tc": lambda: run_tc_leg(args.tc_reps),
                 "batch": lambda: run_batch_leg(max(1, args.steps), max(1, args.warmup), compare=not args.no_compare,
                                                world=world, rank=rank),
-                "diff": lambda: run_diff_leg(1, 1), "large": lambda: run_large_leg(1, 1)}
+                "diff": lambda: run_diff_leg(1, 1), "large": lambda: run_large_leg(1, 1),
+                "tiles": lambda: run_tiles_leg()}
         out = legs[args.leg]()
         if rank == 0:
             print(json.dumps(out))
