@@ -401,15 +401,21 @@ def run_large_leg(steps: int, warmup: int):
         timed(lambda: st.apply_circuit(qc, tiles=True))
         tb_blocks = timed(lambda: st.apply_circuit(bc, bparams, blocks=5))
         tg = timed(lambda: qsim.backward_tiled(st, bc, bparams, obs, work=work))
-        return tq, tb_tiles, tb_blocks, tg
+        # the same gradient over 5-qubit blocks, from the same forward state
+        st.reset([x])
+        timed(lambda: st.apply_circuit(qc, tiles=True))
+        timed(lambda: st.apply_circuit(bc, bparams, blocks=5))
+        tgb = timed(lambda: qsim.backward_blocks(st, bc, bparams, obs, kmax=5, work=work))
+        return tq, tb_tiles, tb_blocks, tg, tgb
 
     for _ in range(warmup):
         run_once()
-    acc = np.zeros(4)
+    acc = np.zeros(5)
     for _ in range(steps):
         acc += np.array(run_once())
-    tq, tbt, tbb, tg = acc / steps
+    tq, tbt, tbb, tgt, tgb = acc / steps
     tf = tq + min(tbt, tbb)
+    tg = min(tgt, tgb)
     S = 8 << n
     return {"metric": "n=32 QFT + depth-20 brickwork forward and <Z_1> gradient", "unit": "s",
             "value": round(tf + tg, 4), "forward_s": round(tf, 4), "backward_s": round(tg, 4),
@@ -418,7 +424,10 @@ def run_large_leg(steps: int, warmup: int):
             "brickwork_blocks5": {"seconds": round(tbb, 4), "passes": nblocks,
                                   "gbs": round(nblocks * 2 * S / tbb / 1e9, 1)},
             "brickwork_forward_used": "blocks5" if tbb < tbt else "tiles",
-            "gradient_tiles": {"seconds": round(tg, 4), "passes": bp, "gbs": round(bp * 4 * S / tg / 1e9, 1)},
+            "gradient_tiles": {"seconds": round(tgt, 4), "passes": bp, "gbs": round(bp * 4 * S / tgt / 1e9, 1)},
+            "gradient_blocks5": {"seconds": round(tgb, 4), "blocks": nblocks,
+                                 "gbs": round(nblocks * 6 * S / tgb / 1e9, 1)},
+            "gradient_used": "blocks5" if tgb < tgt else "tiles",
             "gates": {"qft": len(W.qft(n, swaps=True)), "brickwork": len(bgates)},
             "higher_is_better": False,
             "config": {"workload": "n=32 c64, QFT+swaps on basis state (seed 0), brickwork depth 20 (seed 0), "
@@ -463,12 +472,17 @@ def run_tiles_leg(n: int = 26, reps: int = 3):
     tb = timed(lambda: st.apply_circuit(bc, bparams, tiles=True))
     tk = timed(lambda: st.apply_circuit(bc, bparams, blocks=5))
     tg = timed(lambda: qsim.backward_tiled(st, bc, bparams, obs, work=work))
+    wb = torch.empty(S, dtype=torch.uint8, device="cuda")
+    tgb = timed(lambda: qsim.backward_blocks(st, bc, bparams, obs, kmax=5, work=wb))
     return {"metric": f"tile engine per-pass HBM GB/s at n={n}", "unit": "GB/s",
             "qft": {"passes": qp, "seconds": round(tq, 5), "gbs": round(qp * 2 * S / tq / 1e9, 1)},
             "brickwork": {"passes": bp, "seconds": round(tb, 5), "gbs": round(bp * 2 * S / tb / 1e9, 1)},
             "brickwork_blocks5": {"passes": nblocks, "seconds": round(tk, 5), "gbs": round(nblocks * 2 * S / tk / 1e9, 1)},
             "brickwork_gradient": {"passes": bp, "seconds": round(tg, 5), "gbs": round(bp * 4 * S / tg / 1e9, 1),
-                                   "note": "timed on the reset state (the timing, not the values, matters here)"}}
+                                   "note": "timed on the reset state (the timing, not the values, matters here)"},
+            "brickwork_gradient_blocks5": {"blocks": nblocks, "seconds": round(tgb, 5),
+                                           "gbs_model": "per block: Gram reads psi, lambda; uncompute r+w both",
+                                           "gbs": round(nblocks * 6 * S / tgb / 1e9, 1)}}
 
 
 def run_tc_leg(reps: int = 20):

@@ -292,6 +292,23 @@ int qs_backward(qs_state* s, const qs_circuit* c, const double* host_params,
                 const qs_observable* o, int ckpt_every, const void* dev_ckpts, void* dev_work,
                 double* host_grad, double* host_loss);
 
+/* Reversible backward over k-qubit blocks (QS_APPLY_BLOCKS with width kmax),
+ * Sec. "Reverse Mode" with a fused block as the unit: walking the blocks from
+ * last to first, one pass forms rho = sum_x psi_x lambda_x^dag over the
+ * block's tuples (FP32 products per 128 tuples for complex64, FP64 sums), the
+ * gradients of the block's gates follow on the host in FP64 as
+ * 2 c Im Tr(E H E^dag rho) (E: the block's later gates, H: the generator with
+ * its control projector), then psi and lambda are uncomputed by the block's
+ * adjoint.  s holds the final state of a single register (complex64 or
+ * complex128) and holds the uncomputed initial state on return.  dev_work:
+ * qs_backward_blocks_work_bytes() bytes (lambda).  host_grad: nparams doubles
+ * (written), host_loss: <O> (may be NULL).  Every block must span at most
+ * QS_MAXK qubits (QS_EUNSUPPORTED otherwise).  Synchronises the stream. */
+int qs_backward_blocks_work_bytes(int nqubits, int dtype, size_t* out_bytes);
+int qs_backward_blocks(qs_state* s, const qs_circuit* c, const double* host_params,
+                       const qs_observable* o, int kmax, void* dev_work, double* host_grad,
+                       double* host_loss);
+
 /* ---------------------------------------------------------------- batched registers */
 
 /* A batch of registers of uneven sizes, each with its own circuit, parameter

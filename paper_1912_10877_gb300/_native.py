@@ -84,6 +84,8 @@ SIGNATURES = {
     "qs_backward_work_bytes": ([_I, _PSZ], _I),
     "qs_backward": ([_P, _P, _PD, _P, _I, _P, _P, _PD, _PD], _I),
     "qs_backward_tiled_work_bytes": ([_I, _PSZ], _I),
+    "qs_backward_blocks_work_bytes": ([_I, _I, _PSZ], _I),
+    "qs_backward_blocks": ([_P, _P, _PD, _P, _I, _P, _PD, _PD], _I),
     "qs_backward_tiled": ([_P, _P, _PD, _P, _I, _P, _PD, _PD], _I),
     "qs_measure": ([_P, _PD, _I, _PI64, _I], _I),
     "qs_batch_program_create": ([_I, _PP, _PP, _I, _PP], _I),

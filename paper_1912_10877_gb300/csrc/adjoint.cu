@@ -125,7 +125,7 @@ static int launch_adjoint_param(double2* psi, double2* lam, int n, const qs_gate
 }
 
 // generator H (on the targets) and factor c with U = exp(-i theta c H)
-static int generator(const qs_gate_desc& g, std::vector<cd>& G, double* cfac) {
+int gate_generator(const qs_gate_desc& g, std::vector<cd>& G, double* cfac) {
   const int D = 1 << g.nlocs;
   G.assign(D * D, cd(0, 0));
   switch (g.kind) {
@@ -174,7 +174,7 @@ int backward(qs_state* s, const qs_circuit* c, const double* params, const qs_ob
     dagger(U, g.nlocs);
     if (g.param >= 0 && g.kind != QS_GATE_MATRIX) {
       double cfac = 0;
-      QS_TRY(generator(g, G, &cfac));
+      QS_TRY(gate_generator(g, G, &cfac));
       int rc;
       switch (g.nlocs) {
         case 1: rc = launch_adjoint_param<1>(psi, lam, n, g, G, U, partials, dgrad, cfac, st); break;

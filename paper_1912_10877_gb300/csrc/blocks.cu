@@ -9,6 +9,16 @@
 // for arithmetic per amplitude (2^k complex multiply-adds), and dense blocks
 // of 4 and 5 qubits run on the tensor cores.
 //
+// The reversible backward over blocks (Sec. "Reverse Mode" with blocks as the
+// unit): walking the blocks from last to first with psi and lambda the states
+// right after block B = G_m ... G_1 (support S, 2^w = D), every gate G_j of B
+// with a parameter has psi_j = E_j^dag psi, lambda_j = E_j^dag lambda, where
+// E_j = G_m ... G_{j+1} acts on S only.  So
+//   <lambda_j|H_j|psi_j> = Tr(E_j H_j E_j^dag rho),  rho = sum_x psi_x lambda_x^dag,
+// the sum running over the 2^(n-w) tuples x of S.  One pass over psi and
+// lambda forms the D x D matrix rho; every gradient of the block then follows
+// on the host in FP64, and both states are uncomputed by B^dag.
+//
 // The planner walks the gates in order and keeps several open blocks with
 // pairwise disjoint supports (so they commute).  A gate joins the open blocks
 // it touches when the union of their supports and its own qubits (targets and
@@ -163,11 +173,452 @@ int apply_blocks(qs_state* s, const qs_circuit* c, const double* params, int kma
   return QS_OK;
 }
 
+// ------------------------------------------------------------------ block backward
+
+namespace {
+
+constexpr int kGramThreads = 256;
+constexpr int kGramRows = 128;  // tuples staged per tile
+
+template <int D>
+struct GramArgs {
+  uint64_t total;             // tuples
+  uint64_t reg_stride;
+  IdxSpec s;                  // tuple base index (support bits fixed at 0)
+  int lowbits;                // support qubits 0..lowbits-1 are register qubits 0..lowbits-1
+  uint32_t off[D];            // member offsets (support qubits ascending)
+};
+
+template <typename R> struct AmpOf;
+template <> struct AmpOf<float> { using T = float2; };
+template <> struct AmpOf<double> { using T = double2; };
+
+// Per-CTA FP64 partials of the real Gram matrix G = A^T B over all tuples,
+// A = [Re psi_x | Im psi_x], B = [Re lambda_x | Im lambda_x] (rows = tuples).
+// Thread layout: the (2D)^2 entries are split into RB x RB sub-blocks, one
+// per thread of a group; groups split the tuples of a tile.  Products are
+// summed in R over a tile, then added to FP64 accumulators.
+template <typename R, int D>
+__global__ void __launch_bounds__(kGramThreads) k_gram(const typename AmpOf<R>::T* __restrict__ psi,
+                                                       const typename AmpOf<R>::T* __restrict__ lam,
+                                                       const __grid_constant__ GramArgs<D> a,
+                                                       double* __restrict__ partials) {
+  constexpr int W2 = 2 * D, E = W2 * W2;
+  constexpr int EPT = E >= 16 * kGramThreads ? 16 : (E >= 4 * kGramThreads ? 4 : 1);
+  constexpr int RB = EPT == 16 ? 4 : (EPT == 4 ? 2 : 1);
+  constexpr int NTG = E / EPT;                 // threads covering all entries once
+  constexpr int G = kGramThreads / NTG;        // groups
+  static_assert(NTG * G == kGramThreads && NTG * EPT == E, "thread layout");
+  extern __shared__ unsigned char gsm[];
+  R* As = reinterpret_cast<R*>(gsm);                        // [kGramRows][W2]
+  R* Bs = As + kGramRows * W2;                              // [kGramRows][W2]
+  uint64_t* sb = reinterpret_cast<uint64_t*>(Bs + kGramRows * W2);
+  uint32_t* soff = reinterpret_cast<uint32_t*>(sb + kGramRows);
+  const int tid = threadIdx.x, grp = tid / NTG, li = tid % NTG;
+  if (tid < D) soff[tid] = a.off[tid];
+  const int r0 = (li / (W2 / RB)) * RB, c0 = (li % (W2 / RB)) * RB;
+  const int lb = a.lowbits;
+  const uint32_t lowmask = (1u << lb) - 1u;
+  // element (t, col) of a tile row lives at t W2 + swizzled 16-byte chunk: the
+  // chunk index is XORed with t, so that writes of one column by consecutive
+  // rows and 16-byte reads of one row both spread over the banks
+  constexpr int CM = W2 >= 8 ? W2 / 4 - 1 : 0;
+  auto sw = [](int t, int col) { return t * W2 + ((((col >> 2) ^ (t & CM)) & CM) << 2) + (col & 3) + (CM ? 0 : (col & ~3)); };
+  double accd[RB][RB];
+#pragma unroll
+  for (int i = 0; i < RB; ++i)
+#pragma unroll
+    for (int j = 0; j < RB; ++j) accd[i][j] = 0.0;
+  for (uint64_t t0 = (uint64_t)blockIdx.x * kGramRows; t0 < a.total; t0 += (uint64_t)gridDim.x * kGramRows) {
+    const int rows = a.total - t0 < (uint64_t)kGramRows ? (int)(a.total - t0) : kGramRows;
+    if (tid < kGramRows) {
+      const uint64_t t = t0 + tid;
+      uint64_t b = 0;
+      if (t < a.total) {
+        const uint64_t r = t >> a.s.item_log2, j = t & ((1ull << a.s.item_log2) - 1ull);
+        b = r * a.reg_stride + deposit(j, a.s);
+      }
+      sb[tid] = b;
+    }
+    __syncthreads();
+    for (int e = tid; e < kGramRows * D; e += kGramThreads) {
+      const int t = (e >> lb) & (kGramRows - 1);
+      const int m = (int)(((uint32_t)e & lowmask) | (((uint32_t)e >> (lb + 7)) << lb));
+      typename AmpOf<R>::T x{}, y{};
+      if (t < rows) {
+        const uint64_t idx = sb[t] + soff[m];
+        x = psi[idx];
+        y = lam[idx];
+      }
+      As[sw(t, m)] = x.x;
+      As[sw(t, D + m)] = x.y;
+      Bs[sw(t, m)] = y.x;
+      Bs[sw(t, D + m)] = y.y;
+    }
+    __syncthreads();
+    R acc[RB][RB];
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+#pragma unroll
+      for (int j = 0; j < RB; ++j) acc[i][j] = 0;
+    for (int t = grp; t < rows; t += G) {
+      R av[RB], bv[RB];
+      if constexpr (RB == 4 && sizeof(R) == 4) {  // one 16-byte load per operand
+        const float4 x = *reinterpret_cast<const float4*>(As + sw(t, r0));
+        const float4 y = *reinterpret_cast<const float4*>(Bs + sw(t, c0));
+        av[0] = x.x; av[1] = x.y; av[2] = x.z; av[3] = x.w;
+        bv[0] = y.x; bv[1] = y.y; bv[2] = y.z; bv[3] = y.w;
+      } else {
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+          av[i] = As[sw(t, r0 + i)];
+          bv[i] = Bs[sw(t, c0 + i)];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < RB; ++i)
+#pragma unroll
+        for (int j = 0; j < RB; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+#pragma unroll
+      for (int j = 0; j < RB; ++j) accd[i][j] += (double)acc[i][j];
+    __syncthreads();
+  }
+  double* out = partials + (size_t)blockIdx.x * E;
+  if constexpr (G == 1) {
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+#pragma unroll
+      for (int j = 0; j < RB; ++j) out[(r0 + i) * W2 + c0 + j] = accd[i][j];
+  } else {
+    // groups summed in group order (G * E = 256 doubles fit in the operand tiles)
+    static_assert(G * E * sizeof(double) <= 2 * kGramRows * W2 * sizeof(R), "group reduction fits");
+    double* red = reinterpret_cast<double*>(gsm);
+    red[grp * E + r0 * W2 + c0] = accd[0][0];
+    __syncthreads();
+    for (int e = tid; e < E; e += kGramThreads) {
+      double acc = 0.0;
+      for (int g = 0; g < G; ++g) acc += red[g * E + e];
+      out[e] = acc;
+    }
+  }
+}
+
+// out[e] = sum over rows of partials[row][e]: one CTA per entry, rows strided
+// over the threads, then a fixed-shape tree (the result does not depend on timing)
+__global__ void __launch_bounds__(256) k_gram_fold(const double* __restrict__ partials, int nrows, int E,
+                                                   double* __restrict__ out) {
+  __shared__ double red[256];
+  const int e = blockIdx.x;
+  double acc = 0.0;
+  for (int r = threadIdx.x; r < nrows; r += 256) acc += partials[(size_t)r * E + e];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[e] = red[0];
+}
+
+// lambda (+)= O psi for one register, terms in chunks (Pauli strings X^x Z^z with i^{popcount(x&z)})
+constexpr int kObsTerms = 32;
+struct ObsTerms {
+  int nt;
+  uint64_t x[kObsTerms], z[kObsTerms];
+  int ny[kObsTerms];
+  double c[kObsTerms];
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_obs(const typename AmpOf<R>::T* __restrict__ psi,
+                                             typename AmpOf<R>::T* __restrict__ lam, uint64_t dim, int accumulate,
+                                             const __grid_constant__ ObsTerms o) {
+  const uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x;
+  if (i >= dim) return;
+  typename AmpOf<R>::T acc = accumulate ? lam[i] : typename AmpOf<R>::T{};
+  for (int t = 0; t < o.nt; ++t) {
+    const uint64_t j = i ^ o.x[t];
+    const typename AmpOf<R>::T v = psi[j];
+    const R sgn = (R)((__popcll(j & o.z[t]) & 1) ? -o.c[t] : o.c[t]);
+    R re, im;
+    switch (o.ny[t] & 3) {
+      case 0: re = v.x; im = v.y; break;
+      case 1: re = -v.y; im = v.x; break;
+      case 2: re = -v.x; im = -v.y; break;
+      default: re = v.y; im = -v.x; break;
+    }
+    acc.x = fma(sgn, re, acc.x);
+    acc.y = fma(sgn, im, acc.y);
+  }
+  lam[i] = acc;
+}
+
+template <typename R>
+int apply_obs(const void* psi, void* lam, int n, const qs_observable* o, cudaStream_t st) {
+  using T = typename AmpOf<R>::T;
+  const uint64_t dim = 1ull << n;
+  const int nt = (int)o->terms.size();
+  if (nt == 0) {
+    QS_CUDA(cudaMemsetAsync(lam, 0, sizeof(T) * dim, st));
+    return QS_OK;
+  }
+  for (int c0 = 0; c0 < nt; c0 += kObsTerms) {
+    ObsTerms ch;
+    std::memset(&ch, 0, sizeof(ch));
+    ch.nt = std::min(kObsTerms, nt - c0);
+    for (int t = 0; t < ch.nt; ++t) {
+      const qs_pauli_term& term = o->terms[c0 + t];
+      ch.x[t] = term.x_mask;
+      ch.z[t] = term.z_mask;
+      ch.ny[t] = popc(term.x_mask & term.z_mask) & 3;
+      ch.c[t] = term.coeff;
+    }
+    k_obs<R><<<(unsigned)((dim + 255) / 256), 256, 0, st>>>((const T*)psi, (T*)lam, dim, c0 > 0, ch);
+    QS_LAUNCHED();
+  }
+  return QS_OK;
+}
+
+template <typename R, int D>
+int launch_gram(const void* psi, const void* lam, int n, const std::vector<int>& qubits, double* partials,
+                double* folded, cudaStream_t st) {
+  constexpr int W2 = 2 * D, E = W2 * W2;
+  GramArgs<D> a;
+  std::memset(&a, 0, sizeof(a));
+  uint64_t mask = 0;
+  for (int q : qubits) mask |= 1ull << q;
+  QS_TRY(make_idx(n, mask, 0, &a.s));
+  a.reg_stride = 1ull << n;
+  a.total = 1ull << a.s.item_log2;
+  a.lowbits = 0;
+  while (a.lowbits < (int)qubits.size() && qubits[a.lowbits] == a.lowbits) ++a.lowbits;
+  for (int m = 0; m < D; ++m) {
+    uint64_t o = 0;
+    for (int j = 0; j < (int)qubits.size(); ++j)
+      if ((m >> j) & 1) o |= 1ull << qubits[j];
+    a.off[m] = (uint32_t)o;
+  }
+  const size_t smem = 2 * (size_t)kGramRows * W2 * sizeof(R) + kGramRows * 8 + D * 4;
+  int dev = 0, sms = 0, per_sm = 0;
+  QS_CUDA(cudaGetDevice(&dev));
+  QS_CUDA(cudaFuncSetAttribute(k_gram<R, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  QS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram<R, D>, kGramThreads, smem));
+  if (per_sm < 1) return fail(QS_EDEVICE, "Gram kernel does not fit on an SM");
+  const uint64_t tiles = (a.total + kGramRows - 1) / kGramRows;
+  const int grid = (int)std::min<uint64_t>(tiles, (uint64_t)sms * per_sm);
+  k_gram<R, D><<<grid, kGramThreads, smem, st>>>((const typename AmpOf<R>::T*)psi,
+                                                  (const typename AmpOf<R>::T*)lam, a, partials);
+  QS_LAUNCHED();
+  k_gram_fold<<<E, 256, 0, st>>>(partials, grid, E, folded);
+  QS_LAUNCHED();
+  return QS_OK;
+}
+
+// rows x entries of the partials for a block of width w (upper bound over the grid)
+size_t gram_partials_doubles(int sms) {
+  size_t best = 0;
+  for (int w = 0; w <= QS_MAXK; ++w) {
+    const size_t W2 = (size_t)2 << w, E = W2 * W2;
+    const size_t ept = E >= 16 * kGramThreads ? 16 : (E >= 4 * kGramThreads ? 4 : 1);
+    (void)ept;
+    best = std::max(best, (size_t)sms * 8 * E);
+  }
+  return best;
+}
+
+template <typename R>
+int gram(int w, const void* psi, const void* lam, int n, const std::vector<int>& qubits, double* partials,
+         double* folded, cudaStream_t st) {
+  switch (w) {
+    case 0: return launch_gram<R, 1>(psi, lam, n, qubits, partials, folded, st);
+    case 1: return launch_gram<R, 2>(psi, lam, n, qubits, partials, folded, st);
+    case 2: return launch_gram<R, 4>(psi, lam, n, qubits, partials, folded, st);
+    case 3: return launch_gram<R, 8>(psi, lam, n, qubits, partials, folded, st);
+    case 4: return launch_gram<R, 16>(psi, lam, n, qubits, partials, folded, st);
+    case 5: return launch_gram<R, 32>(psi, lam, n, qubits, partials, folded, st);
+  }
+  return fail(QS_EUNSUPPORTED, "block of %d qubits", w);
+}
+
+// H embedded in the block space: acts as H on the targets where the controls
+// match, and as zero elsewhere (the control projector)
+void embed_generator(const std::vector<cd>& H, int k, const int* tpos, uint32_t cmask, uint32_t cval, int w,
+                     std::vector<cd>& out) {
+  const int Dw = 1 << w, Dk = 1 << k;
+  out.assign((size_t)Dw * Dw, cd(0));
+  uint32_t tmask = 0;
+  std::vector<uint32_t> off(Dk, 0);
+  for (int j = 0; j < k; ++j) tmask |= 1u << tpos[j];
+  for (int m = 0; m < Dk; ++m)
+    for (int j = 0; j < k; ++j)
+      if ((m >> j) & 1) off[m] |= 1u << tpos[j];
+  for (uint32_t x = 0; x < (uint32_t)Dw; ++x) {
+    if ((x & tmask) || (x & cmask) != cval) continue;
+    for (int r = 0; r < Dk; ++r)
+      for (int c = 0; c < Dk; ++c) out[(size_t)(x | off[r]) * Dw + (x | off[c])] = H[(size_t)r * Dk + c];
+  }
+}
+
+// rho <- G^dag rho G for a gate G on the block space (both sides, O(D^2 2^k))
+void conj_by_gate(std::vector<cd>& rho, int w, const std::vector<cd>& U, int k, const int* tpos, uint32_t cmask,
+                  uint32_t cval) {
+  const int D = 1 << w, Dk = 1 << k;
+  std::vector<cd> Ud((size_t)Dk * Dk);
+  for (int r = 0; r < Dk; ++r)
+    for (int c = 0; c < Dk; ++c) Ud[(size_t)r * Dk + c] = std::conj(U[(size_t)c * Dk + r]);
+  left_multiply(rho, w, Ud, k, tpos, cmask, cval);  // G^dag rho
+  std::vector<cd> t((size_t)D * D);                 // (G^dag rho) G = (G^dag (G^dag rho)^dag)^dag
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j) t[(size_t)i * D + j] = std::conj(rho[(size_t)j * D + i]);
+  left_multiply(t, w, Ud, k, tpos, cmask, cval);
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j) rho[(size_t)i * D + j] = std::conj(t[(size_t)j * D + i]);
+}
+
+}  // namespace
+
+int backward_blocks(qs_state* s, const qs_circuit* c, const double* params, const qs_observable* o, int kmax,
+                    void* work, double* host_grad, double* host_loss) {
+  if (s->nreg != 1) return fail(QS_EUNSUPPORTED, "the block backward takes a single register");
+  const int n = s->nq[0];
+  if (n != c->nqubits) return fail(QS_EINVAL, "circuit has %d qubits, state %d", c->nqubits, n);
+  if (kmax < 1 || kmax > QS_MAXK) return fail(QS_EINVAL, "block width %d not in 1..%d", kmax, QS_MAXK);
+  if (!work || !host_grad) return fail(QS_EINVAL, "null argument");
+  if (c->nparams > 0 && !params) return fail(QS_EINVAL, "params is NULL");
+  const std::vector<Block>& blocks = cached_blocks(c, kmax);
+  const int nb = (int)blocks.size();
+  // which blocks need rho, and where it goes in device scratch
+  std::vector<int64_t> rho_off(nb, -1);
+  int64_t rho_total = 0;
+  for (int bi = 0; bi < nb; ++bi) {
+    const Block& b = blocks[bi];
+    if (popc(b.support) > QS_MAXK) return fail(QS_EUNSUPPORTED, "a gate acts on more than %d qubits", QS_MAXK);
+    bool has_param = false;
+    for (int gi : b.gates) has_param = has_param || (c->gates[gi].param >= 0 && c->gates[gi].kind != QS_GATE_MATRIX);
+    if (has_param) {
+      rho_off[bi] = rho_total;
+      rho_total += (int64_t)4 << (2 * popc(b.support));
+    }
+  }
+  cudaStream_t st = s->stream;
+  const bool f32 = s->dtype == QS_C64;
+  const uint64_t dim = 1ull << n;
+  if (host_loss) QS_TRY(expect_raw(s->data, s->dtype, n, 1, o, s, host_loss));
+  void* lam = work;
+  QS_TRY(f32 ? apply_obs<float>(s->data, lam, n, o, st) : apply_obs<double>(s->data, lam, n, o, st));
+  int dev = 0, sms = 0;
+  QS_CUDA(cudaGetDevice(&dev));
+  QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const size_t npart = gram_partials_doubles(sms);
+  QS_TRY(ensure_ws(s, s->ws, sizeof(double) * (npart + (size_t)rho_total) + 256));
+  double* partials = (double*)s->ws.ptr;
+  double* rhos = partials + npart;
+  // device pass: per block, rho (if it has parameters) then the uncompute; no host round trip
+  std::vector<int> qubits;
+  std::vector<cd> M;
+  for (int bi = nb - 1; bi >= 0; --bi) {
+    const Block& b = blocks[bi];
+    qubits.clear();
+    for (int q = 0; q < 64; ++q)
+      if ((b.support >> q) & 1ull) qubits.push_back(q);
+    const int w = (int)qubits.size();
+    if (rho_off[bi] >= 0)
+      QS_TRY(f32 ? gram<float>(w, s->data, lam, n, qubits, partials, rhos + rho_off[bi], st)
+                 : gram<double>(w, s->data, lam, n, qubits, partials, rhos + rho_off[bi], st));
+    Plan p;
+    if (b.gates.size() == 1) {
+      const qs_gate_desc& g = c->gates[b.gates[0]];
+      QS_TRY(gate_matrix(c, g, params, M));
+      dagger(M, g.nlocs);
+      QS_TRY(plan_gate(M.data(), g.nlocs, g.locs, g.ctrl_mask, g.ctrl_vals, &p));
+    } else {
+      QS_TRY(block_matrix(c, b, params, qubits, M));
+      dagger(M, w);
+      QS_TRY(plan_gate(M.data(), w, qubits.data(), 0, 0, &p));
+    }
+    QS_TRY(launch_plan_on(s->data, s->dtype, n, 1, (int64_t)dim, p, s));
+    QS_TRY(launch_plan_on(lam, s->dtype, n, 1, (int64_t)dim, p, s));
+  }
+  std::vector<double> G2((size_t)std::max<int64_t>(1, rho_total));
+  if (rho_total > 0)
+    QS_CUDA(cudaMemcpyAsync(G2.data(), rhos, sizeof(double) * rho_total, cudaMemcpyDeviceToHost, st));
+  QS_CUDA(cudaStreamSynchronize(st));
+  QS_TRY(tc_status_take());
+  // host: every block's gradients from its rho (FP64)
+  std::vector<double> grad(std::max(1, c->nparams), 0.0);
+  std::vector<cd> U, H, Hemb, rho;
+  for (int bi = 0; bi < nb; ++bi) {
+    if (rho_off[bi] < 0) continue;
+    const Block& b = blocks[bi];
+    qubits.clear();
+    for (int q = 0; q < 64; ++q)
+      if ((b.support >> q) & 1ull) qubits.push_back(q);
+    const int w = (int)qubits.size(), D = 1 << w, W2 = 2 * D;
+    int pos[64];
+    for (int j = 0; j < w; ++j) pos[qubits[j]] = j;
+    const double* g2 = G2.data() + rho_off[bi];
+    // rho[p][q] = sum_x psi_x[p] conj(lambda_x[q]), from the real Gram matrix
+    rho.assign((size_t)D * D, cd(0));
+    for (int p = 0; p < D; ++p)
+      for (int q = 0; q < D; ++q)
+        rho[(size_t)p * D + q] = cd(g2[(size_t)p * W2 + q] + g2[(size_t)(D + p) * W2 + D + q],
+                                    g2[(size_t)(D + p) * W2 + q] - g2[(size_t)p * W2 + D + q]);
+    // from the last gate back: rho <- E^dag rho E with E the block's later gates, so that
+    // Tr(E H E^dag rho) = Tr(H rho)
+    for (int gj = (int)b.gates.size() - 1; gj >= 0; --gj) {
+      const qs_gate_desc& g = c->gates[b.gates[gj]];
+      int tpos[QS_MAXK];
+      for (int j = 0; j < g.nlocs; ++j) tpos[j] = pos[g.locs[j]];
+      uint32_t cmask = 0, cval = 0;
+      for (int q = 0; q < 64; ++q)
+        if ((g.ctrl_mask >> q) & 1ull) {
+          cmask |= 1u << pos[q];
+          if ((g.ctrl_vals >> q) & 1ull) cval |= 1u << pos[q];
+        }
+      if (g.param >= 0 && g.kind != QS_GATE_MATRIX) {
+        double cfac = 0;
+        QS_TRY(gate_generator(g, H, &cfac));
+        embed_generator(H, g.nlocs, tpos, cmask, cval, w, Hemb);
+        cd tr = 0;
+        for (int i = 0; i < D; ++i)
+          for (int j = 0; j < D; ++j) {
+            const cd h = Hemb[(size_t)i * D + j];
+            if (h != cd(0)) tr += h * rho[(size_t)j * D + i];
+          }
+        grad[g.param] += 2.0 * cfac * tr.imag();
+      }
+      if (gj > 0) {
+        QS_TRY(gate_matrix(c, g, params, U));
+        conj_by_gate(rho, w, U, g.nlocs, tpos, cmask, cval);
+      }
+    }
+  }
+  std::memcpy(host_grad, grad.data(), sizeof(double) * c->nparams);
+  return QS_OK;
+}
+
 }  // namespace qs
 
 using namespace qs;
 
 extern "C" {
+
+int qs_backward_blocks_work_bytes(int nqubits, int dtype, size_t* out_bytes) {
+  if (!out_bytes || nqubits < 1 || nqubits > QS_MAXQ) return fail(QS_EINVAL, "bad arguments");
+  if (dtype != QS_C64 && dtype != QS_C128) return fail(QS_EINVAL, "bad dtype");
+  *out_bytes = ((size_t)1 << nqubits) * (dtype == QS_C64 ? 8 : 16);
+  return QS_OK;
+}
+
+int qs_backward_blocks(qs_state* s, const qs_circuit* c, const double* params, const qs_observable* o, int kmax,
+                       void* dev_work, double* host_grad, double* host_loss) {
+  if (!s || !c || !o) return fail(QS_EINVAL, "null handle");
+  return backward_blocks(s, c, params, o, kmax, dev_work, host_grad, host_loss);
+}
 
 int qs_circuit_blocks(const qs_circuit* c, const double* params, int kmax, int* nblocks, int32_t* widths,
                       int32_t* locs, double* mats) {

@@ -226,6 +226,11 @@ int tc_status_take();  // QS_ETIMEDOUT (and clears it) if a tensor-core wait gav
 int apply_blocks(qs_state* s, const qs_circuit* c, const double* params, int kmax);
 void free_blocks(const qs_circuit* c);
 
+// generator H on a gate's targets and c with U = exp(-i theta c H) (adjoint.cu)
+int gate_generator(const qs_gate_desc& g, std::vector<cd>& G, double* cfac);
+int expect_raw(const void* data, int dtype, int n, int nreg, const qs_observable* o, qs_state* ws_owner,
+               double* host_out);
+
 // tile-engine forward of a whole circuit (batch.cu); QS_EUNSUPPORTED if it does not fit
 int fused_forward(qs_state* s, const qs_circuit* c, const double* host_params, int tile_qubits);
 int fused_backward(qs_state* s, const qs_circuit* c, const double* host_params, const qs_observable* o,

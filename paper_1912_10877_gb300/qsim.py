@@ -422,3 +422,19 @@ def autotune(state: State, circuit: Circuit, params=None, reps: int = 3):
     N.check(L.qs_autotune_circuit(state.handle, circuit.handle, N.dptr(p), int(reps), ctypes.byref(best),
                                   ctypes.byref(nc), cf.ctypes.data_as(N._PI32), N.dptr(cm)))
     return best.value, {int(cf[i]): float(cm[i]) for i in range(min(nc.value, cap))}
+
+
+def backward_blocks(state: State, circuit: Circuit, params, obs: Observable, kmax: int = 5, work=None):
+    """Reversible gradient over k-qubit blocks: (loss, grad); the state is uncomputed to
+    the circuit's input.  work: optional device buffer of one state."""
+    L = N.lib()
+    b = ctypes.c_size_t()
+    N.check(L.qs_backward_blocks_work_bytes(int(circuit.nqubits), state.dtype_code, ctypes.byref(b)))
+    if work is None:
+        work = torch.empty(b.value, dtype=torch.uint8, device=state.buffer.device)
+    p = _params_array(params, circuit.nparams)
+    grad = np.zeros(max(1, circuit.nparams))
+    loss = np.zeros(1)
+    N.check(L.qs_backward_blocks(state.handle, circuit.handle, N.dptr(p), obs.handle, int(kmax),
+                                 ctypes.c_void_p(work.data_ptr()), N.dptr(grad), N.dptr(loss)))
+    return float(loss[0]), grad[:circuit.nparams]
