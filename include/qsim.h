@@ -146,6 +146,15 @@ int qs_state_sync(qs_state* s);
 int qs_set_option(int option, int value);
 int qs_get_option(int option, int* value);
 
+/* Failure-path self-test (no counterpart in the paper): one device thread waits
+ * on an mbarrier phase that nothing completes, through the bounded wait the
+ * tensor-core kernels use, with a limit of limit_ms (0 < limit_ms <= 1000).
+ * host_result[0] = 1 if the wait (wrongly) succeeded, [1] = the abort flag it
+ * raised, [2] = microseconds waited.  Returns QS_ETIMEDOUT when the wait gave
+ * up and the device status word reported it (the expected outcome), and clears
+ * the word.  Synchronises the device. */
+int qs_selftest_bounded_wait(double limit_ms, int* host_result);
+
 /* ---------------------------------------------------------------- gates */
 
 /* instruct!(reg, U, locs, ctrl_locs, ctrl_vals) on every register of s

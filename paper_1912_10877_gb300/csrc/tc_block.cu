@@ -46,7 +46,7 @@ constexpr int kTcLoaders = kTcLoadWarps * 32;       // 512
 constexpr int kTcEpiWarp0 = kTcLoadWarps;           // warps 16..19 (TMEM lane quarters 0..3)
 constexpr int kTcMmaWarp = kTcLoadWarps + kTcEpiWarps;  // warp 20
 constexpr int kTcThreads = (kTcMmaWarp + 1) * 32;   // 672
-constexpr uint32_t kTcSpinLimit = 1u << 24;         // mbarrier polls before giving up
+constexpr uint32_t kTcSpinLimit = 1u << 20;         // mbarrier polls before giving up
 constexpr uint64_t kTcTimeLimitNs = 2000000000ull;  // and at most 2 s of wall time
 
 // how a loader thread's 16-byte (or 8-byte) unit maps onto the tile
@@ -116,10 +116,12 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // bounded wait for completion of the mbarrier phase with the given parity;
-// gives up (and raises *abort) after the poll or time limit, or when another
-// role has raised *abort.  Each try_wait may suspend the thread until the
-// phase completes (hint: at most 1 ms), so polls are few.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int* abort) {
+// gives up (and raises *abort) after limit_ns of wall time or kTcSpinLimit
+// polls, or when another role has raised *abort.  Each try_wait may suspend
+// the thread for up to 20 us while the phase is incomplete, so polls are few
+// and the poll cap alone bounds the wait (2^20 x 20 us = 21 s).
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int* abort,
+                                          uint64_t limit_ns = kTcTimeLimitNs) {
   uint64_t t0 = 0;
   for (uint32_t it = 0; it < kTcSpinLimit; ++it) {
     uint32_t ok;
@@ -127,13 +129,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volati
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
-        : "r"(mbar), "r"(parity), "r"(1000000u)
+        : "r"(mbar), "r"(parity), "r"(20000u)
         : "memory");
     if (ok) return true;
     if (*abort) return false;
     const uint64_t now = global_ns();
     if (it == 0) t0 = now;
-    else if (now - t0 > kTcTimeLimitNs) break;
+    else if (now - t0 > limit_ns) break;
   }
   *abort = 1;
   return false;
@@ -601,4 +603,37 @@ int tc_status_take() {
   return QS_OK;
 }
 
+// One thread waits on an mbarrier whose phase nothing completes, through the
+// same bounded wait as the tensor-core pipeline, and reports through the same
+// device status word.
+__global__ void k_wait_selftest(uint64_t limit_ns, int* out) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  const uint32_t mb = smem_u32(&bar);
+  mbar_init(mb, 1);
+  abort_flag = 0;
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  const uint64_t t0 = global_ns();
+  const bool ok = mbar_wait(mb, 0, &abort_flag, limit_ns);
+  const uint64_t t1 = global_ns();
+  if (!ok) atomicExch(&g_tc_status, 1);
+  out[0] = ok ? 1 : 0;
+  out[1] = abort_flag;
+  out[2] = (int)((t1 - t0) / 1000ull);  // microseconds waited
+}
+
 }  // namespace qs
+
+using namespace qs;
+
+extern "C" int qs_selftest_bounded_wait(double limit_ms, int* host_result) {
+  if (!host_result || !(limit_ms > 0) || limit_ms > 1000) return fail(QS_EINVAL, "limit_ms must be in (0, 1000]");
+  int* d = nullptr;
+  QS_CUDA(cudaMalloc(&d, 3 * sizeof(int)));
+  k_wait_selftest<<<1, 1>>>((uint64_t)(limit_ms * 1e6), d);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpy(host_result, d, 3 * sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(QS_EDEVICE, "wait self-test: %s", cudaGetErrorString(e));
+  return tc_status_take();
+}
