@@ -434,6 +434,45 @@ def run_large_leg(steps: int, warmup: int):
                                    "grad of <Z_1> wrt 640 angles", "state_gib": 32}}
 
 
+def run_small_leg(reps: int = 50):
+    """The small workload (n = 12, complex128, |0..0>, 10 layers of Rz Rx Rz + CNOT ladder,
+    <sum Z_i Z_{i+1}> open): launch-bound.  Per circuit: the gate-by-gate path (one
+    launch per gate), the default path (single-qubit runs fused on the host), and the
+    default path's launches captured once as a CUDA graph and replayed."""
+    import torch
+    from paper_1912_10877_gb300 import qsim
+    n = 12
+    gates, params = W.variational(n, 10, "ladder", seed=0)
+    circ = qsim.Circuit(gates, n)
+    obs = qsim.Observable(W.zz_chain(n))
+    st = qsim.State(n, dtype=torch.complex128)
+
+    def per_circuit(fn):
+        for _ in range(3):
+            st.reset()
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e3 / reps
+
+    t_unf = per_circuit(lambda: st.apply_circuit(circ, params, fused=False))
+    t_def = per_circuit(lambda: st.apply_circuit(circ, params))
+    st.reset()
+    cap = qsim.CapturedCircuit(st, circ, params)
+    t_graph = per_circuit(cap.replay)
+    st.reset()
+    cap.replay()
+    e = float(st.expect(obs)[0])
+    return {"metric": "small variational circuit latency (n=12, complex128)", "unit": "us per circuit",
+            "gate_by_gate_us": round(t_unf, 1), "default_us": round(t_def, 1), "graph_replay_us": round(t_graph, 1),
+            "gates": len(gates), "expectation": e, "higher_is_better": False}
+
+
 def run_tiles_leg(n: int = 26, reps: int = 3):
     """Tile engine at n = 26 (complex64, 512 MiB): QFT + swaps on a basis state and a
     depth-20 brickwork, forward passes and the brickwork's reversible gradient of <Z_1>;
@@ -586,7 +625,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-tc", action="store_true")
-    ap.add_argument("--leg", default="all", choices=["all", "tc", "batch", "diff", "large", "tiles"],
+    ap.add_argument("--leg", default="all", choices=["all", "tc", "batch", "diff", "large", "tiles", "small"],
                     help="run one secondary leg alone and print its JSON (profiling captures)")
     ap.add_argument("--tc-reps", type=int, default=20, help="timed launches per tensor-core configuration")
     ap.add_argument("--reps", type=int, default=REPS, help="repetitions per gate (profiling runs use 1)")
@@ -635,7 +674,7 @@ def main():
                 "batch": lambda: run_batch_leg(max(1, args.steps), max(1, args.warmup), compare=not args.no_compare,
                                                world=world, rank=rank),
                 "diff": lambda: run_diff_leg(1, 1), "large": lambda: run_large_leg(1, 1),
-                "tiles": lambda: run_tiles_leg()}
+                "tiles": lambda: run_tiles_leg(), "small": lambda: run_small_leg()}
         out = legs[args.leg]()
         if rank == 0:
             print(json.dumps(out))
@@ -687,6 +726,8 @@ def main():
                                          world=world, rank=rank)
     if not args.no_tc and solo:
         extra["tensor_core_blocks"] = run_tc_leg(args.tc_reps)
+    if solo:
+        extra["small"] = run_small_leg()
     if not args.no_large and solo:
         extra["differentiation"] = run_diff_leg(1, 1)
         extra["large"] = run_large_leg(1, 1)

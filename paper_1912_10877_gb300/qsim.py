@@ -438,3 +438,31 @@ def backward_blocks(state: State, circuit: Circuit, params, obs: Observable, kma
     N.check(L.qs_backward_blocks(state.handle, circuit.handle, N.dptr(p), obs.handle, int(kmax),
                                  ctypes.c_void_p(work.data_ptr()), N.dptr(grad), N.dptr(loss)))
     return float(loss[0]), grad[:circuit.nparams]
+
+
+class CapturedCircuit:
+    """One apply of `circuit` (fixed parameters and flags) on `state`, recorded as a
+    CUDA graph and replayed with a single launch: the remedy for launch-bound
+    circuits on small registers.  The constructor applies the circuit once outside
+    the capture (host plans, kernel attributes), so reset the state afterwards;
+    `replay()` then applies it again in the state's memory."""
+
+    def __init__(self, state: State, circuit: Circuit, params=None, **apply_kwargs):
+        self.state = state
+        self.stream = torch.cuda.Stream(device=state.device)
+        prev = state.stream
+        state.sync_stream(self.stream)
+        try:
+            with torch.cuda.stream(self.stream):
+                state.apply_circuit(circuit, params, **apply_kwargs)
+            self.stream.synchronize()
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph, stream=self.stream, capture_error_mode="thread_local"):
+                state.apply_circuit(circuit, params, **apply_kwargs)
+        finally:
+            self.stream.synchronize()
+            state.sync_stream(prev)
+
+    def replay(self):
+        self.graph.replay()
+        return self
