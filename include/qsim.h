@@ -146,6 +146,35 @@ int qs_state_sync(qs_state* s);
 int qs_set_option(int option, int value);
 int qs_get_option(int option, int* value);
 
+/* ---------------------------------------------------------------- faithful gradients */
+
+/* Sec. "Forward Mode: Faithful Quantum Gradients".  Shot-based <O> on every
+ * register of s: the terms are split into groups that share a measurement
+ * basis on every qubit (qubit-wise commuting, in order of first appearance;
+ * qs_observable_groups gives their count G).  Per group, a copy of the state
+ * (dev_work: s's size) is rotated to the group's basis (X: H; Y: S^dag then
+ * H), nshots indices are sampled per register with the deterministic sampler
+ * (see qs_measure) from host_u[g][r][0..nshots-1] in [0, 1), and each term
+ * counts (-1)^(ones of the sample on its qubits); host_out[r] = sum over
+ * groups and terms of coeff * count / nshots, plus the identity terms'
+ * coefficients.  Synchronises the stream. */
+int qs_observable_groups(const qs_observable* o, int* ngroups);
+int qs_shot_expect(qs_state* s, const qs_observable* o, const double* host_u, int nshots, void* dev_work,
+                   double* host_out);
+
+/* Eq. shiftrule for every parameter: d<O>/dtheta_k = (<O>(theta_k + pi/2) -
+ * <O>(theta_k - pi/2)) / 2 from |0...0>.  Every parameter must be used by
+ * exactly one uncontrolled Pauli rotation (RX, RY, RZ, ROT; QS_EUNSUPPORTED
+ * otherwise).  The 2 P shifted circuits run as one batch in dev_states (2 P
+ * registers of the circuit's size in dtype, register 2k: +pi/2, 2k+1: -pi/2;
+ * complex64 circuits that fit the batched engine run in one persistent
+ * launch).  nshots = 0: exact <O>; else shot-based as qs_shot_expect with
+ * host_u[g][2P][nshots] and dev_work of dev_states' size.  stream: a
+ * cudaStream_t.  host_grad: P doubles.  Synchronises the stream. */
+int qs_faithful_gradient(const qs_circuit* c, const double* host_params, const qs_observable* o, int dtype,
+                         int nshots, const double* host_u, void* dev_states, void* dev_work, void* stream,
+                         double* host_grad);
+
 /* Failure-path self-test (no counterpart in the paper): one device thread waits
  * on an mbarrier phase that nothing completes, through the bounded wait the
  * tensor-core kernels use, with a limit of limit_ms (0 < limit_ms <= 1000).

@@ -226,6 +226,11 @@ int tc_status_take();  // QS_ETIMEDOUT (and clears it) if a tensor-core wait gav
 int apply_blocks(qs_state* s, const qs_circuit* c, const double* params, int kmax);
 void free_blocks(const qs_circuit* c);
 
+// samples with device uniforms into device indices (reduce.cu)
+size_t sample_scratch_doubles(int n);
+int sample_dev(const void* data, int dtype, int n, const double* dev_u, int nshots, int64_t* dev_out,
+               double* scratch, cudaStream_t st);
+
 // generator H on a gate's targets and c with U = exp(-i theta c H) (adjoint.cu)
 int gate_generator(const qs_gate_desc& g, std::vector<cd>& G, double* cfac);
 int expect_raw(const void* data, int dtype, int n, int nreg, const qs_observable* o, qs_state* ws_owner,

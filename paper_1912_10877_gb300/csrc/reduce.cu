@@ -325,6 +325,33 @@ __global__ void k_collapse_write(T* psi, uint64_t dim, int64_t x, const double2*
 }
 
 // one register at `data` with 2^n amplitudes
+// samples of one register with device uniforms into device indices; scratch:
+// sample_scratch_doubles(n) doubles (block sums of the three-level walk)
+size_t sample_scratch_doubles(int n) {
+  const uint64_t dim = 1ull << n;
+  const uint64_t nb0 = (dim + kF - 1) / kF, nb1 = (nb0 + kF - 1) / kF;
+  return (size_t)(nb0 + nb1);
+}
+
+int sample_dev(const void* data, int dtype, int n, const double* dev_u, int nshots, int64_t* dev_out,
+               double* scratch, cudaStream_t st) {
+  const uint64_t dim = 1ull << n;
+  const uint64_t nb0 = (dim + kF - 1) / kF, nb1 = (nb0 + kF - 1) / kF;
+  double* s0 = scratch;
+  double* s1 = s0 + nb0;
+  if (dtype == QS_C64) k_level0<float2><<<(unsigned)((nb0 + 127) / 128), 128, 0, st>>>((const float2*)data, dim, nb0, s0);
+  else k_level0<double2><<<(unsigned)((nb0 + 127) / 128), 128, 0, st>>>((const double2*)data, dim, nb0, s0);
+  QS_LAUNCHED();
+  k_level1<<<(unsigned)((nb1 + 127) / 128), 128, 0, st>>>(s0, nb0, nb1, s1);
+  QS_LAUNCHED();
+  if (dtype == QS_C64)
+    k_sample<float2><<<(nshots + 127) / 128, 128, 0, st>>>((const float2*)data, dim, s0, nb0, s1, nb1, dev_u, nshots, dev_out);
+  else
+    k_sample<double2><<<(nshots + 127) / 128, 128, 0, st>>>((const double2*)data, dim, s0, nb0, s1, nb1, dev_u, nshots, dev_out);
+  QS_LAUNCHED();
+  return QS_OK;
+}
+
 int measure_one(void* data, int dtype, int n, const double* host_u, int nshots, int64_t* host_out,
                 int collapse, qs_state* owner) {
   cudaStream_t st = owner->stream;

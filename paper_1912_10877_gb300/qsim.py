@@ -466,3 +466,45 @@ class CapturedCircuit:
     def replay(self):
         self.graph.replay()
         return self
+
+
+def observable_groups(obs: Observable) -> int:
+    """Number of measurement-basis groups shot-based estimates use (uniform sets per register)."""
+    g = ctypes.c_int(0)
+    N.check(N.lib().qs_observable_groups(obs.handle, ctypes.byref(g)))
+    return g.value
+
+
+def shot_expect(state: State, obs: Observable, uniforms, work: torch.Tensor | None = None) -> np.ndarray:
+    """Shot-based <O> per register; uniforms: [groups][nreg][nshots] in [0, 1)."""
+    u = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64))
+    if u.ndim != 3 or u.shape[1] != state.nreg:
+        raise ValueError("uniforms must be [groups][nreg][nshots]")
+    if work is None:
+        work = torch.empty_like(state.buffer)
+    out = np.zeros(state.nreg)
+    N.check(N.lib().qs_shot_expect(state.handle, obs.handle, N.dptr(u), int(u.shape[2]),
+                                   ctypes.c_void_p(work.data_ptr()), N.dptr(out)))
+    return out
+
+
+def faithful_gradient(circuit: Circuit, params, obs: Observable, dtype=torch.complex128, nshots: int = 0,
+                      uniforms=None, device="cuda") -> np.ndarray:
+    """Eq. shiftrule gradient of <O> from |0...0> (exact, or from nshots samples per shifted
+    circuit with uniforms [groups][2 nparams][nshots])."""
+    P = circuit.nparams
+    p = _params_array(params, P)
+    code = _dtype_code(dtype)
+    states = torch.empty((2 * P) << circuit.nqubits, dtype=_TORCH_DTYPE[code], device=device)
+    work = torch.empty_like(states) if nshots > 0 else None
+    u = None
+    if nshots > 0:
+        u = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64))
+        if u.shape[1:] != (2 * P, nshots):
+            raise ValueError("uniforms must be [groups][2 nparams][nshots]")
+    grad = np.zeros(max(1, P))
+    N.check(N.lib().qs_faithful_gradient(circuit.handle, N.dptr(p), obs.handle, code, int(nshots),
+                                         N.dptr(u) if u is not None else None, ctypes.c_void_p(states.data_ptr()),
+                                         ctypes.c_void_p(work.data_ptr()) if work is not None else None,
+                                         _stream_ptr(), N.dptr(grad)))
+    return grad[:P]
