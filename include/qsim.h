@@ -175,6 +175,20 @@ int qs_faithful_gradient(const qs_circuit* c, const double* host_params, const q
                          int nshots, const double* host_u, void* dev_states, void* dev_work, void* stream,
                          double* host_grad);
 
+/* MMD loss of the Born machine p = |circuit |0...0>|^2 against the target
+ * distribution host_target (2^n doubles), Sec. "Forward Mode" (Listing mmd):
+ * L = E_{x,x'~p} K - 2 E_{x~p,y~q} K + E_{y,y'~q} K with the Gaussian kernel
+ * K(x, y) = exp(-(x - y)^2 / (2 sigma^2)) on basis indices, and
+ * dL/dtheta_k = (p_+ - p_-)^T K (p - q) from the circuits at theta_k +- pi/2
+ * (same parameter conditions as qs_faithful_gradient).  dev_states holds
+ * 2P + 1 registers (2k: +pi/2, 2k+1: -pi/2, 2P: unshifted).  nshots = 0:
+ * exact distributions; else the empirical distributions of nshots samples per
+ * register drawn with host_u[2P + 1][nshots] (plug-in estimates).  n <= 16.
+ * host_grad: P doubles; host_loss: L (may be NULL).  Synchronises the stream. */
+int qs_mmd_gradient(const qs_circuit* c, const double* host_params, const double* host_target, double sigma,
+                    int dtype, int nshots, const double* host_u, void* dev_states, void* stream,
+                    double* host_grad, double* host_loss);
+
 /* Failure-path self-test (no counterpart in the paper): one device thread waits
  * on an mbarrier phase that nothing completes, through the bounded wait the
  * tensor-core kernels use, with a limit of limit_ms (0 < limit_ms <= 1000).

@@ -18,6 +18,16 @@
 // parameter k (2 P registers in one batch), takes <O> at each (exact, or
 // shot-based), and returns (<O>_+ - <O>_-) / 2.  It holds for parameters used
 // by exactly one uncontrolled Pauli rotation (a reflexive generator).
+//
+// The MMD loss of a Born machine p_theta against a target distribution q,
+// L = E_{x,x'~p} K(x,x') - 2 E_{x~p,y~q} K(x,y) + E_{y,y'~q} K(y,y'), with the
+// Gaussian kernel K(x,y) = exp(-(x - y)^2 / (2 sigma^2)) on basis indices, has
+// (from the paper's shift formula for order-two statistic functionals applied
+// to both p-dependent terms) dL/dtheta_k = (p_+ - p_-)^T K (p - q), p_+- the
+// output distributions at theta_k +- pi/2.  Exact mode uses |psi|^2; shot mode
+// uses the empirical distributions of nshots samples per register (the
+// plug-in estimate).  K acts as a convolution over the index difference,
+// truncated where the kernel underflows to zero in FP64 (exact).
 #include <cmath>
 #include <cstring>
 
@@ -163,11 +173,198 @@ int shot_expect(qs_state* s, const qs_observable* o, const double* host_u, int n
   return QS_OK;
 }
 
+// ------------------------------------------------------------------ MMD loss
+
+namespace {
+
+// dist[r][x] = |psi_rx|^2 (FP64) for registers of 2^n amplitudes
+template <typename T>
+__global__ void k_probs(const T* __restrict__ psi, uint64_t total, double* __restrict__ dist) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const double a = (double)psi[i].x, b = (double)psi[i].y;
+  dist[i] = a * a + b * b;
+}
+
+// counts[r][x] = number of shots of register r that gave x (integer counts, zeroed before)
+__global__ void k_hist(const int64_t* __restrict__ samples, int nshots, int nreg, uint64_t dim,
+                       unsigned long long* __restrict__ counts) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (uint64_t)nreg * nshots) return;
+  const uint64_t r = i / nshots;
+  atomicAdd(counts + r * dim + (uint64_t)samples[i], 1ull);
+}
+
+// in place: dist = count / nshots (one correctly rounded division per entry)
+__global__ void k_counts_to_dist(double* __restrict__ buf, uint64_t total, int nshots) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const unsigned long long c = reinterpret_cast<const unsigned long long*>(buf)[i];
+  buf[i] = (double)c / (double)nshots;
+}
+
+// out[x] = sum_y kd[|x - y|] v[y] over |x - y| < window (kd is zero beyond: FP64 underflow)
+__global__ void k_kernel_conv(const double* __restrict__ v, const double* __restrict__ kd, int64_t dim, int64_t window,
+                              double* __restrict__ out) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= dim) return;
+  const int64_t y0 = x - window + 1 > 0 ? x - window + 1 : 0;
+  const int64_t y1 = x + window < dim ? x + window : dim;
+  double acc = 0.0;
+  for (int64_t y = y0; y < y1; ++y) acc = fma(kd[x > y ? x - y : y - x], v[y], acc);
+  out[x] = acc;
+}
+
+// dots[k] = sum_x (a_k[x] - b_k[x]) w[x], a_k = dist[2k], b_k = dist[2k+1]; one CTA per k, fixed tree
+__global__ void __launch_bounds__(256) k_shift_dots(const double* __restrict__ dist, uint64_t dim,
+                                                    const double* __restrict__ w, double* __restrict__ dots) {
+  __shared__ double red[256];
+  const int k = blockIdx.x;
+  const double* a = dist + (size_t)(2 * k) * dim;
+  const double* b = a + dim;
+  double acc = 0.0;
+  for (uint64_t x = threadIdx.x; x < dim; x += 256) acc += (a[x] - b[x]) * w[x];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) dots[k] = red[0];
+}
+
+// out[0] = sum_x a[x] w[x] (one CTA, fixed tree)
+__global__ void __launch_bounds__(256) k_dot(const double* __restrict__ a, const double* __restrict__ w, uint64_t dim,
+                                             double* __restrict__ out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (uint64_t x = threadIdx.x; x < dim; x += 256) acc += a[x] * w[x];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+__global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b, uint64_t dim, double* __restrict__ out) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < dim) out[i] = a[i] - b[i];
+}
+
+}  // namespace
+
 }  // namespace qs
 
 using namespace qs;
 
 extern "C" {
+
+int qs_mmd_gradient(const qs_circuit* c, const double* params, const double* host_target, double sigma, int dtype,
+                    int nshots, const double* host_u, void* dev_states, void* stream, double* host_grad,
+                    double* host_loss) {
+  if (!c || !host_target || !host_grad || !dev_states) return fail(QS_EINVAL, "null argument");
+  if (!(sigma > 0)) return fail(QS_EINVAL, "sigma must be > 0");
+  const int P = c->nparams, n = c->nqubits;
+  if (n > 16) return fail(QS_EUNSUPPORTED, "the MMD kernel sums are built for n <= 16");
+  if (P > 0 && !params) return fail(QS_EINVAL, "params is NULL");
+  if (nshots > 0 && !host_u) return fail(QS_EINVAL, "uniforms are NULL");
+  std::vector<int> uses(std::max(1, P), 0);
+  for (const qs_gate_desc& g : c->gates) {
+    if (g.param < 0) continue;
+    const bool pauli_rot = g.kind == QS_GATE_RX || g.kind == QS_GATE_RY || g.kind == QS_GATE_RZ || g.kind == QS_GATE_ROT;
+    if (!pauli_rot || g.ctrl_mask) return fail(QS_EUNSUPPORTED, "parameter shift needs uncontrolled Pauli rotations");
+    ++uses[g.param];
+  }
+  for (int k = 0; k < P; ++k)
+    if (uses[k] != 1) return fail(QS_EUNSUPPORTED, "parameter %d is used %d times (shift rule needs one use)", k, uses[k]);
+  const int R = 2 * P + 1;  // 2k: +pi/2, 2k+1: -pi/2, 2P: unshifted
+  const uint64_t dim = 1ull << n;
+  cudaStream_t st = (cudaStream_t)stream;
+  qs_state* s = nullptr;
+  QS_TRY(qs_state_create(n, dtype, R, dev_states, stream, &s));
+  std::vector<double> pm((size_t)R * std::max(1, P), 0.0);
+  for (int r = 0; r < R; ++r)
+    for (int j = 0; j < P; ++j) {
+      const int k = r / 2;
+      const double sh = (r < 2 * P && j == k) ? ((r & 1) ? -M_PI / 2 : M_PI / 2) : 0.0;
+      pm[(size_t)r * P + j] = params[j] + sh;
+    }
+  int rc = qs_state_reset(s, nullptr);
+  if (rc == QS_OK && P > 0) rc = qs_apply_circuit(s, c, pm.data(), QS_APPLY_PER_REGISTER);
+  else if (rc == QS_OK) rc = qs_apply_circuit(s, c, nullptr, 0);
+  // device scratch: distributions R x dim, target, kd, Kp - Kq, Kq, diff, dots, samples, uniforms
+  const size_t nsr = (size_t)R * std::max(1, nshots);
+  const size_t sscr = sample_scratch_doubles(n);
+  const size_t doubles = (size_t)R * dim + 5 * dim + (size_t)R + 4 + nsr + sscr;
+  if (rc == QS_OK) rc = ensure_ws(s, s->ws, sizeof(double) * doubles + sizeof(int64_t) * nsr + 256);
+  if (rc != QS_OK) {
+    qs_state_destroy(s);
+    return rc;
+  }
+  double* dist = (double*)s->ws.ptr;
+  double* dq = dist + (size_t)R * dim;
+  double* dkd = dq + dim;
+  double* dkp = dkd + dim;  // K p
+  double* dkq = dkp + dim;  // K q
+  double* dw = dkq + dim;   // K p - K q
+  double* ddots = dw + dim;
+  double* dsc = ddots + R;  // [0]: p K p, [1]: p K q, [2]: q K q
+  double* du = dsc + 4;
+  double* dscr = du + nsr;
+  int64_t* dsamp = (int64_t*)(dscr + sscr);
+  const unsigned gb = (unsigned)((R * dim + 255) / 256), g1 = (unsigned)((dim + 255) / 256);
+  auto run = [&]() -> int {
+    if (nshots > 0) {
+      QS_CUDA(cudaMemsetAsync(dist, 0, sizeof(double) * R * dim, st));
+      QS_CUDA(cudaMemcpyAsync(du, host_u, sizeof(double) * nsr, cudaMemcpyHostToDevice, st));
+      const size_t ab = amp_bytes(dtype);
+      for (int r = 0; r < R; ++r)
+        QS_TRY(sample_dev((const char*)s->data + ab * s->off[r], dtype, n, du + (size_t)r * nshots, nshots,
+                          dsamp + (size_t)r * nshots, dscr, st));
+      k_hist<<<(unsigned)((nsr + 255) / 256), 256, 0, st>>>(dsamp, nshots, R, dim, (unsigned long long*)dist);
+      k_counts_to_dist<<<gb, 256, 0, st>>>(dist, (uint64_t)R * dim, nshots);
+    } else if (dtype == QS_C64) {
+      k_probs<float2><<<gb, 256, 0, st>>>((const float2*)s->data, (uint64_t)R * dim, dist);
+    } else {
+      k_probs<double2><<<gb, 256, 0, st>>>((const double2*)s->data, (uint64_t)R * dim, dist);
+    }
+    QS_LAUNCHED();
+    // kernel profile kd[d] = exp(-d^2 / (2 sigma^2)), zero where it underflows
+    std::vector<double> kd(dim, 0.0);
+    int64_t window = 0;
+    for (uint64_t d = 0; d < dim; ++d) {
+      const double v = std::exp(-(double)d * (double)d / (2.0 * sigma * sigma));
+      if (v == 0.0) break;
+      kd[d] = v;
+      window = (int64_t)d + 1;
+    }
+    QS_CUDA(cudaMemcpyAsync(dkd, kd.data(), sizeof(double) * dim, cudaMemcpyHostToDevice, st));
+    QS_CUDA(cudaMemcpyAsync(dq, host_target, sizeof(double) * dim, cudaMemcpyHostToDevice, st));
+    const double* p = dist + (size_t)(2 * P) * dim;
+    k_kernel_conv<<<g1, 256, 0, st>>>(p, dkd, (int64_t)dim, window, dkp);
+    k_kernel_conv<<<g1, 256, 0, st>>>(dq, dkd, (int64_t)dim, window, dkq);
+    k_sub<<<g1, 256, 0, st>>>(dkp, dkq, dim, dw);
+    QS_LAUNCHED();
+    if (P > 0) k_shift_dots<<<P, 256, 0, st>>>(dist, dim, dw, ddots);
+    k_dot<<<1, 256, 0, st>>>(p, dkp, dim, dsc + 0);
+    k_dot<<<1, 256, 0, st>>>(p, dkq, dim, dsc + 1);
+    k_dot<<<1, 256, 0, st>>>(dq, dkq, dim, dsc + 2);
+    QS_LAUNCHED();
+    std::vector<double> dots(std::max(1, P)), sc(3);
+    if (P > 0) QS_CUDA(cudaMemcpyAsync(dots.data(), ddots, sizeof(double) * P, cudaMemcpyDeviceToHost, st));
+    QS_CUDA(cudaMemcpyAsync(sc.data(), dsc, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
+    QS_CUDA(cudaStreamSynchronize(st));
+    for (int k = 0; k < P; ++k) host_grad[k] = dots[k];
+    if (host_loss) *host_loss = sc[0] - 2.0 * sc[1] + sc[2];
+    return QS_OK;
+  };
+  rc = run();
+  qs_state_destroy(s);
+  return rc;
+}
+
 
 int qs_observable_groups(const qs_observable* o, int* ngroups) {
   if (!o || !ngroups) return fail(QS_EINVAL, "null argument");

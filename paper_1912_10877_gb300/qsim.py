@@ -508,3 +508,28 @@ def faithful_gradient(circuit: Circuit, params, obs: Observable, dtype=torch.com
                                          ctypes.c_void_p(work.data_ptr()) if work is not None else None,
                                          _stream_ptr(), N.dptr(grad)))
     return grad[:P]
+
+
+def mmd_gradient(circuit: Circuit, params, target, sigma: float, dtype=torch.complex128, nshots: int = 0,
+                 uniforms=None, device="cuda"):
+    """(loss, grad) of the MMD loss of the circuit's output distribution against target
+    (2^n probabilities), Gaussian kernel of bandwidth sigma on basis indices; exact, or
+    from nshots samples per register with uniforms [2 nparams + 1][nshots]."""
+    P = circuit.nparams
+    p = _params_array(params, P)
+    code = _dtype_code(dtype)
+    q = np.ascontiguousarray(np.asarray(target, dtype=np.float64))
+    if q.size != (1 << circuit.nqubits):
+        raise ValueError("target must have 2^n entries")
+    states = torch.empty((2 * P + 1) << circuit.nqubits, dtype=_TORCH_DTYPE[code], device=device)
+    u = None
+    if nshots > 0:
+        u = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64))
+        if u.shape != (2 * P + 1, nshots):
+            raise ValueError("uniforms must be [2 nparams + 1][nshots]")
+    grad = np.zeros(max(1, P))
+    loss = np.zeros(1)
+    N.check(N.lib().qs_mmd_gradient(circuit.handle, N.dptr(p), N.dptr(q), float(sigma), code, int(nshots),
+                                    N.dptr(u) if u is not None else None, ctypes.c_void_p(states.data_ptr()),
+                                    _stream_ptr(), N.dptr(grad), N.dptr(loss)))
+    return float(loss[0]), grad[:P]

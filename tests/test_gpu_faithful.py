@@ -157,3 +157,54 @@ def test_shift_rule_rejects_controlled_and_shared_parameters(qs):
         with pytest.raises(N.QsimError) as e:
             qs.faithful_gradient(c, [0.3], obs)
         assert e.value.code == N.QS_EUNSUPPORTED
+
+
+def kernel_matrix(n, sigma):
+    x = np.arange(1 << n, dtype=float)
+    return np.exp(-(x[:, None] - x[None, :]) ** 2 / (2 * sigma * sigma))
+
+
+def oracle_mmd(n, gates, params, q, sigma, nshots=0, u=None):
+    """Loss and shift-rule gradient from the oracle's distributions (exact) or from the
+    oracle's samples with the same uniforms (register order: 2k +, 2k+1 -, 2P unshifted)."""
+    P = len(params)
+    K = kernel_matrix(n, sigma)
+    dists = []
+    for r in range(2 * P + 1):
+        pr = np.array(params, dtype=float)
+        if r < 2 * P:
+            pr[r // 2] += -math.pi / 2 if r % 2 else math.pi / 2
+        psi = oracle.apply_circuit(oracle.zero_state(n), n, gates, pr)
+        if nshots:
+            x = oracle.sample(psi, n, u[r])
+            dists.append(np.bincount(np.asarray(x, dtype=np.int64), minlength=1 << n) / nshots)
+        else:
+            dists.append(np.abs(psi) ** 2)
+    p = dists[-1]
+    loss = p @ K @ p - 2 * p @ K @ q + q @ K @ q
+    w = K @ p - K @ q
+    grad = np.array([(dists[2 * k] - dists[2 * k + 1]) @ w for k in range(P)])
+    return loss, grad
+
+
+@pytest.mark.parametrize("sigma", [0.7, 3.0])
+def test_mmd_gradient_exact_and_shots(qs, sigma):
+    n = 5
+    gates, params = W.variational(n, 1, "ladder", seed=4)
+    rs = np.random.default_rng(5)
+    q = rs.random(1 << n)
+    q /= q.sum()
+    circ = qs.Circuit(gates, n)
+    P = len(params)
+    loss, g = qs.mmd_gradient(circ, params, q, sigma)
+    wl, wg = oracle_mmd(n, gates, params, q, sigma)
+    assert abs(loss - wl) < 1e-12 and np.max(np.abs(g - wg)) < 1e-12
+    nshots = 400
+    u = W.shot_uniforms(nshots, seed=9, nreg=2 * P + 1)
+    loss, g = qs.mmd_gradient(circ, params, q, sigma, nshots=nshots, uniforms=u)
+    wl, wg = oracle_mmd(n, gates, params, q, sigma, nshots, u)
+    assert abs(loss - wl) < 1e-12 and np.max(np.abs(g - wg)) < 1e-12
+    # complex64, exact distributions from FP32 amplitudes
+    loss64, g64 = qs.mmd_gradient(circ, params, q, sigma, dtype=torch.complex64)
+    wl, wg = oracle_mmd(n, gates, params, q, sigma)
+    assert abs(loss64 - wl) < 1e-5 and np.max(np.abs(g64 - wg)) < 1e-5
