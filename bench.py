@@ -473,6 +473,29 @@ def run_small_leg(reps: int = 50):
             "gates": len(gates), "expectation": e, "higher_is_better": False}
 
 
+def run_matrix_leg(n: int = 20, reps: int = 5):
+    """mat(heisenberg(n)) (periodic) as a CSR matrix on the device: row pointers (count +
+    scan) and the fill, timed together; the paper reports 6.33 s for n = 20 on a laptop."""
+    import torch
+    from paper_1912_10877_gb300 import qsim
+    obs = qsim.Observable(W.heisenberg(n))
+    qsim.observable_csr(obs, n)
+    torch.cuda.synchronize()
+    ts = []
+    nnz = 0
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        rowptr, cols, vals = qsim.observable_csr(obs, n)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+        nnz = int(cols.numel())
+        del rowptr, cols, vals
+    t = float(np.median(ts))
+    return {"metric": f"mat(heisenberg({n})) CSR construction", "unit": "s", "value": round(t, 5), "nnz": nnz,
+            "bytes_written": nnz * 24 + ((1 << n) + 1) * 8, "higher_is_better": False,
+            "paper_context": "6.330 s for mat(heisenberg(20)) on a laptop (Sec. Matrix Representation and AD Performance)"}
+
+
 def run_tiles_leg(n: int = 26, reps: int = 3):
     """Tile engine at n = 26 (complex64, 512 MiB): QFT + swaps on a basis state and a
     depth-20 brickwork, forward passes and the brickwork's reversible gradient of <Z_1>;
@@ -625,7 +648,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-tc", action="store_true")
-    ap.add_argument("--leg", default="all", choices=["all", "tc", "batch", "diff", "large", "tiles", "small"],
+    ap.add_argument("--leg", default="all", choices=["all", "tc", "batch", "diff", "large", "tiles", "small", "matrix"],
                     help="run one secondary leg alone and print its JSON (profiling captures)")
     ap.add_argument("--tc-reps", type=int, default=20, help="timed launches per tensor-core configuration")
     ap.add_argument("--reps", type=int, default=REPS, help="repetitions per gate (profiling runs use 1)")
@@ -674,7 +697,8 @@ def main():
                 "batch": lambda: run_batch_leg(max(1, args.steps), max(1, args.warmup), compare=not args.no_compare,
                                                world=world, rank=rank),
                 "diff": lambda: run_diff_leg(1, 1), "large": lambda: run_large_leg(1, 1),
-                "tiles": lambda: run_tiles_leg(), "small": lambda: run_small_leg()}
+                "tiles": lambda: run_tiles_leg(), "small": lambda: run_small_leg(),
+                "matrix": lambda: run_matrix_leg()}
         out = legs[args.leg]()
         if rank == 0:
             print(json.dumps(out))
@@ -728,6 +752,7 @@ def main():
         extra["tensor_core_blocks"] = run_tc_leg(args.tc_reps)
     if solo:
         extra["small"] = run_small_leg()
+        extra["matrix"] = run_matrix_leg()
     if not args.no_large and solo:
         extra["differentiation"] = run_diff_leg(1, 1)
         extra["large"] = run_large_leg(1, 1)

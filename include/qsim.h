@@ -189,6 +189,25 @@ int qs_mmd_gradient(const qs_circuit* c, const double* host_params, const double
                     int dtype, int nshots, const double* host_u, void* dev_states, void* stream,
                     double* host_grad, double* host_loss);
 
+/* ---------------------------------------------------------------- sparse matrices */
+
+/* CSR matrix of a Pauli sum on nqubits qubits (Sec. "Matrix Representation",
+ * App. "Matrix Types"; mat(heisenberg(20)) in Sec. "Matrix Representation and
+ * AD Performance"), in two device passes.  qs_observable_csr_rows writes the
+ * row pointers (dev_rowptr: 2^n + 1 int64) using dev_scratch (2^n / 1024 + 2
+ * int64) and returns the nonzero count in *host_nnz (synchronises);
+ * qs_observable_csr_fill then writes the column indices (dev_cols: nnz int64,
+ * ascending within a row) and values (dev_vals: nnz interleaved complex
+ * doubles).  Entry (i, j) = sum of the terms with x_mask = i ^ j of
+ * coeff * i^{popcount(x&z)} * (-1)^{popcount(j&z)} (the action qs_expect
+ * uses); entries that sum to exactly zero are not stored.  At most 64
+ * distinct x masks and 256 terms (QS_EUNSUPPORTED otherwise); nqubits <= 34.
+ * stream: a cudaStream_t. */
+int qs_observable_csr_rows(const qs_observable* o, int nqubits, int64_t* dev_rowptr, int64_t* dev_scratch,
+                           int64_t* host_nnz, void* stream);
+int qs_observable_csr_fill(const qs_observable* o, int nqubits, const int64_t* dev_rowptr, int64_t* dev_cols,
+                           double* dev_vals, void* stream);
+
 /* Failure-path self-test (no counterpart in the paper): one device thread waits
  * on an mbarrier phase that nothing completes, through the bounded wait the
  * tensor-core kernels use, with a limit of limit_ms (0 < limit_ms <= 1000).

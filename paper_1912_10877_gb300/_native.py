@@ -71,6 +71,8 @@ SIGNATURES = {
     "qs_shot_expect": ([_P, _P, _PD, _I, _P, _PD], _I),
     "qs_faithful_gradient": ([_P, _PD, _P, _I, _I, _PD, _P, _P, _P, _PD], _I),
     "qs_mmd_gradient": ([_P, _PD, _PD, _D, _I, _I, _PD, _P, _P, _PD, _PD], _I),
+    "qs_observable_csr_rows": ([_P, _I, _P, _P, _PI64, _P], _I),
+    "qs_observable_csr_fill": ([_P, _I, _P, _P, _P, _P], _I),
     "qs_apply_gate": ([_P, _PD, _I, _PI32, _I, _PI32, _PI32], _I),
     "qs_apply_named": ([_P, _I, _I, _PI32, _PI32, _I, _PI32, _PI32, _D], _I),
     "qs_circuit_create": ([_I, ctypes.POINTER(GateDesc), _I, _PD, ctypes.c_int64, _I, _PP], _I),

@@ -533,3 +533,19 @@ def mmd_gradient(circuit: Circuit, params, target, sigma: float, dtype=torch.com
                                     N.dptr(u) if u is not None else None, ctypes.c_void_p(states.data_ptr()),
                                     _stream_ptr(), N.dptr(grad), N.dptr(loss)))
     return float(loss[0]), grad[:P]
+
+
+def observable_csr(obs: Observable, nqubits: int, device="cuda"):
+    """mat(O) as CSR on the device: (rowptr int64 [2^n + 1], cols int64 [nnz], vals complex128 [nnz])."""
+    L = N.lib()
+    dim = 1 << nqubits
+    rowptr = torch.empty(dim + 1, dtype=torch.int64, device=device)
+    scratch = torch.empty(dim // 1024 + 2, dtype=torch.int64, device=device)
+    nnz = ctypes.c_int64(0)
+    N.check(L.qs_observable_csr_rows(obs.handle, int(nqubits), ctypes.c_void_p(rowptr.data_ptr()),
+                                     ctypes.c_void_p(scratch.data_ptr()), ctypes.byref(nnz), _stream_ptr()))
+    cols = torch.empty(max(1, nnz.value), dtype=torch.int64, device=device)
+    vals = torch.empty(max(1, nnz.value), dtype=torch.complex128, device=device)
+    N.check(L.qs_observable_csr_fill(obs.handle, int(nqubits), ctypes.c_void_p(rowptr.data_ptr()),
+                                     ctypes.c_void_p(cols.data_ptr()), ctypes.c_void_p(vals.data_ptr()), _stream_ptr()))
+    return rowptr, cols[:nnz.value], vals[:nnz.value]
