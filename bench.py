@@ -648,6 +648,8 @@ def main():
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-tc", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--no-matrix", action="store_true")
     ap.add_argument("--leg", default="all", choices=["all", "tc", "batch", "diff", "large", "tiles", "small", "matrix"],
                     help="run one secondary leg alone and print its JSON (profiling captures)")
     ap.add_argument("--tc-reps", type=int, default=20, help="timed launches per tensor-core configuration")
@@ -726,7 +728,7 @@ def main():
     # dominant kernel: largest share of device time
     pc = c64["per_class"]
     dom = max(pc, key=lambda c: pc[c]["seconds"])
-    kname = {"dense1": "k_gate1<float, 4, *> (OP_DENSE1: H, Rx)", "swap1": "k_gate1<float, 2, *> (OP_SWAP1: X, CNOT, Toffoli)",
+    kname = {"dense1": "k_gate1<float, 5|6, *> (OP_REAL1: H; OP_RXLIKE1: Rx)", "swap1": "k_gate1<float, 2, *> (OP_SWAP1: X, CNOT, Toffoli)",
              "diag1": "k_diag1<float> (T: touched half only)"}[dom]
     achieved = pc[dom]["gbs"]
     roof = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
@@ -750,8 +752,9 @@ def main():
                                          world=world, rank=rank)
     if not args.no_tc and solo:
         extra["tensor_core_blocks"] = run_tc_leg(args.tc_reps)
-    if solo:
+    if solo and not args.no_small:
         extra["small"] = run_small_leg()
+    if solo and not args.no_matrix:
         extra["matrix"] = run_matrix_leg()
     if not args.no_large and solo:
         extra["differentiation"] = run_diff_leg(1, 1)

@@ -178,6 +178,8 @@ enum OpClass {
   OP_SWAP1,     // a <-> b (pure X)
   OP_PERM1,     // a' = u01 b, b' = u10 a
   OP_DENSE1,    // [a'; b'] = U [a; b]
+  OP_REAL1,     // OP_DENSE1 with a real U (H, Ry): half the multiply-adds
+  OP_RXLIKE1,   // OP_DENSE1 with real diagonal, imaginary off-diagonal (Rx): half the multiply-adds
   OP_DIAGK,     // amplitude *= d[m], m = gathered target bits
   OP_PERMK,     // y[m] = v[m] x[perm[m]]
   OP_DENSEK     // y = U x over 2^k tuples

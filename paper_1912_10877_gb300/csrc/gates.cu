@@ -89,6 +89,20 @@ __device__ __forceinline__ void pair_op(c2_t<R>& a, c2_t<R>& b, const U4<R>& u) 
     T na = cmul(u.m[1], b);
     T nb = cmul(u.m[2], a);
     a = na; b = nb;
+  } else if constexpr (OP == OP_REAL1) {  // u real: 2 operations per component
+    T na, nb;
+    na.x = fma(u.m[1].x, b.x, u.m[0].x * a.x);
+    na.y = fma(u.m[1].x, b.y, u.m[0].x * a.y);
+    nb.x = fma(u.m[3].x, b.x, u.m[2].x * a.x);
+    nb.y = fma(u.m[3].x, b.y, u.m[2].x * a.y);
+    a = na; b = nb;
+  } else if constexpr (OP == OP_RXLIKE1) {  // u0, u3 real; u1, u2 imaginary
+    T na, nb;
+    na.x = fma(-u.m[1].y, b.y, u.m[0].x * a.x);
+    na.y = fma(u.m[1].y, b.x, u.m[0].x * a.y);
+    nb.x = fma(u.m[3].x, b.x, -u.m[2].y * a.y);
+    nb.y = fma(u.m[3].x, b.y, u.m[2].y * a.x);
+    a = na; b = nb;
   } else {
     T na = cfma(u.m[1], b, cmul(u.m[0], a));
     T nb = cfma(u.m[3], b, cmul(u.m[2], a));
@@ -271,6 +285,8 @@ static int launch_typed(c2_t<R>* psi, int n, int nreg, const Plan& p, cudaStream
     case OP_SWAP1: return launch_1<R, OP_SWAP1>(psi, n, nreg, p, st);
     case OP_PERM1: return launch_1<R, OP_PERM1>(psi, n, nreg, p, st);
     case OP_DENSE1: return launch_1<R, OP_DENSE1>(psi, n, nreg, p, st);
+    case OP_REAL1: return launch_1<R, OP_REAL1>(psi, n, nreg, p, st);
+    case OP_RXLIKE1: return launch_1<R, OP_RXLIKE1>(psi, n, nreg, p, st);
     case OP_DIAGK: return launch_k_op<R, OP_DIAGK>(psi, n, nreg, p, st);
     case OP_PERMK: return launch_k_op<R, OP_PERMK>(psi, n, nreg, p, st);
     case OP_DENSEK: return launch_k_op<R, OP_DENSEK>(psi, n, nreg, p, st);
@@ -370,8 +386,15 @@ int plan_gate(const cd* U, int k, const int* locs, uint64_t ctrl_mask, uint64_t 
   if (k == 1) {
     P.t = locs[0];
     for (int i = 0; i < 4; ++i) P.u[i] = U[i];
-    if (perm) P.op = (U[1] == cd(1, 0) && U[2] == cd(1, 0)) ? OP_SWAP1 : OP_PERM1;
-    else P.op = OP_DENSE1;
+    if (perm) {
+      P.op = (U[1] == cd(1, 0) && U[2] == cd(1, 0)) ? OP_SWAP1 : OP_PERM1;
+    } else if (U[0].imag() == 0 && U[1].imag() == 0 && U[2].imag() == 0 && U[3].imag() == 0) {
+      P.op = OP_REAL1;
+    } else if (U[0].imag() == 0 && U[3].imag() == 0 && U[1].real() == 0 && U[2].real() == 0) {
+      P.op = OP_RXLIKE1;
+    } else {
+      P.op = OP_DENSE1;
+    }
     return QS_OK;
   }
   P.op = perm ? OP_PERMK : OP_DENSEK;
