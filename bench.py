@@ -294,7 +294,18 @@ def run_batch_leg(steps: int, warmup: int, compare: bool = True, world: int = 1,
     t = D.max_over_ranks(e0.elapsed_time(e1) / 1e3 / steps)
     losses = D.gather_per_register(loss.cpu().numpy(), mine, BATCH_NREG)
     assert np.all(np.isfinite(losses)), "a register's loss is missing"
+    # ALU roofline: algorithmic FP32 flops of the method per batch (complex multiply-add = 8
+    # flops).  Forward per layer and qubit: the fused Rz Rx Rz dense 2x2, 16 flops per amplitude.
+    # Backward per layer and qubit: each rotation uncomputes psi and lambda (Rz diagonal 2 x 6,
+    # Rx dense 2 x 16) and adds Im<lambda|G|psi> (8): Rz 20 + Rx 40 + Rz 20 = 80 per amplitude.
+    # CNOTs move amplitudes (0 flops); lambda = O psi and <O> are lower order.
+    flops = sum(float(BATCH_DEPTH * int(n) * (16 + 80)) * (1 << int(n)) for n in counts_all)
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # TFLOP/s: SMs x FP32 FMA/clk x 2 x max SM clock
     res = {"metric": "batched fwd+grad circuits/s", "value": round(BATCH_NREG / t, 1), "unit": "circuits/s",
+           "roofline": {"bound": "alu", "achieved": round(flops / t / 1e12, 2), "peak": round(fp32_peak, 1),
+                        "unit": "TFLOP/s", "frac": round(flops / t / 1e12 / fp32_peak, 4),
+                        "peak_kind": "derived: 152 SMs x 128 FP32 FMA/clk x 2 flops x 2.07 GHz",
+                        "flops_per_batch": flops},
            "ms_per_batch": round(1e3 * t, 3), "dtype": "c64 (f32 gates and uncompute; f64 reductions above warp level)",
            "config": {"workload": f"{BATCH_NREG} registers, n ~ U{{{BATCH_LO}..{BATCH_HI}}} seed 0, Rz.Rx.Rz + "
                                   f"CNOT ladder x {BATCH_DEPTH} layers, <sum Z_i Z_i+1> (open)",

@@ -313,7 +313,7 @@ __device__ __forceinline__ void diag_masked(float2 (&x)[16], float2 f, int cm, i
 
 __device__ __noinline__ void run_phase_fwd(float2* sm, const TPhase* php, const TOp* fops, const float2* dtab, int m,
                                            uint32_t tbase) {
-  const TPhase ph = *php;
+  const TPhase& ph = *php;
   const int ntb = m - kRB;
   if (threadIdx.x < (1u << ntb)) {
     const uint32_t sb = swz(phase_base(threadIdx.x, ph, ntb));
@@ -380,27 +380,26 @@ __device__ __forceinline__ float diagout_bwd(float2 (&x)[16], float2 (&l)[16], c
 
 __device__ __noinline__ void run_phase_bwd(float2* sx, float2* sl, const TPhase* php, const TOp* bops, int m,
                                            float* red, double* gacc, uint32_t tbase) {
-  const TPhase ph = *php;
+  // the phase record stays in memory (L1): with 32 live amplitudes per thread
+  // there are no registers to spare for a copy of it or for 16 slot offsets
+  const TPhase& ph = *php;
   const int ntb = m - kRB;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool active = threadIdx.x < (1u << ntb);
+  const int nbop = ph.nbop, bop0 = ph.bop0;
   float2 x[16], l[16];
-  uint32_t off[16];
   const uint32_t gb = active ? thread_global(threadIdx.x, ph, ntb, tbase) : 0u;
-  {
-    const uint32_t sb = active ? swz(phase_base(threadIdx.x, ph, ntb)) : 0u;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) off[j] = sb ^ ph.sroff[j];
-  }
+  const uint32_t sb = active ? swz(phase_base(threadIdx.x, ph, ntb)) : 0u;
   if (active) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-      x[j] = sx[off[j]];
-      l[j] = sl[off[j]];
+      const uint32_t o = sb ^ ph.sroff[j];
+      x[j] = sx[o];
+      l[j] = sl[o];
     }
   }
-  for (int o = ph.nbop - 1; o >= 0; --o) {
-    const TOp& op = bops[ph.bop0 + o];
+  for (int o = nbop - 1; o >= 0; --o) {
+    const TOp& op = bops[bop0 + o];
     float part = 0.f;
     if (active && (gb & op.tmask) == op.tval)
       part = op.kind == TK_DIAGOUT ? diagout_bwd(x, l, op, gb) : apply_bwd(x, l, op);
@@ -412,8 +411,9 @@ __device__ __noinline__ void run_phase_bwd(float2* sx, float2* sl, const TPhase*
   if (active) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-      sx[off[j]] = x[j];
-      sl[off[j]] = l[j];
+      const uint32_t o = sb ^ ph.sroff[j];
+      sx[o] = x[j];
+      sl[o] = l[j];
     }
   }
   __syncthreads();
@@ -421,8 +421,8 @@ __device__ __noinline__ void run_phase_bwd(float2* sx, float2* sl, const TPhase*
   // parameter is unique in the phase in parallel, the others by one thread
   const int nw = (int)(blockDim.x / 32);
   const int o = threadIdx.x;
-  if (o < ph.nbop) {
-    const TOp& op = bops[ph.bop0 + o];
+  if (o < nbop) {
+    const TOp& op = bops[bop0 + o];
     if (op.gen != GEN_NONE && !op.shared) {
       double v = 0.0;
       for (int w = 0; w < nw; ++w) v += (double)red[o * kWarps + w];
@@ -431,8 +431,8 @@ __device__ __noinline__ void run_phase_bwd(float2* sx, float2* sl, const TPhase*
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int q = 0; q < ph.nbop; ++q) {
-      const TOp& op = bops[ph.bop0 + q];
+    for (int q = 0; q < nbop; ++q) {
+      const TOp& op = bops[bop0 + q];
       if (op.gen == GEN_NONE || !op.shared) continue;
       double v = 0.0;
       for (int w = 0; w < nw; ++w) v += (double)red[q * kWarps + w];
@@ -470,6 +470,55 @@ __device__ void block_loss(double e, BShared& S, double* out) {
   }
 }
 
+// The per-register phase loops of k_batch live in their own (not inlined)
+// functions: a phase call then sees only the loop's few live values, and the
+// phase functions keep their 32 amplitudes per thread in registers.
+__device__ __noinline__ void batch_bwd_resident(float2* sx, float2* sl, const TPass* P, int npass, int m,
+                                                const TPhase* phases, const TOp* bops, float* red, double* gacc) {
+  for (int pi = npass - 1; pi >= 0; --pi) {
+    const int ph0 = P[pi].phase0;
+    for (int f = P[pi].nphase - 1; f >= 0; --f) run_phase_bwd(sx, sl, phases + ph0 + f, bops, m, red, gacc, 0u);
+  }
+}
+
+__device__ __noinline__ void batch_bwd_streamed(float2* sx, float2* sl, const TPass* P, int npass, int m, int g,
+                                                float2* wp, float2* wl, const TPhase* phases, const TOp* bops,
+                                                uint32_t* rowoff, float* red, double* gacc) {
+  const uint64_t ntile = 1ull << g;
+  for (int pi = npass - 1; pi >= 0; --pi) {
+    const TPass& p = P[pi];
+    set_rows(rowoff, p, m);
+    for (uint64_t t = 0; t < ntile; ++t) {
+      const uint64_t tb = tile_base(t, p, g);
+      load_tiles<true>(sx, wp + tb, sl, wl + tb, rowoff, m);
+      __syncthreads();
+      const int ph0 = p.phase0;
+      for (int f = p.nphase - 1; f >= 0; --f) run_phase_bwd(sx, sl, phases + ph0 + f, bops, m, red, gacc, (uint32_t)tb);
+      store_tiles<true>(sx, wp + tb, sl, wl + tb, rowoff, m);
+      __syncthreads();
+    }
+  }
+}
+
+__device__ __noinline__ void batch_fwd_streamed(float2* sx, float2* st, const TPass* P, int npass, int m, int g,
+                                                const TPhase* phases, const TOp* fops, const float2* dtab,
+                                                uint32_t* rowoff) {
+  const uint64_t ntile = 1ull << g;
+  for (int pi = 0; pi < npass; ++pi) {
+    const TPass& p = P[pi];
+    set_rows(rowoff, p, m);
+    for (uint64_t t = 0; t < ntile; ++t) {
+      const uint64_t tb = tile_base(t, p, g);
+      load_tile(sx, st + tb, rowoff, m);
+      __syncthreads();
+      const int ph0 = p.phase0;
+      for (int f = 0; f < p.nphase; ++f) run_phase_fwd(sx, phases + ph0 + f, fops, dtab, m, (uint32_t)tb);
+      store_tile(sx, st + tb, rowoff, m);
+      __syncthreads();
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kTileThreads, 1) k_batch(BArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   BShared& S = *reinterpret_cast<BShared*>(smraw);
@@ -504,29 +553,14 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(BArgs a) {
       store_tile(sx, st, S.rowoff, m);  // psi_N
       block_loss(expect_tile(sx, sl, 0, S.rowoff, m, a.terms + R.term0, R.nterm), S, a.loss + reg);
       __syncthreads();
-      if (grad) {
-        for (int pi = R.npass - 1; pi >= 0; --pi)
-          for (int f = P[pi].nphase - 1; f >= 0; --f)
-            run_phase_bwd(sx, sl, a.phases + P[pi].phase0 + f, a.bops, m, S.red, S.grad, 0u);
-      }
+      if (grad) batch_bwd_resident(sx, sl, P, R.npass, m, a.phases, a.bops, S.red, S.grad);
     } else {
       // ---- tiles streamed through global memory
       if (a.flags & BF_RESET) {
         for (uint64_t i = tid; i < (1ull << n); i += blockDim.x) st[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
         __syncthreads();
       }
-      for (int pi = 0; pi < R.npass; ++pi) {
-        const TPass& p = P[pi];
-        set_rows(S.rowoff, p, m);
-        for (uint64_t t = 0; t < ntile; ++t) {
-          const uint64_t tb = tile_base(t, p, g);
-          load_tile(sx, st + tb, S.rowoff, m);
-          __syncthreads();
-          for (int f = 0; f < p.nphase; ++f) run_phase_fwd(sx, a.phases + p.phase0 + f, a.fops, a.dtab, m, (uint32_t)tb);
-          store_tile(sx, st + tb, S.rowoff, m);
-          __syncthreads();
-        }
-      }
+      batch_fwd_streamed(sx, st, P, R.npass, m, g, a.phases, a.fops, a.dtab, S.rowoff);
       // expectation, lambda = O psi, and the work copy of psi for the uncompute
       double e = 0.0;
       float2* wp = a.wpsi + R.work_off;
@@ -544,21 +578,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(BArgs a) {
       }
       block_loss(e, S, a.loss + reg);
       __syncthreads();
-      if (grad) {
-        for (int pi = R.npass - 1; pi >= 0; --pi) {
-          const TPass& p = P[pi];
-          set_rows(S.rowoff, p, m);
-          for (uint64_t t = 0; t < ntile; ++t) {
-            const uint64_t tb = tile_base(t, p, g);
-            load_tiles<true>(sx, wp + tb, sl, wl + tb, S.rowoff, m);
-            __syncthreads();
-            for (int f = p.nphase - 1; f >= 0; --f)
-              run_phase_bwd(sx, sl, a.phases + p.phase0 + f, a.bops, m, S.red, S.grad, (uint32_t)tb);
-            store_tiles<true>(sx, wp + tb, sl, wl + tb, S.rowoff, m);
-            __syncthreads();
-          }
-        }
-      }
+      if (grad) batch_bwd_streamed(sx, sl, P, R.npass, m, g, wp, wl, a.phases, a.bops, S.rowoff, S.red, S.grad);
     }
     __syncthreads();
     if (grad)
