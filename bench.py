@@ -294,12 +294,13 @@ def run_batch_leg(steps: int, warmup: int, compare: bool = True, world: int = 1,
     t = D.max_over_ranks(e0.elapsed_time(e1) / 1e3 / steps)
     losses = D.gather_per_register(loss.cpu().numpy(), mine, BATCH_NREG)
     assert np.all(np.isfinite(losses)), "a register's loss is missing"
-    # ALU roofline: algorithmic FP32 flops of the method per batch (complex multiply-add = 8
-    # flops).  Forward per layer and qubit: the fused Rz Rx Rz dense 2x2, 16 flops per amplitude.
-    # Backward per layer and qubit: each rotation uncomputes psi and lambda (Rz diagonal 2 x 6,
-    # Rx dense 2 x 16) and adds Im<lambda|G|psi> (8): Rz 20 + Rx 40 + Rz 20 = 80 per amplitude.
-    # CNOTs move amplitudes (0 flops); lambda = O psi and <O> are lower order.
-    flops = sum(float(BATCH_DEPTH * int(n) * (16 + 80)) * (1 << int(n)) for n in counts_all)
+    # ALU roofline: the method's minimal FP32 flops per batch.  Forward per layer and qubit:
+    # the fused Rz Rx Rz, one complex 2x2 = 2 complex multiply-adds = 16 flops per amplitude.
+    # Backward per layer and qubit, rotation by rotation: uncompute psi and lambda (Rz diagonal
+    # and Rx real-diagonal / imaginary off-diagonal: 6 flops per amplitude each, x 2 states)
+    # plus Im<lambda|G|psi> (4 per amplitude): 3 x 16 = 48.  CNOTs move amplitudes (0 flops);
+    # lambda = O psi and <O> are lower order.  Total 64 flops per amplitude, layer and qubit.
+    flops = sum(float(BATCH_DEPTH * int(n) * 64) * (1 << int(n)) for n in counts_all)
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # TFLOP/s: SMs x FP32 FMA/clk x 2 x max SM clock
     res = {"metric": "batched fwd+grad circuits/s", "value": round(BATCH_NREG / t, 1), "unit": "circuits/s",
            "roofline": {"bound": "alu", "achieved": round(flops / t / 1e12, 2), "peak": round(fp32_peak, 1),
