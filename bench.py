@@ -277,9 +277,11 @@ def run_batch_leg(steps: int, warmup: int, compare: bool = True, world: int = 1,
     specs = [specs_all[r] for r in mine]
     circs = [qsim.Circuit(g, int(n)) for n, (g, _) in zip(counts, specs)]
     obs = [qsim.Observable(W.zz_chain(int(n))) for n in counts]
-    prog = qsim.BatchProgram(circs, obs)
     st = qsim.State([int(n) for n in counts], dtype=torch.complex64)
     params = torch.tensor(np.concatenate([p for _, p in specs]), dtype=torch.float64, device="cuda")
+    # tile shape chosen by the autotuner (untimed), then the program is built with it
+    tile, tile_ms = qsim.batch_autotune(circs, obs, st, params, grad=True, reps=1)
+    prog = qsim.BatchProgram(circs, obs, tile_qubits=tile)
     loss = torch.empty(len(mine), dtype=torch.float64, device="cuda")
     grad = torch.empty(prog.nparams, dtype=torch.float64, device="cuda")
     for _ in range(warmup):
@@ -311,7 +313,8 @@ def run_batch_leg(steps: int, warmup: int, compare: bool = True, world: int = 1,
            "config": {"workload": f"{BATCH_NREG} registers, n ~ U{{{BATCH_LO}..{BATCH_HI}}} seed 0, Rz.Rx.Rz + "
                                   f"CNOT ladder x {BATCH_DEPTH} layers, <sum Z_i Z_i+1> (open)",
                       "total_amplitudes": int(sum(1 << int(n) for n in counts_all)), "launches_per_batch": 2,
-                      "ranks": world, "split": "registers by cost 2^n (LPT), losses gathered"}}
+                      "ranks": world, "split": "registers by cost 2^n (LPT), losses gathered",
+                      "tile_qubits": tile, "autotune_ms": {str(k): round(v, 2) for k, v in tile_ms.items()}}}
     if compare and world == 1:
         # gate-by-gate complex128: one launch per gate per register, FP64 adjoint per gate
         rs = np.random.default_rng(0)

@@ -417,6 +417,19 @@ int qs_batch_program_info(const qs_batch_program* p, int* nreg, int64_t* nparams
 int qs_batch_run(qs_state* s, const qs_batch_program* p, const double* dev_params, double* dev_loss,
                  double* dev_grad, int flags);
 
+/* Autotuner of the batched engine's tile shape: builds the program for every
+ * tile size from 13 down to 11 qubits (tile_qubits of qs_batch_program_create;
+ * registers larger than the tile stream tiles of that size, smaller ones stay
+ * resident), runs it on s with dev_params once as warm-up and reps times
+ * timed with CUDA events (forward + gradient when dev_grad is not NULL), and
+ * returns the fastest in *best_tile (pass it to qs_batch_program_create).
+ * If ncand is not NULL it holds the capacity of host_tiles / host_ms on entry
+ * and the candidate count on return (ms = -1: the size does not fit).  s's
+ * amplitudes and dev_loss / dev_grad are overwritten.  Synchronises. */
+int qs_batch_autotune(int nreg, const qs_circuit* const* circuits, const qs_observable* const* observables,
+                      qs_state* s, const double* dev_params, double* dev_loss, double* dev_grad, int reps,
+                      int* best_tile, int* ncand, int32_t* host_tiles, double* host_ms);
+
 /* Device bytes of the work buffer of qs_backward_tiled (two complex64
  * copies: psi and lambda). */
 int qs_backward_tiled_work_bytes(int nqubits, size_t* out_bytes);

@@ -99,6 +99,7 @@ SIGNATURES = {
     "qs_batch_program_destroy": ([_P], _I),
     "qs_batch_program_info": ([_P, ctypes.POINTER(_I), _PI64, _PI64, _PI64], _I),
     "qs_batch_run": ([_P, _P, _P, _P, _P, _I], _I),
+    "qs_batch_autotune": ([_I, _PP, _PP, _P, _P, _P, _P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), _PI32, _PD], _I),
 }
 
 _lib = None

@@ -1384,6 +1384,53 @@ using namespace qs;
 
 extern "C" {
 
+int qs_batch_autotune(int nreg, const qs_circuit* const* circuits, const qs_observable* const* observables,
+                      qs_state* s, const double* dev_params, double* dev_loss, double* dev_grad, int reps,
+                      int* best_tile, int* ncand, int32_t* host_tiles, double* host_ms) {
+  if (!circuits || !observables || !s || !dev_params || !dev_loss || !best_tile) return fail(QS_EINVAL, "null argument");
+  if (reps < 1) reps = 1;
+  const int flags = QS_BATCH_RESET | (dev_grad ? QS_BATCH_GRAD : 0);
+  int best = -1, nc = 0;
+  double best_ms = 0;
+  cudaEvent_t e0, e1;
+  QS_CUDA(cudaEventCreate(&e0));
+  QS_CUDA(cudaEventCreate(&e1));
+  int rc = QS_OK;
+  for (int m = kBatchTile; m >= kRowBits + kRB + 2 && rc == QS_OK; --m) {
+    qs_batch_program* P = nullptr;
+    double ms = -1;
+    const int crc = qs_batch_program_create(nreg, circuits, observables, m, &P);
+    if (crc == QS_OK) {
+      rc = qs_batch_run(s, P, dev_params, dev_loss, dev_grad, flags);  // warm-up
+      if (rc == QS_OK && cudaEventRecord(e0, s->stream) != cudaSuccess) rc = fail(QS_EDEVICE, "event record");
+      for (int r = 0; r < reps && rc == QS_OK; ++r) rc = qs_batch_run(s, P, dev_params, dev_loss, dev_grad, flags);
+      if (rc == QS_OK && cudaEventRecord(e1, s->stream) != cudaSuccess) rc = fail(QS_EDEVICE, "event record");
+      if (rc == QS_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = fail(QS_EDEVICE, "event sync");
+      float t = 0;
+      if (rc == QS_OK && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms = (double)t / reps;
+      qs_batch_program_destroy(P);
+    } else if (crc != QS_EUNSUPPORTED && crc != QS_EINVAL) {
+      rc = crc;
+    }
+    if (ncand && nc < *ncand) {
+      if (host_tiles) host_tiles[nc] = m;
+      if (host_ms) host_ms[nc] = ms;
+    }
+    ++nc;
+    if (ms >= 0 && (best < 0 || ms < best_ms)) {
+      best = m;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != QS_OK) return rc;
+  if (ncand) *ncand = nc;
+  if (best < 0) return fail(QS_EUNSUPPORTED, "no tile size ran the batch");
+  *best_tile = best;
+  return QS_OK;
+}
+
 int qs_batch_program_create(int nreg, const qs_circuit* const* circuits, const qs_observable* const* observables,
                             int tile_qubits, qs_batch_program** out) {
   if (!out || nreg < 1 || !circuits || !observables) return fail(QS_EINVAL, "bad arguments");

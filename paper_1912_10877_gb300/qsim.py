@@ -549,3 +549,25 @@ def observable_csr(obs: Observable, nqubits: int, device="cuda"):
     N.check(L.qs_observable_csr_fill(obs.handle, int(nqubits), ctypes.c_void_p(rowptr.data_ptr()),
                                      ctypes.c_void_p(cols.data_ptr()), ctypes.c_void_p(vals.data_ptr()), _stream_ptr()))
     return rowptr, cols[:nnz.value], vals[:nnz.value]
+
+
+def batch_autotune(circuits, observables, state: State, params: torch.Tensor, grad: bool = True, reps: int = 2):
+    """Tile size (qubits) at which the batched program runs fastest on this state, and
+    {tile: ms}.  The state's amplitudes are overwritten."""
+    L = N.lib()
+    nreg = len(circuits)
+    ch = (ctypes.c_void_p * nreg)(*[c.handle.value for c in circuits])
+    oh = (ctypes.c_void_p * nreg)(*[o.handle.value for o in observables])
+    loss = torch.empty(nreg, dtype=torch.float64, device=params.device)
+    g = torch.empty_like(params) if grad else None
+    best = ctypes.c_int(0)
+    cap = 8
+    nc = ctypes.c_int(cap)
+    tiles = np.zeros(cap, np.int32)
+    ms = np.zeros(cap)
+    N.check(L.qs_batch_autotune(nreg, ctypes.cast(ch, ctypes.POINTER(ctypes.c_void_p)),
+                                ctypes.cast(oh, ctypes.POINTER(ctypes.c_void_p)), state.handle,
+                                ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(loss.data_ptr()),
+                                ctypes.c_void_p(g.data_ptr()) if g is not None else None, int(reps),
+                                ctypes.byref(best), ctypes.byref(nc), tiles.ctypes.data_as(N._PI32), N.dptr(ms)))
+    return best.value, {int(tiles[i]): float(ms[i]) for i in range(min(nc.value, cap))}

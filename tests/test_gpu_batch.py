@@ -105,3 +105,18 @@ def test_batch_forward_only_and_rejects(qs):
         qs.BatchProgram([qs.Circuit(gates, n)], [qs.Observable([(1.0, ((0, "X"),))])])
     with pytest.raises(QsimError):  # two-target gate
         qs.BatchProgram([qs.Circuit([W.Gate("SWAP", (0, 1))], n)], [qs.Observable(W.zz_chain(n))])
+
+
+def test_batch_autotune_picks_a_tile_that_is_correct(qs):
+    specs = []
+    for r, n in enumerate([12, 14, 9, 13, 11]):
+        gates, params = W.variational(n, 2, "ladder", seed=50 + r)
+        specs.append((n, gates, params, W.zz_chain(n)))
+    circs = [qs.Circuit(g, n, nparams=len(p)) for n, g, p, _ in specs]
+    obs = [qs.Observable(t) for *_, t in specs]
+    st = qs.State([s[0] for s in specs], dtype=torch.complex64)
+    p = torch.tensor(np.concatenate([s[2] for s in specs]), dtype=torch.float64, device="cuda")
+    best, times = qs.batch_autotune(circs, obs, st, p, grad=True, reps=1)
+    assert set(times) == {13, 12, 11} and best in times and times[best] > 0
+    assert times[best] == min(v for v in times.values() if v > 0)
+    run_case(qs, specs, tile=best)
