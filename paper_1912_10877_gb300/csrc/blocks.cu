@@ -493,6 +493,7 @@ int backward_blocks(qs_state* s, const qs_circuit* c, const double* params, cons
   const int nb = (int)blocks.size();
   // which blocks need rho, and where it goes in device scratch
   std::vector<int64_t> rho_off(nb, -1);
+  std::vector<char> rho_tc(nb, 0);  // rho of this block came from the tensor cores (interleaved layout)
   int64_t rho_total = 0;
   for (int bi = 0; bi < nb; ++bi) {
     const Block& b = blocks[bi];
@@ -526,9 +527,19 @@ int backward_blocks(qs_state* s, const qs_circuit* c, const double* params, cons
     for (int q = 0; q < 64; ++q)
       if ((b.support >> q) & 1ull) qubits.push_back(q);
     const int w = (int)qubits.size();
-    if (rho_off[bi] >= 0)
-      QS_TRY(f32 ? gram<float>(w, s->data, lam, n, qubits, partials, rhos + rho_off[bi], st)
-                 : gram<double>(w, s->data, lam, n, qubits, partials, rhos + rho_off[bi], st));
+    if (rho_off[bi] >= 0) {
+      if (f32 && (w == 4 || w == 5) && tensor_cores_enabled()) {
+        int grid = 0;
+        QS_TRY(gram_tc(w, (const float2*)s->data, (const float2*)lam, n, qubits.data(), partials, &grid, st));
+        const int E = 4 << (2 * w);
+        k_gram_fold<<<E, 256, 0, st>>>(partials, grid, E, rhos + rho_off[bi]);
+        QS_LAUNCHED();
+        rho_tc[bi] = 1;
+      } else {
+        QS_TRY(f32 ? gram<float>(w, s->data, lam, n, qubits, partials, rhos + rho_off[bi], st)
+                   : gram<double>(w, s->data, lam, n, qubits, partials, rhos + rho_off[bi], st));
+      }
+    }
     Plan p;
     if (b.gates.size() == 1) {
       const qs_gate_desc& g = c->gates[b.gates[0]];
@@ -561,12 +572,16 @@ int backward_blocks(qs_state* s, const qs_circuit* c, const double* params, cons
     int pos[64];
     for (int j = 0; j < w; ++j) pos[qubits[j]] = j;
     const double* g2 = G2.data() + rho_off[bi];
-    // rho[p][q] = sum_x psi_x[p] conj(lambda_x[q]), from the real Gram matrix
+    // rho[p][q] = sum_x psi_x[p] conj(lambda_x[q]), from the real Gram matrix: G[re p][re q]
+    // + G[im p][im q] + i (G[im p][re q] - G[re p][im q]); rows / columns are [re | im]
+    // halves (CUDA-core kernel) or interleaved re, im (tensor-core kernel)
+    auto re = [&](int p) { return rho_tc[bi] ? 2 * p : p; };
+    auto im = [&](int p) { return rho_tc[bi] ? 2 * p + 1 : D + p; };
     rho.assign((size_t)D * D, cd(0));
     for (int p = 0; p < D; ++p)
       for (int q = 0; q < D; ++q)
-        rho[(size_t)p * D + q] = cd(g2[(size_t)p * W2 + q] + g2[(size_t)(D + p) * W2 + D + q],
-                                    g2[(size_t)(D + p) * W2 + q] - g2[(size_t)p * W2 + D + q]);
+        rho[(size_t)p * D + q] = cd(g2[(size_t)re(p) * W2 + re(q)] + g2[(size_t)im(p) * W2 + im(q)],
+                                    g2[(size_t)im(p) * W2 + re(q)] - g2[(size_t)re(p) * W2 + im(q)]);
     // from the last gate back: rho <- E^dag rho E with E the block's later gates, so that
     // Tr(E H E^dag rho) = Tr(H rho)
     for (int gj = (int)b.gates.size() - 1; gj >= 0; --gj) {

@@ -223,6 +223,10 @@ int tensor_cores_enabled();
 bool use_block_tc(int dtype, const Plan& p);
 int launch_block_tc(float2* psi, int n, int nreg, const Plan& p, cudaStream_t st);
 int tc_status_take();  // QS_ETIMEDOUT (and clears it) if a tensor-core wait gave up
+// real Gram matrix sum_x psi_x^T lambda_x of a 4/5-qubit support on the tensor cores
+// (interleaved re/im layout), per-CTA partials [grid][W][W]
+int gram_tc(int w, const float2* psi, const float2* lam, int n, const int* qubits, double* partials, int* grid_out,
+            cudaStream_t st);
 
 // the circuit fused into blocks of at most kmax qubits, gate-by-gate path (blocks.cu)
 int apply_blocks(qs_state* s, const qs_circuit* c, const double* params, int kmax);

@@ -562,6 +562,306 @@ static int launch_tc_t(float2* psi, int n, int nreg, const Plan& p, cudaStream_t
   return launch_tc_mode<K, TC_SCALAR>(a, st);
 }
 
+// ------------------------------------------------------------------ Gram matrix on the tensor cores
+//
+// G = sum over the tuples x of a k-qubit support (k = 4, 5) of psi_x^T lambda_x
+// in the interleaved real form (row / column 2m = Re, 2m + 1 = Im of member m),
+// the one pass of the block backward that forms rho = sum_x psi_x lambda_x^dag.
+// A 128-tuple tile is staged transposed: rows are components (psi in rows
+// 0..63, lambda in rows 64..127, 4-qubit supports zero-padded), columns are the
+// tuples, in the K-major 128-byte-swizzle layout (kind::tf32 takes K-major
+// operands only).  One tcgen05.mma (M = 128, N = 64, K = 8 tuples) takes
+// A = rows 0..127 and B = rows 64..127; rows 0..63 of the accumulator are
+// psi^T lambda.  3xTF32 as in k_block_tc; FP32
+// accumulation in TMEM over groups of 8 tiles, flushed by the epilogue warps
+// into an FP64 matrix in shared memory, written per CTA for a fixed-order fold.
+
+constexpr int kGramGroup = 8;  // tiles per FP32 accumulation group
+
+template <int K>
+struct GramTcSmem {
+  static constexpr uint32_t T_BYTES = kTcRows * 128 * 4;   // 128 x 128 fp32: 64 KB
+  static constexpr uint32_t HI = 0, LO = T_BYTES;
+  static constexpr uint32_t ROWOFF = 2 * T_BYTES;
+  static constexpr uint32_t DTAB = ROWOFF + kTcRows * 8;
+  static constexpr uint32_t OFFS = DTAB + 4 * 256 * 8;
+  static constexpr uint32_t ACC = OFFS + 64 * 4;            // FP64 [64][65]
+  static constexpr int ACC_LD = 65;
+  static constexpr uint32_t MBAR = ACC + 64 * ACC_LD * 8;   // full, empty, tfull[2], tempty[2], fin
+  static constexpr uint32_t FLAGS = MBAR + 7 * 8;
+  static constexpr uint32_t BYTES = FLAGS + 16 + 1024;
+};
+
+template <int K, int MODE>
+__global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const __grid_constant__ TcArgs<K> a, const float2* lam,
+                                                           double* partials) {
+  using L = GramTcSmem<K>;
+  constexpr int D = 1 << K, W = 2 * D;   // components per state
+  constexpr int NU = MODE == TC_SCALAR ? kTcRows * D : kTcRows * D / 2;
+  constexpr int UT = NU / kTcLoaders;
+  static_assert(UT * kTcLoaders == NU && UT <= 8, "tile splits evenly over the loaders");
+  using VT = typename std::conditional<MODE == TC_SCALAR, float2, float4>::type;
+  extern __shared__ unsigned char sm_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)sm_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* s_P = reinterpret_cast<uint64_t*>(sm + L::ROWOFF);
+  uint64_t* s_dtab = reinterpret_cast<uint64_t*>(sm + L::DTAB);
+  uint32_t* s_off = reinterpret_cast<uint32_t*>(sm + L::OFFS);
+  double* acc = reinterpret_cast<double*>(sm + L::ACC);
+  const uint32_t mb0 = smem_u32(sm + L::MBAR);
+  const uint32_t full = mb0, empty = mb0 + 8u, fin = mb0 + 48u;
+  auto tfull = [&](int b) { return mb0 + 16u + 8u * (uint32_t)b; };
+  auto tempty = [&](int b) { return mb0 + 32u + 8u * (uint32_t)b; };
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::FLAGS);
+  volatile int* abort = reinterpret_cast<volatile int*>(sm + L::FLAGS + 4);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // ---- setup: zeroed tiles (4-qubit supports leave columns unused), FP64
+  // accumulator, offsets, tables, barriers, TMEM
+  for (uint32_t e = tid; e < 2 * L::T_BYTES / 16; e += kTcThreads)
+    reinterpret_cast<float4*>(sm + L::HI)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int e = tid; e < 64 * L::ACC_LD; e += kTcThreads) acc[e] = 0.0;
+  if (tid < D) s_off[tid] = a.off[tid];
+  if (tid < kTcRows) s_P[tid] = row_offset(tid, a);
+  for (int e = tid; e < 4 * 256; e += kTcThreads) {
+    const int c = e >> 8, sh = 7 + 8 * c;
+    const uint64_t v = (uint64_t)(e & 255) << sh;
+    s_dtab[e] = (sh < a.lg) ? deposit_nb(v & ((1ull << a.lg) - 1ull), a.s) : 0;
+  }
+  if (tid == 0) {
+    mbar_init(full, kTcLoaders);
+    mbar_init(empty, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull(b), 1);
+      mbar_init(tempty(b), kTcEpiWarps * 32);
+    }
+    mbar_init(fin, 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kTcMmaWarp) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(128u));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint64_t stride_tiles = (uint64_t)gridDim.x;
+  auto tile_row0 = [&](int i) { return ((uint64_t)blockIdx.x + (uint64_t)i * stride_tiles) * kTcRows; };
+  auto tile_rows = [&](uint64_t t0) {
+    return a.total - t0 < (uint64_t)kTcRows ? (int)(a.total - t0) : kTcRows;
+  };
+  int ntiles = 0;
+  while (tile_row0(ntiles) < a.total) ++ntiles;
+  const int ngroups = (ntiles + kGramGroup - 1) / kGramGroup;
+
+  if (warp < kTcLoadWarps) {
+    // ================================================================ loaders (psi and lambda)
+    const int lt = tid, lb = a.lowbits;
+    uint64_t goff[UT];
+    uint32_t tm[UT];  // the unit's tuple t (bits 0..7) and first member m (bits 8..)
+    int tmax = 0;
+#pragma unroll
+    for (int k = 0; k < UT; ++k) {
+      const int u = lt + k * kTcLoaders;
+      int t, m;
+      if (MODE == TC_PAIR_MEMBERS) {
+        const int hb = lb - 1;
+        t = (u >> hb) & (kTcRows - 1);
+        m = 2 * ((u & ((1 << hb) - 1)) | ((u >> (hb + 7)) << hb));
+      } else if (MODE == TC_PAIR_TUPLES) {
+        t = 2 * (u & (kTcRows / 2 - 1));
+        m = u >> 6;
+      } else {
+        t = u & (kTcRows - 1);
+        m = u >> 7;
+      }
+      goff[k] = s_P[t] + s_off[m];
+      tm[k] = (uint32_t)t | ((uint32_t)m << 8);
+      tmax = max(tmax, MODE == TC_PAIR_TUPLES ? t + 1 : t);
+    }
+    VT p0[UT], l0[UT], p1[UT], l1[UT];
+    auto load = [&](uint64_t t0, VT* vp, VT* vl) {
+      const uint64_t tb = tile_base(t0, a, s_dtab);
+      const int rows = tile_rows(t0);
+#pragma unroll
+      for (int k = 0; k < UT; ++k) {
+        const int t = (int)(tm[k] & 255u);
+        const bool ok = tmax < rows || t < rows;
+        vp[k] = ok ? *reinterpret_cast<const VT*>(a.psi + tb + goff[k]) : VT{};
+        vl[k] = ok ? *reinterpret_cast<const VT*>(lam + tb + goff[k]) : VT{};
+      }
+    };
+    // transposed staging: component row r (psi r, lambda 64 + r), tuple column t
+    auto put1 = [&](int r, int t, float v) {
+      const uint32_t o = sw128_off(r, t, kTcRows);
+      const float h = tf32_hi(v);
+      *reinterpret_cast<float*>(sm + L::HI + o) = h;
+      *reinterpret_cast<float*>(sm + L::LO + o) = v - h;
+    };
+    auto put2 = [&](int r, int t, float v0, float v1) {  // columns t, t + 1 (t even): one 8-byte store
+      const uint32_t o = sw128_off(r, t, kTcRows);
+      const float h0 = tf32_hi(v0), h1 = tf32_hi(v1);
+      *reinterpret_cast<float2*>(sm + L::HI + o) = make_float2(h0, h1);
+      *reinterpret_cast<float2*>(sm + L::LO + o) = make_float2(v0 - h0, v1 - h1);
+    };
+    auto put = [&](int r0, uint32_t tmk, const VT& x) {
+      const int t = (int)(tmk & 255u), m = (int)(tmk >> 8);
+      if (MODE == TC_PAIR_MEMBERS) {  // members m, m + 1 of tuple t
+        const float4 v = *reinterpret_cast<const float4*>(&x);
+        put1(r0 + 2 * m, t, v.x);
+        put1(r0 + 2 * m + 1, t, v.y);
+        put1(r0 + 2 * m + 2, t, v.z);
+        put1(r0 + 2 * m + 3, t, v.w);
+      } else if (MODE == TC_PAIR_TUPLES) {  // member m of tuples t, t + 1
+        const float4 v = *reinterpret_cast<const float4*>(&x);
+        put2(r0 + 2 * m, t, v.x, v.z);
+        put2(r0 + 2 * m + 1, t, v.y, v.w);
+      } else {
+        const float2 v = *reinterpret_cast<const float2*>(&x);
+        put1(r0 + 2 * m, t, v.x);
+        put1(r0 + 2 * m + 1, t, v.y);
+      }
+    };
+    auto step = [&](int i, const VT* cp, const VT* cl, VT* np, VT* nl) -> bool {
+      if (i >= ntiles) return false;
+      if (i + 1 < ntiles) load(tile_row0(i + 1), np, nl);
+      if (!mbar_wait(empty, (uint32_t)(i & 1) ^ 1u, abort)) return false;  // the previous tile's MMAs are done
+#pragma unroll
+      for (int k = 0; k < UT; ++k) {
+        put(0, tm[k], cp[k]);
+        put(64, tm[k], cl[k]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(full);
+      return true;
+    };
+    if (ntiles > 0) load(tile_row0(0), p0, l0);
+    for (int i = 0;; i += 2) {
+      if (!step(i, p0, l0, p1, l1)) break;
+      if (!step(i + 1, p1, l1, p0, l0)) break;
+    }
+  } else if (warp < kTcMmaWarp) {
+    // ================================================================ epilogue: FP32 groups into FP64
+    const int q = warp - kTcEpiWarp0;
+    const int row = q * 32 + lane;  // TMEM lane = component of psi (rows < W are used)
+    for (int g = 0; g < ngroups; ++g) {
+      const int b = g & 1;
+      if (!__all_sync(0xffffffffu, mbar_wait(tfull(b), (uint32_t)(g >> 1) & 1u, abort))) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      float y[64];
+      if (q < 2) {
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 64), y);
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 64 + 32), y + 32);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(tempty(b));
+      if (q < 2 && row < W) {
+#pragma unroll
+        for (int c = 0; c < W; ++c) acc[row * L::ACC_LD + c] += (double)y[c];
+      }
+    }
+    __syncwarp();
+  } else {
+    // ================================================================ MMA issue
+    if (lane == 0) {
+      constexpr uint32_t idesc = tf32_idesc(64);
+      const uint32_t base_hi = smem_u32(sm + L::HI), base_lo = smem_u32(sm + L::LO);
+      const uint32_t lam_off = 64u * 128u;  // lambda: rows 64.. of every 128-row column block
+      bool issued = false;
+      for (int i = 0; i < ntiles; ++i) {
+        const int g = i / kGramGroup, b = g & 1;
+        if (!mbar_wait(full, (uint32_t)i & 1u, abort)) break;
+        if (i % kGramGroup == 0 && !mbar_wait(tempty(b), ((uint32_t)(g >> 1) & 1u) ^ 1u, abort)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + (uint32_t)(b * 64);
+#pragma unroll
+        for (int ks = 0; ks < kTcRows / 8; ++ks) {
+          // 8 tuples per MMA: 32 bytes inside a 128-byte column block of 32 tuples
+          const uint32_t ko = (uint32_t)(ks >> 2) * (uint32_t)(kTcRows * 128) + (uint32_t)(ks & 3) * 32u;
+          const uint64_t ah = sw128_desc(base_hi + ko), al = sw128_desc(base_lo + ko);
+          const uint64_t bh = sw128_desc(base_hi + lam_off + ko), bl = sw128_desc(base_lo + lam_off + ko);
+          mma_tf32(d, ah, bh, idesc, (i % kGramGroup != 0 || ks > 0) ? 1u : 0u);
+          mma_tf32(d, ah, bl, idesc, 1u);
+          mma_tf32(d, al, bh, idesc, 1u);
+        }
+        mma_commit(empty);
+        if (i % kGramGroup == kGramGroup - 1 || i == ntiles - 1) mma_commit(tfull(b));
+        issued = true;
+      }
+      if (issued) {
+        mma_commit(fin);
+        volatile int never = 0;
+        mbar_wait(fin, 0, &never);
+      }
+    }
+    __syncwarp();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (tid == 0 && *abort) atomicExch(&g_tc_status, 1);
+  for (int e = tid; e < W * W; e += kTcThreads)
+    partials[(size_t)blockIdx.x * W * W + e] = acc[(e / W) * L::ACC_LD + (e % W)];
+  if (warp == kTcMmaWarp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u));
+}
+
+template <int K, int MODE>
+static int launch_gram_tc_mode(const TcArgs<K>& a, const float2* lam, double* partials, int* grid_out,
+                               cudaStream_t st) {
+  using L = GramTcSmem<K>;
+  int dev = 0, sms = 0;
+  QS_CUDA(cudaGetDevice(&dev));
+  QS_CUDA(cudaFuncSetAttribute(k_gram_tc<K, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES));
+  QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const uint64_t tiles = (a.total + kTcRows - 1) / kTcRows;
+  const unsigned grid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)sms);
+  k_gram_tc<K, MODE><<<grid, kTcThreads, L::BYTES, st>>>(a, lam, partials);
+  QS_LAUNCHED();
+  *grid_out = (int)grid;
+  return QS_OK;
+}
+
+template <int K>
+static int launch_gram_tc_t(const float2* psi, const float2* lam, int n, const int* qubits, double* partials,
+                            int* grid_out, cudaStream_t st) {
+  constexpr int D = 1 << K;
+  TcArgs<K> a;
+  memset(&a, 0, sizeof(a));
+  uint64_t mask = 0;
+  for (int j = 0; j < K; ++j) mask |= 1ull << qubits[j];
+  a.lowbits = 0;
+  while (a.lowbits < K && qubits[a.lowbits] == a.lowbits) ++a.lowbits;
+  for (int m = 0; m < D; ++m) {
+    uint64_t o = 0;
+    for (int j = 0; j < K; ++j)
+      if ((m >> j) & 1) o |= 1ull << qubits[j];
+    if (o >> 32) return fail(QS_EUNSUPPORTED, "tensor-core Gram takes supports below qubit 32");
+    a.off[m] = (uint32_t)o;
+  }
+  QS_TRY(make_idx(n, mask, 0, &a.s));
+  a.psi = const_cast<float2*>(psi);
+  a.lg = a.s.item_log2;
+  a.reg_stride = 1ull << n;
+  a.total = 1ull << a.lg;
+  if (a.lowbits >= 1) return launch_gram_tc_mode<K, TC_PAIR_MEMBERS>(a, lam, partials, grid_out, st);
+  if (a.lg >= 1) return launch_gram_tc_mode<K, TC_PAIR_TUPLES>(a, lam, partials, grid_out, st);
+  return launch_gram_tc_mode<K, TC_SCALAR>(a, lam, partials, grid_out, st);
+}
+
+// Real Gram matrix of a 4- or 5-qubit support (qubits ascending) over a
+// complex64 register, interleaved layout, partials [grid][W][W]; *grid_out
+// receives the row count for the fold.
+int gram_tc(int w, const float2* psi, const float2* lam, int n, const int* qubits, double* partials, int* grid_out,
+            cudaStream_t st) {
+  if (w == 4) return launch_gram_tc_t<4>(psi, lam, n, qubits, partials, grid_out, st);
+  if (w == 5) return launch_gram_tc_t<5>(psi, lam, n, qubits, partials, grid_out, st);
+  return fail(QS_EUNSUPPORTED, "tensor-core Gram takes 4- or 5-qubit supports");
+}
+
 static int g_tc_enabled = 1;
 
 void set_tensor_cores(int mode) { g_tc_enabled = mode < 0 ? 0 : (mode > 2 ? 2 : mode); }

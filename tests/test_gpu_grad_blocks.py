@@ -98,3 +98,28 @@ def test_block_gradient_n20_against_fp64_adjoint(qs):
     loss, grad = qs.backward_blocks(st, circ, params, obs, kmax=5)
     assert abs(loss - wl) < 1e-5
     assert rel(grad, wg) < 1e-4, rel(grad, wg)
+
+
+@pytest.mark.parametrize("kmax", [4, 5])
+def test_block_gradient_tensor_core_gram_matches_cuda_core(qs, kmax):
+    # 4- and 5-qubit supports: rho from the tensor-core Gram kernel (3xTF32, FP64 groups)
+    # against the CUDA-core Gram kernel and the oracle
+    n = 11
+    for name, gates, params in circuits(n):
+        circ = qs.Circuit(gates, n, nparams=len(params))
+        terms = W.zz_chain(n) + [(0.4, ((3, "X"),))]
+        obs = qs.Observable(terms)
+        psi0 = W.haar_state(n, seed=5)
+        out = {}
+        for mode in (1, 0):
+            qs.set_tensor_cores(mode)
+            st = qs.State(n, dtype=torch.complex64)
+            st.upload(psi0)
+            st.apply_circuit(circ, params, blocks=kmax)
+            out[mode] = qs.backward_blocks(st, circ, params, obs, kmax=kmax)
+        qs.set_tensor_cores(1)
+        wl, wg = oracle.gradient(psi0, n, gates, params, terms)
+        for mode in (1, 0):
+            assert abs(out[mode][0] - wl) < 1e-5
+            assert rel(out[mode][1], wg) < 2e-5, (name, mode, rel(out[mode][1], wg))
+        assert rel(out[1][1], out[0][1]) < 2e-5, name
