@@ -751,17 +751,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const __grid_constant
       const int b = g & 1;
       if (!__all_sync(0xffffffffu, mbar_wait(tfull(b), (uint32_t)(g >> 1) & 1u, abort))) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      float y[64];
-      if (q < 2) {
-        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 64), y);
-        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 64 + 32), y + 32);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mbar_arrive(tempty(b));
-      if (q < 2 && row < W) {
+      // 32 columns at a time into the FP64 row; the buffer is released after the last
 #pragma unroll
-        for (int c = 0; c < W; ++c) acc[row * L::ACC_LD + c] += (double)y[c];
+      for (int c0 = 0; c0 < 64; c0 += 32) {
+        float y[32];
+        if (q < 2) {
+          tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 64 + c0), y);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        }
+        if (c0 + 32 == 64) {
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          mbar_arrive(tempty(b));
+        }
+        if (q < 2 && row < W && c0 < W) {
+#pragma unroll
+          for (int c = 0; c < 32; ++c) acc[row * L::ACC_LD + c0 + c] += (double)y[c];
+        }
       }
     }
     __syncwarp();
