@@ -134,6 +134,29 @@ int qs_state_download(const qs_state* s, void* host_amps);
  * QS_EDEVICE. */
 int qs_state_sync(qs_state* s);
 
+/* ---------------------------------------------------------------- level-1 operations
+ *
+ * The pieces of the reversible adjoint (Sec. "Reverse Mode", Eq. apply-back)
+ * for a caller that walks a circuit gate by gate itself, e.g. over a state
+ * split into pieces across processes: the gradient of U = exp(-i theta c H) is
+ * 2 c Im<lambda|H psi>, an inner product; lambda = O psi is a sum of Pauli
+ * strings applied to copies of psi.  a/b, dst/src and x/y must have the same
+ * dtype and register sizes (QS_EINVAL otherwise). */
+
+/* dst <- src, asynchronous on dst's stream (order src's earlier work before
+ * it: same stream or an event). */
+int qs_state_copy(qs_state* dst, const qs_state* src);
+
+/* <a_r|b_r> = sum_i conj(a_r,i) b_r,i per register r into host_out[2 nreg]
+ * (re, im): products and sums in FP64, per-block partial sums folded in block
+ * order (the same result on every run).  Runs on a's stream and synchronises
+ * it. */
+int qs_state_inner(qs_state* a, const qs_state* b, double* host_out);
+
+/* y <- y + alpha x in the states' precision (alpha rounded to FP32 for
+ * complex64), asynchronous on y's stream.  x and y must be distinct. */
+int qs_state_axpy(qs_state* y, double alpha_re, double alpha_im, const qs_state* x);
+
 /* ---------------------------------------------------------------- options */
 
 /* Process-wide switches (not thread-safe against concurrent launches).
@@ -245,6 +268,18 @@ int qs_circuit_create(int nqubits, const qs_gate_desc* host_gates, int ngates,
                       const double* host_mats, int64_t nmat, int nparams, qs_circuit** out);
 int qs_circuit_destroy(qs_circuit* c);
 int qs_circuit_info(const qs_circuit* c, int* nqubits, int* ngates, int* nparams);
+
+/* Host-side view of gate `index` of c (no device work; callable without a
+ * GPU): host_desc (may be NULL) receives its descriptor; host_U (may be NULL)
+ * its 2^k x 2^k matrix at host_params (App. "Builtin Block Types"; row-major,
+ * interleaved re/im, index bit j <-> locs[j], controls not included);
+ * host_G / host_cfac (may be NULL) the generator H on the targets and the
+ * factor c with U = exp(-i theta c H) (Sec. "Reverse Mode"; rotations: Pauli
+ * string, c = 1/2; shift: P1, c = -1; phase: identity, c = -1).  Asking for
+ * H or c of a gate without a parameter is QS_EINVAL. */
+int qs_circuit_gate_matrices(const qs_circuit* c, int index, const double* host_params,
+                             qs_gate_desc* host_desc, double* host_U, double* host_G,
+                             double* host_cfac);
 
 /* Passes and phases of the circuit's tile-engine schedule for tiles of
  * tile_qubits qubits (0 = 13); builds and caches the schedule (device

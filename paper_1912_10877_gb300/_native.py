@@ -64,6 +64,9 @@ SIGNATURES = {
     "qs_state_upload": ([_P, _P], _I),
     "qs_state_download": ([_P, _P], _I),
     "qs_state_sync": ([_P], _I),
+    "qs_state_copy": ([_P, _P], _I),
+    "qs_state_inner": ([_P, _P, _PD], _I),
+    "qs_state_axpy": ([_P, _D, _D, _P], _I),
     "qs_set_option": ([_I, _I], _I),
     "qs_get_option": ([_I, ctypes.POINTER(_I)], _I),
     "qs_selftest_bounded_wait": ([_D, ctypes.POINTER(_I)], _I),
@@ -78,6 +81,7 @@ SIGNATURES = {
     "qs_circuit_create": ([_I, ctypes.POINTER(GateDesc), _I, _PD, ctypes.c_int64, _I, _PP], _I),
     "qs_circuit_destroy": ([_P], _I),
     "qs_circuit_info": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "qs_circuit_gate_matrices": ([_P, _I, _PD, ctypes.POINTER(GateDesc), _PD, _PD, _PD], _I),
     "qs_circuit_schedule_info": ([_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "qs_apply_circuit": ([_P, _P, _PD, _I], _I),
     "qs_circuit_blocks": ([_P, _PD, _I, ctypes.POINTER(_I), _PI32, _PI32, _PD], _I),

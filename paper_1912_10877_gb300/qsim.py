@@ -112,6 +112,24 @@ class State:
         N.check(N.lib().qs_state_download(self.handle, out.ctypes.data))
         return out
 
+    # -- level-1 operations between states of the same shape -------------------
+    def copy_from(self, src: "State"):
+        """self <- src (stream-ordered on self's stream)."""
+        N.check(N.lib().qs_state_copy(self.handle, src.handle))
+        return self
+
+    def inner(self, other: "State") -> np.ndarray:
+        """<self_r|other_r> per register (FP64 sums), complex128 [nreg]."""
+        out = np.zeros(2 * self.nreg)
+        N.check(N.lib().qs_state_inner(self.handle, other.handle, N.dptr(out)))
+        return out.view(np.complex128)
+
+    def axpy(self, alpha, x: "State"):
+        """self <- self + alpha x."""
+        a = complex(alpha)
+        N.check(N.lib().qs_state_axpy(self.handle, a.real, a.imag, x.handle))
+        return self
+
     # -- instructions ---------------------------------------------------------
     def apply(self, g, params=None):
         """instruct! one gate record (workloads.Gate)."""
@@ -218,6 +236,23 @@ class Circuit:
         self.nparams = int(nparams)
         self.ngates = len(gates)
         self.gates = list(gates)
+
+    def gate_matrices(self, index: int, params=None, generator: bool = False):
+        """Host-side matrices of gate `index`: U at `params` (2^k x 2^k complex128) and,
+        with generator=True, (H, c) with U = exp(-i theta c H)."""
+        g = self.gates[index]
+        D = 1 << len(g.locs)
+        p = _params_array(params, self.nparams) if self.nparams else np.zeros(1)
+        U = np.zeros(2 * D * D)
+        G = np.zeros(2 * D * D) if generator else None
+        cf = ctypes.c_double()
+        N.check(N.lib().qs_circuit_gate_matrices(self.handle, int(index), N.dptr(p), None, N.dptr(U),
+                                                 N.dptr(G) if generator else None,
+                                                 ctypes.byref(cf) if generator else None))
+        U = U.view(np.complex128).reshape(D, D)
+        if not generator:
+            return U
+        return U, G.view(np.complex128).reshape(D, D), cf.value
 
     def checkpoint_count(self, every: int) -> int:
         c = ctypes.c_int()

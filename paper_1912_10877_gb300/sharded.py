@@ -1,0 +1,444 @@
+"""Qubit-sharded state vector: one 2^n-amplitude register split into 2^g shards.
+
+A register too large for one device is cut by its top g physical qubits (the
+"global" qubits): shard s holds the 2^L amplitudes (L = n - g) whose physical
+index has s in its top g bits.  Shards live in the processes of a
+torch.distributed group (NCCL between GPUs, gloo on CPU), 2^g / world shards
+per process; with no group every shard is local.
+
+Which logical qubit sits at which physical bit is a permutation kept on the
+host (``pos`` / ``who``), identical on every rank.  Gates follow the general
+instruction of Sec. "Instructions on Quantum Registers" / Sec. "Performance":
+  * a control on a global qubit is a predicate on the shard index: shards
+    whose bit differs skip the gate, the others drop the control;
+  * a diagonal gate never moves data: on each shard its diagonal is restricted
+    to the shard's values of the global targets (a scalar when every target is
+    global);
+  * any other gate first brings its global targets to local bits: physical
+    local bit l and global bit j are exchanged by swapping, between shard s and
+    shard s ^ 2^j, the half of each shard whose bit l differs from the shard's
+    bit j (one pairwise exchange of half the shard, 2^(L-1) amplitudes each way),
+    after which the two logical qubits trade places in the map.  The local bit
+    given up is the highest one not needed by the gate, so the halves are
+    contiguous runs of at least 2^(L-1-k) amplitudes.
+Expectation values (Sec. "Forward Mode") localise the X / Y qubits of each
+Pauli string the same way and read a global Z as the sign (-1)^bit of the
+shard; the per-shard sums are added with one all-reduce.  The reversible
+backward (Sec. "Reverse Mode", Eq. apply-back) runs gate by gate on psi and
+lambda = O psi, which share the map: a parameterised gate U = exp(-i theta c H)
+adds 2 c Im<lambda|(P_ctrl (x) H) psi> from a copy of psi, then both states are
+uncomputed by U^dagger; every shard's gradient partials are added with one
+all-reduce at the end.
+
+Every local operation is a call into libqsim.so (``qsim.State``); this module
+only plans exchanges and predicates, and moves shard halves with
+``torch.distributed`` point-to-point transfers (across processes) or device
+copies (inside one).  ``backend`` lets a caller supply shards of another kind
+with the same methods (used by the CPU multi-process tests of this logic).
+"""
+from __future__ import annotations
+
+import copy
+
+import numpy as np
+import torch
+
+from . import qsim
+
+_PAULI = {"X": np.array([[0, 1], [1, 0]], np.complex128),
+          "Y": np.array([[0, -1j], [1j, 0]], np.complex128),
+          "Z": np.array([[1, 0], [0, -1]], np.complex128)}
+
+
+class LibShard:
+    """One shard as a libqsim register on the current CUDA device."""
+
+    def __init__(self, nqubits: int, dtype):
+        self.n = nqubits
+        self.st = qsim.State(nqubits, dtype=dtype)
+
+    def flat(self) -> torch.Tensor:
+        """The amplitudes as a flat real tensor (re, im interleaved)."""
+        return torch.view_as_real(self.st.buffer).view(-1)
+
+    def reset(self, x=None):
+        self.st.reset(x)
+
+    def zero(self):
+        self.st.reset()
+        self.st.apply_matrix(np.zeros((2, 2), np.complex128), [0])
+
+    def apply_matrix(self, U, locs, ctrl_locs=(), ctrl_vals=()):
+        self.st.apply_matrix(U, list(locs), list(ctrl_locs), list(ctrl_vals))
+
+    def copy_from(self, other: "LibShard"):
+        self.st.copy_from(other.st)
+
+    def inner(self, other: "LibShard") -> complex:
+        return complex(self.st.inner(other.st)[0])
+
+    def axpy(self, alpha, other: "LibShard"):
+        self.st.axpy(alpha, other.st)
+
+    def expect(self, terms) -> float:
+        return float(self.st.expect(qsim.Observable(terms))[0])
+
+    def upload(self, amps):
+        self.st.upload(amps)
+
+    def numpy(self) -> np.ndarray:
+        return self.st.numpy()
+
+
+def _is_diagonal(U: np.ndarray) -> bool:
+    return not np.any(U - np.diag(np.diag(U)))
+
+
+class ShardedState:
+    """A 2^n register over 2^nglobal shards (see the module docstring).
+
+    nqubits, nglobal : n and g (shards of L = n - g qubits, L >= 1)
+    dtype            : torch.complex64 or torch.complex128
+    group            : torch.distributed process group, or None for the default
+                       group when one is initialised (else every shard is local)
+    backend          : callable (L, dtype) -> shard; default LibShard (CUDA)
+    """
+
+    def __init__(self, nqubits: int, nglobal: int, dtype=torch.complex128, group=None, backend=None):
+        import torch.distributed as dist
+        self.n, self.g = int(nqubits), int(nglobal)
+        self.L = self.n - self.g
+        if self.g < 0 or self.L < 1:
+            raise ValueError("need 0 <= nglobal < nqubits")
+        self.nshards = 1 << self.g
+        if dist.is_available() and dist.is_initialized():
+            self.group = group
+            self.world = dist.get_world_size(group)
+            self.rank = dist.get_rank(group)
+        else:
+            self.group, self.world, self.rank = None, 1, 0
+        if self.nshards % self.world:
+            raise ValueError(f"{self.nshards} shards do not split over {self.world} ranks")
+        self.per_rank = self.nshards // self.world
+        self.owned = list(range(self.rank * self.per_rank, (self.rank + 1) * self.per_rank))
+        self.dtype = dtype
+        self._make = backend if backend is not None else (lambda L, dt: LibShard(L, dt))
+        self.pos = list(range(self.n))   # logical qubit -> physical bit
+        self.who = list(range(self.n))   # physical bit -> logical qubit
+        self.vecs = {"psi": [self._make(self.L, dtype) for _ in self.owned]}
+        self.exchanges = 0
+        self.reset()
+
+    # ------------------------------------------------------------------ bookkeeping
+    def _vector(self, name: str):
+        if name not in self.vecs:
+            self.vecs[name] = [self._make(self.L, self.dtype) for _ in self.owned]
+        return self.vecs[name]
+
+    def _drop(self, name: str):
+        self.vecs.pop(name, None)
+
+    def _rank_of(self, shard: int) -> int:
+        import torch.distributed as dist
+        r = shard // self.per_rank
+        return dist.get_global_rank(self.group, r) if self.group is not None else r
+
+    def _phys(self, x: int) -> int:
+        """Physical index of logical basis index x under the current map."""
+        p = 0
+        for q in range(self.n):
+            if (x >> q) & 1:
+                p |= 1 << self.pos[q]
+        return p
+
+    def reset(self, x: int = 0):
+        """|x> (logical basis index) on psi; other vectors are dropped."""
+        for name in list(self.vecs):
+            if name != "psi":
+                self._drop(name)
+        p = self._phys(int(x))
+        s_x, loc = p >> self.L, p & ((1 << self.L) - 1)
+        for s, v in zip(self.owned, self.vecs["psi"]):
+            if s == s_x:
+                v.reset(loc)
+            else:
+                v.zero()
+        return self
+
+    def _sum(self, values: np.ndarray) -> np.ndarray:
+        """Sum of a float64 vector over the ranks of the group."""
+        import torch.distributed as dist
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        if self.world == 1:
+            return v
+        dev = torch.device("cuda") if dist.get_backend(self.group) == "nccl" else torch.device("cpu")
+        t = torch.as_tensor(v, device=dev).clone()
+        dist.all_reduce(t, group=self.group)
+        return t.cpu().numpy()
+
+    # ------------------------------------------------------------------ exchange
+    def _exchange(self, l: int, j: int):
+        """Swap physical local bit l with global bit j (physical L + j) in every vector."""
+        import torch.distributed as dist
+        L = self.L
+        run = 2 << l                      # one run of 2^l amplitudes, in reals
+        nrun = 1 << (L - 1 - l)
+        for vecs in self.vecs.values():
+            flats = {s: v.flat() for s, v in zip(self.owned, vecs)}
+            tmp = None
+            ops, back = [], []
+            for idx, s in enumerate(self.owned):
+                p = s ^ (1 << j)
+                b = (s >> j) & 1
+                x = flats[s]
+                if p in flats:                       # partner in this process
+                    if b == 1:
+                        continue                      # handled from the b = 0 side
+                    y = flats[p]
+                    for a in range(nrun):
+                        xs = x[(2 * a + 1) * run:(2 * a + 2) * run]   # s: bit l = 1
+                        ys = y[(2 * a) * run:(2 * a + 1) * run]       # p: bit l = 0
+                        t = xs.clone()
+                        xs.copy_(ys)
+                        ys.copy_(t)
+                    continue
+                if tmp is None:
+                    tmp = torch.empty(nrun * run * len(self.owned), dtype=x.dtype, device=x.device)
+                peer = self._rank_of(p)
+                for a in range(nrun):
+                    lo = (2 * a + (1 - b)) * run       # runs with bit l = 1 - b
+                    rv = tmp[(idx * nrun + a) * run:(idx * nrun + a + 1) * run]
+                    ops.append(dist.P2POp(dist.isend, x[lo:lo + run], peer, self.group, tag=idx * nrun + a))
+                    ops.append(dist.P2POp(dist.irecv, rv, peer, self.group, tag=idx * nrun + a))
+                    back.append((x[lo:lo + run], rv))
+            if ops:
+                for w in dist.batch_isend_irecv(ops):
+                    w.wait()
+                for dst, src in back:
+                    dst.copy_(src)
+        ql, qg = self.who[l], self.who[L + j]
+        self.who[l], self.who[L + j] = qg, ql
+        self.pos[qg], self.pos[ql] = l, L + j
+        self.exchanges += 1
+
+    def _localize(self, qubits):
+        """Brings every logical qubit of `qubits` to a local physical bit."""
+        need = [q for q in qubits if self.pos[q] >= self.L]
+        if len(set(qubits)) > self.L:
+            raise ValueError(f"{len(set(qubits))} qubits cannot all be local with {self.L} local bits")
+        for q in need:
+            keep = set(qubits)
+            for l in range(self.L - 1, -1, -1):
+                if self.who[l] not in keep:
+                    break
+            else:
+                raise ValueError("no local bit to give up")
+            self._exchange(l, self.pos[q] - self.L)
+
+    # ------------------------------------------------------------------ gates
+    def _restrict(self, s: int, ctrl_locs, ctrl_vals):
+        """(applies, local control positions, values) of shard s."""
+        lc, lv = [], []
+        for c, v in zip(ctrl_locs, ctrl_vals):
+            p = self.pos[c]
+            if p >= self.L:
+                if ((s >> (p - self.L)) & 1) != int(v):
+                    return False, None, None
+            else:
+                lc.append(p)
+                lv.append(int(v))
+        return True, lc, lv
+
+    def apply_matrix(self, U, locs, ctrl_locs=(), ctrl_vals=None, vectors=("psi",)):
+        """instruct!(reg, U, locs, ctrl_locs, ctrl_vals) on the named vectors (logical qubits)."""
+        locs = [int(q) for q in locs]
+        ctrl_locs = [int(q) for q in ctrl_locs]
+        ctrl_vals = [1] * len(ctrl_locs) if ctrl_vals is None else [int(v) for v in ctrl_vals]
+        k = len(locs)
+        U = np.asarray(U, dtype=np.complex128).reshape(1 << k, 1 << k)
+        diag = _is_diagonal(U)
+        if not diag:
+            self._localize(locs)
+        d = np.diag(U)
+        for name in vectors:
+            for s, v in zip(self.owned, self._vector(name)):
+                ok, lc, lv = self._restrict(s, ctrl_locs, ctrl_vals)
+                if not ok:
+                    continue
+                if not diag:
+                    v.apply_matrix(U, [self.pos[q] for q in locs], lc, lv)
+                    continue
+                gl = [(j, self.pos[q] - self.L) for j, q in enumerate(locs) if self.pos[q] >= self.L]
+                ll = [j for j, q in enumerate(locs) if self.pos[q] < self.L]
+                dl = np.zeros(1 << len(ll), np.complex128)
+                for m in range(1 << k):
+                    if all(((m >> j) & 1) == ((s >> gb) & 1) for j, gb in gl):
+                        dl[sum(((m >> j) & 1) << t for t, j in enumerate(ll))] = d[m]
+                if ll:
+                    if np.any(dl != 1):
+                        v.apply_matrix(np.diag(dl), [self.pos[locs[j]] for j in ll], lc, lv)
+                elif dl[0] != 1:
+                    free = next(p for p in range(self.L) if p not in lc)
+                    v.apply_matrix(np.diag([dl[0], dl[0]]), [free], lc, lv)
+        return self
+
+    def apply(self, g, params=None, vectors=("psi",)):
+        """One workloads.Gate record, matrix from the library's gate definitions."""
+        if g.param is None:
+            U = qsim.Circuit([g], self.n, nparams=0).gate_matrices(0)
+        else:
+            one = copy.copy(g)
+            one.param = 0
+            U = qsim.Circuit([one], self.n, nparams=1).gate_matrices(0, [float(params[g.param])])
+        return self.apply_matrix(U, g.locs, g.ctrl_locs, g.ctrl_vals, vectors)
+
+    def apply_circuit(self, circuit: "qsim.Circuit", params=None):
+        """apply!(reg, chain): the circuit's gates in order."""
+        for i, g in enumerate(circuit.gates):
+            U = circuit.gate_matrices(i, params)
+            self.apply_matrix(U, g.locs, g.ctrl_locs, g.ctrl_vals)
+        return self
+
+    # ------------------------------------------------------------------ observables
+    def _local_terms(self, s: int, terms):
+        """Pauli terms evaluable on shard s: physical local positions, signed coefficients."""
+        out = []
+        for coeff, ops in terms:
+            sign = 1.0
+            local = []
+            for q, P in ops:
+                p = self.pos[q]
+                if p >= self.L:
+                    if P != "Z":
+                        raise AssertionError("X/Y on a global qubit")
+                    if (s >> (p - self.L)) & 1:
+                        sign = -sign
+                else:
+                    local.append((p, P))
+            out.append((sign * float(coeff), tuple(local)))
+        return out
+
+    def _batches(self, terms):
+        """Runs of consecutive terms whose X/Y qubits are all local after one localisation."""
+        batch = []
+        for term in terms:
+            xy = [q for q, P in term[1] if P != "Z"]
+            if any(self.pos[q] >= self.L for q in xy):
+                if batch:
+                    yield batch
+                    batch = []
+                self._localize(xy)
+            batch.append(term)
+        if batch:
+            yield batch
+
+    def expect(self, terms) -> float:
+        """<psi|O|psi> for O = sum coeff P (terms as qsim.Observable takes them)."""
+        total = 0.0
+        for batch in self._batches(list(terms)):
+            for s, v in zip(self.owned, self.vecs["psi"]):
+                total += v.expect(self._local_terms(s, batch))
+        return float(self._sum(np.array([total]))[0])
+
+    def _apply_observable(self, terms, src: str, dst: str, tmp: str):
+        """dst <- O src, one Pauli string at a time through tmp."""
+        for v in self._vector(dst):
+            v.zero()
+        self._vector(tmp)
+        for batch in self._batches(list(terms)):
+            for coeff, ops in batch:
+                for s, vt, vs, vd in zip(self.owned, self.vecs[tmp], self.vecs[src], self.vecs[dst]):
+                    vt.copy_from(vs)
+                    sign = 1.0
+                    local = []
+                    for q, P in ops:
+                        p = self.pos[q]
+                        if p >= self.L:
+                            sign = -sign if (s >> (p - self.L)) & 1 else sign
+                        else:
+                            local.append((p, P))
+                    for c0 in range(0, len(local), 5):
+                        chunk = local[c0:c0 + 5]
+                        M = np.ones((1, 1), np.complex128)
+                        for p, P in chunk:
+                            M = np.kron(_PAULI[P], M)   # index bit j <-> chunk[j]
+                        vt.apply_matrix(M, [p for p, _ in chunk])
+                    vd.axpy(sign * float(coeff), vt)
+
+    # ------------------------------------------------------------------ gradient
+    def backward(self, circuit: "qsim.Circuit", params, terms):
+        """expect'(O, reg => circuit): psi holds the circuit's output state; returns
+        (loss, gradient).  psi is uncomputed to the circuit's input state."""
+        params = np.asarray(params, dtype=np.float64)
+        loss = self.expect(terms)
+        self._apply_observable(terms, "psi", "lam", "tmp")
+        grad = np.zeros(max(1, circuit.nparams))
+        for i in range(len(circuit.gates) - 1, -1, -1):
+            g = circuit.gates[i]
+            if g.param is not None:
+                U, G, cfac = circuit.gate_matrices(i, params, generator=True)
+                nt, nc = len(g.locs), len(g.ctrl_locs)
+                if nt + nc > 5:
+                    raise ValueError("generator with its control projector spans more than 5 qubits")
+                # P_ctrl (x) H on (targets, controls): controls occupy the high index bits
+                proj = np.ones((1, 1), np.complex128)
+                for v in g.ctrl_vals:
+                    e = np.zeros((2, 2), np.complex128)
+                    e[int(v), int(v)] = 1.0
+                    proj = np.kron(e, proj)
+                Gf = np.kron(proj, G)
+                for vt, vs in zip(self.vecs["tmp"], self.vecs["psi"]):
+                    vt.copy_from(vs)
+                self.apply_matrix(Gf, list(g.locs) + list(g.ctrl_locs), (), None, vectors=("tmp",))
+                acc = 0.0
+                for vl, vt in zip(self.vecs["lam"], self.vecs["tmp"]):
+                    acc += vl.inner(vt).imag
+                grad[g.param] += 2.0 * cfac * acc
+            else:
+                U = circuit.gate_matrices(i, params)
+            self.apply_matrix(U.conj().T, g.locs, g.ctrl_locs, g.ctrl_vals, vectors=("psi", "lam"))
+        self._drop("tmp")
+        self._drop("lam")
+        grad = self._sum(grad)
+        return loss, grad[:circuit.nparams]
+
+    # ------------------------------------------------------------------ host views (small n)
+    def _perm(self) -> np.ndarray:
+        """perm[x] = physical index of logical index x under the current map."""
+        idx = np.arange(1 << self.n, dtype=np.int64)
+        perm = np.zeros_like(idx)
+        for q in range(self.n):
+            perm |= ((idx >> q) & 1) << self.pos[q]
+        return perm
+
+    def upload(self, amps):
+        """psi <- a whole register given in logical order (host memory; every rank
+        passes the same array and keeps its own shards)."""
+        amps = np.asarray(amps, dtype=np.complex128).ravel()
+        if amps.size != 1 << self.n:
+            raise ValueError("amplitude count does not match the register")
+        for name in list(self.vecs):
+            if name != "psi":
+                self._drop(name)
+        phys = np.empty_like(amps)
+        phys[self._perm()] = amps
+        for s, v in zip(self.owned, self.vecs["psi"]):
+            v.upload(phys[s << self.L:(s + 1) << self.L])
+        return self
+
+    def local_shards(self, name: str = "psi") -> dict:
+        return {s: v.numpy() for s, v in zip(self.owned, self._vector(name))}
+
+    def gather(self, name: str = "psi") -> np.ndarray:
+        """The whole register in logical order on every rank (host memory; for small n)."""
+        import torch.distributed as dist
+        mine = np.concatenate([self.local_shards(name)[s] for s in self.owned]).astype(np.complex128)
+        if self.world > 1:
+            dev = torch.device("cuda") if dist.get_backend(self.group) == "nccl" else torch.device("cpu")
+            t = torch.view_as_real(torch.as_tensor(mine)).contiguous().to(dev)
+            parts = [torch.empty_like(t) for _ in range(self.world)]
+            dist.all_gather(parts, t, group=self.group)
+            phys = np.concatenate([torch.view_as_complex(p.cpu()).numpy() for p in parts])
+        else:
+            phys = mine
+        return phys[self._perm()]

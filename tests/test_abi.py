@@ -110,3 +110,30 @@ def test_package_has_no_cpu_fallback():
         if fn.endswith(".py"):
             src = open(os.path.join(pkg, fn)).read()
             assert "import oracle" not in src and "from oracle" not in src, fn
+
+
+def test_host_gate_matrices_match_the_oracle(L):
+    """qs_circuit_gate_matrices (host code of the library) against the oracle's own
+    gate definitions, and the generator against a finite difference of U:
+    dU/dtheta = -i c H U for U = exp(-i theta c H)."""
+    import oracle
+    import workloads as W
+    from paper_1912_10877_gb300 import qsim
+    oracle.build()
+    gates = [W.Gate("H", (0,)), W.Gate("T", (1,)), W.Gate("RX", (2,), param=0), W.Gate("RY", (0,), (1,), (0,), param=1),
+             W.Gate("RZ", (1,), param=2), W.Gate("SHIFT", (0,), (2,), (1,), param=3), W.Gate("PHASE", (1,), param=4),
+             W.Gate("ROT", (0, 2), paulis="XZ", param=5), W.Gate("SWAP", (1, 2)), W.Gate("SDG", (2,))]
+    params = np.array([0.3, -1.2, 2.5, 0.7, 1.9, -0.4])
+    c = qsim.Circuit(gates, 3)
+    h = 1e-6
+    for i, g in enumerate(gates):
+        theta = params[g.param] if g.param is not None else 0.0
+        U = c.gate_matrices(i, params)
+        assert np.max(np.abs(U - oracle.gate_matrix(g, theta))) < 1e-15, g.name
+        if g.param is None:
+            with pytest.raises(Exception):
+                c.gate_matrices(i, params, generator=True)
+            continue
+        _, G, cf = c.gate_matrices(i, params, generator=True)
+        dU = (oracle.gate_matrix(g, theta + h) - oracle.gate_matrix(g, theta - h)) / (2 * h)
+        assert np.max(np.abs(dU - (-1j * cf * G @ U))) < 1e-9, g.name
