@@ -212,6 +212,53 @@ def run_sweep(dtype_name: str, steps: int, warmup: int, dev, with_events: bool):
     return res
 
 
+def run_sizes_leg(ns=(26, 28, 30, 32), rounds: int = 2, hbm_peak: float = 0.0):
+    """The complex64 single-gate suite at larger registers (one launch per gate and
+    round, per-launch CUDA events).  The state starts as |+...+> made on the device
+    (H on every qubit of |0...0>): a host-made Haar state of 2^32 amplitudes would
+    need 64 GiB of host memory, and the kernels' time does not depend on the values."""
+    import torch
+    from paper_1912_10877_gb300 import qsim
+    out = {}
+    for n in ns:
+        suite = W.single_gate_suite(n)
+        st = qsim.State(n, dtype=torch.complex64)
+        st.reset()
+        for q in range(n):
+            st.apply(W.Gate("H", (q,)))
+        sw = Sweep(st, suite)
+        sw.round()                                   # warm-up round
+        nl = len(suite)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(rounds * nl + 1)]
+        torch.cuda.synchronize()
+        ev[0].record()
+        for r in range(rounds):
+            sw.round(ev, 1 + r * nl)
+        torch.cuda.synchronize()
+        t, b, worst = {}, {}, None
+        for r in range(rounds):
+            for i, (_, g) in enumerate(suite):
+                dt = ev[r * nl + i].elapsed_time(ev[r * nl + i + 1]) / 1e3
+                c = kernel_class(g)
+                gb = gate_bytes(g, n, 8)
+                t[c] = t.get(c, 0.0) + dt
+                b[c] = b.get(c, 0) + gb
+                if r == rounds - 1:
+                    v = gb / dt / 1e9
+                    if worst is None or v < worst[0]:
+                        worst = (v, f"{g.name} {g.locs}" + (f" ctrl {g.ctrl_locs}" if g.ctrl_locs else ""))
+        total_t, total_b = sum(t.values()), sum(b.values())
+        out[str(n)] = {"gbs": round(total_b / total_t / 1e9, 1),
+                       "frac": round(total_b / total_t / 1e9 / hbm_peak, 4) if hbm_peak else None,
+                       "per_class_gbs": {c: round(b[c] / t[c] / 1e9, 1) for c in t},
+                       "slowest_gate": {"gbs": round(worst[0], 1), "gate": worst[1]},
+                       "state_gib": (1 << n) * 8 / 2 ** 30, "launches": rounds * nl}
+        del sw, st
+        torch.cuda.empty_cache()
+    return {"metric": "single-gate suite HBM GB/s at larger registers (complex64)", "unit": "GB/s",
+            "rounds": rounds, "init": "|+...+> made on the device", "sizes": out}
+
+
 def run_e2e(res, steps: int):
     """Same sweep through host buffers: pinned H2D of the input, the sweep, D2H of the result."""
     import torch
@@ -673,7 +720,8 @@ def main():
     ap.add_argument("--no-tc", action="store_true")
     ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--no-matrix", action="store_true")
-    ap.add_argument("--leg", default="all", choices=["all", "tc", "batch", "diff", "large", "tiles", "small", "matrix"],
+    ap.add_argument("--no-sizes", action="store_true")
+    ap.add_argument("--leg", default="all", choices=["all", "tc", "batch", "diff", "large", "tiles", "small", "matrix", "sizes"],
                     help="run one secondary leg alone and print its JSON (profiling captures)")
     ap.add_argument("--tc-reps", type=int, default=20, help="timed launches per tensor-core configuration")
     ap.add_argument("--reps", type=int, default=REPS, help="repetitions per gate (profiling runs use 1)")
@@ -723,7 +771,7 @@ def main():
                                                world=world, rank=rank),
                 "diff": lambda: run_diff_leg(1, 1), "large": lambda: run_large_leg(1, 1),
                 "tiles": lambda: run_tiles_leg(), "small": lambda: run_small_leg(),
-                "matrix": lambda: run_matrix_leg()}
+                "matrix": lambda: run_matrix_leg(), "sizes": lambda: run_sizes_leg(hbm_peak=hbm_peak)}
         out = legs[args.leg]()
         if rank == 0:
             print(json.dumps(out))
@@ -779,6 +827,8 @@ def main():
         extra["small"] = run_small_leg()
     if solo and not args.no_matrix:
         extra["matrix"] = run_matrix_leg()
+    if solo and not args.no_sizes:
+        extra["single_gate_sizes"] = run_sizes_leg(hbm_peak=hbm_peak)
     if not args.no_large and solo:
         extra["differentiation"] = run_diff_leg(1, 1)
         extra["large"] = run_large_leg(1, 1)
