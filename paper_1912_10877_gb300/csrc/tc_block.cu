@@ -19,12 +19,16 @@
 //   warps 0-15  load a tile with 16-byte accesses (the loads of the tile
 //               two ahead are in flight while the current one is split into
 //               A_hi / A_lo in one of two shared-memory stages),
-//   warp 20     issues the W/8 x 3 tcgen05.mma (kind::tf32, K = 8 each) into
+//   warp 24     issues the W/8 x 3 tcgen05.mma (kind::tf32, K = 8 each) into
 //               one of two TMEM accumulators and commits them to mbarriers,
-//   warps 16-19 read the accumulator rows back with tcgen05.ld (warp w owns
-//               TMEM lanes 32 (w mod 4) ..) and store them to global memory
+//   warps 16-23 read the accumulator rows back with one tcgen05.ld of 32
+//               columns each (warp w owns TMEM lanes 32 (w mod 4) .. and
+//               columns 32 ((w - 16) / 4) ..) and store them to global memory
 //               (through a shared-memory staging tile where a row is a run of
 //               adjacent amplitudes, so that the stores stay coalesced).
+// Per-role timestamps showed a tile costing about as long as four epilogue
+// warps took to drain it (two dependent TMEM loads, then staging and stores)
+// while the MMA warp waited for the accumulator; eight warps halve that.
 // Operands use the canonical K-major 128-byte-swizzle layout: 8-row atoms of
 // 128-byte rows, 16-byte chunk c of row r stored at chunk c ^ (r mod 8), and
 // the K extent split into 128-byte column blocks stored one after another.
@@ -46,6 +50,13 @@ constexpr int kTcLoaders = kTcLoadWarps * 32;       // 512
 constexpr int kTcEpiWarp0 = kTcLoadWarps;           // warps 16..19 (TMEM lane quarters 0..3)
 constexpr int kTcMmaWarp = kTcLoadWarps + kTcEpiWarps;  // warp 20
 constexpr int kTcThreads = (kTcMmaWarp + 1) * 32;   // 672
+// k_block_tc drains its accumulators with eight epilogue warps: warp 16 + e
+// reads TMEM lane quarter e mod 4 (the quarter a warp may access is its warp
+// index mod 4) and accumulator columns 32 (e / 4) .. 32 (e / 4) + 31
+constexpr int kBkEpiWarps = 8;
+constexpr int kBkEpiThreads = kBkEpiWarps * 32;      // 256
+constexpr int kBkMmaWarp = kTcLoadWarps + kBkEpiWarps;  // warp 24
+constexpr int kBkThreads = (kBkMmaWarp + 1) * 32;   // 800
 constexpr uint32_t kTcSpinLimit = 1u << 20;         // mbarrier polls before giving up
 constexpr uint64_t kTcTimeLimitNs = 2000000000ull;  // and at most 2 s of wall time
 
@@ -229,7 +240,7 @@ __device__ __forceinline__ uint64_t row_offset(int t, const TcArgs<K>& a) {
 }
 
 template <int K, int MODE>
-__global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constant__ TcArgs<K> a) {
+__global__ void __launch_bounds__(kBkThreads, 1) k_block_tc(const __grid_constant__ TcArgs<K> a) {
   using L = TcSmem<K>;
   constexpr int D = L::D, W = L::W;
   constexpr uint32_t A_BYTES = L::A_BYTES;
@@ -254,7 +265,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   // ---- setup: the matrix (hi / lo), member and row offsets, barriers, TMEM
-  for (int e = tid; e < W * W; e += kTcThreads) {
+  for (int e = tid; e < W * W; e += kBkThreads) {
     const int n = e / W, kk = e % W;
     const float v = a.b[n][kk], h = tf32_hi(v);
     *reinterpret_cast<float*>(sm + L::B_HI + sw128_off(n, kk, W)) = h;
@@ -263,7 +274,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
   if (tid < D) s_off[tid] = a.off[tid];
   if (tid < kTcRows) s_P[tid] = row_offset(tid, a);
   uint64_t* s_dtab = reinterpret_cast<uint64_t*>(sm + L::DTAB);
-  for (int e = tid; e < 4 * 256; e += kTcThreads) {
+  for (int e = tid; e < 4 * 256; e += kBkThreads) {
     const int c = e >> 8, sh = 7 + 8 * c;
     const uint64_t v = (uint64_t)(e & 255) << sh;
     s_dtab[e] = (sh < a.lg) ? deposit_nb(v & ((1ull << a.lg) - 1ull), a.s) : 0;
@@ -273,13 +284,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
       mbar_init(full(s), kTcLoaders);
       mbar_init(empty(s), 1);
       mbar_init(tfull(s), 1);
-      mbar_init(tempty(s), kTcEpiWarps * 32);
+      mbar_init(tempty(s), (W / 32) * 4 * 32);
     }
     mbar_init(fin, 1);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == kTcMmaWarp) {
+  if (warp == kBkMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"((uint32_t)(2 * W)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -392,10 +403,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
       if (!step(i + 1, v1, v0)) break;
       if (!step(i + 2, v2, v1)) break;
     }
-  } else if (warp < kTcMmaWarp) {
+  } else if (warp < kBkMmaWarp) {
     // ================================================================ epilogue
-    const int q = warp - kTcEpiWarp0;  // TMEM lane quarter
-    const int t = q * 32 + lane;       // this thread's row of every tile
+    const int e = warp - kTcEpiWarp0;           // 0..7
+    const int q = warp & 3;                     // TMEM lane quarter
+    const int c = 32 * (e >> 2);                // first accumulator column of this warp
+    const bool reads = c < W;                   // 4-qubit blocks: warps 20..23 only store
+    const int t = q * 32 + lane;                // this thread's row of every tile
+    const int et = e * 32 + lane;               // 0..255
     const uint64_t myP = s_P[t];
     const bool staged = MODE == TC_PAIR_MEMBERS && a.lowbits >= 2;
     float2* stage = reinterpret_cast<float2*>(sm + L::STAGE);
@@ -406,19 +421,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
       const bool valid = t < rows;
       const uint64_t tb = tile_base(t0, a, s_dtab);
       const uint64_t base = tb + myP;
-      // the four epilogue warps agree on giving up (they share named barrier 2)
-      if (bar_or(2, kTcEpiWarps * 32, !mbar_wait(tfull(s), (i >> 1) & 1, abort))) break;
+      // the eight epilogue warps agree on giving up (they share named barrier 2)
+      if (bar_or(2, kBkEpiThreads, !mbar_wait(tfull(s), (i >> 1) & 1, abort))) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // 32 columns (16 amplitudes) at a time; the accumulator is released after the last chunk
-#pragma unroll
-      for (int c = 0; c < W; c += 32) {
+      if (reads) {
+        // 32 columns (16 amplitudes); the accumulator half is released right after the load
         float y[32];
         tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(s * W + c), y);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (c + 32 == W) {
-          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-          mbar_arrive(tempty(s));
-        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(tempty(s));
         const int m0 = c / 2;
         if (staged) {
           // stage the row; it leaves in coalesced runs below
@@ -440,18 +452,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
         }
       }
       if (staged) {
-        bar_sync(2, kTcEpiWarps * 32);
+        bar_sync(2, kBkEpiThreads);
         const int hb = a.lowbits - 1;
+        // 64 D 16-byte units per tile, D / 4 per thread
 #pragma unroll 4
-        for (int k = 0; k < D / 2; ++k) {
-          const int u = t + k * kTcEpiWarps * 32;
+        for (int k = 0; k < D / 4; ++k) {
+          const int u = et + k * kBkEpiThreads;
           const int qq = (u & ((1 << hb) - 1)) | ((u >> (hb + 7)) << hb);
           const int tt = (u >> hb) & (kTcRows - 1);
           if (tt < rows)
             *reinterpret_cast<float4*>(a.psi + tb + s_P[tt] + s_off[2 * qq]) =
                 *reinterpret_cast<const float4*>(stage + tt * L::SROW + 2 * qq);
         }
-        bar_sync(2, kTcEpiWarps * 32);  // the staging buffer is free for the next tile
+        bar_sync(2, kBkEpiThreads);  // the staging buffer is free for the next tile
       }
     }
     __syncwarp();
@@ -497,7 +510,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (tid == 0 && *abort) atomicExch(&g_tc_status, 1);
-  if (warp == kTcMmaWarp)
+  if (warp == kBkMmaWarp)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * W)));
 }
 
@@ -511,7 +524,7 @@ static int launch_tc_mode(const TcArgs<K>& a, cudaStream_t st) {
   QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const uint64_t tiles = (a.total + kTcRows - 1) / kTcRows;
   const unsigned grid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)sms);
-  k_block_tc<K, MODE><<<grid, kTcThreads, smem, st>>>(a);
+  k_block_tc<K, MODE><<<grid, kBkThreads, smem, st>>>(a);
   QS_LAUNCHED();
   return QS_OK;
 }
