@@ -40,6 +40,8 @@
 #include <cstring>
 #include <type_traits>
 
+#include <cuda.h>
+
 #include "common.cuh"
 
 namespace qs {
@@ -529,6 +531,435 @@ static int launch_tc_mode(const TcArgs<K>& a, cudaStream_t st) {
   return QS_OK;
 }
 
+// ------------------------------------------------------------------ TMA-fed blocks on consecutive targets
+//
+// Dense blocks on consecutive targets q .. q+K-1 without controls (every block
+// the planner forms from layered and brickwork circuits).  One producer thread
+// brings each 128-tuple tile into a ring of shared-memory stages with one TMA
+// tensor copy (completion counted in bytes on the stage's mbarrier), so the
+// ring depth, not the registers of loader threads, sets the bytes in flight.
+// Sixteen converter warps read a tile's FP32 values, split them (hi = v with
+// the low 13 mantissa bits cleared, lo = v - hi) and write both into tensor
+// memory with tcgen05.st, where the MMAs read the A operand; shared memory
+// holds only the ring, the matrix B and the epilogue's staging tile.
+//   q = 0 (targets 0..K-1): a tile is 128 consecutive tuples of 2^K adjacent
+//       amplitudes: a 2D tensor map (row = tuple), boxes of 128 rows x 128 B
+//       in the 128-byte swizzle, so a converter lane reading its row's
+//       16-byte chunks meets the other lanes in distinct banks;
+//   q >= 5: member m of tuple t sits at t_low + 2^q m + 2^(q+K) t_high; a 3D
+//       map (low free bits, members, high free bits) with box
+//       (min(2^(q+1), 256) floats, 2^K, 2^(7 - min(q, 7))): the lanes of a
+//       warp read one member of 32 consecutive tuples, 256 contiguous bytes.
+// Warps 0-15 convert (warp w: TMEM lane quarter w mod 4, columns
+// (W/4)(w/4) ..), 16-23 drain the accumulators as in k_block_tc, 24 issues
+// the MMAs, 25 is the producer.  Every wait is bounded as in k_block_tc; the
+// producer waits (bounded) for its last copies before the CTA exits.
+
+constexpr int kTmaConvWarps = 16;
+constexpr int kTmaConv = kTmaConvWarps * 32;                 // 512
+constexpr int kTmaEpiWarp0 = kTmaConvWarps;                  // 16..23
+constexpr int kTmaMmaWarp = kTmaConvWarps + kBkEpiWarps;     // 24
+constexpr int kTmaProdWarp = kTmaMmaWarp + 1;                // 25
+constexpr int kTmaThreads = (kTmaProdWarp + 1) * 32;         // 832
+constexpr int kTmaRing = 4;                                  // raw tile stages
+
+enum { TMA_ROWS = 0,     // q = 0: row-major tuples, 2D map, 128-byte swizzle
+       TMA_MEMBERS = 1 };  // q >= 5: 3D map (low bits, members, high bits)
+
+template <int K>
+struct TmaSmem {
+  static constexpr int D = 1 << K, W = 2 * D;
+  static constexpr uint32_t RAW_BYTES = kTcRows * W * 4;     // 32 KB (K = 5)
+  static constexpr uint32_t RAW0 = 0;                          // ring, 1024-aligned stages
+  static constexpr uint32_t B_HI = kTmaRing * RAW_BYTES, B_LO = B_HI + W * W * 4;
+  static constexpr uint32_t ROWOFF = B_LO + W * W * 4;
+  static constexpr uint32_t DTAB = ROWOFF + kTcRows * 8;
+  static constexpr uint32_t OFFS = DTAB + 4 * 256 * 8;
+  // raw_full[R], raw_empty[R], afull[2], aempty[2], tfull[2], tempty[2], fin
+  static constexpr uint32_t MBAR = OFFS + D * 4;
+  static constexpr uint32_t FLAGS = MBAR + (2 * kTmaRing + 9) * 8;
+  static constexpr int SROW = D + 2;
+  static constexpr uint32_t STAGE = (FLAGS + 16 + 15) & ~15u;
+  static constexpr uint32_t BYTES = STAGE + kTcRows * SROW * 8 + 1024;
+  // tensor memory: accumulators at columns [0, 2W), A stages (hi | lo) at [2W, 6W)
+  static constexpr uint32_t TCOLS = 6 * W <= 256 ? 256 : 512;
+  __host__ __device__ static constexpr uint32_t a_col(int s) { return 2 * W + (uint32_t)s * 2 * W; }
+};
+
+template <int K>
+struct TmaArgs {
+  TcArgs<K> a;
+  int q;       // lowest target
+  int ql;      // min(q, 7): tuple-index bits below the targets inside a tile
+};
+
+__device__ __forceinline__ void mma_tf32_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}\n" ::"r"(mbar),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* map, int x, int y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const void* map, int x, int y, int z, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(mbar)
+      : "memory");
+}
+
+// 32 lanes x N consecutive 32-bit TMEM columns from registers (thread i -> lane base + i)
+template <int N>
+__device__ __forceinline__ void tmem_st(uint32_t taddr, const float* v);
+template <>
+__device__ __forceinline__ void tmem_st<16>(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};\n" ::"r"(taddr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
+      "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
+      : "memory");
+}
+template <>
+__device__ __forceinline__ void tmem_st<8>(uint32_t taddr, const float* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"r"(taddr),
+               "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+               : "memory");
+}
+
+template <int K, int CASE>
+__global__ void __launch_bounds__(kTmaThreads, 1)
+k_block_tma(const __grid_constant__ TmaArgs<K> ta, const __grid_constant__ CUtensorMap map) {
+  using L = TmaSmem<K>;
+  constexpr int D = L::D, W = L::W;
+  constexpr int CPW = W / 4;   // TMEM columns written per converter thread (16 or 8)
+  const TcArgs<K>& a = ta.a;
+
+  extern __shared__ unsigned char sm_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)sm_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* s_P = reinterpret_cast<uint64_t*>(sm + L::ROWOFF);
+  uint32_t* s_off = reinterpret_cast<uint32_t*>(sm + L::OFFS);
+  uint64_t* s_dtab = reinterpret_cast<uint64_t*>(sm + L::DTAB);
+  const uint32_t mb0 = smem_u32(sm + L::MBAR);
+  auto raw_full = [&](int r) { return mb0 + 8u * (uint32_t)r; };
+  auto raw_empty = [&](int r) { return mb0 + 8u * (uint32_t)(kTmaRing + r); };
+  auto afull = [&](int s) { return mb0 + 8u * (uint32_t)(2 * kTmaRing + s); };
+  auto aempty = [&](int s) { return mb0 + 8u * (uint32_t)(2 * kTmaRing + 2 + s); };
+  auto tfull = [&](int s) { return mb0 + 8u * (uint32_t)(2 * kTmaRing + 4 + s); };
+  auto tempty = [&](int s) { return mb0 + 8u * (uint32_t)(2 * kTmaRing + 6 + s); };
+  const uint32_t fin = mb0 + 8u * (uint32_t)(2 * kTmaRing + 8);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::FLAGS);
+  volatile int* abort = reinterpret_cast<volatile int*>(sm + L::FLAGS + 4);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // ---- setup: the matrix (hi / lo), offsets and tables for the epilogue, barriers, TMEM
+  for (int e = tid; e < W * W; e += kTmaThreads) {
+    const int n = e / W, kk = e % W;
+    const float v = a.b[n][kk], h = tf32_hi(v);
+    *reinterpret_cast<float*>(sm + L::B_HI + sw128_off(n, kk, W)) = h;
+    *reinterpret_cast<float*>(sm + L::B_LO + sw128_off(n, kk, W)) = v - h;
+  }
+  if (tid < D) s_off[tid] = a.off[tid];
+  if (tid < kTcRows) s_P[tid] = row_offset(tid, a);
+  for (int e = tid; e < 4 * 256; e += kTmaThreads) {
+    const int c = e >> 8, sh = 7 + 8 * c;
+    const uint64_t v = (uint64_t)(e & 255) << sh;
+    s_dtab[e] = (sh < a.lg) ? deposit_nb(v & ((1ull << a.lg) - 1ull), a.s) : 0;
+  }
+  if (tid == 0) {
+    for (int r = 0; r < kTmaRing; ++r) {
+      mbar_init(raw_full(r), 1);
+      mbar_init(raw_empty(r), kTmaConv);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(afull(s), kTmaConv);
+      mbar_init(aempty(s), 1);
+      mbar_init(tfull(s), 1);
+      mbar_init(tempty(s), (W / 32) * 4 * 32);
+    }
+    mbar_init(fin, 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kTmaMmaWarp) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(L::TCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint64_t stride_tiles = (uint64_t)gridDim.x;
+  auto tile_row0 = [&](int i) { return ((uint64_t)blockIdx.x + (uint64_t)i * stride_tiles) * kTcRows; };
+  auto tile_rows = [&](uint64_t t0) {
+    return a.total - t0 < (uint64_t)kTcRows ? (int)(a.total - t0) : kTcRows;
+  };
+
+  if (warp < kTmaConvWarps) {
+    // ================================================================ converters
+    const int qd = warp & 3, cg = warp >> 2;
+    const int t = qd * 32 + lane;            // this thread's tuple (row, TMEM lane)
+    const int m0 = cg * (CPW / 2);           // first member of this thread
+    uint32_t roff[CPW / 2];                  // byte offsets of the members inside a raw stage
+#pragma unroll
+    for (int j = 0; j < CPW / 2; ++j) {
+      const int m = m0 + j;
+      if (CASE == TMA_ROWS) {
+        const int b = m >> 4, c16 = (m & 15) >> 1;
+        roff[j] = (uint32_t)(b * kTcRows * 128 + t * 128 + ((c16 ^ (t & 7)) << 4) + (m & 1) * 8);
+      } else {
+        const int z = t >> ta.ql, x = t & ((1 << ta.ql) - 1);
+        roff[j] = (uint32_t)((((z * D + m) << ta.ql) + x) * 8);
+      }
+    }
+    const uint32_t lane_base = (uint32_t)(32 * qd) << 16;
+    for (int i = 0; tile_row0(i) < a.total; ++i) {
+      const int r = i % kTmaRing, s = i & 1;
+      float v[CPW], lo[CPW];
+      if (!mbar_wait(raw_full(r), (uint32_t)(i / kTmaRing) & 1u, abort)) break;
+      const unsigned char* raw = sm + L::RAW0 + (uint32_t)r * L::RAW_BYTES;
+#pragma unroll
+      for (int j = 0; j < CPW / 2; ++j) {
+        const float2 x = *reinterpret_cast<const float2*>(raw + roff[j]);
+        v[2 * j] = x.x;
+        v[2 * j + 1] = x.y;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(raw_empty(r));
+#pragma unroll
+      for (int e = 0; e < CPW; ++e) {
+        const float h = tf32_hi(v[e]);
+        lo[e] = v[e] - h;
+        v[e] = h;
+      }
+      // the A stage is free once the MMAs that read it two tiles ago have completed
+      if (!mbar_wait(aempty(s), ((uint32_t)(i >> 1) & 1u) ^ 1u, abort)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t col = L::a_col(s) + (uint32_t)(cg * CPW);
+      tmem_st<CPW>(tmem + lane_base + col, v);
+      tmem_st<CPW>(tmem + lane_base + col + W, lo);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(afull(s));
+    }
+  } else if (warp < kTmaMmaWarp) {
+    // ================================================================ epilogue (as in k_block_tc)
+    const int e = warp - kTmaEpiWarp0;
+    const int q = warp & 3;
+    const int c = 32 * (e >> 2);
+    const bool reads = c < W;
+    const int t = q * 32 + lane;
+    const int et = e * 32 + lane;
+    const uint64_t myP = s_P[t];
+    const bool staged = CASE == TMA_ROWS;   // rows are runs of 2^K >= 16 adjacent amplitudes
+    float2* stage = reinterpret_cast<float2*>(sm + L::STAGE);
+    for (int i = 0; tile_row0(i) < a.total; ++i) {
+      const int s = i & 1;
+      const uint64_t t0 = tile_row0(i);
+      const int rows = tile_rows(t0);
+      const bool valid = t < rows;
+      const uint64_t tb = tile_base(t0, a, s_dtab);
+      const uint64_t base = tb + myP;
+      if (bar_or(2, kBkEpiThreads, !mbar_wait(tfull(s), (i >> 1) & 1, abort))) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (reads) {
+        float y[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(s * W + c), y);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(tempty(s));
+        const int mm = c / 2;
+        if (staged) {
+#pragma unroll
+          for (int m = 0; m < 16; m += 2)
+            *reinterpret_cast<float4*>(stage + t * L::SROW + mm + m) =
+                make_float4(y[2 * m], y[2 * m + 1], y[2 * m + 2], y[2 * m + 3]);
+        } else if (valid) {
+#pragma unroll
+          for (int m = 0; m < 16; ++m) a.psi[base + s_off[mm + m]] = make_float2(y[2 * m], y[2 * m + 1]);
+        }
+      }
+      if (staged) {
+        bar_sync(2, kBkEpiThreads);
+        constexpr int hb = K - 1;
+#pragma unroll 4
+        for (int k = 0; k < D / 4; ++k) {
+          const int u = et + k * kBkEpiThreads;
+          const int qq = (u & ((1 << hb) - 1)) | ((u >> (hb + 7)) << hb);
+          const int tt = (u >> hb) & (kTcRows - 1);
+          if (tt < rows)
+            *reinterpret_cast<float4*>(a.psi + tb + s_P[tt] + s_off[2 * qq]) =
+                *reinterpret_cast<const float4*>(stage + tt * L::SROW + 2 * qq);
+        }
+        bar_sync(2, kBkEpiThreads);
+      }
+    }
+    __syncwarp();
+  } else if (warp == kTmaMmaWarp) {
+    // ================================================================ MMA issue (A from TMEM)
+    if (lane == 0) {
+      constexpr uint32_t idesc = tf32_idesc(W);
+      const uint32_t b_hi = smem_u32(sm + L::B_HI), b_lo = smem_u32(sm + L::B_LO);
+      bool issued = false;
+      for (int i = 0; tile_row0(i) < a.total; ++i) {
+        const int s = i & 1;
+        const uint32_t ph = (uint32_t)(i >> 1) & 1u;
+        if (!mbar_wait(afull(s), ph, abort)) break;
+        if (!mbar_wait(tempty(s), ph ^ 1u, abort)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + (uint32_t)(s * W);
+        const uint32_t ahi = tmem + L::a_col(s), alo = ahi + W;
+#pragma unroll
+        for (int ks = 0; ks < W / 8; ++ks) {
+          const uint32_t koff = (uint32_t)(ks & 3) * 32u;
+          const uint32_t bblk = (uint32_t)(ks >> 2) * (uint32_t)(W * 128);
+          const uint64_t dbh = sw128_desc(b_hi + bblk + koff), dbl = sw128_desc(b_lo + bblk + koff);
+          mma_tf32_ta(d, ahi + 8u * ks, dbh, idesc, ks > 0 ? 1u : 0u);
+          mma_tf32_ta(d, ahi + 8u * ks, dbl, idesc, 1u);
+          mma_tf32_ta(d, alo + 8u * ks, dbh, idesc, 1u);
+        }
+        mma_commit(aempty(s));
+        mma_commit(tfull(s));
+        issued = true;
+      }
+      if (issued) {
+        mma_commit(fin);
+        volatile int never = 0;
+        mbar_wait(fin, 0, &never);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ================================================================ producer (TMA)
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map)) : "memory");
+      int issued = 0;
+      for (int i = 0; tile_row0(i) < a.total; ++i) {
+        const int r = i % kTmaRing;
+        if (!mbar_wait(raw_empty(r), ((uint32_t)(i / kTmaRing) & 1u) ^ 1u, abort)) break;
+        const uint32_t dst = smem_u32(sm + L::RAW0 + (uint32_t)r * L::RAW_BYTES);
+        const uint64_t t0 = tile_row0(i);
+        mbar_expect_tx(raw_full(r), L::RAW_BYTES);
+        if (CASE == TMA_ROWS) {
+#pragma unroll
+          for (int b = 0; b < W / 32; ++b)
+            tma_load_2d(dst + (uint32_t)b * kTcRows * 128, &map, 32 * b, (int)t0, raw_full(r));
+        } else {
+          const uint64_t low = t0 & ((1ull << ta.q) - 1ull);
+          tma_load_3d(dst, &map, (int)(2 * low), 0, (int)(t0 >> ta.q), raw_full(r));
+        }
+        issued = i + 1;
+      }
+      // the last copies into every stage have landed before the CTA may exit
+      volatile int never = 0;
+      for (int j = issued > kTmaRing ? issued - kTmaRing : 0; j < issued; ++j)
+        mbar_wait(raw_full(j % kTmaRing), (uint32_t)(j / kTmaRing) & 1u, &never);
+    }
+    __syncwarp();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (tid == 0 && *abort) atomicExch(&g_tc_status, 1);
+  if (warp == kTmaMmaWarp)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::TCOLS));
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+static int g_tma_enabled = 1;  // TMA-fed kernel for consecutive targets (QS_OPT_TENSOR_CORES >= 1)
+
+// q: lowest target; the caller checked consecutive targets, no controls, a
+// uniform batch, and 2^(n-K) >= 128 tuples per register.
+template <int K>
+static int launch_tma(const TcArgs<K>& a, int n, int nreg, int q, cudaStream_t st, bool* done) {
+  using L = TmaSmem<K>;
+  *done = false;
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return QS_OK;
+  TmaArgs<K> ta;
+  ta.a = a;
+  ta.q = q;
+  ta.ql = std::min(q, 7);
+  CUtensorMap map;
+  memset(&map, 0, sizeof(map));
+  const uint64_t tuples = (uint64_t)nreg << (n - K);
+  CUresult rc;
+  if (q == 0) {
+    if (tuples >= (1ull << 31)) return QS_OK;
+    const cuuint64_t dims[2] = {(cuuint64_t)(2 << K), (cuuint64_t)tuples};
+    const cuuint64_t strides[1] = {(cuuint64_t)(8u << K)};
+    const cuuint32_t box[2] = {32, (cuuint32_t)kTcRows};
+    const cuuint32_t es[2] = {1, 1};
+    rc = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)a.psi, dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    if (q < 5 || q > 30 || q + K > n) return QS_OK;
+    const uint64_t high = tuples >> q;   // free-bit combinations above the targets, over all registers
+    if (high >= (1ull << 31)) return QS_OK;
+    const int ql = std::min(q, 7);
+    const cuuint64_t dims[3] = {(cuuint64_t)(2ull << q), (cuuint64_t)(1u << K), (cuuint64_t)high};
+    const cuuint64_t strides[2] = {(cuuint64_t)(8ull << q), (cuuint64_t)(8ull << (q + K))};
+    const cuuint32_t box[3] = {(cuuint32_t)std::min(2 << ql, 256), (cuuint32_t)(1u << K), (cuuint32_t)(1u << (7 - ql))};
+    const cuuint32_t es[3] = {1, 1, 1};
+    rc = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)a.psi, dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  if (rc != CUDA_SUCCESS) return QS_OK;   // not expressible as a tensor map: the register-fed kernel runs
+  int dev = 0, sms = 0;
+  QS_CUDA(cudaGetDevice(&dev));
+  QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const size_t smem = L::BYTES;
+  const uint64_t tiles = (a.total + kTcRows - 1) / kTcRows;
+  const unsigned grid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)sms);
+  if (q == 0) {
+    QS_CUDA(cudaFuncSetAttribute(k_block_tma<K, TMA_ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_block_tma<K, TMA_ROWS><<<grid, kTmaThreads, smem, st>>>(ta, map);
+  } else {
+    QS_CUDA(cudaFuncSetAttribute(k_block_tma<K, TMA_MEMBERS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_block_tma<K, TMA_MEMBERS><<<grid, kTmaThreads, smem, st>>>(ta, map);
+  }
+  QS_LAUNCHED();
+  *done = true;
+  return QS_OK;
+}
+
 template <int K>
 static int launch_tc_t(float2* psi, int n, int nreg, const Plan& p, cudaStream_t st) {
   constexpr int D = 1 << K;
@@ -570,6 +1001,15 @@ static int launch_tc_t(float2* psi, int n, int nreg, const Plan& p, cudaStream_t
   a.reg_stride = 1ull << n;
   a.total = (1ull << a.lg) * (uint64_t)nreg;
   if (a.total == 0) return QS_OK;
+  {
+    const int q = p.locs[order[0]];
+    const bool consecutive = p.locs[order[K - 1]] == q + K - 1;
+    if (g_tma_enabled && consecutive && p.ctrl_mask == 0 && n - K >= 7) {
+      bool done = false;
+      QS_TRY(launch_tma<K>(a, n, nreg, q, st, &done));
+      if (done) return QS_OK;
+    }
+  }
   if (a.lowbits >= 1) return launch_tc_mode<K, TC_PAIR_MEMBERS>(a, st);
   if (!(p.ctrl_mask & 1ull) && a.lg >= 1) return launch_tc_mode<K, TC_PAIR_TUPLES>(a, st);
   return launch_tc_mode<K, TC_SCALAR>(a, st);
@@ -899,6 +1339,11 @@ bool use_block_tc(int dtype, const Plan& p) {
     lo = std::min(lo, p.locs[j]);
     q0 = q0 || p.locs[j] == 0;
   }
+  // consecutive targets without controls take the TMA-fed kernel, faster than
+  // the CUDA-core kernel at every such placement measured (k = 4 and 5)
+  int hi = 0;
+  for (int j = 0; j < p.k; ++j) hi = std::max(hi, p.locs[j]);
+  if (g_tma_enabled && p.ctrl_mask == 0 && hi - lo == p.k - 1 && (lo == 0 || lo >= 5)) return true;
   if (p.k == 4) return q0;
   return q0 || lo < 5 || (p.ctrl_mask & 1ull);
 }

@@ -158,3 +158,31 @@ def test_block_full_size_n25_sampled(qs, locs):
     assert worst < TOL, worst
     # the whole state stays normalised (unitary block)
     assert abs(np.linalg.norm(out.astype(np.complex128)) - 1.0) < 1e-4
+
+
+@pytest.mark.parametrize("k", [4, 5])
+def test_tma_fed_blocks_consecutive_targets(qs, k):
+    """Consecutive targets q..q+k-1 without controls take the TMA-fed kernel
+    (q = 0: row-major tuples through a swizzled 2D map; q >= 5: a 3D map over
+    low bits, members and high bits, with 2^(7 - min(q, 7)) high rows per tile
+    when q < 7); n - k = 7 is one tile per register.  Uniform batches of three
+    registers, against the oracle."""
+    rs = np.random.default_rng(60 + k)
+    for n in (k + 7, k + 9, 16):
+        psi = [W.haar_state(n, seed=200 + r) for r in range(3)]
+        for q in sorted({0, 5, 6, 7, 8, n - k}):
+            if q + k > n or (0 < q < 5):
+                continue
+            locs = tuple(range(q, q + k))
+            if q % 2:
+                locs = locs[::-1]   # a permuted target order is the same kernel
+            U = rand_unitary(k, rs)
+            g = W.Gate("MATRIX", locs, matrix=U)
+            st = qs.State(n, dtype=torch.complex64, nbatch=3)
+            st.upload(np.concatenate(psi))
+            st.apply(g)
+            st.sync()
+            got = st.numpy().reshape(3, -1)
+            for r in range(3):
+                want = oracle.apply_circuit(psi[r], n, [g])
+                assert np.max(np.abs(got[r] - want)) < TOL, (n, locs, r)
