@@ -27,6 +27,7 @@
 // matrices are formed for each parameter vector.
 #include <chrono>
 #include <cstring>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -306,6 +307,105 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(const typename AmpOf<R>::
   }
 }
 
+// The same partials for complex64 supports of 1..3 qubits without staging:
+// each warp walks whole 128-tuple tiles; a group of SPLIT lanes shares one
+// tuple (lane j of the group takes psi members [j MPL, (j+1) MPL) and every
+// lambda member), so a lane keeps RPL x 2D FP32 products of its tuples in
+// registers (16 or 32).  Every 16 steps the lanes of a warp fold their FP32
+// sums with shuffles (fixed tree) and add them to per-warp FP64 accumulators
+// in shared memory; the warps are added in warp order at the end.
+template <int D>
+__global__ void __launch_bounds__(256, 3) k_gram_reg(const float2* __restrict__ psi, const float2* __restrict__ lam,
+                                                  const __grid_constant__ GramArgs<D> a, double* __restrict__ partials) {
+  static_assert(D == 2 || D == 4 || D == 8, "1..3-qubit supports");
+  constexpr int W2 = 2 * D, E = W2 * W2;
+  constexpr int SPLIT = D == 8 ? 8 : D / 2;       // lanes per tuple
+  constexpr int MPL = D / SPLIT;                   // psi members per lane
+  constexpr int RPL = 2 * MPL;                     // psi rows (re, im) per lane
+  constexpr int NACC = RPL * W2;                   // 16 / 32 / 32
+  constexpr int TPW = 32 / SPLIT;                  // tuples per warp step
+  constexpr int STEPS = kGramRows / TPW;           // steps per tile
+  constexpr int FLUSH = 16;                        // steps between FP64 folds
+  constexpr int NW = 256 / 32;
+  __shared__ double wacc[NW][E];
+  __shared__ uint64_t sP[kGramRows];
+  __shared__ uint32_t soff[D];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int j = lane % SPLIT, tup = lane / SPLIT;
+  for (int e = tid; e < NW * E; e += 256) (&wacc[0][0])[e] = 0.0;
+  if (tid < D) soff[tid] = a.off[tid];
+  if (tid < kGramRows) {
+    // offset of tile-local tuple t: deposit of t into the free bits (support bits zero)
+    sP[tid] = deposit((uint64_t)tid & ((1ull << (a.s.item_log2 < 7 ? a.s.item_log2 : 7)) - 1ull), a.s) & ~a.s.set_bits;
+  }
+  __syncthreads();
+  float acc[NACC];
+#pragma unroll
+  for (int e = 0; e < NACC; ++e) acc[e] = 0.f;
+  int since = 0;
+  auto flush = [&]() {
+#pragma unroll
+    for (int e = 0; e < NACC; ++e) {
+      float v = acc[e];
+#pragma unroll
+      for (int o = SPLIT; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      acc[e] = 0.f;
+      if (tup == 0) {
+        const int r = j * RPL + e / W2, c = e % W2;
+        wacc[warp][r * W2 + c] += (double)v;
+      }
+    }
+    since = 0;
+  };
+  const uint64_t ntiles = (a.total + kGramRows - 1) / kGramRows;
+  const uint64_t per_reg = 1ull << a.s.item_log2;
+  for (uint64_t tile = (uint64_t)blockIdx.x * NW + warp; tile < ntiles; tile += (uint64_t)gridDim.x * NW) {
+    const uint64_t t0 = tile * kGramRows;
+    const int rows = a.total - t0 < (uint64_t)kGramRows ? (int)(a.total - t0) : kGramRows;
+    // tile base: register offset + deposit of the tuple bits above the tile
+    const uint64_t r = t0 / per_reg, jj = t0 % per_reg;
+    const uint64_t tb = r * a.reg_stride + deposit(jj, a.s);
+    for (int st = 0; st < STEPS; ++st) {
+      const int t = st * TPW + tup;
+      float2 pv[MPL], lv[D];
+      if (t < rows) {
+        const uint64_t base = tb + sP[t];
+#pragma unroll
+        for (int m = 0; m < MPL; ++m) pv[m] = psi[base + soff[j * MPL + m]];
+#pragma unroll
+        for (int m = 0; m < D; ++m) lv[m] = lam[base + soff[m]];
+      } else {
+#pragma unroll
+        for (int m = 0; m < MPL; ++m) pv[m] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int m = 0; m < D; ++m) lv[m] = make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int m = 0; m < MPL; ++m) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          // rows 2m' (re), 2m'+1 (im) of psi member m' = j MPL + m; columns c (re) and D + c (im)
+          acc[(2 * m) * W2 + c] = fmaf(pv[m].x, lv[c].x, acc[(2 * m) * W2 + c]);
+          acc[(2 * m) * W2 + D + c] = fmaf(pv[m].x, lv[c].y, acc[(2 * m) * W2 + D + c]);
+          acc[(2 * m + 1) * W2 + c] = fmaf(pv[m].y, lv[c].x, acc[(2 * m + 1) * W2 + c]);
+          acc[(2 * m + 1) * W2 + D + c] = fmaf(pv[m].y, lv[c].y, acc[(2 * m + 1) * W2 + D + c]);
+        }
+      }
+      if (++since == FLUSH) flush();
+    }
+  }
+  flush();
+  __syncthreads();
+  // rows of this layout are (member, re/im) pairs; the partials use rows m (re) and D + m (im)
+  for (int e = tid; e < E; e += 256) {
+    const int r = e / W2, c = e % W2;
+    const int m = r >> 1, part = r & 1;
+    double v = 0.0;
+    for (int w = 0; w < NW; ++w) v += wacc[w][e];
+    partials[(size_t)blockIdx.x * E + (part * D + m) * W2 + c] = v;
+  }
+}
+
 // out[e] = sum over rows of partials[row][e]: one CTA per entry, rows strided
 // over the threads, then a fixed-shape tree (the result does not depend on timing)
 __global__ void __launch_bounds__(256) k_gram_fold(const double* __restrict__ partials, int nrows, int E,
@@ -401,9 +501,21 @@ int launch_gram(const void* psi, const void* lam, int n, const std::vector<int>&
       if ((m >> j) & 1) o |= 1ull << qubits[j];
     a.off[m] = (uint32_t)o;
   }
-  const size_t smem = 2 * (size_t)kGramRows * W2 * sizeof(R) + kGramRows * 8 + D * 4;
   int dev = 0, sms = 0, per_sm = 0;
   QS_CUDA(cudaGetDevice(&dev));
+  if constexpr (std::is_same<R, float>::value && (D == 2 || D == 4 || D == 8)) {
+    QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    QS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram_reg<D>, 256, 0));
+    if (per_sm < 1) return fail(QS_EDEVICE, "Gram kernel does not fit on an SM");
+    const uint64_t tiles = (a.total + kGramRows - 1) / kGramRows;
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((tiles + 7) / 8, (uint64_t)sms * per_sm));
+    k_gram_reg<D><<<grid, 256, 0, st>>>((const float2*)psi, (const float2*)lam, a, partials);
+    QS_LAUNCHED();
+    k_gram_fold<<<E, 256, 0, st>>>(partials, grid, E, folded);
+    QS_LAUNCHED();
+    return QS_OK;
+  }
+  const size_t smem = 2 * (size_t)kGramRows * W2 * sizeof(R) + kGramRows * 8 + D * 4;
   QS_CUDA(cudaFuncSetAttribute(k_gram<R, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   QS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram<R, D>, kGramThreads, smem));
