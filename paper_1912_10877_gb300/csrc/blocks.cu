@@ -309,30 +309,36 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(const typename AmpOf<R>::
 
 // The same partials for complex64 supports of 1..3 qubits without staging:
 // each warp walks whole 128-tuple tiles; a group of SPLIT lanes shares one
-// tuple (lane j of the group takes psi members [j MPL, (j+1) MPL) and every
-// lambda member), so a lane keeps RPL x 2D FP32 products of its tuples in
-// registers (16 or 32).  Every 16 steps the lanes of a warp fold their FP32
-// sums with shuffles (fixed tree) and add them to per-warp FP64 accumulators
-// in shared memory; the warps are added in warp order at the end.
+// tuple (lane j of the group takes psi rows [j RPL, (j+1) RPL) of the 2D
+// rows (member, re/im) and every lambda member), so a lane keeps RPL x 2D FP32
+// products of its tuples in registers (16 or 32).  Each iteration loads two
+// tuple steps before multiplying, so two steps of loads are in flight per
+// warp.  Every 16 steps the lanes of a warp fold their FP32 sums with
+// shuffles (fixed tree) and add them to per-warp FP64 accumulators in shared
+// memory; the warps are added in warp order at the end.
 template <int D>
 __global__ void __launch_bounds__(256, 3) k_gram_reg(const float2* __restrict__ psi, const float2* __restrict__ lam,
-                                                  const __grid_constant__ GramArgs<D> a, double* __restrict__ partials) {
+                                                     const __grid_constant__ GramArgs<D> a, double* __restrict__ partials) {
   static_assert(D == 2 || D == 4 || D == 8, "1..3-qubit supports");
   constexpr int W2 = 2 * D, E = W2 * W2;
-  constexpr int SPLIT = D == 8 ? 8 : D / 2;       // lanes per tuple
-  constexpr int MPL = D / SPLIT;                   // psi members per lane
-  constexpr int RPL = 2 * MPL;                     // psi rows (re, im) per lane
+  constexpr int SPLIT = D == 2 ? 1 : (D == 4 ? 2 : 8);   // lanes per tuple
+  constexpr int RPL = W2 / SPLIT;                  // psi rows per lane: 4, 4, 2
+  constexpr int MPL = (RPL + 1) / 2;               // psi members loaded per lane
   constexpr int NACC = RPL * W2;                   // 16 / 32 / 32
   constexpr int TPW = 32 / SPLIT;                  // tuples per warp step
-  constexpr int STEPS = kGramRows / TPW;           // steps per tile
+  constexpr int STEPS = kGramRows / TPW;           // steps per tile (even)
+  constexpr int UNR = 2;                           // steps loaded together
   constexpr int FLUSH = 16;                        // steps between FP64 folds
   constexpr int NW = 256 / 32;
-  __shared__ double wacc[NW][E];
-  __shared__ uint64_t sP[kGramRows];
-  __shared__ uint32_t soff[D];
+  static_assert(STEPS % UNR == 0 && FLUSH % UNR == 0, "step unrolling");
+  extern __shared__ __align__(16) unsigned char gsm_reg[];
+  double* wacc = reinterpret_cast<double*>(gsm_reg);                       // [NW][E]
+  uint64_t* sP = reinterpret_cast<uint64_t*>(wacc + NW * E);                // [kGramRows]
+  uint32_t* soff = reinterpret_cast<uint32_t*>(sP + kGramRows);             // [D]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int j = lane % SPLIT, tup = lane / SPLIT;
-  for (int e = tid; e < NW * E; e += 256) (&wacc[0][0])[e] = 0.0;
+  const int m0 = (j * RPL) >> 1;                   // first psi member of this lane
+  for (int e = tid; e < NW * E; e += 256) wacc[e] = 0.0;
   if (tid < D) soff[tid] = a.off[tid];
   if (tid < kGramRows) {
     // offset of tile-local tuple t: deposit of t into the free bits (support bits zero)
@@ -350,10 +356,7 @@ __global__ void __launch_bounds__(256, 3) k_gram_reg(const float2* __restrict__ 
 #pragma unroll
       for (int o = SPLIT; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       acc[e] = 0.f;
-      if (tup == 0) {
-        const int r = j * RPL + e / W2, c = e % W2;
-        wacc[warp][r * W2 + c] += (double)v;
-      }
+      if (tup == 0) wacc[warp * E + (j * RPL + e / W2) * W2 + e % W2] += (double)v;
     }
     since = 0;
   };
@@ -362,36 +365,35 @@ __global__ void __launch_bounds__(256, 3) k_gram_reg(const float2* __restrict__ 
   for (uint64_t tile = (uint64_t)blockIdx.x * NW + warp; tile < ntiles; tile += (uint64_t)gridDim.x * NW) {
     const uint64_t t0 = tile * kGramRows;
     const int rows = a.total - t0 < (uint64_t)kGramRows ? (int)(a.total - t0) : kGramRows;
-    // tile base: register offset + deposit of the tuple bits above the tile
     const uint64_t r = t0 / per_reg, jj = t0 % per_reg;
     const uint64_t tb = r * a.reg_stride + deposit(jj, a.s);
-    for (int st = 0; st < STEPS; ++st) {
-      const int t = st * TPW + tup;
-      float2 pv[MPL], lv[D];
-      if (t < rows) {
-        const uint64_t base = tb + sP[t];
+    for (int st = 0; st < STEPS; st += UNR) {
+      float2 pv[UNR][MPL], lv[UNR][D];
 #pragma unroll
-        for (int m = 0; m < MPL; ++m) pv[m] = psi[base + soff[j * MPL + m]];
+      for (int u = 0; u < UNR; ++u) {
+        const int t = (st + u) * TPW + tup;
+        const bool ok = t < rows;
+        const uint64_t base = tb + sP[ok ? t : 0];
 #pragma unroll
-        for (int m = 0; m < D; ++m) lv[m] = lam[base + soff[m]];
-      } else {
+        for (int m = 0; m < MPL; ++m) pv[u][m] = ok ? psi[base + soff[m0 + m]] : make_float2(0.f, 0.f);
 #pragma unroll
-        for (int m = 0; m < MPL; ++m) pv[m] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int m = 0; m < D; ++m) lv[m] = make_float2(0.f, 0.f);
+        for (int m = 0; m < D; ++m) lv[u][m] = ok ? lam[base + soff[m]] : make_float2(0.f, 0.f);
       }
 #pragma unroll
-      for (int m = 0; m < MPL; ++m) {
+      for (int u = 0; u < UNR; ++u) {
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-          // rows 2m' (re), 2m'+1 (im) of psi member m' = j MPL + m; columns c (re) and D + c (im)
-          acc[(2 * m) * W2 + c] = fmaf(pv[m].x, lv[c].x, acc[(2 * m) * W2 + c]);
-          acc[(2 * m) * W2 + D + c] = fmaf(pv[m].x, lv[c].y, acc[(2 * m) * W2 + D + c]);
-          acc[(2 * m + 1) * W2 + c] = fmaf(pv[m].y, lv[c].x, acc[(2 * m + 1) * W2 + c]);
-          acc[(2 * m + 1) * W2 + D + c] = fmaf(pv[m].y, lv[c].y, acc[(2 * m + 1) * W2 + D + c]);
+        for (int rr = 0; rr < RPL; ++rr) {
+          // local row rr is 2D row j RPL + rr: member (j RPL + rr) / 2, re (even) or im (odd)
+          const float v = (((j * RPL + rr) & 1) == 0) ? pv[u][rr >> 1].x : pv[u][rr >> 1].y;
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            acc[rr * W2 + c] = fmaf(v, lv[u][c].x, acc[rr * W2 + c]);
+            acc[rr * W2 + D + c] = fmaf(v, lv[u][c].y, acc[rr * W2 + D + c]);
+          }
         }
       }
-      if (++since == FLUSH) flush();
+      since += UNR;
+      if (since == FLUSH) flush();
     }
   }
   flush();
@@ -401,10 +403,13 @@ __global__ void __launch_bounds__(256, 3) k_gram_reg(const float2* __restrict__ 
     const int r = e / W2, c = e % W2;
     const int m = r >> 1, part = r & 1;
     double v = 0.0;
-    for (int w = 0; w < NW; ++w) v += wacc[w][e];
+    for (int w = 0; w < NW; ++w) v += wacc[w * E + e];
     partials[(size_t)blockIdx.x * E + (part * D + m) * W2 + c] = v;
   }
 }
+
+template <int D>
+constexpr size_t gram_reg_smem() { return sizeof(double) * 8 * (2 * D) * (2 * D) + 8 * kGramRows + 4 * D; }
 
 // out[e] = sum over rows of partials[row][e]: one CTA per entry, rows strided
 // over the threads, then a fixed-shape tree (the result does not depend on timing)
@@ -504,12 +509,14 @@ int launch_gram(const void* psi, const void* lam, int n, const std::vector<int>&
   int dev = 0, sms = 0, per_sm = 0;
   QS_CUDA(cudaGetDevice(&dev));
   if constexpr (std::is_same<R, float>::value && (D == 2 || D == 4 || D == 8)) {
+    constexpr size_t rsm = gram_reg_smem<D>();
     QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    QS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram_reg<D>, 256, 0));
+    QS_CUDA(cudaFuncSetAttribute(k_gram_reg<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+    QS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gram_reg<D>, 256, rsm));
     if (per_sm < 1) return fail(QS_EDEVICE, "Gram kernel does not fit on an SM");
     const uint64_t tiles = (a.total + kGramRows - 1) / kGramRows;
     const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((tiles + 7) / 8, (uint64_t)sms * per_sm));
-    k_gram_reg<D><<<grid, 256, 0, st>>>((const float2*)psi, (const float2*)lam, a, partials);
+    k_gram_reg<D><<<grid, 256, rsm, st>>>((const float2*)psi, (const float2*)lam, a, partials);
     QS_LAUNCHED();
     k_gram_fold<<<E, 256, 0, st>>>(partials, grid, E, folded);
     QS_LAUNCHED();
