@@ -304,6 +304,24 @@ __device__ __forceinline__ uint32_t thread_global(uint32_t tid, const TPhase& ph
   return b;
 }
 
+// shared-memory slot of amplitude j of a phase: swz is linear over XOR, so
+// slot(j) = swz(base) ^ (XOR of swz(offset of bit b) over the set bits b of j);
+// the four per-bit values stay in registers instead of reloading sroff[j]
+struct PhaseSlots {
+  uint32_t b, s0, s1, s2, s3;
+};
+__device__ __forceinline__ PhaseSlots phase_slots(uint32_t sb, const TPhase& ph) {
+  return PhaseSlots{sb, ph.sroff[1], ph.sroff[2], ph.sroff[4], ph.sroff[8]};
+}
+__device__ __forceinline__ uint32_t slot(const PhaseSlots& p, int j) {
+  uint32_t o = p.b;
+  if (j & 1) o ^= p.s0;
+  if (j & 2) o ^= p.s1;
+  if (j & 4) o ^= p.s2;
+  if (j & 8) o ^= p.s3;
+  return o;
+}
+
 // out-of-phase diagonal gate with phase-local controls: x_j *= f where (j & cm) == cv
 __device__ __forceinline__ void diag_masked(float2 (&x)[16], float2 f, int cm, int cv) {
 #pragma unroll
@@ -316,11 +334,11 @@ __device__ __noinline__ void run_phase_fwd(float2* sm, const TPhase* php, const 
   const TPhase& ph = *php;
   const int ntb = m - kRB;
   if (threadIdx.x < (1u << ntb)) {
-    const uint32_t sb = swz(phase_base(threadIdx.x, ph, ntb));
+    const PhaseSlots ps = phase_slots(swz(phase_base(threadIdx.x, ph, ntb)), ph);
     const uint32_t gb = thread_global(threadIdx.x, ph, ntb, tbase);
     float2 x[16];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) x[j] = sm[sb ^ ph.sroff[j]];
+    for (int j = 0; j < 16; ++j) x[j] = sm[slot(ps, j)];
     // factors of out-of-phase diagonal gates without phase-local controls are
     // scalars for this thread: they commute with the phase and are applied once
     float2 pend = make_float2(1.f, 0.f);
@@ -349,7 +367,7 @@ __device__ __noinline__ void run_phase_fwd(float2* sm, const TPhase* php, const 
       for (int j = 0; j < 16; ++j) x[j] = cmulf(x[j], pend);
     }
 #pragma unroll
-    for (int j = 0; j < 16; ++j) sm[sb ^ ph.sroff[j]] = x[j];
+    for (int j = 0; j < 16; ++j) sm[slot(ps, j)] = x[j];
   }
   __syncthreads();
 }
@@ -389,11 +407,11 @@ __device__ __noinline__ void run_phase_bwd(float2* sx, float2* sl, const TPhase*
   const int nbop = ph.nbop, bop0 = ph.bop0;
   float2 x[16], l[16];
   const uint32_t gb = active ? thread_global(threadIdx.x, ph, ntb, tbase) : 0u;
-  const uint32_t sb = active ? swz(phase_base(threadIdx.x, ph, ntb)) : 0u;
+  const PhaseSlots ps = phase_slots(active ? swz(phase_base(threadIdx.x, ph, ntb)) : 0u, ph);
   if (active) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-      const uint32_t o = sb ^ ph.sroff[j];
+      const uint32_t o = slot(ps, j);
       x[j] = sx[o];
       l[j] = sl[o];
     }
@@ -411,7 +429,7 @@ __device__ __noinline__ void run_phase_bwd(float2* sx, float2* sl, const TPhase*
   if (active) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-      const uint32_t o = sb ^ ph.sroff[j];
+      const uint32_t o = slot(ps, j);
       sx[o] = x[j];
       sl[o] = l[j];
     }
