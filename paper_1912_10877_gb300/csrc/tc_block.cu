@@ -90,13 +90,13 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
-// instruction descriptor, kind::tf32: D f32, A and B tf32, both K-major, N, M = 128
-__host__ __device__ constexpr uint32_t tf32_idesc(int n_dim) {
+// instruction descriptor, kind::tf32: D f32, A and B tf32, both K-major, N, M (128 by default)
+__host__ __device__ constexpr uint32_t tf32_idesc(int n_dim, int m_dim = kTcRows) {
   return (1u << 4)                            // bits 4-5: D format f32
          | (2u << 7)                          // bits 7-9: A format tf32
          | (2u << 10)                         // bits 10-12: B format tf32
          | ((uint32_t)(n_dim >> 3) << 17)     // bits 17-22: N / 8
-         | ((uint32_t)(kTcRows >> 4) << 24);  // bits 24-28: M / 16
+         | ((uint32_t)(m_dim >> 4) << 24);    // bits 24-28: M / 16
 }
 
 __device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
@@ -1024,9 +1024,10 @@ static int launch_tc_t(float2* psi, int n, int nreg, const Plan& p, cudaStream_t
 // A 128-tuple tile is staged transposed: rows are components (psi in rows
 // 0..63, lambda in rows 64..127, 4-qubit supports zero-padded), columns are the
 // tuples, in the K-major 128-byte-swizzle layout (kind::tf32 takes K-major
-// operands only).  One tcgen05.mma (M = 128, N = 64, K = 8 tuples) takes
-// A = rows 0..127 and B = rows 64..127; rows 0..63 of the accumulator are
-// psi^T lambda.  3xTF32 as in k_block_tc; FP32
+// operands only).  One tcgen05.mma (M = 64, N = 2^(K+1), K = 8 tuples) takes
+// A = rows 0..63 (psi^T) and B = rows 64.. (lambda^T): the accumulator is
+// psi^T lambda (an M = 128 MMA over rows 0..127 would spend half its work on
+// lambda^T lambda).  3xTF32 as in k_block_tc; FP32
 // accumulation in TMEM over groups of 8 tiles, flushed by the epilogue warps
 // into an FP64 matrix in shared memory, written per CTA for a fixed-order fold.
 
@@ -1200,24 +1201,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const __grid_constant
   } else if (warp < kTcMmaWarp) {
     // ================================================================ epilogue: FP32 groups into FP64
     const int q = warp - kTcEpiWarp0;
-    const int row = q * 32 + lane;  // TMEM lane = component of psi (rows < W are used)
+    // M = 64 accumulator: row r sits in TMEM lane 32 (r / 16) + r mod 16 (measured on
+    // GB300), so lanes 0..15 of every lane quarter hold rows 16 q .. 16 q + 15
+    const int row = 16 * q + lane;
+    const bool valid_row = lane < 16 && row < W;
     for (int g = 0; g < ngroups; ++g) {
       const int b = g & 1;
       if (!__all_sync(0xffffffffu, mbar_wait(tfull(b), (uint32_t)(g >> 1) & 1u, abort))) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       // 32 columns at a time into the FP64 row; the buffer is released after the last
 #pragma unroll
-      for (int c0 = 0; c0 < 64; c0 += 32) {
+      for (int c0 = 0; c0 < W; c0 += 32) {
         float y[32];
-        if (q < 2) {
-          tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 64 + c0), y);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        }
-        if (c0 + 32 == 64) {
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 64 + c0), y);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (c0 + 32 == W) {
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           mbar_arrive(tempty(b));
         }
-        if (q < 2 && row < W && c0 < W) {
+        if (valid_row) {
 #pragma unroll
           for (int c = 0; c < 32; ++c) acc[row * L::ACC_LD + c0 + c] += (double)y[c];
         }
@@ -1227,7 +1229,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const __grid_constant
   } else {
     // ================================================================ MMA issue
     if (lane == 0) {
-      constexpr uint32_t idesc = tf32_idesc(64);
+      // D (64 x W) = psi^T (rows 0..63) x lambda^T (rows 64..64+W-1): M = 64, N = W
+      constexpr uint32_t idesc = tf32_idesc(W, 64);
       const uint32_t base_hi = smem_u32(sm + L::HI), base_lo = smem_u32(sm + L::LO);
       const uint32_t lam_off = 64u * 128u;  // lambda: rows 64.. of every 128-row column block
       bool issued = false;
