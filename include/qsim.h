@@ -164,9 +164,8 @@ int qs_state_axpy(qs_state* y, double alpha_re, double alpha_im, const qs_state*
  * complex64 states.  2: always the tensor cores (complex product as a real
  * 3xTF32 GEMM, FP32 accuracy); 0: always the CUDA cores; 1 (default): the
  * tensor cores for the target placements where they measured faster: targets
- * q..q+k-1 without controls with q = 0 or q >= 3 (read by TMA tensor copies),
- * other 5-qubit blocks unless every target is at qubit 5 or above, other
- * 4-qubit blocks on qubit 0. */
+ * q..q+k-1 without controls (read by TMA tensor copies), other 5-qubit blocks
+ * unless every target is at qubit 5 or above, other 4-qubit blocks on qubit 0. */
 #define QS_OPT_TENSOR_CORES 1
 int qs_set_option(int option, int value);
 int qs_get_option(int option, int* value);

@@ -546,11 +546,13 @@ static int launch_tc_mode(const TcArgs<K>& a, cudaStream_t st) {
 //       amplitudes: a 2D tensor map (row = tuple), boxes of 128 rows x 128 B
 //       in the 128-byte swizzle, so a converter lane reading its row's
 //       16-byte chunks meets the other lanes in distinct banks;
-//   q >= 3: member m of tuple t sits at t_low + 2^q m + 2^(q+K) t_high; a 3D
+//   q >= 1: member m of tuple t sits at t_low + 2^q m + 2^(q+K) t_high; a 3D
 //       map (low free bits, members, high free bits) with box
 //       (min(2^(q+1), 256) floats, 2^K, 2^(7 - min(q, 7))): the lanes of a
 //       warp read one member of 32 consecutive tuples, in runs of 2^min(q, 5)
-//       lanes at consecutive addresses (2^(5-q)-way bank conflicts for q < 5).
+//       lanes at consecutive addresses (2^(5-q)-way bank conflicts for q < 5;
+//       at q = 1, 2 still faster than the register-fed kernel: 1.13 vs 1.6 ms
+//       per 5-qubit block at n = 28).
 // Warps 0-15 convert (warp w: TMEM lane quarter w mod 4, columns
 // (W/4)(w/4) ..), 16-23 drain the accumulators as in k_block_tc, 24 issues
 // the MMAs, 25 is the producer.  Every wait is bounded as in k_block_tc; the
@@ -930,7 +932,7 @@ static int launch_tma(const TcArgs<K>& a, int n, int nreg, int q, cudaStream_t s
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   } else {
-    if (q < 3 || q > 30 || q + K > n) return QS_OK;
+    if (q < 1 || q > 30 || q + K > n) return QS_OK;
     const uint64_t high = tuples >> q;   // free-bit combinations above the targets, over all registers
     if (high >= (1ull << 31)) return QS_OK;
     const int ql = std::min(q, 7);
@@ -1347,7 +1349,7 @@ bool use_block_tc(int dtype, const Plan& p) {
   // the CUDA-core kernel at every such placement measured (k = 4 and 5)
   int hi = 0;
   for (int j = 0; j < p.k; ++j) hi = std::max(hi, p.locs[j]);
-  if (g_tma_enabled && p.ctrl_mask == 0 && hi - lo == p.k - 1 && (lo == 0 || lo >= 3)) return true;
+  if (g_tma_enabled && p.ctrl_mask == 0 && hi - lo == p.k - 1) return true;
   if (p.k == 4) return q0;
   return q0 || lo < 5 || (p.ctrl_mask & 1ull);
 }
