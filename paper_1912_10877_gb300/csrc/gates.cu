@@ -17,6 +17,8 @@
 #include <cmath>
 #include <cstring>
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace qs {
@@ -188,6 +190,31 @@ k_gatek(c2_t<R>* __restrict__ psi, uint64_t nitems, IdxSpec s, const __grid_cons
   }
 }
 
+// complex64 dense 2- and 3-qubit gates whose targets and controls leave qubit 0
+// free: items 2i and 2i + 1 are adjacent amplitudes of every member, so a
+// thread takes both tuples with one 16-byte access per member
+template <int K>
+__global__ void __launch_bounds__(kThreads)
+k_gatek_pair(float2* __restrict__ psi, uint64_t npairs, IdxSpec s, const __grid_constant__ MatK<float, K> M) {
+  constexpr int D = 1 << K;
+  const uint64_t pi = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (pi >= npairs) return;
+  const uint64_t base = item_index(2 * pi, s);
+  float4 v[D];
+#pragma unroll
+  for (int m = 0; m < D; ++m) v[m] = *reinterpret_cast<const float4*>(psi + base + M.off[m]);
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      a0 = cfma(M.m[m * D + j], make_float2(v[j].x, v[j].y), a0);
+      a1 = cfma(M.m[m * D + j], make_float2(v[j].z, v[j].w), a1);
+    }
+    *reinterpret_cast<float4*>(psi + base + M.off[m]) = make_float4(a0.x, a0.y, a1.x, a1.y);
+  }
+}
+
 // ------------------------------------------------------------------ launchers
 
 static inline unsigned blocks_for(uint64_t items, int per_block) {
@@ -227,6 +254,13 @@ static int launch_k_t(c2_t<R>* psi, int n, int nreg, const Plan& p, cudaStream_t
   QS_TRY(make_idx(n, locmask | p.ctrl_mask, p.ctrl_vals, &s));
   const uint64_t items = (uint64_t)nreg << s.item_log2;
   if (items == 0) return QS_OK;
+  if constexpr (std::is_same<R, float>::value && OP == OP_DENSEK && (K == 2 || K == 3)) {
+    if (!((locmask | p.ctrl_mask) & 1ull) && s.item_log2 >= 1) {
+      k_gatek_pair<K><<<blocks_for(items / 2, kThreads), kThreads, 0, st>>>(psi, items / 2, s, M);
+      QS_LAUNCHED();
+      return QS_OK;
+    }
+  }
   k_gatek<R, K, OP><<<blocks_for(items, kThreads), kThreads, 0, st>>>(psi, items, s, M);
   QS_LAUNCHED();
   return QS_OK;
