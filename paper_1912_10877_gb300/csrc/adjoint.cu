@@ -81,6 +81,63 @@ k_adjoint_param(double2* __restrict__ psi, double2* __restrict__ lam, uint64_t n
   }
 }
 
+// Single-target parameterised gates in structured forms (FP64 is scarce on
+// this part: the dense 2x2 path spends 64 FP64 multiply-adds per pair):
+//   ADJ_DIAG: U^dag = diag(u0, u3), H = diag(g0, g3) real (Rz, shift, phase):
+//             ~20 per pair;
+//   ADJ_RX:   U^dag = [[c, i s], [i s, c]], H = X (Rx): ~24 per pair.
+enum { ADJ_DIAG = 0, ADJ_RX = 1 };
+
+struct AdjForm1 {
+  double2 u0, u3;   // ADJ_DIAG: the diagonal of U^dag
+  double g0, g3;    // ADJ_DIAG: the diagonal of H
+  double c, s;      // ADJ_RX: U^dag = [[c, i s], [i s, c]]
+  uint64_t off1;    // offset of the target bit
+};
+
+template <int FORM>
+__global__ void __launch_bounds__(kAdjThreads)
+k_adjoint_param1(double2* __restrict__ psi, double2* __restrict__ lam, uint64_t nitems, IdxSpec s,
+                 const __grid_constant__ AdjForm1 F, double* __restrict__ partials) {
+  double acc = 0.0;
+  for (uint64_t it = (uint64_t)blockIdx.x * kAdjThreads + threadIdx.x; it < nitems;
+       it += (uint64_t)gridDim.x * kAdjThreads) {
+    const uint64_t b0 = item_index(it, s), b1 = b0 + F.off1;
+    double2 x0 = psi[b0], x1 = psi[b1], l0 = lam[b0], l1 = lam[b1];
+    if (FORM == ADJ_DIAG) {
+      // Im conj(l) H x with H diagonal and real
+      acc = fma(F.g0, fma(l0.x, x0.y, -l0.y * x0.x), acc);
+      acc = fma(F.g3, fma(l1.x, x1.y, -l1.y * x1.x), acc);
+      x0 = cmul(F.u0, x0);
+      x1 = cmul(F.u3, x1);
+      l0 = cmul(F.u0, l0);
+      l1 = cmul(F.u3, l1);
+    } else {
+      // Im (conj(l0) x1 + conj(l1) x0) for H = X
+      acc += fma(l0.x, x1.y, -l0.y * x1.x) + fma(l1.x, x0.y, -l1.y * x0.x);
+      const double c = F.c, sn = F.s;
+      const double2 nx0 = make_double2(fma(c, x0.x, -sn * x1.y), fma(c, x0.y, sn * x1.x));
+      const double2 nx1 = make_double2(fma(c, x1.x, -sn * x0.y), fma(c, x1.y, sn * x0.x));
+      const double2 nl0 = make_double2(fma(c, l0.x, -sn * l1.y), fma(c, l0.y, sn * l1.x));
+      const double2 nl1 = make_double2(fma(c, l1.x, -sn * l0.y), fma(c, l1.y, sn * l0.x));
+      x0 = nx0; x1 = nx1; l0 = nl0; l1 = nl1;
+    }
+    psi[b0] = x0;
+    psi[b1] = x1;
+    lam[b0] = l0;
+    lam[b1] = l1;
+  }
+  __shared__ double red[kAdjThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < kAdjThreads / 32; ++w) v += red[w];
+    partials[blockIdx.x] = v;
+  }
+}
+
 // grad[param] += scale * (pairwise fold of partials[0..n))
 __global__ void k_fold_into(const double* __restrict__ partials, int n, double scale, double* __restrict__ grad,
                             int param) {
@@ -94,10 +151,49 @@ __global__ void k_fold_into(const double* __restrict__ partials, int n, double s
   if (threadIdx.x == 0) grad[param] += scale * buf[0];
 }
 
+// the structured form of a single-target gate, or -1
+static int adj_form1(const std::vector<cd>& G, const std::vector<cd>& Ud, AdjForm1* F) {
+  const cd z(0, 0);
+  if (G[1] == z && G[2] == z && G[0].imag() == 0 && G[3].imag() == 0 && Ud[1] == z && Ud[2] == z) {
+    F->u0 = make_double2(Ud[0].real(), Ud[0].imag());
+    F->u3 = make_double2(Ud[3].real(), Ud[3].imag());
+    F->g0 = G[0].real();
+    F->g3 = G[3].real();
+    return ADJ_DIAG;
+  }
+  if (G[0] == z && G[3] == z && G[1] == cd(1, 0) && G[2] == cd(1, 0) && Ud[0] == Ud[3] && Ud[0].imag() == 0 &&
+      Ud[1] == Ud[2] && Ud[1].real() == 0) {
+    F->c = Ud[0].real();
+    F->s = Ud[1].imag();
+    return ADJ_RX;
+  }
+  return -1;
+}
+
 template <int K>
 static int launch_adjoint_param(double2* psi, double2* lam, int n, const qs_gate_desc& g,
                                 const std::vector<cd>& G, const std::vector<cd>& Ud, double* partials,
                                 double* dgrad, double cfac, cudaStream_t st) {
+  if constexpr (K == 1) {
+    AdjForm1 F;
+    memset(&F, 0, sizeof(F));
+    const int form = adj_form1(G, Ud, &F);
+    if (form >= 0) {
+      F.off1 = 1ull << g.locs[0];
+      IdxSpec s;
+      QS_TRY(make_idx(n, F.off1 | g.ctrl_mask, g.ctrl_vals & g.ctrl_mask, &s));
+      const uint64_t items = 1ull << s.item_log2;
+      const int nblk = (int)std::min<uint64_t>(kAdjMaxBlocks, std::max<uint64_t>(1, (items + kAdjThreads * 4 - 1) / (kAdjThreads * 4)));
+      if (form == ADJ_DIAG)
+        k_adjoint_param1<ADJ_DIAG><<<nblk, kAdjThreads, 0, st>>>(psi, lam, items, s, F, partials);
+      else
+        k_adjoint_param1<ADJ_RX><<<nblk, kAdjThreads, 0, st>>>(psi, lam, items, s, F, partials);
+      QS_LAUNCHED();
+      k_fold_into<<<1, 256, 0, st>>>(partials, nblk, 2.0 * cfac, dgrad, g.param);
+      QS_LAUNCHED();
+      return QS_OK;
+    }
+  }
   AdjMat<K> M;
   memset(&M, 0, sizeof(M));
   constexpr int D = 1 << K;
