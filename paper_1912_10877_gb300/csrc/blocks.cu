@@ -82,6 +82,41 @@ void plan_blocks(const qs_circuit* c, int kmax, std::vector<Block>& out) {
     open.swap(rest);
   }
   for (Block& b : open) out.push_back(std::move(b));
+  // Commutation-aware merging: block j may move earlier past blocks whose
+  // support is disjoint from its own (they commute), so it joins the earliest
+  // block it can reach whose union with it still spans at most kmax qubits
+  // (the nearest earlier block that shares a qubit with j ends the search).
+  // The greedy pass above closes every open block a gate touches when their
+  // union is too wide, which leaves many 1-3-qubit blocks; each costs a full
+  // pass over the state, as much as a 5-qubit block.
+  bool changed = true;
+  while (changed) {
+    changed = false;
+    for (size_t j = 1; j < out.size();) {
+      const uint64_t sj = out[j].support;
+      long best = -1;
+      if (popc(sj) <= kmax) {
+        for (long i = (long)j - 1; i >= 0; --i) {
+          const uint64_t si = out[(size_t)i].support;
+          if (popc(si | sj) <= kmax) {
+            best = i;
+            if (si & sj) break;
+          } else if (si & sj) {
+            break;
+          }
+        }
+      }
+      if (best >= 0) {
+        Block& t = out[(size_t)best];
+        t.support |= sj;
+        t.gates.insert(t.gates.end(), out[j].gates.begin(), out[j].gates.end());
+        out.erase(out.begin() + (long)j);
+        changed = true;
+      } else {
+        ++j;
+      }
+    }
+  }
 }
 
 // M <- G M for a gate G (matrix U over targets tpos, controls cmask/cval) on
