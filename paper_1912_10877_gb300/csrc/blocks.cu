@@ -69,16 +69,34 @@ void plan_blocks(const qs_circuit* c, int kmax, std::vector<Block>& out) {
       open.swap(rest);
       continue;
     }
+    // The union is too wide.  Keep the widest touched block that can still take
+    // the gate open and close the other touched blocks (open blocks are
+    // disjoint, so the closed ones commute with it and may be applied first);
+    // if none can take it, close them all and start a block with the gate.
+    long keep = -1;
+    for (size_t i = 0; i < open.size(); ++i)
+      if ((open[i].support & q) && popc(open[i].support | q) <= kmax &&
+          (keep < 0 || popc(open[i].support) > popc(open[(size_t)keep].support)))
+        keep = (long)i;
     std::vector<Block> rest;
-    for (Block& b : open) {
+    for (size_t i = 0; i < open.size(); ++i) {
+      Block& b = open[i];
+      if ((long)i == keep) continue;
       if (b.support & q) out.push_back(std::move(b));
       else rest.push_back(std::move(b));
     }
-    Block nb;
-    nb.support = q;
-    nb.gates.push_back(gi);
-    if (popc(q) > kmax) out.push_back(std::move(nb));  // wider than k: stays a gate of its own
-    else rest.push_back(std::move(nb));
+    if (keep >= 0) {
+      Block kb = std::move(open[(size_t)keep]);
+      kb.support |= q;
+      kb.gates.push_back(gi);
+      rest.push_back(std::move(kb));
+    } else {
+      Block nb;
+      nb.support = q;
+      nb.gates.push_back(gi);
+      if (popc(q) > kmax) out.push_back(std::move(nb));  // wider than k: stays a gate of its own
+      else rest.push_back(std::move(nb));
+    }
     open.swap(rest);
   }
   for (Block& b : open) out.push_back(std::move(b));
@@ -89,6 +107,8 @@ void plan_blocks(const qs_circuit* c, int kmax, std::vector<Block>& out) {
   // The greedy pass above closes every open block a gate touches when their
   // union is too wide, which leaves many 1-3-qubit blocks; each costs a full
   // pass over the state, as much as a 5-qubit block.
+  // Then the mirror image: block i may move later past disjoint blocks and join
+  // the latest block it can reach (its gates go first in the merged block).
   bool changed = true;
   while (changed) {
     changed = false;
@@ -114,6 +134,27 @@ void plan_blocks(const qs_circuit* c, int kmax, std::vector<Block>& out) {
         changed = true;
       } else {
         ++j;
+      }
+    }
+    for (long i = (long)out.size() - 2; i >= 0; --i) {
+      const uint64_t si = out[(size_t)i].support;
+      if (popc(si) > kmax) continue;
+      long best = -1;
+      for (size_t j = (size_t)i + 1; j < out.size(); ++j) {
+        const uint64_t sj = out[j].support;
+        if (popc(si | sj) <= kmax) {
+          best = (long)j;
+          if (si & sj) break;
+        } else if (si & sj) {
+          break;
+        }
+      }
+      if (best >= 0) {
+        Block& t = out[(size_t)best];
+        t.support |= si;
+        t.gates.insert(t.gates.begin(), out[(size_t)i].gates.begin(), out[(size_t)i].gates.end());
+        out.erase(out.begin() + i);
+        changed = true;
       }
     }
   }
