@@ -90,6 +90,26 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
+// K-major 32-byte-swizzle layout for operands read 8 tf32 (32 bytes) per row
+// per MMA: K step ks of a `rows`-row operand is a block of rows x 32 bytes at
+// ks x rows x 32, 8-row atoms 256 bytes apart, 16-byte chunk index XOR row bit 2
+// (with the 128-byte swizzle a K = 8 MMA reads 32 of every 128-byte row, and
+// MMAs with both operands in shared memory ran at half the rate of the block
+// kernel's, whose A operand is in tensor memory)
+__host__ __device__ __forceinline__ uint32_t sw32_off(int row, int k, int rows) {
+  const int ks = k >> 3, kk = k & 7;
+  return (uint32_t)(ks * rows * 32 + row * 32 + ((((kk >> 2) & 1) ^ ((row >> 2) & 1)) << 4) + ((kk & 3) << 2));
+}
+__device__ __forceinline__ uint64_t sw32_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address / 16
+  d |= (uint64_t)1u << 16;                   // leading byte offset (unused when swizzled)
+  d |= (uint64_t)(256u >> 4) << 32;          // stride byte offset: 8-row atoms of 8 x 32 bytes
+  d |= (uint64_t)1u << 46;                   // version
+  d |= (uint64_t)6u << 61;                   // 32-byte swizzle
+  return d;
+}
+
 // instruction descriptor, kind::tf32: D f32, A and B tf32, both K-major, N, M (128 by default)
 __host__ __device__ constexpr uint32_t tf32_idesc(int n_dim, int m_dim = kTcRows) {
   return (1u << 4)                            // bits 4-5: D format f32
@@ -1316,11 +1336,341 @@ static int launch_gram_tc_t(const float2* psi, const float2* lam, int n, const i
   return launch_gram_tc_mode<K, TC_SCALAR>(a, lam, partials, grid_out, st);
 }
 
+// ------------------------------------------------------------------ TMA-fed Gram on consecutive supports
+//
+// The same Gram matrix for supports q..q+K-1 with the loads done by TMA: a
+// producer thread copies each 32-tuple tile of psi and of lambda into an
+// eight-stage ring, 128 KB in flight per SM (the register-held loads of
+// k_gram_tc, 64 KB in flight, bound it to ~21 GB/s per SM, about 3 TB/s, and
+// so did a two-stage ring), sixteen converter warps write it transposed and split (hi / lo)
+// into one of two operand stages (a warp step writes one 128-byte row segment:
+// 32 tuples of one component).  A = [psi_hi^T; psi_lo^T] fills all M = 128
+// rows, and two MMAs per 8 tuples (B = lambda_hi^T, then lambda_lo^T) give
+// rows r + rows r + 64 = psi^T lambda to FP32 accuracy (an M = 64 MMA over
+// psi^T alone cost about as much as an M = 128 one: measured 150 TFLOP/s
+// against 300 for the M = 128 block kernel).  Raw layouts as in k_block_tma:
+// q = 0 row-major tuples (2D map, 128-byte swizzle), q >= 1 members x tuples
+// (3D map; box (min(2^(q+1), 64) floats, 2^K, 2^(5 - min(q, 5)))).
+constexpr int kGtTuples = 32;
+constexpr int kGtRing = 4;
+constexpr int kGtStages = 4;                     // operand stages (MMA completion runs several tiles behind)
+constexpr int kGtGroup = 32;                     // tiles per FP32 accumulation group (1024 tuples)
+constexpr int kGtConvWarps = 16;
+constexpr int kGtConv = kGtConvWarps * 32;
+constexpr int kGtEpiWarp0 = kGtConvWarps;        // 16..19
+constexpr int kGtMmaWarp = kGtConvWarps + 4;     // 20
+constexpr int kGtProdWarp = kGtMmaWarp + 1;      // 21
+constexpr int kGtThreads = (kGtProdWarp + 1) * 32;
+
+template <int K>
+struct GramTmaSmem {
+  static constexpr int D = 1 << K, W = 2 * D;
+  static constexpr uint32_t RAW_STATE = kGtTuples * W * 4;               // one state's tile: 8 KB (K = 5)
+  static constexpr uint32_t RAW_STAGE = 2 * RAW_STATE;                   // psi then lambda
+  static constexpr uint32_t OP_BYTES = kTcRows * kGtTuples * 4;          // 128 rows x 32 tuples: 16 KB
+  static constexpr uint32_t RAW0 = 0;
+  __host__ __device__ static constexpr uint32_t raw(int r) { return RAW0 + (uint32_t)r * 16384u; }
+  // stage s: A = [psi_hi^T; psi_lo^T] at op_a(s), B = [lambda_hi^T; lambda_lo^T] after it
+  static constexpr uint32_t OP0 = kGtRing * 16384u;
+  static constexpr uint32_t OP_END = OP0 + kGtStages * 2 * OP_BYTES;
+  __host__ __device__ static constexpr uint32_t op_a(int s) { return OP0 + (uint32_t)s * 2 * OP_BYTES; }
+  static constexpr uint32_t ACC = OP_END;                                // FP64 [64][65]
+  static constexpr int ACC_LD = 65;
+  // raw_full[R], raw_empty[R], op_full[S], op_empty[S], tfull[2], tempty[2], fin
+  static constexpr uint32_t MBAR = ACC + 64 * ACC_LD * 8;
+  static constexpr uint32_t FLAGS = MBAR + (2 * kGtRing + 2 * kGtStages + 5) * 8;
+  static constexpr uint32_t BYTES = FLAGS + 16 + 1024;
+};
+
+template <int K, int CASE>
+__global__ void __launch_bounds__(kGtThreads, 1)
+k_gram_tma(const __grid_constant__ CUtensorMap map_psi, const __grid_constant__ CUtensorMap map_lam, uint64_t total,
+           int q, double* partials) {
+  using L = GramTmaSmem<K>;
+  constexpr int D = L::D, W = L::W;
+  constexpr int GT = kGtTuples;
+  extern __shared__ unsigned char sm_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)sm_raw + 1023) & ~(uintptr_t)1023);
+  double* acc = reinterpret_cast<double*>(sm + L::ACC);
+  const uint32_t mb0 = smem_u32(sm + L::MBAR);
+  auto raw_full = [&](int r) { return mb0 + 8u * (uint32_t)r; };
+  auto raw_empty = [&](int r) { return mb0 + 8u * (uint32_t)(kGtRing + r); };
+  auto op_full = [&](int s) { return mb0 + 8u * (uint32_t)(2 * kGtRing + s); };
+  auto op_empty = [&](int s) { return mb0 + 8u * (uint32_t)(2 * kGtRing + kGtStages + s); };
+  auto tfull = [&](int b) { return mb0 + 8u * (uint32_t)(2 * kGtRing + 2 * kGtStages + b); };
+  auto tempty = [&](int b) { return mb0 + 8u * (uint32_t)(2 * kGtRing + 2 * kGtStages + 2 + b); };
+  const uint32_t fin = mb0 + 8u * (uint32_t)(2 * kGtRing + 2 * kGtStages + 4);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L::FLAGS);
+  volatile int* abort = reinterpret_cast<volatile int*>(sm + L::FLAGS + 4);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ql = q < 5 ? q : 5;
+
+  // ---- setup: zero operand stages (4-qubit supports leave rows unused), FP64 accumulator, barriers, TMEM
+  for (uint32_t e = tid; e < kGtStages * 2 * L::OP_BYTES / 16; e += kGtThreads)
+    reinterpret_cast<float4*>(sm + L::OP0)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int e = tid; e < 64 * L::ACC_LD; e += kGtThreads) acc[e] = 0.0;
+  if (tid == 0) {
+    for (int r = 0; r < kGtRing; ++r) {
+      mbar_init(raw_full(r), 1);
+      mbar_init(raw_empty(r), kGtConvWarps);
+    }
+    for (int r = 0; r < kGtStages; ++r) {
+      mbar_init(op_full(r), kGtConvWarps);
+      mbar_init(op_empty(r), 1);
+    }
+    for (int r = 0; r < 2; ++r) {
+      mbar_init(tfull(r), 1);
+      mbar_init(tempty(r), 4 * 32);
+    }
+    mbar_init(fin, 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kGtMmaWarp) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(128u));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint64_t stride_tiles = (uint64_t)gridDim.x;
+  auto tile_t0 = [&](int i) { return ((uint64_t)blockIdx.x + (uint64_t)i * stride_tiles) * GT; };
+  int ntiles = 0;
+  while (tile_t0(ntiles) < total) ++ntiles;
+  const int ngroups = (ntiles + kGtGroup - 1) / kGtGroup;
+
+  if (warp < kGtConvWarps) {
+    // ================================================================ converters
+    // unit u = warp + 16 j (j < 8): state (psi / lambda), 4 components c0..c0+3 and one K
+    // step of 8 tuples; lane = 8 (component offset) + tuple offset.  A warp writes the
+    // hi rows c0..c0+3 (one 128-byte run) and the lo rows 64 + c0.. of its state's operand.
+    const int lc = lane >> 3, lt = lane & 7;
+    for (int i = 0; i < ntiles; ++i) {
+      const int r0 = i % kGtRing, s = i % kGtStages;
+      if (!mbar_wait(raw_full(r0), (uint32_t)(i / kGtRing) & 1u, abort)) break;
+      const unsigned char* raw = sm + L::raw(r0);
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int u = warp + 16 * j;               // 0..127
+        const int st = u >> 6, cg = (u >> 2) & 15, ks = u & 3;
+        const int c = 4 * cg + lc, t = 8 * ks + lt;
+        float x = 0.f;
+        if (c < W) {
+          const unsigned char* sp = raw + (st ? L::RAW_STATE : 0u);
+          uint32_t o;
+          if (CASE == TMA_ROWS) {
+            const int bb = c >> 5, c16 = (c & 31) >> 2;
+            o = (uint32_t)(bb * GT * 128 + t * 128 + ((c16 ^ (t & 7)) << 4) + (c & 3) * 4);
+          } else {
+            const int z = t >> ql, xx = t & ((1 << ql) - 1);
+            o = (uint32_t)(((((z * D + (c >> 1)) << ql) + xx) * 2 + (c & 1)) * 4);
+          }
+          x = *reinterpret_cast<const float*>(sp + o);
+        }
+        v[j] = x;
+      }
+      // one arrival per warp: its lanes' reads are ordered before lane 0's arrive
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(raw_empty(r0));
+      // the operand stage is free once the MMAs of tile i - kGtStages have completed
+      if (!mbar_wait(op_empty(s), ((uint32_t)(i / kGtStages) & 1u) ^ 1u, abort)) break;
+      unsigned char* oa = sm + L::op_a(s);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int u = warp + 16 * j;
+        const int st = u >> 6, cg = (u >> 2) & 15, ks = u & 3;
+        const int c = 4 * cg + lc, t = 8 * ks + lt;
+        if (c >= W) continue;
+        unsigned char* ob = oa + (st ? L::OP_BYTES : 0u);
+        const float hv = tf32_hi(v[j]);
+        *reinterpret_cast<float*>(ob + sw32_off(c, t, kTcRows)) = hv;
+        *reinterpret_cast<float*>(ob + sw32_off(64 + c, t, kTcRows)) = v[j] - hv;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(op_full(s));
+    }
+  } else if (warp < kGtMmaWarp) {
+    // ================================================================ epilogue: FP32 groups into FP64
+    // M = 128 accumulator: TMEM lane r = row r; rows r (psi_hi) and r + 64 (psi_lo)
+    // both add into component r, the lo half after the hi half (named barrier 3)
+    const int qd = warp - kGtEpiWarp0;
+    const int row = (32 * qd + lane) & 63;
+    const bool valid_row = row < W;
+    for (int g = 0; g < ngroups; ++g) {
+      const int b = g & 1;
+      // the four epilogue warps agree on giving up (they share named barrier 3)
+      if (bar_or(3, 4 * 32, !mbar_wait(tfull(b), (uint32_t)(g >> 1) & 1u, abort))) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int cc = 0; cc < W / 32; ++cc) {
+        float y[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(b * 64 + 32 * cc), y);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (cc == W / 32 - 1) {
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          mbar_arrive(tempty(b));
+        }
+        for (int half = 0; half < 2; ++half) {
+          if ((qd >> 1) == half && valid_row) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) acc[row * L::ACC_LD + 32 * cc + c] += (double)y[c];
+          }
+          bar_sync(3, 4 * 32);
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == kGtMmaWarp) {
+    // ================================================================ MMA issue
+    if (lane == 0) {
+      constexpr uint32_t idesc = tf32_idesc(W);   // M = 128, N = W
+      const uint32_t lo_off = 64u * 32u;           // rows 64.. inside every K step's block
+      bool issued = false;
+      for (int i = 0; i < ntiles; ++i) {
+        const int g = i / kGtGroup, b = g & 1, s = i % kGtStages;
+        if (!mbar_wait(op_full(s), (uint32_t)(i / kGtStages) & 1u, abort)) break;
+        if (i % kGtGroup == 0 && !mbar_wait(tempty(b), ((uint32_t)(g >> 1) & 1u) ^ 1u, abort)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t base_a = smem_u32(sm + L::op_a(s)), base_b = base_a + L::OP_BYTES;
+        const uint32_t d = tmem + (uint32_t)(b * 64);
+#pragma unroll
+        for (int ks = 0; ks < GT / 8; ++ks) {
+          const uint32_t ko = (uint32_t)ks * (uint32_t)(kTcRows * 32);   // K step: 128 rows x 32 bytes
+          const uint64_t da = sw32_desc(base_a + ko);
+          const uint64_t bh = sw32_desc(base_b + ko), bl = sw32_desc(base_b + lo_off + ko);
+          mma_tf32(d, da, bh, idesc, (i % kGtGroup != 0 || ks > 0) ? 1u : 0u);
+          mma_tf32(d, da, bl, idesc, 1u);
+        }
+        mma_commit(op_empty(s));
+        if (i % kGtGroup == kGtGroup - 1 || i == ntiles - 1) mma_commit(tfull(b));
+        issued = true;
+      }
+      if (issued) {
+        mma_commit(fin);
+        volatile int never = 0;
+        mbar_wait(fin, 0, &never);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ================================================================ producer (TMA, psi and lambda)
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_psi)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_lam)) : "memory");
+      int issued = 0;
+      for (int i = 0; i < ntiles; ++i) {
+        const int r = i % kGtRing;
+        if (!mbar_wait(raw_empty(r), ((uint32_t)(i / kGtRing) & 1u) ^ 1u, abort)) break;
+        const uint32_t dst = smem_u32(sm + L::raw(r));
+        const uint64_t t0 = tile_t0(i);
+        mbar_expect_tx(raw_full(r), L::RAW_STAGE);
+        if (CASE == TMA_ROWS) {
+#pragma unroll
+          for (int b = 0; b < W / 32; ++b) {
+            tma_load_2d(dst + (uint32_t)b * GT * 128, &map_psi, 32 * b, (int)t0, raw_full(r));
+            tma_load_2d(dst + L::RAW_STATE + (uint32_t)b * GT * 128, &map_lam, 32 * b, (int)t0, raw_full(r));
+          }
+        } else {
+          const uint64_t low = t0 & ((1ull << q) - 1ull);
+          tma_load_3d(dst, &map_psi, (int)(2 * low), 0, (int)(t0 >> q), raw_full(r));
+          tma_load_3d(dst + L::RAW_STATE, &map_lam, (int)(2 * low), 0, (int)(t0 >> q), raw_full(r));
+        }
+        issued = i + 1;
+      }
+      volatile int never = 0;
+      for (int j = issued > kGtRing ? issued - kGtRing : 0; j < issued; ++j)
+        mbar_wait(raw_full(j % kGtRing), (uint32_t)(j / kGtRing) & 1u, &never);
+    }
+    __syncwarp();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (tid == 0 && *abort) atomicExch(&g_tc_status, 1);
+  for (int e = tid; e < W * W; e += kGtThreads)
+    partials[(size_t)blockIdx.x * W * W + e] = acc[(e / W) * L::ACC_LD + (e % W)];
+  if (warp == kGtMmaWarp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u));
+}
+
+// psi and lambda tensor maps of one register for a consecutive support q..q+K-1
+// (the same geometry as k_block_tma's, with 64-tuple boxes); false if not expressible
+template <int K>
+static bool gram_maps(const float2* psi, const float2* lam, int n, int q, CUtensorMap* mp, CUtensorMap* ml) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return false;
+  const uint64_t tuples = 1ull << (n - K);
+  for (int which = 0; which < 2; ++which) {
+    CUtensorMap* map = which ? ml : mp;
+    void* base = (void*)(which ? lam : psi);
+    memset(map, 0, sizeof(*map));
+    CUresult rc;
+    if (q == 0) {
+      const cuuint64_t dims[2] = {(cuuint64_t)(2 << K), (cuuint64_t)tuples};
+      const cuuint64_t strides[1] = {(cuuint64_t)(8u << K)};
+      const cuuint32_t box[2] = {32, (cuuint32_t)kGtTuples};   // (32 floats, 32 rows)
+      const cuuint32_t es[2] = {1, 1};
+      rc = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+      const uint64_t high = tuples >> q;
+      if (high >= (1ull << 31) || q > 30) return false;
+      const int ql = std::min(q, 5);
+      const cuuint64_t dims[3] = {(cuuint64_t)(2ull << q), (cuuint64_t)(1u << K), (cuuint64_t)high};
+      const cuuint64_t strides[2] = {(cuuint64_t)(8ull << q), (cuuint64_t)(8ull << (q + K))};
+      const cuuint32_t box[3] = {(cuuint32_t)std::min(2 << ql, 64), (cuuint32_t)(1u << K), (cuuint32_t)(1u << (5 - ql))};
+      const cuuint32_t es[3] = {1, 1, 1};
+      rc = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    if (rc != CUDA_SUCCESS) return false;
+  }
+  return true;
+}
+
+template <int K>
+static int launch_gram_tma(const float2* psi, const float2* lam, int n, int q, double* partials, int* grid_out,
+                           cudaStream_t st, bool* done) {
+  using L = GramTmaSmem<K>;
+  *done = false;
+  if (n - K < 5 || (n - K) >= 31 + 5) return QS_OK;
+  CUtensorMap mp, ml;
+  if (!gram_maps<K>(psi, lam, n, q, &mp, &ml)) return QS_OK;
+  int dev = 0, sms = 0;
+  QS_CUDA(cudaGetDevice(&dev));
+  QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const uint64_t total = 1ull << (n - K);
+  const uint64_t tiles = total / kGtTuples;
+  const unsigned grid = (unsigned)std::min<uint64_t>(tiles, (uint64_t)sms);
+  if (q == 0) {
+    QS_CUDA(cudaFuncSetAttribute(k_gram_tma<K, TMA_ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES));
+    k_gram_tma<K, TMA_ROWS><<<grid, kGtThreads, L::BYTES, st>>>(mp, ml, total, q, partials);
+  } else {
+    QS_CUDA(cudaFuncSetAttribute(k_gram_tma<K, TMA_MEMBERS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::BYTES));
+    k_gram_tma<K, TMA_MEMBERS><<<grid, kGtThreads, L::BYTES, st>>>(mp, ml, total, q, partials);
+  }
+  QS_LAUNCHED();
+  *grid_out = (int)grid;
+  *done = true;
+  return QS_OK;
+}
+
 // Real Gram matrix of a 4- or 5-qubit support (qubits ascending) over a
 // complex64 register, interleaved layout, partials [grid][W][W]; *grid_out
 // receives the row count for the fold.
 int gram_tc(int w, const float2* psi, const float2* lam, int n, const int* qubits, double* partials, int* grid_out,
             cudaStream_t st) {
+  if (g_tma_enabled && (w == 4 || w == 5) && qubits[w - 1] == qubits[0] + w - 1) {
+    bool done = false;
+    if (w == 4) QS_TRY(launch_gram_tma<4>(psi, lam, n, qubits[0], partials, grid_out, st, &done));
+    else QS_TRY(launch_gram_tma<5>(psi, lam, n, qubits[0], partials, grid_out, st, &done));
+    if (done) return QS_OK;
+  }
   if (w == 4) return launch_gram_tc_t<4>(psi, lam, n, qubits, partials, grid_out, st);
   if (w == 5) return launch_gram_tc_t<5>(psi, lam, n, qubits, partials, grid_out, st);
   return fail(QS_EUNSUPPORTED, "tensor-core Gram takes 4- or 5-qubit supports");
