@@ -79,3 +79,49 @@ def test_wider_blocks_mean_fewer_passes(qs):
     counts = [len(qs.circuit_blocks(circ, params, k, matrices=False)) for k in range(1, 6)]
     assert counts[0] <= len(gates)
     assert counts[-1] < counts[1] < counts[0], counts
+
+
+def random_circuit(n, seed, ngates=60):
+    """Random gates on random qubits, many of them overlapping, so that the
+    planner's reordering (blocks moved past blocks of disjoint support, merged
+    forward and backward) meets gates that do not commute."""
+    rs = np.random.default_rng(seed)
+    gates = []
+    for _ in range(ngates):
+        kind = int(rs.integers(0, 7))
+        q = [int(x) for x in rs.permutation(n)]
+        if kind == 0:
+            gates.append(W.Gate("RY", (q[0],), theta=float(rs.uniform(-3, 3))))
+        elif kind == 1:
+            gates.append(W.cnot(q[0], q[1]))
+        elif kind == 2:
+            gates.append(W.Gate("H", (q[0],), (q[1],), (int(rs.integers(0, 2)),)))
+        elif kind == 3:
+            gates.append(W.Gate("MATRIX", (q[0], q[1]), matrix=_unitary(4, rs)))
+        elif kind == 4:
+            gates.append(W.Gate("SHIFT", (q[0],), (q[1], q[2]), (1, 0), theta=float(rs.uniform(-3, 3))))
+        elif kind == 5:
+            gates.append(W.Gate("MATRIX", (q[0], q[1], q[2]), matrix=_unitary(8, rs)))
+        else:
+            gates.append(W.Gate("SWAP", (q[0], q[1])))
+    return gates
+
+
+def _unitary(d, rs):
+    a = rs.standard_normal((d, d)) + 1j * rs.standard_normal((d, d))
+    q, r = np.linalg.qr(a)
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_circuits_fused_in_any_width(qs, seed):
+    n = 7
+    gates = random_circuit(n, seed)
+    circ = qs.Circuit(gates, n)
+    psi = W.haar_state(n, seed=seed)
+    want = oracle.apply_circuit(psi, n, gates)
+    for kmax in (2, 3, 4, 5):
+        blocks = qs.circuit_blocks(circ, None, kmax)
+        got = oracle.apply_circuit(psi, n, [W.Gate("MATRIX", q, matrix=m) for q, m in blocks])
+        assert np.max(np.abs(got - want)) < 1e-12, (seed, kmax)
+        assert all(len(q) <= max(kmax, 3) for q, _ in blocks)
