@@ -90,3 +90,43 @@ def test_tiled_backward_vs_oracle(qs, n, tile, depth):
     rloss, rgrad = oracle.gradient(oracle.zero_state(n), n, gates, params, terms)
     assert abs(loss - rloss) < 1e-5
     assert np.max(np.abs(grad - rgrad)) / np.max(np.abs(rgrad)) < 1e-4
+
+
+@pytest.mark.parametrize("n,tile,seed", [(13, 9, 0), (13, 10, 1), (16, 13, 2)])
+def test_runs_of_diagonal_gates(qs, n, tile, seed):
+    """Long runs of diagonal gates between a few Hadamards: phase gates with
+    thread-bit controls, single phase-local controls of either value, general
+    (non-unitary, one with a zero entry) diagonal matrices, all folded into
+    per-bit factors that the non-diagonal gates settle first."""
+    rs = np.random.default_rng(seed)
+    gates = []
+    for i in range(300):
+        perm = [int(x) for x in rs.permutation(n)]
+        if i % 23 == 0:
+            gates.append(W.Gate("H", (perm[0],)))
+            continue
+        nc = int(rs.integers(0, 3))
+        ctrls, vals = tuple(perm[1:1 + nc]), tuple(int(v) for v in rs.integers(0, 2, nc))
+        kind = i % 5
+        if kind == 0:
+            gates.append(W.Gate("SHIFT", (perm[0],), ctrls, vals, theta=float(rs.uniform(-3, 3))))
+        elif kind == 1:
+            gates.append(W.Gate("RZ", (perm[0],), ctrls, vals, theta=float(rs.uniform(-3, 3))))
+        elif kind == 2:
+            d = rs.uniform(0.8, 1.25, 2) * np.exp(1j * rs.uniform(-3, 3, 2))
+            if i % 47 == 2:
+                d[int(i % 2)] = 0.0
+            gates.append(W.Gate("MATRIX", (perm[0],), ctrls, vals, matrix=np.diag(d)))
+        elif kind == 3:
+            gates.append(W.Gate(["T", "S", "Z"][i % 3], (perm[0],), ctrls, vals))
+        else:
+            gates.append(W.Gate("RX", (perm[0],), ctrls, vals, theta=float(rs.uniform(-3, 3))))
+    circ = qs.Circuit(gates, n)
+    psi = W.haar_state(n, seed=seed)
+    st = qs.State(n, dtype=torch.complex64)
+    st.upload(psi)
+    st.apply_circuit(circ, None, tiles=True, tile_qubits=tile)
+    got = st.numpy()
+    want = oracle.apply_circuit(psi, n, gates)
+    scale = max(1.0, float(np.max(np.abs(want))))
+    assert np.max(np.abs(got - want)) < 2e-5 * scale
