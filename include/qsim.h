@@ -44,7 +44,7 @@ extern "C" {
 #define QS_ENOMEM (-2)        /* device or host allocation failed */
 #define QS_EDEVICE (-3)       /* a CUDA call or kernel failed */
 #define QS_ETIMEDOUT (-4)     /* a bounded device-side wait gave up */
-#define QS_EUNSUPPORTED (-5)  /* valid request this build does not implement */
+#define QS_EUNSUPPORTED (-5)  /* valid request the library does not implement */
 
 /* amplitude types */
 #define QS_C64 0   /* complex64: FP32 math and accumulation for gate application */
