@@ -1339,18 +1339,21 @@ static int launch_gram_tc_t(const float2* psi, const float2* lam, int n, const i
 // ------------------------------------------------------------------ TMA-fed Gram on consecutive supports
 //
 // The same Gram matrix for supports q..q+K-1 with the loads done by TMA: a
-// producer thread copies each 32-tuple tile of psi and of lambda into an
-// eight-stage ring, 128 KB in flight per SM (the register-held loads of
-// k_gram_tc, 64 KB in flight, bound it to ~21 GB/s per SM, about 3 TB/s, and
-// so did a two-stage ring), sixteen converter warps write it transposed and split (hi / lo)
-// into one of two operand stages (a warp step writes one 128-byte row segment:
-// 32 tuples of one component).  A = [psi_hi^T; psi_lo^T] fills all M = 128
-// rows, and two MMAs per 8 tuples (B = lambda_hi^T, then lambda_lo^T) give
-// rows r + rows r + 64 = psi^T lambda to FP32 accuracy (an M = 64 MMA over
-// psi^T alone cost about as much as an M = 128 one: measured 150 TFLOP/s
-// against 300 for the M = 128 block kernel).  Raw layouts as in k_block_tma:
-// q = 0 row-major tuples (2D map, 128-byte swizzle), q >= 1 members x tuples
-// (3D map; box (min(2^(q+1), 64) floats, 2^K, 2^(5 - min(q, 5)))).
+// producer thread copies each 32-tuple tile of psi and of lambda into a
+// four-stage ring (the register-held loads of k_gram_tc, 64 KB in flight per
+// SM, bound it to about 3 TB/s), sixteen converter warps write it transposed
+// and split (hi / lo) into one of four operand stages (a warp step writes one
+// 32-byte-swizzle K step: 4 components x 8 tuples).  A = [psi_hi^T; psi_lo^T]
+// fills all M = 128 rows, and two MMAs per 8 tuples (B = lambda_hi^T, then
+// lambda_lo^T) give rows r + rows r + 64 = psi^T lambda to FP32 accuracy.
+// Measured alternatives (n = 28 brickwork gradient 0.179 s with this form):
+// one N = 128 MMA over B = [lambda_hi^T; lambda_lo^T] instead of two N = 64
+// ones 0.188 s; rings of 6 or 8 stages with 3 or 2 operand stages unchanged;
+// A in tensor memory issues no faster than A in shared memory (an issue loop
+// of M = 128, N = 64, K = 8 tf32 MMAs: ~94 cycles each either way).  Raw
+// layouts as in k_block_tma: q = 0 row-major tuples (2D map, 128-byte
+// swizzle), q >= 1 members x tuples (3D map; box (min(2^(q+1), 64) floats,
+// 2^K, 2^(5 - min(q, 5)))).
 constexpr int kGtTuples = 32;
 constexpr int kGtRing = 4;
 constexpr int kGtStages = 4;                     // operand stages (MMA completion runs several tiles behind)

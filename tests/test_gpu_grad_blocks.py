@@ -123,3 +123,24 @@ def test_block_gradient_tensor_core_gram_matches_cuda_core(qs, kmax):
             assert abs(out[mode][0] - wl) < 1e-5
             assert rel(out[mode][1], wg) < 2e-5, (name, mode, rel(out[mode][1], wg))
         assert rel(out[1][1], out[0][1]) < 2e-5, name
+
+
+def test_block_gradient_tensor_core_gram_many_groups(qs):
+    # n = 24: 2^19 tuples per 5-qubit Gram, so every CTA of the TMA-fed Gram runs
+    # several FP32 accumulation groups through both accumulator buffers; the
+    # gradient with tensor cores on must match the CUDA-core Gram's
+    n = 24
+    gates, params = W.brickwork(n, 2, seed=7)
+    circ = qs.Circuit(gates, n, nparams=len(params))
+    obs = qs.Observable([(1.0, ((1, "Z"),)), (0.5, ((12, "X"), (13, "X")))])
+    psi0 = W.haar_state(n, seed=8)
+    out = {}
+    for mode in (1, 0):
+        qs.set_tensor_cores(mode)
+        st = qs.State(n, dtype=torch.complex64)
+        st.upload(psi0)
+        st.apply_circuit(circ, params, blocks=5)
+        out[mode] = qs.backward_blocks(st, circ, params, obs, kmax=5)
+    qs.set_tensor_cores(1)
+    assert abs(out[1][0] - out[0][0]) < 1e-5
+    assert rel(out[1][1], out[0][1]) < 1e-4, rel(out[1][1], out[0][1])
