@@ -58,7 +58,13 @@ class _Term(ctypes.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile liboracle.so with gcc (plain C, OpenMP over basis indices)."""
+    """Compile liboracle.so with gcc (plain C, OpenMP over basis indices).
+
+    QSIM_ORACLE_LIB names a prebuilt copy to load instead (the mutation tests
+    load copies with planted mistakes this way, each in its own process)."""
+    alt = os.environ.get("QSIM_ORACLE_LIB")
+    if alt:
+        return alt
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp",
                "-ffp-contract=off", "-fcx-limited-range", _SRC, "-o", _LIB + ".tmp", "-lm"]

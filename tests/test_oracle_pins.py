@@ -100,6 +100,28 @@ def test_single_qubit_gates_match_kron_formula():
             assert np.allclose(oracle.apply_circuit(psi, n, [g]), full @ psi, atol=1e-13)
 
 
+def test_named_gates_are_their_textbook_matrices():
+    # App. "Builtin Block Types": the constant gates written out here, not taken
+    # from the oracle; the oracle applied to basis vectors must reproduce them
+    # entry by entry (a global sign or phase counts as a mistake here: controlled
+    # versions expose it)
+    r2 = 1 / np.sqrt(2)
+    th = 0.61
+    want = {
+        "X": PAULI["X"], "Y": PAULI["Y"], "Z": PAULI["Z"],
+        "H": np.array([[r2, r2], [r2, -r2]]),
+        "S": np.diag([1, 1j]), "SDG": np.diag([1, -1j]),
+        "T": np.diag([1, (1 + 1j) * r2]), "TDG": np.diag([1, (1 - 1j) * r2]),
+        "SHIFT": np.diag([1, np.exp(1j * th)]), "PHASE": np.exp(1j * th) * np.eye(2),
+    }
+    for name, U in want.items():
+        g = W.Gate(name, (0,), theta=th)
+        assert np.allclose(full_matrix(1, [g]), U, atol=1e-15), name
+        gc = W.Gate(name, (1,), (0,), (1,), theta=th)
+        P0, P1 = np.diag([1, 0]), np.diag([0, 1])
+        assert np.allclose(full_matrix(2, [gc]), np.kron(np.eye(2), P0) + np.kron(U, P1), atol=1e-15), name
+
+
 def test_cnot_matches_projector_kron():
     n = 4
     P0 = np.diag([1, 0]).astype(complex)
@@ -261,6 +283,27 @@ def test_norm_and_inverse_identity():
     out = oracle.apply_circuit(psi, n, gates, params)
     assert abs(np.linalg.norm(out) - 1) < 1e-13
     assert np.allclose(oracle.apply_dagger(out, n, gates, params), psi, atol=1e-13)
+
+
+def test_dagger_of_every_gate_kind_inverts_it():
+    # the dagger rules (Sec. "Manipulating Quantum Circuits") for each kind on its
+    # own, with and without controls: U^dag U = 1 on a Haar state
+    n = 5
+    rs = np.random.default_rng(6)
+    psi = W.haar_state(n, seed=6)
+    kinds = ["I", "X", "Y", "Z", "H", "S", "SDG", "T", "TDG", "RX", "RY", "RZ", "SHIFT", "PHASE"]
+    gates = [W.Gate(k, (2,), theta=0.77) for k in kinds]
+    gates += [W.Gate("SWAP", (1, 3)), W.Gate("ROT", (0, 4), theta=-1.3, paulis="YZ"),
+              W.Gate("MATRIX", (3, 1), matrix=scipy.stats.unitary_group.rvs(4, random_state=7))]
+    for g in list(gates):
+        ctrl = tuple(q for q in range(n) if q not in g.locs)[:2]
+        gates.append(W.Gate(g.name, g.locs, ctrl, (1, 0), theta=g.theta, paulis=g.paulis, matrix=g.matrix))
+    for g in gates:
+        out = oracle.apply_circuit(psi, n, [g])
+        back = oracle.apply_dagger(out, n, [g])
+        assert np.max(np.abs(back - psi)) < 1e-14, (g.name, g.ctrl_locs)
+        if g.name != "I":
+            assert np.max(np.abs(out - psi)) > 1e-3, g.name   # the gate itself is not the identity here
 
 
 def test_single_gate_suite_repetition_invariants():
