@@ -287,6 +287,21 @@ int qs_circuit_gate_matrices(const qs_circuit* c, int index, const double* host_
  * tables) if needed.  QS_EUNSUPPORTED if the circuit does not fit the engine. */
 int qs_circuit_schedule_info(const qs_circuit* c, int tile_qubits, int* npasses, int* nphases);
 
+/* The order in which the tile engine applies the circuit's gates for tiles of
+ * tile_qubits qubits (0 = 13), host only (no device work).  The engine first
+ * rewrites each SWAP(a, b) as X(b) controlled by a, X(a) controlled by b, X(b)
+ * controlled by a (each also carrying the SWAP's controls); host_order[i] is
+ * the index, in that expanded list, of the i-th gate applied and host_pass[i]
+ * its pass.  Inside a pass the engine may still fuse runs of gates on one
+ * qubit and apply commuting diagonal gates together; the order here is the
+ * scheduler's (Sec. "Representing Quantum Circuits": reordering is valid only
+ * between gates on disjoint qubits).  *ngates receives the expanded gate count;
+ * call with NULL arrays to size them.  QS_EUNSUPPORTED if the circuit does not
+ * fit the engine (fewer than 5 or more than 32 qubits, multi-target gates
+ * other than SWAP). */
+int qs_circuit_tile_order(const qs_circuit* c, int tile_qubits, int* ngates, int32_t* host_order,
+                          int32_t* host_pass);
+
 /* apply!(reg, chain): gates in list order on every register of s (Sec.
  * "Representing Quantum Circuits").  host_params: nparams doubles shared by
  * all registers, or nbatch * nparams (register-major) with

@@ -83,6 +83,7 @@ SIGNATURES = {
     "qs_circuit_info": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "qs_circuit_gate_matrices": ([_P, _I, _PD, ctypes.POINTER(GateDesc), _PD, _PD, _PD], _I),
     "qs_circuit_schedule_info": ([_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "qs_circuit_tile_order": ([_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], _I),
     "qs_apply_circuit": ([_P, _P, _PD, _I], _I),
     "qs_circuit_blocks": ([_P, _PD, _I, ctypes.POINTER(_I), _PI32, _PI32, _PD], _I),
     "qs_autotune_circuit": ([_P, _P, _PD, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), _PI32, _PD], _I),

@@ -398,6 +398,20 @@ int qs_circuit_schedule_info(const qs_circuit* c, int tile_qubits, int* npasses,
   return schedule_info(c, tile_qubits, npasses, nphases);
 }
 
+int qs_circuit_tile_order(const qs_circuit* c, int tile_qubits, int* ngates, int32_t* host_order,
+                          int32_t* host_pass) {
+  if (!c || !ngates) return fail(QS_EINVAL, "null argument");
+  if (tile_qubits < 0 || tile_qubits > 13) return fail(QS_EINVAL, "tile_qubits must be 0 or 9..13");
+  std::vector<int> order, pass;
+  QS_TRY(tile_order(c, tile_qubits, order, pass));
+  *ngates = (int)order.size();
+  for (size_t i = 0; i < order.size(); ++i) {
+    if (host_order) host_order[i] = order[i];
+    if (host_pass) host_pass[i] = pass[i];
+  }
+  return QS_OK;
+}
+
 int qs_apply_circuit(qs_state* s, const qs_circuit* c, const double* params, int flags) {
   return apply_circuit_impl(s, c, params, flags, 0, nullptr);
 }

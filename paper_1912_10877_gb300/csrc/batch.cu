@@ -1297,6 +1297,26 @@ int schedule_info(const qs_circuit* c, int tile_qubits, int* npasses, int* nphas
   return QS_OK;
 }
 
+int tile_order(const qs_circuit* c, int tile_qubits, std::vector<int>& order, std::vector<int>& pass) {
+  const int M = tile_qubits > 0 ? tile_qubits : kBatchTile;
+  if (M < kRowBits + kRB || M > kBatchTile) return fail(QS_EINVAL, "tile_qubits must be in %d..%d", kRowBits + kRB, kBatchTile);
+  const int n = c->nqubits;
+  if (n < kRowBits || n > 32) return fail(QS_EUNSUPPORTED, "%d qubits outside the tile engine's range", n);
+  qs_circuit tmp;
+  expand_swaps(c, &tmp);
+  std::vector<HostPass> hp;
+  QS_TRY(plan_passes(&tmp, n, std::min(n, M), kMaxPhaseOps, hp));
+  order.clear();
+  pass.clear();
+  for (size_t p = 0; p < hp.size(); ++p)
+    for (const HostPhase& ph : hp[p].phases)
+      for (int gi : ph.gates) {
+        order.push_back(gi);
+        pass.push_back((int)p);
+      }
+  return QS_OK;
+}
+
 int expect_raw(const void* data, int dtype, int n, int nreg, const qs_observable* o, qs_state* ws_owner,
                double* host_out);
 

@@ -248,5 +248,7 @@ int fused_backward(qs_state* s, const qs_circuit* c, const double* host_params, 
                    void* dev_work, double* host_grad, double* host_loss, int tile_qubits);
 void free_fused(qs_batch_program* p);
 int schedule_info(const qs_circuit* c, int tile_qubits, int* npasses, int* nphases);
+// the scheduler's gate order (expanded SWAPs) and pass of each gate, host only (batch.cu)
+int tile_order(const qs_circuit* c, int tile_qubits, std::vector<int>& order, std::vector<int>& pass);
 
 }  // namespace qs

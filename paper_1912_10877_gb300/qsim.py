@@ -405,6 +405,20 @@ def schedule_info(circuit: Circuit, tile_qubits: int = 0):
     return p.value, f.value
 
 
+def tile_order(circuit: Circuit, tile_qubits: int = 0):
+    """(order, pass) of the tile engine's schedule, host only: order[i] indexes the
+    circuit's gate list with every SWAP rewritten as three controlled X gates."""
+    L = N.lib()
+    cnt = ctypes.c_int()
+    N.check(L.qs_circuit_tile_order(circuit.handle, int(tile_qubits), ctypes.byref(cnt), None, None))
+    order = np.zeros(max(1, cnt.value), np.int32)
+    passes = np.zeros(max(1, cnt.value), np.int32)
+    P32 = ctypes.POINTER(ctypes.c_int32)
+    N.check(L.qs_circuit_tile_order(circuit.handle, int(tile_qubits), ctypes.byref(cnt),
+                                    order.ctypes.data_as(P32), passes.ctypes.data_as(P32)))
+    return order[:cnt.value], passes[:cnt.value]
+
+
 def set_tensor_cores(mode) -> None:
     """Kernel for dense 4- and 5-qubit complex64 gates: True or 2 = always the tensor
     cores, False or 0 = the CUDA cores, 1 = per target placement (default)."""
