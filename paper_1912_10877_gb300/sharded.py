@@ -28,7 +28,11 @@ backward (Sec. "Reverse Mode", Eq. apply-back) runs gate by gate on psi and
 lambda = O psi, which share the map: a parameterised gate U = exp(-i theta c H)
 adds 2 c Im<lambda|(P_ctrl (x) H) psi> from a copy of psi, then both states are
 uncomputed by U^dagger; every shard's gradient partials are added with one
-all-reduce at the end.
+all-reduce at the end.  Measurement (Sec. "Instructions on Quantum
+Registers", measure) draws a shard from the shard weights P_s = <psi_s|psi_s>
+(one all-reduce), then an index inside it with the shard's own sampler and
+the uniform rescaled to that shard's share, and maps the physical index back
+to the logical one.
 
 Every local operation is a call into libqsim.so (``qsim.State``); this module
 only plans exchanges and predicates, and moves shard halves with
@@ -88,6 +92,10 @@ class LibShard:
 
     def numpy(self) -> np.ndarray:
         return self.st.numpy()
+
+    def measure(self, u) -> np.ndarray:
+        """Indices inside the shard sampled with the uniforms u (the library's sampler)."""
+        return self.st.measure(np.asarray(u, np.float64).reshape(1, -1))[0]
 
 
 def _is_diagonal(U: np.ndarray) -> bool:
@@ -401,6 +409,62 @@ class ShardedState:
         self._drop("lam")
         grad = self._sum(grad)
         return loss, grad[:circuit.nparams]
+
+    # ------------------------------------------------------------------ measurement
+    @staticmethod
+    def _pick(weights: np.ndarray, t: float):
+        """First s whose running left-fold prefix passes t, with the prefix before
+        it (the last positive weight if rounding leaves t beyond the total)."""
+        acc, last, acc_last = 0.0, -1, 0.0
+        for s, w in enumerate(weights):
+            nxt = acc + w
+            if nxt > t:
+                return s, acc
+            if w > 0:
+                last, acc_last = s, acc
+            acc = nxt
+        return (last, acc_last) if last >= 0 else (len(weights) - 1, acc)
+
+    def _logical(self, phys: np.ndarray) -> np.ndarray:
+        x = np.zeros_like(phys)
+        for q in range(self.n):
+            x |= ((phys >> self.pos[q]) & 1) << q
+        return x
+
+    def measure(self, u) -> np.ndarray:
+        """Logical basis indices sampled from |psi|^2 with the uniforms u in [0, 1),
+        one per shot; the state is unchanged.  Shard s is drawn with probability
+        P_s / T (t = u T walked over the left-fold prefixes of the shard weights
+        P_s = <psi_s|psi_s>, FP64), the index inside it by the shard's sampler with
+        u' = (t - prefix) / P_s; with one shard, the register's sampler with u.
+        Every rank returns all shots."""
+        u = np.ascontiguousarray(np.ravel(u), dtype=np.float64)
+        if not np.all((u >= 0.0) & (u < 1.0)):
+            raise ValueError("uniforms must lie in [0, 1)")
+        psi = self.vecs["psi"]
+        if self.nshards == 1:
+            return self._logical(np.asarray(psi[0].measure(u), np.int64))
+        w = np.zeros(self.nshards)
+        for s, v in zip(self.owned, psi):
+            w[s] = v.inner(v).real
+        w = self._sum(w)
+        total = 0.0
+        for x in w:
+            total = total + x
+        pick = np.empty(len(u), np.int64)
+        sub = np.empty(len(u), np.float64)
+        top = np.nextafter(1.0, 0.0)
+        for i, ui in enumerate(u):
+            t = ui * total
+            sh, acc = self._pick(w, t)
+            pick[i] = sh
+            sub[i] = min(max((t - acc) / w[sh], 0.0), top) if w[sh] > 0 else 0.0
+        phys = np.zeros(len(u), np.float64)
+        for s, v in zip(self.owned, psi):
+            m = pick == s
+            if m.any():
+                phys[m] = (s << self.L) | np.asarray(v.measure(sub[m]), np.int64)
+        return self._logical(self._sum(phys).astype(np.int64))
 
     # ------------------------------------------------------------------ host views (small n)
     def _perm(self) -> np.ndarray:

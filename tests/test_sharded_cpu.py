@@ -1,8 +1,9 @@
 """Host logic of the qubit-sharded register (paper_1912_10877_gb300.sharded) on
 CPU: the global/local qubit map, the pairwise half-shard exchanges, control
 predicates and diagonal restriction on global qubits, expectation values with
-global Z signs, and the gate-by-gate reversible backward with one all-reduce
-of the gradient.  Shards here are FP64 host vectors whose local operations are
+global Z signs, the gate-by-gate reversible backward with one all-reduce
+of the gradient, and measurement (shard drawn from the shard weights, index
+from the shard's sampler, physical index mapped back to the logical one).  Shards here are FP64 host vectors whose local operations are
 oracle calls, so these tests check the sharding against the oracle's
 whole-register results; exchanges run in one process (every shard local) and
 across gloo ranks (world size 2: shards paired inside a rank and across
@@ -68,6 +69,9 @@ class OracleShard:
 
     def numpy(self):
         return self.a.copy()
+
+    def measure(self, u):
+        return oracle.sample(self.a, self.n, u)
 
 
 def mixed_circuit(n, seed):
@@ -160,6 +164,71 @@ def test_global_diagonal_and_control_move_no_data():
     assert np.max(np.abs(sh.gather() - oracle.apply_circuit(psi0, n, gates))) < TOL
 
 
+def sampled_register(n, nglobal, group=None):
+    from paper_1912_10877_gb300 import qsim
+    from paper_1912_10877_gb300.sharded import ShardedState
+    gates, params = mixed_circuit(n, seed=n + nglobal)
+    sh = ShardedState(n, nglobal, torch.complex128, group=group, backend=OracleShard)
+    sh.upload(W.haar_state(n, seed=4))
+    sh.apply_circuit(qsim.Circuit(gates, n), params)
+    return sh
+
+
+def two_level_reference(sh, u):
+    """The sharded sampling rule written out on the gathered physical shards."""
+    psi = sh.gather()
+    phys = np.empty_like(psi)
+    phys[sh._perm()] = psi
+    shards = phys.reshape(sh.nshards, -1)
+    w = [float(np.vdot(v, v).real) for v in shards]
+    total = 0.0
+    for x in w:
+        total = total + x
+    out = []
+    for ui in u:
+        t = ui * total
+        acc = 0.0
+        for s_, ws in enumerate(w):
+            if acc + ws > t:
+                break
+            acc = acc + ws
+        sub = min((t - acc) / w[s_], np.nextafter(1.0, 0.0))
+        i = int(oracle.sample(shards[s_], sh.L, [sub])[0])
+        p = (s_ << sh.L) | i
+        out.append(sum(((p >> sh.pos[q]) & 1) << q for q in range(sh.n)))
+    return np.array(out, np.int64)
+
+
+@pytest.mark.parametrize("n,nglobal", [(7, 2), (8, 3)])
+def test_sampling_follows_the_two_level_rule(n, nglobal):
+    sh = sampled_register(n, nglobal)
+    assert sh.exchanges > 0 and sh.pos != list(range(n))
+    u = W.shot_uniforms(3000, seed=n)[0]
+    assert np.array_equal(sh.measure(u), two_level_reference(sh, u))
+
+
+def test_sampling_distribution_and_basis_states():
+    import scipy.stats
+    from paper_1912_10877_gb300.sharded import ShardedState
+    n = 6
+    sh = sampled_register(n, 2)
+    p = np.abs(sh.gather()) ** 2
+    shots = sh.measure(W.shot_uniforms(40000, seed=9)[0])
+    counts = np.bincount(shots, minlength=1 << n)
+    keep = p * len(shots) >= 5
+    stat = scipy.stats.chisquare(counts[keep], p[keep] / p[keep].sum() * counts[keep].sum())
+    assert stat.pvalue > 1e-4, stat
+    assert np.all(p[shots] > 0)
+    b = ShardedState(n, 2, torch.complex128, backend=OracleShard)
+    b.apply_matrix(np.array([[0, 1], [1, 0]]), [n - 1])   # moves the map
+    b.reset(0b110101)
+    assert np.all(b.measure(W.shot_uniforms(50, seed=1)[0]) == 0b110101)
+    one = ShardedState(n, 0, torch.complex128, backend=OracleShard)
+    one.upload(W.haar_state(n, seed=2))
+    u = W.shot_uniforms(200, seed=3)[0]
+    assert np.array_equal(one.measure(u), oracle.sample(W.haar_state(n, seed=2), n, u))
+
+
 def free_port() -> int:
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
@@ -176,6 +245,26 @@ def _worker(rank, world, port, n, nglobal, out_dir):
                 np.array([r[k] for k in ("state", "expect", "loss", "grad", "uncompute", "exchanges")]))
     finally:
         dist.destroy_process_group()
+
+
+def _sample_worker(rank, world, port, n, nglobal, out_dir):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        sh = sampled_register(n, nglobal)
+        np.save(os.path.join(out_dir, f"s{rank}.npy"), sh.measure(W.shot_uniforms(2000, seed=5)[0]))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_gloo_world_two_sampling(tmp_path):
+    n, nglobal, world = 7, 2, 2
+    mp.start_processes(_sample_worker, args=(world, free_port(), n, nglobal, str(tmp_path)), nprocs=world,
+                       join=True, start_method="spawn")
+    want = sampled_register(n, nglobal).measure(W.shot_uniforms(2000, seed=5)[0])
+    for rank in range(world):
+        assert np.array_equal(np.load(tmp_path / f"s{rank}.npy"), want), rank
 
 
 @pytest.mark.parametrize("n,nglobal", [(6, 1), (7, 2)])
