@@ -1,5 +1,9 @@
 // api.cu -- the C ABI of include/qsim.h: argument validation, object lifetime,
 // and the host-side circuit walk (gate matrices, same-qubit fusion, launches).
+// The register and instruction model is that of Sec. "Quantum Registers" and
+// Sec. "Instructions on Quantum Registers"; apply! of a chain follows Sec.
+// "Representing Quantum Circuits" (gates in list order; consecutive
+// single-qubit gates on one qubit are multiplied into one 2x2 first).
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>

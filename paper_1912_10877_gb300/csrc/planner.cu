@@ -1,6 +1,8 @@
 // planner.cu -- host-side scheduling of a gate list into fused tile passes and
 // register phases (see tiles.cuh).  Gates move earlier only past gates that
-// share no qubit with them, so the schedule applies the same operator.  Only
+// share no qubit with them, so the schedule applies the same operator (a
+// chain is the product of its parts in order, Sec. "Representing Quantum
+// Circuits"; factors on disjoint qubits commute).  Only
 // the target of a non-diagonal gate has to lie in the pass's tile and in the
 // phase's register bits: controls are tested per thread on the global index,
 // and a diagonal gate only multiplies amplitudes, so it fits anywhere.

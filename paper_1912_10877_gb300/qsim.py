@@ -32,7 +32,8 @@ def _stream_ptr(stream=None):
 
 
 class State:
-    """A register or a batch of registers in device memory owned by a torch tensor."""
+    """A register or a batch of registers in device memory owned by a torch tensor
+    (Sec. "Quantum Registers", Sec. "Batched Quantum Registers")."""
 
     def __init__(self, nqubits, dtype=torch.complex64, nbatch: int = 1, device="cuda", stream=None):
         L = N.lib()
@@ -132,7 +133,8 @@ class State:
 
     # -- instructions ---------------------------------------------------------
     def apply(self, g, params=None):
-        """instruct! one gate record (workloads.Gate)."""
+        """instruct! one gate record (workloads.Gate): Sec. "Instructions on Quantum
+        Registers", the general multi-control instruction of Sec. "Performance"."""
         cl = N.i32(g.ctrl_locs)
         cv = N.i32(g.ctrl_vals)
         locs = N.i32(g.locs)
@@ -152,6 +154,7 @@ class State:
         return self
 
     def apply_matrix(self, U, locs, ctrl_locs=(), ctrl_vals=()):
+        """instruct!(reg, U, locs, ctrl_locs, ctrl_vals) with a dense 2^k x 2^k matrix."""
         m = np.ascontiguousarray(U, dtype=np.complex128).view(np.float64)
         N.check(N.lib().qs_apply_gate(self.handle, N.dptr(m), len(locs), N.i32(locs), len(ctrl_locs),
                                       N.i32(ctrl_locs), N.i32(ctrl_vals or [1] * len(ctrl_locs))))
@@ -159,7 +162,7 @@ class State:
 
     def apply_circuit(self, circuit: "Circuit", params=None, per_register=False, fused=True, tiles=False,
                       tile_qubits=0, blocks=0, flags=None):
-        """apply!(reg, chain).  fused=False: one launch per gate; tiles=True: force the
+        """apply!(reg, chain) (Sec. "Representing Quantum Circuits").  fused=False: one launch per gate; tiles=True: force the
         tile engine (fused passes over 2^tile_qubits-amplitude tiles); blocks=k: fuse
         the gates into blocks of at most k qubits; flags: raw qs_apply_circuit flags
         (e.g. from autotune), overriding the others."""
@@ -173,12 +176,15 @@ class State:
         return self
 
     def expect(self, obs: "Observable") -> np.ndarray:
+        """expect(O, reg) per register (Sec. "Forward Mode"), FP64 sums."""
         out = np.zeros(self.nreg)
         N.check(N.lib().qs_expect(self.handle, obs.handle, N.dptr(out)))
         return out
 
     def measure(self, u, collapse=False) -> np.ndarray:
-        """Sample basis indices with the given uniforms [nreg][nshots] in [0, 1)."""
+        """measure / measure! (Sec. "Instructions on Quantum Registers"): basis indices
+        sampled with the given uniforms [nreg][nshots] in [0, 1) under the sampling
+        contract of qsim.h; collapse=True projects onto the single sampled state."""
         u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(self.nreg, -1))
         out = np.zeros(u.shape, dtype=np.int64)
         N.check(N.lib().qs_measure(self.handle, N.dptr(u), u.shape[1],
@@ -196,7 +202,8 @@ def _params_array(params, count):
 
 
 class Circuit:
-    """Immutable flat gate list (qs_circuit)."""
+    """Immutable flat gate list (qs_circuit): the put / control / chain blocks of
+    Sec. "Representing Quantum Circuits" flattened into gate records."""
 
     def __init__(self, gates, nqubits: int, nparams: int | None = None):
         L = N.lib()
@@ -269,7 +276,8 @@ class Circuit:
 
 
 class Observable:
-    """sum_t coeff_t P_t from terms [(coeff, ((loc, 'X'|'Y'|'Z'), ...)), ...]."""
+    """sum_t coeff_t P_t from terms [(coeff, ((loc, 'X'|'Y'|'Z'), ...)), ...] (the
+    Hamiltonians of Sec. "Forward Mode" and Listing "Heisenberg Hamiltonian")."""
 
     def __init__(self, terms):
         arr = (N.PauliTerm * max(1, len(terms)))()
@@ -317,7 +325,8 @@ def apply_circuit_ckpt(state: State, circuit: Circuit, params, every: int, ckpts
 
 def backward(state: State, circuit: Circuit, params, obs: Observable, ckpt_every: int = 0,
              ckpts: torch.Tensor | None = None, work: torch.Tensor | None = None):
-    """expect'(O, reg => circuit): (loss, grad) from the circuit's output state (left unchanged)."""
+    """expect'(O, reg => circuit): (loss, grad) from the circuit's output state (left
+    unchanged), by the reversible adjoint of Sec. "Reverse Mode" (Eq. apply-back)."""
     p = _params_array(params, circuit.nparams)
     if work is None:
         work = backward_work(state.nqubits, state.device)
@@ -399,7 +408,8 @@ def backward_tiled(state: State, circuit: Circuit, params, obs: Observable, tile
 
 
 def schedule_info(circuit: Circuit, tile_qubits: int = 0):
-    """(passes, phases) of the circuit's tile-engine schedule."""
+    """(passes, phases) of the circuit's tile-engine schedule (gates reordered only
+    past gates on disjoint qubits, Sec. "Representing Quantum Circuits")."""
     p, f = ctypes.c_int(), ctypes.c_int()
     N.check(N.lib().qs_circuit_schedule_info(circuit.handle, int(tile_qubits), ctypes.byref(p), ctypes.byref(f)))
     return p.value, f.value
@@ -433,7 +443,8 @@ def tensor_cores() -> int:
 
 
 def circuit_blocks(circuit: Circuit, params=None, kmax: int = 5, matrices: bool = True):
-    """The k-qubit blocks of circuit (application order): list of (qubits, matrix or None)."""
+    """The k-qubit blocks of circuit (application order): list of (qubits, matrix or None);
+    a block's matrix is the product of its gates (Sec. "Matrix Representation")."""
     L = N.lib()
     nb = ctypes.c_int(0)
     p = _params_array(params, circuit.nparams)
