@@ -120,3 +120,40 @@ def test_batch_autotune_picks_a_tile_that_is_correct(qs):
     assert set(times) == {13, 12, 11} and best in times and times[best] > 0
     assert times[best] == min(v for v in times.values() if v > 0)
     run_case(qs, specs, tile=best)
+
+
+def test_batch_full_size_sampled(qs, record_property):
+    # the benchmarked batch itself: 1024 registers, n ~ U{10..18} (seed 0), 20 layers
+    # of Rz Rx Rz + CNOT ladder, <sum Z_i Z_{i+1}>, one persistent launch with
+    # 13-qubit tiles; registers of every size class checked against the oracle
+    # (gradient tolerance 1e-4 relative, as for the other batches: FP32 forward and
+    # uncompute through up to 1420 gates; measured on GB300: 2.7e-6)
+    counts = W.batch_qubit_counts(1024, 10, 18, seed=0)
+    specs = W.batch_variational(counts, 20, seed=0)
+    circs = [qs.Circuit(g, int(n), nparams=len(p)) for n, (g, p) in zip(counts, specs)]
+    obs = [qs.Observable(W.zz_chain(int(n))) for n in counts]
+    prog = qs.BatchProgram(circs, obs, tile_qubits=13)
+    st = qs.State([int(n) for n in counts], dtype=torch.complex64)
+    params = torch.tensor(np.concatenate([p for _, p in specs]), dtype=torch.float64, device="cuda")
+    loss, grad = prog.run(st, params, grad=True, reset=True)
+    torch.cuda.synchronize()
+    loss, grad = loss.cpu().numpy(), grad.cpu().numpy()
+    assert np.all(np.isfinite(loss)) and np.all(np.isfinite(grad))
+    rs = np.random.default_rng(1)
+    picks = sorted({int(np.flatnonzero(np.asarray(counts) == n)[0]) for n in (10, 13, 14, 18)} |
+                   {int(x) for x in rs.choice(len(counts), 2, replace=False)})
+    worst = 0.0
+    for r in picks:
+        n = int(counts[r])
+        gates, p = specs[r]
+        got = st.numpy()[int(st.offsets[r]):int(st.offsets[r + 1])]
+        ref = oracle.apply_circuit(oracle.zero_state(n), n, gates, p)
+        assert np.max(np.abs(got - ref)) < 2e-5, ("state", r, n)
+        rl, rg = oracle.gradient(oracle.zero_state(n), n, gates, p, W.zz_chain(n))
+        assert abs(loss[r] - rl) < 1e-5, ("loss", r, n)
+        g = grad[prog.param_offsets[r]:prog.param_offsets[r + 1]]
+        err = float(np.max(np.abs(g - rg)) / np.max(np.abs(rg)))
+        worst = max(worst, err)
+        assert err < 1e-4, ("grad", r, n, err)
+    record_property("worst_relative_gradient_error", worst)
+    print(f"registers {picks}: worst relative gradient error {worst:.2e}")
