@@ -412,18 +412,16 @@ class ShardedState:
 
     # ------------------------------------------------------------------ measurement
     @staticmethod
-    def _pick(weights: np.ndarray, t: float):
-        """First s whose running left-fold prefix passes t, with the prefix before
-        it (the last positive weight if rounding leaves t beyond the total)."""
-        acc, last, acc_last = 0.0, -1, 0.0
-        for s, w in enumerate(weights):
-            nxt = acc + w
-            if nxt > t:
-                return s, acc
-            if w > 0:
-                last, acc_last = s, acc
-            acc = nxt
-        return (last, acc_last) if last >= 0 else (len(weights) - 1, acc)
+    def _pick(weights: np.ndarray, t: np.ndarray):
+        """For each t: the first shard s whose left-fold prefix P_0 + .. + P_s passes
+        t, and the prefix before it (the last positive weight where rounding leaves
+        t at or beyond the total).  np.cumsum adds left to right, as the fold."""
+        pre = np.cumsum(weights)
+        s = np.searchsorted(pre, t, side="right")
+        pos = np.flatnonzero(weights > 0)
+        s[s >= len(weights)] = pos[-1] if len(pos) else len(weights) - 1
+        acc = np.where(s > 0, pre[np.maximum(s - 1, 0)], 0.0)
+        return s, acc
 
     def _logical(self, phys: np.ndarray) -> np.ndarray:
         x = np.zeros_like(phys)
@@ -451,14 +449,12 @@ class ShardedState:
         total = 0.0
         for x in w:
             total = total + x
-        pick = np.empty(len(u), np.int64)
-        sub = np.empty(len(u), np.float64)
-        top = np.nextafter(1.0, 0.0)
-        for i, ui in enumerate(u):
-            t = ui * total
-            sh, acc = self._pick(w, t)
-            pick[i] = sh
-            sub[i] = min(max((t - acc) / w[sh], 0.0), top) if w[sh] > 0 else 0.0
+        t = u * total
+        pick, acc = self._pick(w, t)
+        ws = w[pick]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            sub = np.where(ws > 0, (t - acc) / ws, 0.0)
+        sub = np.clip(sub, 0.0, np.nextafter(1.0, 0.0))
         phys = np.zeros(len(u), np.float64)
         for s, v in zip(self.owned, psi):
             m = pick == s
