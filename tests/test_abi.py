@@ -137,3 +137,47 @@ def test_host_gate_matrices_match_the_oracle(L):
         _, G, cf = c.gate_matrices(i, params, generator=True)
         dU = (oracle.gate_matrix(g, theta + h) - oracle.gate_matrix(g, theta - h)) / (2 * h)
         assert np.max(np.abs(dU - (-1j * cf * G @ U))) < 1e-9, g.name
+
+
+def test_host_validation_of_gate_records(L):
+    # malformed gate records are refused at circuit creation (QS_EINVAL), before any device work
+    from paper_1912_10877_gb300 import _native as N
+
+    def gate(kind, locs, ctrl=0, vals=0, param=-1, paulis=(), mat_offset=0):
+        g = N.GateDesc()
+        g.kind, g.nlocs, g.param = N.GATE_KIND[kind], len(locs), param
+        for j, q in enumerate(locs):
+            g.locs[j] = q
+        for j, p in enumerate(paulis):
+            g.paulis[j] = p
+        g.ctrl_mask, g.ctrl_vals, g.mat_offset = ctrl, vals, mat_offset
+        return g
+
+    wide = gate("MATRIX", [0, 1, 2, 3, 4])
+    wide.nlocs = 6
+    bad = [
+        ([wide], 8, 0),                                         # more targets than QS_MAXK
+        ([gate("X", [])], 8, 0),                                # no target
+        ([gate("SWAP", [2, 2])], 8, 0),                         # repeated target
+        ([gate("SWAP", [2])], 8, 0),                            # SWAP needs two targets
+        ([gate("X", [0], ctrl=1 << 8)], 8, 0),                  # control outside the register
+        ([gate("RX", [0], param=3)], 8, 2),                     # parameter index past nparams
+        ([gate("ROT", [0, 1], paulis=(1, 4))], 8, 0),           # not a Pauli code
+        ([gate("MATRIX", [0], mat_offset=0)], 8, 0),            # matrix pool too small (empty)
+    ]
+    for gates, n, nparams in bad:
+        rc, h = _circuit(L, gates, n, nparams=nparams)
+        assert rc == N.QS_EINVAL, (gates[0].kind, L.qs_last_error())
+    for n in (0, N.QS_MAXQ + 1 if hasattr(N, "QS_MAXQ") else 41):
+        rc, h = _circuit(L, [], n)
+        assert rc == N.QS_EINVAL
+    # host-only planners: argument ranges
+    rc, h = _circuit(L, [gate("H", [0]), gate("X", [3], ctrl=1)], 8)
+    assert rc == N.QS_OK
+    cnt = ctypes.c_int()
+    assert L.qs_circuit_tile_order(h, 8, ctypes.byref(cnt), None, None) == N.QS_EINVAL
+    assert L.qs_circuit_tile_order(h, 9, ctypes.byref(cnt), None, None) == N.QS_OK and cnt.value == 2
+    assert L.qs_circuit_destroy(h) == 0
+    rc, h = _circuit(L, [gate("H", [0])], 4)
+    assert L.qs_circuit_tile_order(h, 0, ctypes.byref(cnt), None, None) == N.QS_EUNSUPPORTED
+    assert L.qs_circuit_destroy(h) == 0
