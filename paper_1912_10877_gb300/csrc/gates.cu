@@ -56,12 +56,12 @@ __global__ void __launch_bounds__(kThreads)
 k_diag1(c2_t<R>* __restrict__ psi, uint64_t nitems, IdxSpec s, int t, c2_t<R> d0, c2_t<R> d1,
         int lane_sel) {
   using T = c2_t<R>;
-  const uint64_t first = (uint64_t)blockIdx.x * (kThreads * kIPT) + threadIdx.x;
+  const uint64_t first = (uint64_t)blockIdx.x * (blockDim.x * kIPT) + threadIdx.x;
   uint64_t idx[kIPT];
   T a0[kIPT], a1[kIPT];
 #pragma unroll
   for (int u = 0; u < kIPT; ++u) {
-    const uint64_t it = first + (uint64_t)u * kThreads;
+    const uint64_t it = first + (uint64_t)u * blockDim.x;
     idx[u] = it < nitems ? item_index(it, s) : ~0ull;
     if (idx[u] == ~0ull) continue;
     if (lane_sel < 0) ld_pair(psi + idx[u], a0[u], a1[u]);
@@ -119,13 +119,13 @@ template <typename R, int OP, bool T0>
 __global__ void __launch_bounds__(kThreads)
 k_gate1(c2_t<R>* __restrict__ psi, uint64_t nitems, IdxSpec s, int t, U4<R> u, int lane_sel) {
   using T = c2_t<R>;
-  const uint64_t first = (uint64_t)blockIdx.x * (kThreads * kIPT) + threadIdx.x;
+  const uint64_t first = (uint64_t)blockIdx.x * (blockDim.x * kIPT) + threadIdx.x;
   uint64_t idx[kIPT];
   T a0[kIPT], a1[kIPT], b0[kIPT], b1[kIPT];
   const uint64_t stride = 1ull << t;
 #pragma unroll
   for (int v = 0; v < kIPT; ++v) {
-    const uint64_t it = first + (uint64_t)v * kThreads;
+    const uint64_t it = first + (uint64_t)v * blockDim.x;
     idx[v] = it < nitems ? item_index(it, s) : ~0ull;
     if (idx[v] == ~0ull) continue;
     ld_pair(psi + idx[v], a0[v], a1[v]);
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kThreads)
 k_gatek(c2_t<R>* __restrict__ psi, uint64_t nitems, IdxSpec s, const __grid_constant__ MatK<R, K> M) {
   using T = c2_t<R>;
   constexpr int D = 1 << K;
-  const uint64_t it = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+  const uint64_t it = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (it >= nitems) return;
   const uint64_t base = item_index(it, s);
   T x[D];
@@ -197,7 +197,7 @@ template <int K>
 __global__ void __launch_bounds__(kThreads)
 k_gatek_pair(float2* __restrict__ psi, uint64_t npairs, IdxSpec s, const __grid_constant__ MatK<float, K> M) {
   constexpr int D = 1 << K;
-  const uint64_t pi = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+  const uint64_t pi = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (pi >= npairs) return;
   const uint64_t base = item_index(2 * pi, s);
   float4 v[D];
@@ -219,6 +219,23 @@ k_gatek_pair(float2* __restrict__ psi, uint64_t npairs, IdxSpec s, const __grid_
 
 static inline unsigned blocks_for(uint64_t items, int per_block) {
   return (unsigned)((items + per_block - 1) / per_block);
+}
+
+// Threads per CTA for `items` work items of `ipt` items per thread: kThreads,
+// halved (down to one warp) while that leaves fewer than two CTAs per SM.  A
+// small register then spreads over many SMs instead of a few full CTAs, which
+// matters most for complex128, whose FP64 rate per SM is low on this GPU.
+static int cta_threads(uint64_t items, int ipt) {
+  static int sms[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  if (!sms[dev] && cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    sms[dev] = 1;
+  }
+  int nt = kThreads;
+  while (nt > 32 && blocks_for(items, nt * ipt) < 2u * (unsigned)sms[dev]) nt >>= 1;
+  return nt;
 }
 
 template <typename R> static c2_t<R> to_dev(cd z) {
@@ -256,12 +273,14 @@ static int launch_k_t(c2_t<R>* psi, int n, int nreg, const Plan& p, cudaStream_t
   if (items == 0) return QS_OK;
   if constexpr (std::is_same<R, float>::value && OP == OP_DENSEK && (K == 2 || K == 3)) {
     if (!((locmask | p.ctrl_mask) & 1ull) && s.item_log2 >= 1) {
-      k_gatek_pair<K><<<blocks_for(items / 2, kThreads), kThreads, 0, st>>>(psi, items / 2, s, M);
+      const int nt = cta_threads(items / 2, 1);
+      k_gatek_pair<K><<<blocks_for(items / 2, nt), nt, 0, st>>>(psi, items / 2, s, M);
       QS_LAUNCHED();
       return QS_OK;
     }
   }
-  k_gatek<R, K, OP><<<blocks_for(items, kThreads), kThreads, 0, st>>>(psi, items, s, M);
+  const int nt = cta_threads(items, 1);
+  k_gatek<R, K, OP><<<blocks_for(items, nt), nt, 0, st>>>(psi, items, s, M);
   QS_LAUNCHED();
   return QS_OK;
 }
@@ -288,14 +307,16 @@ static int launch_1(c2_t<R>* psi, int n, int nreg, const Plan& p, cudaStream_t s
     QS_TRY(make_idx(n, 1ull | p.ctrl_mask, p.ctrl_vals, &s));
     const uint64_t items = (uint64_t)nreg << s.item_log2;
     if (!items) return QS_OK;
-    k_gate1<R, OP, true><<<blocks_for(items, kThreads * kIPT), kThreads, 0, st>>>(psi, items, s, 0, u, -1);
+    const int nt = cta_threads(items, kIPT);
+    k_gate1<R, OP, true><<<blocks_for(items, nt * kIPT), nt, 0, st>>>(psi, items, s, 0, u, -1);
   } else {
     IdxSpec s;
     QS_TRY(make_idx(n, 1ull | (1ull << t) | p.ctrl_mask, p.ctrl_vals & ~1ull, &s));
     const uint64_t items = (uint64_t)nreg << s.item_log2;
     if (!items) return QS_OK;
     const int lane = (p.ctrl_mask & 1ull) ? (int)(p.ctrl_vals & 1ull) : -1;
-    k_gate1<R, OP, false><<<blocks_for(items, kThreads * kIPT), kThreads, 0, st>>>(psi, items, s, t, u, lane);
+    const int nt = cta_threads(items, kIPT);
+    k_gate1<R, OP, false><<<blocks_for(items, nt * kIPT), nt, 0, st>>>(psi, items, s, t, u, lane);
   }
   QS_LAUNCHED();
   return QS_OK;
@@ -311,7 +332,8 @@ static int launch_typed(c2_t<R>* psi, int n, int nreg, const Plan& p, cudaStream
       const uint64_t items = (uint64_t)nreg << s.item_log2;
       if (!items) return QS_OK;
       const int lane = (p.mask & 1ull) ? (int)(p.vals & 1ull) : -1;
-      k_diag1<R><<<blocks_for(items, kThreads * kIPT), kThreads, 0, st>>>(
+      const int nt = cta_threads(items, kIPT);
+      k_diag1<R><<<blocks_for(items, nt * kIPT), nt, 0, st>>>(
           psi, items, s, p.t, to_dev<R>(p.d0), to_dev<R>(p.d1), lane);
       QS_LAUNCHED();
       return QS_OK;
