@@ -283,7 +283,9 @@ def run_e2e(res, steps: int):
 
 
 def traffic_for(kernel: str):
-    """Per-launch DRAM bytes from a committed ncu summary, if the kernel source is unchanged."""
+    """(per-launch DRAM bytes, note) from a committed ncu summary: the bytes only if the
+    kernel's source file is unchanged since the capture, else None and a note naming the
+    stale figure."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -291,10 +293,11 @@ def traffic_for(kernel: str):
         entry = t[kernel]
         src = open(os.path.join(ROOT, "paper_1912_10877_gb300", "csrc", entry["source"]), "rb").read()
         if hashlib.sha256(src).hexdigest() != entry["sha256"]:
-            return None
-        return entry["dram_bytes_per_launch"]
+            return None, (f"{entry['source']} changed since the capture of {entry['dram_bytes_per_launch']} bytes "
+                          f"per launch ({entry.get('changed_since', 'see profiles/traffic.json')})")
+        return entry["dram_bytes_per_launch"], None
     except Exception:
-        return None
+        return None, "no committed capture"
 
 
 # ------------------------------------------------------------------ batched registers (fwd + grad)
@@ -813,10 +816,13 @@ def main():
     achieved = pc[dom]["gbs"]
     roof = {"kernel": kname, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
             "peak_kind": f"{peak_kind} (copy GB/s)", "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
-            "traffic": traffic_for(dom + "_c64"),
+            "traffic": None,
             "per_class_gbs": {c: round(v["gbs"], 1) for c, v in pc.items()},
             "per_class_share": {c: round(v["seconds"] / sum(x["seconds"] for x in pc.values()), 4)
                                 for c, v in pc.items()}}
+    roof["traffic"], note = traffic_for(dom + "_c64")
+    if note:
+        roof["traffic_note"] = note
     del c64
     extra = {}
     # secondary single-GPU legs run at N = 1 only (scaling runs time the headline and the sharded batch)
