@@ -313,10 +313,11 @@ int qs_circuit_tile_order(const qs_circuit* c, int tile_qubits, int* ngates, int
  * list is scheduled into passes over 13-qubit tiles (gates move earlier only
  * past gates on other qubits), one HBM round trip of the state per pass, with
  * every gate of a pass applied in shared memory / registers.  It takes
- * single-target gates with up to 3 controls plus SWAPs (as three CNOTs);
- * other circuits use the per-gate path.  QS_APPLY_TILES forces the tile
- * engine (QS_EUNSUPPORTED if the circuit does not fit) and
- * QS_APPLY_TILE_QUBITS(m) sets the tile size (5..13).  A circuit keeps its
+ * single-target gates (their controls, tested per amplitude, may sit on any
+ * qubit) plus SWAPs (as three CNOTs) on registers of 5..32 qubits; other
+ * circuits use the per-gate path.  QS_APPLY_TILES forces the tile engine
+ * (QS_EUNSUPPORTED if the circuit does not fit) and QS_APPLY_TILE_QUBITS(m)
+ * sets the tile size (9..13; registers smaller than the tile form one tile).  A circuit keeps its
  * schedule and a parameter buffer between calls, so applies of one circuit
  * must not overlap on different streams.
  * QS_APPLY_BLOCKS fuses the gates into blocks of at most k qubits

@@ -899,7 +899,7 @@ static void free_program(qs_batch_program* p) {
 static int build_program(int nreg, const qs_circuit* const* circs, const qs_observable* const* obs, int tile_qubits,
                          qs_batch_program* P) {
   const int M = tile_qubits > 0 ? tile_qubits : kBatchTile;
-  // a tile holds register qubits 0..4 plus room for any gate (target and 3 controls)
+  // a tile holds register qubits 0..4 (contiguous rows) plus a phase's 4 register bits
   if (M < kRowBits + kRB || M > kBatchTile)
     return fail(QS_EINVAL, "tile_qubits must be in %d..%d", kRowBits + kRB, kBatchTile);
   std::vector<BReg> regs(nreg);
