@@ -92,3 +92,19 @@ def test_unsupported_circuits_are_refused(qs):
         qs.tile_order(qs.Circuit(W.qft(4), 4))
     with pytest.raises(QsimError):
         qs.tile_order(qs.Circuit([W.Gate("ROT", (0, 3), theta=0.2, paulis="XX")], 8))
+
+
+def test_many_controls_schedule(qs):
+    # controls are predicates on the amplitude index, so gates with many controls
+    # (here up to 6) schedule like any other single-target gate
+    n = 12
+    rs = np.random.default_rng(3)
+    gates = []
+    for i in range(120):
+        q = [int(x) for x in rs.permutation(n)]
+        nc = int(rs.integers(0, 7))
+        name = ["H", "X", "RY", "T", "SHIFT", "Z"][i % 6]
+        gates.append(W.Gate(name, (q[0],), tuple(q[1:1 + nc]), tuple(int(v) for v in rs.integers(0, 2, nc)),
+                            theta=float(rs.uniform(-3, 3))))
+    for tile in (9, 13):
+        check_schedule(qs, n, gates, None, tile)
