@@ -444,7 +444,7 @@ int qs_backward_blocks(qs_state* s, const qs_circuit* c, const double* host_para
  * 5..30 qubits and at most 2048 parameters, observables are diagonal (sums
  * of Z strings).  circuits[r]->nqubits is register r's size.  Each circuit is
  * scheduled into fused passes over tiles of tile_qubits qubits (0 = 13) and
- * 5-qubit register phases; the program holds device tables and the backward
+ * 4-qubit register phases; the program holds device tables and the backward
  * work buffers (two complex64 copies of every register larger than a tile). */
 typedef struct qs_batch_program qs_batch_program;
 
