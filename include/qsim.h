@@ -511,7 +511,9 @@ int qs_backward_tiled(qs_state* s, const qs_circuit* c, const double* host_param
  * each level walks its values from the carried prefix, takes the first
  * value whose running sum exceeds t (else the last positive value, else the
  * last) and carries its exclusive prefix down.  collapse != 0 (requires
- * nshots == 1) projects each register onto its sample and renormalises. */
+ * nshots == 1) projects each register onto its sample and renormalises.
+ * QS_EINVAL for nshots < 1, a uniform outside [0, 1) or collapse with
+ * nshots != 1.  Synchronises the stream (host_out is written on return). */
 int qs_measure(qs_state* s, const double* host_u, int nshots, int64_t* host_out, int collapse);
 
 #ifdef __cplusplus
