@@ -319,7 +319,11 @@ int qs_circuit_tile_order(const qs_circuit* c, int tile_qubits, int* ngates, int
  * (QS_EUNSUPPORTED if the circuit does not fit) and QS_APPLY_TILE_QUBITS(m)
  * sets the tile size (9..13; registers smaller than the tile form one tile).  A circuit keeps its
  * schedule and a parameter buffer between calls, so applies of one circuit
- * must not overlap on different streams.
+ * (and qs_backward_tiled, which shares them) must not overlap on different
+ * streams: the caller serialises them.  The schedule's tables are memory of the
+ * device that was current when it was built; an apply with another device
+ * current rebuilds them there (a circuit used on two devices in turn pays
+ * that rebuild at each switch).
  * QS_APPLY_BLOCKS fuses the gates into blocks of at most k qubits
  * (QS_APPLY_BLOCK_QUBITS(k), 1..5, default 5; targets and controls both
  * count) and applies each block as one k-qubit instruction with the product
@@ -391,7 +395,11 @@ int qs_expect(qs_state* s, const qs_observable* o, double* host_out);
  * different host threads) race on it and must be serialised by the caller.
  * The first call on each device resolves the array's device address
  * (cudaGetSymbolAddress, which may load the library's GPU module); make
- * that first call before any stream capture. */
+ * that first call before any stream capture.  The address is kept for the
+ * life of the process: it assumes the device's primary context lives that
+ * long, so do not call this entry point after a cudaDeviceReset on that
+ * device (a launch failure inside this call clears the cached address, and
+ * the next call resolves it again). */
 int qs_expect_static(const void* dev_amps, int dtype, int nqubits, int nreg,
                      const qs_pauli_term* host_terms, int nterms, double* dev_out, void* stream);
 
@@ -462,7 +470,10 @@ int qs_batch_program_info(const qs_batch_program* p, int* nreg, int64_t* nparams
                           int64_t* host_param_offsets, int64_t* host_amp_offsets);
 
 /* One persistent launch on s's stream (s: a qs_batch_create state of the
- * same register sizes, QS_C64).  dev_params: the registers' parameter
+ * same register sizes, QS_C64).  The device current at
+ * qs_batch_program_create holds the program's tables and must be current here
+ * (QS_EINVAL otherwise); runs of one program must not overlap on the GPU (they
+ * share its work buffers and work counter).  dev_params: the registers' parameter
  * vectors back to back (device, FP64); dev_loss[nreg] receives <O_r>;
  * with QS_BATCH_GRAD, dev_grad (same layout as dev_params) receives the
  * gradients.  The final states psi_N are left in s. */

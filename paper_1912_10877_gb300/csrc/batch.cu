@@ -821,6 +821,7 @@ __global__ void k_batch_prep(PrepArgs a) {
 // ------------------------------------------------------------------ host: the program object
 
 struct qs_batch_program {
+  int device = -1;                   // CUDA device that holds the tables below
   int nreg = 0;
   std::vector<int> nq;
   std::vector<int64_t> param_off;    // nreg + 1
@@ -889,10 +890,15 @@ static int upload(T** dst, const std::vector<T>& v) {
 
 static void free_program(qs_batch_program* p) {
   if (!p) return;
+  // the tables live on the device that built them, which need not be the current one
+  int cur = -1;
+  const bool swap = p->device >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != p->device &&
+                    cudaSetDevice(p->device) == cudaSuccess;
   void* ptrs[] = {p->regs, p->order, p->passes, p->phases, p->fops, p->bops, p->terms, p->gspec, p->fmem,
                   p->bgate, p->dmem, p->dref, p->dtab, p->counter, p->wpsi, p->wlam, p->dparams};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  if (swap) cudaSetDevice(cur);
   delete p;
 }
 
@@ -902,6 +908,7 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
   // a tile holds register qubits 0..4 (contiguous rows) plus a phase's 4 register bits
   if (M < kRowBits + kRB || M > kBatchTile)
     return fail(QS_EINVAL, "tile_qubits must be in %d..%d", kRowBits + kRB, kBatchTile);
+  QS_CUDA(cudaGetDevice(&P->device));
   std::vector<BReg> regs(nreg);
   std::vector<TPass> passes;
   std::vector<TPhase> phases;
@@ -1220,8 +1227,12 @@ static void expand_swaps(const qs_circuit* c, qs_circuit* out) {
 }
 
 // the circuit's tile-engine schedule for tiles of M qubits, built once and cached
+// on the current device (a schedule built on another device is rebuilt here: its
+// tables are that device's memory)
 static int ensure_schedule(const qs_circuit* c, int M) {
-  if (c->fused && c->fused_tile == M) return QS_OK;
+  int dev = 0;
+  QS_CUDA(cudaGetDevice(&dev));
+  if (c->fused && c->fused_tile == M && c->fused->device == dev) return QS_OK;
   if (c->fused) {
     free_program(c->fused);
     c->fused = nullptr;
@@ -1509,6 +1520,10 @@ int qs_batch_run(qs_state* s, const qs_batch_program* p, const double* dev_param
   if (p->param_off[p->nreg] > 0 && !dev_params) return fail(QS_EINVAL, "params is NULL");
   const bool grad = (flags & QS_BATCH_GRAD) != 0;
   if (grad && !dev_grad) return fail(QS_EINVAL, "grad is NULL");
+  int dev = 0;
+  QS_CUDA(cudaGetDevice(&dev));
+  if (dev != p->device)
+    return fail(QS_EINVAL, "the program was built on device %d; the current device is %d", p->device, dev);
   cudaStream_t st = s->stream;
   QS_TRY(launch_prep(p, dev_params, true, st));
   QS_CUDA(cudaMemsetAsync(p->counter, 0, sizeof(int), st));

@@ -520,6 +520,8 @@ extern "C" int qs_expect_static(const void* dev_amps, int dtype, int nqubits, in
   }
   double* partials = nullptr;
   QS_TRY(static_partials(&partials));
+  int cur_dev = 0;
+  cudaGetDevice(&cur_dev);
   // terms ordered by x mask (insertion sort on the stack, stable)
   int order[kStaticTerms];
   for (int t = 0; t < nterms; ++t) {
@@ -560,6 +562,7 @@ extern "C" int qs_expect_static(const void* dev_amps, int dtype, int nqubits, in
     base += tg.nt;
   }
   k_expect_final_static<<<(nreg + 127) / 128, 128, 0, st>>>(partials, (int)nblk, nterms, co, nreg, dev_out);
+  if (cudaPeekAtLastError() != cudaSuccess) g_static_addr[cur_dev] = nullptr;  // resolve again next call
   QS_LAUNCHED();
   return QS_OK;
 }

@@ -1,0 +1,159 @@
+"""The large workload's pipeline exactly as the bench times it, against the oracle.
+
+Pipeline (complex64): the QFT with its swap network on a seeded basis state on
+the tile engine, the depth-20 brickwork of Rz + Haar SU(2) + CZ as fused blocks
+of at most 5 qubits (QS_APPLY_BLOCKS; the consecutive 4/5-qubit blocks take the
+TMA-fed tensor-core kernel), then the reversible gradient of <Z_1> over the same
+blocks (qs_backward_blocks with the tensor-core Grams), which also uncomputes the
+state back to the brickwork's input (Sec. "Reverse Mode", Eqs. apply-back and
+outer-product).
+
+- n = 22: every amplitude, the loss, every gradient entry and the uncomputed
+  state against the oracle at full size.
+- n = 32 (32 GiB): the oracle cannot hold the state, but <Z_1> only sees the
+  backward light cone of qubit 0.  The QFT of a basis state with the swap
+  network is a product state (App. "Extending QBIR": |x> -> sum_k
+  e^{2 pi i rev(x) rev(k) / N} |k> / sqrt(N), whose phase is linear in the bits
+  of k), so dropping every gate outside the light cone leaves a 20-qubit
+  circuit on the first 20 qubits with the same loss and the same gradient for
+  every angle (angles outside the cone have gradient 0).  The oracle runs that
+  circuit; the GPU's 640 gradient entries, its loss, the QFT amplitudes at
+  sampled indices (closed form) and the state uncomputed by the backward pass
+  (again the QFT output) are checked against it.
+
+The measured errors are recorded as test properties (junit xml).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEPTH = 20
+
+
+@pytest.fixture(scope="module")
+def qs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1912_10877_gb300 import qsim
+    qsim.set_tensor_cores(1)
+    return qsim
+
+
+def rel(got, want):
+    return float(np.max(np.abs(got - want)) / max(1e-300, np.max(np.abs(want))))
+
+
+def bench_pipeline(qs, n, seed=0):
+    """QFT + swaps on tiles, brickwork as 5-qubit blocks, gradient over the blocks."""
+    x = W.random_basis(n, seed=seed)
+    bgates, bparams = W.brickwork(n, DEPTH, seed=seed)
+    st = qs.State(n, dtype=torch.complex64)
+    st.reset([x])
+    st.apply_circuit(qs.Circuit(W.qft(n, swaps=True), n), tiles=True)
+    bcirc = qs.Circuit(bgates, n, nparams=len(bparams))
+    return x, bgates, bparams, st, bcirc
+
+
+def qft_closed_form(n, x, ks):
+    """Amplitudes of QFT-with-swaps |x> at basis indices ks (little-endian):
+    e^{2 pi i rev(x) rev(k) / N} / sqrt(N), rev = n-bit reversal."""
+    N = 1 << n
+
+    def rev(v):
+        return int(format(int(v), "0%db" % n)[::-1], 2)
+
+    rx = rev(x)
+    return np.array([np.exp(2j * np.pi * ((rx * rev(k)) % N) / N) for k in ks]) / math.sqrt(N)
+
+
+def light_cone(gates, n, q0):
+    """Qubits whose input state can reach qubit q0 at the end: walk the gate list
+    backwards, a gate touching the cone adds all its qubits."""
+    cone = {q0}
+    for g in reversed(gates):
+        qs_ = set(g.locs) | set(g.ctrl_locs)
+        if qs_ & cone:
+            cone |= qs_
+    return cone
+
+
+def restricted_gates(gates, keep):
+    return [g for g in gates if (set(g.locs) | set(g.ctrl_locs)) <= keep]
+
+
+def test_large_pipeline_blocks_n22_against_oracle(qs, record_property):
+    n = 22
+    x, bgates, bparams, st, bcirc = bench_pipeline(qs, n)
+    psi0 = oracle.apply_circuit(oracle.basis_state(n, x), n, W.qft(n, swaps=True))
+    got0 = st.numpy()
+    err_qft = float(np.max(np.abs(got0 - psi0)))
+    st.apply_circuit(bcirc, bparams, blocks=5)
+    psiN = oracle.apply_circuit(psi0, n, bgates, bparams)
+    err_state = float(np.max(np.abs(st.numpy() - psiN)))
+    loss, grad = qs.backward_blocks(st, bcirc, bparams, qs.Observable(W.z_on(0)), kmax=5)
+    rl, rg = oracle.gradient(psi0, n, bgates, bparams, W.z_on(0))
+    err_grad = rel(grad, rg)
+    err_back = float(np.max(np.abs(st.numpy() - psi0)))
+    for k, v in (("qft_state_abs", err_qft), ("brickwork_state_abs", err_state), ("loss_abs", abs(loss - rl)),
+                 ("grad_rel", err_grad), ("uncomputed_state_abs", err_back)):
+        record_property(k, v)
+    print(f"n=22 blocks pipeline: qft {err_qft:.2e} state {err_state:.2e} loss {abs(loss - rl):.2e} "
+          f"grad {err_grad:.2e} uncompute {err_back:.2e}")
+    assert err_qft < 2e-5 and err_state < 2e-5
+    assert abs(loss - rl) < 1e-5
+    assert err_grad < 1e-4
+    assert err_back < 2e-5
+
+
+def test_large_pipeline_blocks_n32_light_cone_oracle(qs, record_property):
+    n = 32
+    x, bgates, bparams, st, bcirc = bench_pipeline(qs, n)
+    N = 1 << n
+    ks = np.concatenate([np.arange(8), W.rng(1).integers(0, N, 56), [N - 1]]).astype(np.int64)
+    want_qft = qft_closed_form(n, x, ks)
+    kt = torch.as_tensor(ks, device="cuda")
+    got = st.buffer[kt].cpu().numpy().astype(np.complex128)
+    err_qft = float(np.max(np.abs(got - want_qft)) * math.sqrt(N))
+    st.apply_circuit(bcirc, bparams, blocks=5)
+    nrm = float(torch.sum(torch.abs(st.buffer.to(torch.complex128)) ** 2).item())
+    loss, grad = qs.backward_blocks(st, bcirc, bparams, qs.Observable(W.z_on(0)), kmax=5)
+    back = st.buffer[kt].cpu().numpy().astype(np.complex128)
+    err_back = float(np.max(np.abs(back - want_qft)) * math.sqrt(N))
+    # the oracle on the light cone of qubit 0
+    cone = light_cone(bgates, n, 0)
+    m = len(cone)
+    assert cone == set(range(m)) and m == DEPTH, sorted(cone)
+    sub = restricted_gates(bgates, cone)
+    # product input on qubits 0..m-1: qubit j carries (|0> + e^{2 pi i rev(x) / 2^(j+1)} |1>) / sqrt(2)
+    rx = int(format(x, "0%db" % n)[::-1], 2)
+    psi_in = np.array([1.0 + 0j])
+    for j in range(m):
+        ph = np.exp(2j * np.pi * (rx % (1 << (j + 1))) / (1 << (j + 1)))
+        psi_in = np.kron(np.array([1.0, ph]) / math.sqrt(2.0), psi_in)  # qubit j is bit j
+    assert np.max(np.abs(psi_in[ks[ks < (1 << m)]] * math.sqrt(1 << m) -
+                         qft_closed_form(n, x, ks[ks < (1 << m)]) * math.sqrt(N))) < 1e-9
+    rl, rg_sub = oracle.gradient(psi_in, m, sub, bparams, W.z_on(0))
+    # gradient entries: Rz of layer l on qubit q is parameter l * n + q
+    want = rg_sub.copy()
+    used = {g.param for g in sub if g.param is not None}
+    outside = np.array([p not in used for p in range(len(bparams))])
+    want[outside] = 0.0
+    err_grad = rel(grad, want)
+    for k, v in (("qft_amp_x_sqrtN", err_qft), ("norm_dev", abs(nrm - 1.0)), ("loss_abs", abs(loss - rl)),
+                 ("grad_rel", err_grad), ("uncomputed_amp_x_sqrtN", err_back),
+                 ("outside_cone_max", float(np.max(np.abs(grad[outside]))))):
+        record_property(k, v)
+    print(f"n=32 blocks pipeline: qft {err_qft:.2e} |norm-1| {abs(nrm - 1):.2e} loss {abs(loss - rl):.2e} "
+          f"grad {err_grad:.2e} uncompute {err_back:.2e} (light cone {m} qubits, {int(outside.sum())} angles outside)")
+    assert err_qft < 1e-3
+    assert abs(nrm - 1.0) < 1e-4
+    assert abs(loss - rl) < 1e-5
+    assert err_grad < 1e-4
+    assert err_back < 2e-3

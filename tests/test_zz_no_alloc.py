@@ -3,13 +3,16 @@ memory (frameworks owning all device memory, loops that must avoid
 cudaMalloc/cudaFree, fixed memory budgets).  Its scratch is a fixed device
 array inside the library, so this file checks, through the C ABI, that two
 calls in a row give the same values as qs_expect (which uses allocated
-scratch), within the tolerances the other GPU tests use, and that requests
-larger than the fixed array are rejected.  Collected last on purpose."""
+scratch) and as the FP64 oracle's expectation of the same amplitudes (a
+complex64 state is promoted exactly, so both precisions are held to 1e-12),
+and that requests larger than the fixed array are rejected.  Collected last on
+purpose."""
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import workloads as W
 
 torch = pytest.importorskip("torch")
@@ -61,6 +64,8 @@ def test_static_matches_allocating_entry_point_twice(env, dt):
         st = qs.State(n, dtype=TDT[dt], nbatch=nreg)
         st.upload(np.concatenate([W.haar_state(n, seed=r + 7 * n) for r in range(nreg)]))
         ref = st.expect(qs.Observable(terms))
+        amps = st.numpy().astype(np.complex128).reshape(nreg, 1 << n)
+        want = np.array([oracle.expect(amps[r], n, terms) for r in range(nreg)])
         out = torch.full((nreg,), float("nan"), dtype=torch.float64, device="cuda")
         arr = _terms(terms)
         stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
@@ -72,6 +77,7 @@ def test_static_matches_allocating_entry_point_twice(env, dt):
             got = out.cpu().numpy()
             assert np.all(np.isfinite(got)), (n, nreg, call)
             assert np.max(np.abs(got - ref)) < TOL[dt], (n, nreg, call)
+            assert np.max(np.abs(got - want)) < 1e-12, (n, nreg, call, np.max(np.abs(got - want)))
 
 
 def test_static_rejects_oversize_requests(env):
