@@ -462,6 +462,30 @@ typedef struct qs_batch_program qs_batch_program;
 int qs_batch_program_create(int nreg, const qs_circuit* const* circuits,
                             const qs_observable* const* observables, int tile_qubits,
                             qs_batch_program** out);
+
+/* The same with the fusion width and the precision chosen by the caller.
+ * phase_qubits (2..4, 0 = 4): register qubits per phase, i.e. every gate on
+ * those qubits inside a phase is applied to 2^phase_qubits amplitudes held in
+ * one thread's registers (the batched engine's k-qubit fusion); the tile then
+ * holds at most 9 + phase_qubits qubits (512 threads x 2^phase_qubits
+ * amplitudes), tile_qubits 0 = that maximum.
+ * flags QS_BATCH_PRECISE (phase_qubits 2 or 3): the forward pass stays in
+ * complex64 with FP32 arithmetic, but every gate matrix is applied with its
+ * FP32 rounding error compensated (U = U_hi + U_lo, both FP32, U_lo = the
+ * FP64 matrix minus U_hi, the U_lo terms added first; this removes the
+ * coherent error of rounding the same matrix for every amplitude); the
+ * reversible uncompute of psi and lambda (Sec. "Reverse Mode", Eq. apply-back)
+ * runs in double-float arithmetic (each real a pair hi + lo of FP32 values,
+ * about 48 significant bits: FP64-class accuracy on the FP32 units; psi and
+ * lambda of registers larger than the tile stream through double-float work
+ * buffers, 16 bytes per amplitude each); gradient contributions are FP32
+ * products of the hi parts summed in FP32 over a thread's pairs and a warp,
+ * then in FP64.  The program's shape is read back with qs_batch_program_shape. */
+#define QS_BATCH_PRECISE 1
+int qs_batch_program_create_ex(int nreg, const qs_circuit* const* circuits,
+                               const qs_observable* const* observables, int tile_qubits,
+                               int phase_qubits, int flags, qs_batch_program** out);
+int qs_batch_program_shape(const qs_batch_program* p, int* tile_qubits, int* phase_qubits, int* flags);
 int qs_batch_program_destroy(qs_batch_program* p);
 
 /* Register count, total parameters, parameter offsets (nreg + 1, host) and
@@ -492,6 +516,17 @@ int qs_batch_run(qs_state* s, const qs_batch_program* p, const double* dev_param
 int qs_batch_autotune(int nreg, const qs_circuit* const* circuits, const qs_observable* const* observables,
                       qs_state* s, const double* dev_params, double* dev_loss, double* dev_grad, int reps,
                       int* best_tile, int* ncand, int32_t* host_tiles, double* host_ms);
+
+/* Autotuner of the fusion width and the tile shape together: for every phase
+ * width from 4 (3 with QS_BATCH_PRECISE) down to 2 and the three largest tile
+ * sizes that width allows, builds the program with flags, runs it as
+ * qs_batch_autotune does, and returns the fastest in *best_tile and
+ * *best_phase (pass them to qs_batch_program_create_ex).  host_tiles /
+ * host_phases / host_ms list the candidates as in qs_batch_autotune. */
+int qs_batch_autotune_ex(int nreg, const qs_circuit* const* circuits, const qs_observable* const* observables,
+                         int flags, qs_state* s, const double* dev_params, double* dev_loss, double* dev_grad,
+                         int reps, int* best_tile, int* best_phase, int* ncand, int32_t* host_tiles,
+                         int32_t* host_phases, double* host_ms);
 
 /* Device bytes of the work buffer of qs_backward_tiled (two complex64
  * copies: psi and lambda). */
@@ -526,6 +561,17 @@ int qs_backward_tiled(qs_state* s, const qs_circuit* c, const double* host_param
  * QS_EINVAL for nshots < 1, a uniform outside [0, 1) or collapse with
  * nshots != 1.  Synchronises the stream (host_out is written on return). */
 int qs_measure(qs_state* s, const double* host_u, int nshots, int64_t* host_out, int collapse);
+
+/* qs_measure with its uniforms generated on the device from a seed, so that a
+ * seed alone fixes the sampled indices (bit for bit, whatever the caller's
+ * random source).  The paper fixes no random source; this library's is
+ * SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): draw k (k >= 1) is the
+ * 64-bit finaliser (x ^= x >> 30, x *= 0xBF58476D1CE4E5B9, x ^= x >> 27,
+ * x *= 0x94D049BB133111EB, x ^= x >> 31) of x = seed + k * 0x9E3779B97F4A7C15
+ * (mod 2^64), and u = (x >> 11) * 2^-53.  Register r's shot j takes draw
+ * k = r * nshots + j + 1; the walk from u is qs_measure's.  Same arguments,
+ * errors and synchronisation as qs_measure. */
+int qs_measure_seeded(qs_state* s, uint64_t seed, int nshots, int64_t* host_out, int collapse);
 
 #ifdef __cplusplus
 }

@@ -21,6 +21,8 @@ Functions and the passages they follow:
   fd_gradient     central finite differences of ``expect``
   sample/collapse Sec. "Instructions on Quantum Registers" (measure / measure!),
                   with the deterministic sampling contract stated in the C file
+  sample_seeded   the same with uniforms from SplitMix64 (Steele, Lea and Flood
+                  2014), the library's seeded-measurement contract
 """
 from __future__ import annotations
 
@@ -270,6 +272,35 @@ def sample(psi, n, u) -> np.ndarray:
     _check(lib().orc_sample(psi.ctypes.data, n, _dp(u), len(u),
                             out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))), "sample")
     return out
+
+
+def splitmix64(seed: int, k: int) -> int:
+    """The k-th output (k >= 1) of SplitMix64 started from ``seed``."""
+    f = lib().orc_splitmix64
+    f.restype = ctypes.c_uint64
+    f.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+    return int(f(seed, k))
+
+
+def seeded_uniforms(seed: int, nreg: int, nshots: int) -> np.ndarray:
+    """Uniforms [nreg][nshots] of the seeded measurement: register r's shot j is
+    draw k = r * nshots + j + 1 of SplitMix64(seed), u = (x >> 11) * 2^-53."""
+    u = np.zeros(nreg * nshots)
+    f = lib().orc_seeded_uniforms
+    f.restype = None
+    f.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]
+    f(seed, 0, nreg * nshots, _dp(u))
+    return u.reshape(nreg, nshots)
+
+
+def sample_seeded(psi, n, seed: int, nshots: int, reg: int = 0) -> np.ndarray:
+    """``sample`` with register ``reg``'s uniforms of the seeded measurement."""
+    u = np.zeros(nshots)
+    f = lib().orc_seeded_uniforms
+    f.restype = None
+    f.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]
+    f(seed, reg * nshots, nshots, _dp(u))
+    return sample(psi, n, u)
 
 
 def collapse(psi, n, x) -> np.ndarray:

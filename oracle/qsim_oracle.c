@@ -434,3 +434,25 @@ void orc_collapse(cplx* psi, int n, int64_t x) {
   for (int64_t i = 0; i < dim; ++i) psi[i] = 0;
   psi[x] = r > 0 ? a / r : 1.0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Seeded measurement (the paper fixes no random source; this is the         */
+/* library's contract).  The uniform of draw k (k = 1, 2, ...) is the k-th     */
+/* output of SplitMix64 started from `seed` (Steele, Lea and Flood,           */
+/* "Fast splittable pseudorandom number generators", OOPSLA 2014, with the    */
+/* 64-bit finaliser of Stafford's "Mix13"): the generator's state after k     */
+/* steps is seed + k * gamma, gamma = 0x9E3779B97F4A7C15, and the output is    */
+/* the finaliser of that state.  u = (x >> 11) * 2^-53 keeps the top 53 bits. */
+/* Register r's shot j uses draw k = r * nshots + j + 1.                       */
+
+uint64_t orc_splitmix64(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + k * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+void orc_seeded_uniforms(uint64_t seed, uint64_t k0, int64_t count, double* u) {
+  for (int64_t i = 0; i < count; ++i)
+    u[i] = (double)(orc_splitmix64(seed, k0 + (uint64_t)i + 1) >> 11) * (1.0 / 9007199254740992.0);
+}

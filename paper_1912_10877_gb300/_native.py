@@ -15,6 +15,7 @@ QS_OK, QS_EINVAL, QS_ENOMEM, QS_EDEVICE, QS_ETIMEDOUT, QS_EUNSUPPORTED = 0, -1, 
 QS_C64, QS_C128 = 0, 1
 QS_MAXK = 5
 QS_BATCH_RESET, QS_BATCH_GRAD = 1, 2
+QS_BATCH_PRECISE = 1
 QS_APPLY_PER_REGISTER, QS_APPLY_UNFUSED, QS_APPLY_TILES, QS_APPLY_BLOCKS = 1, 2, 4, 8
 QS_OPT_TENSOR_CORES = 1
 
@@ -100,7 +101,12 @@ SIGNATURES = {
     "qs_backward_blocks": ([_P, _P, _PD, _P, _I, _P, _PD, _PD], _I),
     "qs_backward_tiled": ([_P, _P, _PD, _P, _I, _P, _PD, _PD], _I),
     "qs_measure": ([_P, _PD, _I, _PI64, _I], _I),
+    "qs_measure_seeded": ([_P, ctypes.c_uint64, _I, _PI64, _I], _I),
     "qs_batch_program_create": ([_I, _PP, _PP, _I, _PP], _I),
+    "qs_batch_program_create_ex": ([_I, _PP, _PP, _I, _I, _I, _PP], _I),
+    "qs_batch_program_shape": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "qs_batch_autotune_ex": ([_I, _PP, _PP, _I, _P, _P, _P, _P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                              ctypes.POINTER(_I), _PI32, _PI32, _PD], _I),
     "qs_batch_program_destroy": ([_P], _I),
     "qs_batch_program_info": ([_P, ctypes.POINTER(_I), _PI64, _PI64, _PI64], _I),
     "qs_batch_run": ([_P, _P, _P, _P, _P, _I], _I),

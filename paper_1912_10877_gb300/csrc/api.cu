@@ -55,7 +55,7 @@ int ensure_ws(qs_state* s, Workspace& w, size_t bytes) {
 int expect_raw(const void* data, int dtype, int n, int nreg, const qs_observable* o, qs_state* ws_owner,
                double* host_out);
 int measure_one(void* data, int dtype, int n, const double* host_u, int nshots, int64_t* host_out,
-                int collapse, qs_state* owner);
+                int collapse, qs_state* owner, const uint64_t* seed, uint64_t k0);
 int reset_basis(qs_state* s, const uint64_t* host_basis);
 int backward(qs_state* s, const qs_circuit* c, const double* params, const qs_observable* o, int ckpt_every,
              const void* ckpts, void* work, double* host_grad, double* host_loss);
@@ -492,7 +492,18 @@ int qs_measure(qs_state* s, const double* u, int nshots, int64_t* out, int colla
   const size_t ab = amp_bytes(s->dtype);
   for (int r = 0; r < s->nreg; ++r)
     QS_TRY(measure_one((char*)s->data + ab * s->off[r], s->dtype, s->nq[r], u + (size_t)r * nshots, nshots,
-                       out + (size_t)r * nshots, collapse, s));
+                       out + (size_t)r * nshots, collapse, s, nullptr, 0));
+  return QS_OK;
+}
+
+int qs_measure_seeded(qs_state* s, uint64_t seed, int nshots, int64_t* out, int collapse) {
+  if (!s || !out) return fail(QS_EINVAL, "null argument");
+  if (nshots < 1) return fail(QS_EINVAL, "nshots must be >= 1");
+  if (collapse && nshots != 1) return fail(QS_EINVAL, "collapse needs nshots == 1");
+  const size_t ab = amp_bytes(s->dtype);
+  for (int r = 0; r < s->nreg; ++r)
+    QS_TRY(measure_one((char*)s->data + ab * s->off[r], s->dtype, s->nq[r], nullptr, nshots,
+                       out + (size_t)r * nshots, collapse, s, &seed, (uint64_t)r * (uint64_t)nshots));
   return QS_OK;
 }
 

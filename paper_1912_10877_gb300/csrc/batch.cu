@@ -57,8 +57,13 @@ struct BTerm {
 
 struct BArgs {
   float2* state;
-  float2* wpsi;          // backward work copies of psi (n > 13)
-  float2* wlam;          // lambda (n > 13)
+  float2* wpsi;          // backward work copies of psi (registers larger than the tile)
+  float2* wlam;          // lambda (same)
+  float4* wpsif;         // precise path: double-float psi work copies
+  float4* wlamf;         // precise path: double-float lambda
+  const float2* flo;     // precise path: corrections U - U_hi of the forward ops (4 each)
+  const float2* dtlo;    // precise path: corrections of the diagonal tables (16 each)
+  const float2* blo;     // precise path: corrections of the backward ops' U^dagger (4 each)
   const BReg* regs;
   const int32_t* order;
   const TPass* passes;
@@ -76,7 +81,17 @@ struct BArgs {
 
 enum { BF_RESET = 1, BF_GRAD = 2 };
 
-// ------------------------------------------------------------------ device: ops on 16 amplitudes
+// ------------------------------------------------------------------ device: ops on the amplitudes of a phase
+//
+// A phase of RB register bits (RB = 2..4) keeps 2^RB amplitudes per thread in
+// registers.  The complex64 path computes in FP32.  The precise path of the
+// batched engine (PREC) applies the forward gates with compensated matrices
+// (every FP32 entry U_hi has a correction U_lo = U - U_hi kept beside it, so
+// the state sees U to ~2^-48 while it is still stored and multiplied in FP32)
+// and runs the reversible uncompute of psi and lambda in double-float
+// arithmetic (each real number a pair hi + lo of FP32 values, ~48 bits): the
+// uncompute is FP64-class without the FP64 units, which run at 1/64 of the
+// FP32 rate on this GPU.
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -116,49 +131,90 @@ __device__ __forceinline__ void pair_apply(float2& a, float2& b, float2 u0, floa
   }
 }
 
-template <int T, int KIND, bool CTRL>
-__device__ __forceinline__ void op_fwd(float2 (&x)[16], const TOp& op) {
+// compensated forward pair: (a, b) <- (U_hi + U_lo)(a, b) in FP32, the small
+// U_lo terms first so that every large product enters through one FMA
+template <int KIND>
+__device__ __forceinline__ void pair_apply_c(float2& a, float2& b, const float2 (&u)[4], const float2 (&w)[4]) {
+  if (KIND == TK_SWAP) {
+    const float2 t = a; a = b; b = t;
+  } else if (KIND == TK_DIAG) {
+    a = cmaf(u[0], a, cmulf(w[0], a));
+    b = cmaf(u[3], b, cmulf(w[3], b));
+  } else {
+    const float2 na = cmaf(u[1], b, cmaf(u[0], a, cmaf(w[1], b, cmulf(w[0], a))));
+    const float2 nb = cmaf(u[3], b, cmaf(u[2], a, cmaf(w[3], b, cmulf(w[2], a))));
+    a = na; b = nb;
+  }
+}
+
+template <int RB, int T, int KIND, bool CTRL>
+__device__ __forceinline__ void op_fwd(float2 (&x)[1 << RB], const TOp& op) {
   const int cm = op.cmask, cv = op.cval;
   const float2 u0 = op.u[0], u1 = op.u[1], u2 = op.u[2], u3 = op.u[3];
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
+  for (int j = 0; j < (1 << RB); ++j) {
     if (j & (1 << T)) continue;
     if (CTRL && (j & cm) != cv) continue;
     pair_apply<KIND>(x[j], x[j | (1 << T)], u0, u1, u2, u3);
   }
 }
 
-template <int T>
-__device__ __forceinline__ void op_fwd_k(float2 (&x)[16], const TOp& op) {
-  if (op.kind == TK_SWAP) op_fwd<T, TK_SWAP, true>(x, op);
-  else if (op.cmask == 0) {
-    if (op.kind == TK_DIAG) op_fwd<T, TK_DIAG, false>(x, op);
-    else op_fwd<T, TK_DENSE, false>(x, op);
-  } else {
-    if (op.kind == TK_DIAG) op_fwd<T, TK_DIAG, true>(x, op);
-    else op_fwd<T, TK_DENSE, true>(x, op);
+template <int RB, int T, int KIND, bool CTRL>
+__device__ __forceinline__ void op_fwd_c(float2 (&x)[1 << RB], const TOp& op, const float2* lo) {
+  const int cm = op.cmask, cv = op.cval;
+  const float2 u[4] = {op.u[0], op.u[1], op.u[2], op.u[3]};
+  const float2 w[4] = {lo[0], lo[1], lo[2], lo[3]};
+#pragma unroll
+  for (int j = 0; j < (1 << RB); ++j) {
+    if (j & (1 << T)) continue;
+    if (CTRL && (j & cm) != cv) continue;
+    pair_apply_c<KIND>(x[j], x[j | (1 << T)], u, w);
   }
 }
 
-__device__ __forceinline__ void apply_fwd(float2 (&x)[16], const TOp& op) {
+template <int RB, int T, bool COMP>
+__device__ __forceinline__ void op_fwd_k(float2 (&x)[1 << RB], const TOp& op, const float2* lo) {
+  if (COMP) {
+    if (op.kind == TK_SWAP) op_fwd<RB, T, TK_SWAP, true>(x, op);
+    else if (op.cmask == 0) {
+      if (op.kind == TK_DIAG) op_fwd_c<RB, T, TK_DIAG, false>(x, op, lo);
+      else op_fwd_c<RB, T, TK_DENSE, false>(x, op, lo);
+    } else {
+      if (op.kind == TK_DIAG) op_fwd_c<RB, T, TK_DIAG, true>(x, op, lo);
+      else op_fwd_c<RB, T, TK_DENSE, true>(x, op, lo);
+    }
+    return;
+  }
+  if (op.kind == TK_SWAP) op_fwd<RB, T, TK_SWAP, true>(x, op);
+  else if (op.cmask == 0) {
+    if (op.kind == TK_DIAG) op_fwd<RB, T, TK_DIAG, false>(x, op);
+    else op_fwd<RB, T, TK_DENSE, false>(x, op);
+  } else {
+    if (op.kind == TK_DIAG) op_fwd<RB, T, TK_DIAG, true>(x, op);
+    else op_fwd<RB, T, TK_DENSE, true>(x, op);
+  }
+}
+
+template <int RB, bool COMP>
+__device__ __forceinline__ void apply_fwd(float2 (&x)[1 << RB], const TOp& op, const float2* lo) {
   switch (op.t) {
-    case 0: op_fwd_k<0>(x, op); break;
-    case 1: op_fwd_k<1>(x, op); break;
-    case 2: op_fwd_k<2>(x, op); break;
-    default: op_fwd_k<3>(x, op); break;
+    case 0: op_fwd_k<RB, 0, COMP>(x, op, lo); break;
+    case 1: op_fwd_k<RB, 1, COMP>(x, op, lo); break;
+    case 2: if constexpr (RB > 2) op_fwd_k<RB, 2, COMP>(x, op, lo); break;
+    default: if constexpr (RB > 3) op_fwd_k<RB, 3, COMP>(x, op, lo); break;
   }
 }
 
 // Backward op: first this thread's share of Im<lambda|G|psi> over its pairs
 // (GK 0: none; 1: diagonal generator diag(g0, g3); 2: X; 3: Y), then
 // psi <- U^dag psi and lambda <- U^dag lambda.
-template <int T, int KIND, int GK, bool CTRL>
-__device__ __forceinline__ float op_bwd(float2 (&x)[16], float2 (&l)[16], const TOp& op, float g0, float g3) {
+template <int RB, int T, int KIND, int GK, bool CTRL>
+__device__ __forceinline__ float op_bwd(float2 (&x)[1 << RB], float2 (&l)[1 << RB], const TOp& op, float g0, float g3) {
   const int cm = op.cmask, cv = op.cval;
   const float2 u0 = op.u[0], u1 = op.u[1], u2 = op.u[2], u3 = op.u[3];
   float acc = 0.f;
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
+  for (int j = 0; j < (1 << RB); ++j) {
     if (j & (1 << T)) continue;
     if (CTRL && (j & cm) != cv) continue;
     const int k = j | (1 << T);
@@ -171,33 +227,191 @@ __device__ __forceinline__ float op_bwd(float2 (&x)[16], float2 (&l)[16], const 
   return acc;
 }
 
-template <int T, bool CTRL>
-__device__ __forceinline__ float op_bwd_c(float2 (&x)[16], float2 (&l)[16], const TOp& op) {
+template <int RB, int T, bool CTRL>
+__device__ __forceinline__ float op_bwd_c(float2 (&x)[1 << RB], float2 (&l)[1 << RB], const TOp& op) {
   switch (op.gen) {
-    case GEN_X: return op_bwd<T, TK_RX, 2, CTRL>(x, l, op, 0.f, 0.f);
-    case GEN_Y: return op_bwd<T, TK_RY, 3, CTRL>(x, l, op, 0.f, 0.f);
-    case GEN_Z: return op_bwd<T, TK_DIAG, 1, CTRL>(x, l, op, 1.f, -1.f);
-    case GEN_P1: return op_bwd<T, TK_DIAG, 1, CTRL>(x, l, op, 0.f, 1.f);
-    default: return op_bwd<T, TK_DIAG, 1, CTRL>(x, l, op, 1.f, 1.f);  // GEN_I
+    case GEN_X: return op_bwd<RB, T, TK_RX, 2, CTRL>(x, l, op, 0.f, 0.f);
+    case GEN_Y: return op_bwd<RB, T, TK_RY, 3, CTRL>(x, l, op, 0.f, 0.f);
+    case GEN_Z: return op_bwd<RB, T, TK_DIAG, 1, CTRL>(x, l, op, 1.f, -1.f);
+    case GEN_P1: return op_bwd<RB, T, TK_DIAG, 1, CTRL>(x, l, op, 0.f, 1.f);
+    default: return op_bwd<RB, T, TK_DIAG, 1, CTRL>(x, l, op, 1.f, 1.f);  // GEN_I
   }
 }
 
-template <int T>
-__device__ __forceinline__ float op_bwd_t(float2 (&x)[16], float2 (&l)[16], const TOp& op) {
+template <int RB, int T>
+__device__ __forceinline__ float op_bwd_t(float2 (&x)[1 << RB], float2 (&l)[1 << RB], const TOp& op) {
   if (op.gen == GEN_NONE) {
-    if (op.kind == TK_SWAP) return op_bwd<T, TK_SWAP, 0, true>(x, l, op, 0.f, 0.f);
-    if (op.kind == TK_DIAG) return op_bwd<T, TK_DIAG, 0, true>(x, l, op, 0.f, 0.f);
-    return op_bwd<T, TK_DENSE, 0, true>(x, l, op, 0.f, 0.f);
+    if (op.kind == TK_SWAP) return op_bwd<RB, T, TK_SWAP, 0, true>(x, l, op, 0.f, 0.f);
+    if (op.kind == TK_DIAG) return op_bwd<RB, T, TK_DIAG, 0, true>(x, l, op, 0.f, 0.f);
+    return op_bwd<RB, T, TK_DENSE, 0, true>(x, l, op, 0.f, 0.f);
   }
-  return op.cmask ? op_bwd_c<T, true>(x, l, op) : op_bwd_c<T, false>(x, l, op);
+  return op.cmask ? op_bwd_c<RB, T, true>(x, l, op) : op_bwd_c<RB, T, false>(x, l, op);
 }
 
-__device__ __forceinline__ float apply_bwd(float2 (&x)[16], float2 (&l)[16], const TOp& op) {
+template <int RB>
+__device__ __forceinline__ float apply_bwd(float2 (&x)[1 << RB], float2 (&l)[1 << RB], const TOp& op) {
   switch (op.t) {
-    case 0: return op_bwd_t<0>(x, l, op);
-    case 1: return op_bwd_t<1>(x, l, op);
-    case 2: return op_bwd_t<2>(x, l, op);
-    default: return op_bwd_t<3>(x, l, op);
+    case 0: return op_bwd_t<RB, 0>(x, l, op);
+    case 1: return op_bwd_t<RB, 1>(x, l, op);
+    case 2: if constexpr (RB > 2) return op_bwd_t<RB, 2>(x, l, op); return 0.f;
+    default: if constexpr (RB > 3) return op_bwd_t<RB, 3>(x, l, op); return 0.f;
+  }
+}
+
+// ------------------------------------------------------------------ device: double-float arithmetic
+//
+// A double-float value is an unevaluated sum hi + lo of two FP32 numbers with
+// |lo| <= ulp(hi) / 2 (Dekker 1971).  The building blocks are Knuth's
+// error-free TwoSum and the FMA form of TwoProduct (the rounding error of
+// a * b is fma(a, b, -a * b) exactly); a sum of products accumulates the large
+// parts with TwoSum and every small part in a running FP32 correction, and is
+// renormalised once at the end (Joldes, Muller and Popescu, ACM TOMS 2017,
+// give the error bounds of these double-word operations).  The _rn
+// intrinsics keep the compiler from fusing the exact-error steps.
+
+struct ffc {         // complex double-float: (h.x + l.x) + i (h.y + l.y)
+  float2 h, l;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+struct DWAcc {       // running sum s + e of double-float products
+  float s, e;
+};
+
+// (xh + xl) * (yh + yl) without the xl * yl term (below 2^-48 relative)
+__device__ __forceinline__ void dw_first(DWAcc& A, float xh, float xl, float yh, float yl) {
+  A.s = __fmul_rn(xh, yh);
+  A.e = fmaf(xh, yl, fmaf(xl, yh, fmaf(xh, yh, -A.s)));
+}
+__device__ __forceinline__ void dw_add(DWAcc& A, float xh, float xl, float yh, float yl) {
+  const float p = __fmul_rn(xh, yh);
+  const float pe = fmaf(xh, yl, fmaf(xl, yh, fmaf(xh, yh, -p)));
+  float s, t;
+  two_sum(A.s, p, s, t);
+  A.s = s;
+  A.e = __fadd_rn(A.e, __fadd_rn(t, pe));
+}
+__device__ __forceinline__ void dw_out(const DWAcc& A, float& h, float& l) { two_sum(A.s, A.e, h, l); }
+
+// a * u for complex double-floats (u = uh + ul)
+__device__ __forceinline__ ffc ff_cmul(const ffc& a, float2 uh, float2 ul) {
+  DWAcc re, im;
+  dw_first(re, a.h.x, a.l.x, uh.x, ul.x);
+  dw_add(re, -a.h.y, -a.l.y, uh.y, ul.y);
+  dw_first(im, a.h.x, a.l.x, uh.y, ul.y);
+  dw_add(im, a.h.y, a.l.y, uh.x, ul.x);
+  ffc r;
+  dw_out(re, r.h.x, r.l.x);
+  dw_out(im, r.h.y, r.l.y);
+  return r;
+}
+
+// u0 * a + u1 * b for complex double-floats
+__device__ __forceinline__ ffc ff_cdot2(const ffc& a, float2 u0h, float2 u0l, const ffc& b, float2 u1h, float2 u1l) {
+  DWAcc re, im;
+  dw_first(re, a.h.x, a.l.x, u0h.x, u0l.x);
+  dw_add(re, -a.h.y, -a.l.y, u0h.y, u0l.y);
+  dw_add(re, b.h.x, b.l.x, u1h.x, u1l.x);
+  dw_add(re, -b.h.y, -b.l.y, u1h.y, u1l.y);
+  dw_first(im, a.h.x, a.l.x, u0h.y, u0l.y);
+  dw_add(im, a.h.y, a.l.y, u0h.x, u0l.x);
+  dw_add(im, b.h.x, b.l.x, u1h.y, u1l.y);
+  dw_add(im, b.h.y, b.l.y, u1h.x, u1l.x);
+  ffc r;
+  dw_out(re, r.h.x, r.l.x);
+  dw_out(im, r.h.y, r.l.y);
+  return r;
+}
+
+// (a, b) <- U (a, b) in double-float; U = u + w (hi + lo), row-major
+template <int KIND>
+__device__ __forceinline__ void pair_apply_ff(ffc& a, ffc& b, const float2 (&u)[4], const float2 (&w)[4]) {
+  if (KIND == TK_SWAP) {
+    const ffc t = a; a = b; b = t;
+  } else if (KIND == TK_DIAG) {
+    a = ff_cmul(a, u[0], w[0]);
+    b = ff_cmul(b, u[3], w[3]);
+  } else if (KIND == TK_RX) {  // [[c, i s], [i s, c]]: a' = c a + i s b
+    const float ch = u[0].x, cl = w[0].x, sh = u[1].y, sl = w[1].y;
+    DWAcc r0, i0, r1, i1;
+    dw_first(r0, a.h.x, a.l.x, ch, cl); dw_add(r0, -b.h.y, -b.l.y, sh, sl);
+    dw_first(i0, a.h.y, a.l.y, ch, cl); dw_add(i0, b.h.x, b.l.x, sh, sl);
+    dw_first(r1, b.h.x, b.l.x, ch, cl); dw_add(r1, -a.h.y, -a.l.y, sh, sl);
+    dw_first(i1, b.h.y, b.l.y, ch, cl); dw_add(i1, a.h.x, a.l.x, sh, sl);
+    dw_out(r0, a.h.x, a.l.x); dw_out(i0, a.h.y, a.l.y);
+    dw_out(r1, b.h.x, b.l.x); dw_out(i1, b.h.y, b.l.y);
+  } else if (KIND == TK_RY) {  // real [[c, p], [q, c]]
+    const float ch = u[0].x, cl = w[0].x, ph = u[1].x, pl = w[1].x, qh = u[2].x, ql = w[2].x;
+    DWAcc r0, i0, r1, i1;
+    dw_first(r0, a.h.x, a.l.x, ch, cl); dw_add(r0, b.h.x, b.l.x, ph, pl);
+    dw_first(i0, a.h.y, a.l.y, ch, cl); dw_add(i0, b.h.y, b.l.y, ph, pl);
+    dw_first(r1, a.h.x, a.l.x, qh, ql); dw_add(r1, b.h.x, b.l.x, ch, cl);
+    dw_first(i1, a.h.y, a.l.y, qh, ql); dw_add(i1, b.h.y, b.l.y, ch, cl);
+    dw_out(r0, a.h.x, a.l.x); dw_out(i0, a.h.y, a.l.y);
+    dw_out(r1, b.h.x, b.l.x); dw_out(i1, b.h.y, b.l.y);
+  } else {
+    const ffc na = ff_cdot2(a, u[0], w[0], b, u[1], w[1]);
+    const ffc nb = ff_cdot2(a, u[2], w[2], b, u[3], w[3]);
+    a = na; b = nb;
+  }
+}
+
+// the backward op of the precise path: gradient share from the hi parts
+// (FP32 products, FP64 above the warp), then the double-float uncompute
+template <int RB, int T, int KIND, int GK, bool CTRL>
+__device__ __forceinline__ float op_bwd_ff(ffc (&x)[1 << RB], ffc (&l)[1 << RB], const TOp& op, const float2* lo,
+                                           float g0, float g3) {
+  const int cm = op.cmask, cv = op.cval;
+  const float2 u[4] = {op.u[0], op.u[1], op.u[2], op.u[3]};
+  const float2 w[4] = {lo[0], lo[1], lo[2], lo[3]};
+  float acc = 0.f;
+#pragma unroll
+  for (int j = 0; j < (1 << RB); ++j) {
+    if (j & (1 << T)) continue;
+    if (CTRL && (j & cm) != cv) continue;
+    const int k = j | (1 << T);
+    if (GK == 1) acc += fmaf(g0, imcj(l[j].h, x[j].h), g3 * imcj(l[k].h, x[k].h));
+    if (GK == 2) acc += imcj(l[j].h, x[k].h) + imcj(l[k].h, x[j].h);
+    if (GK == 3) acc += recj(l[k].h, x[j].h) - recj(l[j].h, x[k].h);
+    pair_apply_ff<KIND>(x[j], x[k], u, w);
+    pair_apply_ff<KIND>(l[j], l[k], u, w);
+  }
+  return acc;
+}
+
+template <int RB, int T, bool CTRL>
+__device__ __forceinline__ float op_bwd_ff_c(ffc (&x)[1 << RB], ffc (&l)[1 << RB], const TOp& op, const float2* lo) {
+  switch (op.gen) {
+    case GEN_X: return op_bwd_ff<RB, T, TK_RX, 2, CTRL>(x, l, op, lo, 0.f, 0.f);
+    case GEN_Y: return op_bwd_ff<RB, T, TK_RY, 3, CTRL>(x, l, op, lo, 0.f, 0.f);
+    case GEN_Z: return op_bwd_ff<RB, T, TK_DIAG, 1, CTRL>(x, l, op, lo, 1.f, -1.f);
+    case GEN_P1: return op_bwd_ff<RB, T, TK_DIAG, 1, CTRL>(x, l, op, lo, 0.f, 1.f);
+    default: return op_bwd_ff<RB, T, TK_DIAG, 1, CTRL>(x, l, op, lo, 1.f, 1.f);  // GEN_I
+  }
+}
+
+template <int RB, int T>
+__device__ __forceinline__ float op_bwd_ff_t(ffc (&x)[1 << RB], ffc (&l)[1 << RB], const TOp& op, const float2* lo) {
+  if (op.gen == GEN_NONE) {
+    if (op.kind == TK_SWAP) return op_bwd_ff<RB, T, TK_SWAP, 0, true>(x, l, op, lo, 0.f, 0.f);
+    if (op.kind == TK_DIAG) return op_bwd_ff<RB, T, TK_DIAG, 0, true>(x, l, op, lo, 0.f, 0.f);
+    return op_bwd_ff<RB, T, TK_DENSE, 0, true>(x, l, op, lo, 0.f, 0.f);
+  }
+  return op.cmask ? op_bwd_ff_c<RB, T, true>(x, l, op, lo) : op_bwd_ff_c<RB, T, false>(x, l, op, lo);
+}
+
+template <int RB>
+__device__ __forceinline__ float apply_bwd_ff(ffc (&x)[1 << RB], ffc (&l)[1 << RB], const TOp& op, const float2* lo) {
+  switch (op.t) {
+    case 0: return op_bwd_ff_t<RB, 0>(x, l, op, lo);
+    case 1: return op_bwd_ff_t<RB, 1>(x, l, op, lo);
+    case 2: if constexpr (RB > 2) return op_bwd_ff_t<RB, 2>(x, l, op, lo); return 0.f;
+    default: if constexpr (RB > 3) return op_bwd_ff_t<RB, 3>(x, l, op, lo); return 0.f;
   }
 }
 
@@ -291,6 +505,44 @@ __device__ __forceinline__ void store_tile(const float2* sm, float2* dst, const 
   store_tiles<false>(sm, dst, nullptr, nullptr, rowoff, m);
 }
 
+// double-float tiles of psi and lambda (one float4 = hi.re, hi.im, lo.re, lo.im
+// per amplitude, in global and shared memory)
+__device__ __noinline__ void load_tiles_ff(float4* sm0, const float4* src0, float4* sm1, const float4* src1,
+                                           const uint32_t* rowoff, int m) {
+  const uint32_t cnt = 1u << m;
+  constexpr int C = kLdChunk / 2;
+  for (uint32_t q0 = 0; q0 < cnt; q0 += C * kTileThreads) {
+    float4 v0[C], v1[C];
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      const uint32_t q = q0 + threadIdx.x + k * kTileThreads;
+      if (q < cnt) {
+        const uint32_t off = rowoff[q >> kRowBits] + (q & 31u);
+        v0[k] = src0[off];
+        v1[k] = src1[off];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      const uint32_t q = q0 + threadIdx.x + k * kTileThreads;
+      if (q < cnt) {
+        sm0[swz(q)] = v0[k];
+        sm1[swz(q)] = v1[k];
+      }
+    }
+  }
+}
+
+__device__ __noinline__ void store_tiles_ff(const float4* sm0, float4* dst0, const float4* sm1, float4* dst1,
+                                            const uint32_t* rowoff, int m) {
+  const uint32_t cnt = 1u << m;
+  for (uint32_t q = threadIdx.x; q < cnt; q += kTileThreads) {
+    const uint32_t off = rowoff[q >> kRowBits] + (q & 31u);
+    dst0[off] = sm0[swz(q)];
+    dst1[off] = sm1[swz(q)];
+  }
+}
+
 __device__ __forceinline__ uint32_t phase_base(uint32_t tid, const TPhase& ph, int nthreadbits) {
   uint32_t b = 0;
   for (int k = 0; k < nthreadbits; ++k) b |= ((tid >> k) & 1u) << ph.tpos[k];
@@ -306,7 +558,7 @@ __device__ __forceinline__ uint32_t thread_global(uint32_t tid, const TPhase& ph
 
 // shared-memory slot of amplitude j of a phase: swz is linear over XOR, so
 // slot(j) = swz(base) ^ (XOR of swz(offset of bit b) over the set bits b of j);
-// the four per-bit values stay in registers instead of reloading sroff[j]
+// the per-bit values stay in registers instead of reloading sroff[j]
 struct PhaseSlots {
   uint32_t b, s0, s1, s2, s3;
 };
@@ -323,121 +575,123 @@ __device__ __forceinline__ uint32_t slot(const PhaseSlots& p, int j) {
 }
 
 // out-of-phase diagonal gate with phase-local controls: x_j *= f where (j & cm) == cv
-__device__ __forceinline__ void diag_masked(float2 (&x)[16], float2 f, int cm, int cv) {
+template <int RB>
+__device__ __forceinline__ void diag_masked(float2 (&x)[1 << RB], float2 f, int cm, int cv) {
 #pragma unroll
-  for (int j = 0; j < 16; ++j)
+  for (int j = 0; j < (1 << RB); ++j)
     if ((j & cm) == cv) x[j] = cmulf(x[j], f);
 }
 
-__device__ __noinline__ void run_phase_fwd(float2* sm, const TPhase* php, const TOp* fops, const float2* dtab, int m,
-                                           uint32_t tbase) {
+// COMP: compensated matrices (flo: 4 corrections per forward op, dtlo: 16 per
+// diagonal table); out-of-phase diagonal factors are then applied one by one
+template <int RB, bool COMP>
+__device__ __noinline__ void run_phase_fwd(float2* sm, const TPhase* php, const TOp* fops, const float2* dtab,
+                                           const float2* flo, const float2* dtlo, int m, uint32_t tbase) {
+  constexpr int A = 1 << RB;
   const TPhase& ph = *php;
-  const int ntb = m - kRB;
+  const int ntb = m - RB;
   if (threadIdx.x < (1u << ntb)) {
     const PhaseSlots ps = phase_slots(swz(phase_base(threadIdx.x, ph, ntb)), ph);
     const uint32_t gb = thread_global(threadIdx.x, ph, ntb, tbase);
-    float2 x[16];
+    float2 x[A];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) x[j] = sm[slot(ps, j)];
+    for (int j = 0; j < A; ++j) x[j] = sm[slot(ps, j)];
     // factors of out-of-phase diagonal gates without phase-local controls are
     // scalars for this thread: they commute with the phase and are applied once
     float2 pend = make_float2(1.f, 0.f);
     bool has_pend = false;
     for (int o = 0; o < ph.nfop; ++o) {
-      const TOp& cur = fops[ph.fop0 + o];
+      const int oi = ph.fop0 + o;
+      const TOp& cur = fops[oi];
       if ((gb & cur.tmask) != cur.tval) continue;
       if (cur.kind == TK_DIAGOUT) {
-        const float2 f = ((gb >> cur.t) & 1u) ? cur.u[3] : cur.u[0];
-        if (cur.cmask == 0) {
+        const bool b1 = (gb >> cur.t) & 1u;
+        const float2 f = b1 ? cur.u[3] : cur.u[0];
+        if (COMP) {
+          const float2 fl = flo[4 * oi + (b1 ? 3 : 0)];
+#pragma unroll
+          for (int j = 0; j < A; ++j)
+            if ((j & cur.cmask) == cur.cval) x[j] = cmaf(f, x[j], cmulf(fl, x[j]));
+        } else if (cur.cmask == 0) {
           pend = cmulf(pend, f);
           has_pend = true;
         } else {
-          diag_masked(x, f, cur.cmask, cur.cval);
+          diag_masked<RB>(x, f, cur.cmask, cur.cval);
         }
       } else if (cur.kind == TK_DIAG16) {
         const float2* t = dtab + 16 * cur.param;
+        if (COMP) {
+          const float2* tl = dtlo + 16 * cur.param;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) x[j] = cmulf(x[j], t[j]);
+          for (int j = 0; j < A; ++j) x[j] = cmaf(t[j], x[j], cmulf(tl[j], x[j]));
+        } else {
+#pragma unroll
+          for (int j = 0; j < A; ++j) x[j] = cmulf(x[j], t[j]);
+        }
       } else {
-        apply_fwd(x, cur);
+        apply_fwd<RB, COMP>(x, cur, COMP ? flo + 4 * oi : nullptr);
       }
     }
-    if (has_pend) {
+    if (!COMP && has_pend) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) x[j] = cmulf(x[j], pend);
+      for (int j = 0; j < A; ++j) x[j] = cmulf(x[j], pend);
     }
 #pragma unroll
-    for (int j = 0; j < 16; ++j) sm[slot(ps, j)] = x[j];
+    for (int j = 0; j < A; ++j) sm[slot(ps, j)] = x[j];
   }
   __syncthreads();
 }
 
 // backward of an out-of-phase diagonal gate: the generator is diagonal on the
 // target (Z, P1 or 1), whose value is fixed for this thread
-__device__ __forceinline__ float diagout_bwd(float2 (&x)[16], float2 (&l)[16], const TOp& op, uint32_t gb) {
+__device__ __forceinline__ float diagout_sign(const TOp& op, bool b) {
+  switch (op.gen) {
+    case GEN_Z: return b ? -1.f : 1.f;
+    case GEN_P1: return b ? 1.f : 0.f;
+    case GEN_I: return 1.f;
+    default: return 0.f;
+  }
+}
+
+template <int RB>
+__device__ __forceinline__ float diagout_bwd(float2 (&x)[1 << RB], float2 (&l)[1 << RB], const TOp& op, uint32_t gb) {
   const bool b = (gb >> op.t) & 1u;
   const float2 d = b ? op.u[3] : op.u[0];
-  float gsign = 0.f;
-  switch (op.gen) {
-    case GEN_Z: gsign = b ? -1.f : 1.f; break;
-    case GEN_P1: gsign = b ? 1.f : 0.f; break;
-    case GEN_I: gsign = 1.f; break;
-    default: break;
-  }
   const int cm = op.cmask, cv = op.cval;
   float acc = 0.f;
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
+  for (int j = 0; j < (1 << RB); ++j) {
     if ((j & cm) != cv) continue;
     acc += imcj(l[j], x[j]);
     x[j] = cmulf(x[j], d);
     l[j] = cmulf(l[j], d);
   }
-  return gsign * acc;
+  return diagout_sign(op, b) * acc;
 }
 
-__device__ __noinline__ void run_phase_bwd(float2* sx, float2* sl, const TPhase* php, const TOp* bops, int m,
-                                           float* red, double* gacc, uint32_t tbase) {
-  // the phase record stays in memory (L1): with 32 live amplitudes per thread
-  // there are no registers to spare for a copy of it or for 16 slot offsets
-  const TPhase& ph = *php;
-  const int ntb = m - kRB;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool active = threadIdx.x < (1u << ntb);
-  const int nbop = ph.nbop, bop0 = ph.bop0;
-  float2 x[16], l[16];
-  const uint32_t gb = active ? thread_global(threadIdx.x, ph, ntb, tbase) : 0u;
-  const PhaseSlots ps = phase_slots(active ? swz(phase_base(threadIdx.x, ph, ntb)) : 0u, ph);
-  if (active) {
+template <int RB>
+__device__ __forceinline__ float diagout_bwd_ff(ffc (&x)[1 << RB], ffc (&l)[1 << RB], const TOp& op, const float2* lo,
+                                                uint32_t gb) {
+  const bool b = (gb >> op.t) & 1u;
+  const float2 d = b ? op.u[3] : op.u[0];
+  const float2 dl = b ? lo[3] : lo[0];
+  const int cm = op.cmask, cv = op.cval;
+  float acc = 0.f;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const uint32_t o = slot(ps, j);
-      x[j] = sx[o];
-      l[j] = sl[o];
-    }
+  for (int j = 0; j < (1 << RB); ++j) {
+    if ((j & cm) != cv) continue;
+    acc += imcj(l[j].h, x[j].h);
+    x[j] = ff_cmul(x[j], d, dl);
+    l[j] = ff_cmul(l[j], d, dl);
   }
-  for (int o = nbop - 1; o >= 0; --o) {
-    const TOp& op = bops[bop0 + o];
-    float part = 0.f;
-    if (active && (gb & op.tmask) == op.tval)
-      part = op.kind == TK_DIAGOUT ? diagout_bwd(x, l, op, gb) : apply_bwd(x, l, op);
-    if (op.gen != GEN_NONE) {
-      for (int s = 16; s > 0; s >>= 1) part += __shfl_xor_sync(0xffffffffu, part, s);
-      if (lane == 0) red[o * kWarps + warp] = part;
-    }
-  }
-  if (active) {
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const uint32_t o = slot(ps, j);
-      sx[o] = x[j];
-      sl[o] = l[j];
-    }
-  }
-  __syncthreads();
-  // fold the warp partials of every parameterised op in FP64; ops whose
-  // parameter is unique in the phase in parallel, the others by one thread
+  return diagout_sign(op, b) * acc;
+}
+
+// fold the warp partials of every parameterised op of a phase in FP64; ops
+// whose parameter is unique in the phase in parallel, the others by one thread
+__device__ __forceinline__ void fold_phase_grad(const TPhase& ph, const TOp* bops, const float* red, double* gacc) {
   const int nw = (int)(blockDim.x / 32);
+  const int nbop = ph.nbop, bop0 = ph.bop0;
   const int o = threadIdx.x;
   if (o < nbop) {
     const TOp& op = bops[bop0 + o];
@@ -460,6 +714,104 @@ __device__ __noinline__ void run_phase_bwd(float2* sx, float2* sl, const TPhase*
   __syncthreads();
 }
 
+template <int RB>
+__device__ __noinline__ void run_phase_bwd(float2* sx, float2* sl, const TPhase* php, const TOp* bops, int m,
+                                           float* red, double* gacc, uint32_t tbase) {
+  // the phase record stays in memory (L1): with 2 x 2^RB live amplitudes per
+  // thread there are no registers to spare for a copy of it
+  constexpr int A = 1 << RB;
+  const TPhase& ph = *php;
+  const int ntb = m - RB;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool active = threadIdx.x < (1u << ntb);
+  const int nbop = ph.nbop, bop0 = ph.bop0;
+  float2 x[A], l[A];
+  const uint32_t gb = active ? thread_global(threadIdx.x, ph, ntb, tbase) : 0u;
+  const PhaseSlots ps = phase_slots(active ? swz(phase_base(threadIdx.x, ph, ntb)) : 0u, ph);
+  if (active) {
+#pragma unroll
+    for (int j = 0; j < A; ++j) {
+      const uint32_t o = slot(ps, j);
+      x[j] = sx[o];
+      l[j] = sl[o];
+    }
+  }
+  for (int o = nbop - 1; o >= 0; --o) {
+    const TOp& op = bops[bop0 + o];
+    float part = 0.f;
+    if (active && (gb & op.tmask) == op.tval)
+      part = op.kind == TK_DIAGOUT ? diagout_bwd<RB>(x, l, op, gb) : apply_bwd<RB>(x, l, op);
+    if (op.gen != GEN_NONE) {
+      for (int s = 16; s > 0; s >>= 1) part += __shfl_xor_sync(0xffffffffu, part, s);
+      if (lane == 0) red[o * kWarps + warp] = part;
+    }
+  }
+  if (active) {
+#pragma unroll
+    for (int j = 0; j < A; ++j) {
+      const uint32_t o = slot(ps, j);
+      sx[o] = x[j];
+      sl[o] = l[j];
+    }
+  }
+  __syncthreads();
+  fold_phase_grad(ph, bops, red, gacc);
+}
+
+template <int RB>
+__device__ __noinline__ void run_phase_bwd_ff(float4* sx, float4* sl, const TPhase* php, const TOp* bops,
+                                              const float2* blo, int m, float* red, double* gacc, uint32_t tbase) {
+  constexpr int A = 1 << RB;
+  const TPhase& ph = *php;
+  const int ntb = m - RB;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool active = threadIdx.x < (1u << ntb);
+  const int nbop = ph.nbop, bop0 = ph.bop0;
+  ffc x[A], l[A];
+  const uint32_t gb = active ? thread_global(threadIdx.x, ph, ntb, tbase) : 0u;
+  const PhaseSlots ps = phase_slots(active ? swz(phase_base(threadIdx.x, ph, ntb)) : 0u, ph);
+  if (active) {
+#pragma unroll
+    for (int j = 0; j < A; ++j) {
+      const uint32_t o = slot(ps, j);
+      const float4 a = sx[o], b = sl[o];
+      x[j].h = make_float2(a.x, a.y);
+      x[j].l = make_float2(a.z, a.w);
+      l[j].h = make_float2(b.x, b.y);
+      l[j].l = make_float2(b.z, b.w);
+    }
+  }
+  for (int o = nbop - 1; o >= 0; --o) {
+    const int oi = bop0 + o;
+    const TOp& op = bops[oi];
+    float part = 0.f;
+    if (active && (gb & op.tmask) == op.tval)
+      part = op.kind == TK_DIAGOUT ? diagout_bwd_ff<RB>(x, l, op, blo + 4 * oi, gb)
+                                   : apply_bwd_ff<RB>(x, l, op, blo + 4 * oi);
+    if (op.gen != GEN_NONE) {
+      for (int s = 16; s > 0; s >>= 1) part += __shfl_xor_sync(0xffffffffu, part, s);
+      if (lane == 0) red[o * kWarps + warp] = part;
+    }
+  }
+  if (active) {
+#pragma unroll
+    for (int j = 0; j < A; ++j) {
+      const uint32_t o = slot(ps, j);
+      sx[o] = make_float4(x[j].h.x, x[j].h.y, x[j].l.x, x[j].l.y);
+      sl[o] = make_float4(l[j].h.x, l[j].h.y, l[j].l.x, l[j].l.y);
+    }
+  }
+  __syncthreads();
+  fold_phase_grad(ph, bops, red, gacc);
+}
+
+// the diagonal observable's weight w(i) = sum_t c_t (-1)^popcount(i & z_t)
+__device__ __forceinline__ double obs_weight(uint64_t gi, const BTerm* terms, int nterm) {
+  double w = 0.0;
+  for (int t = 0; t < nterm; ++t) w += (__popcll(gi & terms[t].z) & 1) ? -terms[t].coeff : terms[t].coeff;
+  return w;
+}
+
 // loss partial and lambda = w psi for the diagonal observable, over a tile in smem
 __device__ double expect_tile(float2* sx, float2* sl, uint64_t tbase, const uint32_t* rowoff, int m,
                               const BTerm* terms, int nterm) {
@@ -467,12 +819,30 @@ __device__ double expect_tile(float2* sx, float2* sl, uint64_t tbase, const uint
   double acc = 0.0;
   for (uint32_t l = threadIdx.x; l < cnt; l += blockDim.x) {
     const uint64_t gi = tbase + rowoff[l >> kRowBits] + (l & 31u);
-    double w = 0.0;
-    for (int t = 0; t < nterm; ++t) w += (__popcll(gi & terms[t].z) & 1) ? -terms[t].coeff : terms[t].coeff;
+    const double w = obs_weight(gi, terms, nterm);
     const float2 a = sx[swz(l)];
     acc += w * ((double)a.x * a.x + (double)a.y * a.y);
     const float wf = (float)w;
     sl[swz(l)] = make_float2(wf * a.x, wf * a.y);
+  }
+  return acc;
+}
+
+// the same from a complex64 tile into double-float psi and lambda tiles
+// (w psi formed in FP64 and split into hi + lo)
+__device__ double expect_tile_ff(const float2* s2, float4* sxf, float4* slf, uint64_t tbase, const uint32_t* rowoff,
+                                 int m, const BTerm* terms, int nterm) {
+  const uint32_t cnt = 1u << m;
+  double acc = 0.0;
+  for (uint32_t l = threadIdx.x; l < cnt; l += blockDim.x) {
+    const uint64_t gi = tbase + rowoff[l >> kRowBits] + (l & 31u);
+    const double w = obs_weight(gi, terms, nterm);
+    const float2 a = s2[swz(l)];
+    acc += w * ((double)a.x * a.x + (double)a.y * a.y);
+    const double lr = w * (double)a.x, li = w * (double)a.y;
+    const float hr = (float)lr, hi = (float)li;
+    sxf[swz(l)] = make_float4(a.x, a.y, 0.f, 0.f);
+    slf[swz(l)] = make_float4(hr, hi, (float)(lr - (double)hr), (float)(li - (double)hi));
   }
   return acc;
 }
@@ -482,23 +852,37 @@ __device__ void block_loss(double e, BShared& S, double* out) {
   if ((threadIdx.x & 31) == 0) S.lred[threadIdx.x >> 5] = e;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double v = 0.0;
-    for (int w = 0; w < (int)(blockDim.x / 32); ++w) v += S.lred[w];
-    *out = v;
+    static_assert(kWarps == 16, "loss tree below is written for 16 warps");
+    const double* v = S.lred;
+    *out = (((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]))) +
+           (((v[8] + v[9]) + (v[10] + v[11])) + ((v[12] + v[13]) + (v[14] + v[15])));
   }
 }
 
 // The per-register phase loops of k_batch live in their own (not inlined)
 // functions: a phase call then sees only the loop's few live values, and the
-// phase functions keep their 32 amplitudes per thread in registers.
+// phase functions keep their amplitudes in registers.
+template <int RB>
 __device__ __noinline__ void batch_bwd_resident(float2* sx, float2* sl, const TPass* P, int npass, int m,
                                                 const TPhase* phases, const TOp* bops, float* red, double* gacc) {
   for (int pi = npass - 1; pi >= 0; --pi) {
     const int ph0 = P[pi].phase0;
-    for (int f = P[pi].nphase - 1; f >= 0; --f) run_phase_bwd(sx, sl, phases + ph0 + f, bops, m, red, gacc, 0u);
+    for (int f = P[pi].nphase - 1; f >= 0; --f) run_phase_bwd<RB>(sx, sl, phases + ph0 + f, bops, m, red, gacc, 0u);
   }
 }
 
+template <int RB>
+__device__ __noinline__ void batch_bwd_resident_ff(float4* sx, float4* sl, const TPass* P, int npass, int m,
+                                                   const TPhase* phases, const TOp* bops, const float2* blo,
+                                                   float* red, double* gacc) {
+  for (int pi = npass - 1; pi >= 0; --pi) {
+    const int ph0 = P[pi].phase0;
+    for (int f = P[pi].nphase - 1; f >= 0; --f)
+      run_phase_bwd_ff<RB>(sx, sl, phases + ph0 + f, bops, blo, m, red, gacc, 0u);
+  }
+}
+
+template <int RB>
 __device__ __noinline__ void batch_bwd_streamed(float2* sx, float2* sl, const TPass* P, int npass, int m, int g,
                                                 float2* wp, float2* wl, const TPhase* phases, const TOp* bops,
                                                 uint32_t* rowoff, float* red, double* gacc) {
@@ -511,16 +895,39 @@ __device__ __noinline__ void batch_bwd_streamed(float2* sx, float2* sl, const TP
       load_tiles<true>(sx, wp + tb, sl, wl + tb, rowoff, m);
       __syncthreads();
       const int ph0 = p.phase0;
-      for (int f = p.nphase - 1; f >= 0; --f) run_phase_bwd(sx, sl, phases + ph0 + f, bops, m, red, gacc, (uint32_t)tb);
+      for (int f = p.nphase - 1; f >= 0; --f)
+        run_phase_bwd<RB>(sx, sl, phases + ph0 + f, bops, m, red, gacc, (uint32_t)tb);
       store_tiles<true>(sx, wp + tb, sl, wl + tb, rowoff, m);
       __syncthreads();
     }
   }
 }
 
+template <int RB>
+__device__ __noinline__ void batch_bwd_streamed_ff(float4* sx, float4* sl, const TPass* P, int npass, int m, int g,
+                                                   float4* wp, float4* wl, const TPhase* phases, const TOp* bops,
+                                                   const float2* blo, uint32_t* rowoff, float* red, double* gacc) {
+  const uint64_t ntile = 1ull << g;
+  for (int pi = npass - 1; pi >= 0; --pi) {
+    const TPass& p = P[pi];
+    set_rows(rowoff, p, m);
+    for (uint64_t t = 0; t < ntile; ++t) {
+      const uint64_t tb = tile_base(t, p, g);
+      load_tiles_ff(sx, wp + tb, sl, wl + tb, rowoff, m);
+      __syncthreads();
+      const int ph0 = p.phase0;
+      for (int f = p.nphase - 1; f >= 0; --f)
+        run_phase_bwd_ff<RB>(sx, sl, phases + ph0 + f, bops, blo, m, red, gacc, (uint32_t)tb);
+      store_tiles_ff(sx, wp + tb, sl, wl + tb, rowoff, m);
+      __syncthreads();
+    }
+  }
+}
+
+template <int RB, bool COMP>
 __device__ __noinline__ void batch_fwd_streamed(float2* sx, float2* st, const TPass* P, int npass, int m, int g,
                                                 const TPhase* phases, const TOp* fops, const float2* dtab,
-                                                uint32_t* rowoff) {
+                                                const float2* flo, const float2* dtlo, uint32_t* rowoff) {
   const uint64_t ntile = 1ull << g;
   for (int pi = 0; pi < npass; ++pi) {
     const TPass& p = P[pi];
@@ -530,18 +937,28 @@ __device__ __noinline__ void batch_fwd_streamed(float2* sx, float2* st, const TP
       load_tile(sx, st + tb, rowoff, m);
       __syncthreads();
       const int ph0 = p.phase0;
-      for (int f = 0; f < p.nphase; ++f) run_phase_fwd(sx, phases + ph0 + f, fops, dtab, m, (uint32_t)tb);
+      for (int f = 0; f < p.nphase; ++f)
+        run_phase_fwd<RB, COMP>(sx, phases + ph0 + f, fops, dtab, flo, dtlo, m, (uint32_t)tb);
       store_tile(sx, st + tb, rowoff, m);
       __syncthreads();
     }
   }
 }
 
+// Shared memory of k_batch after the BShared header: the complex64 path holds
+// psi and lambda tiles (2 x 2^13 x 8 bytes); the precise path holds double-float
+// psi and lambda tiles (2 x 2^m x 16 bytes) and a complex64 forward tile.
+template <int RB, bool PREC>
 __global__ void __launch_bounds__(kTileThreads, 1) k_batch(BArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   BShared& S = *reinterpret_cast<BShared*>(smraw);
-  float2* sx = reinterpret_cast<float2*>(smraw + ((sizeof(BShared) + 255) & ~size_t(255)));
-  float2* sl = sx + (1 << kMaxTileBits);
+  constexpr int MT = kTileThreads == 512 ? 9 + RB : 0;  // largest tile: 512 threads x 2^RB amplitudes
+  static_assert(MT >= kRowBits + RB && MT <= kMaxTileBits, "tile size");
+  unsigned char* body = smraw + ((sizeof(BShared) + 255) & ~size_t(255));
+  float2* sx = reinterpret_cast<float2*>(body);                   // complex64 psi tile (forward, and FP32 backward)
+  float2* sl = sx + (1 << MT);                                    // complex64 lambda tile (FP32 backward)
+  float4* sxf = reinterpret_cast<float4*>(body + (size_t)8 * (1 << MT));   // double-float psi (precise)
+  float4* slf = sxf + (1 << MT);                                           // double-float lambda (precise)
   const int tid = threadIdx.x;
   for (;;) {
     if (tid == 0) S.reg = atomicAdd(a.counter, 1);
@@ -567,41 +984,75 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_batch(BArgs a) {
       }
       __syncthreads();
       for (int pi = 0; pi < R.npass; ++pi)
-        for (int f = 0; f < P[pi].nphase; ++f) run_phase_fwd(sx, a.phases + P[pi].phase0 + f, a.fops, a.dtab, m, 0u);
+        for (int f = 0; f < P[pi].nphase; ++f)
+          run_phase_fwd<RB, PREC>(sx, a.phases + P[pi].phase0 + f, a.fops, a.dtab, a.flo, a.dtlo, m, 0u);
       store_tile(sx, st, S.rowoff, m);  // psi_N
-      block_loss(expect_tile(sx, sl, 0, S.rowoff, m, a.terms + R.term0, R.nterm), S, a.loss + reg);
-      __syncthreads();
-      if (grad) batch_bwd_resident(sx, sl, P, R.npass, m, a.phases, a.bops, S.red, S.grad);
+      if (PREC) {
+        block_loss(expect_tile_ff(sx, sxf, slf, 0, S.rowoff, m, a.terms + R.term0, R.nterm), S, a.loss + reg);
+        __syncthreads();
+        if (grad) batch_bwd_resident_ff<RB>(sxf, slf, P, R.npass, m, a.phases, a.bops, a.blo, S.red, S.grad);
+      } else {
+        block_loss(expect_tile(sx, sl, 0, S.rowoff, m, a.terms + R.term0, R.nterm), S, a.loss + reg);
+        __syncthreads();
+        if (grad) batch_bwd_resident<RB>(sx, sl, P, R.npass, m, a.phases, a.bops, S.red, S.grad);
+      }
     } else {
       // ---- tiles streamed through global memory
       if (a.flags & BF_RESET) {
         for (uint64_t i = tid; i < (1ull << n); i += blockDim.x) st[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
         __syncthreads();
       }
-      batch_fwd_streamed(sx, st, P, R.npass, m, g, a.phases, a.fops, a.dtab, S.rowoff);
+      batch_fwd_streamed<RB, PREC>(sx, st, P, R.npass, m, g, a.phases, a.fops, a.dtab, a.flo, a.dtlo, S.rowoff);
       // expectation, lambda = O psi, and the work copy of psi for the uncompute
       double e = 0.0;
-      float2* wp = a.wpsi + R.work_off;
-      float2* wl = a.wlam + R.work_off;
       const TPass& p0 = P[0];
       set_rows(S.rowoff, p0, m);
       for (uint64_t t = 0; t < ntile; ++t) {
         const uint64_t tb = tile_base(t, p0, g);
         load_tile(sx, st + tb, S.rowoff, m);
         __syncthreads();
-        e += expect_tile(sx, sl, tb, S.rowoff, m, a.terms + R.term0, R.nterm);
-        __syncthreads();
-        if (grad) store_tiles<true>(sx, wp + tb, sl, wl + tb, S.rowoff, m);
+        if (PREC) {
+          e += expect_tile_ff(sx, sxf, slf, tb, S.rowoff, m, a.terms + R.term0, R.nterm);
+          __syncthreads();
+          if (grad) store_tiles_ff(sxf, a.wpsif + R.work_off + tb, slf, a.wlamf + R.work_off + tb, S.rowoff, m);
+        } else {
+          e += expect_tile(sx, sl, tb, S.rowoff, m, a.terms + R.term0, R.nterm);
+          __syncthreads();
+          if (grad) store_tiles<true>(sx, a.wpsi + R.work_off + tb, sl, a.wlam + R.work_off + tb, S.rowoff, m);
+        }
         __syncthreads();
       }
       block_loss(e, S, a.loss + reg);
       __syncthreads();
-      if (grad) batch_bwd_streamed(sx, sl, P, R.npass, m, g, wp, wl, a.phases, a.bops, S.rowoff, S.red, S.grad);
+      if (grad) {
+        if (PREC)
+          batch_bwd_streamed_ff<RB>(sxf, slf, P, R.npass, m, g, a.wpsif + R.work_off, a.wlamf + R.work_off, a.phases,
+                                    a.bops, a.blo, S.rowoff, S.red, S.grad);
+        else
+          batch_bwd_streamed<RB>(sx, sl, P, R.npass, m, g, a.wpsi + R.work_off, a.wlam + R.work_off, a.phases,
+                                 a.bops, S.rowoff, S.red, S.grad);
+      }
     }
     __syncthreads();
     if (grad)
       for (int i = tid; i < R.nparam; i += blockDim.x) a.grad[R.param_off + i] = S.grad[i];
     __syncthreads();
+  }
+}
+
+// bytes of dynamic shared memory of k_batch<RB, PREC>
+static size_t batch_smem(int rb, bool prec) {
+  const size_t mt = (size_t)1 << (9 + rb);
+  return ((sizeof(BShared) + 255) & ~size_t(255)) + (prec ? (8 + 32) * mt : 16 * mt);
+}
+
+// the instantiation of k_batch for a phase width and path
+static const void* batch_kernel(int rb, bool prec) {
+  if (prec) return rb == 2 ? (const void*)k_batch<2, true> : (const void*)k_batch<3, true>;
+  switch (rb) {
+    case 2: return (const void*)k_batch<2, false>;
+    case 3: return (const void*)k_batch<3, false>;
+    default: return (const void*)k_batch<4, false>;
   }
 }
 
@@ -635,7 +1086,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_fused_pass(FArgs a) {
     float2* base = a.state + r * a.reg_stride + tb;
     load_tile(sx, base, rowoff, a.m);
     __syncthreads();
-    for (int f = 0; f < p.nphase; ++f) run_phase_fwd(sx, a.phases + p.phase0 + f, a.fops, a.dtab, a.m, (uint32_t)tb);
+    for (int f = 0; f < p.nphase; ++f)
+      run_phase_fwd<kRB, false>(sx, a.phases + p.phase0 + f, a.fops, a.dtab, nullptr, nullptr, a.m, (uint32_t)tb);
     store_tile(sx, base, rowoff, a.m);
     __syncthreads();
   }
@@ -672,7 +1124,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_fused_bwd_pass(FBArgs a) {
     load_tiles<true>(sx, a.wpsi + tb, sl, a.wlam + tb, rowoff, a.m);
     __syncthreads();
     for (int f = p.nphase - 1; f >= 0; --f)
-      run_phase_bwd(sx, sl, a.phases + p.phase0 + f, a.bops, a.m, red, gacc, (uint32_t)tb);
+      run_phase_bwd<kRB>(sx, sl, a.phases + p.phase0 + f, a.bops, a.m, red, gacc, (uint32_t)tb);
     store_tiles<true>(sx, a.wpsi + tb, sl, a.wlam + tb, rowoff, a.m);
     __syncthreads();
   }
@@ -734,6 +1186,9 @@ struct PrepArgs {
   const GSpec* gspec;
   const FMem* fmem;
   const int32_t* bgate;
+  float2* flo;             // if not NULL: corrections of the forward matrices (precise path)
+  float2* blo;             // backward U^dagger corrections
+  float2* dtlo;            // diagonal table corrections
   const DMem* dmem;
   const DRef* dref;
   TOp* fops;
@@ -775,6 +1230,13 @@ __device__ __forceinline__ double2 zmul(double2 a, double2 b) {
 }
 __device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 
+// FP32 value of v and its correction v - hi (both components)
+__device__ __forceinline__ float2 hi_of(double2 v) { return make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ float2 lo_of(double2 v) {
+  const float2 h = hi_of(v);
+  return make_float2((float)(v.x - (double)h.x), (float)(v.y - (double)h.y));
+}
+
 __global__ void k_batch_prep(PrepArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < a.nfop) {
@@ -789,16 +1251,19 @@ __global__ void k_batch_prep(PrepArgs a) {
       const double2 C3 = zadd(zmul(U[2], A[1]), zmul(U[3], A[3]));
       A[0] = C0; A[1] = C1; A[2] = C2; A[3] = C3;
     }
-    for (int k = 0; k < 4; ++k) a.fops[i].u[k] = make_float2((float)A[k].x, (float)A[k].y);
+    for (int k = 0; k < 4; ++k) a.fops[i].u[k] = hi_of(A[k]);
+    if (a.flo)
+      for (int k = 0; k < 4; ++k) a.flo[4 * i + k] = lo_of(A[k]);
   } else if (i < a.nfop + a.nbop) {
     const int j = i - a.nfop;
     double2 U[4];
     gate_mat(a.gspec[a.bgate[j]], a.params, U);
     // U^dagger
-    a.bops[j].u[0] = make_float2((float)U[0].x, (float)-U[0].y);
-    a.bops[j].u[1] = make_float2((float)U[2].x, (float)-U[2].y);
-    a.bops[j].u[2] = make_float2((float)U[1].x, (float)-U[1].y);
-    a.bops[j].u[3] = make_float2((float)U[3].x, (float)-U[3].y);
+    const double2 D[4] = {make_double2(U[0].x, -U[0].y), make_double2(U[2].x, -U[2].y),
+                          make_double2(U[1].x, -U[1].y), make_double2(U[3].x, -U[3].y)};
+    for (int k = 0; k < 4; ++k) a.bops[j].u[k] = hi_of(D[k]);
+    if (a.blo)
+      for (int k = 0; k < 4; ++k) a.blo[4 * j + k] = lo_of(D[k]);
   } else if (i < a.nfop + a.nbop + a.ndiag) {
     // product of the member gates' diagonals on the 16 phase amplitudes
     const int d = i - a.nfop - a.nbop;
@@ -812,7 +1277,9 @@ __global__ void k_batch_prep(PrepArgs a) {
       for (int j = 0; j < 16; ++j)
         if ((j & mb.cm) == mb.cv) f[j] = zmul(f[j], ((j >> mb.tb) & 1) ? U[3] : U[0]);
     }
-    for (int j = 0; j < 16; ++j) a.dtab[16 * d + j] = make_float2((float)f[j].x, (float)f[j].y);
+    for (int j = 0; j < 16; ++j) a.dtab[16 * d + j] = hi_of(f[j]);
+    if (a.dtlo)
+      for (int j = 0; j < 16; ++j) a.dtlo[16 * d + j] = lo_of(f[j]);
   }
 }
 
@@ -845,6 +1312,15 @@ struct qs_batch_program {
   int* counter = nullptr;
   float2* wpsi = nullptr;
   float2* wlam = nullptr;
+  // phase width and the precise path (compensated forward, double-float uncompute)
+  int rb = qs::kRB;
+  int tile = 0;
+  bool precise = false;
+  float2* flo = nullptr;   // corrections of the forward ops (4 per op)
+  float2* blo = nullptr;   // corrections of the backward ops (4 per op)
+  float2* dtlo = nullptr;  // corrections of the diagonal tables (16 per table)
+  float4* wpsif = nullptr;
+  float4* wlamf = nullptr;
   int nfop = 0, nbop = 0;
   int64_t npass = 0, nphase = 0;
   int blocks = 0;
@@ -895,19 +1371,29 @@ static void free_program(qs_batch_program* p) {
   const bool swap = p->device >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != p->device &&
                     cudaSetDevice(p->device) == cudaSuccess;
   void* ptrs[] = {p->regs, p->order, p->passes, p->phases, p->fops, p->bops, p->terms, p->gspec, p->fmem,
-                  p->bgate, p->dmem, p->dref, p->dtab, p->counter, p->wpsi, p->wlam, p->dparams};
+                  p->bgate, p->dmem, p->dref, p->dtab, p->counter, p->wpsi, p->wlam, p->dparams,
+                  p->flo, p->blo, p->dtlo, p->wpsif, p->wlamf};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (swap) cudaSetDevice(cur);
   delete p;
 }
 
+// largest tile of the batched kernel for rb-bit phases: 512 threads x 2^rb amplitudes
+static int max_tile(int rb) { return std::min(kBatchTile, 9 + rb); }
+
 static int build_program(int nreg, const qs_circuit* const* circs, const qs_observable* const* obs, int tile_qubits,
-                         qs_batch_program* P) {
-  const int M = tile_qubits > 0 ? tile_qubits : kBatchTile;
-  // a tile holds register qubits 0..4 (contiguous rows) plus a phase's 4 register bits
-  if (M < kRowBits + kRB || M > kBatchTile)
-    return fail(QS_EINVAL, "tile_qubits must be in %d..%d", kRowBits + kRB, kBatchTile);
+                         qs_batch_program* P, int rb = kRB, bool precise = false) {
+  if (rb < kMinRB || rb > kRB) return fail(QS_EINVAL, "phase_qubits must be in %d..%d", kMinRB, kRB);
+  if (precise && rb > 3) return fail(QS_EINVAL, "the precise path takes phases of at most 3 qubits");
+  const int MT = max_tile(rb);
+  const int M = tile_qubits > 0 ? tile_qubits : MT;
+  // a tile holds register qubits 0..4 (contiguous rows) plus a phase's register bits
+  if (M < kRowBits + rb || M > MT)
+    return fail(QS_EINVAL, "tile_qubits must be in %d..%d for %d-qubit phases", kRowBits + rb, MT, rb);
+  P->rb = rb;
+  P->precise = precise;
+  P->tile = M;
   QS_CUDA(cudaGetDevice(&P->device));
   std::vector<BReg> regs(nreg);
   std::vector<TPass> passes;
@@ -938,7 +1424,7 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
     P->amp_off[r + 1] = P->amp_off[r] + (1ll << n);
     const int m = std::min(n, M);
     std::vector<HostPass> hp;
-    QS_TRY(plan_passes(c, n, m, kMaxPhaseOps, hp));
+    QS_TRY(plan_passes(c, n, m, kMaxPhaseOps, hp, rb));
     BReg& R = regs[r];
     memset(&R, 0, sizeof(R));
     R.n = n;
@@ -988,16 +1474,16 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
       tp.nphase = (int)p.phases.size();
       for (const HostPhase& ph : p.phases) {
         TPhase t;
-        phase_positions(p, ph, &t);
+        phase_positions(p, ph, &t, rb);
         // register qubit -> phase bit index
         auto pbit = [&](int qb) {
-          for (int k = 0; k < kRB; ++k)
+          for (int k = 0; k < rb; ++k)
             if (ph.rbits[k] == qb) return k;
           return -1;
         };
         t.bop0 = (int)bops.size();
         t.fop0 = (int)fops.size();
-        std::vector<int> last(kRB, -1);  // forward op index (in fops) open for fusion per phase bit
+        std::vector<int> last(rb, -1);   // forward op index (in fops) open for fusion per phase bit
         int dg = -1;                     // open TK_DIAG16 table of this phase
         uint8_t nondiag = 0;             // phase bits touched by non-diagonal gates since it opened
         for (int gi : ph.gates) {
@@ -1064,7 +1550,7 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
             f.t = (uint8_t)g.locs[0];
             fops.push_back(f);
             fmem.push_back(fm);
-            for (int k = 0; k < kRB; ++k)
+            for (int k = 0; k < rb; ++k)
               if ((cm >> k) & 1) last[k] = -1;
             continue;
           }
@@ -1104,7 +1590,7 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
           }
           // a controlled gate closes fusion on its target and its phase-local controls
           if (cm || tmask) {
-            for (int k = 0; k < kRB; ++k)
+            for (int k = 0; k < rb; ++k)
               if ((cm >> k) & 1) last[k] = -1;
             last[tb] = -1;
           }
@@ -1143,11 +1629,21 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
   P->ndiag = (int)drefs.size();
   QS_TRY(upload(&P->dtab, std::vector<float2>(16 * std::max<size_t>(1, drefs.size()))));
   QS_TRY(upload(&P->counter, std::vector<int>(1, 0)));
-  if (work > 0) {
+  if (work > 0 && !precise) {
     if (cudaMalloc(&P->wpsi, sizeof(float2) * work) != cudaSuccess ||
         cudaMalloc(&P->wlam, sizeof(float2) * work) != cudaSuccess) {
       cudaGetLastError();
       return fail(QS_ENOMEM, "cudaMalloc of the backward work buffers failed");
+    }
+  }
+  if (precise) {
+    if ((work > 0 && (cudaMalloc(&P->wpsif, sizeof(float4) * work) != cudaSuccess ||
+                      cudaMalloc(&P->wlamf, sizeof(float4) * work) != cudaSuccess)) ||
+        cudaMalloc(&P->flo, sizeof(float2) * 4 * std::max<size_t>(1, fops.size())) != cudaSuccess ||
+        cudaMalloc(&P->blo, sizeof(float2) * 4 * std::max<size_t>(1, bops.size())) != cudaSuccess ||
+        cudaMalloc(&P->dtlo, sizeof(float2) * 16 * std::max<size_t>(1, drefs.size())) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(QS_ENOMEM, "cudaMalloc of the precise path's buffers failed");
     }
   }
   P->host_passes = passes;
@@ -1162,12 +1658,13 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
     P->blocks = sms * per_sm;
     return QS_OK;
   }
-  P->smem = ((sizeof(BShared) + 255) & ~size_t(255)) + 2 * sizeof(float2) * (1 << kBatchTile);
-  QS_CUDA(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smem));
+  P->smem = batch_smem(rb, precise);
+  const void* kfn = batch_kernel(rb, precise);
+  QS_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smem));
   int dev = 0, sms = 0, per_sm = 0;
   QS_CUDA(cudaGetDevice(&dev));
   QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  QS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kTileThreads, P->smem));
+  QS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kTileThreads, P->smem));
   if (per_sm < 1) return fail(QS_EDEVICE, "batched kernel does not fit on an SM");
   P->blocks = std::min(nreg, sms * per_sm);
   return QS_OK;
@@ -1180,6 +1677,9 @@ static int launch_prep(const qs_batch_program* P, const double* dev_params, bool
   pa.gspec = P->gspec;
   pa.fmem = P->fmem;
   pa.bgate = P->bgate;
+  pa.flo = P->flo;
+  pa.blo = P->blo;
+  pa.dtlo = P->dtlo;
   pa.dmem = P->dmem;
   pa.dref = P->dref;
   pa.fops = P->fops;
@@ -1495,6 +1995,88 @@ int qs_batch_program_create(int nreg, const qs_circuit* const* circuits, const q
   return QS_OK;
 }
 
+int qs_batch_program_create_ex(int nreg, const qs_circuit* const* circuits, const qs_observable* const* observables,
+                               int tile_qubits, int phase_qubits, int flags, qs_batch_program** out) {
+  if (!out || nreg < 1 || !circuits || !observables) return fail(QS_EINVAL, "bad arguments");
+  if (flags & ~QS_BATCH_PRECISE) return fail(QS_EINVAL, "unknown program flags 0x%x", flags);
+  *out = nullptr;
+  qs_batch_program* P = new qs_batch_program();
+  const int rc = build_program(nreg, circuits, observables, tile_qubits, P, phase_qubits > 0 ? phase_qubits : kRB,
+                               (flags & QS_BATCH_PRECISE) != 0);
+  if (rc != QS_OK) {
+    const std::string msg = qs_last_error();
+    free_program(P);
+    return fail(rc, "%s", msg.c_str());
+  }
+  *out = P;
+  return QS_OK;
+}
+
+int qs_batch_program_shape(const qs_batch_program* p, int* tile_qubits, int* phase_qubits, int* flags) {
+  if (!p) return fail(QS_EINVAL, "null program");
+  if (tile_qubits) *tile_qubits = p->tile;
+  if (phase_qubits) *phase_qubits = p->rb;
+  if (flags) *flags = p->precise ? QS_BATCH_PRECISE : 0;
+  return QS_OK;
+}
+
+int qs_batch_autotune_ex(int nreg, const qs_circuit* const* circuits, const qs_observable* const* observables,
+                         int flags, qs_state* s, const double* dev_params, double* dev_loss, double* dev_grad,
+                         int reps, int* best_tile, int* best_phase, int* ncand, int32_t* host_tiles,
+                         int32_t* host_phases, double* host_ms) {
+  if (!circuits || !observables || !s || !dev_params || !dev_loss || !best_tile || !best_phase)
+    return fail(QS_EINVAL, "null argument");
+  if (flags & ~QS_BATCH_PRECISE) return fail(QS_EINVAL, "unknown program flags 0x%x", flags);
+  if (reps < 1) reps = 1;
+  const bool precise = (flags & QS_BATCH_PRECISE) != 0;
+  const int rflags = QS_BATCH_RESET | (dev_grad ? QS_BATCH_GRAD : 0);
+  int best = -1, bestrb = -1, nc = 0;
+  double best_ms = 0;
+  cudaEvent_t e0, e1;
+  QS_CUDA(cudaEventCreate(&e0));
+  QS_CUDA(cudaEventCreate(&e1));
+  int rc = QS_OK;
+  for (int rb = precise ? 3 : kRB; rb >= kMinRB && rc == QS_OK; --rb) {
+    const int mt = max_tile(rb);
+    for (int m = mt; m >= std::max(kRowBits + rb + 2, mt - 2) && rc == QS_OK; --m) {
+      qs_batch_program* P = nullptr;
+      double ms = -1;
+      const int crc = qs_batch_program_create_ex(nreg, circuits, observables, m, rb, flags, &P);
+      if (crc == QS_OK) {
+        rc = qs_batch_run(s, P, dev_params, dev_loss, dev_grad, rflags);  // warm-up
+        if (rc == QS_OK && cudaEventRecord(e0, s->stream) != cudaSuccess) rc = fail(QS_EDEVICE, "event record");
+        for (int r = 0; r < reps && rc == QS_OK; ++r) rc = qs_batch_run(s, P, dev_params, dev_loss, dev_grad, rflags);
+        if (rc == QS_OK && cudaEventRecord(e1, s->stream) != cudaSuccess) rc = fail(QS_EDEVICE, "event record");
+        if (rc == QS_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = fail(QS_EDEVICE, "event sync");
+        float t = 0;
+        if (rc == QS_OK && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms = (double)t / reps;
+        qs_batch_program_destroy(P);
+      } else if (crc != QS_EUNSUPPORTED && crc != QS_EINVAL) {
+        rc = crc;
+      }
+      if (ncand && nc < *ncand) {
+        if (host_tiles) host_tiles[nc] = m;
+        if (host_phases) host_phases[nc] = rb;
+        if (host_ms) host_ms[nc] = ms;
+      }
+      ++nc;
+      if (ms >= 0 && (best < 0 || ms < best_ms)) {
+        best = m;
+        bestrb = rb;
+        best_ms = ms;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != QS_OK) return rc;
+  if (ncand) *ncand = nc;
+  if (best < 0) return fail(QS_EUNSUPPORTED, "no program shape ran the batch");
+  *best_tile = best;
+  *best_phase = bestrb;
+  return QS_OK;
+}
+
 int qs_batch_program_destroy(qs_batch_program* p) {
   free_program(p);
   return QS_OK;
@@ -1532,6 +2114,11 @@ int qs_batch_run(qs_state* s, const qs_batch_program* p, const double* dev_param
   a.dtab = p->dtab;
   a.wpsi = p->wpsi;
   a.wlam = p->wlam;
+  a.wpsif = p->wpsif;
+  a.wlamf = p->wlamf;
+  a.flo = p->flo;
+  a.blo = p->blo;
+  a.dtlo = p->dtlo;
   a.regs = p->regs;
   a.order = p->order;
   a.passes = p->passes;
@@ -1544,7 +2131,16 @@ int qs_batch_run(qs_state* s, const qs_batch_program* p, const double* dev_param
   a.counter = p->counter;
   a.nreg = p->nreg;
   a.flags = ((flags & QS_BATCH_RESET) ? BF_RESET : 0) | (grad ? BF_GRAD : 0);
-  k_batch<<<p->blocks, kTileThreads, p->smem, st>>>(a);
+  if (p->precise) {
+    if (p->rb == 2) k_batch<2, true><<<p->blocks, kTileThreads, p->smem, st>>>(a);
+    else k_batch<3, true><<<p->blocks, kTileThreads, p->smem, st>>>(a);
+  } else {
+    switch (p->rb) {
+      case 2: k_batch<2, false><<<p->blocks, kTileThreads, p->smem, st>>>(a); break;
+      case 3: k_batch<3, false><<<p->blocks, kTileThreads, p->smem, st>>>(a); break;
+      default: k_batch<4, false><<<p->blocks, kTileThreads, p->smem, st>>>(a); break;
+    }
+  }
   QS_LAUNCHED();
   return QS_OK;
 }

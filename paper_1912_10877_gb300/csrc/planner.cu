@@ -60,10 +60,11 @@ static std::vector<int> bits_of(uint64_t m) {
   return v;
 }
 
-int plan_passes(const qs_circuit* c, int n, int m, int max_phase_ops, std::vector<HostPass>& out) {
+int plan_passes(const qs_circuit* c, int n, int m, int max_phase_ops, std::vector<HostPass>& out, int rb) {
   out.clear();
   if (m < kRowBits || m > n || m > kMaxTileBits)
     return fail(QS_EINVAL, "tile of %d qubits for a register of %d", m, n);
+  if (rb < kMinRB || rb > kRB || rb > m) return fail(QS_EINVAL, "%d register bits per phase (tile of %d)", rb, m);
   const int G = (int)c->gates.size();
   std::vector<uint64_t> dep(G), fit(G);
   for (int i = 0; i < G; ++i) {
@@ -89,14 +90,15 @@ int plan_passes(const qs_circuit* c, int n, int m, int max_phase_ops, std::vecto
     while (!prem.empty()) {
       uint64_t R = 0;
       std::vector<int> pt, pl;
-      scan(prem, dep, fit, R, kRB, (size_t)max_phase_ops, pt, pl);
+      scan(prem, dep, fit, R, rb, (size_t)max_phase_ops, pt, pl);
       for (int b : P.tbits) {
-        if (__builtin_popcountll(R) >= kRB) break;
+        if (__builtin_popcountll(R) >= rb) break;
         R |= 1ull << b;
       }
       HostPhase ph;
-      std::vector<int> rb = bits_of(R);
-      for (int k = 0; k < kRB; ++k) ph.rbits[k] = rb[k];
+      for (int k = 0; k < kRB; ++k) ph.rbits[k] = -1;
+      std::vector<int> rbits = bits_of(R);
+      for (int k = 0; k < rb; ++k) ph.rbits[k] = rbits[k];
       ph.gates = pt;
       P.phases.push_back(ph);
       prem.swap(pl);
@@ -107,14 +109,14 @@ int plan_passes(const qs_circuit* c, int n, int m, int max_phase_ops, std::vecto
   return QS_OK;
 }
 
-void phase_positions(const HostPass& p, const HostPhase& ph, TPhase* out) {
+void phase_positions(const HostPass& p, const HostPhase& ph, TPhase* out, int rb) {
   memset(out, 0, sizeof(*out));
   const int m = (int)p.tbits.size();
   int nt = 0, nr = 0;
   for (int l = 0; l < m; ++l) {
     const int qb = p.tbits[l];
     bool inR = false;
-    for (int k = 0; k < kRB; ++k)
+    for (int k = 0; k < rb; ++k)
       if (ph.rbits[k] == qb) inR = true;
     if (inR) {
       out->rpos[nr++] = (uint8_t)l;
@@ -123,9 +125,9 @@ void phase_positions(const HostPass& p, const HostPhase& ph, TPhase* out) {
       out->tpos[nt++] = (uint8_t)l;
     }
   }
-  for (int j = 0; j < (1 << kRB); ++j) {
+  for (int j = 0; j < (1 << rb); ++j) {
     uint32_t r = 0;
-    for (int k = 0; k < kRB; ++k)
+    for (int k = 0; k < rb; ++k)
       if ((j >> k) & 1) r |= 1u << out->rpos[k];
     out->sroff[j] = (uint16_t)swz(r);
   }

@@ -6,8 +6,12 @@
 // <psi|P|psi> = sum_i ph(i) conj(psi_{i^x}) psi_i.  Terms are grouped by their
 // x mask; one streaming pass per group reads each amplitude (or each pair
 // (i, i^x) once, counting it twice) and accumulates every term of the group in
-// FP64.  Per-block partial sums go to scratch memory and a second kernel folds
-// them in a fixed order, so results are reproducible run to run.
+// FP64.  The sum is pairwise: a thread adds at most kSerialItems items in
+// order (the serial base case), warps and blocks combine by balanced trees,
+// and a second kernel folds the per-block partials of every term by a
+// balanced tree as well (fixed shapes, so results are reproducible run to
+// run).  Error bound: (kSerialItems + log2 of the item count) * 2^-53 of the
+// sum of the absolute terms.
 //
 // measure (Sec. "Instructions on Quantum Registers"): the deterministic
 // contract of qsim.h -- FP64 probabilities with separately rounded multiply
@@ -22,6 +26,7 @@
 namespace qs {
 
 constexpr int kRedThreads = 256;
+constexpr int kSerialItems = 64;  // serial base case of the pairwise expectation sums
 constexpr int kGroupTerms = 16;   // terms of one x-mask group handled per launch
 constexpr int kObsChunk = 64;     // terms per lambda = O psi launch
 
@@ -93,28 +98,81 @@ k_expect_group(const T* __restrict__ psi, uint64_t reg_stride, TermGroup g, doub
   }
   __syncthreads();
   if (threadIdx.x < g.nt) {
-    double v = 0.0;
-    for (int w = 0; w < kRedThreads / 32; ++w) v += red[w][threadIdx.x];
+    static_assert(kRedThreads / 32 == 8, "block tree below is written for 8 warps");
+    const int t = threadIdx.x;
+    const double v = ((red[0][t] + red[1][t]) + (red[2][t] + red[3][t])) +
+                     ((red[4][t] + red[5][t]) + (red[6][t] + red[7][t]));
     const double f = g.h >= 0 ? 2.0 : 1.0;
     partials[((r * nt_total) + term_base + threadIdx.x) * nblk + blockIdx.x] = f * v;
   }
 }
 
-// one thread per register: fold block partials per term (pairwise in place
-// would need scratch; a left fold over <= a few thousand FP64 partials is
-// exact enough and deterministic), then sum c_t * v_t in term order.
-__global__ void k_expect_final(const double* __restrict__ partials, int nblk, int nt_total,
-                               const double* __restrict__ coeff, int nreg, double* __restrict__ out) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nreg) return;
-  double total = 0.0;
-  for (int t = 0; t < nt_total; ++t) {
-    const double* q = partials + ((size_t)r * nt_total + t) * nblk;
-    double v = 0.0;
-    for (int b = 0; b < nblk; ++b) v += q[b];
-    total += coeff[t] * v;
+// Pairwise sum in index order of the values add()ed one by one: a binary
+// counter of partial sums, so 2^k values form a balanced tree.
+struct PairwiseAcc {
+  double stk[40];
+  uint64_t cnt = 0;
+  __device__ void add(double v) {
+    int lvl = 0;
+    while ((cnt >> lvl) & 1ull) {
+      v = stk[lvl] + v;
+      ++lvl;
+    }
+    stk[lvl] = v;
+    ++cnt;
   }
-  out[r] = total;
+  __device__ double total() const {
+    double r = 0.0;
+    bool any = false;
+    for (int lvl = 0; lvl < 40; ++lvl)
+      if ((cnt >> lvl) & 1ull) {
+        r = any ? stk[lvl] + r : stk[lvl];
+        any = true;
+      }
+    return r;
+  }
+};
+
+constexpr int kFoldThreads = 256;
+
+// Pairwise sum of v[0..len) by one CTA of kFoldThreads threads: contiguous
+// chunks per thread (binary counter), then a shared-memory tree.  Every thread
+// receives the result.
+__device__ double block_pairwise(const double* __restrict__ v, int64_t len, double* sh) {
+  const int64_t chunk = (len + kFoldThreads - 1) / kFoldThreads;
+  const int64_t lo = (int64_t)threadIdx.x * chunk, hi = lo + chunk < len ? lo + chunk : len;
+  PairwiseAcc acc;
+  for (int64_t i = lo; i < hi; ++i) acc.add(v[i]);
+  sh[threadIdx.x] = acc.total();
+  __syncthreads();
+  for (int w = kFoldThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] = sh[threadIdx.x] + sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// one CTA per register: every term's block partials folded pairwise, then the
+// terms' c_t * v_t pairwise in term order.
+__global__ void __launch_bounds__(kFoldThreads)
+k_expect_final(const double* __restrict__ partials, int nblk, int nt_total, const double* __restrict__ coeff,
+               double* __restrict__ out) {
+  __shared__ double sh[kFoldThreads];
+  const int r = blockIdx.x;
+  PairwiseAcc terms;
+  for (int t = 0; t < nt_total; ++t) {
+    const double v = block_pairwise(partials + ((size_t)r * nt_total + t) * nblk, nblk, sh);
+    terms.add(coeff[t] * v);
+  }
+  if (threadIdx.x == 0) out[r] = terms.total();
+}
+
+// blocks per register for the pairwise expectation: at most kSerialItems items per thread
+static int expect_blocks(uint64_t items) {
+  const uint64_t per_block = (uint64_t)kRedThreads * kSerialItems;
+  return (int)std::max<uint64_t>(1, (items + per_block - 1) / per_block);
 }
 
 struct ObsChunk {
@@ -169,8 +227,8 @@ int expect_raw(const void* data, int dtype, int n, int nreg, const qs_observable
   std::vector<std::pair<uint64_t, std::vector<int>>> groups;
   grouped(o, groups);
   const uint64_t dim = 1ull << n;
-  int nblk = (int)std::min<uint64_t>(std::max<uint64_t>(1, dim / (kRedThreads * 8)),
-                                     std::max(1, 1216 / std::max(1, nreg)));
+  // every group's items: 2^n (x = 0) or 2^(n-1) pairs; the grid covers the larger
+  const int nblk = expect_blocks(dim);
   const size_t part_bytes = sizeof(double) * (size_t)nreg * std::max(1, nt_total) * nblk;
   const size_t coeff_off = (part_bytes + 255) / 256 * 256;
   const size_t out_off = coeff_off + (sizeof(double) * std::max(1, nt_total) + 255) / 256 * 256;
@@ -212,7 +270,7 @@ int expect_raw(const void* data, int dtype, int n, int nreg, const qs_observable
   if (nt_total == 0) {
     QS_CUDA(cudaMemsetAsync(dev_out, 0, sizeof(double) * nreg, st));
   } else {
-    k_expect_final<<<(nreg + 127) / 128, 128, 0, st>>>(partials, nblk, nt_total, dcoeff, nreg, dev_out);
+    k_expect_final<<<nreg, kFoldThreads, 0, st>>>(partials, nblk, nt_total, dcoeff, dev_out);
     QS_LAUNCHED();
   }
   QS_CUDA(cudaMemcpyAsync(host_out, dev_out, sizeof(double) * nreg, cudaMemcpyDeviceToHost, st));
@@ -352,8 +410,22 @@ int sample_dev(const void* data, int dtype, int n, const double* dev_u, int nsho
   return QS_OK;
 }
 
+// Uniforms of the seeded measurement: draw k of SplitMix64 started from `seed`
+// (Steele, Lea and Flood 2014): state seed + k * 0x9E3779B97F4A7C15, then the
+// 64-bit finaliser (xor-shift 30, multiply, xor-shift 27, multiply, xor-shift
+// 31); u = top 53 bits / 2^53.  Shot j of this call is draw k0 + j + 1.
+__global__ void k_seeded_uniforms(uint64_t seed, uint64_t k0, int nshots, double* __restrict__ u) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nshots) return;
+  uint64_t x = seed + (k0 + (uint64_t)j + 1ull) * 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  x ^= x >> 31;
+  u[j] = (double)(x >> 11) * 0x1.0p-53;
+}
+
 int measure_one(void* data, int dtype, int n, const double* host_u, int nshots, int64_t* host_out,
-                int collapse, qs_state* owner) {
+                int collapse, qs_state* owner, const uint64_t* seed, uint64_t k0) {
   cudaStream_t st = owner->stream;
   const uint64_t dim = 1ull << n;
   const uint64_t nb0 = (dim + kF - 1) / kF, nb1 = (nb0 + kF - 1) / kF;
@@ -365,7 +437,12 @@ int measure_one(void* data, int dtype, int n, const double* host_u, int nshots, 
   double* du = s1 + nb1;
   int64_t* dout = (int64_t*)(du + nshots);
   double2* keep = (double2*)(((uintptr_t)(dout + nshots) + 15) & ~(uintptr_t)15);
-  QS_CUDA(cudaMemcpyAsync(du, host_u, sizeof(double) * nshots, cudaMemcpyHostToDevice, st));
+  if (seed) {
+    k_seeded_uniforms<<<(nshots + 127) / 128, 128, 0, st>>>(*seed, k0, nshots, du);
+    QS_LAUNCHED();
+  } else {
+    QS_CUDA(cudaMemcpyAsync(du, host_u, sizeof(double) * nshots, cudaMemcpyHostToDevice, st));
+  }
   if (dtype == QS_C64) {
     k_level0<float2><<<(unsigned)((nb0 + 127) / 128), 128, 0, st>>>((const float2*)data, dim, nb0, s0);
   } else {
@@ -461,18 +538,17 @@ struct StaticCoeffs {
   double c[kStaticTerms];
 };
 
-__global__ void k_expect_final_static(const double* __restrict__ partials, int nblk, int nt_total,
-                                      const __grid_constant__ StaticCoeffs co, int nreg, double* __restrict__ out) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nreg) return;
-  double total = 0.0;
+__global__ void __launch_bounds__(kFoldThreads)
+k_expect_final_static(const double* __restrict__ partials, int nblk, int nt_total,
+                      const __grid_constant__ StaticCoeffs co, double* __restrict__ out) {
+  __shared__ double sh[kFoldThreads];
+  const int r = blockIdx.x;
+  PairwiseAcc terms;
   for (int t = 0; t < nt_total; ++t) {
-    const double* q = partials + ((size_t)r * nt_total + t) * nblk;
-    double v = 0.0;
-    for (int b = 0; b < nblk; ++b) v += q[b];
-    total += co.c[t] * v;
+    const double v = block_pairwise(partials + ((size_t)r * nt_total + t) * nblk, nblk, sh);
+    terms.add(co.c[t] * v);
   }
-  out[r] = total;
+  if (threadIdx.x == 0) out[r] = terms.total();
 }
 
 // device address of g_static_partials on the current device, resolved once per
@@ -533,8 +609,7 @@ extern "C" int qs_expect_static(const void* dev_amps, int dtype, int nqubits, in
     order[j] = t;
   }
   const uint64_t dim = 1ull << nqubits;
-  long long nblk = (long long)std::min<uint64_t>(std::max<uint64_t>(1, dim / (kRedThreads * 8)),
-                                                 std::max(1, 1216 / nreg));
+  long long nblk = expect_blocks(dim);
   nblk = std::max(1LL, std::min(nblk, (long long)kStaticPartials / ((long long)nreg * nterms)));
   StaticCoeffs co;
   memset(&co, 0, sizeof(co));
@@ -561,7 +636,7 @@ extern "C" int qs_expect_static(const void* dev_amps, int dtype, int nqubits, in
     QS_LAUNCHED();
     base += tg.nt;
   }
-  k_expect_final_static<<<(nreg + 127) / 128, 128, 0, st>>>(partials, (int)nblk, nterms, co, nreg, dev_out);
+  k_expect_final_static<<<nreg, kFoldThreads, 0, st>>>(partials, (int)nblk, nterms, co, dev_out);
   if (cudaPeekAtLastError() != cudaSuccess) g_static_addr[cur_dev] = nullptr;  // resolve again next call
   QS_LAUNCHED();
   return QS_OK;

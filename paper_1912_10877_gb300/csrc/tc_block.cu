@@ -119,7 +119,13 @@ __host__ __device__ constexpr uint32_t tf32_idesc(int n_dim, int m_dim = kTcRows
          | ((uint32_t)(m_dim >> 4) << 24);    // bits 24-28: M / 16
 }
 
-__device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); }
+// v rounded to the nearest TF32 value (10 stored mantissa bits, ties away from
+// zero): exactly representable, so the tensor core reads it unchanged
+__device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u); }
+// the correction v - hi (exact in FP32), itself rounded to TF32: hi + lo = v to
+// 2^-24 relative, unbiased (a lo left in FP32 would be truncated by the tensor
+// core, a bias of up to 2^-22 that accumulates over blocks)
+__device__ __forceinline__ float tf32_lo(float v, float h) { return tf32_hi(v - h); }
 
 __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
@@ -291,7 +297,7 @@ __global__ void __launch_bounds__(kBkThreads, 1) k_block_tc(const __grid_constan
     const int n = e / W, kk = e % W;
     const float v = a.b[n][kk], h = tf32_hi(v);
     *reinterpret_cast<float*>(sm + L::B_HI + sw128_off(n, kk, W)) = h;
-    *reinterpret_cast<float*>(sm + L::B_LO + sw128_off(n, kk, W)) = v - h;
+    *reinterpret_cast<float*>(sm + L::B_LO + sw128_off(n, kk, W)) = tf32_lo(v, h);
   }
   if (tid < D) s_off[tid] = a.off[tid];
   if (tid < kTcRows) s_P[tid] = row_offset(tid, a);
@@ -385,21 +391,22 @@ __global__ void __launch_bounds__(kBkThreads, 1) k_block_tc(const __grid_constan
           const float4 x = *reinterpret_cast<const float4*>(&v[k]);
           const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
           *reinterpret_cast<float4*>(ah + soff[k]) = h;  // columns 2m..2m+3: one 16-byte chunk
-          *reinterpret_cast<float4*>(al + soff[k]) = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+          *reinterpret_cast<float4*>(al + soff[k]) =
+              make_float4(tf32_lo(x.x, h.x), tf32_lo(x.y, h.y), tf32_lo(x.z, h.z), tf32_lo(x.w, h.w));
         } else if (MODE == TC_PAIR_TUPLES) {
           const float4 x = *reinterpret_cast<const float4*>(&v[k]);
           const float2 h0 = make_float2(tf32_hi(x.x), tf32_hi(x.y)), h1 = make_float2(tf32_hi(x.z), tf32_hi(x.w));
           // row t + 1 of the same column: next 128-byte row, chunk index ^ 1 when t is even
           const uint32_t o0 = soff[k], o1 = (o0 + 128u) ^ 16u;
           *reinterpret_cast<float2*>(ah + o0) = h0;
-          *reinterpret_cast<float2*>(al + o0) = make_float2(x.x - h0.x, x.y - h0.y);
+          *reinterpret_cast<float2*>(al + o0) = make_float2(tf32_lo(x.x, h0.x), tf32_lo(x.y, h0.y));
           *reinterpret_cast<float2*>(ah + o1) = h1;
-          *reinterpret_cast<float2*>(al + o1) = make_float2(x.z - h1.x, x.w - h1.y);
+          *reinterpret_cast<float2*>(al + o1) = make_float2(tf32_lo(x.z, h1.x), tf32_lo(x.w, h1.y));
         } else {
           const float2 x = *reinterpret_cast<const float2*>(&v[k]);
           const float2 h = make_float2(tf32_hi(x.x), tf32_hi(x.y));
           *reinterpret_cast<float2*>(ah + soff[k]) = h;
-          *reinterpret_cast<float2*>(al + soff[k]) = make_float2(x.x - h.x, x.y - h.y);
+          *reinterpret_cast<float2*>(al + soff[k]) = make_float2(tf32_lo(x.x, h.x), tf32_lo(x.y, h.y));
         }
       }
     };
@@ -694,7 +701,7 @@ k_block_tma(const __grid_constant__ TmaArgs<K> ta, const __grid_constant__ CUten
     const int n = e / W, kk = e % W;
     const float v = a.b[n][kk], h = tf32_hi(v);
     *reinterpret_cast<float*>(sm + L::B_HI + sw128_off(n, kk, W)) = h;
-    *reinterpret_cast<float*>(sm + L::B_LO + sw128_off(n, kk, W)) = v - h;
+    *reinterpret_cast<float*>(sm + L::B_LO + sw128_off(n, kk, W)) = tf32_lo(v, h);
   }
   if (tid < D) s_off[tid] = a.off[tid];
   if (tid < kTcRows) s_P[tid] = row_offset(tid, a);
@@ -768,7 +775,7 @@ k_block_tma(const __grid_constant__ TmaArgs<K> ta, const __grid_constant__ CUten
 #pragma unroll
       for (int e = 0; e < CPW; ++e) {
         const float h = tf32_hi(v[e]);
-        lo[e] = v[e] - h;
+        lo[e] = tf32_lo(v[e], h);
         v[e] = h;
       }
       // the A stage is free once the MMAs that read it two tiles ago have completed
@@ -1176,13 +1183,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const __grid_constant
       const uint32_t o = sw128_off(r, t, kTcRows);
       const float h = tf32_hi(v);
       *reinterpret_cast<float*>(sm + L::HI + o) = h;
-      *reinterpret_cast<float*>(sm + L::LO + o) = v - h;
+      *reinterpret_cast<float*>(sm + L::LO + o) = tf32_lo(v, h);
     };
     auto put2 = [&](int r, int t, float v0, float v1) {  // columns t, t + 1 (t even): one 8-byte store
       const uint32_t o = sw128_off(r, t, kTcRows);
       const float h0 = tf32_hi(v0), h1 = tf32_hi(v1);
       *reinterpret_cast<float2*>(sm + L::HI + o) = make_float2(h0, h1);
-      *reinterpret_cast<float2*>(sm + L::LO + o) = make_float2(v0 - h0, v1 - h1);
+      *reinterpret_cast<float2*>(sm + L::LO + o) = make_float2(tf32_lo(v0, h0), tf32_lo(v1, h1));
     };
     auto put = [&](int r0, uint32_t tmk, const VT& x) {
       const int t = (int)(tmk & 255u), m = (int)(tmk >> 8);
@@ -1492,7 +1499,7 @@ k_gram_tma(const __grid_constant__ CUtensorMap map_psi, const __grid_constant__ 
         unsigned char* ob = oa + (st ? L::OP_BYTES : 0u);
         const float hv = tf32_hi(v[j]);
         *reinterpret_cast<float*>(ob + sw32_off(c, t, kTcRows)) = hv;
-        *reinterpret_cast<float*>(ob + sw32_off(64 + c, t, kTcRows)) = v[j] - hv;
+        *reinterpret_cast<float*>(ob + sw32_off(64 + c, t, kTcRows)) = tf32_lo(v[j], hv);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();

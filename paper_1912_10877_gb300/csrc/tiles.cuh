@@ -5,10 +5,11 @@
 // qubits (its tile bits): the state is cut into 2^(n-m) tiles of 2^m
 // amplitudes that differ only in those bits, each tile is staged in shared
 // memory, and every non-diagonal gate of the pass has its target in B.  A pass
-// is cut into PHASES: a phase owns 4 of the tile's bits (its register bits R);
-// each of the 2^(m-4) threads holds the 16 amplitudes of the tile that differ
-// only in R in registers, applies the phase's gates there, and writes them
-// back.  A thread knows the global index of its amplitudes, so a gate's
+// is cut into PHASES: a phase owns rb of the tile's bits (its register bits R,
+// rb = 2..4, the fusion width: every gate on those qubits in the phase is
+// applied to amplitudes held in registers); each of the 2^(m-rb) threads
+// holds the 2^rb amplitudes of the tile that differ only in R in registers,
+// applies the phase's gates there, and writes them back.  A thread knows the global index of its amplitudes, so a gate's
 // controls outside R become a per-thread predicate, and a diagonal gate whose
 // target is outside R becomes a per-thread factor.  The planner keeps gate
 // order valid by moving a gate earlier only past gates that share no qubit
@@ -19,13 +20,14 @@
 
 namespace qs {
 
-constexpr int kRB = 4;             // register bits per phase (16 amplitudes per thread)
+constexpr int kRB = 4;             // register bits per phase by default (16 amplitudes per thread); the most
+constexpr int kMinRB = 2;          // the fewest
 constexpr int kRowBits = 5;        // tile rows: 32 consecutive amplitudes (register qubits 0..4)
 constexpr int kMaxTileBits = 13;
 constexpr int kTileThreads = 1 << (kMaxTileBits - kRB);  // 512
 
-// one gate inside a phase.  t, cmask and cval are phase-local (bits 0..3 of the
-// register index j); the gate's other controls are register qubits outside the
+// one gate inside a phase.  t, cmask and cval are phase-local (bits 0..rb-1 of
+// the register index j); the gate's other controls are register qubits outside the
 // phase, tested per thread on its global base index: (base & tmask) == tval.
 struct TOp {
   uint8_t kind;   // TK_*
@@ -52,7 +54,7 @@ enum { TK_DENSE = 0, TK_SWAP = 1, TK_DIAG = 2, TK_RX = 3, TK_RY = 4, TK_DIAG16 =
 enum { GEN_NONE = 0, GEN_X = 1, GEN_Y = 2, GEN_Z = 3, GEN_P1 = 4, GEN_I = 5 };
 
 struct TPhase {
-  uint8_t rpos[kRB];        // tile-local positions of the register bits (ascending)
+  uint8_t rpos[kRB];        // tile-local positions of the register bits (ascending; rb used)
   uint8_t tpos[12];         // tile-local positions of the thread bits (ascending)
   uint8_t tq[12];           // register qubits of the thread bits
   uint16_t sroff[1 << kRB]; // swz(register offset of amplitude j): slot = swz(base) ^ sroff[j]
@@ -67,7 +69,7 @@ struct TPass {
 };
 
 struct HostPhase {
-  int rbits[kRB];           // register qubits of the phase (ascending)
+  int rbits[kRB];           // register qubits of the phase (ascending; rb used)
   std::vector<int> gates;   // circuit gate indices in forward order
 };
 
@@ -77,17 +79,17 @@ struct HostPass {
 };
 
 // Greedy commutation-aware scheduling: passes of m qubits (always containing
-// register qubits 0..4, so tile rows are contiguous), phases of exactly kRB of
+// register qubits 0..4, so tile rows are contiguous), phases of exactly rb of
 // the pass's qubits.  Gates must be single-target; a non-diagonal gate's target
 // lies in its phase, its controls and diagonal gates may be anywhere.  Returns
 // QS_OK or QS_EUNSUPPORTED.
-int plan_passes(const qs_circuit* c, int n, int m, int max_phase_ops, std::vector<HostPass>& out);
+int plan_passes(const qs_circuit* c, int n, int m, int max_phase_ops, std::vector<HostPass>& out, int rb = kRB);
 
 // diagonal gates (fit in any phase: they only multiply amplitudes)
 bool gate_is_diagonal(const qs_circuit* c, const qs_gate_desc& g);
 
 // tile-local positions of a phase's register bits and thread bits
-void phase_positions(const HostPass& p, const HostPhase& ph, TPhase* out);
+void phase_positions(const HostPass& p, const HostPhase& ph, TPhase* out, int rb = kRB);
 
 // swizzled shared-memory slot of tile-local amplitude l (spreads the 8-byte
 // accesses of a half-warp over all banks for the phase patterns used here).

@@ -191,6 +191,14 @@ class State:
                                    out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 1 if collapse else 0))
         return out
 
+    def measure_seeded(self, seed: int, nshots: int, collapse=False) -> np.ndarray:
+        """measure with the uniforms drawn on the device from ``seed`` (SplitMix64, see
+        qs_measure_seeded in qsim.h): [nreg][nshots] basis indices fixed by the seed."""
+        out = np.zeros((self.nreg, int(nshots)), dtype=np.int64)
+        N.check(N.lib().qs_measure_seeded(self.handle, ctypes.c_uint64(int(seed) & ((1 << 64) - 1)), int(nshots),
+                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 1 if collapse else 0))
+        return out
+
 
 def _params_array(params, count):
     if count == 0:
@@ -340,9 +348,11 @@ def backward(state: State, circuit: Circuit, params, obs: Observable, ckpt_every
 
 class BatchProgram:
     """Per-register circuits and diagonal observables of a batch of uneven registers,
-    scheduled once into fused tile passes (qs_batch_program)."""
+    scheduled once into fused tile passes (qs_batch_program).  phase_qubits: the fusion
+    width (qubits whose gates a phase applies in registers, 2..4; 0 = 4); precise: the
+    compensated forward and double-float uncompute of qs_batch_program_create_ex."""
 
-    def __init__(self, circuits, observables, tile_qubits: int = 0):
+    def __init__(self, circuits, observables, tile_qubits: int = 0, phase_qubits: int = 0, precise: bool = False):
         L = N.lib()
         nreg = len(circuits)
         if len(observables) != nreg:
@@ -350,10 +360,14 @@ class BatchProgram:
         ch = (ctypes.c_void_p * nreg)(*[c.handle.value for c in circuits])
         oh = (ctypes.c_void_p * nreg)(*[o.handle.value for o in observables])
         h = ctypes.c_void_p()
-        N.check(L.qs_batch_program_create(nreg, ctypes.cast(ch, ctypes.POINTER(ctypes.c_void_p)),
-                                          ctypes.cast(oh, ctypes.POINTER(ctypes.c_void_p)), int(tile_qubits),
-                                          ctypes.byref(h)))
+        N.check(L.qs_batch_program_create_ex(nreg, ctypes.cast(ch, ctypes.POINTER(ctypes.c_void_p)),
+                                             ctypes.cast(oh, ctypes.POINTER(ctypes.c_void_p)), int(tile_qubits),
+                                             int(phase_qubits), N.QS_BATCH_PRECISE if precise else 0,
+                                             ctypes.byref(h)))
         self.handle = h
+        t, ph, fl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        N.check(L.qs_batch_program_shape(h, ctypes.byref(t), ctypes.byref(ph), ctypes.byref(fl)))
+        self.tile_qubits, self.phase_qubits, self.precise = t.value, ph.value, bool(fl.value & N.QS_BATCH_PRECISE)
         self.nreg = nreg
         self.counts = [c.nqubits for c in circuits]
         tot = ctypes.c_int64()
@@ -631,3 +645,30 @@ def batch_autotune(circuits, observables, state: State, params: torch.Tensor, gr
                                 ctypes.c_void_p(g.data_ptr()) if g is not None else None, int(reps),
                                 ctypes.byref(best), ctypes.byref(nc), tiles.ctypes.data_as(N._PI32), N.dptr(ms)))
     return best.value, {int(tiles[i]): float(ms[i]) for i in range(min(nc.value, cap))}
+
+
+def batch_autotune_shape(circuits, observables, state: State, params: torch.Tensor, grad: bool = True,
+                         precise: bool = False, reps: int = 2):
+    """Fusion width (phase qubits) and tile size at which the batched program runs fastest
+    on this state (qs_batch_autotune_ex): (tile, phase_qubits, {(tile, phase): ms}).  The
+    state's amplitudes are overwritten."""
+    L = N.lib()
+    nreg = len(circuits)
+    ch = (ctypes.c_void_p * nreg)(*[c.handle.value for c in circuits])
+    oh = (ctypes.c_void_p * nreg)(*[o.handle.value for o in observables])
+    loss = torch.empty(nreg, dtype=torch.float64, device=params.device)
+    g = torch.empty_like(params) if grad else None
+    bt, bp = ctypes.c_int(0), ctypes.c_int(0)
+    cap = 16
+    nc = ctypes.c_int(cap)
+    tiles = np.zeros(cap, np.int32)
+    phases = np.zeros(cap, np.int32)
+    ms = np.zeros(cap)
+    N.check(L.qs_batch_autotune_ex(nreg, ctypes.cast(ch, ctypes.POINTER(ctypes.c_void_p)),
+                                   ctypes.cast(oh, ctypes.POINTER(ctypes.c_void_p)),
+                                   N.QS_BATCH_PRECISE if precise else 0, state.handle,
+                                   ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(loss.data_ptr()),
+                                   ctypes.c_void_p(g.data_ptr()) if g is not None else None, int(reps),
+                                   ctypes.byref(bt), ctypes.byref(bp), ctypes.byref(nc), tiles.ctypes.data_as(N._PI32),
+                                   phases.ctypes.data_as(N._PI32), N.dptr(ms)))
+    return bt.value, bp.value, {(int(tiles[i]), int(phases[i])): float(ms[i]) for i in range(min(nc.value, cap))}

@@ -39,7 +39,7 @@ def mixed_circuit(n, seed):
     return gates + extra + gates[: 3 * n], params
 
 
-def run_case(qs, specs, tile=0):
+def run_case(qs, specs, tile=0, phase=0, precise=False, gtol=1e-4):
     circs, obs, plist, terms_l, gl = [], [], [], [], []
     for n, gates, params, terms in specs:
         circs.append(qs.Circuit(gates, n, nparams=len(params)))
@@ -47,10 +47,11 @@ def run_case(qs, specs, tile=0):
         plist.append(params)
         terms_l.append(terms)
         gl.append(gates)
-    prog = qs.BatchProgram(circs, obs, tile_qubits=tile)
+    prog = qs.BatchProgram(circs, obs, tile_qubits=tile, phase_qubits=phase, precise=precise)
     st = qs.State([s[0] for s in specs], dtype=torch.complex64)
     p = torch.tensor(np.concatenate(plist), dtype=torch.float64, device="cuda")
     loss, grad = prog.run(st, p, grad=True, reset=True)
+    worst = 0.0
     torch.cuda.synchronize()
     out = st.numpy()
     loss = loss.cpu().numpy()
@@ -62,7 +63,10 @@ def run_case(qs, specs, tile=0):
         rl, rg = oracle.gradient(oracle.zero_state(n), n, gates, params, terms)
         assert abs(loss[r] - rl) < 1e-5, ("loss", r, n, loss[r], rl)
         g = grad[prog.param_offsets[r]:prog.param_offsets[r + 1]]
-        assert np.max(np.abs(g - rg)) / max(1e-12, np.max(np.abs(rg))) < 1e-4, ("grad", r, n)
+        err = float(np.max(np.abs(g - rg)) / max(1e-12, np.max(np.abs(rg))))
+        worst = max(worst, err)
+        assert err < gtol, ("grad", r, n, err)
+    return worst
 
 
 def test_batch_variational_uneven_sizes(qs):
@@ -71,6 +75,25 @@ def test_batch_variational_uneven_sizes(qs):
         gates, params = W.variational(n, 3, "ladder", seed=100 + r)
         specs.append((n, gates, params, W.zz_chain(n)))
     run_case(qs, specs)
+
+
+@pytest.mark.parametrize("phase", [2, 3])
+@pytest.mark.parametrize("precise", [False, True])
+def test_batch_phase_widths_and_precise_path(qs, phase, precise, record_property):
+    # fusion widths 2 and 3 (2^phase amplitudes per thread), with the FP32 path and
+    # the precise path (compensated forward, double-float uncompute); resident and
+    # streamed registers, controlled and diagonal gates of every kind
+    specs = []
+    for r, n in enumerate([5, 12, 7, 13, 9, 14]):
+        gates, params = W.variational(n, 3, "ladder", seed=300 + r)
+        specs.append((n, gates, params, W.zz_chain(n)))
+    for r, n in enumerate([6, 11, 13]):
+        gates, params = mixed_circuit(n, 40 + r)
+        specs.append((n, gates, params, W.zz_chain(n, periodic=True)))
+    worst = run_case(qs, specs, phase=phase, precise=precise, gtol=1e-4)
+    worst9 = run_case(qs, specs[:5], tile=9, phase=phase, precise=precise, gtol=1e-4)
+    record_property("worst_relative_gradient_error", max(worst, worst9))
+    print(f"phase {phase} precise {precise}: worst relative gradient error {worst:.2e} / tile 9 {worst9:.2e}")
 
 
 def test_batch_streamed_tiles_small_tile(qs):
@@ -157,3 +180,38 @@ def test_batch_full_size_sampled(qs, record_property):
         assert err < 1e-4, ("grad", r, n, err)
     record_property("worst_relative_gradient_error", worst)
     print(f"registers {picks}: worst relative gradient error {worst:.2e}")
+
+
+def test_batch_full_size_sampled_precise(qs, record_property):
+    # the benchmarked batch through the precise path (compensated complex64 forward,
+    # double-float uncompute) with the autotuned shape; sampled registers of every
+    # size class against the oracle's gradient
+    counts = W.batch_qubit_counts(1024, 10, 18, seed=0)
+    specs = W.batch_variational(counts, 20, seed=0)
+    circs = [qs.Circuit(g, int(n), nparams=len(p)) for n, (g, p) in zip(counts, specs)]
+    obs = [qs.Observable(W.zz_chain(int(n))) for n in counts]
+    st = qs.State([int(n) for n in counts], dtype=torch.complex64)
+    params = torch.tensor(np.concatenate([p for _, p in specs]), dtype=torch.float64, device="cuda")
+    tile, phase, times = qs.batch_autotune_shape(circs, obs, st, params, grad=True, precise=True, reps=1)
+    assert phase in (2, 3) and times[(tile, phase)] == min(v for v in times.values() if v > 0)
+    prog = qs.BatchProgram(circs, obs, tile_qubits=tile, phase_qubits=phase, precise=True)
+    loss, grad = prog.run(st, params, grad=True, reset=True)
+    torch.cuda.synchronize()
+    loss, grad = loss.cpu().numpy(), grad.cpu().numpy()
+    assert np.all(np.isfinite(loss)) and np.all(np.isfinite(grad))
+    rs = np.random.default_rng(1)
+    picks = sorted({int(np.flatnonzero(np.asarray(counts) == n)[0]) for n in (10, 12, 13, 14, 16, 18)} |
+                   {int(x) for x in rs.choice(len(counts), 4, replace=False)})
+    worst = 0.0
+    for r in picks:
+        n = int(counts[r])
+        gates, p = specs[r]
+        rl, rg = oracle.gradient(oracle.zero_state(n), n, gates, p, W.zz_chain(n))
+        assert abs(loss[r] - rl) < 1e-5, ("loss", r, n)
+        g = grad[prog.param_offsets[r]:prog.param_offsets[r + 1]]
+        err = float(np.max(np.abs(g - rg)) / np.max(np.abs(rg)))
+        worst = max(worst, err)
+        assert err < 1e-4, ("grad", r, n, err)
+    record_property("worst_relative_gradient_error", worst)
+    print(f"precise batch, tile {tile} phase {phase}: registers {picks}: worst relative gradient error {worst:.2e}; "
+          f"shapes {times}")

@@ -188,6 +188,29 @@ def test_sampling_bit_exact(qs, dt, n):
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+def test_seeded_sampling_bit_exact(qs, dt):
+    # the seed alone fixes the indices: device SplitMix64 uniforms against the oracle's
+    counts = [3, 10, 21, 7]
+    st = qs.State(counts, dtype=TDT[dt])
+    st.upload(np.concatenate([W.haar_state(c, seed=c + 60) for c in counts]))
+    nshots = 700
+    for seed in (0, 2 ** 63 + 12345):
+        got = st.measure_seeded(seed, nshots)
+        out = st.numpy()
+        for r, c in enumerate(counts):
+            seg = out[int(st.offsets[r]):int(st.offsets[r + 1])].astype(np.complex128)
+            assert np.array_equal(got[r], oracle.sample_seeded(seg, c, seed, nshots, reg=r)), (dt, seed, r)
+    # collapse from a seed on one register
+    n = 6
+    psi = W.haar_state(n, seed=5)
+    s1 = qs.State(n, dtype=TDT[dt])
+    s1.upload(psi)
+    x = int(s1.measure_seeded(99, 1, collapse=True)[0, 0])
+    stored = psi.astype(np.complex64).astype(np.complex128) if dt == "c64" else psi
+    assert x == int(oracle.sample_seeded(stored, n, 99, 1)[0])
+
+
 def test_measure_listing_and_collapse(qs):
     st = qs.State(4, dtype=torch.complex128)
     st.reset()

@@ -53,6 +53,9 @@ MUTANTS = {
                                 "case ORC_RY: U[1] = I; U[2] = -I; cfac = 0.5; break;"),
     "gradient_uncomputes_lambda_only": ("    orc_apply(psi, n, g->k, g->locs, U, g->nctrl, g->ctrl_locs, g->ctrl_vals);\n    orc_apply(lam,",
                                         "    orc_apply(lam,"),
+    "splitmix_shift": ("z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;", "z = (z ^ (z >> 31)) * 0xBF58476D1CE4E5B9ull;"),
+    "splitmix_counter_off_by_one": ("u[i] = (double)(orc_splitmix64(seed, k0 + (uint64_t)i + 1) >> 11)",
+                                    "u[i] = (double)(orc_splitmix64(seed, k0 + (uint64_t)i) >> 11)"),
     "sample_drops_imag": ("p[i] = r2 + i2;", "p[i] = r2;"),
     "sample_ties_go_left": ("if (nxt > t) { *acc = a; return j; }", "if (nxt >= t) { *acc = a; return j; }"),
     "collapse_not_normalised": ("psi[x] = r > 0 ? a / r : 1.0;", "psi[x] = r > 0 ? a : 1.0;"),

@@ -1,6 +1,7 @@
 """Pins for the FP64 oracle: each test checks it against something other than itself
 (values the paper prints, closed forms, library routines, brute force, invariants)."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -445,3 +446,26 @@ def test_collapse():
     out = oracle.collapse(psi, 4, 9)
     assert abs(abs(out[9]) - 1) < 1e-15 and np.count_nonzero(out) == 1
     assert np.angle(out[9]) == pytest.approx(np.angle(psi[9]))
+
+
+def test_splitmix64_published_outputs_and_uniforms():
+    # the seeded measurement's generator against its published reference outputs
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "splitmix64.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    for seed, k, want in rows:
+        assert oracle.splitmix64(int(seed), int(k)) == int(want, 16), (seed, k)
+    # u = top 53 bits / 2^53: in [0, 1), and draw k of register r is r * nshots + j + 1
+    u = oracle.seeded_uniforms(0, 2, 3)
+    assert u[0, 0] == (0xE220A8397B1DCDAF >> 11) / 2.0 ** 53
+    assert u[0, 2] == (0x06C45D188009454F >> 11) / 2.0 ** 53
+    assert u[1, 0] == (oracle.splitmix64(0, 4) >> 11) / 2.0 ** 53
+    big = oracle.seeded_uniforms(12345, 4, 5000)
+    assert big.min() >= 0.0 and big.max() < 1.0
+    # uniformity: chi-square over 20 bins of 20000 draws (p > 1e-4)
+    h, _ = np.histogram(big, bins=20, range=(0, 1))
+    chi2 = float(np.sum((h - 1000.0) ** 2 / 1000.0))
+    assert chi2 < 56.0, chi2
+    # seeded sampling = sampling with those uniforms
+    n = 5
+    psi = W.haar_state(n, seed=2)
+    assert (oracle.sample_seeded(psi, n, 7, 64, reg=1) == oracle.sample(psi, n, oracle.seeded_uniforms(7, 2, 64)[1])).all()
