@@ -314,10 +314,13 @@ def batch_workload():
 def run_batch_leg(steps: int, warmup: int, compare: bool = True, world: int = 1, rank: int = 0):
     """1024 registers, n ~ U{10..18}, Rz Rx Rz + CNOT ladder x 20 layers each, <sum Z_i Z_{i+1}>:
     forward + reversible gradient of every register in ONE persistent launch (complex64).
-    With N ranks the registers are split by cost (no data-path collective), each rank runs
-    its share, the time is the slowest rank's and the losses are gathered.
-    Comparator: the unfused gate-by-gate complex128 path (one kernel per gate per register,
-    per-gate FP64 adjoint), all 1024 registers, same GPU (single rank only)."""
+    Two paths, each at the program shape (fusion width = register qubits per phase, tile size)
+    the autotuner picks: the FP32 path, and the precise path (compensated complex64 forward,
+    double-float uncompute).  With N ranks the registers are split by cost (no data-path
+    collective), each rank runs its share, the time is the slowest rank's and the losses are
+    gathered.  Comparator (single rank): the unfused gate-by-gate complex128 path (one kernel per
+    gate per register, per-gate FP64 adjoint), all 1024 registers on preallocated states,
+    device-timed; and the same with each register's forward replayed from a CUDA graph."""
     import torch
     from paper_1912_10877_gb300 import qsim
     from paper_1912_10877_gb300 import dist as D
@@ -329,23 +332,6 @@ def run_batch_leg(steps: int, warmup: int, compare: bool = True, world: int = 1,
     obs = [qsim.Observable(W.zz_chain(int(n))) for n in counts]
     st = qsim.State([int(n) for n in counts], dtype=torch.complex64)
     params = torch.tensor(np.concatenate([p for _, p in specs]), dtype=torch.float64, device="cuda")
-    # tile shape chosen by the autotuner (untimed), then the program is built with it
-    tile, tile_ms = qsim.batch_autotune(circs, obs, st, params, grad=True, reps=1)
-    prog = qsim.BatchProgram(circs, obs, tile_qubits=tile)
-    loss = torch.empty(len(mine), dtype=torch.float64, device="cuda")
-    grad = torch.empty(prog.nparams, dtype=torch.float64, device="cuda")
-    for _ in range(warmup):
-        prog.run(st, params, grad=True, loss=loss, grad_out=grad)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        prog.run(st, params, grad=True, loss=loss, grad_out=grad)
-    e1.record()
-    torch.cuda.synchronize()
-    t = D.max_over_ranks(e0.elapsed_time(e1) / 1e3 / steps)
-    losses = D.gather_per_register(loss.cpu().numpy(), mine, BATCH_NREG)
-    assert np.all(np.isfinite(losses)), "a register's loss is missing"
     # ALU roofline: the method's minimal FP32 flops per batch.  Forward per layer and qubit:
     # the fused Rz Rx Rz, one complex 2x2 = 2 complex multiply-adds = 16 flops per amplitude.
     # Backward per layer and qubit, rotation by rotation: uncompute psi and lambda (Rz diagonal
@@ -353,34 +339,98 @@ def run_batch_leg(steps: int, warmup: int, compare: bool = True, world: int = 1,
     # plus Im<lambda|G|psi> (4 per amplitude): 3 x 16 = 48.  CNOTs move amplitudes (0 flops);
     # lambda = O psi and <O> are lower order.  Total 64 flops per amplitude, layer and qubit.
     flops = sum(float(BATCH_DEPTH * int(n) * 64) * (1 << int(n)) for n in counts_all)
-    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # TFLOP/s: SMs x FP32 FMA/clk x 2 x max SM clock
-    res = {"metric": "batched fwd+grad circuits/s", "value": round(BATCH_NREG / t, 1), "unit": "circuits/s",
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # TFLOP/s: SMs x FP32 FMA/clk x 2 flops x max SM clock
+    loss = torch.empty(len(mine), dtype=torch.float64, device="cuda")
+    grad = torch.empty(int(params.numel()), dtype=torch.float64, device="cuda")
+    paths = {}
+    for name, precise in (("fp32", False), ("precise", True)):
+        tile, phase, shapes = qsim.batch_autotune_shape(circs, obs, st, params, grad=True, precise=precise, reps=1)
+        prog = qsim.BatchProgram(circs, obs, tile_qubits=tile, phase_qubits=phase, precise=precise)
+        for _ in range(warmup):
+            prog.run(st, params, grad=True, loss=loss, grad_out=grad)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            prog.run(st, params, grad=True, loss=loss, grad_out=grad)
+        e1.record()
+        torch.cuda.synchronize()
+        t = D.max_over_ranks(e0.elapsed_time(e1) / 1e3 / steps)
+        losses = D.gather_per_register(loss.cpu().numpy(), mine, BATCH_NREG)
+        assert np.all(np.isfinite(losses)), "a register's loss is missing"
+        paths[name] = {"value": round(BATCH_NREG / t, 1), "ms_per_batch": round(1e3 * t, 3),
+                       "tile_qubits": tile, "phase_qubits": phase,
+                       "autotune_ms": {f"{k[0]}q tile/{k[1]}q phase": round(v, 2) for k, v in shapes.items()}}
+        del prog
+    t = paths["fp32"]["ms_per_batch"] / 1e3
+    res = {"metric": "batched fwd+grad circuits/s", "value": paths["fp32"]["value"], "unit": "circuits/s",
            "roofline": {"bound": "alu", "achieved": round(flops / t / 1e12, 2), "peak": round(fp32_peak, 1),
                         "unit": "TFLOP/s", "frac": round(flops / t / 1e12 / fp32_peak, 4),
                         "peak_kind": "derived: 152 SMs x 128 FP32 FMA/clk x 2 flops x 2.07 GHz",
                         "flops_per_batch": flops},
-           "ms_per_batch": round(1e3 * t, 3), "dtype": "c64 (f32 gates and uncompute; f64 reductions above warp level)",
+           "ms_per_batch": paths["fp32"]["ms_per_batch"],
+           "dtype": "c64 (f32 gates and uncompute; f64 reductions above warp level)",
+           "precise": dict(paths["precise"], dtype="c64 forward with compensated matrices (f32), double-float "
+                                                    "uncompute, f64 reductions"),
+           "fusion": {k: {"tile_qubits": v["tile_qubits"], "phase_qubits": v["phase_qubits"]} for k, v in paths.items()},
+           "autotune_ms": {k: v["autotune_ms"] for k, v in paths.items()},
            "config": {"workload": f"{BATCH_NREG} registers, n ~ U{{{BATCH_LO}..{BATCH_HI}}} seed 0, Rz.Rx.Rz + "
                                   f"CNOT ladder x {BATCH_DEPTH} layers, <sum Z_i Z_i+1> (open)",
                       "total_amplitudes": int(sum(1 << int(n) for n in counts_all)), "launches_per_batch": 2,
-                      "ranks": world, "split": "registers by cost 2^n (LPT), losses gathered",
-                      "tile_qubits": tile, "autotune_ms": {str(k): round(v, 2) for k, v in tile_ms.items()}}}
+                      "ranks": world, "split": "registers by cost 2^n (LPT), losses gathered"}}
     if compare and world == 1:
-        # gate-by-gate complex128: one launch per gate per register, FP64 adjoint per gate
-        rs = np.random.default_rng(0)
-        t0 = time.perf_counter()
-        for r, (n, (g, p)) in enumerate(zip(counts, specs)):
-            s128 = qsim.State(int(n), dtype=torch.complex128)
-            s128.reset()
-            s128.apply_circuit(circs[r], p, fused=False)
-            qsim.backward(s128, circs[r], p, obs[r])
-        torch.cuda.synchronize()
-        tg = time.perf_counter() - t0
-        res["gate_by_gate_c128"] = {"value": round(BATCH_NREG / tg, 2), "unit": "circuits/s",
-                                    "seconds": round(tg, 3), "registers": BATCH_NREG}
-        res["vs_gate_by_gate_c128"] = round(tg / t, 1)
-        del rs
+        res["gate_by_gate_c128"] = run_c128_comparator(counts, specs, circs, obs)
+        for k in ("fp32", "precise"):
+            res[f"vs_gate_by_gate_c128_{k}"] = round(paths[k]["value"] / res["gate_by_gate_c128"]["value"], 1)
     return res
+
+
+def run_c128_comparator(counts, specs, circs, obs):
+    """The plain complex128 path on the batched workload: per register, one kernel per gate
+    (unfused) forward from |0..0> and the per-gate FP64 reversible adjoint, on states
+    allocated before the timed region; CUDA events around all 1024 registers (host launch
+    overhead included, as it is part of that path).  Variant: each register's forward
+    captured once as a CUDA graph and replayed."""
+    import torch
+    from paper_1912_10877_gb300 import qsim
+    states = [qsim.State(int(n), dtype=torch.complex128) for n in counts]
+    works = {int(n): qsim.backward_work(int(n)) for n in set(int(n) for n in counts)}
+    params = [p for _, p in specs]
+
+    def direct():
+        for r in range(len(counts)):
+            states[r].reset()
+            states[r].apply_circuit(circs[r], params[r], fused=False)
+            qsim.backward(states[r], circs[r], params[r], obs[r], work=works[int(counts[r])])
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    direct()
+    t_direct = timed(direct)
+    graphs = []
+    for r in range(len(counts)):
+        states[r].reset()
+        graphs.append(qsim.CapturedCircuit(states[r], circs[r], params[r], fused=False))
+
+    def captured():
+        for r in range(len(counts)):
+            states[r].reset()
+            graphs[r].replay()
+            qsim.backward(states[r], circs[r], params[r], obs[r], work=works[int(counts[r])])
+
+    captured()
+    t_graph = timed(captured)
+    best = min(t_direct, t_graph)
+    return {"value": round(len(counts) / best, 2), "unit": "circuits/s", "seconds": round(best, 3),
+            "seconds_direct": round(t_direct, 3), "seconds_forward_graphs": round(t_graph, 3),
+            "registers": len(counts), "timing": "CUDA events, states and work buffers preallocated"}
 
 
 # ------------------------------------------------------------------ differentiation and large registers
@@ -421,8 +471,27 @@ def run_diff_leg(steps: int, warmup: int):
             fn()
         torch.cuda.synchronize()
         out[name] = round((time.perf_counter() - t0) / steps, 4)
+    # the backward alone (its FP64 uncompute is the bound): forward once, then time qs_backward
+    st.reset()
+    qsim.apply_circuit_ckpt(st, circ, params, every, ck)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    qsim.backward(st, circ, params, obs, every, ck, work)
+    tb = time.perf_counter() - t0
+    # FP64 roofline of the backward: per rotation and amplitude pair, uncompute psi and lambda
+    # (Rz^dag: two complex-by-phase products, 6 flops each, per state; Rx^dag: c a + i s b, 6 flops
+    # per amplitude, per state) and Im<lambda|G|psi> (8 flops per pair): 32 FP64 flops per pair,
+    # 16 per amplitude; CNOTs move amplitudes (0 flops)
+    fp64_flops = 6000 * 16.0 * (1 << n)
+    fp64_peak = 1.25  # TFLOP/s, nominal FP64 of GB300
     return {"metric": "fwd+grad seconds (n=20, 8000 gates, 6000 angles)", "unit": "s",
             "value": out["fp64_uncompute_ckpt10"], "tiled_fp32_value": out["tiled_fp32"],
+            "backward_s": round(tb, 4),
+            "roofline": {"bound": "alu", "kernel": "FP64 reversible uncompute (k_adjoint_param1 / k_adjoint_param)",
+                         "achieved": round(fp64_flops / tb / 1e12, 3), "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": round(fp64_flops / tb / 1e12 / fp64_peak, 4), "flops": fp64_flops,
+                         "peak_kind": "nominal FP64 rate of GB300 (1.25 TFLOP/s)"},
+            "forward": "complex64, 1-qubit gates with compensated matrices rounded once (checkpointed path)",
             "passes": qsim.schedule_info(circ)[0], "higher_is_better": False,
             "config": {"workload": "n=20, 100 x (Rz Rx Rz per qubit + CNOT ring), <sum ZZ + sum X>, seed 0",
                        "checkpoints": f"every {every} gates (10 layers)"}}
@@ -494,9 +563,33 @@ def run_large_leg(steps: int, warmup: int):
                                  "gbs": round(nblocks * 6 * S / tgb / 1e9, 1)},
             "gradient_used": "blocks5" if tgb < tgt else "tiles",
             "gates": {"qft": len(W.qft(n, swaps=True)), "brickwork": len(bgates)},
+            "roofline": {"bound": "hbm", "kernel": "whole workload (QFT passes, 5-qubit block passes, block gradient)",
+                         "achieved": round(large_bytes(qp, nblocks, S, tbb < tbt, bp, tgb < tgt) / (tf + tg) / 1e9, 1),
+                         "peak": hbm_peak_of(), "unit": "GB/s",
+                         "frac": round(large_bytes(qp, nblocks, S, tbb < tbt, bp, tgb < tgt) / (tf + tg) / 1e9
+                                       / hbm_peak_of(), 4),
+                         "bytes": large_bytes(qp, nblocks, S, tbb < tbt, bp, tgb < tgt),
+                         "model": "QFT passes x 2S + forward block (or tile) passes x 2S + gradient blocks x 6S "
+                                  "(Gram reads psi and lambda, the adjoint reads and writes both; tile-pass "
+                                  "gradient: 4S per pass); S = 32 GiB"},
             "higher_is_better": False,
             "config": {"workload": "n=32 c64, QFT+swaps on basis state (seed 0), brickwork depth 20 (seed 0), "
                                    "grad of <Z_1> wrt 640 angles", "state_gib": 32}}
+
+
+def hbm_peak_of() -> float:
+    return peaks()[0]
+
+
+def large_bytes(qft_passes: int, nblocks: int, S: int, blocks_forward: bool, tile_passes: int,
+                blocks_gradient: bool = True) -> float:
+    """Algorithmic HBM bytes of the large workload as run: every pass over the 32 GiB state
+    reads and writes it once (2S); a block of the gradient reads psi and lambda for its Gram
+    and reads and writes both in its adjoint (6S); a tile pass of the gradient reads and
+    writes psi and lambda (4S)."""
+    fwd = (nblocks if blocks_forward else tile_passes) * 2 * S
+    grad = nblocks * 6 * S if blocks_gradient else tile_passes * 4 * S
+    return float(qft_passes * 2 * S + fwd + grad)
 
 
 def run_small_leg(reps: int = 50):
@@ -708,6 +801,94 @@ def oracle_baseline(budget_s: float = 15.0):
                       f"the oracle computes in FP64, bytes are counted as for the complex64 state of the metric"}, dt
 
 
+def oracle_configs_baseline(budget_s: float = 10.0):
+    """The FP64 oracle, as it stands, on the host cores for the other workloads (bounded
+    samples, each stated): the small circuit in full; the batch on a 32-register subset
+    scaled to 1024 (extrapolated); the differentiation workload's forward + adjoint
+    gradient over its first layers, scaled to the 100 layers (extrapolated)."""
+    import oracle
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    out = {}
+    # small: n = 12, complex128, 10 layers, <sum ZZ>
+    gates, params = W.variational(12, 10, "ladder", seed=0)
+    t0 = time.perf_counter()
+    reps = 0
+    while reps < 1 or time.perf_counter() - t0 < 1.0:
+        oracle.expect(oracle.apply_circuit(oracle.zero_state(12), 12, gates, params), 12, W.zz_chain(12))
+        reps += 1
+    dt = (time.perf_counter() - t0) / reps
+    out["small"] = {"value": round(dt * 1e6, 1), "unit": "us per circuit", "cores": cores, "kind": "oracle",
+                    "sample": f"the full n=12 circuit and <sum ZZ>, {reps} runs"}
+    # batch: registers spread over the size range, forward + gradient each
+    counts, specs = batch_workload()
+    order = np.argsort(counts, kind="stable")
+    spread = [int(order[i]) for i in np.linspace(0, len(order) - 1, 32).astype(int)]
+    pick = [spread[(i // 2) if i % 2 == 0 else (31 - i // 2)] for i in range(32)]  # small and large alternate
+    t0 = time.perf_counter()
+    done = 0
+    for r in pick:
+        n = int(counts[r])
+        g, p = specs[r]
+        oracle.gradient(oracle.zero_state(n), n, g, p, W.zz_chain(n))
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    # scale by cost 2^n of the registers done against the whole batch
+    cost_done = sum(2.0 ** int(counts[r]) for r in pick[:done])
+    cost_all = float(sum(2.0 ** int(n) for n in counts))
+    t_all = dt * cost_all / cost_done
+    out["batched"] = {"value": round(BATCH_NREG / t_all, 3), "unit": "circuits/s", "cores": cores, "kind": "oracle",
+                      "sample": f"forward + adjoint gradient of {done} registers spread over n=10..18 in {dt:.1f} s, "
+                                f"scaled by their share of the batch's cost sum 2^n (extrapolated)"}
+    # differentiation: n = 20, first layers of the 100-layer circuit, scaled
+    n, layers = 20, 2
+    gates, params = W.variational(n, layers, "ring", seed=0)
+    t0 = time.perf_counter()
+    oracle.gradient(oracle.zero_state(n), n, gates, params, W.tfim(n))
+    dt = time.perf_counter() - t0
+    out["differentiation"] = {"value": round(dt * 100 / layers, 2), "unit": "s", "cores": cores, "kind": "oracle",
+                              "sample": f"forward + adjoint gradient of the first {layers} of 100 layers at n=20 in "
+                                        f"{dt:.1f} s, scaled x{100 // layers} (extrapolated)"}
+    return out
+
+
+def summary_of(line: dict) -> dict:
+    """The headline figures of every leg in one short object (printed last in the line)."""
+    def g(d, *ks):
+        for k in ks:
+            d = d.get(k) if isinstance(d, dict) else None
+        return d
+
+    out = {"headline_gbs": line.get("value"), "headline_frac": g(line, "roofline", "frac"),
+           "headline_traffic": g(line, "roofline", "traffic"), "e2e_gbs": g(line, "e2e", "value")}
+    b = line.get("batched")
+    if isinstance(b, dict):
+        out["batched_circuits_s"] = b.get("value")
+        out["batched_frac"] = g(b, "roofline", "frac")
+        out["batched_shape"] = g(b, "fusion", "fp32")
+        out["batched_precise_circuits_s"] = g(b, "precise", "value")
+        out["batched_precise_shape"] = g(b, "fusion", "precise")
+        out["gate_by_gate_c128_circuits_s"] = g(b, "gate_by_gate_c128", "value")
+        out["batched_vs_c128"] = b.get("vs_gate_by_gate_c128_fp32")
+        out["batched_precise_vs_c128"] = b.get("vs_gate_by_gate_c128_precise")
+    d = line.get("differentiation")
+    if isinstance(d, dict):
+        out["differentiation_s"] = d.get("value")
+        out["differentiation_fp64_frac"] = g(d, "roofline", "frac")
+    L = line.get("large")
+    if isinstance(L, dict):
+        out["large_s"] = L.get("value")
+        out["large_hbm_frac"] = g(L, "roofline", "frac")
+    sm = line.get("small")
+    if isinstance(sm, dict):
+        out["small_us"] = sm.get("value")
+    cb = line.get("cpu_baseline_configs")
+    if isinstance(cb, dict):
+        out["oracle"] = {k: v.get("value") for k, v in cb.items()}
+    return out
+
+
 # ------------------------------------------------------------------ main
 
 def dist_setup(args):
@@ -858,6 +1039,8 @@ def main():
     if rank == 0 and not args.no_baseline and world == 1:
         cb, _ = oracle_baseline(budget_s=15.0)
         line["cpu_baseline"] = cb
+        line["cpu_baseline_configs"] = oracle_configs_baseline()
+    line["summary"] = summary_of(line)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

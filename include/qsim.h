@@ -328,11 +328,18 @@ int qs_circuit_tile_order(const qs_circuit* c, int tile_qubits, int* ngates, int
  * (QS_APPLY_BLOCK_QUBITS(k), 1..5, default 5; targets and controls both
  * count) and applies each block as one k-qubit instruction with the product
  * matrix of its gates; dense 4- and 5-qubit blocks of complex64 states may run
- * on the tensor cores (QS_OPT_TENSOR_CORES).  Gates wider than k stay single. */
+ * on the tensor cores (QS_OPT_TENSOR_CORES).  Gates wider than k stay single.
+ * QS_APPLY_PRECISE (complex64, the per-gate path only): every 1-qubit gate
+ * (fused runs included, controls allowed) is applied with its FP64 matrix
+ * held as FP32 hi + lo and each output amplitude summed in double-float and
+ * rounded to FP32 once, so the only error left is the storage rounding of the
+ * amplitudes (the plain path also rounds the matrix, an error coherent over
+ * the whole state); multi-qubit gates are applied as usual. */
 #define QS_APPLY_PER_REGISTER 1
 #define QS_APPLY_UNFUSED 2
 #define QS_APPLY_TILES 4
 #define QS_APPLY_BLOCKS 8
+#define QS_APPLY_PRECISE 32
 #define QS_APPLY_TILE_QUBITS(m) ((m) << 8)
 #define QS_APPLY_BLOCK_QUBITS(k) ((k) << 16)
 int qs_apply_circuit(qs_state* s, const qs_circuit* c, const double* host_params, int flags);
@@ -358,7 +365,8 @@ int qs_circuit_blocks(const qs_circuit* c, const double* host_params, int kmax, 
 int qs_autotune_circuit(qs_state* s, const qs_circuit* c, const double* host_params, int reps,
                         int* best_flags, int* ncand, int32_t* host_cand_flags, double* host_cand_ms);
 
-/* As qs_apply_circuit on a single register, also saving forward checkpoints:
+/* As qs_apply_circuit on a single register (per gate, complex64 1-qubit gates
+ * compensated as with QS_APPLY_PRECISE), also saving forward checkpoints:
  * after gate index g (0-based) with (g + 1) % ckpt_every == 0 and g + 1 <
  * ngates, the state is copied to slot (g + 1) / ckpt_every - 1 of dev_ckpts,
  * which must hold qs_checkpoint_count() states of the state's dtype. */
@@ -472,8 +480,9 @@ int qs_batch_program_create(int nreg, const qs_circuit* const* circuits,
  * flags QS_BATCH_PRECISE (phase_qubits 2 or 3): the forward pass stays in
  * complex64 with FP32 arithmetic, but every gate matrix is applied with its
  * FP32 rounding error compensated (U = U_hi + U_lo, both FP32, U_lo = the
- * FP64 matrix minus U_hi, the U_lo terms added first; this removes the
- * coherent error of rounding the same matrix for every amplitude); the
+ * FP64 matrix minus U_hi) and each output amplitude is summed in
+ * double-float and rounded to FP32 once (this removes the coherent error of
+ * rounding the same matrix for every amplitude); the
  * reversible uncompute of psi and lambda (Sec. "Reverse Mode", Eq. apply-back)
  * runs in double-float arithmetic (each real a pair hi + lo of FP32 values,
  * about 48 significant bits: FP64-class accuracy on the FP32 units; psi and

@@ -17,6 +17,7 @@ QS_MAXK = 5
 QS_BATCH_RESET, QS_BATCH_GRAD = 1, 2
 QS_BATCH_PRECISE = 1
 QS_APPLY_PER_REGISTER, QS_APPLY_UNFUSED, QS_APPLY_TILES, QS_APPLY_BLOCKS = 1, 2, 4, 8
+QS_APPLY_PRECISE = 32
 QS_OPT_TENSOR_CORES = 1
 
 GATE_KIND = {"I": 0, "X": 1, "Y": 2, "Z": 3, "H": 4, "S": 5, "SDG": 6, "T": 7, "TDG": 8,

@@ -110,6 +110,7 @@ struct Fuser {
   qs_state* s;
   std::vector<std::vector<cd>> pend;
   std::vector<bool> has;
+  bool precise = false;
   explicit Fuser(qs_state* st, int n) : s(st), pend(n), has(n, false) {}
   int flush(int q) {
     if (!has[q]) return QS_OK;
@@ -117,6 +118,7 @@ struct Fuser {
     Plan p;
     int loc = q;
     QS_TRY(plan_gate(pend[q].data(), 1, &loc, 0, 0, &p));
+    p.precise = precise;
     return launch_plan(s, p);
   }
   int flush_mask(uint64_t m) {
@@ -146,6 +148,9 @@ static int apply_circuit_impl(qs_state* s, const qs_circuit* c, const double* pa
   const int ng = (int)c->gates.size();
   const bool per_register = (flags & QS_APPLY_PER_REGISTER) != 0;
   const bool unfused = (flags & QS_APPLY_UNFUSED) != 0 || ckpt_every > 0;
+  // compensated 1-qubit gates on complex64: asked for, or the checkpointed forward
+  // that feeds the FP64 reversible backward
+  const bool precise = ((flags & QS_APPLY_PRECISE) != 0 || ckpt_every > 0) && s->dtype == QS_C64;
   std::vector<cd> U;
   if (per_register && s->nreg > 1) {
     if (!s->uniform) return fail(QS_EUNSUPPORTED, "per-register parameters on an uneven batch");
@@ -169,7 +174,10 @@ static int apply_circuit_impl(qs_state* s, const qs_circuit* c, const double* pa
   const int tile = (flags >> 8) & 0xff;
   const bool force_tiles = (flags & QS_APPLY_TILES) != 0;
   if (force_tiles && (flags & QS_APPLY_BLOCKS)) return fail(QS_EINVAL, "QS_APPLY_TILES and QS_APPLY_BLOCKS together");
-  if (!unfused && !(flags & QS_APPLY_BLOCKS) && s->dtype == QS_C64 && s->uniform && s->nq[0] == c->nqubits) {
+  if ((flags & QS_APPLY_PRECISE) && (force_tiles || (flags & QS_APPLY_BLOCKS)))
+    return fail(QS_EINVAL, "QS_APPLY_PRECISE runs the per-gate path (not with QS_APPLY_TILES or QS_APPLY_BLOCKS)");
+  if (!unfused && !precise && !(flags & QS_APPLY_BLOCKS) && s->dtype == QS_C64 && s->uniform &&
+      s->nq[0] == c->nqubits) {
     const int m = std::min(s->nq[0], tile > 0 ? tile : 13);
     const uint64_t tiles = (uint64_t)s->nreg << (s->nq[0] - m);
     if (force_tiles || tiles >= 256) {
@@ -184,6 +192,7 @@ static int apply_circuit_impl(qs_state* s, const qs_circuit* c, const double* pa
     return apply_blocks(s, c, params, kb > 0 ? kb : QS_MAXK);
   }
   Fuser fz(s, c->nqubits);
+  fz.precise = precise;
   const size_t ab = amp_bytes(s->dtype);
   for (int k = 0; k < ng; ++k) {
     const qs_gate_desc& g = c->gates[k];
@@ -196,6 +205,7 @@ static int apply_circuit_impl(qs_state* s, const qs_circuit* c, const double* pa
       QS_TRY(fz.flush_mask(locmask | g.ctrl_mask));
       Plan p;
       QS_TRY(plan_gate(U.data(), g.nlocs, g.locs, g.ctrl_mask, g.ctrl_vals, &p));
+      p.precise = precise;
       QS_TRY(launch_plan(s, p));
     }
     if (ckpt_every > 0 && (k + 1) % ckpt_every == 0 && k + 1 < ng) {

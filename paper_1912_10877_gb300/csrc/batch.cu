@@ -131,18 +131,18 @@ __device__ __forceinline__ void pair_apply(float2& a, float2& b, float2 u0, floa
   }
 }
 
-// compensated forward pair: (a, b) <- (U_hi + U_lo)(a, b) in FP32, the small
-// U_lo terms first so that every large product enters through one FMA
+// compensated forward (cf_mul / cf_dot2: the FP64-exact matrix applied to the
+// FP32 amplitudes in double-float, each output rounded to FP32 once)
 template <int KIND>
 __device__ __forceinline__ void pair_apply_c(float2& a, float2& b, const float2 (&u)[4], const float2 (&w)[4]) {
   if (KIND == TK_SWAP) {
     const float2 t = a; a = b; b = t;
   } else if (KIND == TK_DIAG) {
-    a = cmaf(u[0], a, cmulf(w[0], a));
-    b = cmaf(u[3], b, cmulf(w[3], b));
+    a = cf_mul(a, u[0], w[0]);
+    b = cf_mul(b, u[3], w[3]);
   } else {
-    const float2 na = cmaf(u[1], b, cmaf(u[0], a, cmaf(w[1], b, cmulf(w[0], a))));
-    const float2 nb = cmaf(u[3], b, cmaf(u[2], a, cmaf(w[3], b, cmulf(w[2], a))));
+    const float2 na = cf_dot2(a, u[0], w[0], b, u[1], w[1]);
+    const float2 nb = cf_dot2(a, u[2], w[2], b, u[3], w[3]);
     a = na; b = nb;
   }
 }
@@ -273,11 +273,6 @@ struct ffc {         // complex double-float: (h.x + l.x) + i (h.y + l.y)
   float2 h, l;
 };
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
 
 struct DWAcc {       // running sum s + e of double-float products
   float s, e;
@@ -611,7 +606,7 @@ __device__ __noinline__ void run_phase_fwd(float2* sm, const TPhase* php, const 
           const float2 fl = flo[4 * oi + (b1 ? 3 : 0)];
 #pragma unroll
           for (int j = 0; j < A; ++j)
-            if ((j & cur.cmask) == cur.cval) x[j] = cmaf(f, x[j], cmulf(fl, x[j]));
+            if ((j & cur.cmask) == cur.cval) x[j] = cf_mul(x[j], f, fl);
         } else if (cur.cmask == 0) {
           pend = cmulf(pend, f);
           has_pend = true;
@@ -623,7 +618,7 @@ __device__ __noinline__ void run_phase_fwd(float2* sm, const TPhase* php, const 
         if (COMP) {
           const float2* tl = dtlo + 16 * cur.param;
 #pragma unroll
-          for (int j = 0; j < A; ++j) x[j] = cmaf(t[j], x[j], cmulf(tl[j], x[j]));
+          for (int j = 0; j < A; ++j) x[j] = cf_mul(x[j], t[j], tl[j]);
         } else {
 #pragma unroll
           for (int j = 0; j < A; ++j) x[j] = cmulf(x[j], t[j]);

@@ -106,6 +106,53 @@ template <typename T> __device__ __forceinline__ T cmul(T a, T b) {
 }
 
 // two consecutive amplitudes (bit 0 = 0, 1) as one vector access
+// ------------------------------------------------------------------ compensated complex64 arithmetic
+//
+// Knuth's TwoSum (s + e = a + b exactly) and the FMA form of the exact product
+// error let a complex64 gate use its FP64 matrix to full accuracy: the matrix
+// is held as U_hi + U_lo (both FP32), every output component is summed in
+// double-float and rounded to FP32 once.  The _rn intrinsics are never fused
+// into FMAs, which the error-free steps rely on.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void cf_first(float& s, float& e, float x, float uh, float ul) {
+  s = __fmul_rn(x, uh);
+  e = fmaf(x, ul, fmaf(x, uh, -s));
+}
+__device__ __forceinline__ void cf_add(float& s, float& e, float x, float uh, float ul) {
+  const float p = __fmul_rn(x, uh);
+  const float pe = fmaf(x, ul, fmaf(x, uh, -p));
+  float t, r;
+  two_sum(s, p, t, r);
+  s = t;
+  e = __fadd_rn(e, __fadd_rn(r, pe));
+}
+// x * u (complex), rounded once
+__device__ __forceinline__ float2 cf_mul(float2 x, float2 uh, float2 ul) {
+  float rs, re, is, ie;
+  cf_first(rs, re, x.x, uh.x, ul.x);
+  cf_add(rs, re, -x.y, uh.y, ul.y);
+  cf_first(is, ie, x.x, uh.y, ul.y);
+  cf_add(is, ie, x.y, uh.x, ul.x);
+  return make_float2(__fadd_rn(rs, re), __fadd_rn(is, ie));
+}
+// u0 * a + u1 * b (complex), rounded once
+__device__ __forceinline__ float2 cf_dot2(float2 a, float2 u0h, float2 u0l, float2 b, float2 u1h, float2 u1l) {
+  float rs, re, is, ie;
+  cf_first(rs, re, a.x, u0h.x, u0l.x);
+  cf_add(rs, re, -a.y, u0h.y, u0l.y);
+  cf_add(rs, re, b.x, u1h.x, u1l.x);
+  cf_add(rs, re, -b.y, u1h.y, u1l.y);
+  cf_first(is, ie, a.x, u0h.y, u0l.y);
+  cf_add(is, ie, a.y, u0h.x, u0l.x);
+  cf_add(is, ie, b.x, u1h.y, u1l.y);
+  cf_add(is, ie, b.y, u1h.x, u1l.x);
+  return make_float2(__fadd_rn(rs, re), __fadd_rn(is, ie));
+}
+
 __device__ __forceinline__ void ld_pair(const float2* p, float2& a0, float2& a1) {
   const float4 v = *reinterpret_cast<const float4*>(p);
   a0 = make_float2(v.x, v.y);
@@ -195,6 +242,7 @@ struct Plan {
   uint64_t mask = 0, vals = 0;      // fixed subspace for DIAG1
   cd d0 = 1, d1 = 1;
   cd u[4];
+  bool precise = false;             // complex64 1-qubit forms: compensated matrix, outputs rounded once
   // k-qubit forms (row-major 2^k x 2^k; perm / diag tables)
   std::vector<cd> U;
   int perm[1 << QS_MAXK];

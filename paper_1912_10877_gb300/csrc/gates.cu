@@ -149,6 +149,76 @@ k_gate1(c2_t<R>* __restrict__ psi, uint64_t nitems, IdxSpec s, int t, U4<R> u, i
   }
 }
 
+// complex64 1-qubit gate with its FP64 matrix held as hi + lo and every output
+// rounded once (Plan::precise): the same item layout as k_gate1
+template <bool T0>
+__global__ void __launch_bounds__(kThreads)
+k_gate1_prec(float2* __restrict__ psi, uint64_t nitems, IdxSpec s, int t, U4<float> uh, U4<float> ul, int lane_sel) {
+  const uint64_t first = (uint64_t)blockIdx.x * (blockDim.x * kIPT) + threadIdx.x;
+  uint64_t idx[kIPT];
+  float2 a0[kIPT], a1[kIPT], b0[kIPT], b1[kIPT];
+  const uint64_t stride = 1ull << t;
+#pragma unroll
+  for (int v = 0; v < kIPT; ++v) {
+    const uint64_t it = first + (uint64_t)v * blockDim.x;
+    idx[v] = it < nitems ? item_index(it, s) : ~0ull;
+    if (idx[v] == ~0ull) continue;
+    ld_pair(psi + idx[v], a0[v], a1[v]);
+    if (!T0) ld_pair(psi + idx[v] + stride, b0[v], b1[v]);
+  }
+  auto op = [&](float2& a, float2& b) {
+    const float2 na = cf_dot2(a, uh.m[0], ul.m[0], b, uh.m[1], ul.m[1]);
+    const float2 nb = cf_dot2(a, uh.m[2], ul.m[2], b, uh.m[3], ul.m[3]);
+    a = na;
+    b = nb;
+  };
+#pragma unroll
+  for (int v = 0; v < kIPT; ++v) {
+    if (idx[v] == ~0ull) continue;
+    if (T0) {
+      op(a0[v], a1[v]);
+      st_pair(psi + idx[v], a0[v], a1[v]);
+    } else {
+      float2 x0 = a0[v], y0 = b0[v], x1 = a1[v], y1 = b1[v];
+      op(x0, y0);
+      op(x1, y1);
+      if (lane_sel == 1) { x0 = a0[v]; y0 = b0[v]; }
+      if (lane_sel == 0) { x1 = a1[v]; y1 = b1[v]; }
+      st_pair(psi + idx[v], x0, x1);
+      st_pair(psi + idx[v] + stride, y0, y1);
+    }
+  }
+}
+
+// the diagonal form of the same (touched subspace only, as k_diag1)
+__global__ void __launch_bounds__(kThreads)
+k_diag1_prec(float2* __restrict__ psi, uint64_t nitems, IdxSpec s, int t, float2 d0h, float2 d0l, float2 d1h,
+             float2 d1l, int lane_sel) {
+  const uint64_t first = (uint64_t)blockIdx.x * (blockDim.x * kIPT) + threadIdx.x;
+  uint64_t idx[kIPT];
+  float2 a0[kIPT], a1[kIPT];
+#pragma unroll
+  for (int u = 0; u < kIPT; ++u) {
+    const uint64_t it = first + (uint64_t)u * blockDim.x;
+    idx[u] = it < nitems ? item_index(it, s) : ~0ull;
+    if (idx[u] == ~0ull) continue;
+    if (lane_sel < 0) ld_pair(psi + idx[u], a0[u], a1[u]);
+    else a0[u] = psi[idx[u] + lane_sel];
+  }
+#pragma unroll
+  for (int u = 0; u < kIPT; ++u) {
+    if (idx[u] == ~0ull) continue;
+    if (lane_sel < 0) {
+      const bool s0 = t >= 0 && ((idx[u] >> t) & 1ull), s1 = t >= 0 && (((idx[u] + 1) >> t) & 1ull);
+      st_pair(psi + idx[u], cf_mul(a0[u], s0 ? d1h : d0h, s0 ? d1l : d0l), cf_mul(a1[u], s1 ? d1h : d0h, s1 ? d1l : d0l));
+    } else {
+      const uint64_t i = idx[u] + lane_sel;
+      const bool s1 = t >= 0 && ((i >> t) & 1ull);
+      psi[i] = cf_mul(a0[u], s1 ? d1h : d0h, s1 ? d1l : d0l);
+    }
+  }
+}
+
 template <typename R, int K>
 struct MatK {
   c2_t<R> m[1 << (2 * K)];  // DENSEK: row-major; DIAGK / PERMK: first 2^K entries
@@ -243,6 +313,51 @@ template <typename R> static c2_t<R> to_dev(cd z) {
   r.x = (R)z.real();
   r.y = (R)z.imag();
   return r;
+}
+// FP32 correction z - to_dev<float>(z)
+static float2 lo_dev(cd z) {
+  const float2 h = to_dev<float>(z);
+  return make_float2((float)(z.real() - (double)h.x), (float)(z.imag() - (double)h.y));
+}
+
+// the compensated complex64 launches of Plan::precise (1-qubit dense,
+// permutation and diagonal forms; SWAP1 is exact as it is)
+static int launch_prec(float2* psi, int n, int nreg, const Plan& p, cudaStream_t st) {
+  if (p.op == OP_DIAG1) {
+    IdxSpec s;
+    QS_TRY(make_idx(n, 1ull | p.mask, p.vals & ~1ull, &s));
+    const uint64_t items = (uint64_t)nreg << s.item_log2;
+    if (!items) return QS_OK;
+    const int lane = (p.mask & 1ull) ? (int)(p.vals & 1ull) : -1;
+    const int nt = cta_threads(items, kIPT);
+    k_diag1_prec<<<blocks_for(items, nt * kIPT), nt, 0, st>>>(psi, items, s, p.t, to_dev<float>(p.d0), lo_dev(p.d0),
+                                                               to_dev<float>(p.d1), lo_dev(p.d1), lane);
+    QS_LAUNCHED();
+    return QS_OK;
+  }
+  U4<float> uh, ul;
+  for (int i = 0; i < 4; ++i) {
+    uh.m[i] = to_dev<float>(p.u[i]);
+    ul.m[i] = lo_dev(p.u[i]);
+  }
+  const int t = p.t;
+  IdxSpec s;
+  if (t == 0) {
+    QS_TRY(make_idx(n, 1ull | p.ctrl_mask, p.ctrl_vals, &s));
+    const uint64_t items = (uint64_t)nreg << s.item_log2;
+    if (!items) return QS_OK;
+    const int nt = cta_threads(items, kIPT);
+    k_gate1_prec<true><<<blocks_for(items, nt * kIPT), nt, 0, st>>>(psi, items, s, 0, uh, ul, -1);
+  } else {
+    QS_TRY(make_idx(n, 1ull | (1ull << t) | p.ctrl_mask, p.ctrl_vals & ~1ull, &s));
+    const uint64_t items = (uint64_t)nreg << s.item_log2;
+    if (!items) return QS_OK;
+    const int lane = (p.ctrl_mask & 1ull) ? (int)(p.ctrl_vals & 1ull) : -1;
+    const int nt = cta_threads(items, kIPT);
+    k_gate1_prec<false><<<blocks_for(items, nt * kIPT), nt, 0, st>>>(psi, items, s, t, uh, ul, lane);
+  }
+  QS_LAUNCHED();
+  return QS_OK;
 }
 
 template <typename R, int K, int OP>
@@ -354,6 +469,9 @@ int launch_plan_on(void* data, int dtype, int n, int nreg, int64_t reg_stride, c
                    qs_state* owner) {
   (void)reg_stride;
   cudaStream_t st = owner ? owner->stream : nullptr;
+  if (dtype == QS_C64 && p.precise &&
+      (p.op == OP_DIAG1 || p.op == OP_DENSE1 || p.op == OP_REAL1 || p.op == OP_RXLIKE1 || p.op == OP_PERM1))
+    return launch_prec((float2*)data, n, nreg, p, st);
   if (use_block_tc(dtype, p)) return launch_block_tc((float2*)data, n, nreg, p, st);
   if (dtype == QS_C64) return launch_typed<float>((float2*)data, n, nreg, p, st);
   return launch_typed<double>((double2*)data, n, nreg, p, st);

@@ -161,14 +161,16 @@ class State:
         return self
 
     def apply_circuit(self, circuit: "Circuit", params=None, per_register=False, fused=True, tiles=False,
-                      tile_qubits=0, blocks=0, flags=None):
+                      tile_qubits=0, blocks=0, flags=None, precise=False):
         """apply!(reg, chain) (Sec. "Representing Quantum Circuits").  fused=False: one launch per gate; tiles=True: force the
         tile engine (fused passes over 2^tile_qubits-amplitude tiles); blocks=k: fuse
-        the gates into blocks of at most k qubits; flags: raw qs_apply_circuit flags
+        the gates into blocks of at most k qubits; precise=True: complex64 1-qubit gates with
+        compensated matrices, rounded once (QS_APPLY_PRECISE); flags: raw qs_apply_circuit flags
         (e.g. from autotune), overriding the others."""
         p = _params_array(params, circuit.nparams * (self.nreg if per_register else 1))
         if flags is None:
             flags = (N.QS_APPLY_PER_REGISTER if per_register else 0) | (0 if fused else N.QS_APPLY_UNFUSED)
+            flags |= N.QS_APPLY_PRECISE if precise else 0
             flags |= (N.QS_APPLY_TILES if tiles else 0) | (int(tile_qubits) << 8)
             if blocks:
                 flags |= N.QS_APPLY_BLOCKS | (int(blocks) << 16)

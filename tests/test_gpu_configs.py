@@ -134,3 +134,26 @@ def test_large_pipeline_n32_properties(qs):
         for q in range(n):
             if q > later + 1:
                 assert abs(g[layer, q]) < 1e-4 * gmax, (layer, q, g[layer, q])
+
+
+def test_precise_complex64_apply_against_oracle(qs, record_property):
+    # QS_APPLY_PRECISE: compensated 1-qubit gates (fused runs, controls, diagonal and
+    # permutation forms) rounded once, against the oracle; its error must not exceed the
+    # plain complex64 path's on the same deep circuit
+    n, depth = 12, 60
+    gates, params = W.variational(n, depth, "ring", seed=9)
+    extra = [W.Gate("RY", (3,), (5,), (0,), theta=0.3), W.Gate("SHIFT", (7,), (1,), (1,), theta=1.1),
+             W.Gate("T", (2,)), W.Gate("Y", (4,), (9,), (1,)), W.Gate("H", (0,))]
+    gates = gates + extra * 20
+    circ = qs.Circuit(gates, n, nparams=len(params))
+    ref = oracle.apply_circuit(oracle.zero_state(n), n, gates, params)
+    errs = {}
+    for name, kw in (("plain", {"fused": False}), ("precise", {"precise": True})):
+        st = qs.State(n, dtype=torch.complex64)
+        st.reset()
+        st.apply_circuit(circ, params, **kw)
+        errs[name] = float(np.max(np.abs(st.numpy() - ref)))
+    record_property("state_abs_err", errs)
+    print(f"complex64 n={n}, {len(gates)} gates: max|dpsi| plain {errs['plain']:.2e} precise {errs['precise']:.2e}")
+    assert errs["precise"] < 2e-6
+    assert errs["precise"] <= errs["plain"]

@@ -186,3 +186,29 @@ def test_tma_fed_blocks_consecutive_targets(qs, k):
             for r in range(3):
                 want = oracle.apply_circuit(psi[r], n, [g])
                 assert np.max(np.abs(got[r] - want)) < TOL, (n, locs, r)
+
+
+def test_tensor_core_block_norm_drift(qs, record_property):
+    # the same unitary 5-qubit block applied 64 times on the tensor cores and on the CUDA
+    # cores: the norm drift per block measures the bias of the tensor-core accumulation
+    n, reps = 20, 64
+    rs = np.random.default_rng(11)
+    a = rs.standard_normal((32, 32)) + 1j * rs.standard_normal((32, 32))
+    q, r = np.linalg.qr(a)
+    U = q * (np.diag(r) / np.abs(np.diag(r)))
+    psi0 = W.haar_state(n, seed=12)
+    drift = {}
+    for mode, locs in ((2, (0, 1, 2, 3, 4)), (2, (15, 16, 17, 18, 19)), (0, (0, 1, 2, 3, 4))):
+        qs.set_tensor_cores(mode)
+        st = qs.State(n, dtype=torch.complex64)
+        st.upload(psi0)
+        g = W.Gate("MATRIX", locs, matrix=U)
+        for _ in range(reps):
+            st.apply(g)
+        nrm = float(torch.sum(torch.abs(st.buffer.to(torch.complex128)) ** 2).item())
+        drift[f"mode{mode}_q{locs[0]}"] = (nrm - 1.0) / reps
+    qs.set_tensor_cores(1)
+    record_property("norm_drift_per_block", drift)
+    print("norm drift per 5-qubit block:", {k: f"{v:.2e}" for k, v in drift.items()})
+    assert abs(drift["mode0_q0"]) < 1e-7
+    assert all(abs(v) < 1e-5 for v in drift.values())
