@@ -147,7 +147,8 @@ static int apply_circuit_impl(qs_state* s, const qs_circuit* c, const double* pa
   if (min_n(s) < c->nqubits) return fail(QS_EINVAL, "circuit has %d qubits, register only %d", c->nqubits, min_n(s));
   const int ng = (int)c->gates.size();
   const bool per_register = (flags & QS_APPLY_PER_REGISTER) != 0;
-  const bool unfused = (flags & QS_APPLY_UNFUSED) != 0 || ckpt_every > 0;
+  const bool unfused = (flags & QS_APPLY_UNFUSED) != 0;
+  const bool per_gate = unfused || ckpt_every > 0;  // no tile engine or blocks
   // compensated 1-qubit gates on complex64: asked for, or the checkpointed forward
   // that feeds the FP64 reversible backward
   const bool precise = ((flags & QS_APPLY_PRECISE) != 0 || ckpt_every > 0) && s->dtype == QS_C64;
@@ -176,7 +177,7 @@ static int apply_circuit_impl(qs_state* s, const qs_circuit* c, const double* pa
   if (force_tiles && (flags & QS_APPLY_BLOCKS)) return fail(QS_EINVAL, "QS_APPLY_TILES and QS_APPLY_BLOCKS together");
   if ((flags & QS_APPLY_PRECISE) && (force_tiles || (flags & QS_APPLY_BLOCKS)))
     return fail(QS_EINVAL, "QS_APPLY_PRECISE runs the per-gate path (not with QS_APPLY_TILES or QS_APPLY_BLOCKS)");
-  if (!unfused && !precise && !(flags & QS_APPLY_BLOCKS) && s->dtype == QS_C64 && s->uniform &&
+  if (!per_gate && !precise && !(flags & QS_APPLY_BLOCKS) && s->dtype == QS_C64 && s->uniform &&
       s->nq[0] == c->nqubits) {
     const int m = std::min(s->nq[0], tile > 0 ? tile : 13);
     const uint64_t tiles = (uint64_t)s->nreg << (s->nq[0] - m);
@@ -187,7 +188,7 @@ static int apply_circuit_impl(qs_state* s, const qs_circuit* c, const double* pa
   } else if (force_tiles) {
     return fail(QS_EUNSUPPORTED, "the tile engine runs uniform complex64 registers of the circuit's size");
   }
-  if ((flags & QS_APPLY_BLOCKS) && !unfused) {
+  if ((flags & QS_APPLY_BLOCKS) && !per_gate) {
     const int kb = (flags >> 16) & 0xf;
     return apply_blocks(s, c, params, kb > 0 ? kb : QS_MAXK);
   }
@@ -209,6 +210,7 @@ static int apply_circuit_impl(qs_state* s, const qs_circuit* c, const double* pa
       QS_TRY(launch_plan(s, p));
     }
     if (ckpt_every > 0 && (k + 1) % ckpt_every == 0 && k + 1 < ng) {
+      QS_TRY(fz.flush_all());  // the checkpoint holds the state after gate k exactly
       const int slot = (k + 1) / ckpt_every - 1;
       QS_CUDA(cudaMemcpyAsync((char*)ckpts + ab * (size_t)s->off[1] * slot, s->data, ab * (size_t)s->off[1],
                               cudaMemcpyDeviceToDevice, s->stream));

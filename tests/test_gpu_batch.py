@@ -1,6 +1,9 @@
 """Batched uneven registers in one persistent launch (complex64) against the FP64
 oracle: final states (2e-5 absolute), losses (1e-5) and gradients (max abs error
-relative to the largest oracle gradient entry, 1e-4: FP32 forward and uncompute)."""
+relative to the largest oracle gradient entry).  Gradient tolerances are about 3x
+the errors measured on GB300: the FP32 path (FP32 forward and uncompute) 7e-7 on
+the small batches and 2.7e-6 on the benchmarked 1024-register batch; the precise
+path (compensated forward, double-float uncompute) 4.6e-7 and 9.0e-7."""
 import numpy as np
 import pytest
 
@@ -39,7 +42,7 @@ def mixed_circuit(n, seed):
     return gates + extra + gates[: 3 * n], params
 
 
-def run_case(qs, specs, tile=0, phase=0, precise=False, gtol=1e-4):
+def run_case(qs, specs, tile=0, phase=0, precise=False, gtol=5e-6):
     circs, obs, plist, terms_l, gl = [], [], [], [], []
     for n, gates, params, terms in specs:
         circs.append(qs.Circuit(gates, n, nparams=len(params)))
@@ -90,8 +93,9 @@ def test_batch_phase_widths_and_precise_path(qs, phase, precise, record_property
     for r, n in enumerate([6, 11, 13]):
         gates, params = mixed_circuit(n, 40 + r)
         specs.append((n, gates, params, W.zz_chain(n, periodic=True)))
-    worst = run_case(qs, specs, phase=phase, precise=precise, gtol=1e-4)
-    worst9 = run_case(qs, specs[:5], tile=9, phase=phase, precise=precise, gtol=1e-4)
+    tol = 1.5e-6 if precise else 3e-6
+    worst = run_case(qs, specs, phase=phase, precise=precise, gtol=tol)
+    worst9 = run_case(qs, specs[:5], tile=9, phase=phase, precise=precise, gtol=tol)
     record_property("worst_relative_gradient_error", max(worst, worst9))
     print(f"phase {phase} precise {precise}: worst relative gradient error {worst:.2e} / tile 9 {worst9:.2e}")
 
@@ -149,8 +153,7 @@ def test_batch_full_size_sampled(qs, record_property):
     # the benchmarked batch itself: 1024 registers, n ~ U{10..18} (seed 0), 20 layers
     # of Rz Rx Rz + CNOT ladder, <sum Z_i Z_{i+1}>, one persistent launch with
     # 13-qubit tiles; registers of every size class checked against the oracle
-    # (gradient tolerance 1e-4 relative, as for the other batches: FP32 forward and
-    # uncompute through up to 1420 gates; measured on GB300: 2.7e-6)
+    # (FP32 forward and uncompute through up to 1420 gates; measured on GB300: 2.7e-6)
     counts = W.batch_qubit_counts(1024, 10, 18, seed=0)
     specs = W.batch_variational(counts, 20, seed=0)
     circs = [qs.Circuit(g, int(n), nparams=len(p)) for n, (g, p) in zip(counts, specs)]
@@ -177,7 +180,7 @@ def test_batch_full_size_sampled(qs, record_property):
         g = grad[prog.param_offsets[r]:prog.param_offsets[r + 1]]
         err = float(np.max(np.abs(g - rg)) / np.max(np.abs(rg)))
         worst = max(worst, err)
-        assert err < 1e-4, ("grad", r, n, err)
+        assert err < 8e-6, ("grad", r, n, err)
     record_property("worst_relative_gradient_error", worst)
     print(f"registers {picks}: worst relative gradient error {worst:.2e}")
 
@@ -211,7 +214,7 @@ def test_batch_full_size_sampled_precise(qs, record_property):
         g = grad[prog.param_offsets[r]:prog.param_offsets[r + 1]]
         err = float(np.max(np.abs(g - rg)) / np.max(np.abs(rg)))
         worst = max(worst, err)
-        assert err < 1e-4, ("grad", r, n, err)
+        assert err < 2e-6, ("grad", r, n, err)  # measured on GB300: 9.0e-7
     record_property("worst_relative_gradient_error", worst)
     print(f"precise batch, tile {tile} phase {phase}: registers {picks}: worst relative gradient error {worst:.2e}; "
           f"shapes {times}")

@@ -74,8 +74,10 @@ def test_differentiation_n20_full_size(qs, record_property):
     record_property("grad_rel_err_c64_forward_fp64_uncompute", err)
     record_property("loss_abs_err", abs(loss - rl))
     print(f"n=20 differentiation: |dloss|={abs(loss - rl):.3e} grad max rel err={err:.3e}")
-    assert abs(loss - rl) < 1e-4
-    assert err < 1e-4
+    # measured on GB300: loss 9.2e-9, gradient 2.5e-6 (the storage rounding of the complex64
+    # forward over 100 layers; compensated gate matrices and the FP64 uncompute remove the rest)
+    assert abs(loss - rl) < 1e-6
+    assert err < 8e-6
 
 
 def large_pipeline(qs, n, depth, seed=0):
@@ -98,8 +100,10 @@ def test_large_pipeline_n22_against_oracle(qs):
     psiN = oracle.apply_circuit(psi0, n, bgates, bparams)
     assert np.max(np.abs(st.numpy() - psiN)) < 2e-5
     rl, rg = oracle.gradient(psi0, n, bgates, bparams, W.z_on(0))
+    err = float(np.max(np.abs(grad - rg)) / np.max(np.abs(rg)))
+    print(f"n=22 tile-engine pipeline: loss {abs(loss - rl):.2e} grad {err:.2e}")
     assert abs(loss - rl) < 1e-5
-    assert np.max(np.abs(grad - rg)) / np.max(np.abs(rg)) < 1e-4
+    assert err < 1e-4
 
 
 def test_large_pipeline_n32_properties(qs):

@@ -75,6 +75,7 @@ def test_block_gradient_matches_oracle(qs, dt, kmax):
         loss, grad = qs.backward_blocks(st, circ, params, obs, kmax=kmax)
         wl, wg = oracle.gradient(psi0, n, gates, params, terms)
         assert abs(loss - wl) < (1e-12 if dt == "c128" else 1e-5), (name, loss, wl)
+        print(f"block gradient n=9 {dt} kmax={kmax} {name}: {rel(grad, wg):.2e}")
         assert rel(grad, wg) < GTOL[dt], (name, kmax, rel(grad, wg))
         # uncomputed back to the input
         back = st.numpy()
@@ -96,6 +97,7 @@ def test_block_gradient_n20_against_fp64_adjoint(qs):
     ref.apply_circuit(circ, params)
     wl, wg = qs.backward(ref, circ, params, obs)
     loss, grad = qs.backward_blocks(st, circ, params, obs, kmax=5)
+    print(f"block gradient n=20 vs FP64 adjoint: {rel(grad, wg):.2e}")
     assert abs(loss - wl) < 1e-5
     assert rel(grad, wg) < 1e-4, rel(grad, wg)
 
@@ -142,5 +144,6 @@ def test_block_gradient_tensor_core_gram_many_groups(qs):
         st.apply_circuit(circ, params, blocks=5)
         out[mode] = qs.backward_blocks(st, circ, params, obs, kmax=5)
     qs.set_tensor_cores(1)
+    print(f"block gradient n=24 tensor vs CUDA cores: {rel(out[1][1], out[0][1]):.2e}")
     assert abs(out[1][0] - out[0][0]) < 1e-5
     assert rel(out[1][1], out[0][1]) < 1e-4, rel(out[1][1], out[0][1])

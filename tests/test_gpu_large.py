@@ -21,7 +21,13 @@ outer-product).
   sampled indices (closed form) and the state uncomputed by the backward pass
   (again the QFT output) are checked against it.
 
-The measured errors are recorded as test properties (junit xml).
+The measured errors are recorded as test properties (junit xml).  Tolerances
+are about 3x the errors measured on GB300.  The tensor-core blocks dominate
+them: the MMA accumulates in FP32 with truncation, a measured norm drift of
+-8.9e-7 per 5-qubit block (the CUDA-core kernel: 1.7e-9), so psi and lambda
+shrink by ~1e-4 over the 71 forward blocks and 71 block adjoints of n = 32
+and the gradient carries that relative error; the same pipeline with the
+tensor cores off is checked at n = 22 to the complex64 rounding level.
 """
 import math
 
@@ -88,8 +94,20 @@ def restricted_gates(gates, keep):
     return [g for g in gates if (set(g.locs) | set(g.ctrl_locs)) <= keep]
 
 
-def test_large_pipeline_blocks_n22_against_oracle(qs, record_property):
+@pytest.mark.parametrize("tc", [1, 0])
+def test_large_pipeline_blocks_n22_against_oracle(qs, tc, record_property):
     n = 22
+    qs.set_tensor_cores(tc)
+    try:
+        _n22(qs, n, tc, record_property)
+    finally:
+        qs.set_tensor_cores(1)
+
+
+GRAD_TOL_N22 = {1: 2e-4, 0: 2e-5}  # measured on GB300: 7.2e-5 (tensor cores), CUDA cores below
+
+
+def _n22(qs, n, tc, record_property):
     x, bgates, bparams, st, bcirc = bench_pipeline(qs, n)
     psi0 = oracle.apply_circuit(oracle.basis_state(n, x), n, W.qft(n, swaps=True))
     got0 = st.numpy()
@@ -104,11 +122,11 @@ def test_large_pipeline_blocks_n22_against_oracle(qs, record_property):
     for k, v in (("qft_state_abs", err_qft), ("brickwork_state_abs", err_state), ("loss_abs", abs(loss - rl)),
                  ("grad_rel", err_grad), ("uncomputed_state_abs", err_back)):
         record_property(k, v)
-    print(f"n=22 blocks pipeline: qft {err_qft:.2e} state {err_state:.2e} loss {abs(loss - rl):.2e} "
-          f"grad {err_grad:.2e} uncompute {err_back:.2e}")
+    print(f"n=22 blocks pipeline (tensor cores {tc}): qft {err_qft:.2e} state {err_state:.2e} "
+          f"loss {abs(loss - rl):.2e} grad {err_grad:.2e} uncompute {err_back:.2e}")
     assert err_qft < 2e-5 and err_state < 2e-5
     assert abs(loss - rl) < 1e-5
-    assert err_grad < 1e-4
+    assert err_grad < GRAD_TOL_N22[tc]
     assert err_back < 2e-5
 
 
@@ -152,8 +170,9 @@ def test_large_pipeline_blocks_n32_light_cone_oracle(qs, record_property):
         record_property(k, v)
     print(f"n=32 blocks pipeline: qft {err_qft:.2e} |norm-1| {abs(nrm - 1):.2e} loss {abs(loss - rl):.2e} "
           f"grad {err_grad:.2e} uncompute {err_back:.2e} (light cone {m} qubits, {int(outside.sum())} angles outside)")
+    # measured on GB300: |norm - 1| 6.2e-5, loss 3.5e-6, gradient 1.2e-4, uncompute 6.6e-5
     assert err_qft < 1e-3
-    assert abs(nrm - 1.0) < 1e-4
+    assert abs(nrm - 1.0) < 2e-4
     assert abs(loss - rl) < 1e-5
-    assert err_grad < 1e-4
-    assert err_back < 2e-3
+    assert err_grad < 4e-4
+    assert err_back < 2e-4
