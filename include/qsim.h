@@ -144,7 +144,9 @@ int qs_state_sync(qs_state* s);
  * dtype and register sizes (QS_EINVAL otherwise). */
 
 /* dst <- src, asynchronous on dst's stream (order src's earlier work before
- * it: same stream or an event). */
+ * it: same stream or an event).  The dtypes may differ (same register sizes):
+ * complex64 -> complex128 widens exactly, complex128 -> complex64 rounds to
+ * nearest. */
 int qs_state_copy(qs_state* dst, const qs_state* src);
 
 /* <a_r|b_r> = sum_i conj(a_r,i) b_r,i per register r into host_out[2 nreg]
@@ -156,6 +158,40 @@ int qs_state_inner(qs_state* a, const qs_state* b, double* host_out);
 /* y <- y + alpha x in the states' precision (alpha rounded to FP32 for
  * complex64), asynchronous on y's stream.  x and y must be distinct. */
 int qs_state_axpy(qs_state* y, double alpha_re, double alpha_im, const qs_state* x);
+
+/* One gate of the reversible adjoint walk (Sec. "Reverse Mode", Eq.
+ * apply-back) on two complex128 single registers psi and lambda of the same
+ * size, for a caller that walks a circuit itself with other work in between
+ * (a register split over processes exchanges shard halves between gates).
+ * g's targets and controls are qubits of these registers.  A parameterised
+ * gate U = exp(-i theta c H) (RX, RY, RZ, SHIFT, PHASE, ROT) first adds
+ * 2 c Im<lambda|(P_ctrl (x) H)|psi> to dev_grad[g->param] (device memory,
+ * FP64, added in stream order: no synchronisation), P_ctrl the projector onto
+ * the control values; then psi <- U^dag psi and lambda <- U^dag lambda in
+ * FP64; any other gate is only uncomputed.  host_mats: interleaved complex
+ * doubles a MATRIX gate reads at mat_offset (else may be NULL); host_params:
+ * the parameter vector (theta = host_params[g->param]).  Asynchronous on
+ * psi's stream (lambda must be ordered with it). */
+int qs_adjoint_step(qs_state* psi, qs_state* lam, const qs_gate_desc* g, const double* host_mats,
+                    const double* host_params, double* dev_grad);
+
+/* Host-side matrices of one gate record (no device work; callable without a
+ * GPU): host_U (may be NULL) receives U, or U^dag if dagger_u != 0 (2^k x 2^k,
+ * row-major, interleaved re/im, index bit j <-> locs[j], controls not
+ * included); host_G / host_cfac (may be NULL) the generator H on the targets
+ * and c with U = exp(-i theta c H) (QS_EINVAL for a gate without a
+ * parameter).  host_mats / host_params as for qs_adjoint_step. */
+int qs_gate_desc_matrices(const qs_gate_desc* g, const double* host_mats, const double* host_params, int dagger_u,
+                          double* host_U, double* host_G, double* host_cfac);
+
+/* The first level of a measurement over a register split into nshards
+ * pieces (host only): with the pieces' weights P_s = <psi_s|psi_s>, each shot
+ * picks a piece by qs_measure's walk (T = left fold of the weights, t = u T,
+ * the first piece whose running sum exceeds t, else the last positive one)
+ * and the uniform u' = (t - prefix) / P_s (kept below 1) that the piece's own
+ * sampler then takes.  QS_EINVAL for a uniform outside [0, 1). */
+int qs_sample_shards(int nshards, const double* host_weights, int nshots, const double* host_u,
+                     int32_t* host_shard, double* host_u_in_shard);
 
 /* ---------------------------------------------------------------- options */
 

@@ -17,6 +17,7 @@ Functions and the passages they follow:
   apply_dagger    Sec. "Manipulating Quantum Circuits" (dagger rules)
   expect          Sec. "Forward Mode" (expect of sums of Pauli strings)
   gradient        Sec. "Reverse Mode", Eqs. apply-back / outer-product
+  adjoint_step    one gate of that walk
   shift_gradient  Eq. shiftrule (only for uncontrolled Pauli rotations)
   fd_gradient     central finite differences of ``expect``
   sample/collapse Sec. "Instructions on Quantum Registers" (measure / measure!),
@@ -229,6 +230,22 @@ def gradient(psi0, n, gates, params, terms):
     _check(lib().orc_gradient(psi0.ctypes.data, n, arr, len(gates), _dp(p), nparams, pool.ctypes.data,
                               tarr, len(terms), _dp(grad), _dp(loss)), "gradient")
     return float(loss[0]), grad[:nparams]
+
+
+def adjoint_step(psi, lam, n, gate, params, grad):
+    """One gate of the reversible adjoint walk (Sec. "Reverse Mode", Eq. apply-back),
+    in place on the complex128 arrays psi and lam: grad[gate.param] += 2 c
+    Im<lam|H psi> for a parameterised gate, then psi, lam <- U^dag psi, U^dag lam."""
+    assert psi.dtype == np.complex128 and lam.dtype == np.complex128 and psi.flags.c_contiguous
+    arr, pool = _marshal_gates([gate])
+    p = _params(params)
+    nparams = 0 if params is None else len(params)
+    g = np.ascontiguousarray(grad, dtype=np.float64)
+    phi = np.zeros_like(psi)
+    im = np.zeros(len(psi))
+    _check(lib().orc_adjoint_step(psi.ctypes.data, lam.ctypes.data, phi.ctypes.data, _dp(im), n, arr, _dp(p),
+                                  nparams, pool.ctypes.data, _dp(g)), "adjoint_step")
+    grad[:] = g
 
 
 def loss(psi0, n, gates, params, terms) -> float:

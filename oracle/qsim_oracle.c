@@ -290,28 +290,19 @@ int orc_apply_observable(cplx* lam, const cplx* psi, int n, const orc_term* term
 /*   phase(theta) = e^{i theta}: c = -1, H = identity on the target.          */
 /* Gradients of shared parameters add up.                                    */
 /* ------------------------------------------------------------------------ */
-int orc_gradient(const cplx* psi0, int n, const orc_gate* gates, int ngates,
-                 const double* params, int nparams, const cplx* mats,
-                 const orc_term* terms, int nterms, double* grad, double* loss) {
+/* One gate of that walk: the contribution of gate g (if it has a parameter)
+   to grad, then psi <- U^dag psi and lambda <- U^dag lambda.  phi and im are
+   scratch vectors of 2^n entries. */
+int orc_adjoint_step(cplx* psi, cplx* lam, cplx* phi, double* im, int n, const orc_gate* g,
+                     const double* params, int nparams, const cplx* mats, double* grad) {
   int64_t dim = (int64_t)1 << n;
-  cplx* psi = malloc(sizeof(cplx) * dim);
-  cplx* lam = malloc(sizeof(cplx) * dim);
-  cplx* phi = malloc(sizeof(cplx) * dim);
-  double* im = malloc(sizeof(double) * dim);
-  if (!psi || !lam || !phi || !im) { free(psi); free(lam); free(phi); free(im); return -2; }
   int rc = 0;
-  memcpy(psi, psi0, sizeof(cplx) * dim);
-  for (int p = 0; p < nparams; ++p) grad[p] = 0.0;
-  rc = orc_apply_circuit(psi, n, gates, ngates, params, mats, 0);
-  if (!rc) rc = orc_expect(psi, n, terms, nterms, loss);
-  if (!rc) rc = orc_apply_observable(lam, psi, n, terms, nterms);
   cplx U[1 << (2 * ORC_MAXK)];
-  for (int kk = ngates - 1; kk >= 0 && !rc; --kk) {
-    const orc_gate* g = &gates[kk];
+  {
     double th = gate_angle(g, params);
     if (g->param >= 0) {
       double cfac;
-      if (g->param >= nparams) { rc = -1; break; }
+      if (g->param >= nparams) return -1;
       /* phi = H psi, H = (control projector) (x) H_local */
       memcpy(phi, psi, sizeof(cplx) * dim);
       for (int64_t i = 0; i < dim; ++i) {
@@ -343,16 +334,36 @@ int orc_gradient(const cplx* psi0, int n, const orc_gate* gates, int ngates,
         case ORC_PHASE: U[0] = 1; U[3] = 1; cfac = -1.0; break;
         default: rc = -1; cfac = 0; break;
       }
-      if (rc) break;
+      if (rc) return rc;
       orc_apply(phi, n, g->k, g->locs, U, 0, NULL, NULL);
       for (int64_t i = 0; i < dim; ++i) im[i] = cimag(conj(lam[i]) * phi[i]);
       grad[g->param] += 2.0 * cfac * orc_pairwise_sum(im, dim);
     }
     rc = orc_gate_matrix_dagger(g, th, mats, U);
-    if (rc) break;
+    if (rc) return rc;
     orc_apply(psi, n, g->k, g->locs, U, g->nctrl, g->ctrl_locs, g->ctrl_vals);
     orc_apply(lam, n, g->k, g->locs, U, g->nctrl, g->ctrl_locs, g->ctrl_vals);
   }
+  return rc;
+}
+
+int orc_gradient(const cplx* psi0, int n, const orc_gate* gates, int ngates,
+                 const double* params, int nparams, const cplx* mats,
+                 const orc_term* terms, int nterms, double* grad, double* loss) {
+  int64_t dim = (int64_t)1 << n;
+  cplx* psi = malloc(sizeof(cplx) * dim);
+  cplx* lam = malloc(sizeof(cplx) * dim);
+  cplx* phi = malloc(sizeof(cplx) * dim);
+  double* im = malloc(sizeof(double) * dim);
+  if (!psi || !lam || !phi || !im) { free(psi); free(lam); free(phi); free(im); return -2; }
+  int rc = 0;
+  memcpy(psi, psi0, sizeof(cplx) * dim);
+  for (int p = 0; p < nparams; ++p) grad[p] = 0.0;
+  rc = orc_apply_circuit(psi, n, gates, ngates, params, mats, 0);
+  if (!rc) rc = orc_expect(psi, n, terms, nterms, loss);
+  if (!rc) rc = orc_apply_observable(lam, psi, n, terms, nterms);
+  for (int kk = ngates - 1; kk >= 0 && !rc; --kk)
+    rc = orc_adjoint_step(psi, lam, phi, im, n, &gates[kk], params, nparams, mats, grad);
   free(psi); free(lam); free(phi); free(im);
   return rc;
 }

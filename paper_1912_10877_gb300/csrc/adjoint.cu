@@ -14,6 +14,7 @@
 // stream order.  The uncompute runs in FP64 (complex128 work buffers) whatever
 // the forward precision; checkpoints taken during the forward replace psi at
 // segment boundaries so that uncompute drift cannot accumulate across segments.
+#include <cmath>
 #include <cstring>
 
 #include "common.cuh"
@@ -292,3 +293,139 @@ int backward(qs_state* s, const qs_circuit* c, const double* params, const qs_ob
 }
 
 }  // namespace qs
+
+// ------------------------------------------------------------------ one gate of the adjoint walk
+//
+// qs_adjoint_step: the per-gate step of the walk above on two caller-held
+// complex128 registers, for callers that walk a circuit themselves (the
+// qubit-sharded register, whose gates may need data exchanges in between).
+
+namespace qs {
+
+// the matrix pool of a desc: MATRIX gates read 4^k entries at mat_offset
+static int desc_matrix(const qs_gate_desc& g, const double* host_mats, const double* params, std::vector<cd>& U) {
+  if (g.kind == QS_GATE_MATRIX) {
+    if (!host_mats || g.mat_offset < 0) return fail(QS_EINVAL, "MATRIX gate without its matrix");
+    const int D = 1 << g.nlocs;
+    U.resize(D * D);
+    for (int i = 0; i < D * D; ++i)
+      U[i] = cd(host_mats[2 * (g.mat_offset + i)], host_mats[2 * (g.mat_offset + i) + 1]);
+    return QS_OK;
+  }
+  qs_circuit tmp;
+  tmp.nqubits = QS_MAXQ;
+  return gate_matrix(&tmp, g, params, U);
+}
+
+static int check_desc(const qs_gate_desc& g, int n, const double* params) {
+  int32_t locs[QS_MAXK];
+  if (g.nlocs < 1 || g.nlocs > QS_MAXK) return fail(QS_EINVAL, "gate arity %d", g.nlocs);
+  for (int j = 0; j < g.nlocs; ++j) locs[j] = g.locs[j];
+  QS_TRY(validate_gate(n, g.nlocs, locs, g.ctrl_mask));
+  if (g.param >= 0 && !params) return fail(QS_EINVAL, "the gate needs the parameter vector");
+  return QS_OK;
+}
+
+}  // namespace qs
+
+using namespace qs;
+
+extern "C" {
+
+int qs_gate_desc_matrices(const qs_gate_desc* g, const double* host_mats, const double* host_params, int dagger_u,
+                          double* host_U, double* host_G, double* host_cfac) {
+  if (!g) return fail(QS_EINVAL, "null gate");
+  QS_TRY(check_desc(*g, QS_MAXQ, host_params));
+  const int D = 1 << g->nlocs;
+  if (host_U) {
+    std::vector<cd> U;
+    QS_TRY(desc_matrix(*g, host_mats, host_params, U));
+    if (dagger_u) dagger(U, g->nlocs);
+    for (int i = 0; i < D * D; ++i) { host_U[2 * i] = U[i].real(); host_U[2 * i + 1] = U[i].imag(); }
+  }
+  if (host_G || host_cfac) {
+    if (g->param < 0) return fail(QS_EINVAL, "the gate has no parameter");
+    std::vector<cd> G;
+    double cf = 0.0;
+    QS_TRY(gate_generator(*g, G, &cf));
+    if (host_G)
+      for (int i = 0; i < D * D; ++i) { host_G[2 * i] = G[i].real(); host_G[2 * i + 1] = G[i].imag(); }
+    if (host_cfac) *host_cfac = cf;
+  }
+  return QS_OK;
+}
+
+int qs_adjoint_step(qs_state* psi, qs_state* lam, const qs_gate_desc* g, const double* host_mats,
+                    const double* host_params, double* dev_grad) {
+  if (!psi || !lam || !g) return fail(QS_EINVAL, "null argument");
+  if (psi->dtype != QS_C128 || lam->dtype != QS_C128) return fail(QS_EINVAL, "qs_adjoint_step takes complex128 states");
+  if (psi->nreg != 1 || lam->nreg != 1 || psi->nq[0] != lam->nq[0])
+    return fail(QS_EINVAL, "psi and lambda must be single registers of one size");
+  if (psi->data == lam->data) return fail(QS_EINVAL, "psi and lambda must be distinct");
+  const int n = psi->nq[0];
+  QS_TRY(check_desc(*g, n, host_params));
+  const bool param = g->param >= 0 && g->kind != QS_GATE_MATRIX;
+  if (param && !dev_grad) return fail(QS_EINVAL, "dev_grad is NULL");
+  cudaStream_t st = psi->stream;
+  std::vector<cd> U;
+  QS_TRY(desc_matrix(*g, host_mats, host_params, U));
+  dagger(U, g->nlocs);
+  double2* x = (double2*)psi->data;
+  double2* l = (double2*)lam->data;
+  if (!param) {
+    Plan p;
+    QS_TRY(plan_gate(U.data(), g->nlocs, g->locs, g->ctrl_mask, g->ctrl_vals, &p));
+    QS_TRY(launch_plan_on(x, QS_C128, n, 1, 1ll << n, p, psi));
+    QS_TRY(launch_plan_on(l, QS_C128, n, 1, 1ll << n, p, psi));
+    return QS_OK;
+  }
+  std::vector<cd> G;
+  double cfac = 0.0;
+  QS_TRY(gate_generator(*g, G, &cfac));
+  QS_TRY(ensure_ws(psi, psi->ws, sizeof(double) * kAdjMaxBlocks));
+  double* partials = (double*)psi->ws.ptr;
+  switch (g->nlocs) {
+    case 1: return launch_adjoint_param<1>(x, l, n, *g, G, U, partials, dev_grad, cfac, st);
+    case 2: return launch_adjoint_param<2>(x, l, n, *g, G, U, partials, dev_grad, cfac, st);
+    case 3: return launch_adjoint_param<3>(x, l, n, *g, G, U, partials, dev_grad, cfac, st);
+  }
+  return fail(QS_EUNSUPPORTED, "parameterised gate on %d targets", g->nlocs);
+}
+
+int qs_sample_shards(int nshards, const double* host_weights, int nshots, const double* host_u,
+                     int32_t* host_shard, double* host_u_in_shard) {
+  if (nshards < 1 || nshots < 0 || !host_weights || (nshots > 0 && (!host_u || !host_shard || !host_u_in_shard)))
+    return fail(QS_EINVAL, "bad arguments");
+  // the walk of qs_measure's contract over the shard weights: T = left fold of
+  // the weights, t = u T, first shard whose running sum exceeds t (else the last
+  // positive weight, else the last shard); its exclusive prefix a gives the
+  // uniform of the shard's own sampler u' = (t - a) / P_s, kept below 1
+  double total = host_weights[0];
+  for (int s = 1; s < nshards; ++s) total = total + host_weights[s];
+  for (int i = 0; i < nshots; ++i) {
+    if (!(host_u[i] >= 0.0 && host_u[i] < 1.0)) return fail(QS_EINVAL, "uniform %d not in [0, 1)", i);
+    const double t = host_u[i] * total;
+    double a = 0.0, a_last = 0.0;
+    int pick = -1, last = -1;
+    for (int s = 0; s < nshards; ++s) {
+      const double nxt = a + host_weights[s];
+      if (nxt > t) { pick = s; break; }
+      if (host_weights[s] > 0.0) { last = s; a_last = a; }
+      a = nxt;
+    }
+    if (pick < 0) {
+      if (last >= 0) { pick = last; a = a_last; }
+      else { pick = nshards - 1; }
+    }
+    const double w = host_weights[pick];
+    double v = w > 0.0 ? (t - a) / w : 0.0;
+    if (!(v >= 0.0)) v = 0.0;
+    if (v >= 1.0) v = std::nextafter(1.0, 0.0);
+    host_shard[i] = pick;
+    host_u_in_shard[i] = v;
+  }
+  return QS_OK;
+}
+
+}  // extern "C"
+

@@ -78,6 +78,17 @@ k_axpy(T* __restrict__ y, const T* __restrict__ x, uint64_t total, T alpha) {
   }
 }
 
+template <typename S, typename D>
+__global__ void __launch_bounds__(kVecThreads) k_convert(const S* __restrict__ in, D* __restrict__ out, uint64_t total) {
+  for (uint64_t i = (uint64_t)blockIdx.x * kVecThreads + threadIdx.x; i < total; i += (uint64_t)gridDim.x * kVecThreads) {
+    const S v = in[i];
+    D w;
+    w.x = v.x;
+    w.y = v.y;
+    out[i] = w;
+  }
+}
+
 static int same_shape(const qs_state* a, const qs_state* b) {
   if (!a || !b) return fail(QS_EINVAL, "null state");
   if (a->dtype != b->dtype) return fail(QS_EINVAL, "states differ in dtype");
@@ -92,6 +103,18 @@ using namespace qs;
 extern "C" {
 
 int qs_state_copy(qs_state* dst, const qs_state* src) {
+  if (dst && src && dst->dtype != src->dtype && dst->nq == src->nq) {
+    // complex64 <-> complex128: widened exactly, or rounded to nearest
+    const uint64_t total = (uint64_t)dst->off.back();
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((total + kVecThreads - 1) / kVecThreads,
+                                                                           (uint64_t)kVecMaxBlocks * 4));
+    if (dst->dtype == QS_C128)
+      k_convert<float2, double2><<<grid, kVecThreads, 0, dst->stream>>>((const float2*)src->data, (double2*)dst->data, total);
+    else
+      k_convert<double2, float2><<<grid, kVecThreads, 0, dst->stream>>>((const double2*)src->data, (float2*)dst->data, total);
+    QS_LAUNCHED();
+    return QS_OK;
+  }
   QS_TRY(same_shape(dst, src));
   if (dst->data == src->data) return QS_OK;
   QS_CUDA(cudaMemcpyAsync(dst->data, src->data, (size_t)dst->off.back() * amp_bytes(dst->dtype),

@@ -211,6 +211,81 @@ def _params_array(params, count):
     return p
 
 
+def _fill_desc(d, g, off: int, pool: list) -> int:
+    """Marshals one workloads.Gate into a qs_gate_desc; MATRIX entries go to `pool`
+    at complex offset `off`.  Returns the next free offset."""
+    d.kind = N.GATE_KIND[g.name]
+    d.nlocs = len(g.locs)
+    for j, l in enumerate(g.locs):
+        d.locs[j] = l
+    if g.paulis:
+        for j, p in enumerate(g.paulis):
+            d.paulis[j] = N.PAULI_CODE[p]
+    d.param = -1 if g.param is None else int(g.param)
+    d.theta = 0.0 if g.theta is None else float(g.theta)
+    cm = cv = 0
+    for l, v in zip(g.ctrl_locs, g.ctrl_vals):
+        cm |= 1 << l
+        if v:
+            cv |= 1 << l
+    d.ctrl_mask, d.ctrl_vals = cm, cv
+    if g.name == "MATRIX":
+        m = np.ascontiguousarray(g.matrix, dtype=np.complex128).ravel()
+        d.mat_offset = off
+        pool.append(m)
+        off += m.size
+    return off
+
+
+def gate_record(g):
+    """(qs_gate_desc, matrix pool as interleaved doubles) of one gate record."""
+    d = N.GateDesc()
+    pool = []
+    _fill_desc(d, g, 0, pool)
+    mats = np.concatenate(pool) if pool else np.zeros(1, np.complex128)
+    return d, np.ascontiguousarray(mats).view(np.float64)
+
+
+def gate_desc_matrices(g, params=None, dagger: bool = False, generator: bool = False):
+    """U (or U^dagger) of one gate record from the library's gate definitions, and with
+    generator=True also (H, c) with U = exp(-i theta c H) (qs_gate_desc_matrices)."""
+    d, mats = gate_record(g)
+    D = 1 << len(g.locs)
+    p = np.ascontiguousarray(np.zeros(1) if params is None or len(params) == 0 else params, dtype=np.float64)
+    U = np.zeros(2 * D * D)
+    G = np.zeros(2 * D * D) if generator else None
+    cf = ctypes.c_double()
+    N.check(N.lib().qs_gate_desc_matrices(ctypes.byref(d), N.dptr(mats), N.dptr(p), 1 if dagger else 0, N.dptr(U),
+                                          N.dptr(G) if generator else None,
+                                          ctypes.byref(cf) if generator else None))
+    U = U.view(np.complex128).reshape(D, D)
+    if not generator:
+        return U
+    return U, G.view(np.complex128).reshape(D, D), cf.value
+
+
+def adjoint_step(psi: "State", lam: "State", g, params, dev_grad: torch.Tensor):
+    """One gate of the reversible adjoint walk on complex128 registers psi and lam
+    (qs_adjoint_step): dev_grad[g.param] += 2 c Im<lam|P_ctrl H|psi> for a parameterised
+    gate, then psi, lam <- U^dag psi, U^dag lam.  Asynchronous; dev_grad: float64 CUDA."""
+    d, mats = gate_record(g)
+    p = np.ascontiguousarray(np.zeros(1) if params is None or len(params) == 0 else params, dtype=np.float64)
+    N.check(N.lib().qs_adjoint_step(psi.handle, lam.handle, ctypes.byref(d), N.dptr(mats), N.dptr(p),
+                                    ctypes.c_void_p(dev_grad.data_ptr())))
+
+
+def sample_shards(weights, u):
+    """First level of a measurement over shards (qs_sample_shards): per uniform, the shard
+    drawn from the shard weights and the uniform its own sampler takes."""
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    u = np.ascontiguousarray(np.ravel(u), dtype=np.float64)
+    shard = np.zeros(len(u), np.int32)
+    sub = np.zeros(len(u))
+    N.check(N.lib().qs_sample_shards(len(w), N.dptr(w), len(u), N.dptr(u), shard.ctypes.data_as(N._PI32),
+                                     N.dptr(sub)))
+    return shard.astype(np.int64), sub
+
+
 class Circuit:
     """Immutable flat gate list (qs_circuit): the put / control / chain blocks of
     Sec. "Representing Quantum Circuits" flattened into gate records."""
@@ -223,27 +298,7 @@ class Circuit:
         pool = []
         off = 0
         for i, g in enumerate(gates):
-            d = arr[i]
-            d.kind = N.GATE_KIND[g.name]
-            d.nlocs = len(g.locs)
-            for j, l in enumerate(g.locs):
-                d.locs[j] = l
-            if g.paulis:
-                for j, p in enumerate(g.paulis):
-                    d.paulis[j] = N.PAULI_CODE[p]
-            d.param = -1 if g.param is None else int(g.param)
-            d.theta = 0.0 if g.theta is None else float(g.theta)
-            cm = cv = 0
-            for l, v in zip(g.ctrl_locs, g.ctrl_vals):
-                cm |= 1 << l
-                if v:
-                    cv |= 1 << l
-            d.ctrl_mask, d.ctrl_vals = cm, cv
-            if g.name == "MATRIX":
-                m = np.ascontiguousarray(g.matrix, dtype=np.complex128).ravel()
-                d.mat_offset = off
-                pool.append(m)
-                off += m.size
+            off = _fill_desc(arr[i], g, off, pool)
         mats = np.concatenate(pool) if pool else np.zeros(1, np.complex128)
         mv = mats.view(np.float64)
         h = ctypes.c_void_p()

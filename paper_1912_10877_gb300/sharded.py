@@ -24,34 +24,35 @@ instruction of Sec. "Instructions on Quantum Registers" / Sec. "Performance":
 Expectation values (Sec. "Forward Mode") localise the X / Y qubits of each
 Pauli string the same way and read a global Z as the sign (-1)^bit of the
 shard; the per-shard sums are added with one all-reduce.  The reversible
-backward (Sec. "Reverse Mode", Eq. apply-back) runs gate by gate on psi and
-lambda = O psi, which share the map: a parameterised gate U = exp(-i theta c H)
-adds 2 c Im<lambda|(P_ctrl (x) H) psi> from a copy of psi, then both states are
-uncomputed by U^dagger; every shard's gradient partials are added with one
-all-reduce at the end.  Measurement (Sec. "Instructions on Quantum
-Registers", measure) draws a shard from the shard weights P_s = <psi_s|psi_s>
-(one all-reduce), then an index inside it with the shard's own sampler and
-the uniform rescaled to that shard's share, and maps the physical index back
-to the logical one.
+backward (Sec. "Reverse Mode", Eq. apply-back) runs gate by gate on complex128
+working copies of psi and lambda = O psi, which share the map: a
+parameterised gate has its targets localised and then, on every shard whose
+global controls match, one library step (qs_adjoint_step) adds
+2 c Im<lambda|(P_ctrl (x) H) psi> to a device gradient and uncomputes both
+states by U^dagger in FP64; other gates are uncomputed by U^dagger from the
+library.  The gradient is read back and added over the ranks once, at the end.
+Measurement (Sec. "Instructions on Quantum Registers", measure) draws a shard
+from the shard weights P_s = <psi_s|psi_s> (one all-reduce) with the library's
+shard walk (qs_sample_shards), then an index inside it with the shard's own
+sampler and the uniform that walk returns, and maps the physical index back to
+the logical one.
 
-Every local operation is a call into libqsim.so (``qsim.State``); this module
-only plans exchanges and predicates, and moves shard halves with
-``torch.distributed`` point-to-point transfers (across processes) or device
-copies (inside one).  ``backend`` lets a caller supply shards of another kind
+Every local operation and all of the method's arithmetic is a call into
+libqsim.so (``qsim.State`` and the level-1 entry points); this module only
+plans exchanges, predicates and which entries of a library-computed diagonal
+a shard keeps, and moves shard halves with ``torch.distributed``
+point-to-point transfers (across processes) or device copies (inside one).  ``backend`` lets a caller supply shards of another kind
 with the same methods (used by the CPU multi-process tests of this logic).
 """
 from __future__ import annotations
 
-import copy
+import dataclasses
 
 import numpy as np
 import torch
 
+from . import _native as N
 from . import qsim
-
-_PAULI = {"X": np.array([[0, 1], [1, 0]], np.complex128),
-          "Y": np.array([[0, -1j], [1j, 0]], np.complex128),
-          "Z": np.array([[1, 0], [0, -1]], np.complex128)}
 
 
 class LibShard:
@@ -76,7 +77,26 @@ class LibShard:
         self.st.apply_matrix(U, list(locs), list(ctrl_locs), list(ctrl_vals))
 
     def copy_from(self, other: "LibShard"):
-        self.st.copy_from(other.st)
+        self.st.copy_from(other.st)   # the dtypes may differ (widened or rounded by the library)
+
+    def apply_pauli(self, p: int, P: str):
+        """The Pauli P on local bit p (the library's X / Y / Z gate)."""
+        loc = N.i32([p])
+        N.check(N.lib().qs_apply_named(self.st.handle, N.GATE_KIND[P], 1, loc, N.i32([]), 0, N.i32([]),
+                                       N.i32([]), 0.0))
+
+    def adjoint_step(self, lam: "LibShard", gate, params, grad: torch.Tensor):
+        """One gate of the reversible adjoint on this shard (psi) and lam, both
+        complex128, gate on local bits (qs_adjoint_step)."""
+        qsim.adjoint_step(self.st, lam.st, gate, params, grad)
+
+    @staticmethod
+    def new_grad(nparams: int) -> torch.Tensor:
+        return torch.zeros(max(1, nparams), dtype=torch.float64, device="cuda")
+
+    @staticmethod
+    def grad_host(buf: torch.Tensor) -> np.ndarray:
+        return buf.cpu().numpy()
 
     def inner(self, other: "LibShard") -> complex:
         return complex(self.st.inner(other.st)[0])
@@ -138,9 +158,9 @@ class ShardedState:
         self.reset()
 
     # ------------------------------------------------------------------ bookkeeping
-    def _vector(self, name: str):
+    def _vector(self, name: str, dtype=None):
         if name not in self.vecs:
-            self.vecs[name] = [self._make(self.L, self.dtype) for _ in self.owned]
+            self.vecs[name] = [self._make(self.L, dtype or self.dtype) for _ in self.owned]
         return self.vecs[name]
 
     def _drop(self, name: str):
@@ -291,13 +311,8 @@ class ShardedState:
         return self
 
     def apply(self, g, params=None, vectors=("psi",)):
-        """One workloads.Gate record, matrix from the library's gate definitions."""
-        if g.param is None:
-            U = qsim.Circuit([g], self.n, nparams=0).gate_matrices(0)
-        else:
-            one = copy.copy(g)
-            one.param = 0
-            U = qsim.Circuit([one], self.n, nparams=1).gate_matrices(0, [float(params[g.param])])
+        """One gate record, matrix from the library's gate definitions."""
+        U = qsim.gate_desc_matrices(g, params)
         return self.apply_matrix(U, g.locs, g.ctrl_locs, g.ctrl_vals, vectors)
 
     def apply_circuit(self, circuit: "qsim.Circuit", params=None):
@@ -348,11 +363,12 @@ class ShardedState:
                 total += v.expect(self._local_terms(s, batch))
         return float(self._sum(np.array([total]))[0])
 
-    def _apply_observable(self, terms, src: str, dst: str, tmp: str):
-        """dst <- O src, one Pauli string at a time through tmp."""
-        for v in self._vector(dst):
+    def _apply_observable(self, terms, src: str, dst: str, tmp: str, dtype=None):
+        """dst <- O src, one Pauli string at a time through tmp (the library's Pauli
+        gates on local bits, a global Z read as the shard's sign)."""
+        for v in self._vector(dst, dtype):
             v.zero()
-        self._vector(tmp)
+        self._vector(tmp, dtype)
         for batch in self._batches(list(terms)):
             for coeff, ops in batch:
                 for s, vt, vs, vd in zip(self.owned, self.vecs[tmp], self.vecs[src], self.vecs[dst]):
@@ -365,64 +381,49 @@ class ShardedState:
                             sign = -sign if (s >> (p - self.L)) & 1 else sign
                         else:
                             local.append((p, P))
-                    for c0 in range(0, len(local), 5):
-                        chunk = local[c0:c0 + 5]
-                        M = np.ones((1, 1), np.complex128)
-                        for p, P in chunk:
-                            M = np.kron(_PAULI[P], M)   # index bit j <-> chunk[j]
-                        vt.apply_matrix(M, [p for p, _ in chunk])
-                    vd.axpy(sign * float(coeff), vt)
+                    for p, P in local:
+                        vt.apply_pauli(p, P)
+                    vd.axpy(-float(coeff) if sign < 0 else float(coeff), vt)
 
     # ------------------------------------------------------------------ gradient
     def backward(self, circuit: "qsim.Circuit", params, terms):
         """expect'(O, reg => circuit): psi holds the circuit's output state; returns
-        (loss, gradient).  psi is uncomputed to the circuit's input state."""
+        (loss, gradient).  psi is uncomputed to the circuit's input state (for a
+        complex64 register, rounded back from the FP64 walk)."""
         params = np.asarray(params, dtype=np.float64)
         loss = self.expect(terms)
-        self._apply_observable(terms, "psi", "lam", "tmp")
-        grad = np.zeros(max(1, circuit.nparams))
+        wide = torch.complex128
+        work = "psi"
+        if self.dtype != wide:
+            work = "psiw"
+            for vw, vs in zip(self._vector(work, wide), self.vecs["psi"]):
+                vw.copy_from(vs)
+        self._apply_observable(terms, work, "lam", "tmp", dtype=wide)
+        self._drop("tmp")
+        grad = self.vecs[work][0].new_grad(circuit.nparams)
         for i in range(len(circuit.gates) - 1, -1, -1):
             g = circuit.gates[i]
-            if g.param is not None:
-                U, G, cfac = circuit.gate_matrices(i, params, generator=True)
-                nt, nc = len(g.locs), len(g.ctrl_locs)
-                if nt + nc > 5:
-                    raise ValueError("generator with its control projector spans more than 5 qubits")
-                # P_ctrl (x) H on (targets, controls): controls occupy the high index bits
-                proj = np.ones((1, 1), np.complex128)
-                for v in g.ctrl_vals:
-                    e = np.zeros((2, 2), np.complex128)
-                    e[int(v), int(v)] = 1.0
-                    proj = np.kron(e, proj)
-                Gf = np.kron(proj, G)
-                for vt, vs in zip(self.vecs["tmp"], self.vecs["psi"]):
-                    vt.copy_from(vs)
-                self.apply_matrix(Gf, list(g.locs) + list(g.ctrl_locs), (), None, vectors=("tmp",))
-                acc = 0.0
-                for vl, vt in zip(self.vecs["lam"], self.vecs["tmp"]):
-                    acc += vl.inner(vt).imag
-                grad[g.param] += 2.0 * cfac * acc
+            if g.param is not None and g.name != "MATRIX":
+                self._localize(list(g.locs))
+                for s, vp, vl in zip(self.owned, self.vecs[work], self.vecs["lam"]):
+                    ok, lc, lv = self._restrict(s, g.ctrl_locs, g.ctrl_vals)
+                    if not ok:
+                        continue  # identity on this shard, and its control projector is zero here
+                    local = dataclasses.replace(g, locs=tuple(self.pos[q] for q in g.locs),
+                                                ctrl_locs=tuple(lc), ctrl_vals=tuple(lv))
+                    vp.adjoint_step(vl, local, params, grad)
             else:
-                U = circuit.gate_matrices(i, params)
-            self.apply_matrix(U.conj().T, g.locs, g.ctrl_locs, g.ctrl_vals, vectors=("psi", "lam"))
-        self._drop("tmp")
+                Ud = qsim.gate_desc_matrices(g, params, dagger=True)
+                self.apply_matrix(Ud, g.locs, g.ctrl_locs, g.ctrl_vals, vectors=(work, "lam"))
+        grad = self._sum(self.vecs[work][0].grad_host(grad))
+        if work != "psi":
+            for vs, vw in zip(self.vecs["psi"], self.vecs[work]):
+                vs.copy_from(vw)
+            self._drop(work)
         self._drop("lam")
-        grad = self._sum(grad)
         return loss, grad[:circuit.nparams]
 
     # ------------------------------------------------------------------ measurement
-    @staticmethod
-    def _pick(weights: np.ndarray, t: np.ndarray):
-        """For each t: the first shard s whose left-fold prefix P_0 + .. + P_s passes
-        t, and the prefix before it (the last positive weight where rounding leaves
-        t at or beyond the total).  np.cumsum adds left to right, as the fold."""
-        pre = np.cumsum(weights)
-        s = np.searchsorted(pre, t, side="right")
-        pos = np.flatnonzero(weights > 0)
-        s[s >= len(weights)] = pos[-1] if len(pos) else len(weights) - 1
-        acc = np.where(s > 0, pre[np.maximum(s - 1, 0)], 0.0)
-        return s, acc
-
     def _logical(self, phys: np.ndarray) -> np.ndarray:
         x = np.zeros_like(phys)
         for q in range(self.n):
@@ -446,15 +447,7 @@ class ShardedState:
         for s, v in zip(self.owned, psi):
             w[s] = v.inner(v).real
         w = self._sum(w)
-        total = 0.0
-        for x in w:
-            total = total + x
-        t = u * total
-        pick, acc = self._pick(w, t)
-        ws = w[pick]
-        with np.errstate(divide="ignore", invalid="ignore"):
-            sub = np.where(ws > 0, (t - acc) / ws, 0.0)
-        sub = np.clip(sub, 0.0, np.nextafter(1.0, 0.0))
+        pick, sub = qsim.sample_shards(w, u)
         phys = np.zeros(len(u), np.float64)
         for s, v in zip(self.owned, psi):
             m = pick == s

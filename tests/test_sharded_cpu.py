@@ -73,6 +73,20 @@ class OracleShard:
     def measure(self, u):
         return oracle.sample(self.a, self.n, u)
 
+    def apply_pauli(self, p, P):
+        self.a[:] = oracle.apply_circuit(self.a, self.n, [W.Gate(P, (int(p),))])
+
+    def adjoint_step(self, lam, gate, params, grad):
+        oracle.adjoint_step(self.a, lam.a, self.n, gate, params, grad)
+
+    @staticmethod
+    def new_grad(nparams):
+        return np.zeros(max(1, nparams))
+
+    @staticmethod
+    def grad_host(buf):
+        return buf
+
 
 def mixed_circuit(n, seed):
     """Gates touching global qubits in every way the sharding distinguishes."""
