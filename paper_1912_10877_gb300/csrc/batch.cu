@@ -940,11 +940,15 @@ __device__ __noinline__ void batch_fwd_streamed(float2* sx, float2* st, const TP
   }
 }
 
+// CTAs per SM the register budget is sized for: narrow phases leave room for two
+template <int RB, bool PREC>
+constexpr int kBatchMinBlocks = (RB <= 3 && !PREC) ? 2 : 1;
+
 // Shared memory of k_batch after the BShared header: the complex64 path holds
 // psi and lambda tiles (2 x 2^13 x 8 bytes); the precise path holds double-float
 // psi and lambda tiles (2 x 2^m x 16 bytes) and a complex64 forward tile.
 template <int RB, bool PREC>
-__global__ void __launch_bounds__(kTileThreads, 1) k_batch(BArgs a) {
+__global__ void __launch_bounds__(kTileThreads, kBatchMinBlocks<RB, PREC>) k_batch(BArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   BShared& S = *reinterpret_cast<BShared*>(smraw);
   constexpr int MT = kTileThreads == 512 ? 9 + RB : 0;  // largest tile: 512 threads x 2^RB amplitudes

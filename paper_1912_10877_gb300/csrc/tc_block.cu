@@ -511,17 +511,25 @@ __global__ void __launch_bounds__(kBkThreads, 1) k_block_tc(const __grid_constan
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t a_hi = smem_u32(sm + L::a_hi(s)), a_lo = a_hi + A_BYTES;
         const uint32_t d = tmem + (uint32_t)(s * W);
+        // the small hi x lo and lo x hi terms first, then hi x hi: the MMA truncates
+        // its FP32 sum toward zero, so the large terms should pass through the
+        // accumulator as few times as possible (W / 8 instead of 3 W / 8)
 #pragma unroll
-        for (int ks = 0; ks < W / 8; ++ks) {
-          const uint32_t koff = (uint32_t)(ks & 3) * 32u;  // 8 tf32 = 32 bytes inside a 128-byte block
-          const uint32_t ablk = (uint32_t)(ks >> 2) * (uint32_t)(kTcRows * 128);
-          const uint32_t bblk = (uint32_t)(ks >> 2) * (uint32_t)(W * 128);
-          const uint64_t dah = sw128_desc(a_hi + ablk + koff), dal = sw128_desc(a_lo + ablk + koff);
-          const uint64_t dbh = sw128_desc(b_hi + bblk + koff), dbl = sw128_desc(b_lo + bblk + koff);
-          mma_tf32(d, dah, dbh, idesc, ks > 0 ? 1u : 0u);
-          mma_tf32(d, dah, dbl, idesc, 1u);
-          mma_tf32(d, dal, dbh, idesc, 1u);
-        }
+        for (int pass = 0; pass < 2; ++pass)
+#pragma unroll
+          for (int ks = 0; ks < W / 8; ++ks) {
+            const uint32_t koff = (uint32_t)(ks & 3) * 32u;  // 8 tf32 = 32 bytes inside a 128-byte block
+            const uint32_t ablk = (uint32_t)(ks >> 2) * (uint32_t)(kTcRows * 128);
+            const uint32_t bblk = (uint32_t)(ks >> 2) * (uint32_t)(W * 128);
+            const uint64_t dah = sw128_desc(a_hi + ablk + koff), dal = sw128_desc(a_lo + ablk + koff);
+            const uint64_t dbh = sw128_desc(b_hi + bblk + koff), dbl = sw128_desc(b_lo + bblk + koff);
+            if (pass == 0) {
+              mma_tf32(d, dah, dbl, idesc, ks > 0 ? 1u : 0u);
+              mma_tf32(d, dal, dbh, idesc, 1u);
+            } else {
+              mma_tf32(d, dah, dbh, idesc, 1u);
+            }
+          }
         mma_commit(empty(s));
         mma_commit(tfull(s));
         issued = true;
@@ -855,15 +863,21 @@ k_block_tma(const __grid_constant__ TmaArgs<K> ta, const __grid_constant__ CUten
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t d = tmem + (uint32_t)(s * W);
         const uint32_t ahi = tmem + L::a_col(s), alo = ahi + W;
+        // corrections first, then hi x hi (see k_block_tc)
 #pragma unroll
-        for (int ks = 0; ks < W / 8; ++ks) {
-          const uint32_t koff = (uint32_t)(ks & 3) * 32u;
-          const uint32_t bblk = (uint32_t)(ks >> 2) * (uint32_t)(W * 128);
-          const uint64_t dbh = sw128_desc(b_hi + bblk + koff), dbl = sw128_desc(b_lo + bblk + koff);
-          mma_tf32_ta(d, ahi + 8u * ks, dbh, idesc, ks > 0 ? 1u : 0u);
-          mma_tf32_ta(d, ahi + 8u * ks, dbl, idesc, 1u);
-          mma_tf32_ta(d, alo + 8u * ks, dbh, idesc, 1u);
-        }
+        for (int pass = 0; pass < 2; ++pass)
+#pragma unroll
+          for (int ks = 0; ks < W / 8; ++ks) {
+            const uint32_t koff = (uint32_t)(ks & 3) * 32u;
+            const uint32_t bblk = (uint32_t)(ks >> 2) * (uint32_t)(W * 128);
+            const uint64_t dbh = sw128_desc(b_hi + bblk + koff), dbl = sw128_desc(b_lo + bblk + koff);
+            if (pass == 0) {
+              mma_tf32_ta(d, ahi + 8u * ks, dbl, idesc, ks > 0 ? 1u : 0u);
+              mma_tf32_ta(d, alo + 8u * ks, dbh, idesc, 1u);
+            } else {
+              mma_tf32_ta(d, ahi + 8u * ks, dbh, idesc, 1u);
+            }
+          }
         mma_commit(aempty(s));
         mma_commit(tfull(s));
         issued = true;
@@ -1269,16 +1283,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const __grid_constant
         if (i % kGramGroup == 0 && !mbar_wait(tempty(b), ((uint32_t)(g >> 1) & 1u) ^ 1u, abort)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t d = tmem + (uint32_t)(b * 64);
+        // corrections first, then hi x hi (fewer truncating passes of the large terms)
 #pragma unroll
-        for (int ks = 0; ks < kTcRows / 8; ++ks) {
-          // 8 tuples per MMA: 32 bytes inside a 128-byte column block of 32 tuples
-          const uint32_t ko = (uint32_t)(ks >> 2) * (uint32_t)(kTcRows * 128) + (uint32_t)(ks & 3) * 32u;
-          const uint64_t ah = sw128_desc(base_hi + ko), al = sw128_desc(base_lo + ko);
-          const uint64_t bh = sw128_desc(base_hi + lam_off + ko), bl = sw128_desc(base_lo + lam_off + ko);
-          mma_tf32(d, ah, bh, idesc, (i % kGramGroup != 0 || ks > 0) ? 1u : 0u);
-          mma_tf32(d, ah, bl, idesc, 1u);
-          mma_tf32(d, al, bh, idesc, 1u);
-        }
+        for (int pass = 0; pass < 2; ++pass)
+#pragma unroll
+          for (int ks = 0; ks < kTcRows / 8; ++ks) {
+            // 8 tuples per MMA: 32 bytes inside a 128-byte column block of 32 tuples
+            const uint32_t ko = (uint32_t)(ks >> 2) * (uint32_t)(kTcRows * 128) + (uint32_t)(ks & 3) * 32u;
+            const uint64_t ah = sw128_desc(base_hi + ko), al = sw128_desc(base_lo + ko);
+            const uint64_t bh = sw128_desc(base_hi + lam_off + ko), bl = sw128_desc(base_lo + lam_off + ko);
+            if (pass == 0) {
+              mma_tf32(d, ah, bl, idesc, (i % kGramGroup != 0 || ks > 0) ? 1u : 0u);
+              mma_tf32(d, al, bh, idesc, 1u);
+            } else {
+              mma_tf32(d, ah, bh, idesc, 1u);
+            }
+          }
         mma_commit(empty);
         if (i % kGramGroup == kGramGroup - 1 || i == ntiles - 1) mma_commit(tfull(b));
         issued = true;
@@ -1549,14 +1569,17 @@ k_gram_tma(const __grid_constant__ CUtensorMap map_psi, const __grid_constant__ 
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t base_a = smem_u32(sm + L::op_a(s)), base_b = base_a + L::OP_BYTES;
         const uint32_t d = tmem + (uint32_t)(b * 64);
+        // the lambda_lo products first, then lambda_hi (fewer truncating passes of the large terms)
 #pragma unroll
-        for (int ks = 0; ks < GT / 8; ++ks) {
-          const uint32_t ko = (uint32_t)ks * (uint32_t)(kTcRows * 32);   // K step: 128 rows x 32 bytes
-          const uint64_t da = sw32_desc(base_a + ko);
-          const uint64_t bh = sw32_desc(base_b + ko), bl = sw32_desc(base_b + lo_off + ko);
-          mma_tf32(d, da, bh, idesc, (i % kGtGroup != 0 || ks > 0) ? 1u : 0u);
-          mma_tf32(d, da, bl, idesc, 1u);
-        }
+        for (int pass = 0; pass < 2; ++pass)
+#pragma unroll
+          for (int ks = 0; ks < GT / 8; ++ks) {
+            const uint32_t ko = (uint32_t)ks * (uint32_t)(kTcRows * 32);   // K step: 128 rows x 32 bytes
+            const uint64_t da = sw32_desc(base_a + ko);
+            const uint64_t bh = sw32_desc(base_b + ko), bl = sw32_desc(base_b + lo_off + ko);
+            if (pass == 0) mma_tf32(d, da, bl, idesc, (i % kGtGroup != 0 || ks > 0) ? 1u : 0u);
+            else mma_tf32(d, da, bh, idesc, 1u);
+          }
         mma_commit(op_empty(s));
         if (i % kGtGroup == kGtGroup - 1 || i == ntiles - 1) mma_commit(tfull(b));
         issued = true;
