@@ -380,6 +380,22 @@ int qs_circuit_tile_order(const qs_circuit* c, int tile_qubits, int* ngates, int
 #define QS_APPLY_BLOCK_QUBITS(k) ((k) << 16)
 int qs_apply_circuit(qs_state* s, const qs_circuit* c, const double* host_params, int flags);
 
+/* A whole circuit on one small register (n <= 24) in ONE kernel launch, for
+ * registers whose gate-by-gate launches cost more than their arithmetic: the
+ * circuit's blocks of at most kmax qubits (qs_circuit_blocks: dense matrices,
+ * controls inside the block) run back to back in a cooperative launch of
+ * grid_ctas CTAs (0 = one per SM), each block reading the state from one
+ * buffer and writing the other (every output amplitude of a tuple is a work
+ * item), with a grid barrier between blocks; complex128 in FP64, complex64 in
+ * FP32.  If o is not NULL (diagonal observables only: Z strings, at most 64
+ * terms) <O> is evaluated in the same launch (pairwise FP64 sums) into
+ * dev_out[0] (device).  Every grid-barrier wait is bounded; a wait that gives
+ * up leaves the state unspecified and makes the next qs_state_sync return
+ * QS_ETIMEDOUT.  Asynchronous on s's stream; uses s's scratch (a second state
+ * buffer and the block tables). */
+int qs_run_circuit_one_launch(qs_state* s, const qs_circuit* c, const double* host_params, int kmax,
+                              const qs_observable* o, int grid_ctas, double* dev_out);
+
 /* The k-qubit blocks QS_APPLY_BLOCKS applies (host only, no device work).
  * *nblocks receives their count.  If not NULL: host_widths[b] = block b's
  * qubit count; host_locs[b * QS_MAXK + j] = its qubits, ascending, padded

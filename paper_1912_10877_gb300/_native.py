@@ -104,6 +104,7 @@ SIGNATURES = {
     "qs_measure": ([_P, _PD, _I, _PI64, _I], _I),
     "qs_measure_seeded": ([_P, ctypes.c_uint64, _I, _PI64, _I], _I),
     "qs_adjoint_step": ([_P, _P, _P, _PD, _PD, _P], _I),
+    "qs_run_circuit_one_launch": ([_P, _P, _PD, _I, _P, _I, _P], _I),
     "qs_gate_desc_matrices": ([_P, _PD, _PD, _I, _PD, _PD, _PD], _I),
     "qs_sample_shards": ([_I, _PD, _I, _PD, _PI32, _PD], _I),
     "qs_batch_program_create": ([_I, _PP, _PP, _I, _PP], _I),

@@ -270,7 +270,8 @@ void set_tensor_cores(int on);
 int tensor_cores_enabled();
 bool use_block_tc(int dtype, const Plan& p);
 int launch_block_tc(float2* psi, int n, int nreg, const Plan& p, cudaStream_t st);
-int tc_status_take();  // QS_ETIMEDOUT (and clears it) if a tensor-core wait gave up
+int tc_status_take();  // QS_ETIMEDOUT (and clears it) if a bounded device wait gave up
+int tc_status_address(int** out);  // device address of that status word (current device)
 // real Gram matrix sum_x psi_x^T lambda_x of a 4/5-qubit support on the tensor cores
 // (interleaved re/im layout), per-CTA partials [grid][W][W]
 int gram_tc(int w, const float2* psi, const float2* lam, int n, const int* qubits, double* partials, int* grid_out,

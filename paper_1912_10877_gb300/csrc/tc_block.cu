@@ -1743,6 +1743,15 @@ int launch_block_tc(float2* psi, int n, int nreg, const Plan& p, cudaStream_t st
   return fail(QS_EUNSUPPORTED, "tensor-core blocks take 4 or 5 targets");
 }
 
+// device address of the status word on the current device, for kernels of
+// other files that report a bounded wait that gave up
+int tc_status_address(int** out) {
+  void* p = nullptr;
+  QS_CUDA(cudaGetSymbolAddress(&p, g_tc_status));
+  *out = (int*)p;
+  return QS_OK;
+}
+
 // reads and clears the device status word (synchronous)
 int tc_status_take() {
   int e = 0;
@@ -1750,7 +1759,7 @@ int tc_status_take() {
   if (e) {
     const int z = 0;
     QS_CUDA(cudaMemcpyToSymbol(g_tc_status, &z, sizeof(int)));
-    return fail(QS_ETIMEDOUT, "a tensor-core MMA completion wait gave up");
+    return fail(QS_ETIMEDOUT, "a bounded device-side wait (tensor-core pipeline or grid barrier) gave up");
   }
   return QS_OK;
 }

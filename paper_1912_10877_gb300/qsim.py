@@ -571,6 +571,20 @@ def backward_blocks(state: State, circuit: Circuit, params, obs: Observable, kma
     return float(loss[0]), grad[:circuit.nparams]
 
 
+def run_one_launch(state: State, circuit: Circuit, params=None, kmax: int = 4, obs: "Observable | None" = None,
+                   grid_ctas: int = 0, out: torch.Tensor | None = None):
+    """The whole circuit on one small register in a single cooperative launch
+    (qs_run_circuit_one_launch), with <obs> (diagonal) evaluated in the same launch into
+    `out` (a float64 CUDA tensor of one element, returned).  Asynchronous."""
+    p = _params_array(params, circuit.nparams)
+    if obs is not None and out is None:
+        out = torch.empty(1, dtype=torch.float64, device=state.device)
+    N.check(N.lib().qs_run_circuit_one_launch(state.handle, circuit.handle, N.dptr(p), int(kmax),
+                                              obs.handle if obs is not None else None, int(grid_ctas),
+                                              ctypes.c_void_p(out.data_ptr()) if out is not None else None))
+    return out
+
+
 class CapturedCircuit:
     """One apply of `circuit` (fixed parameters and flags) on `state`, recorded as a
     CUDA graph and replayed with a single launch: the remedy for launch-bound
