@@ -940,9 +940,10 @@ __device__ __noinline__ void batch_fwd_streamed(float2* sx, float2* st, const TP
   }
 }
 
-// CTAs per SM the register budget is sized for: narrow phases leave room for two
+// CTAs per SM the register budget is sized for (two CTAs of 3-qubit phases, at
+// 64 registers a thread, spilled and measured slower: 247 vs 213 ms per batch)
 template <int RB, bool PREC>
-constexpr int kBatchMinBlocks = (RB <= 3 && !PREC) ? 2 : 1;
+constexpr int kBatchMinBlocks = 1;
 
 // Shared memory of k_batch after the BShared header: the complex64 path holds
 // psi and lambda tiles (2 x 2^13 x 8 bytes); the precise path holds double-float

@@ -1,8 +1,9 @@
 """GPU parity of the reversible backward over k-qubit blocks (qs_backward_blocks)
 against the oracle's reversible-adjoint gradient and loss: complex128 within
-1e-10 relative (max-norm), complex64 within 2e-5 relative at n = 9 and 1e-4
-at n = 20 (FP32 states through the forward blocks and their adjoints, as in
-the FP32 tiled backward; measured 2.2e-5), FP64 sums; block widths 1..5; controlled
+1e-10 relative (max-norm), complex64 within 2e-5 relative at n = 9 (measured
+3.0e-6 with 5-qubit tensor-core blocks, 6.4e-7 without) and 3e-5 at n = 20
+(FP32 states through the forward blocks and their adjoints on the tensor
+cores; measured 7.2e-6), FP64 sums; block widths 1..5; controlled
 rotations, shift and phase gates, multi-qubit Pauli rotations and a shared
 parameter; the state is uncomputed to the circuit's input."""
 import numpy as np
@@ -99,7 +100,7 @@ def test_block_gradient_n20_against_fp64_adjoint(qs):
     loss, grad = qs.backward_blocks(st, circ, params, obs, kmax=5)
     print(f"block gradient n=20 vs FP64 adjoint: {rel(grad, wg):.2e}")
     assert abs(loss - wl) < 1e-5
-    assert rel(grad, wg) < 1e-4, rel(grad, wg)
+    assert rel(grad, wg) < 3e-5, rel(grad, wg)  # measured on GB300: 7.2e-6
 
 
 @pytest.mark.parametrize("kmax", [4, 5])
@@ -146,4 +147,4 @@ def test_block_gradient_tensor_core_gram_many_groups(qs):
     qs.set_tensor_cores(1)
     print(f"block gradient n=24 tensor vs CUDA cores: {rel(out[1][1], out[0][1]):.2e}")
     assert abs(out[1][0] - out[0][0]) < 1e-5
-    assert rel(out[1][1], out[0][1]) < 1e-4, rel(out[1][1], out[0][1])
+    assert rel(out[1][1], out[0][1]) < 1.5e-5, rel(out[1][1], out[0][1])  # measured on GB300: 4.2e-6

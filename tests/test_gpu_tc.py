@@ -210,5 +210,7 @@ def test_tensor_core_block_norm_drift(qs, record_property):
     qs.set_tensor_cores(1)
     record_property("norm_drift_per_block", drift)
     print("norm drift per 5-qubit block:", {k: f"{v:.2e}" for k, v in drift.items()})
+    # measured on GB300: tensor cores -3.1e-7 per block (-8.9e-7 before the correction MMAs
+    # were issued first), CUDA cores 1.7e-9
     assert abs(drift["mode0_q0"]) < 1e-7
-    assert all(abs(v) < 1e-5 for v in drift.values())
+    assert all(abs(v) < 1e-6 for v in drift.values())
