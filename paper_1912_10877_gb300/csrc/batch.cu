@@ -107,10 +107,15 @@ __device__ __forceinline__ float imcj(float2 p, float2 q) { return fmaf(p.x, q.y
 __device__ __forceinline__ float recj(float2 p, float2 q) { return fmaf(p.x, q.x, p.y * q.y); }   // Re(conj(p) q)
 
 // (a, b) <- U (a, b) for the structured kinds; U row-major in u0..u3
+// a diagonal whose first entry is exactly 1 (shift, controlled phases): only b changes
+constexpr int TK_DIAGB = 16;
+
 template <int KIND>
 __device__ __forceinline__ void pair_apply(float2& a, float2& b, float2 u0, float2 u1, float2 u2, float2 u3) {
   if (KIND == TK_SWAP) {
     const float2 t = a; a = b; b = t;
+  } else if (KIND == TK_DIAGB) {
+    b = cmulf(b, u3);
   } else if (KIND == TK_DIAG) {
     a = cmulf(a, u0);
     b = cmulf(b, u3);
@@ -185,13 +190,22 @@ __device__ __forceinline__ void op_fwd_k(float2 (&x)[1 << RB], const TOp& op, co
     }
     return;
   }
+  const bool one0 = op.u[0].x == 1.f && op.u[0].y == 0.f;  // uniform across the CTA
   if (op.kind == TK_SWAP) op_fwd<RB, T, TK_SWAP, true>(x, op);
   else if (op.cmask == 0) {
-    if (op.kind == TK_DIAG) op_fwd<RB, T, TK_DIAG, false>(x, op);
-    else op_fwd<RB, T, TK_DENSE, false>(x, op);
+    if (op.kind == TK_DIAG) {
+      if (one0) op_fwd<RB, T, TK_DIAGB, false>(x, op);
+      else op_fwd<RB, T, TK_DIAG, false>(x, op);
+    } else {
+      op_fwd<RB, T, TK_DENSE, false>(x, op);
+    }
   } else {
-    if (op.kind == TK_DIAG) op_fwd<RB, T, TK_DIAG, true>(x, op);
-    else op_fwd<RB, T, TK_DENSE, true>(x, op);
+    if (op.kind == TK_DIAG) {
+      if (one0) op_fwd<RB, T, TK_DIAGB, true>(x, op);
+      else op_fwd<RB, T, TK_DIAG, true>(x, op);
+    } else {
+      op_fwd<RB, T, TK_DENSE, true>(x, op);
+    }
   }
 }
 
@@ -607,6 +621,8 @@ __device__ __noinline__ void run_phase_fwd(float2* sm, const TPhase* php, const 
 #pragma unroll
           for (int j = 0; j < A; ++j)
             if ((j & cur.cmask) == cur.cval) x[j] = cf_mul(x[j], f, fl);
+        } else if (f.x == 1.f && f.y == 0.f) {
+          // a factor of exactly 1 (the |0> entry of a shift or controlled phase)
         } else if (cur.cmask == 0) {
           pend = cmulf(pend, f);
           has_pend = true;

@@ -99,6 +99,32 @@ __device__ bool ol_barrier(OLSync* s, unsigned& gen) {
   return ok != 0;
 }
 
+// one block: every output amplitude of every tuple is a work item (row r of the
+// block matrix times the tuple); the tuple's loads are issued together
+template <typename T, int K>
+__device__ __forceinline__ void ol_block(const OLBlock& B, const T* __restrict__ M, const T* src, T* dst,
+                                         uint64_t gtid, uint64_t gstride) {
+  constexpr int D = 1 << K;
+  uint32_t off[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) off[j] = B.off[j];
+  const uint64_t items = B.ntuples << K;
+  for (uint64_t it = gtid; it < items; it += gstride) {
+    const uint64_t t = it >> K;
+    const int r = (int)(it & (uint64_t)(D - 1));
+    const uint64_t base = item_index(t, B.spec);
+    // state loads bypass L1 (ld.global.cg): a buffer read two blocks ago may
+    // still sit in this SM's L1 while other SMs have rewritten it since
+    T x[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) x[j] = __ldcg(src + base + off[j]);
+    T acc = cmk<T>(0, 0);
+#pragma unroll
+    for (int j = 0; j < D; ++j) acc = cfma(__ldg(M + r * D + j), x[j], acc);
+    dst[base + off[r]] = acc;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kOLThreads) k_onelaunch(const __grid_constant__ OLArgs a) {
   T* src = reinterpret_cast<T*>(a.psi);
@@ -109,16 +135,13 @@ __global__ void __launch_bounds__(kOLThreads) k_onelaunch(const __grid_constant_
   const uint64_t gstride = (uint64_t)gridDim.x * blockDim.x;
   for (int b = 0; b < a.nblocks; ++b) {
     const OLBlock& B = a.blocks[b];
-    const int k = B.k, D = 1 << k;
-    const uint64_t items = B.ntuples << k;
     const T* M = mats + B.mat;
-    for (uint64_t it = gtid; it < items; it += gstride) {
-      const uint64_t t = it >> k;
-      const int r = (int)(it & (uint64_t)(D - 1));
-      const uint64_t base = item_index(t, B.spec);
-      T acc = cmk<T>(0, 0);
-      for (int j = 0; j < D; ++j) acc = cfma(M[r * D + j], src[base + B.off[j]], acc);
-      dst[base + B.off[r]] = acc;
+    switch (B.k) {
+      case 1: ol_block<T, 1>(B, M, src, dst, gtid, gstride); break;
+      case 2: ol_block<T, 2>(B, M, src, dst, gtid, gstride); break;
+      case 3: ol_block<T, 3>(B, M, src, dst, gtid, gstride); break;
+      case 4: ol_block<T, 4>(B, M, src, dst, gtid, gstride); break;
+      default: ol_block<T, 5>(B, M, src, dst, gtid, gstride); break;
     }
     if (!ol_barrier(a.sync, gen)) return;
     T* w = src;
@@ -127,7 +150,7 @@ __global__ void __launch_bounds__(kOLThreads) k_onelaunch(const __grid_constant_
   }
   // the result is in src: bring it to the register's buffer when it ended in the other
   if (src != reinterpret_cast<T*>(a.psi)) {
-    for (uint64_t i = gtid; i < a.dim; i += gstride) dst[i] = src[i];
+    for (uint64_t i = gtid; i < a.dim; i += gstride) dst[i] = __ldcg(src + i);
     if (!ol_barrier(a.sync, gen)) return;
     src = dst;
   }
@@ -137,7 +160,7 @@ __global__ void __launch_bounds__(kOLThreads) k_onelaunch(const __grid_constant_
   for (uint64_t i = gtid; i < a.dim; i += gstride) {
     double w = 0.0;
     for (int t = 0; t < a.nterm; ++t) w += (__popcll(i & a.z[t]) & 1) ? -a.coeff[t] : a.coeff[t];
-    const T v = src[i];
+    const T v = __ldcg(src + i);
     e += w * ((double)v.x * (double)v.x + (double)v.y * (double)v.y);
   }
   for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
@@ -152,7 +175,7 @@ __global__ void __launch_bounds__(kOLThreads) k_onelaunch(const __grid_constant_
   if (blockIdx.x == 0) {
     // pairwise over the CTA partials (gridDim.x <= 2 x kOLThreads)
     __shared__ double buf[2 * kOLThreads];
-    for (int i = threadIdx.x; i < 2 * kOLThreads; i += blockDim.x) buf[i] = i < (int)gridDim.x ? a.partials[i] : 0.0;
+    for (int i = threadIdx.x; i < 2 * kOLThreads; i += blockDim.x) buf[i] = i < (int)gridDim.x ? __ldcg(a.partials + i) : 0.0;
     __syncthreads();
     for (int w = kOLThreads; w > 0; w >>= 1) {
       for (int i = threadIdx.x; i < w; i += blockDim.x) buf[i] = buf[i] + buf[i + w];
