@@ -656,6 +656,46 @@ def run_small_leg(reps: int = 50):
             "gates": len(gates), "expectation": e, "expectation_one_launch": e1, "higher_is_better": False}
 
 
+def run_sharded_leg(n: int = 24, nglobal: int = 2, depth: int = 4):
+    """The qubit-sharded register on one GPU (all 2^g shards in this process, exchanges as
+    device copies): the variational circuit forward, <sum ZZ + sum X> and the reversible
+    gradient (complex128 working copies, one library adjoint step per gate and shard),
+    against the same work on one unsharded complex64 register (per-gate FP64 adjoint)."""
+    import torch
+    from paper_1912_10877_gb300 import qsim
+    from paper_1912_10877_gb300.sharded import ShardedState
+    gates, params = W.variational(n, depth, "ring", seed=0)
+    terms = W.tfim(n)
+    circ = qsim.Circuit(gates, n)
+
+    def sharded():
+        sh = ShardedState(n, nglobal, torch.complex64)
+        sh.apply_circuit(circ, params)
+        loss, grad = sh.backward(circ, params, terms)
+        torch.cuda.synchronize()
+        return sh.exchanges
+
+    def plain():
+        st = qsim.State(n, dtype=torch.complex64)
+        st.reset()
+        st.apply_circuit(circ, params, fused=False)
+        qsim.backward(st, circ, params, qsim.Observable(terms))
+        torch.cuda.synchronize()
+
+    sharded()
+    plain()
+    t0 = time.perf_counter()
+    ex = sharded()
+    ts = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    plain()
+    tp = time.perf_counter() - t0
+    return {"metric": f"qubit-sharded register fwd+grad seconds (n={n}, {1 << nglobal} shards, one GPU)", "unit": "s",
+            "value": round(ts, 4), "unsharded_s": round(tp, 4), "exchanges": ex, "gates": len(gates),
+            "params": len(params), "higher_is_better": False,
+            "note": "host wall clock; shards exchange halves by device copies in one process"}
+
+
 def run_matrix_leg(n: int = 20, reps: int = 5):
     """mat(heisenberg(n)) (periodic) as a CSR matrix on the device: row pointers (count +
     scan) and the fill, timed together; the paper reports 6.33 s for n = 20 on a laptop."""
@@ -932,7 +972,8 @@ def main():
     ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--no-matrix", action="store_true")
     ap.add_argument("--no-sizes", action="store_true")
-    ap.add_argument("--leg", default="all", choices=["all", "tc", "batch", "diff", "large", "tiles", "small", "matrix", "sizes"],
+    ap.add_argument("--leg", default="all",
+                    choices=["all", "tc", "batch", "diff", "large", "tiles", "small", "matrix", "sizes", "sharded"],
                     help="run one secondary leg alone and print its JSON (profiling captures)")
     ap.add_argument("--tc-reps", type=int, default=20, help="timed launches per tensor-core configuration")
     ap.add_argument("--reps", type=int, default=REPS, help="repetitions per gate (profiling runs use 1)")
@@ -981,7 +1022,8 @@ def main():
                                                world=world, rank=rank),
                 "diff": lambda: run_diff_leg(1, 1), "large": lambda: run_large_leg(1, 1),
                 "tiles": lambda: run_tiles_leg(), "small": lambda: run_small_leg(),
-                "matrix": lambda: run_matrix_leg(), "sizes": lambda: run_sizes_leg(hbm_peak=hbm_peak)}
+                "matrix": lambda: run_matrix_leg(), "sizes": lambda: run_sizes_leg(hbm_peak=hbm_peak),
+                "sharded": lambda: run_sharded_leg()}
         out = legs[args.leg]()
         if rank == 0:
             print(json.dumps(out))
@@ -1040,6 +1082,7 @@ def main():
         extra["small"] = run_small_leg()
     if solo and not args.no_matrix:
         extra["matrix"] = run_matrix_leg()
+        extra["sharded"] = run_sharded_leg()
     if solo and not args.no_sizes:
         extra["single_gate_sizes"] = run_sizes_leg(hbm_peak=hbm_peak)
     if not args.no_large and solo:
