@@ -109,6 +109,8 @@ __device__ __forceinline__ void ol_block(const OLBlock& B, const T* __restrict__
 #pragma unroll
   for (int j = 0; j < D; ++j) off[j] = B.off[j];
   const uint64_t items = B.ntuples << K;
+  // items are dealt to the CTAs in turn, so that a block of a few thousand items
+  // reaches every SM's FP64 units, not the first few CTAs only
   for (uint64_t it = gtid; it < items; it += gstride) {
     const uint64_t t = it >> K;
     const int r = (int)(it & (uint64_t)(D - 1));
@@ -131,7 +133,7 @@ __global__ void __launch_bounds__(kOLThreads) k_onelaunch(const __grid_constant_
   T* dst = reinterpret_cast<T*>(a.tmp);
   const T* mats = reinterpret_cast<const T*>(a.mats);
   unsigned gen = 0;
-  const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t gtid = (uint64_t)threadIdx.x * gridDim.x + blockIdx.x;  // CTA-interleaved work items
   const uint64_t gstride = (uint64_t)gridDim.x * blockDim.x;
   for (int b = 0; b < a.nblocks; ++b) {
     const OLBlock& B = a.blocks[b];

@@ -176,3 +176,27 @@ def test_large_pipeline_blocks_n32_light_cone_oracle(qs, record_property):
     assert abs(loss - rl) < 5e-6
     assert err_grad < 1.5e-4
     assert err_back < 7e-5
+
+
+@pytest.mark.parametrize("tc", [1, 0])
+def test_large_pipeline_n22_fp64_block_backward(qs, tc, record_property):
+    # the benchmark spec's split: complex64 forward (QFT on tiles, brickwork as 5-qubit blocks),
+    # then the reversible backward over the same blocks with psi and lambda in FP64 (the final
+    # state widened to complex128, FP64 block adjoints and Grams)
+    n = 22
+    qs.set_tensor_cores(tc)
+    try:
+        x, bgates, bparams, st, bcirc = bench_pipeline(qs, n)
+        st.apply_circuit(bcirc, bparams, blocks=5)
+        wide = qs.State(n, dtype=torch.complex128)
+        wide.copy_from(st)
+        loss, grad = qs.backward_blocks(wide, bcirc, bparams, qs.Observable(W.z_on(0)), kmax=5)
+    finally:
+        qs.set_tensor_cores(1)
+    psi0 = oracle.apply_circuit(oracle.basis_state(n, x), n, W.qft(n, swaps=True))
+    rl, rg = oracle.gradient(psi0, n, bgates, bparams, W.z_on(0))
+    err = rel(grad, rg)
+    record_property("grad_rel", err)
+    print(f"n=22 complex64 forward (tensor cores {tc}) + FP64 block backward: loss {abs(loss - rl):.2e} grad {err:.2e}")
+    assert abs(loss - rl) < 1e-5
+    assert err < (1e-4 if tc else 5e-6)
