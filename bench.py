@@ -696,6 +696,41 @@ def run_sharded_leg(n: int = 24, nglobal: int = 2, depth: int = 4):
             "note": "host wall clock; shards exchange halves by device copies in one process"}
 
 
+def run_faithful_leg(n: int = 10, depth: int = 4, nshots: int = 1024):
+    """Shot-based faithful gradients (Eq. shiftrule) of the transverse-field Ising energy for
+    the n = 10 variational circuit: 2P shifted circuits run as one batch (complex64, the
+    batched engine), each sampled nshots times per measurement-basis group; and the MMD
+    loss gradient of the same circuit's Born distribution against a seeded target."""
+    import torch
+    from paper_1912_10877_gb300 import qsim
+    gates, params = W.variational(n, depth, "ladder", seed=0)
+    circ = qsim.Circuit(gates, n)
+    obs = qsim.Observable(W.tfim(n))
+    P = len(params)
+    G = qsim.observable_groups(obs)
+    u = W.rng(5).random((G, 2 * P, nshots))
+    um = W.rng(6).random((2 * P + 1, nshots))
+    target = W.rng(7).random(1 << n)
+    target /= target.sum()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    t_shot = timed(lambda: qsim.faithful_gradient(circ, params, obs, dtype=torch.complex64, nshots=nshots, uniforms=u))
+    t_exact = timed(lambda: qsim.faithful_gradient(circ, params, obs, dtype=torch.complex64))
+    t_mmd = timed(lambda: qsim.mmd_gradient(circ, params, target, 2.0, dtype=torch.complex64, nshots=nshots,
+                                            uniforms=um))
+    return {"metric": f"faithful (parameter-shift) gradient seconds, n={n}, {P} parameters", "unit": "s",
+            "value": round(t_shot, 4), "exact_expectation_s": round(t_exact, 4), "mmd_shots_s": round(t_mmd, 4),
+            "shots_per_circuit": nshots, "groups": G, "shifted_circuits": 2 * P, "higher_is_better": False,
+            "note": "host wall clock around one call (launches, sampling and the host reduction included)"}
+
+
 def run_matrix_leg(n: int = 20, reps: int = 5):
     """mat(heisenberg(n)) (periodic) as a CSR matrix on the device: row pointers (count +
     scan) and the fill, timed together; the paper reports 6.33 s for n = 20 on a laptop."""
@@ -940,6 +975,10 @@ def summary_of(line: dict) -> dict:
     sm = line.get("small")
     if isinstance(sm, dict):
         out["small_us"] = sm.get("value")
+    for k in ("sharded", "faithful", "matrix"):
+        v = line.get(k)
+        if isinstance(v, dict):
+            out[f"{k}_s"] = v.get("value")
     cb = line.get("cpu_baseline_configs")
     if isinstance(cb, dict):
         out["oracle"] = {k: v.get("value") for k, v in cb.items()}
@@ -973,7 +1012,8 @@ def main():
     ap.add_argument("--no-matrix", action="store_true")
     ap.add_argument("--no-sizes", action="store_true")
     ap.add_argument("--leg", default="all",
-                    choices=["all", "tc", "batch", "diff", "large", "tiles", "small", "matrix", "sizes", "sharded"],
+                    choices=["all", "tc", "batch", "diff", "large", "tiles", "small", "matrix", "sizes", "sharded",
+                             "faithful"],
                     help="run one secondary leg alone and print its JSON (profiling captures)")
     ap.add_argument("--tc-reps", type=int, default=20, help="timed launches per tensor-core configuration")
     ap.add_argument("--reps", type=int, default=REPS, help="repetitions per gate (profiling runs use 1)")
@@ -1023,7 +1063,7 @@ def main():
                 "diff": lambda: run_diff_leg(1, 1), "large": lambda: run_large_leg(1, 1),
                 "tiles": lambda: run_tiles_leg(), "small": lambda: run_small_leg(),
                 "matrix": lambda: run_matrix_leg(), "sizes": lambda: run_sizes_leg(hbm_peak=hbm_peak),
-                "sharded": lambda: run_sharded_leg()}
+                "sharded": lambda: run_sharded_leg(), "faithful": lambda: run_faithful_leg()}
         out = legs[args.leg]()
         if rank == 0:
             print(json.dumps(out))
@@ -1083,6 +1123,7 @@ def main():
     if solo and not args.no_matrix:
         extra["matrix"] = run_matrix_leg()
         extra["sharded"] = run_sharded_leg()
+        extra["faithful"] = run_faithful_leg()
     if solo and not args.no_sizes:
         extra["single_gate_sizes"] = run_sizes_leg(hbm_peak=hbm_peak)
     if not args.no_large and solo:
