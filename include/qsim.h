@@ -164,7 +164,8 @@ int qs_state_axpy(qs_state* y, double alpha_re, double alpha_im, const qs_state*
  * size, for a caller that walks a circuit itself with other work in between
  * (a register split over processes exchanges shard halves between gates).
  * g's targets and controls are qubits of these registers.  A parameterised
- * gate U = exp(-i theta c H) (RX, RY, RZ, SHIFT, PHASE, ROT) first adds
+ * gate U = exp(-i theta c H) (RX, RY, RZ, SHIFT, PHASE, ROT on at most 3
+ * targets; QS_EUNSUPPORTED beyond) first adds
  * 2 c Im<lambda|(P_ctrl (x) H)|psi> to dev_grad[g->param] (device memory,
  * FP64, added in stream order: no synchronisation), P_ctrl the projector onto
  * the control values; then psi <- U^dag psi and lambda <- U^dag lambda in
