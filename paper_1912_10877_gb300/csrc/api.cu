@@ -396,6 +396,7 @@ int qs_circuit_create(int nqubits, const qs_gate_desc* gates, int ngates, const 
 int qs_circuit_destroy(qs_circuit* c) {
   if (c && c->fused) free_fused(c->fused);
   if (c) free_blocks(c);
+  if (c) free_onelaunch(c);
   delete c;
   return QS_OK;
 }

@@ -203,6 +203,9 @@ struct qs_circuit {
   // k-qubit block plan of this circuit (built on first block apply)
   mutable void* blocks = nullptr;
   mutable int block_k = 0;
+  // device tables of the one-launch path (built on first use, rebuilt when the
+  // block width, dtype, device or parameters change)
+  mutable void* onelaunch = nullptr;
 };
 
 struct qs_observable {
@@ -272,6 +275,7 @@ bool use_block_tc(int dtype, const Plan& p);
 int launch_block_tc(float2* psi, int n, int nreg, const Plan& p, cudaStream_t st);
 int tc_status_take();  // QS_ETIMEDOUT (and clears it) if a bounded device wait gave up
 int tc_status_address(int** out);  // device address of that status word (current device)
+void free_onelaunch(const qs_circuit* c);  // releases the one-launch tables of a circuit
 // real Gram matrix sum_x psi_x^T lambda_x of a 4/5-qubit support on the tensor cores
 // (interleaved re/im layout), per-CTA partials [grid][W][W]
 int gram_tc(int w, const float2* psi, const float2* lam, int n, const int* qubits, double* partials, int* grid_out,

@@ -37,6 +37,8 @@ struct OLBlock {
   uint32_t off[1 << QS_MAXK];  // member offsets of a tuple
   int32_t k;                 // block width
   int32_t mat;               // offset (entries) of its 2^k x 2^k matrix
+  int32_t group;             // tuples a CTA takes at a time
+  int32_t pad;
   uint64_t ntuples;
 };
 
@@ -44,7 +46,6 @@ struct OLSync {
   unsigned count;
   unsigned gen;
   int error;
-  int* status;               // the library's device status word (qs_state_sync reports it)
 };
 
 struct OLArgs {
@@ -55,6 +56,7 @@ struct OLArgs {
   int nblocks;
   uint64_t dim;
   OLSync* sync;
+  int* status;               // the library's device status word (qs_state_sync reports it)
   double* partials;          // [gridDim.x] when an observable is given
   double* out;               // <O> (device)
   int nterm;
@@ -69,7 +71,7 @@ __device__ __forceinline__ uint64_t ol_clock() {
 }
 
 // all CTAs arrive; returns false (for every CTA) once any wait has given up
-__device__ bool ol_barrier(OLSync* s, unsigned& gen) {
+__device__ bool ol_barrier(OLSync* s, int* status, unsigned& gen) {
   __syncthreads();
   __shared__ int ok;
   if (threadIdx.x == 0) {
@@ -85,7 +87,7 @@ __device__ bool ol_barrier(OLSync* s, unsigned& gen) {
       while (atomicAdd(&s->gen, 0u) == g) {
         if (++spins > (1l << 24) || ol_clock() - t0 > 2000000000ull || atomicAdd(&s->error, 0) != 0) {
           atomicExch(&s->error, 1);
-          atomicExch(s->status, 1);
+          atomicExch(status, 1);
           break;
         }
         __nanosleep(64);
@@ -99,31 +101,40 @@ __device__ bool ol_barrier(OLSync* s, unsigned& gen) {
   return ok != 0;
 }
 
-// one block: every output amplitude of every tuple is a work item (row r of the
-// block matrix times the tuple); the tuple's loads are issued together
+// one block: a CTA takes G tuples at a time (G = B.group, a power of two with
+// G x 2^K <= the CTA's threads); thread (lt, r) loads member r of local tuple
+// lt into shared memory, then computes output row r of that tuple from the
+// shared copy.  G is chosen on the host so that the block's tuples spread over
+// every CTA (FP64 work reaches every SM's units) before they fill a CTA.
 template <typename T, int K>
 __device__ __forceinline__ void ol_block(const OLBlock& B, const T* __restrict__ M, const T* src, T* dst,
-                                         uint64_t gtid, uint64_t gstride) {
+                                         T* xs) {
   constexpr int D = 1 << K;
-  uint32_t off[D];
+  const int G = B.group;
+  const int lt = (int)threadIdx.x >> K, r = (int)threadIdx.x & (D - 1);
+  const bool active = lt < G;
+  const uint32_t offr = B.off[r];
+  T row[D];
+  if (active) {
 #pragma unroll
-  for (int j = 0; j < D; ++j) off[j] = B.off[j];
-  const uint64_t items = B.ntuples << K;
-  // items are dealt to the CTAs in turn, so that a block of a few thousand items
-  // reaches every SM's FP64 units, not the first few CTAs only
-  for (uint64_t it = gtid; it < items; it += gstride) {
-    const uint64_t t = it >> K;
-    const int r = (int)(it & (uint64_t)(D - 1));
-    const uint64_t base = item_index(t, B.spec);
+    for (int j = 0; j < D; ++j) row[j] = __ldg(M + r * D + j);
+  }
+  for (uint64_t t0 = (uint64_t)blockIdx.x * G; t0 < B.ntuples; t0 += (uint64_t)gridDim.x * G) {
+    const uint64_t t = t0 + lt;
+    const bool on = active && t < B.ntuples;
+    const uint64_t base = on ? item_index(t, B.spec) : 0;
     // state loads bypass L1 (ld.global.cg): a buffer read two blocks ago may
     // still sit in this SM's L1 while other SMs have rewritten it since
-    T x[D];
+    if (on) xs[threadIdx.x] = __ldcg(src + base + offr);
+    __syncthreads();
+    if (on) {
+      const T* x = xs + (lt << K);
+      T acc = cmk<T>(0, 0);
 #pragma unroll
-    for (int j = 0; j < D; ++j) x[j] = __ldcg(src + base + off[j]);
-    T acc = cmk<T>(0, 0);
-#pragma unroll
-    for (int j = 0; j < D; ++j) acc = cfma(__ldg(M + r * D + j), x[j], acc);
-    dst[base + off[r]] = acc;
+      for (int j = 0; j < D; ++j) acc = cfma(row[j], x[j], acc);
+      dst[base + offr] = acc;
+    }
+    __syncthreads();
   }
 }
 
@@ -135,17 +146,18 @@ __global__ void __launch_bounds__(kOLThreads) k_onelaunch(const __grid_constant_
   unsigned gen = 0;
   const uint64_t gtid = (uint64_t)threadIdx.x * gridDim.x + blockIdx.x;  // CTA-interleaved work items
   const uint64_t gstride = (uint64_t)gridDim.x * blockDim.x;
+  __shared__ T xs[kOLThreads];
   for (int b = 0; b < a.nblocks; ++b) {
     const OLBlock& B = a.blocks[b];
     const T* M = mats + B.mat;
     switch (B.k) {
-      case 1: ol_block<T, 1>(B, M, src, dst, gtid, gstride); break;
-      case 2: ol_block<T, 2>(B, M, src, dst, gtid, gstride); break;
-      case 3: ol_block<T, 3>(B, M, src, dst, gtid, gstride); break;
-      case 4: ol_block<T, 4>(B, M, src, dst, gtid, gstride); break;
-      default: ol_block<T, 5>(B, M, src, dst, gtid, gstride); break;
+      case 1: ol_block<T, 1>(B, M, src, dst, xs); break;
+      case 2: ol_block<T, 2>(B, M, src, dst, xs); break;
+      case 3: ol_block<T, 3>(B, M, src, dst, xs); break;
+      case 4: ol_block<T, 4>(B, M, src, dst, xs); break;
+      default: ol_block<T, 5>(B, M, src, dst, xs); break;
     }
-    if (!ol_barrier(a.sync, gen)) return;
+    if (!ol_barrier(a.sync, a.status, gen)) return;
     T* w = src;
     src = dst;
     dst = w;
@@ -153,7 +165,7 @@ __global__ void __launch_bounds__(kOLThreads) k_onelaunch(const __grid_constant_
   // the result is in src: bring it to the register's buffer when it ended in the other
   if (src != reinterpret_cast<T*>(a.psi)) {
     for (uint64_t i = gtid; i < a.dim; i += gstride) dst[i] = __ldcg(src + i);
-    if (!ol_barrier(a.sync, gen)) return;
+    if (!ol_barrier(a.sync, a.status, gen)) return;
     src = dst;
   }
   if (a.nterm <= 0) return;
@@ -173,7 +185,7 @@ __global__ void __launch_bounds__(kOLThreads) k_onelaunch(const __grid_constant_
     static_assert(kOLThreads / 32 == 8, "CTA tree below is written for 8 warps");
     a.partials[blockIdx.x] = ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
   }
-  if (!ol_barrier(a.sync, gen)) return;
+  if (!ol_barrier(a.sync, a.status, gen)) return;
   if (blockIdx.x == 0) {
     // pairwise over the CTA partials (gridDim.x <= 2 x kOLThreads)
     __shared__ double buf[2 * kOLThreads];
@@ -185,6 +197,102 @@ __global__ void __launch_bounds__(kOLThreads) k_onelaunch(const __grid_constant_
     }
     if (threadIdx.x == 0) *a.out = buf[0];
   }
+}
+
+// device tables of one circuit's blocks for one block width, dtype, device and
+// parameter vector
+struct OLCache {
+  int kmax = 0, dtype = -1, device = -1, nb = 0;
+  std::vector<double> params;
+  std::vector<OLBlock> host_blocks;   // group fields set per launch
+  OLBlock* blocks = nullptr;          // device copy (rewritten when the groups change)
+  void* mats = nullptr;
+  int grid = -1;
+};
+
+void free_onelaunch(const qs_circuit* c) {
+  OLCache* k = static_cast<OLCache*>(c->onelaunch);
+  if (!k) return;
+  int cur = -1;
+  const bool swap = k->device >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != k->device &&
+                    cudaSetDevice(k->device) == cudaSuccess;
+  if (k->blocks) cudaFree(k->blocks);
+  if (k->mats) cudaFree(k->mats);
+  if (swap) cudaSetDevice(cur);
+  delete k;
+  c->onelaunch = nullptr;
+}
+
+// the circuit's blocks (matrices formed on the host) as device tables, reused
+// while the width, dtype, device and parameters stay the same
+static int onelaunch_tables(qs_state* s, const qs_circuit* c, const double* host_params, int kmax, OLCache** out) {
+  int dev = 0;
+  QS_CUDA(cudaGetDevice(&dev));
+  OLCache* k = static_cast<OLCache*>(c->onelaunch);
+  const int np = c->nparams;
+  if (k && k->kmax == kmax && k->dtype == s->dtype && k->device == dev && (int)k->params.size() == np &&
+      (np == 0 || std::memcmp(k->params.data(), host_params, sizeof(double) * np) == 0)) {
+    *out = k;
+    return QS_OK;
+  }
+  free_onelaunch(c);
+  const int n = c->nqubits;
+  int nb = 0;
+  QS_TRY(qs_circuit_blocks(c, host_params, kmax, &nb, nullptr, nullptr, nullptr));
+  std::vector<int32_t> widths(std::max(1, nb)), locs((size_t)std::max(1, nb) * QS_MAXK);
+  const size_t stride = (size_t)1 << (2 * QS_MAXK);
+  std::vector<double> mats((size_t)2 * stride * std::max(1, nb));
+  QS_TRY(qs_circuit_blocks(c, host_params, kmax, &nb, widths.data(), locs.data(), mats.data()));
+  const size_t ab = amp_bytes(s->dtype);
+  std::vector<OLBlock> blocks(nb);
+  std::vector<unsigned char> pool;
+  for (int b = 0; b < nb; ++b) {
+    OLBlock& B = blocks[b];
+    memset(&B, 0, sizeof(B));
+    const int w = widths[b], D = 1 << w;
+    if (w > QS_MAXK) return fail(QS_EUNSUPPORTED, "a gate spans more than %d qubits", QS_MAXK);
+    uint64_t mask = 0;
+    for (int j = 0; j < w; ++j) mask |= 1ull << locs[b * QS_MAXK + j];
+    QS_TRY(make_idx(n, mask, 0, &B.spec));
+    for (int m = 0; m < D; ++m) {
+      uint32_t off = 0;
+      for (int j = 0; j < w; ++j)
+        if ((m >> j) & 1) off |= 1u << locs[b * QS_MAXK + j];
+      B.off[m] = off;
+    }
+    B.k = w;
+    B.ntuples = 1ull << (n - w);
+    B.mat = (int32_t)(pool.size() / ab);
+    const double* M = mats.data() + 2 * stride * b;
+    const size_t at = pool.size();
+    pool.resize(at + ab * (size_t)D * D);
+    for (int i = 0; i < D * D; ++i) {
+      if (s->dtype == QS_C128) {
+        const double2 v = make_double2(M[2 * i], M[2 * i + 1]);
+        std::memcpy(pool.data() + at + ab * i, &v, sizeof(v));
+      } else {
+        const float2 v = make_float2((float)M[2 * i], (float)M[2 * i + 1]);
+        std::memcpy(pool.data() + at + ab * i, &v, sizeof(v));
+      }
+    }
+  }
+  k = new OLCache();
+  k->kmax = kmax;
+  k->dtype = s->dtype;
+  k->device = dev;
+  k->nb = nb;
+  k->params.assign(host_params ? host_params : nullptr, host_params ? host_params + np : nullptr);
+  k->host_blocks = blocks;
+  c->onelaunch = k;  // owned by the circuit from here (freed with it)
+  if (cudaMalloc((void**)&k->blocks, sizeof(OLBlock) * std::max(1, nb)) != cudaSuccess ||
+      cudaMalloc(&k->mats, std::max<size_t>(16, pool.size())) != cudaSuccess) {
+    cudaGetLastError();
+    free_onelaunch(c);
+    return fail(QS_ENOMEM, "cudaMalloc of the one-launch tables failed");
+  }
+  if (!pool.empty()) QS_CUDA(cudaMemcpy(k->mats, pool.data(), pool.size(), cudaMemcpyHostToDevice));
+  *out = k;
+  return QS_OK;
 }
 
 }  // namespace qs
@@ -214,73 +322,53 @@ int qs_run_circuit_one_launch(qs_state* s, const qs_circuit* c, const double* ho
       ++a.nterm;
     }
   }
-  // the circuit's fused blocks (targets and controls inside each block)
-  int nb = 0;
-  QS_TRY(qs_circuit_blocks(c, host_params, kmax, &nb, nullptr, nullptr, nullptr));
-  std::vector<int32_t> widths(std::max(1, nb)), locs((size_t)std::max(1, nb) * QS_MAXK);
-  const size_t stride = (size_t)1 << (2 * QS_MAXK);
-  std::vector<double> mats((size_t)2 * stride * std::max(1, nb));
-  QS_TRY(qs_circuit_blocks(c, host_params, kmax, &nb, widths.data(), locs.data(), mats.data()));
+  OLCache* k = nullptr;
+  QS_TRY(onelaunch_tables(s, c, host_params, kmax, &k));
+  const int nb = k->nb;
   const size_t ab = amp_bytes(s->dtype);
-  std::vector<OLBlock> blocks(nb);
-  std::vector<unsigned char> pool;
-  for (int b = 0; b < nb; ++b) {
-    OLBlock& B = blocks[b];
-    memset(&B, 0, sizeof(B));
-    const int k = widths[b], D = 1 << k;
-    if (k > QS_MAXK) return fail(QS_EUNSUPPORTED, "a gate spans more than %d qubits", QS_MAXK);
-    uint64_t mask = 0;
-    for (int j = 0; j < k; ++j) mask |= 1ull << locs[b * QS_MAXK + j];
-    QS_TRY(make_idx(n, mask, 0, &B.spec));
-    for (int m = 0; m < D; ++m) {
-      uint32_t off = 0;
-      for (int j = 0; j < k; ++j)
-        if ((m >> j) & 1) off |= 1u << locs[b * QS_MAXK + j];
-      B.off[m] = off;
-    }
-    B.k = k;
-    B.ntuples = 1ull << (n - k);
-    B.mat = (int32_t)(pool.size() / ab);
-    const double* M = mats.data() + 2 * stride * b;
-    for (int i = 0; i < D * D; ++i) {
-      if (s->dtype == QS_C128) {
-        const double2 v = make_double2(M[2 * i], M[2 * i + 1]);
-        pool.insert(pool.end(), (const unsigned char*)&v, (const unsigned char*)&v + sizeof(v));
-      } else {
-        const float2 v = make_float2((float)M[2 * i], (float)M[2 * i + 1]);
-        pool.insert(pool.end(), (const unsigned char*)&v, (const unsigned char*)&v + sizeof(v));
-      }
-    }
-  }
   // grid: every SM (or the caller's count), all CTAs resident (cooperative launch)
-  int dev = 0, sms = 0, per_sm = 0, coop = 0;
+  static int sms_of[64] = {0}, per_sm_of[2][64] = {{0}};
+  int dev = 0;
   QS_CUDA(cudaGetDevice(&dev));
-  QS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  QS_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-  if (!coop) return fail(QS_EUNSUPPORTED, "the device has no cooperative launch");
+  if (dev < 0 || dev >= 64) return fail(QS_EUNSUPPORTED, "device ordinal %d", dev);
   const void* fn = s->dtype == QS_C128 ? (const void*)k_onelaunch<double2> : (const void*)k_onelaunch<float2>;
-  QS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kOLThreads, 0));
+  if (!sms_of[dev]) {
+    int coop = 0;
+    QS_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) return fail(QS_EUNSUPPORTED, "the device has no cooperative launch");
+    QS_CUDA(cudaDeviceGetAttribute(&sms_of[dev], cudaDevAttrMultiProcessorCount, dev));
+  }
+  int& per_sm = per_sm_of[s->dtype == QS_C128 ? 1 : 0][dev];
+  if (!per_sm) QS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kOLThreads, 0));
+  const int sms = sms_of[dev];
   const int max_grid = std::min(sms * std::max(1, per_sm), 2 * kOLThreads);
   const int grid = grid_ctas > 0 ? std::min(grid_ctas, max_grid) : std::min(sms, max_grid);
-  // scratch: second state buffer | blocks | matrices | sync | partials | out
+  cudaStream_t st = s->stream;
+  if (k->grid != grid) {
+    // tuples per CTA at a time: as many as fill it, no more than spreads the block over every CTA
+    for (OLBlock& B : k->host_blocks) {
+      int g = 1;
+      while ((g << 1) * (1 << B.k) <= kOLThreads && (uint64_t)(g << 1) * (uint64_t)grid <= B.ntuples) g <<= 1;
+      B.group = g;
+    }
+    if (nb > 0)
+      QS_CUDA(cudaMemcpyAsync(k->blocks, k->host_blocks.data(), sizeof(OLBlock) * nb, cudaMemcpyHostToDevice, st));
+    k->grid = grid;
+  }
+  // scratch: second state buffer | sync | partials
   const uint64_t dim = 1ull << n;
   auto al = [](size_t x) { return (x + 255) / 256 * 256; };
-  const size_t o_tmp = 0, o_blk = al(ab * dim), o_mat = o_blk + al(sizeof(OLBlock) * std::max(1, nb)),
-               o_sync = o_mat + al(std::max<size_t>(16, pool.size())), o_part = o_sync + 256,
-               o_out = o_part + al(sizeof(double) * grid);
+  const size_t o_sync = al(ab * dim), o_part = o_sync + 256, o_out = o_part + al(sizeof(double) * grid);
   QS_TRY(ensure_ws(s, s->ws, o_out + 256));
   char* w = (char*)s->ws.ptr;
-  cudaStream_t st = s->stream;
-  if (nb > 0) QS_CUDA(cudaMemcpyAsync(w + o_blk, blocks.data(), sizeof(OLBlock) * nb, cudaMemcpyHostToDevice, st));
-  if (!pool.empty()) QS_CUDA(cudaMemcpyAsync(w + o_mat, pool.data(), pool.size(), cudaMemcpyHostToDevice, st));
-  OLSync sy;
-  memset(&sy, 0, sizeof(sy));
-  QS_TRY(tc_status_address(&sy.status));
-  QS_CUDA(cudaMemcpyAsync(w + o_sync, &sy, sizeof(OLSync), cudaMemcpyHostToDevice, st));
+  static int* status_of[64] = {nullptr};
+  if (!status_of[dev]) QS_TRY(tc_status_address(&status_of[dev]));
+  QS_CUDA(cudaMemsetAsync(w + o_sync, 0, sizeof(OLSync), st));
+  a.status = status_of[dev];
   a.psi = s->data;
-  a.tmp = w + o_tmp;
-  a.blocks = (const OLBlock*)(w + o_blk);
-  a.mats = w + o_mat;
+  a.tmp = w;
+  a.blocks = k->blocks;
+  a.mats = k->mats;
   a.nblocks = nb;
   a.dim = dim;
   a.sync = (OLSync*)(w + o_sync);
