@@ -128,11 +128,19 @@ __device__ __forceinline__ void ol_block(const OLBlock& B, const T* __restrict__
     if (on) xs[threadIdx.x] = __ldcg(src + base + offr);
     __syncthreads();
     if (on) {
+      // four independent partial sums: the FP64 multiply-add latency, not its
+      // rate, bounds one warp's chain of 4 x 2^K dependent operations
       const T* x = xs + (lt << K);
-      T acc = cmk<T>(0, 0);
+      T acc[4] = {cmk<T>(0, 0), cmk<T>(0, 0), cmk<T>(0, 0), cmk<T>(0, 0)};
 #pragma unroll
-      for (int j = 0; j < D; ++j) acc = cfma(row[j], x[j], acc);
-      dst[base + offr] = acc;
+      for (int j = 0; j < D; ++j) acc[j & 3] = cfma(row[j], x[j], acc[j & 3]);
+      T sum = acc[0];
+#pragma unroll
+      for (int q = 1; q < 4 && q < D; ++q) {
+        sum.x += acc[q].x;
+        sum.y += acc[q].y;
+      }
+      dst[base + offr] = sum;
     }
     __syncthreads();
   }
