@@ -101,23 +101,32 @@ __device__ bool ol_barrier(OLSync* s, int* status, unsigned& gen) {
   return ok != 0;
 }
 
-// one block: a CTA takes G tuples at a time (G = B.group, a power of two with
-// G x 2^K <= the CTA's threads); thread (lt, r) loads member r of local tuple
-// lt into shared memory, then computes output row r of that tuple from the
-// shared copy.  G is chosen on the host so that the block's tuples spread over
-// every CTA (FP64 work reaches every SM's units) before they fill a CTA.
+// one block: a CTA takes G tuples at a time (G = B.group); every output row of
+// a tuple is computed by kOLSplit threads, each summing a quarter of the row's
+// products, in different warps: one warp keeps only its own SM sub-partition's
+// FP64 unit busy, and a row split over four warps uses all four.  Thread
+// (lt, s, r) loads member r of local tuple lt (s = 0) into shared memory,
+// sums the products j = s (mod kOLSplit) of row r, and the s = 0 thread adds
+// the four partial sums and stores the row.  G is chosen on the host so that
+// the block's tuples spread over every CTA before they fill one.
+constexpr int kOLSplit = 4;
+
 template <typename T, int K>
 __device__ __forceinline__ void ol_block(const OLBlock& B, const T* __restrict__ M, const T* src, T* dst,
-                                         T* xs) {
+                                         T* xs, T* ps) {
   constexpr int D = 1 << K;
+  constexpr int S = D >= kOLSplit ? kOLSplit : D;   // partial sums per row
+  constexpr int TPT = S * D;                         // threads per tuple
+  constexpr int J = D / S;                           // products per thread
   const int G = B.group;
-  const int lt = (int)threadIdx.x >> K, r = (int)threadIdx.x & (D - 1);
+  const int lt = (int)threadIdx.x / TPT, rem = (int)threadIdx.x % TPT;
+  const int r = rem & (D - 1), sp = rem >> K;
   const bool active = lt < G;
   const uint32_t offr = B.off[r];
-  T row[D];
+  T row[J];
   if (active) {
 #pragma unroll
-    for (int j = 0; j < D; ++j) row[j] = __ldg(M + r * D + j);
+    for (int q = 0; q < J; ++q) row[q] = __ldg(M + r * D + sp + q * S);
   }
   for (uint64_t t0 = (uint64_t)blockIdx.x * G; t0 < B.ntuples; t0 += (uint64_t)gridDim.x * G) {
     const uint64_t t = t0 + lt;
@@ -125,24 +134,26 @@ __device__ __forceinline__ void ol_block(const OLBlock& B, const T* __restrict__
     const uint64_t base = on ? item_index(t, B.spec) : 0;
     // state loads bypass L1 (ld.global.cg): a buffer read two blocks ago may
     // still sit in this SM's L1 while other SMs have rewritten it since
-    if (on) xs[threadIdx.x] = __ldcg(src + base + offr);
+    if (on && sp == 0) xs[lt * D + r] = __ldcg(src + base + offr);
     __syncthreads();
     if (on) {
-      // four independent partial sums: the FP64 multiply-add latency, not its
-      // rate, bounds one warp's chain of 4 x 2^K dependent operations
-      const T* x = xs + (lt << K);
-      T acc[4] = {cmk<T>(0, 0), cmk<T>(0, 0), cmk<T>(0, 0), cmk<T>(0, 0)};
+      const T* x = xs + lt * D;
+      T acc = cmk<T>(0, 0);
 #pragma unroll
-      for (int j = 0; j < D; ++j) acc[j & 3] = cfma(row[j], x[j], acc[j & 3]);
-      T sum = acc[0];
+      for (int q = 0; q < J; ++q) acc = cfma(row[q], x[sp + q * S], acc);
+      ps[threadIdx.x] = acc;
+    }
+    __syncthreads();
+    if (on && sp == 0) {
+      T sum = ps[threadIdx.x];
 #pragma unroll
-      for (int q = 1; q < 4 && q < D; ++q) {
-        sum.x += acc[q].x;
-        sum.y += acc[q].y;
+      for (int q = 1; q < S; ++q) {
+        const T v = ps[threadIdx.x + q * D];
+        sum.x += v.x;
+        sum.y += v.y;
       }
       dst[base + offr] = sum;
     }
-    __syncthreads();
   }
 }
 
@@ -155,15 +166,16 @@ __global__ void __launch_bounds__(kOLThreads) k_onelaunch(const __grid_constant_
   const uint64_t gtid = (uint64_t)threadIdx.x * gridDim.x + blockIdx.x;  // CTA-interleaved work items
   const uint64_t gstride = (uint64_t)gridDim.x * blockDim.x;
   __shared__ T xs[kOLThreads];
+  __shared__ T ps[kOLThreads];
   for (int b = 0; b < a.nblocks; ++b) {
     const OLBlock& B = a.blocks[b];
     const T* M = mats + B.mat;
     switch (B.k) {
-      case 1: ol_block<T, 1>(B, M, src, dst, xs); break;
-      case 2: ol_block<T, 2>(B, M, src, dst, xs); break;
-      case 3: ol_block<T, 3>(B, M, src, dst, xs); break;
-      case 4: ol_block<T, 4>(B, M, src, dst, xs); break;
-      default: ol_block<T, 5>(B, M, src, dst, xs); break;
+      case 1: ol_block<T, 1>(B, M, src, dst, xs, ps); break;
+      case 2: ol_block<T, 2>(B, M, src, dst, xs, ps); break;
+      case 3: ol_block<T, 3>(B, M, src, dst, xs, ps); break;
+      case 4: ol_block<T, 4>(B, M, src, dst, xs, ps); break;
+      default: ol_block<T, 5>(B, M, src, dst, xs, ps); break;
     }
     if (!ol_barrier(a.sync, a.status, gen)) return;
     T* w = src;
@@ -355,8 +367,9 @@ int qs_run_circuit_one_launch(qs_state* s, const qs_circuit* c, const double* ho
   if (k->grid != grid) {
     // tuples per CTA at a time: as many as fill it, no more than spreads the block over every CTA
     for (OLBlock& B : k->host_blocks) {
+      const int D = 1 << B.k, tpt = D * (D >= kOLSplit ? kOLSplit : D);
       int g = 1;
-      while ((g << 1) * (1 << B.k) <= kOLThreads && (uint64_t)(g << 1) * (uint64_t)grid <= B.ntuples) g <<= 1;
+      while ((g << 1) * tpt <= kOLThreads && (uint64_t)(g << 1) * (uint64_t)grid <= B.ntuples) g <<= 1;
       B.group = g;
     }
     if (nb > 0)
