@@ -591,42 +591,9 @@ __device__ __forceinline__ void diag_masked(float2 (&x)[1 << RB], float2 f, int 
     if ((j & cm) == cv) x[j] = cmulf(x[j], f);
 }
 
-// per-bit pending factors (FOLD): a diagonal gate diag(1, f) on phase bit t
-// (controls outside the phase only) multiplies the half of the thread's
-// amplitudes with bit t set by f.  It commutes with every other diagonal
-// gate and with any gate that only reads bit t as a control, so its factor is
-// kept pending, multiplied into pb[t], and applied to the 2^(RB-1)
-// amplitudes once, before the next gate that changes bit t or at the end of
-// the phase: one complex product per gate instead of 2^(RB-1).
-template <int RB, int T>
-__device__ __forceinline__ void flush_bit(float2 (&x)[1 << RB], float2 f) {
-#pragma unroll
-  for (int j = 0; j < (1 << RB); ++j)
-    if (j & (1 << T)) x[j] = cmulf(x[j], f);
-}
-template <int RB>
-__device__ __forceinline__ void pb_mul(float2 (&pb)[RB], int t, float2 f) {
-  switch (t) {
-    case 0: pb[0] = cmulf(pb[0], f); break;
-    case 1: pb[1] = cmulf(pb[1], f); break;
-    case 2: if constexpr (RB > 2) pb[2] = cmulf(pb[2], f); break;
-    default: if constexpr (RB > 3) pb[3] = cmulf(pb[3], f); break;
-  }
-}
-template <int RB>
-__device__ __forceinline__ void pb_flush(float2 (&x)[1 << RB], float2 (&pb)[RB], int t) {
-  switch (t) {
-    case 0: flush_bit<RB, 0>(x, pb[0]); pb[0] = make_float2(1.f, 0.f); break;
-    case 1: flush_bit<RB, 1>(x, pb[1]); pb[1] = make_float2(1.f, 0.f); break;
-    case 2: if constexpr (RB > 2) { flush_bit<RB, 2>(x, pb[2]); pb[2] = make_float2(1.f, 0.f); } break;
-    default: if constexpr (RB > 3) { flush_bit<RB, 3>(x, pb[3]); pb[3] = make_float2(1.f, 0.f); } break;
-  }
-}
-
 // COMP: compensated matrices (flo: 4 corrections per forward op, dtlo: 16 per
-// diagonal table); out-of-phase diagonal factors are then applied one by one.
-// FOLD: per-bit pending factors (above).
-template <int RB, bool COMP, bool FOLD = false>
+// diagonal table); out-of-phase diagonal factors are then applied one by one
+template <int RB, bool COMP>
 __device__ __noinline__ void run_phase_fwd(float2* sm, const TPhase* php, const TOp* fops, const float2* dtab,
                                            const float2* flo, const float2* dtlo, int m, uint32_t tbase) {
   constexpr int A = 1 << RB;
@@ -642,23 +609,10 @@ __device__ __noinline__ void run_phase_fwd(float2* sm, const TPhase* php, const 
     // scalars for this thread: they commute with the phase and are applied once
     float2 pend = make_float2(1.f, 0.f);
     bool has_pend = false;
-    float2 pb[RB];
-#pragma unroll
-    for (int b = 0; b < RB; ++b) pb[b] = make_float2(1.f, 0.f);
-    uint32_t has_pb = 0;
     for (int o = 0; o < ph.nfop; ++o) {
       const int oi = ph.fop0 + o;
       const TOp& cur = fops[oi];
-      if (FOLD && (cur.kind == TK_DENSE || cur.kind == TK_SWAP) && ((has_pb >> cur.t) & 1u)) {
-        pb_flush<RB>(x, pb, cur.t);  // the gate changes bit t: settle its pending factor first
-        has_pb &= ~(1u << cur.t);
-      }
       if ((gb & cur.tmask) != cur.tval) continue;
-      if (FOLD && cur.kind == TK_DIAG && cur.cmask == 0 && cur.u[0].x == 1.f && cur.u[0].y == 0.f) {
-        pb_mul<RB>(pb, cur.t, cur.u[3]);
-        has_pb |= 1u << cur.t;
-        continue;
-      }
       if (cur.kind == TK_DIAGOUT) {
         const bool b1 = (gb >> cur.t) & 1u;
         const float2 f = b1 ? cur.u[3] : cur.u[0];
@@ -688,11 +642,6 @@ __device__ __noinline__ void run_phase_fwd(float2* sm, const TPhase* php, const 
       } else {
         apply_fwd<RB, COMP>(x, cur, COMP ? flo + 4 * oi : nullptr);
       }
-    }
-    if (FOLD) {
-#pragma unroll
-      for (int b = 0; b < RB; ++b)
-        if ((has_pb >> b) & 1u) pb_flush<RB>(x, pb, b);
     }
     if (!COMP && has_pend) {
 #pragma unroll
@@ -1154,8 +1103,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_fused_pass(FArgs a) {
     load_tile(sx, base, rowoff, a.m);
     __syncthreads();
     for (int f = 0; f < p.nphase; ++f)
-      run_phase_fwd<kRB, false, true>(sx, a.phases + p.phase0 + f, a.fops, a.dtab, nullptr, nullptr, a.m,
-                                      (uint32_t)tb);
+      run_phase_fwd<kRB, false>(sx, a.phases + p.phase0 + f, a.fops, a.dtab, nullptr, nullptr, a.m, (uint32_t)tb);
     store_tile(sx, base, rowoff, a.m);
     __syncthreads();
   }
