@@ -366,12 +366,14 @@ int qs_circuit_tile_order(const qs_circuit* c, int tile_qubits, int* ngates, int
  * count) and applies each block as one k-qubit instruction with the product
  * matrix of its gates; dense 4- and 5-qubit blocks of complex64 states may run
  * on the tensor cores (QS_OPT_TENSOR_CORES).  Gates wider than k stay single.
- * QS_APPLY_PRECISE (complex64, the per-gate path only): every 1-qubit gate
- * (fused runs included, controls allowed) is applied with its FP64 matrix
- * held as FP32 hi + lo and each output amplitude summed in double-float and
- * rounded to FP32 once, so the only error left is the storage rounding of the
- * amplitudes (the plain path also rounds the matrix, an error coherent over
- * the whole state); multi-qubit gates are applied as usual. */
+ * QS_APPLY_PRECISE (complex64; the per-gate path, or with QS_APPLY_BLOCKS the
+ * block path; QS_EINVAL with QS_APPLY_TILES): every gate or block in a
+ * dense, diagonal or phased-permutation form of up to 5 qubits (fused 1-qubit
+ * runs included, controls allowed) is applied with its FP64 matrix held as
+ * FP32 hi + lo and each output amplitude summed in double-float and rounded to
+ * FP32 once, on the CUDA cores, so the only error left is the storage rounding
+ * of the amplitudes (the plain path also rounds the matrix, an error coherent
+ * over the whole state; the tensor-core blocks are not used). */
 #define QS_APPLY_PER_REGISTER 1
 #define QS_APPLY_UNFUSED 2
 #define QS_APPLY_TILES 4

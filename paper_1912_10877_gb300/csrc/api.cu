@@ -149,7 +149,7 @@ static int apply_circuit_impl(qs_state* s, const qs_circuit* c, const double* pa
   const bool per_register = (flags & QS_APPLY_PER_REGISTER) != 0;
   const bool unfused = (flags & QS_APPLY_UNFUSED) != 0;
   const bool per_gate = unfused || ckpt_every > 0;  // no tile engine or blocks
-  // compensated 1-qubit gates on complex64: asked for, or the checkpointed forward
+  // compensated gates on complex64: asked for, or the checkpointed forward
   // that feeds the FP64 reversible backward
   const bool precise = ((flags & QS_APPLY_PRECISE) != 0 || ckpt_every > 0) && s->dtype == QS_C64;
   std::vector<cd> U;
@@ -175,8 +175,8 @@ static int apply_circuit_impl(qs_state* s, const qs_circuit* c, const double* pa
   const int tile = (flags >> 8) & 0xff;
   const bool force_tiles = (flags & QS_APPLY_TILES) != 0;
   if (force_tiles && (flags & QS_APPLY_BLOCKS)) return fail(QS_EINVAL, "QS_APPLY_TILES and QS_APPLY_BLOCKS together");
-  if ((flags & QS_APPLY_PRECISE) && (force_tiles || (flags & QS_APPLY_BLOCKS)))
-    return fail(QS_EINVAL, "QS_APPLY_PRECISE runs the per-gate path (not with QS_APPLY_TILES or QS_APPLY_BLOCKS)");
+  if ((flags & QS_APPLY_PRECISE) && force_tiles)
+    return fail(QS_EINVAL, "QS_APPLY_PRECISE runs the per-gate or block path (not with QS_APPLY_TILES)");
   if (!per_gate && !precise && !(flags & QS_APPLY_BLOCKS) && s->dtype == QS_C64 && s->uniform &&
       s->nq[0] == c->nqubits) {
     const int m = std::min(s->nq[0], tile > 0 ? tile : 13);
@@ -190,7 +190,7 @@ static int apply_circuit_impl(qs_state* s, const qs_circuit* c, const double* pa
   }
   if ((flags & QS_APPLY_BLOCKS) && !per_gate) {
     const int kb = (flags >> 16) & 0xf;
-    return apply_blocks(s, c, params, kb > 0 ? kb : QS_MAXK);
+    return apply_blocks(s, c, params, kb > 0 ? kb : QS_MAXK, precise);
   }
   Fuser fz(s, c->nqubits);
   fz.precise = precise;

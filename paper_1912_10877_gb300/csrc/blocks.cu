@@ -230,7 +230,7 @@ void free_blocks(const qs_circuit* c) {
   c->blocks = nullptr;
 }
 
-int apply_blocks(qs_state* s, const qs_circuit* c, const double* params, int kmax) {
+int apply_blocks(qs_state* s, const qs_circuit* c, const double* params, int kmax, bool precise) {
   if (kmax < 1 || kmax > QS_MAXK) return fail(QS_EINVAL, "block width %d not in 1..%d", kmax, QS_MAXK);
   const std::vector<Block>& blocks = cached_blocks(c, kmax);
   std::vector<int> qubits;
@@ -245,6 +245,7 @@ int apply_blocks(qs_state* s, const qs_circuit* c, const double* params, int kma
       QS_TRY(block_matrix(c, b, params, qubits, M));
       QS_TRY(plan_gate(M.data(), (int)qubits.size(), qubits.data(), 0, 0, &p));
     }
+    p.precise = precise && s->dtype == QS_C64;
     QS_TRY(launch_plan(s, p));
   }
   return QS_OK;

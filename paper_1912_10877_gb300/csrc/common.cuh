@@ -245,7 +245,7 @@ struct Plan {
   uint64_t mask = 0, vals = 0;      // fixed subspace for DIAG1
   cd d0 = 1, d1 = 1;
   cd u[4];
-  bool precise = false;             // complex64 1-qubit forms: compensated matrix, outputs rounded once
+  bool precise = false;             // complex64: compensated matrix, each output rounded once
   // k-qubit forms (row-major 2^k x 2^k; perm / diag tables)
   std::vector<cd> U;
   int perm[1 << QS_MAXK];
@@ -282,7 +282,7 @@ int gram_tc(int w, const float2* psi, const float2* lam, int n, const int* qubit
             cudaStream_t st);
 
 // the circuit fused into blocks of at most kmax qubits, gate-by-gate path (blocks.cu)
-int apply_blocks(qs_state* s, const qs_circuit* c, const double* params, int kmax);
+int apply_blocks(qs_state* s, const qs_circuit* c, const double* params, int kmax, bool precise);
 void free_blocks(const qs_circuit* c);
 
 // samples with device uniforms into device indices (reduce.cu)

@@ -260,6 +260,51 @@ k_gatek(c2_t<R>* __restrict__ psi, uint64_t nitems, IdxSpec s, const __grid_cons
   }
 }
 
+// complex64 k-qubit gate with its FP64 matrix held as hi + lo (MatK M and its
+// corrections W) and every output amplitude summed in double-float and rounded
+// once (Plan::precise): one tuple per thread, as k_gatek
+template <int K, int OP>
+__global__ void __launch_bounds__(kThreads)
+k_gatek_prec(float2* __restrict__ psi, uint64_t nitems, IdxSpec s, const __grid_constant__ MatK<float, K> M,
+             const __grid_constant__ MatK<float, K> W) {
+  constexpr int D = 1 << K;
+  const uint64_t it = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= nitems) return;
+  const uint64_t base = item_index(it, s);
+  float2 x[D];
+  if constexpr (OP == OP_PERMK) {
+#pragma unroll
+    for (int m = 0; m < D; ++m) x[m] = psi[base + M.off[M.perm[m]]];
+#pragma unroll
+    for (int m = 0; m < D; ++m) psi[base + M.off[m]] = cf_mul(x[m], M.m[m], W.m[m]);
+    return;
+  }
+#pragma unroll
+  for (int m = 0; m < D; ++m) x[m] = psi[base + M.off[m]];
+  if constexpr (OP == OP_DIAGK) {
+#pragma unroll
+    for (int m = 0; m < D; ++m) psi[base + M.off[m]] = cf_mul(x[m], M.m[m], W.m[m]);
+    return;
+  }
+#pragma unroll 1
+  for (int m = 0; m < D; ++m) {
+    float rs, re, is, ie;
+    cf_first(rs, re, x[0].x, M.m[m * D].x, W.m[m * D].x);
+    cf_add(rs, re, -x[0].y, M.m[m * D].y, W.m[m * D].y);
+    cf_first(is, ie, x[0].x, M.m[m * D].y, W.m[m * D].y);
+    cf_add(is, ie, x[0].y, M.m[m * D].x, W.m[m * D].x);
+#pragma unroll
+    for (int j = 1; j < D; ++j) {
+      const float2 u = M.m[m * D + j], w = W.m[m * D + j];
+      cf_add(rs, re, x[j].x, u.x, w.x);
+      cf_add(rs, re, -x[j].y, u.y, w.y);
+      cf_add(is, ie, x[j].x, u.y, w.y);
+      cf_add(is, ie, x[j].y, u.x, w.x);
+    }
+    psi[base + M.off[m]] = make_float2(__fadd_rn(rs, re), __fadd_rn(is, ie));
+  }
+}
+
 // complex64 dense 2- and 3-qubit gates whose targets and controls leave qubit 0
 // free: items 2i and 2i + 1 are adjacent amplitudes of every member, so a
 // thread takes both tuples with one 16-byte access per member
@@ -320,9 +365,60 @@ static float2 lo_dev(cd z) {
   return make_float2((float)(z.real() - (double)h.x), (float)(z.imag() - (double)h.y));
 }
 
+template <int K, int OP>
+static int launch_prec_k(float2* psi, int n, int nreg, const Plan& p, cudaStream_t st) {
+  MatK<float, K> M, W;
+  memset(&M, 0, sizeof(M));
+  memset(&W, 0, sizeof(W));
+  constexpr int D = 1 << K;
+  uint64_t locmask = 0;
+  for (int j = 0; j < K; ++j) locmask |= 1ull << p.locs[j];
+  for (int m = 0; m < D; ++m) {
+    uint64_t o = 0;
+    for (int j = 0; j < K; ++j)
+      if ((m >> j) & 1) o |= 1ull << p.locs[j];
+    M.off[m] = o;
+  }
+  if (OP == OP_DENSEK)
+    for (int i = 0; i < D * D; ++i) {
+      M.m[i] = to_dev<float>(p.U[i]);
+      W.m[i] = lo_dev(p.U[i]);
+    }
+  else
+    for (int m = 0; m < D; ++m) {
+      const cd v = OP == OP_DIAGK ? p.U[m * D + m] : p.pv[m];
+      M.m[m] = to_dev<float>(v);
+      W.m[m] = lo_dev(v);
+      if (OP == OP_PERMK) M.perm[m] = (int8_t)p.perm[m];
+    }
+  IdxSpec s;
+  QS_TRY(make_idx(n, locmask | p.ctrl_mask, p.ctrl_vals, &s));
+  const uint64_t items = (uint64_t)nreg << s.item_log2;
+  if (items == 0) return QS_OK;
+  const int nt = cta_threads(items, 1);
+  k_gatek_prec<K, OP><<<blocks_for(items, nt), nt, 0, st>>>(psi, items, s, M, W);
+  QS_LAUNCHED();
+  return QS_OK;
+}
+
+template <int OP>
+static int launch_prec_op(float2* psi, int n, int nreg, const Plan& p, cudaStream_t st) {
+  switch (p.k) {
+    case 2: return launch_prec_k<2, OP>(psi, n, nreg, p, st);
+    case 3: return launch_prec_k<3, OP>(psi, n, nreg, p, st);
+    case 4: return launch_prec_k<4, OP>(psi, n, nreg, p, st);
+    case 5: return launch_prec_k<5, OP>(psi, n, nreg, p, st);
+  }
+  return fail(QS_EUNSUPPORTED, "gate arity %d", p.k);
+}
+
 // the compensated complex64 launches of Plan::precise (1-qubit dense,
-// permutation and diagonal forms; SWAP1 is exact as it is)
+// permutation and diagonal forms, k-qubit dense, diagonal and phased-permutation
+// forms; SWAP1 is exact as it is)
 static int launch_prec(float2* psi, int n, int nreg, const Plan& p, cudaStream_t st) {
+  if (p.op == OP_DENSEK) return launch_prec_op<OP_DENSEK>(psi, n, nreg, p, st);
+  if (p.op == OP_DIAGK) return launch_prec_op<OP_DIAGK>(psi, n, nreg, p, st);
+  if (p.op == OP_PERMK) return launch_prec_op<OP_PERMK>(psi, n, nreg, p, st);
   if (p.op == OP_DIAG1) {
     IdxSpec s;
     QS_TRY(make_idx(n, 1ull | p.mask, p.vals & ~1ull, &s));
@@ -470,7 +566,8 @@ int launch_plan_on(void* data, int dtype, int n, int nreg, int64_t reg_stride, c
   (void)reg_stride;
   cudaStream_t st = owner ? owner->stream : nullptr;
   if (dtype == QS_C64 && p.precise &&
-      (p.op == OP_DIAG1 || p.op == OP_DENSE1 || p.op == OP_REAL1 || p.op == OP_RXLIKE1 || p.op == OP_PERM1))
+      (p.op == OP_DIAG1 || p.op == OP_DENSE1 || p.op == OP_REAL1 || p.op == OP_RXLIKE1 || p.op == OP_PERM1 ||
+       ((p.op == OP_DENSEK || p.op == OP_DIAGK || p.op == OP_PERMK) && p.k >= 2 && p.k <= 5)))
     return launch_prec((float2*)data, n, nreg, p, st);
   if (use_block_tc(dtype, p)) return launch_block_tc((float2*)data, n, nreg, p, st);
   if (dtype == QS_C64) return launch_typed<float>((float2*)data, n, nreg, p, st);

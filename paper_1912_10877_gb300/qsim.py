@@ -164,8 +164,8 @@ class State:
                       tile_qubits=0, blocks=0, flags=None, precise=False):
         """apply!(reg, chain) (Sec. "Representing Quantum Circuits").  fused=False: one launch per gate; tiles=True: force the
         tile engine (fused passes over 2^tile_qubits-amplitude tiles); blocks=k: fuse
-        the gates into blocks of at most k qubits; precise=True: complex64 1-qubit gates with
-        compensated matrices, rounded once (QS_APPLY_PRECISE); flags: raw qs_apply_circuit flags
+        the gates into blocks of at most k qubits; precise=True: complex64 gates (or blocks) with
+        compensated matrices, each output rounded once (QS_APPLY_PRECISE); flags: raw qs_apply_circuit flags
         (e.g. from autotune), overriding the others."""
         p = _params_array(params, circuit.nparams * (self.nreg if per_register else 1))
         if flags is None:

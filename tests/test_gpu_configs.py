@@ -161,3 +161,47 @@ def test_precise_complex64_apply_against_oracle(qs, record_property):
     print(f"complex64 n={n}, {len(gates)} gates: max|dpsi| plain {errs['plain']:.2e} precise {errs['precise']:.2e}")
     assert errs["precise"] < 2e-6
     assert errs["precise"] <= errs["plain"]
+
+
+def _diag_perm_sections(n, reps, seed):
+    """Gate runs whose fused blocks are diagonal (Rz, controlled phases, CZ, T) and
+    phased permutations (CNOT, SWAP, Y, Toffoli, S, phase), plus one dense run."""
+    r = W.rng(seed)
+    diag, perm = [], []
+    for _ in range(reps):
+        q = int(r.integers(0, n - 1))
+        diag += [W.Gate("RZ", (q,), theta=float(r.uniform(0, 6.3))), W.Gate("Z", (q + 1,), (q,), (1,)),
+                 W.Gate("SHIFT", (q,), (q + 1,), (1,), theta=float(r.uniform(0, 6.3))), W.Gate("T", (q + 1,)),
+                 W.Gate("PHASE", (q,), theta=float(r.uniform(0, 6.3)))]
+        c = int(r.integers(0, n - 2))
+        perm += [W.cnot(c, c + 1), W.Gate("SWAP", (c + 1, c + 2)), W.Gate("Y", (c,)), W.toffoli(c, c + 1, c + 2),
+                 W.Gate("S", (c + 2,)), W.Gate("SHIFT", (c + 1,), theta=float(r.uniform(0, 6.3)))]
+    return diag, perm
+
+
+@pytest.mark.parametrize("kind", ["dense", "diagonal", "permutation"])
+def test_precise_blocks_against_oracle(qs, kind, record_property):
+    # QS_APPLY_PRECISE with QS_APPLY_BLOCKS: every fused block (dense, diagonal or phased
+    # permutation of up to 5 qubits) applied with its FP64 matrix as FP32 hi + lo, each
+    # output rounded once; the error must stay at the storage-rounding level and not
+    # exceed the plain block path's
+    n = 12
+    if kind == "dense":
+        gates, params = W.brickwork(n, 40, seed=4)
+    else:
+        diag, perm = _diag_perm_sections(n, 150, seed=5)
+        gates, params = (diag if kind == "diagonal" else perm), np.zeros(0)
+    circ = qs.Circuit(gates, n, nparams=len(params))
+    psi_in = W.haar_state(n, seed=6)
+    ref = oracle.apply_circuit(psi_in, n, gates, params)
+    errs = {}
+    for name, kw in (("plain", {}), ("precise", {"precise": True})):
+        st = qs.State(n, dtype=torch.complex64)
+        st.upload(psi_in)
+        st.apply_circuit(circ, params, blocks=5, **kw)
+        errs[name] = float(np.max(np.abs(st.numpy() - ref)))
+    record_property("state_abs_err", errs)
+    print(f"complex64 {kind} blocks n={n}, {len(gates)} gates: max|dpsi| plain {errs['plain']:.2e} "
+          f"precise {errs['precise']:.2e}")
+    assert errs["precise"] < 1e-6
+    assert errs["precise"] <= errs["plain"]

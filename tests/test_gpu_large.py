@@ -200,3 +200,39 @@ def test_large_pipeline_n22_fp64_block_backward(qs, tc, record_property):
     print(f"n=22 complex64 forward (tensor cores {tc}) + FP64 block backward: loss {abs(loss - rl):.2e} grad {err:.2e}")
     assert abs(loss - rl) < 1e-5
     assert err < (1e-4 if tc else 5e-6)
+
+
+@pytest.mark.parametrize("qft_path", ["precise", "tiles"])
+def test_large_pipeline_n22_precise_blocks_fp64_backward(qs, qft_path, record_property):
+    # complex64 forward with compensated gates (the QFT per gate with QS_APPLY_PRECISE, or on
+    # the tile engine; the brickwork as compensated 5-qubit blocks on the CUDA cores), then the
+    # FP64 reversible block backward on the widened final state
+    n = 22
+    x = W.random_basis(n, seed=0)
+    bgates, bparams = W.brickwork(n, DEPTH, seed=0)
+    st = qs.State(n, dtype=torch.complex64)
+    st.reset([x])
+    qcirc = qs.Circuit(W.qft(n, swaps=True), n)
+    if qft_path == "tiles":
+        st.apply_circuit(qcirc, tiles=True)
+    else:
+        st.apply_circuit(qcirc, precise=True)
+    psi0 = oracle.apply_circuit(oracle.basis_state(n, x), n, W.qft(n, swaps=True))
+    err_qft = float(np.max(np.abs(st.numpy() - psi0)))
+    bcirc = qs.Circuit(bgates, n, nparams=len(bparams))
+    st.apply_circuit(bcirc, bparams, blocks=5, precise=True)
+    psiN = oracle.apply_circuit(psi0, n, bgates, bparams)
+    err_state = float(np.max(np.abs(st.numpy() - psiN)))
+    wide = qs.State(n, dtype=torch.complex128)
+    wide.copy_from(st)
+    loss, grad = qs.backward_blocks(wide, bcirc, bparams, qs.Observable(W.z_on(0)), kmax=5)
+    rl, rg = oracle.gradient(psi0, n, bgates, bparams, W.z_on(0))
+    err = rel(grad, rg)
+    for k, v in (("qft_state_abs", err_qft), ("brickwork_state_abs", err_state), ("loss_abs", abs(loss - rl)),
+                 ("grad_rel", err)):
+        record_property(k, v)
+    print(f"n=22 compensated complex64 forward (QFT {qft_path}) + FP64 block backward: qft {err_qft:.2e} "
+          f"state {err_state:.2e} loss {abs(loss - rl):.2e} grad {err:.2e}")
+    assert err_qft < 2e-5 and err_state < 2e-5
+    assert abs(loss - rl) < 1e-5
+    assert err < (1e-6 if qft_path == "precise" else 5e-6)
