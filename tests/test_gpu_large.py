@@ -235,4 +235,6 @@ def test_large_pipeline_n22_precise_blocks_fp64_backward(qs, qft_path, record_pr
           f"state {err_state:.2e} loss {abs(loss - rl):.2e} grad {err:.2e}")
     assert err_qft < 2e-5 and err_state < 2e-5
     assert abs(loss - rl) < 1e-5
-    assert err < (1e-6 if qft_path == "precise" else 5e-6)
+    # measured on GB300: 2.1e-8 (QFT per gate, compensated), 1.3e-6 (QFT on the FP32 tile engine,
+    # whose rounded phase factors then dominate)
+    assert err < (1e-7 if qft_path == "precise" else 4e-6)
