@@ -583,6 +583,56 @@ __device__ __forceinline__ uint32_t slot(const PhaseSlots& p, int j) {
   return o;
 }
 
+// ---- shared-memory copies of a pass's phase records and ops
+//
+// Every tile of a pass runs the same phases, so a CTA that streams tiles reads
+// each op record once per tile.  Read from global memory, those records are
+// evicted from L1 by the tile traffic and every op then waits on L2 before
+// its first arithmetic (the records are read by a chain of dependent loads:
+// the control test, the kind, the target, the matrix).  The pass's records are
+// therefore copied into shared memory once per pass, with the phases' op
+// indices rebased to the pass's first op.  A pass larger than the staging
+// area keeps reading global memory.
+constexpr int kStagePhases = 32;
+constexpr int kStageOps = 512;
+static_assert(sizeof(TOp) == 64 && sizeof(TOp) % 16 == 0, "TOp is copied as 16-byte words");
+constexpr size_t kStagePhaseBytes = (sizeof(TPhase) * kStagePhases + 15) & ~size_t(15);
+constexpr size_t kStageBytes = kStagePhaseBytes + sizeof(TOp) * kStageOps;
+
+struct StagedPass {
+  const TPhase* ph;  // the pass's first phase
+  const TOp* ops;    // op table the phases index
+  int first;         // index of ops[0] in the global op table (0 when not staged)
+};
+
+// FWD: the forward ops (fop0 / nfop), else the backward ops (bop0 / nbop).
+// buf: kStageBytes of shared memory, or nullptr.  Every thread of the CTA
+// calls this (it ends with a barrier when it copies).
+template <bool FWD>
+__device__ StagedPass stage_pass(const TPass& p, const TPhase* phases, const TOp* ops, unsigned char* buf) {
+  StagedPass r{phases + p.phase0, ops, 0};
+  if (!buf || p.nphase <= 0 || p.nphase > kStagePhases) return r;
+  const TPhase& f0 = phases[p.phase0];
+  const TPhase& fl = phases[p.phase0 + p.nphase - 1];
+  const int first = FWD ? f0.fop0 : f0.bop0;
+  const int count = FWD ? fl.fop0 + fl.nfop - first : fl.bop0 + fl.nbop - first;
+  if (count < 0 || count > kStageOps) return r;
+  TPhase* sph = reinterpret_cast<TPhase*>(buf);
+  TOp* sop = reinterpret_cast<TOp*>(buf + kStagePhaseBytes);
+  constexpr int W = (int)(sizeof(TOp) / 16);
+  const uint4* src = reinterpret_cast<const uint4*>(ops + first);
+  uint4* dst = reinterpret_cast<uint4*>(sop);
+  for (int i = threadIdx.x; i < count * W; i += blockDim.x) dst[i] = src[i];
+  if ((int)threadIdx.x < p.nphase) {
+    TPhase q = phases[p.phase0 + threadIdx.x];
+    if (FWD) q.fop0 -= first;
+    else q.bop0 -= first;
+    sph[threadIdx.x] = q;
+  }
+  __syncthreads();
+  return StagedPass{sph, sop, first};
+}
+
 // out-of-phase diagonal gate with phase-local controls: x_j *= f where (j & cm) == cv
 template <int RB>
 __device__ __forceinline__ void diag_masked(float2 (&x)[1 << RB], float2 f, int cm, int cv) {
@@ -896,18 +946,18 @@ __device__ __noinline__ void batch_bwd_resident_ff(float4* sx, float4* sl, const
 template <int RB>
 __device__ __noinline__ void batch_bwd_streamed(float2* sx, float2* sl, const TPass* P, int npass, int m, int g,
                                                 float2* wp, float2* wl, const TPhase* phases, const TOp* bops,
-                                                uint32_t* rowoff, float* red, double* gacc) {
+                                                uint32_t* rowoff, float* red, double* gacc, unsigned char* stage) {
   const uint64_t ntile = 1ull << g;
   for (int pi = npass - 1; pi >= 0; --pi) {
     const TPass& p = P[pi];
     set_rows(rowoff, p, m);
+    const StagedPass sp = stage_pass<false>(p, phases, bops, stage);
     for (uint64_t t = 0; t < ntile; ++t) {
       const uint64_t tb = tile_base(t, p, g);
       load_tiles<true>(sx, wp + tb, sl, wl + tb, rowoff, m);
       __syncthreads();
-      const int ph0 = p.phase0;
       for (int f = p.nphase - 1; f >= 0; --f)
-        run_phase_bwd<RB>(sx, sl, phases + ph0 + f, bops, m, red, gacc, (uint32_t)tb);
+        run_phase_bwd<RB>(sx, sl, sp.ph + f, sp.ops, m, red, gacc, (uint32_t)tb);
       store_tiles<true>(sx, wp + tb, sl, wl + tb, rowoff, m);
       __syncthreads();
     }
@@ -917,18 +967,20 @@ __device__ __noinline__ void batch_bwd_streamed(float2* sx, float2* sl, const TP
 template <int RB>
 __device__ __noinline__ void batch_bwd_streamed_ff(float4* sx, float4* sl, const TPass* P, int npass, int m, int g,
                                                    float4* wp, float4* wl, const TPhase* phases, const TOp* bops,
-                                                   const float2* blo, uint32_t* rowoff, float* red, double* gacc) {
+                                                   const float2* blo, uint32_t* rowoff, float* red, double* gacc,
+                                                   unsigned char* stage) {
   const uint64_t ntile = 1ull << g;
   for (int pi = npass - 1; pi >= 0; --pi) {
     const TPass& p = P[pi];
     set_rows(rowoff, p, m);
+    const StagedPass sp = stage_pass<false>(p, phases, bops, stage);
+    const float2* lo = blo + 4 * (size_t)sp.first;
     for (uint64_t t = 0; t < ntile; ++t) {
       const uint64_t tb = tile_base(t, p, g);
       load_tiles_ff(sx, wp + tb, sl, wl + tb, rowoff, m);
       __syncthreads();
-      const int ph0 = p.phase0;
       for (int f = p.nphase - 1; f >= 0; --f)
-        run_phase_bwd_ff<RB>(sx, sl, phases + ph0 + f, bops, blo, m, red, gacc, (uint32_t)tb);
+        run_phase_bwd_ff<RB>(sx, sl, sp.ph + f, sp.ops, lo, m, red, gacc, (uint32_t)tb);
       store_tiles_ff(sx, wp + tb, sl, wl + tb, rowoff, m);
       __syncthreads();
     }
@@ -938,18 +990,20 @@ __device__ __noinline__ void batch_bwd_streamed_ff(float4* sx, float4* sl, const
 template <int RB, bool COMP>
 __device__ __noinline__ void batch_fwd_streamed(float2* sx, float2* st, const TPass* P, int npass, int m, int g,
                                                 const TPhase* phases, const TOp* fops, const float2* dtab,
-                                                const float2* flo, const float2* dtlo, uint32_t* rowoff) {
+                                                const float2* flo, const float2* dtlo, uint32_t* rowoff,
+                                                unsigned char* stage) {
   const uint64_t ntile = 1ull << g;
   for (int pi = 0; pi < npass; ++pi) {
     const TPass& p = P[pi];
     set_rows(rowoff, p, m);
+    const StagedPass sp = stage_pass<true>(p, phases, fops, stage);
+    const float2* lo = COMP ? flo + 4 * (size_t)sp.first : nullptr;
     for (uint64_t t = 0; t < ntile; ++t) {
       const uint64_t tb = tile_base(t, p, g);
       load_tile(sx, st + tb, rowoff, m);
       __syncthreads();
-      const int ph0 = p.phase0;
       for (int f = 0; f < p.nphase; ++f)
-        run_phase_fwd<RB, COMP>(sx, phases + ph0 + f, fops, dtab, flo, dtlo, m, (uint32_t)tb);
+        run_phase_fwd<RB, COMP>(sx, sp.ph + f, sp.ops, dtab, lo, dtlo, m, (uint32_t)tb);
       store_tile(sx, st + tb, rowoff, m);
       __syncthreads();
     }
@@ -975,6 +1029,7 @@ __global__ void __launch_bounds__(kTileThreads, kBatchMinBlocks<RB, PREC>) k_bat
   float2* sl = sx + (1 << MT);                                    // complex64 lambda tile (FP32 backward)
   float4* sxf = reinterpret_cast<float4*>(body + (size_t)8 * (1 << MT));   // double-float psi (precise)
   float4* slf = sxf + (1 << MT);                                           // double-float lambda (precise)
+  unsigned char* stage = body + (size_t)(PREC ? 40 : 16) * (1 << MT);      // a pass's records (streamed registers)
   const int tid = threadIdx.x;
   for (;;) {
     if (tid == 0) S.reg = atomicAdd(a.counter, 1);
@@ -1018,7 +1073,8 @@ __global__ void __launch_bounds__(kTileThreads, kBatchMinBlocks<RB, PREC>) k_bat
         for (uint64_t i = tid; i < (1ull << n); i += blockDim.x) st[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
         __syncthreads();
       }
-      batch_fwd_streamed<RB, PREC>(sx, st, P, R.npass, m, g, a.phases, a.fops, a.dtab, a.flo, a.dtlo, S.rowoff);
+      batch_fwd_streamed<RB, PREC>(sx, st, P, R.npass, m, g, a.phases, a.fops, a.dtab, a.flo, a.dtlo, S.rowoff,
+                                   stage);
       // expectation, lambda = O psi, and the work copy of psi for the uncompute
       double e = 0.0;
       const TPass& p0 = P[0];
@@ -1043,10 +1099,10 @@ __global__ void __launch_bounds__(kTileThreads, kBatchMinBlocks<RB, PREC>) k_bat
       if (grad) {
         if (PREC)
           batch_bwd_streamed_ff<RB>(sxf, slf, P, R.npass, m, g, a.wpsif + R.work_off, a.wlamf + R.work_off, a.phases,
-                                    a.bops, a.blo, S.rowoff, S.red, S.grad);
+                                    a.bops, a.blo, S.rowoff, S.red, S.grad, stage);
         else
           batch_bwd_streamed<RB>(sx, sl, P, R.npass, m, g, a.wpsi + R.work_off, a.wlam + R.work_off, a.phases,
-                                 a.bops, S.rowoff, S.red, S.grad);
+                                 a.bops, S.rowoff, S.red, S.grad, stage);
       }
     }
     __syncthreads();
@@ -1059,7 +1115,7 @@ __global__ void __launch_bounds__(kTileThreads, kBatchMinBlocks<RB, PREC>) k_bat
 // bytes of dynamic shared memory of k_batch<RB, PREC>
 static size_t batch_smem(int rb, bool prec) {
   const size_t mt = (size_t)1 << (9 + rb);
-  return ((sizeof(BShared) + 255) & ~size_t(255)) + (prec ? (8 + 32) * mt : 16 * mt);
+  return ((sizeof(BShared) + 255) & ~size_t(255)) + (prec ? (8 + 32) * mt : 16 * mt) + kStageBytes;
 }
 
 // the instantiation of k_batch for a phase width and path
@@ -1093,8 +1149,10 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_fused_pass(FArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   uint32_t* rowoff = reinterpret_cast<uint32_t*>(smraw);
   float2* sx = reinterpret_cast<float2*>(smraw + sizeof(uint32_t) * (1 << (kMaxTileBits - kRowBits)));
+  unsigned char* stage = reinterpret_cast<unsigned char*>(sx + (1 << kBatchTile));
   const TPass& p = *a.pass;
   set_rows(rowoff, p, a.m);
+  const StagedPass sp = stage_pass<true>(p, a.phases, a.fops, stage);
   const uint64_t total = a.ntile * (uint64_t)a.nreg;
   for (uint64_t t = blockIdx.x; t < total; t += gridDim.x) {
     const uint64_t r = t / a.ntile, tl = t - r * a.ntile;
@@ -1103,7 +1161,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_fused_pass(FArgs a) {
     load_tile(sx, base, rowoff, a.m);
     __syncthreads();
     for (int f = 0; f < p.nphase; ++f)
-      run_phase_fwd<kRB, false>(sx, a.phases + p.phase0 + f, a.fops, a.dtab, nullptr, nullptr, a.m, (uint32_t)tb);
+      run_phase_fwd<kRB, false>(sx, sp.ph + f, sp.ops, a.dtab, nullptr, nullptr, a.m, (uint32_t)tb);
     store_tile(sx, base, rowoff, a.m);
     __syncthreads();
   }
@@ -1121,6 +1179,7 @@ struct FBArgs {
   const TPhase* phases;
   const TOp* bops;
   int m, g, nparam;
+  int stage;             // 1: kStageBytes of shared memory after the tiles hold the pass's records
   uint64_t ntile;
   double* partials;      // [gridDim.x][nparam]
 };
@@ -1132,15 +1191,17 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_fused_bwd_pass(FBArgs a) {
   double* gacc = reinterpret_cast<double*>(red + kMaxPhaseOps * kWarps);
   float2* sx = reinterpret_cast<float2*>(gacc + ((a.nparam + 1) & ~1));
   float2* sl = sx + (1 << a.m);
+  unsigned char* stage = a.stage ? reinterpret_cast<unsigned char*>(sl + (1 << a.m)) : nullptr;
   const TPass& p = *a.pass;
   for (int i = threadIdx.x; i < a.nparam; i += blockDim.x) gacc[i] = 0.0;
   set_rows(rowoff, p, a.m);
+  const StagedPass sp = stage_pass<false>(p, a.phases, a.bops, stage);
   for (uint64_t t = blockIdx.x; t < a.ntile; t += gridDim.x) {
     const uint64_t tb = tile_base(t, p, a.g);
     load_tiles<true>(sx, a.wpsi + tb, sl, a.wlam + tb, rowoff, a.m);
     __syncthreads();
     for (int f = p.nphase - 1; f >= 0; --f)
-      run_phase_bwd<kRB>(sx, sl, a.phases + p.phase0 + f, a.bops, a.m, red, gacc, (uint32_t)tb);
+      run_phase_bwd<kRB>(sx, sl, sp.ph + f, sp.ops, a.m, red, gacc, (uint32_t)tb);
     store_tiles<true>(sx, a.wpsi + tb, sl, a.wlam + tb, rowoff, a.m);
     __syncthreads();
   }
@@ -1664,7 +1725,7 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
   }
   P->host_passes = passes;
   if (P->fused_only) {
-    P->smem = sizeof(uint32_t) * (1 << (kMaxTileBits - kRowBits)) + sizeof(float2) * (1 << kBatchTile);
+    P->smem = sizeof(uint32_t) * (1 << (kMaxTileBits - kRowBits)) + sizeof(float2) * (1 << kBatchTile) + kStageBytes;
     QS_CUDA(cudaFuncSetAttribute(k_fused_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smem));
     int dev = 0, sms = 0, per_sm = 0;
     QS_CUDA(cudaGetDevice(&dev));
@@ -1867,9 +1928,11 @@ int fused_backward(qs_state* s, const qs_circuit* c, const double* host_params, 
   qs_batch_program* P = c->fused;
   cudaStream_t st = s->stream;
   const int np = c->nparams;
-  const size_t smem = sizeof(uint32_t) * (1 << (kMaxTileBits - kRowBits)) + sizeof(float) * kMaxPhaseOps * kWarps +
-                      sizeof(double) * ((np + 1) & ~1) + 2 * sizeof(float2) * (1ull << m);
+  size_t smem = sizeof(uint32_t) * (1 << (kMaxTileBits - kRowBits)) + sizeof(float) * kMaxPhaseOps * kWarps +
+                sizeof(double) * ((np + 1) & ~1) + 2 * sizeof(float2) * (1ull << m);
   if (smem > 227 * 1024) return fail(QS_EUNSUPPORTED, "%d parameters do not fit the tiled backward's shared memory", np);
+  const bool stage = smem + kStageBytes <= 227 * 1024;
+  if (stage) smem += kStageBytes;
   if (host_loss) QS_TRY(expect_raw(s->data, QS_C64, n, 1, o, s, host_loss));
   if (np > 0) {
     if (P->dparams_n < np) {
@@ -1927,6 +1990,7 @@ int fused_backward(qs_state* s, const qs_circuit* c, const double* host_params, 
   a.m = m;
   a.g = g;
   a.nparam = np;
+  a.stage = stage ? 1 : 0;
   a.ntile = ntile;
   a.partials = partials;
   for (int64_t pi = P->npass - 1; pi >= 0; --pi) {
