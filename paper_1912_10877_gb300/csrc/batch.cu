@@ -644,8 +644,8 @@ __device__ __forceinline__ void diag_masked(float2 (&x)[1 << RB], float2 f, int 
 // COMP: compensated matrices (flo: 4 corrections per forward op, dtlo: 16 per
 // diagonal table); out-of-phase diagonal factors are then applied one by one
 template <int RB, bool COMP>
-__device__ __noinline__ void run_phase_fwd(float2* sm, const TPhase* php, const TOp* fops, const float2* dtab,
-                                           const float2* flo, const float2* dtlo, int m, uint32_t tbase) {
+__device__ __forceinline__ void phase_fwd_body(float2* sm, const TPhase* php, const TOp* fops, const float2* dtab,
+                                               const float2* flo, const float2* dtlo, int m, uint32_t tbase) {
   constexpr int A = 1 << RB;
   const TPhase& ph = *php;
   const int ntb = m - RB;
@@ -701,6 +701,14 @@ __device__ __noinline__ void run_phase_fwd(float2* sm, const TPhase* php, const 
     for (int j = 0; j < A; ++j) sm[slot(ps, j)] = x[j];
   }
   __syncthreads();
+}
+
+// All phases of a pass on one tile, in order (one call per tile)
+template <int RB, bool COMP>
+__device__ __noinline__ void run_tile_fwd(float2* sm, const TPhase* ph, int nphase, const TOp* fops,
+                                          const float2* dtab, const float2* flo, const float2* dtlo, int m,
+                                          uint32_t tbase) {
+  for (int f = 0; f < nphase; ++f) phase_fwd_body<RB, COMP>(sm, ph + f, fops, dtab, flo, dtlo, m, tbase);
 }
 
 // backward of an out-of-phase diagonal gate: the generator is diagonal on the
@@ -776,8 +784,8 @@ __device__ __forceinline__ void fold_phase_grad(const TPhase& ph, const TOp* bop
 }
 
 template <int RB>
-__device__ __noinline__ void run_phase_bwd(float2* sx, float2* sl, const TPhase* php, const TOp* bops, int m,
-                                           float* red, double* gacc, uint32_t tbase) {
+__device__ __forceinline__ void phase_bwd_body(float2* sx, float2* sl, const TPhase* php, const TOp* bops, int m,
+                                               float* red, double* gacc, uint32_t tbase) {
   // the phase record stays in memory (L1): with 2 x 2^RB live amplitudes per
   // thread there are no registers to spare for a copy of it
   constexpr int A = 1 << RB;
@@ -817,6 +825,14 @@ __device__ __noinline__ void run_phase_bwd(float2* sx, float2* sl, const TPhase*
   }
   __syncthreads();
   fold_phase_grad(ph, bops, red, gacc);
+}
+
+// All phases of a pass on one tile, last phase first: one call per tile, so
+// that the callers' loop state is saved once per tile rather than per phase
+template <int RB>
+__device__ __noinline__ void run_tile_bwd(float2* sx, float2* sl, const TPhase* ph, int nphase, const TOp* bops,
+                                          int m, float* red, double* gacc, uint32_t tbase) {
+  for (int f = nphase - 1; f >= 0; --f) phase_bwd_body<RB>(sx, sl, ph + f, bops, m, red, gacc, tbase);
 }
 
 template <int RB>
@@ -926,10 +942,8 @@ __device__ void block_loss(double e, BShared& S, double* out) {
 template <int RB>
 __device__ __noinline__ void batch_bwd_resident(float2* sx, float2* sl, const TPass* P, int npass, int m,
                                                 const TPhase* phases, const TOp* bops, float* red, double* gacc) {
-  for (int pi = npass - 1; pi >= 0; --pi) {
-    const int ph0 = P[pi].phase0;
-    for (int f = P[pi].nphase - 1; f >= 0; --f) run_phase_bwd<RB>(sx, sl, phases + ph0 + f, bops, m, red, gacc, 0u);
-  }
+  for (int pi = npass - 1; pi >= 0; --pi)
+    run_tile_bwd<RB>(sx, sl, phases + P[pi].phase0, P[pi].nphase, bops, m, red, gacc, 0u);
 }
 
 template <int RB>
@@ -956,8 +970,7 @@ __device__ __noinline__ void batch_bwd_streamed(float2* sx, float2* sl, const TP
       const uint64_t tb = tile_base(t, p, g);
       load_tiles<true>(sx, wp + tb, sl, wl + tb, rowoff, m);
       __syncthreads();
-      for (int f = p.nphase - 1; f >= 0; --f)
-        run_phase_bwd<RB>(sx, sl, sp.ph + f, sp.ops, m, red, gacc, (uint32_t)tb);
+      run_tile_bwd<RB>(sx, sl, sp.ph, p.nphase, sp.ops, m, red, gacc, (uint32_t)tb);
       store_tiles<true>(sx, wp + tb, sl, wl + tb, rowoff, m);
       __syncthreads();
     }
@@ -1002,8 +1015,7 @@ __device__ __noinline__ void batch_fwd_streamed(float2* sx, float2* st, const TP
       const uint64_t tb = tile_base(t, p, g);
       load_tile(sx, st + tb, rowoff, m);
       __syncthreads();
-      for (int f = 0; f < p.nphase; ++f)
-        run_phase_fwd<RB, COMP>(sx, sp.ph + f, sp.ops, dtab, lo, dtlo, m, (uint32_t)tb);
+      run_tile_fwd<RB, COMP>(sx, sp.ph, p.nphase, sp.ops, dtab, lo, dtlo, m, (uint32_t)tb);
       store_tile(sx, st + tb, rowoff, m);
       __syncthreads();
     }
@@ -1055,8 +1067,7 @@ __global__ void __launch_bounds__(kTileThreads, kBatchMinBlocks<RB, PREC>) k_bat
       }
       __syncthreads();
       for (int pi = 0; pi < R.npass; ++pi)
-        for (int f = 0; f < P[pi].nphase; ++f)
-          run_phase_fwd<RB, PREC>(sx, a.phases + P[pi].phase0 + f, a.fops, a.dtab, a.flo, a.dtlo, m, 0u);
+        run_tile_fwd<RB, PREC>(sx, a.phases + P[pi].phase0, P[pi].nphase, a.fops, a.dtab, a.flo, a.dtlo, m, 0u);
       store_tile(sx, st, S.rowoff, m);  // psi_N
       if (PREC) {
         block_loss(expect_tile_ff(sx, sxf, slf, 0, S.rowoff, m, a.terms + R.term0, R.nterm), S, a.loss + reg);
@@ -1160,8 +1171,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_fused_pass(FArgs a) {
     float2* base = a.state + r * a.reg_stride + tb;
     load_tile(sx, base, rowoff, a.m);
     __syncthreads();
-    for (int f = 0; f < p.nphase; ++f)
-      run_phase_fwd<kRB, false>(sx, sp.ph + f, sp.ops, a.dtab, nullptr, nullptr, a.m, (uint32_t)tb);
+    run_tile_fwd<kRB, false>(sx, sp.ph, p.nphase, sp.ops, a.dtab, nullptr, nullptr, a.m, (uint32_t)tb);
     store_tile(sx, base, rowoff, a.m);
     __syncthreads();
   }
@@ -1200,8 +1210,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_fused_bwd_pass(FBArgs a) {
     const uint64_t tb = tile_base(t, p, a.g);
     load_tiles<true>(sx, a.wpsi + tb, sl, a.wlam + tb, rowoff, a.m);
     __syncthreads();
-    for (int f = p.nphase - 1; f >= 0; --f)
-      run_phase_bwd<kRB>(sx, sl, sp.ph + f, sp.ops, a.m, red, gacc, (uint32_t)tb);
+    run_tile_bwd<kRB>(sx, sl, sp.ph, p.nphase, sp.ops, a.m, red, gacc, (uint32_t)tb);
     store_tiles<true>(sx, a.wpsi + tb, sl, a.wlam + tb, rowoff, a.m);
     __syncthreads();
   }
