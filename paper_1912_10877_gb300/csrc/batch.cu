@@ -756,27 +756,71 @@ __device__ __forceinline__ float diagout_bwd_ff(ffc (&x)[1 << RB], ffc (&l)[1 <<
   return diagout_sign(op, b) * acc;
 }
 
-// fold the warp partials of every parameterised op of a phase in FP64; ops
-// whose parameter is unique in the phase in parallel, the others by one thread
+// Warp sums of the gradient ops' lane partials, two ops at a time: the two
+// shuffle trees interleave, so a warp waits on one chain of shuffle latencies
+// per pair of ops instead of per op.  pend / pend_o hold the first op of a pair
+// (pend_o is the same in every lane).
+__device__ __forceinline__ void warp_partial(float part, int o, float& pend, int& pend_o, float* red, int lane,
+                                             int warp) {
+  if (pend_o < 0) {
+    pend = part;
+    pend_o = o;
+    return;
+  }
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    pend += __shfl_xor_sync(0xffffffffu, pend, s);
+    part += __shfl_xor_sync(0xffffffffu, part, s);
+  }
+  if (lane == 0) {
+    red[pend_o * kWarps + warp] = pend;
+    red[o * kWarps + warp] = part;
+  }
+  pend_o = -1;
+}
+__device__ __forceinline__ void flush_partial(float pend, int pend_o, float* red, int lane, int warp) {
+  if (pend_o < 0) return;
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) pend += __shfl_xor_sync(0xffffffffu, pend, s);
+  if (lane == 0) red[pend_o * kWarps + warp] = pend;
+}
+
+// fold the warp partials of every parameterised op of a phase: the 16 warp
+// partials of an op are summed by 16 lanes in a TwoSum tree (the double-float
+// sum s + e of the FP32 partials, exact to ~2^-48), one op per 16 lanes, all
+// ops at once; the leader adds (s + e) cfac2 to the FP64 accumulator.  Ops whose
+// parameter another op of the phase shares are added by one thread afterwards.
+// (FP64 arithmetic runs at 1/64 of the FP32 rate here: summing in FP64 took
+// one warp thousands of cycles per phase while the others waited.)
 __device__ __forceinline__ void fold_phase_grad(const TPhase& ph, const TOp* bops, const float* red, double* gacc) {
-  const int nw = (int)(blockDim.x / 32);
+  static_assert(kWarps == 16, "one op per 16 lanes");
   const int nbop = ph.nbop, bop0 = ph.bop0;
-  const int o = threadIdx.x;
-  if (o < nbop) {
-    const TOp& op = bops[bop0 + o];
-    if (op.gen != GEN_NONE && !op.shared) {
-      double v = 0.0;
-      for (int w = 0; w < nw; ++w) v += (double)red[o * kWarps + w];
-      gacc[op.param] += (double)op.cfac2 * v;
+  for (int base = 0; base < nbop * kWarps; base += blockDim.x) {
+    const int t = base + (int)threadIdx.x;
+    const int o = t >> 4, w = t & 15;
+    const bool valid = o < nbop && bops[bop0 + o].gen != GEN_NONE;
+    float s = valid ? red[o * kWarps + w] : 0.f, e = 0.f;
+#pragma unroll
+    for (int d = 8; d > 0; d >>= 1) {
+      const float so = __shfl_xor_sync(0xffffffffu, s, d), eo = __shfl_xor_sync(0xffffffffu, e, d);
+      float q, r;
+      two_sum(s, so, q, r);
+      s = q;
+      e = __fadd_rn(__fadd_rn(e, eo), r);
+    }
+    if (w == 0 && valid) {
+      const TOp& op = bops[bop0 + o];
+      if (!op.shared) gacc[op.param] += (double)op.cfac2 * ((double)s + (double)e);
     }
   }
   __syncthreads();
+  if (ph.nshared == 0) return;
   if (threadIdx.x == 0) {
     for (int q = 0; q < nbop; ++q) {
       const TOp& op = bops[bop0 + q];
       if (op.gen == GEN_NONE || !op.shared) continue;
       double v = 0.0;
-      for (int w = 0; w < nw; ++w) v += (double)red[q * kWarps + w];
+      for (int w = 0; w < kWarps; ++w) v += (double)red[q * kWarps + w];
       gacc[op.param] += (double)op.cfac2 * v;
     }
   }
@@ -805,16 +849,16 @@ __device__ __forceinline__ void phase_bwd_body(float2* sx, float2* sl, const TPh
       l[j] = sl[o];
     }
   }
+  float pend = 0.f;  // warp partial of a gradient op waiting for a partner (pend_o >= 0)
+  int pend_o = -1;
   for (int o = nbop - 1; o >= 0; --o) {
     const TOp& op = bops[bop0 + o];
     float part = 0.f;
     if (active && (gb & op.tmask) == op.tval)
       part = op.kind == TK_DIAGOUT ? diagout_bwd<RB>(x, l, op, gb) : apply_bwd<RB>(x, l, op);
-    if (op.gen != GEN_NONE) {
-      for (int s = 16; s > 0; s >>= 1) part += __shfl_xor_sync(0xffffffffu, part, s);
-      if (lane == 0) red[o * kWarps + warp] = part;
-    }
+    if (op.gen != GEN_NONE) warp_partial(part, o, pend, pend_o, red, lane, warp);
   }
+  flush_partial(pend, pend_o, red, lane, warp);
   if (active) {
 #pragma unroll
     for (int j = 0; j < A; ++j) {
@@ -858,6 +902,8 @@ __device__ __noinline__ void run_phase_bwd_ff(float4* sx, float4* sl, const TPha
       l[j].l = make_float2(b.z, b.w);
     }
   }
+  float pend = 0.f;
+  int pend_o = -1;
   for (int o = nbop - 1; o >= 0; --o) {
     const int oi = bop0 + o;
     const TOp& op = bops[oi];
@@ -865,11 +911,9 @@ __device__ __noinline__ void run_phase_bwd_ff(float4* sx, float4* sl, const TPha
     if (active && (gb & op.tmask) == op.tval)
       part = op.kind == TK_DIAGOUT ? diagout_bwd_ff<RB>(x, l, op, blo + 4 * oi, gb)
                                    : apply_bwd_ff<RB>(x, l, op, blo + 4 * oi);
-    if (op.gen != GEN_NONE) {
-      for (int s = 16; s > 0; s >>= 1) part += __shfl_xor_sync(0xffffffffu, part, s);
-      if (lane == 0) red[o * kWarps + warp] = part;
-    }
+    if (op.gen != GEN_NONE) warp_partial(part, o, pend, pend_o, red, lane, warp);
   }
+  flush_partial(pend, pend_o, red, lane, warp);
   if (active) {
 #pragma unroll
     for (int j = 0; j < A; ++j) {
@@ -1683,6 +1727,8 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
         }
         t.nbop = (int)bops.size() - t.bop0;
         t.nfop = (int)fops.size() - t.fop0;
+        t.nshared = 0;
+        for (int q = t.bop0; q < (int)bops.size(); ++q) t.nshared += bops[q].shared ? 1 : 0;
         if (t.nbop > kMaxPhaseOps) return fail(QS_EUNSUPPORTED, "phase with %d ops", t.nbop);
         phases.push_back(t);
         cost += (double)(1ll << n) * (1 + 0.02 * t.nbop);

@@ -60,6 +60,7 @@ struct TPhase {
   uint16_t sroff[1 << kRB]; // swz(register offset of amplitude j): slot = swz(base) ^ sroff[j]
   int32_t fop0, nfop;       // forward ops (fused), applied in order
   int32_t bop0, nbop;       // backward ops (unfused), applied in reverse order
+  int32_t nshared;          // backward ops whose parameter another op of the phase shares
 };
 
 struct TPass {
