@@ -583,6 +583,32 @@ __device__ __forceinline__ uint32_t slot(const PhaseSlots& p, int j) {
   return o;
 }
 
+// An op record in registers from four 16-byte loads issued together: one
+// memory latency per op, instead of a chain of dependent field loads behind
+// the op's control test and kind branches
+__device__ __forceinline__ TOp load_op(const TOp* p) {
+  const uint4* s = reinterpret_cast<const uint4*>(p);
+  const uint4 a = s[0], b = s[1], c = s[2], d = s[3];
+  TOp r;
+  r.kind = (uint8_t)(a.x & 0xffu);
+  r.t = (uint8_t)((a.x >> 8) & 0xffu);
+  r.cmask = (uint8_t)((a.x >> 16) & 0xffu);
+  r.cval = (uint8_t)(a.x >> 24);
+  r.gen = (uint8_t)(a.y & 0xffu);
+  r.shared = (uint8_t)((a.y >> 8) & 0xffu);
+  r.pad[0] = r.pad[1] = 0;
+  r.param = (int32_t)a.z;
+  r.cfac2 = __uint_as_float(a.w);
+  r.tmask = b.x;
+  r.tval = b.y;
+  r.pad2 = 0;
+  r.u[0] = make_float2(__uint_as_float(c.x), __uint_as_float(c.y));
+  r.u[1] = make_float2(__uint_as_float(c.z), __uint_as_float(c.w));
+  r.u[2] = make_float2(__uint_as_float(d.x), __uint_as_float(d.y));
+  r.u[3] = make_float2(__uint_as_float(d.z), __uint_as_float(d.w));
+  return r;
+}
+
 // ---- shared-memory copies of a pass's phase records and ops
 //
 // Every tile of a pass runs the same phases, so a CTA that streams tiles reads
@@ -661,7 +687,7 @@ __device__ __forceinline__ void phase_fwd_body(float2* sm, const TPhase* php, co
     bool has_pend = false;
     for (int o = 0; o < ph.nfop; ++o) {
       const int oi = ph.fop0 + o;
-      const TOp& cur = fops[oi];
+      const TOp cur = load_op(fops + oi);
       if ((gb & cur.tmask) != cur.tval) continue;
       if (cur.kind == TK_DIAGOUT) {
         const bool b1 = (gb >> cur.t) & 1u;
@@ -852,7 +878,7 @@ __device__ __forceinline__ void phase_bwd_body(float2* sx, float2* sl, const TPh
   float pend = 0.f;  // warp partial of a gradient op waiting for a partner (pend_o >= 0)
   int pend_o = -1;
   for (int o = nbop - 1; o >= 0; --o) {
-    const TOp& op = bops[bop0 + o];
+    const TOp op = load_op(bops + bop0 + o);
     float part = 0.f;
     if (active && (gb & op.tmask) == op.tval)
       part = op.kind == TK_DIAGOUT ? diagout_bwd<RB>(x, l, op, gb) : apply_bwd<RB>(x, l, op);
@@ -906,7 +932,7 @@ __device__ __noinline__ void run_phase_bwd_ff(float4* sx, float4* sl, const TPha
   int pend_o = -1;
   for (int o = nbop - 1; o >= 0; --o) {
     const int oi = bop0 + o;
-    const TOp& op = bops[oi];
+    const TOp op = load_op(bops + oi);
     float part = 0.f;
     if (active && (gb & op.tmask) == op.tval)
       part = op.kind == TK_DIAGOUT ? diagout_bwd_ff<RB>(x, l, op, blo + 4 * oi, gb)
