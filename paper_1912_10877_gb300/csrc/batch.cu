@@ -209,6 +209,55 @@ __device__ __forceinline__ void op_fwd_k(float2 (&x)[1 << RB], const TOp& op, co
   }
 }
 
+// Forward op forms by TOp::var: 0 out-of-phase diagonal, 1 diagonal table,
+// 2 + t controlled swap, 6 + t / 10 + t diagonal without / with phase-local
+// controls, 14 + t / 18 + t dense without / with them (t: target phase bit)
+enum { FV_DIAGOUT = 0, FV_DIAG16 = 1, FV_SWAP = 2, FV_DIAG = 6, FV_DIAGC = 10, FV_DENSE = 14, FV_DENSEC = 18,
+       FV_COUNT = 22 };
+
+template <int RB, int T, int KIND, bool CTRL, bool COMP>
+__device__ __forceinline__ void fwd_form(float2 (&x)[1 << RB], const TOp& op, const float2* lo) {
+  if constexpr (T < RB) {
+    if constexpr (KIND == TK_SWAP) {
+      op_fwd<RB, T, TK_SWAP, true>(x, op);
+    } else if constexpr (COMP) {
+      op_fwd_c<RB, T, KIND, CTRL>(x, op, lo);
+    } else if constexpr (KIND == TK_DIAG) {
+      if (op.u[0].x == 1.f && op.u[0].y == 0.f) op_fwd<RB, T, TK_DIAGB, CTRL>(x, op);
+      else op_fwd<RB, T, TK_DIAG, CTRL>(x, op);
+    } else {
+      op_fwd<RB, T, KIND, CTRL>(x, op);
+    }
+  }
+}
+
+template <int RB, bool COMP>
+__device__ __forceinline__ void apply_fwd_var(float2 (&x)[1 << RB], const TOp& op, const float2* lo) {
+  switch (op.var) {
+    case FV_SWAP + 0: fwd_form<RB, 0, TK_SWAP, true, COMP>(x, op, lo); break;
+    case FV_SWAP + 1: fwd_form<RB, 1, TK_SWAP, true, COMP>(x, op, lo); break;
+    case FV_SWAP + 2: fwd_form<RB, 2, TK_SWAP, true, COMP>(x, op, lo); break;
+    case FV_SWAP + 3: fwd_form<RB, 3, TK_SWAP, true, COMP>(x, op, lo); break;
+    case FV_DIAG + 0: fwd_form<RB, 0, TK_DIAG, false, COMP>(x, op, lo); break;
+    case FV_DIAG + 1: fwd_form<RB, 1, TK_DIAG, false, COMP>(x, op, lo); break;
+    case FV_DIAG + 2: fwd_form<RB, 2, TK_DIAG, false, COMP>(x, op, lo); break;
+    case FV_DIAG + 3: fwd_form<RB, 3, TK_DIAG, false, COMP>(x, op, lo); break;
+    case FV_DIAGC + 0: fwd_form<RB, 0, TK_DIAG, true, COMP>(x, op, lo); break;
+    case FV_DIAGC + 1: fwd_form<RB, 1, TK_DIAG, true, COMP>(x, op, lo); break;
+    case FV_DIAGC + 2: fwd_form<RB, 2, TK_DIAG, true, COMP>(x, op, lo); break;
+    case FV_DIAGC + 3: fwd_form<RB, 3, TK_DIAG, true, COMP>(x, op, lo); break;
+    case FV_DENSE + 0: fwd_form<RB, 0, TK_DENSE, false, COMP>(x, op, lo); break;
+    case FV_DENSE + 1: fwd_form<RB, 1, TK_DENSE, false, COMP>(x, op, lo); break;
+    case FV_DENSE + 2: fwd_form<RB, 2, TK_DENSE, false, COMP>(x, op, lo); break;
+    case FV_DENSE + 3: fwd_form<RB, 3, TK_DENSE, false, COMP>(x, op, lo); break;
+    case FV_DENSEC + 0: fwd_form<RB, 0, TK_DENSE, true, COMP>(x, op, lo); break;
+    case FV_DENSEC + 1: fwd_form<RB, 1, TK_DENSE, true, COMP>(x, op, lo); break;
+    case FV_DENSEC + 2: fwd_form<RB, 2, TK_DENSE, true, COMP>(x, op, lo); break;
+    case FV_DENSEC + 3: fwd_form<RB, 3, TK_DENSE, true, COMP>(x, op, lo); break;
+    default: break;
+  }
+}
+
 template <int RB, bool COMP>
 __device__ __forceinline__ void apply_fwd(float2 (&x)[1 << RB], const TOp& op, const float2* lo) {
   switch (op.t) {
@@ -596,7 +645,8 @@ __device__ __forceinline__ TOp load_op(const TOp* p) {
   r.cval = (uint8_t)(a.x >> 24);
   r.gen = (uint8_t)(a.y & 0xffu);
   r.shared = (uint8_t)((a.y >> 8) & 0xffu);
-  r.pad[0] = r.pad[1] = 0;
+  r.var = (uint8_t)((a.y >> 16) & 0xffu);
+  r.pad = 0;
   r.param = (int32_t)a.z;
   r.cfac2 = __uint_as_float(a.w);
   r.tmask = b.x;
@@ -716,7 +766,7 @@ __device__ __forceinline__ void phase_fwd_body(float2* sm, const TPhase* php, co
           for (int j = 0; j < A; ++j) x[j] = cmulf(x[j], t[j]);
         }
       } else {
-        apply_fwd<RB, COMP>(x, cur, COMP ? flo + 4 * oi : nullptr);
+        apply_fwd_var<RB, COMP>(x, cur, COMP ? flo + 4 * oi : nullptr);
       }
     }
     if (!COMP && has_pend) {
@@ -1538,6 +1588,17 @@ static void free_program(qs_batch_program* p) {
 // largest tile of the batched kernel for rb-bit phases: 512 threads x 2^rb amplitudes
 static int max_tile(int rb) { return std::min(kBatchTile, 9 + rb); }
 
+// TOp::var of a forward op (FV_* forms)
+static uint8_t fwd_variant(const TOp& f) {
+  switch (f.kind) {
+    case TK_DIAGOUT: return FV_DIAGOUT;
+    case TK_DIAG16: return FV_DIAG16;
+    case TK_SWAP: return (uint8_t)(FV_SWAP + f.t);
+    case TK_DIAG: return (uint8_t)((f.cmask ? FV_DIAGC : FV_DIAG) + f.t);
+    default: return (uint8_t)((f.cmask ? FV_DENSEC : FV_DENSE) + f.t);
+  }
+}
+
 static int build_program(int nreg, const qs_circuit* const* circs, const qs_observable* const* obs, int tile_qubits,
                          qs_batch_program* P, int rb = kRB, bool precise = false) {
   if (rb < kMinRB || rb > kRB) return fail(QS_EINVAL, "phase_qubits must be in %d..%d", kMinRB, kRB);
@@ -1763,6 +1824,7 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
     }
     R.cost = cost;
   }
+  for (TOp& f : fops) f.var = fwd_variant(f);
   // decreasing cost order
   std::vector<int32_t> order(nreg);
   std::iota(order.begin(), order.end(), 0);

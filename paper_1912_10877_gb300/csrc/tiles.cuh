@@ -36,7 +36,8 @@ struct TOp {
   uint8_t cval;   // their required values
   uint8_t gen;    // backward ops: generator code (GEN_*), 0 = no parameter
   uint8_t shared; // backward ops: the parameter also appears in another op of the phase
-  uint8_t pad[2];
+  uint8_t var;    // forward ops: the specialised form (fwd_variant), one jump per op
+  uint8_t pad;
   int32_t param;  // register-local parameter index (forward TK_DIAG16: table index), -1 = none
   float cfac2;    // 2 c for U = exp(-i theta c H)
   uint32_t tmask; // controls outside the phase (register qubit bits)
