@@ -71,6 +71,7 @@ struct BArgs {
   const TOp* fops;
   const TOp* bops;
   const float2* dtab;    // TK_DIAG16 factor tables
+  const DRun* druns;     // TK_DIAGRUN entries
   const BTerm* terms;
   double* loss;
   double* grad;
@@ -209,11 +210,50 @@ __device__ __forceinline__ void op_fwd_k(float2 (&x)[1 << RB], const TOp& op, co
   }
 }
 
+// x_j *= (bit T of j ? p1 : p0)
+template <int RB, int T>
+__device__ __forceinline__ void mul_by_bit(float2 (&x)[1 << RB], float2 p0, float2 p1) {
+#pragma unroll
+  for (int j = 0; j < (1 << RB); ++j) x[j] = cmulf(x[j], ((j >> T) & 1) ? p1 : p0);
+}
+
+// a TK_DIAGRUN op: the products p0, p1 of its entries' factors where their
+// controls hold (selects, no branch on the thread's bits), then one pass over
+// the amplitudes by phase bit t
+template <int RB>
+__device__ __forceinline__ void diag_run(float2 (&x)[1 << RB], const TOp& op, const DRun* runs, uint32_t gb) {
+  float2 p0 = make_float2(1.f, 0.f), p1 = p0;
+  const DRun* e = runs + op.param;
+#pragma unroll 2
+  for (uint32_t k = 0; k < op.count; ++k) {
+    const uint4* w = reinterpret_cast<const uint4*>(e + k);
+    const uint4 a = w[0], b = w[1];  // tmask, tval, gate, tq | u0, u3
+    const float2 u0 = make_float2(__uint_as_float(b.x), __uint_as_float(b.y));
+    const float2 u3 = make_float2(__uint_as_float(b.z), __uint_as_float(b.w));
+    const bool on = (gb & a.x) == a.y;
+    float2 f0 = u0, f1 = u3;
+    if (a.w != 0xffffffffu) {  // target outside the phase: one factor by its bit
+      f0 = ((gb >> (a.w & 31u)) & 1u) ? u3 : u0;
+      f1 = f0;
+    }
+    const float2 q0 = cmulf(p0, f0), q1 = cmulf(p1, f1);
+    p0 = on ? q0 : p0;
+    p1 = on ? q1 : p1;
+  }
+  switch (op.t) {
+    case 0: mul_by_bit<RB, 0>(x, p0, p1); break;
+    case 1: mul_by_bit<RB, 1>(x, p0, p1); break;
+    case 2: if constexpr (RB > 2) mul_by_bit<RB, 2>(x, p0, p1); break;
+    default: if constexpr (RB > 3) mul_by_bit<RB, 3>(x, p0, p1); break;
+  }
+}
+
 // Forward op forms by TOp::var: 0 out-of-phase diagonal, 1 diagonal table,
 // 2 + t controlled swap, 6 + t / 10 + t diagonal without / with phase-local
-// controls, 14 + t / 18 + t dense without / with them (t: target phase bit)
+// controls, 14 + t / 18 + t dense without / with them (t: target phase bit),
+// 22 a run of diagonal gates (TK_DIAGRUN)
 enum { FV_DIAGOUT = 0, FV_DIAG16 = 1, FV_SWAP = 2, FV_DIAG = 6, FV_DIAGC = 10, FV_DENSE = 14, FV_DENSEC = 18,
-       FV_COUNT = 22 };
+       FV_DIAGRUN = 22 };
 
 template <int RB, int T, int KIND, bool CTRL, bool COMP>
 __device__ __forceinline__ void fwd_form(float2 (&x)[1 << RB], const TOp& op, const float2* lo) {
@@ -232,8 +272,12 @@ __device__ __forceinline__ void fwd_form(float2 (&x)[1 << RB], const TOp& op, co
 }
 
 template <int RB, bool COMP>
-__device__ __forceinline__ void apply_fwd_var(float2 (&x)[1 << RB], const TOp& op, const float2* lo) {
+__device__ __forceinline__ void apply_fwd_var(float2 (&x)[1 << RB], const TOp& op, const float2* lo,
+                                              const DRun* runs, uint32_t gb) {
   switch (op.var) {
+    case FV_DIAGRUN:
+      if constexpr (!COMP) diag_run<RB>(x, op, runs, gb);
+      break;
     case FV_SWAP + 0: fwd_form<RB, 0, TK_SWAP, true, COMP>(x, op, lo); break;
     case FV_SWAP + 1: fwd_form<RB, 1, TK_SWAP, true, COMP>(x, op, lo); break;
     case FV_SWAP + 2: fwd_form<RB, 2, TK_SWAP, true, COMP>(x, op, lo); break;
@@ -651,7 +695,7 @@ __device__ __forceinline__ TOp load_op(const TOp* p) {
   r.cfac2 = __uint_as_float(a.w);
   r.tmask = b.x;
   r.tval = b.y;
-  r.pad2 = 0;
+  r.count = b.z;
   r.u[0] = make_float2(__uint_as_float(c.x), __uint_as_float(c.y));
   r.u[1] = make_float2(__uint_as_float(c.z), __uint_as_float(c.w));
   r.u[2] = make_float2(__uint_as_float(d.x), __uint_as_float(d.y));
@@ -671,23 +715,28 @@ __device__ __forceinline__ TOp load_op(const TOp* p) {
 // area keeps reading global memory.
 constexpr int kStagePhases = 32;
 constexpr int kStageOps = 512;
+constexpr int kStageRuns = 256;
 static_assert(sizeof(TOp) == 64 && sizeof(TOp) % 16 == 0, "TOp is copied as 16-byte words");
+static_assert(sizeof(DRun) == 32, "DRun is copied as 16-byte words");
 constexpr size_t kStagePhaseBytes = (sizeof(TPhase) * kStagePhases + 15) & ~size_t(15);
-constexpr size_t kStageBytes = kStagePhaseBytes + sizeof(TOp) * kStageOps;
+constexpr size_t kStageBytes = kStagePhaseBytes + sizeof(TOp) * kStageOps + sizeof(DRun) * kStageRuns;
 
 struct StagedPass {
   const TPhase* ph;  // the pass's first phase
   const TOp* ops;    // op table the phases index
   int first;         // index of ops[0] in the global op table (0 when not staged)
+  const DRun* runs;  // the pass's TK_DIAGRUN entries (forward)
 };
 
 // FWD: the forward ops (fop0 / nfop), else the backward ops (bop0 / nbop).
 // buf: kStageBytes of shared memory, or nullptr.  Every thread of the CTA
 // calls this (it ends with a barrier when it copies).
 template <bool FWD>
-__device__ StagedPass stage_pass(const TPass& p, const TPhase* phases, const TOp* ops, unsigned char* buf) {
-  StagedPass r{phases + p.phase0, ops, 0};
+__device__ StagedPass stage_pass(const TPass& p, const TPhase* phases, const TOp* ops, unsigned char* buf,
+                                 const DRun* druns = nullptr) {
+  StagedPass r{phases + p.phase0, ops, 0, druns ? druns + p.drun0 : nullptr};
   if (!buf || p.nphase <= 0 || p.nphase > kStagePhases) return r;
+  if (FWD && druns && p.ndrun > kStageRuns) return r;
   const TPhase& f0 = phases[p.phase0];
   const TPhase& fl = phases[p.phase0 + p.nphase - 1];
   const int first = FWD ? f0.fop0 : f0.bop0;
@@ -705,8 +754,16 @@ __device__ StagedPass stage_pass(const TPass& p, const TPhase* phases, const TOp
     else q.bop0 -= first;
     sph[threadIdx.x] = q;
   }
+  const DRun* runs = nullptr;
+  if (FWD && druns) {
+    DRun* srun = reinterpret_cast<DRun*>(buf + kStagePhaseBytes + sizeof(TOp) * kStageOps);
+    const uint4* rs = reinterpret_cast<const uint4*>(druns + p.drun0);
+    uint4* rd = reinterpret_cast<uint4*>(srun);
+    for (int i = threadIdx.x; i < p.ndrun * 2; i += blockDim.x) rd[i] = rs[i];
+    runs = srun;
+  }
   __syncthreads();
-  return StagedPass{sph, sop, first};
+  return StagedPass{sph, sop, first, runs};
 }
 
 // out-of-phase diagonal gate with phase-local controls: x_j *= f where (j & cm) == cv
@@ -721,7 +778,8 @@ __device__ __forceinline__ void diag_masked(float2 (&x)[1 << RB], float2 f, int 
 // diagonal table); out-of-phase diagonal factors are then applied one by one
 template <int RB, bool COMP>
 __device__ __forceinline__ void phase_fwd_body(float2* sm, const TPhase* php, const TOp* fops, const float2* dtab,
-                                               const float2* flo, const float2* dtlo, int m, uint32_t tbase) {
+                                               const float2* flo, const float2* dtlo, const DRun* runs, int m,
+                                               uint32_t tbase) {
   constexpr int A = 1 << RB;
   const TPhase& ph = *php;
   const int ntb = m - RB;
@@ -766,7 +824,7 @@ __device__ __forceinline__ void phase_fwd_body(float2* sm, const TPhase* php, co
           for (int j = 0; j < A; ++j) x[j] = cmulf(x[j], t[j]);
         }
       } else {
-        apply_fwd_var<RB, COMP>(x, cur, COMP ? flo + 4 * oi : nullptr);
+        apply_fwd_var<RB, COMP>(x, cur, COMP ? flo + 4 * oi : nullptr, runs, gb);
       }
     }
     if (!COMP && has_pend) {
@@ -782,9 +840,9 @@ __device__ __forceinline__ void phase_fwd_body(float2* sm, const TPhase* php, co
 // All phases of a pass on one tile, in order (one call per tile)
 template <int RB, bool COMP>
 __device__ __noinline__ void run_tile_fwd(float2* sm, const TPhase* ph, int nphase, const TOp* fops,
-                                          const float2* dtab, const float2* flo, const float2* dtlo, int m,
-                                          uint32_t tbase) {
-  for (int f = 0; f < nphase; ++f) phase_fwd_body<RB, COMP>(sm, ph + f, fops, dtab, flo, dtlo, m, tbase);
+                                          const float2* dtab, const float2* flo, const float2* dtlo,
+                                          const DRun* runs, int m, uint32_t tbase) {
+  for (int f = 0; f < nphase; ++f) phase_fwd_body<RB, COMP>(sm, ph + f, fops, dtab, flo, dtlo, runs, m, tbase);
 }
 
 // backward of an out-of-phase diagonal gate: the generator is diagonal on the
@@ -1123,19 +1181,19 @@ __device__ __noinline__ void batch_bwd_streamed_ff(float4* sx, float4* sl, const
 template <int RB, bool COMP>
 __device__ __noinline__ void batch_fwd_streamed(float2* sx, float2* st, const TPass* P, int npass, int m, int g,
                                                 const TPhase* phases, const TOp* fops, const float2* dtab,
-                                                const float2* flo, const float2* dtlo, uint32_t* rowoff,
-                                                unsigned char* stage) {
+                                                const float2* flo, const float2* dtlo, const DRun* druns,
+                                                uint32_t* rowoff, unsigned char* stage) {
   const uint64_t ntile = 1ull << g;
   for (int pi = 0; pi < npass; ++pi) {
     const TPass& p = P[pi];
     set_rows(rowoff, p, m);
-    const StagedPass sp = stage_pass<true>(p, phases, fops, stage);
+    const StagedPass sp = stage_pass<true>(p, phases, fops, stage, druns);
     const float2* lo = COMP ? flo + 4 * (size_t)sp.first : nullptr;
     for (uint64_t t = 0; t < ntile; ++t) {
       const uint64_t tb = tile_base(t, p, g);
       load_tile(sx, st + tb, rowoff, m);
       __syncthreads();
-      run_tile_fwd<RB, COMP>(sx, sp.ph, p.nphase, sp.ops, dtab, lo, dtlo, m, (uint32_t)tb);
+      run_tile_fwd<RB, COMP>(sx, sp.ph, p.nphase, sp.ops, dtab, lo, dtlo, sp.runs, m, (uint32_t)tb);
       store_tile(sx, st + tb, rowoff, m);
       __syncthreads();
     }
@@ -1187,7 +1245,8 @@ __global__ void __launch_bounds__(kTileThreads, kBatchMinBlocks<RB, PREC>) k_bat
       }
       __syncthreads();
       for (int pi = 0; pi < R.npass; ++pi)
-        run_tile_fwd<RB, PREC>(sx, a.phases + P[pi].phase0, P[pi].nphase, a.fops, a.dtab, a.flo, a.dtlo, m, 0u);
+        run_tile_fwd<RB, PREC>(sx, a.phases + P[pi].phase0, P[pi].nphase, a.fops, a.dtab, a.flo, a.dtlo,
+                               a.druns + P[pi].drun0, m, 0u);
       store_tile(sx, st, S.rowoff, m);  // psi_N
       if (PREC) {
         block_loss(expect_tile_ff(sx, sxf, slf, 0, S.rowoff, m, a.terms + R.term0, R.nterm), S, a.loss + reg);
@@ -1204,8 +1263,8 @@ __global__ void __launch_bounds__(kTileThreads, kBatchMinBlocks<RB, PREC>) k_bat
         for (uint64_t i = tid; i < (1ull << n); i += blockDim.x) st[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
         __syncthreads();
       }
-      batch_fwd_streamed<RB, PREC>(sx, st, P, R.npass, m, g, a.phases, a.fops, a.dtab, a.flo, a.dtlo, S.rowoff,
-                                   stage);
+      batch_fwd_streamed<RB, PREC>(sx, st, P, R.npass, m, g, a.phases, a.fops, a.dtab, a.flo, a.dtlo, a.druns,
+                                   S.rowoff, stage);
       // expectation, lambda = O psi, and the work copy of psi for the uncompute
       double e = 0.0;
       const TPass& p0 = P[0];
@@ -1268,6 +1327,7 @@ struct FArgs {
   const TPhase* phases;
   const TOp* fops;
   const float2* dtab;
+  const DRun* druns;
   int m, g;
   uint64_t ntile;          // tiles per register
   uint64_t reg_stride;     // amplitudes per register
@@ -1283,7 +1343,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_fused_pass(FArgs a) {
   unsigned char* stage = reinterpret_cast<unsigned char*>(sx + (1 << kBatchTile));
   const TPass& p = *a.pass;
   set_rows(rowoff, p, a.m);
-  const StagedPass sp = stage_pass<true>(p, a.phases, a.fops, stage);
+  const StagedPass sp = stage_pass<true>(p, a.phases, a.fops, stage, a.druns);
   const uint64_t total = a.ntile * (uint64_t)a.nreg;
   for (uint64_t t = blockIdx.x; t < total; t += gridDim.x) {
     const uint64_t r = t / a.ntile, tl = t - r * a.ntile;
@@ -1291,7 +1351,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_fused_pass(FArgs a) {
     float2* base = a.state + r * a.reg_stride + tb;
     load_tile(sx, base, rowoff, a.m);
     __syncthreads();
-    run_tile_fwd<kRB, false>(sx, sp.ph, p.nphase, sp.ops, a.dtab, nullptr, nullptr, a.m, (uint32_t)tb);
+    run_tile_fwd<kRB, false>(sx, sp.ph, p.nphase, sp.ops, a.dtab, nullptr, nullptr, sp.runs, a.m, (uint32_t)tb);
     store_tile(sx, base, rowoff, a.m);
     __syncthreads();
   }
@@ -1400,8 +1460,9 @@ struct PrepArgs {
   TOp* fops;
   TOp* bops;
   float2* dtab;
+  DRun* druns;
   const double* params;
-  int nfop, nbop, ndiag;
+  int nfop, nbop, ndiag, ndrun;
 };
 
 __device__ void gate_mat(const GSpec& gs, const double* params, double2 (&U)[4]) {
@@ -1486,6 +1547,12 @@ __global__ void k_batch_prep(PrepArgs a) {
     for (int j = 0; j < 16; ++j) a.dtab[16 * d + j] = hi_of(f[j]);
     if (a.dtlo)
       for (int j = 0; j < 16; ++j) a.dtlo[16 * d + j] = lo_of(f[j]);
+  } else if (i < a.nfop + a.nbop + a.ndiag + a.ndrun) {
+    DRun& e = a.druns[i - a.nfop - a.nbop - a.ndiag];
+    double2 U[4];
+    gate_mat(a.gspec[e.gate], a.params, U);
+    e.u0 = hi_of(U[0]);
+    e.u3 = hi_of(U[3]);
   }
 }
 
@@ -1515,6 +1582,8 @@ struct qs_batch_program {
   qs::DRef* dref = nullptr;
   float2* dtab = nullptr;
   int ndiag = 0;
+  qs::DRun* druns = nullptr;  // TK_DIAGRUN entries
+  int ndrun = 0;
   int* counter = nullptr;
   float2* wpsi = nullptr;
   float2* wlam = nullptr;
@@ -1578,7 +1647,7 @@ static void free_program(qs_batch_program* p) {
                     cudaSetDevice(p->device) == cudaSuccess;
   void* ptrs[] = {p->regs, p->order, p->passes, p->phases, p->fops, p->bops, p->terms, p->gspec, p->fmem,
                   p->bgate, p->dmem, p->dref, p->dtab, p->counter, p->wpsi, p->wlam, p->dparams,
-                  p->flo, p->blo, p->dtlo, p->wpsif, p->wlamf};
+                  p->flo, p->blo, p->dtlo, p->wpsif, p->wlamf, p->druns};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (swap) cudaSetDevice(cur);
@@ -1593,6 +1662,7 @@ static uint8_t fwd_variant(const TOp& f) {
   switch (f.kind) {
     case TK_DIAGOUT: return FV_DIAGOUT;
     case TK_DIAG16: return FV_DIAG16;
+    case TK_DIAGRUN: return FV_DIAGRUN;
     case TK_SWAP: return (uint8_t)(FV_SWAP + f.t);
     case TK_DIAG: return (uint8_t)((f.cmask ? FV_DIAGC : FV_DIAG) + f.t);
     default: return (uint8_t)((f.cmask ? FV_DENSEC : FV_DENSE) + f.t);
@@ -1622,6 +1692,7 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
   std::vector<int32_t> bgate;
   std::vector<DMem> dmems;
   std::vector<DRef> drefs;
+  std::vector<DRun> druns;
   P->nreg = nreg;
   P->nq.resize(nreg);
   P->param_off.assign(nreg + 1, 0);
@@ -1688,6 +1759,7 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
       for (int qb = 0; qb < n; ++qb)
         if (std::find(p.tbits.begin(), p.tbits.end(), qb) == p.tbits.end()) tp.gbits[ng++] = (uint8_t)qb;
       tp.phase0 = (int)phases.size();
+      tp.drun0 = (int)druns.size();
       tp.nphase = (int)p.phases.size();
       for (const HostPhase& ph : p.phases) {
         TPhase t;
@@ -1702,6 +1774,13 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
         t.fop0 = (int)fops.size();
         std::vector<int> last(rb, -1);   // forward op index (in fops) open for fusion per phase bit
         int dg = -1;                     // open TK_DIAG16 table of this phase
+        // TK_DIAGRUN runs of this phase (complex64 path): the op each opened,
+        // its entries, the run open per phase bit and the latest run opened
+        std::vector<int> run_op;
+        std::vector<std::vector<DRun>> run_ent;
+        std::vector<int> run_bit;
+        std::vector<int> run_open(rb, -1);
+        int run_last = -1;
         uint8_t nondiag = 0;             // phase bits touched by non-diagonal gates since it opened
         for (int gi : ph.gates) {
           const qs_gate_desc& g = c->gates[gi];
@@ -1762,6 +1841,17 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
           memset(&fm, 0, sizeof(fm));
           fm.count = 1;
           fm.g[0] = g0 + gi;
+          if (tb < 0 && !precise && cm == 0 && run_last >= 0 && run_open[run_bit[run_last]] == run_last) {
+            // a scalar for each thread: commutes with every op of the phase
+            DRun e;
+            memset(&e, 0, sizeof(e));
+            e.tmask = tmask;
+            e.tval = tval;
+            e.gate = g0 + gi;
+            e.tq = (uint32_t)g.locs[0];
+            run_ent[run_last].push_back(e);
+            continue;
+          }
           if (tb < 0) {
             f.kind = TK_DIAGOUT;
             f.t = (uint8_t)g.locs[0];
@@ -1774,10 +1864,34 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
           const bool fusable = cm == 0 && tmask == 0 && g.kind != QS_GATE_X;
           const uint8_t gbits = (uint8_t)(cm | (1u << tb));
           if (!diag) nondiag |= gbits;
+          if (!diag) run_open[tb] = -1;  // a run moves no later gate past this one
           if (fusable && last[tb] >= 0 && fmem[last[tb]].count < 4) {
             FMem& fmo = fmem[last[tb]];
             fmo.g[fmo.count++] = g0 + gi;
             if (!diag) fops[last[tb]].kind = TK_DENSE;
+          } else if (!precise && diag && cm == 0 && tmask != 0) {
+            // joins (or opens) the run on its target: diagonal gates commute, and
+            // no non-diagonal op on this bit was emitted since the run opened
+            if (run_open[tb] < 0) {
+              f.kind = TK_DIAGRUN;
+              f.t = (uint8_t)tb;
+              f.tmask = f.tval = 0;
+              fm.count = 0;
+              run_open[tb] = (int)run_op.size();
+              run_last = run_open[tb];
+              run_op.push_back((int)fops.size());
+              run_ent.emplace_back();
+              run_bit.push_back(tb);
+              fops.push_back(f);
+              fmem.push_back(fm);
+            }
+            DRun e;
+            memset(&e, 0, sizeof(e));
+            e.tmask = tmask;
+            e.tval = tval;
+            e.gate = g0 + gi;
+            e.tq = 0xffffffffu;
+            run_ent[run_open[tb]].push_back(e);
           } else if (diag && cm != 0 && tmask == 0) {
             if (dg < 0 || (gbits & nondiag)) {
               f.kind = TK_DIAG16;
@@ -1812,6 +1926,23 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
             last[tb] = -1;
           }
         }
+        for (size_t r = 0; r < run_op.size(); ++r) {
+          TOp& ro = fops[run_op[r]];
+          if (run_ent[r].size() == 1) {
+            // a run of one gate stays that gate's own op (its outside controls as tmask)
+            const DRun& e = run_ent[r][0];
+            ro.kind = TK_DIAG;
+            ro.tmask = e.tmask;
+            ro.tval = e.tval;
+            ro.param = -1;
+            fmem[run_op[r]].count = 1;
+            fmem[run_op[r]].g[0] = e.gate;
+            continue;
+          }
+          ro.param = (int)druns.size() - tp.drun0;
+          ro.count = (uint32_t)run_ent[r].size();
+          druns.insert(druns.end(), run_ent[r].begin(), run_ent[r].end());
+        }
         t.nbop = (int)bops.size() - t.bop0;
         t.nfop = (int)fops.size() - t.fop0;
         t.nshared = 0;
@@ -1820,6 +1951,7 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
         phases.push_back(t);
         cost += (double)(1ll << n) * (1 + 0.02 * t.nbop);
       }
+      tp.ndrun = (int)druns.size() - tp.drun0;
       passes.push_back(tp);
     }
     R.cost = cost;
@@ -1847,6 +1979,8 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
   QS_TRY(upload(&P->dmem, dmems));
   QS_TRY(upload(&P->dref, drefs));
   P->ndiag = (int)drefs.size();
+  P->ndrun = (int)druns.size();
+  QS_TRY(upload(&P->druns, druns.empty() ? std::vector<DRun>(1) : druns));
   QS_TRY(upload(&P->dtab, std::vector<float2>(16 * std::max<size_t>(1, drefs.size()))));
   QS_TRY(upload(&P->counter, std::vector<int>(1, 0)));
   if (work > 0 && !precise) {
@@ -1905,11 +2039,13 @@ static int launch_prep(const qs_batch_program* P, const double* dev_params, bool
   pa.fops = P->fops;
   pa.bops = P->bops;
   pa.dtab = P->dtab;
+  pa.druns = P->druns;
   pa.params = dev_params;
   pa.nfop = P->nfop;
   pa.nbop = bwd ? P->nbop : 0;
   pa.ndiag = P->ndiag;
-  const int tot = pa.nfop + pa.nbop + pa.ndiag;
+  pa.ndrun = P->ndrun;
+  const int tot = pa.nfop + pa.nbop + pa.ndiag + pa.ndrun;
   if (tot > 0) {
     k_batch_prep<<<(tot + 255) / 256, 256, 0, st>>>(pa);
     QS_LAUNCHED();
@@ -2004,6 +2140,7 @@ int fused_forward(qs_state* s, const qs_circuit* c, const double* host_params, i
   a.phases = P->phases;
   a.fops = P->fops;
   a.dtab = P->dtab;
+  a.druns = P->druns;
   a.m = m;
   a.g = g;
   a.ntile = 1ull << g;
@@ -2335,6 +2472,7 @@ int qs_batch_run(qs_state* s, const qs_batch_program* p, const double* dev_param
   BArgs a;
   a.state = (float2*)s->data;
   a.dtab = p->dtab;
+  a.druns = p->druns;
   a.wpsi = p->wpsi;
   a.wlam = p->wlam;
   a.wpsif = p->wpsif;

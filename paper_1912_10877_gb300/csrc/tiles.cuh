@@ -42,7 +42,7 @@ struct TOp {
   float cfac2;    // 2 c for U = exp(-i theta c H)
   uint32_t tmask; // controls outside the phase (register qubit bits)
   uint32_t tval;
-  uint32_t pad2;
+  uint32_t count; // TK_DIAGRUN: entries (param: the first, relative to the pass's drun0)
   float2 u[4];    // forward: U; backward: U^dagger (row-major 2x2)
 };
 
@@ -51,7 +51,20 @@ struct TOp {
 // product of consecutive diagonal gates inside the phase (they commute);
 // TK_DIAGOUT: diagonal gate whose target qubit is outside the phase: every
 // amplitude of the thread takes the factor u0 or u3 by that qubit's value
-enum { TK_DENSE = 0, TK_SWAP = 1, TK_DIAG = 2, TK_RX = 3, TK_RY = 4, TK_DIAG16 = 5, TK_DIAGOUT = 6 };
+// TK_DIAGRUN (forward, complex64 path): a run of diagonal gates without
+// phase-local controls that all commute with the ops between them: each entry
+// (DRun) multiplies, where its outside controls hold, the amplitudes whose phase
+// bit t is 0 by one factor and those whose bit t is 1 by another (a scalar when
+// its target is outside the phase); the products are formed per thread and
+// applied to the amplitudes once
+enum { TK_DENSE = 0, TK_SWAP = 1, TK_DIAG = 2, TK_RX = 3, TK_RY = 4, TK_DIAG16 = 5, TK_DIAGOUT = 6, TK_DIAGRUN = 7 };
+
+struct DRun {
+  uint32_t tmask, tval;  // its controls (register qubit bits), all outside the phase
+  int32_t gate;          // gate spec index (the matrix is formed from the parameters on the device)
+  uint32_t tq;           // target register qubit when outside the phase (scalar entry), else 0xffffffff
+  float2 u0, u3;         // the gate's diagonal
+};
 enum { GEN_NONE = 0, GEN_X = 1, GEN_Y = 2, GEN_Z = 3, GEN_P1 = 4, GEN_I = 5 };
 
 struct TPhase {
@@ -68,6 +81,7 @@ struct TPass {
   uint8_t tbits[16];        // register qubits of tile-local bits 0..m-1 (ascending)
   uint8_t gbits[32];        // register qubits of the tile-id bits (ascending)
   int32_t phase0, nphase;
+  int32_t drun0, ndrun;     // the pass's TK_DIAGRUN entries
 };
 
 struct HostPhase {
