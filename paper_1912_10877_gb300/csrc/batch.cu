@@ -1178,25 +1178,50 @@ __device__ __noinline__ void batch_bwd_streamed_ff(float4* sx, float4* sl, const
   }
 }
 
+// cp.async copies (8 bytes each: the swizzled slots of a 16-byte pair may be
+// swapped) of the next tile into a second buffer while the current one is computed
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// issue the copies of one tile (2^m amplitudes) into sm (no wait)
+__device__ __forceinline__ void load_tile_async(float2* sm, const float2* src, const uint32_t* rowoff, int m) {
+  const uint32_t n = 1u << m;
+  for (uint32_t l = threadIdx.x; l < n; l += kTileThreads)
+    cp_async8(sm + swz(l), src + rowoff[l >> kRowBits] + (l & 31u));
+}
+
 template <int RB, bool COMP>
-__device__ __noinline__ void batch_fwd_streamed(float2* sx, float2* st, const TPass* P, int npass, int m, int g,
-                                                const TPhase* phases, const TOp* fops, const float2* dtab,
-                                                const float2* flo, const float2* dtlo, const DRun* druns,
-                                                uint32_t* rowoff, unsigned char* stage) {
+__device__ __noinline__ void batch_fwd_streamed(float2* sx, float2* sx2, float2* st, const TPass* P, int npass,
+                                                int m, int g, const TPhase* phases, const TOp* fops,
+                                                const float2* dtab, const float2* flo, const float2* dtlo,
+                                                const DRun* druns, uint32_t* rowoff, unsigned char* stage) {
   const uint64_t ntile = 1ull << g;
   for (int pi = 0; pi < npass; ++pi) {
     const TPass& p = P[pi];
     set_rows(rowoff, p, m);
     const StagedPass sp = stage_pass<true>(p, phases, fops, stage, druns);
     const float2* lo = COMP ? flo + 4 * (size_t)sp.first : nullptr;
+    // two tile buffers (sx, sx2): the next tile's copies are in flight while
+    // the current one is computed
+    load_tile_async(sx, st + tile_base(0, p, g), rowoff, m);
+    cp_async_commit();
     for (uint64_t t = 0; t < ntile; ++t) {
-      const uint64_t tb = tile_base(t, p, g);
-      load_tile(sx, st + tb, rowoff, m);
+      float2* cur = (t & 1) ? sx2 : sx;
+      if (t + 1 < ntile) load_tile_async((t & 1) ? sx : sx2, st + tile_base(t + 1, p, g), rowoff, m);
+      cp_async_commit();
+      cp_async_wait_prev();
       __syncthreads();
-      run_tile_fwd<RB, COMP>(sx, sp.ph, p.nphase, sp.ops, dtab, lo, dtlo, sp.runs, m, (uint32_t)tb);
-      store_tile(sx, st + tb, rowoff, m);
+      const uint64_t tb = tile_base(t, p, g);
+      run_tile_fwd<RB, COMP>(cur, sp.ph, p.nphase, sp.ops, dtab, lo, dtlo, sp.runs, m, (uint32_t)tb);
+      store_tile(cur, st + tb, rowoff, m);
       __syncthreads();
     }
+    cp_async_wait_all();
   }
 }
 
@@ -1263,8 +1288,8 @@ __global__ void __launch_bounds__(kTileThreads, kBatchMinBlocks<RB, PREC>) k_bat
         for (uint64_t i = tid; i < (1ull << n); i += blockDim.x) st[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
         __syncthreads();
       }
-      batch_fwd_streamed<RB, PREC>(sx, st, P, R.npass, m, g, a.phases, a.fops, a.dtab, a.flo, a.dtlo, a.druns,
-                                   S.rowoff, stage);
+      batch_fwd_streamed<RB, PREC>(sx, PREC ? reinterpret_cast<float2*>(sxf) : sl, st, P, R.npass, m, g, a.phases,
+                                   a.fops, a.dtab, a.flo, a.dtlo, a.druns, S.rowoff, stage);
       // expectation, lambda = O psi, and the work copy of psi for the uncompute
       double e = 0.0;
       const TPass& p0 = P[0];
@@ -1336,25 +1361,44 @@ struct FArgs {
 
 // One pass over every register of a uniform batch: CTA-strided over tiles,
 // each tile staged in shared memory once and run through all phases of the pass.
+//
+// Two tile buffers: the next tile's amplitudes are copied into one with
+// cp.async (8-byte copies into the swizzled slots) while the phases run on the
+// other, so the pass does not wait on the state's DRAM latency once per tile.
 __global__ void __launch_bounds__(kTileThreads, 1) k_fused_pass(FArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   uint32_t* rowoff = reinterpret_cast<uint32_t*>(smraw);
-  float2* sx = reinterpret_cast<float2*>(smraw + sizeof(uint32_t) * (1 << (kMaxTileBits - kRowBits)));
-  unsigned char* stage = reinterpret_cast<unsigned char*>(sx + (1 << kBatchTile));
+  float2* sbuf = reinterpret_cast<float2*>(smraw + sizeof(uint32_t) * (1 << (kMaxTileBits - kRowBits)));
+  unsigned char* stage = reinterpret_cast<unsigned char*>(sbuf + 2 * (1 << kBatchTile));
   const TPass& p = *a.pass;
   set_rows(rowoff, p, a.m);
   const StagedPass sp = stage_pass<true>(p, a.phases, a.fops, stage, a.druns);
   const uint64_t total = a.ntile * (uint64_t)a.nreg;
-  for (uint64_t t = blockIdx.x; t < total; t += gridDim.x) {
+  auto tile_src = [&](uint64_t t, uint64_t& tb) {
     const uint64_t r = t / a.ntile, tl = t - r * a.ntile;
-    const uint64_t tb = tile_base(tl, p, a.g);
-    float2* base = a.state + r * a.reg_stride + tb;
-    load_tile(sx, base, rowoff, a.m);
+    tb = tile_base(tl, p, a.g);
+    return a.state + r * a.reg_stride + tb;
+  };
+  uint64_t tb = 0;
+  if (blockIdx.x < total) load_tile_async(sbuf, tile_src(blockIdx.x, tb), rowoff, a.m);
+  cp_async_commit();
+  int i = 0;
+  for (uint64_t t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+    float2* sx = sbuf + (size_t)(i & 1) * (1 << kBatchTile);
+    const uint64_t tn = t + gridDim.x;
+    if (tn < total) {
+      uint64_t tbn;
+      load_tile_async(sbuf + (size_t)((i + 1) & 1) * (1 << kBatchTile), tile_src(tn, tbn), rowoff, a.m);
+    }
+    cp_async_commit();
+    cp_async_wait_prev();  // this tile's copies (all groups but the one just issued)
     __syncthreads();
+    float2* base = tile_src(t, tb);
     run_tile_fwd<kRB, false>(sx, sp.ph, p.nphase, sp.ops, a.dtab, nullptr, nullptr, sp.runs, a.m, (uint32_t)tb);
     store_tile(sx, base, rowoff, a.m);
     __syncthreads();
   }
+  cp_async_wait_all();
 }
 
 
@@ -2002,7 +2046,7 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
   }
   P->host_passes = passes;
   if (P->fused_only) {
-    P->smem = sizeof(uint32_t) * (1 << (kMaxTileBits - kRowBits)) + sizeof(float2) * (1 << kBatchTile) + kStageBytes;
+    P->smem = sizeof(uint32_t) * (1 << (kMaxTileBits - kRowBits)) + 2 * sizeof(float2) * (1 << kBatchTile) + kStageBytes;
     QS_CUDA(cudaFuncSetAttribute(k_fused_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smem));
     int dev = 0, sms = 0, per_sm = 0;
     QS_CUDA(cudaGetDevice(&dev));
