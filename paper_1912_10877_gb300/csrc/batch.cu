@@ -837,8 +837,11 @@ __device__ __forceinline__ void phase_fwd_body(float2* sm, const TPhase* php, co
   __syncthreads();
 }
 
-// All phases of a pass on one tile, in order (one call per tile)
-template <int RB, bool COMP>
+// All phases of a pass on one tile, in order (one call per tile).  SITE gives
+// each call site its own copy: ptxas allocates a called function's registers
+// per kernel, and one copy shared by the resident and streamed loops of
+// k_batch spilled several times as much (ptxas -v) as two copies do.
+template <int RB, bool COMP, int SITE = 0>
 __device__ __noinline__ void run_tile_fwd(float2* sm, const TPhase* ph, int nphase, const TOp* fops,
                                           const float2* dtab, const float2* flo, const float2* dtlo,
                                           const DRun* runs, int m, uint32_t tbase) {
@@ -1217,7 +1220,7 @@ __device__ __noinline__ void batch_fwd_streamed(float2* sx, float2* sx2, float2*
       cp_async_wait_prev();
       __syncthreads();
       const uint64_t tb = tile_base(t, p, g);
-      run_tile_fwd<RB, COMP>(cur, sp.ph, p.nphase, sp.ops, dtab, lo, dtlo, sp.runs, m, (uint32_t)tb);
+      run_tile_fwd<RB, COMP, 1>(cur, sp.ph, p.nphase, sp.ops, dtab, lo, dtlo, sp.runs, m, (uint32_t)tb);
       store_tile(cur, st + tb, rowoff, m);
       __syncthreads();
     }
