@@ -776,7 +776,7 @@ __device__ __forceinline__ void diag_masked(float2 (&x)[1 << RB], float2 f, int 
 
 // COMP: compensated matrices (flo: 4 corrections per forward op, dtlo: 16 per
 // diagonal table); out-of-phase diagonal factors are then applied one by one
-template <int RB, bool COMP>
+template <int RB, bool COMP, bool RESLOT>
 __device__ __forceinline__ void phase_fwd_body(float2* sm, const TPhase* php, const TOp* fops, const float2* dtab,
                                                const float2* flo, const float2* dtlo, const DRun* runs, int m,
                                                uint32_t tbase) {
@@ -831,8 +831,12 @@ __device__ __forceinline__ void phase_fwd_body(float2* sm, const TPhase* php, co
 #pragma unroll
       for (int j = 0; j < A; ++j) x[j] = cmulf(x[j], pend);
     }
+    // RESLOT: the slot offsets again (from shared memory) rather than live
+    // through the op loop (fewer spills in k_batch; slower in the tile engine,
+    // whose loop does not spill)
+    const PhaseSlots ps2 = RESLOT ? phase_slots(swz(phase_base(threadIdx.x, ph, ntb)), ph) : ps;
 #pragma unroll
-    for (int j = 0; j < A; ++j) sm[slot(ps, j)] = x[j];
+    for (int j = 0; j < A; ++j) sm[slot(ps2, j)] = x[j];
   }
   __syncthreads();
 }
@@ -840,12 +844,14 @@ __device__ __forceinline__ void phase_fwd_body(float2* sm, const TPhase* php, co
 // All phases of a pass on one tile, in order (one call per tile).  SITE gives
 // each call site its own copy: ptxas allocates a called function's registers
 // per kernel, and one copy shared by the resident and streamed loops of
-// k_batch spilled several times as much (ptxas -v) as two copies do.
+// k_batch spilled several times as much (ptxas -v) as two copies do; SITE 2
+// is the tile engine's pass.
 template <int RB, bool COMP, int SITE = 0>
 __device__ __noinline__ void run_tile_fwd(float2* sm, const TPhase* ph, int nphase, const TOp* fops,
                                           const float2* dtab, const float2* flo, const float2* dtlo,
                                           const DRun* runs, int m, uint32_t tbase) {
-  for (int f = 0; f < nphase; ++f) phase_fwd_body<RB, COMP>(sm, ph + f, fops, dtab, flo, dtlo, runs, m, tbase);
+  for (int f = 0; f < nphase; ++f)
+    phase_fwd_body<RB, COMP, SITE != 2>(sm, ph + f, fops, dtab, flo, dtlo, runs, m, tbase);
 }
 
 // backward of an out-of-phase diagonal gate: the generator is diagonal on the
@@ -1397,7 +1403,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_fused_pass(FArgs a) {
     cp_async_wait_prev();  // this tile's copies (all groups but the one just issued)
     __syncthreads();
     float2* base = tile_src(t, tb);
-    run_tile_fwd<kRB, false>(sx, sp.ph, p.nphase, sp.ops, a.dtab, nullptr, nullptr, sp.runs, a.m, (uint32_t)tb);
+    run_tile_fwd<kRB, false, 2>(sx, sp.ph, p.nphase, sp.ops, a.dtab, nullptr, nullptr, sp.runs, a.m, (uint32_t)tb);
     store_tile(sx, base, rowoff, a.m);
     __syncthreads();
   }
