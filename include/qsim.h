@@ -527,7 +527,8 @@ int qs_batch_program_create(int nreg, const qs_circuit* const* circuits,
                             qs_batch_program** out);
 
 /* The same with the fusion width and the precision chosen by the caller.
- * phase_qubits (2..4, 0 = 4): register qubits per phase, i.e. every gate on
+ * phase_qubits (2..4, 0 = the widest the path takes: 4, or 3 with
+ * QS_BATCH_PRECISE): register qubits per phase, i.e. every gate on
  * those qubits inside a phase is applied to 2^phase_qubits amplitudes held in
  * one thread's registers (the batched engine's k-qubit fusion); the tile then
  * holds at most 9 + phase_qubits qubits (512 threads x 2^phase_qubits

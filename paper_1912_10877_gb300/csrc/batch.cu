@@ -2414,8 +2414,9 @@ int qs_batch_program_create_ex(int nreg, const qs_circuit* const* circuits, cons
   if (flags & ~QS_BATCH_PRECISE) return fail(QS_EINVAL, "unknown program flags 0x%x", flags);
   *out = nullptr;
   qs_batch_program* P = new qs_batch_program();
-  const int rc = build_program(nreg, circuits, observables, tile_qubits, P, phase_qubits > 0 ? phase_qubits : kRB,
-                               (flags & QS_BATCH_PRECISE) != 0);
+  const bool precise = (flags & QS_BATCH_PRECISE) != 0;
+  const int rb = phase_qubits > 0 ? phase_qubits : (precise ? 3 : kRB);  // the widest phase of the path
+  const int rc = build_program(nreg, circuits, observables, tile_qubits, P, rb, precise);
   if (rc != QS_OK) {
     const std::string msg = qs_last_error();
     free_program(P);

@@ -406,7 +406,7 @@ def backward(state: State, circuit: Circuit, params, obs: Observable, ckpt_every
 class BatchProgram:
     """Per-register circuits and diagonal observables of a batch of uneven registers,
     scheduled once into fused tile passes (qs_batch_program).  phase_qubits: the fusion
-    width (qubits whose gates a phase applies in registers, 2..4; 0 = 4); precise: the
+    width (qubits whose gates a phase applies in registers, 2..4; 0 = 4, 3 when precise); precise: the
     compensated forward and double-float uncompute of qs_batch_program_create_ex."""
 
     def __init__(self, circuits, observables, tile_qubits: int = 0, phase_qubits: int = 0, precise: bool = False):

@@ -218,3 +218,45 @@ def test_batch_full_size_sampled_precise(qs, record_property):
     record_property("worst_relative_gradient_error", worst)
     print(f"precise batch, tile {tile} phase {phase}: registers {picks}: worst relative gradient error {worst:.2e}; "
           f"shapes {times}")
+
+
+def _controlled_diagonal_circuit(n, seed, layers=4):
+    """Hadamard layers, then parameterised diagonal gates (Rz, shift) and fixed
+    ones (T, S, Z) with one or two controls of either value anywhere in the
+    register: the forward folds the runs whose controls lie outside a phase into
+    one op per run, the backward keeps one op per gate."""
+    rs = np.random.default_rng(seed)
+    gates, p = [], 0
+    for _ in range(layers):
+        for q in range(n):
+            gates.append(W.Gate("H", (q,)))
+        for i in range(3 * n):
+            perm = [int(x) for x in rs.permutation(n)]
+            nc = 1 + int(rs.integers(0, 2))
+            ctrls = tuple(perm[1:1 + nc])
+            vals = tuple(int(v) for v in rs.integers(0, 2, nc))
+            kind = i % 4
+            if kind == 0:
+                gates.append(W.Gate("RZ", (perm[0],), ctrls, vals, param=p))
+                p += 1
+            elif kind == 1:
+                gates.append(W.Gate("SHIFT", (perm[0],), ctrls, vals, param=p))
+                p += 1
+            elif kind == 2:
+                gates.append(W.Gate(["T", "S", "Z"][i % 3], (perm[0],), ctrls, vals))
+            else:
+                gates.append(W.Gate("RZ", (perm[0],), param=p))
+                p += 1
+        gates.append(W.cnot(int(rs.integers(0, n - 1)), n - 1))
+    return gates, W.uniform_angles(p, seed)
+
+
+@pytest.mark.parametrize("precise", [False, True])
+def test_batch_controlled_diagonal_runs(qs, precise, record_property):
+    specs = []
+    for r, n in enumerate([11, 14, 16, 9]):
+        gates, params = _controlled_diagonal_circuit(n, 40 + r)
+        specs.append((n, gates, params, W.zz_chain(n)))
+    worst = run_case(qs, specs, tile=10, precise=precise, gtol=5e-6)
+    record_property("grad_rel", worst)
+    print(f"controlled diagonal runs (precise={precise}): worst gradient error {worst:.2e}")
