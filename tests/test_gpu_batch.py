@@ -257,6 +257,7 @@ def test_batch_controlled_diagonal_runs(qs, precise, record_property):
     for r, n in enumerate([11, 14, 16, 9]):
         gates, params = _controlled_diagonal_circuit(n, 40 + r)
         specs.append((n, gates, params, W.zz_chain(n)))
-    worst = run_case(qs, specs, tile=10, precise=precise, gtol=5e-6)
+    # measured on GB300: 3.9e-6 (FP32 path), 4.3e-7 (precise path)
+    worst = run_case(qs, specs, tile=10, precise=precise, gtol=1.5e-6 if precise else 1.2e-5)
     record_property("grad_rel", worst)
     print(f"controlled diagonal runs (precise={precise}): worst gradient error {worst:.2e}")
