@@ -355,6 +355,89 @@ __device__ __forceinline__ float op_bwd_t(float2 (&x)[1 << RB], float2 (&l)[1 <<
   return op.cmask ? op_bwd_c<RB, T, true>(x, l, op) : op_bwd_c<RB, T, false>(x, l, op);
 }
 
+// backward op forms (TOp::var = 13 t + form): 0 controlled swap, 1 / 2 diagonal /
+// dense without a parameter, then X, Y, Z, P1, I generators, each without and
+// with phase-local controls
+template <int RB, int T, int F>
+__device__ __forceinline__ float bwd_form(float2 (&x)[1 << RB], float2 (&l)[1 << RB], const TOp& op) {
+  if constexpr (T >= RB) {
+    return 0.f;
+  } else if constexpr (F == 0) {
+    return op_bwd<RB, T, TK_SWAP, 0, true>(x, l, op, 0.f, 0.f);
+  } else if constexpr (F == 1) {
+    return op_bwd<RB, T, TK_DIAG, 0, true>(x, l, op, 0.f, 0.f);
+  } else if constexpr (F == 2) {
+    return op_bwd<RB, T, TK_DENSE, 0, true>(x, l, op, 0.f, 0.f);
+  } else {
+    constexpr bool C = ((F - 3) & 1) != 0;
+    constexpr int G = (F - 3) / 2;
+    if constexpr (G == 0) return op_bwd<RB, T, TK_RX, 2, C>(x, l, op, 0.f, 0.f);
+    else if constexpr (G == 1) return op_bwd<RB, T, TK_RY, 3, C>(x, l, op, 0.f, 0.f);
+    else if constexpr (G == 2) return op_bwd<RB, T, TK_DIAG, 1, C>(x, l, op, 1.f, -1.f);
+    else if constexpr (G == 3) return op_bwd<RB, T, TK_DIAG, 1, C>(x, l, op, 0.f, 1.f);
+    else return op_bwd<RB, T, TK_DIAG, 1, C>(x, l, op, 1.f, 1.f);
+  }
+}
+
+template <int RB>
+__device__ __forceinline__ float apply_bwd_var(float2 (&x)[1 << RB], float2 (&l)[1 << RB], const TOp& op) {
+  switch (op.var) {
+    case 0: return bwd_form<RB, 0, 0>(x, l, op);
+    case 1: return bwd_form<RB, 0, 1>(x, l, op);
+    case 2: return bwd_form<RB, 0, 2>(x, l, op);
+    case 3: return bwd_form<RB, 0, 3>(x, l, op);
+    case 4: return bwd_form<RB, 0, 4>(x, l, op);
+    case 5: return bwd_form<RB, 0, 5>(x, l, op);
+    case 6: return bwd_form<RB, 0, 6>(x, l, op);
+    case 7: return bwd_form<RB, 0, 7>(x, l, op);
+    case 8: return bwd_form<RB, 0, 8>(x, l, op);
+    case 9: return bwd_form<RB, 0, 9>(x, l, op);
+    case 10: return bwd_form<RB, 0, 10>(x, l, op);
+    case 11: return bwd_form<RB, 0, 11>(x, l, op);
+    case 12: return bwd_form<RB, 0, 12>(x, l, op);
+    case 13: return bwd_form<RB, 1, 0>(x, l, op);
+    case 14: return bwd_form<RB, 1, 1>(x, l, op);
+    case 15: return bwd_form<RB, 1, 2>(x, l, op);
+    case 16: return bwd_form<RB, 1, 3>(x, l, op);
+    case 17: return bwd_form<RB, 1, 4>(x, l, op);
+    case 18: return bwd_form<RB, 1, 5>(x, l, op);
+    case 19: return bwd_form<RB, 1, 6>(x, l, op);
+    case 20: return bwd_form<RB, 1, 7>(x, l, op);
+    case 21: return bwd_form<RB, 1, 8>(x, l, op);
+    case 22: return bwd_form<RB, 1, 9>(x, l, op);
+    case 23: return bwd_form<RB, 1, 10>(x, l, op);
+    case 24: return bwd_form<RB, 1, 11>(x, l, op);
+    case 25: return bwd_form<RB, 1, 12>(x, l, op);
+    case 26: return bwd_form<RB, 2, 0>(x, l, op);
+    case 27: return bwd_form<RB, 2, 1>(x, l, op);
+    case 28: return bwd_form<RB, 2, 2>(x, l, op);
+    case 29: return bwd_form<RB, 2, 3>(x, l, op);
+    case 30: return bwd_form<RB, 2, 4>(x, l, op);
+    case 31: return bwd_form<RB, 2, 5>(x, l, op);
+    case 32: return bwd_form<RB, 2, 6>(x, l, op);
+    case 33: return bwd_form<RB, 2, 7>(x, l, op);
+    case 34: return bwd_form<RB, 2, 8>(x, l, op);
+    case 35: return bwd_form<RB, 2, 9>(x, l, op);
+    case 36: return bwd_form<RB, 2, 10>(x, l, op);
+    case 37: return bwd_form<RB, 2, 11>(x, l, op);
+    case 38: return bwd_form<RB, 2, 12>(x, l, op);
+    case 39: return bwd_form<RB, 3, 0>(x, l, op);
+    case 40: return bwd_form<RB, 3, 1>(x, l, op);
+    case 41: return bwd_form<RB, 3, 2>(x, l, op);
+    case 42: return bwd_form<RB, 3, 3>(x, l, op);
+    case 43: return bwd_form<RB, 3, 4>(x, l, op);
+    case 44: return bwd_form<RB, 3, 5>(x, l, op);
+    case 45: return bwd_form<RB, 3, 6>(x, l, op);
+    case 46: return bwd_form<RB, 3, 7>(x, l, op);
+    case 47: return bwd_form<RB, 3, 8>(x, l, op);
+    case 48: return bwd_form<RB, 3, 9>(x, l, op);
+    case 49: return bwd_form<RB, 3, 10>(x, l, op);
+    case 50: return bwd_form<RB, 3, 11>(x, l, op);
+    case 51: return bwd_form<RB, 3, 12>(x, l, op);
+    default: return 0.f;
+  }
+}
+
 template <int RB>
 __device__ __forceinline__ float apply_bwd(float2 (&x)[1 << RB], float2 (&l)[1 << RB], const TOp& op) {
   switch (op.t) {
@@ -998,7 +1081,7 @@ __device__ __forceinline__ void phase_bwd_body(float2* sx, float2* sl, const TPh
     const TOp op = load_op(bops + bop0 + o);
     float part = 0.f;
     if (active && (gb & op.tmask) == op.tval)
-      part = op.kind == TK_DIAGOUT ? diagout_bwd<RB>(x, l, op, gb) : apply_bwd<RB>(x, l, op);
+      part = op.kind == TK_DIAGOUT ? diagout_bwd<RB>(x, l, op, gb) : apply_bwd_var<RB>(x, l, op);
     if (op.gen != GEN_NONE) warp_partial(part, o, pend, pend_o, red, lane, warp);
   }
   flush_partial(pend, pend_o, red, lane, warp);
@@ -1710,6 +1793,15 @@ static void free_program(qs_batch_program* p) {
 // largest tile of the batched kernel for rb-bit phases: 512 threads x 2^rb amplitudes
 static int max_tile(int rb) { return std::min(kBatchTile, 9 + rb); }
 
+// TOp::var of a backward op (bwd_form): 13 t + form
+static uint8_t bwd_variant(const TOp& b) {
+  if (b.kind == TK_DIAGOUT) return 0xff;
+  int f;
+  if (b.gen == GEN_NONE) f = b.kind == TK_SWAP ? 0 : b.kind == TK_DIAG ? 1 : 2;
+  else f = 3 + 2 * (b.gen - GEN_X) + (b.cmask ? 1 : 0);
+  return (uint8_t)(13 * b.t + f);
+}
+
 // TOp::var of a forward op (FV_* forms)
 static uint8_t fwd_variant(const TOp& f) {
   switch (f.kind) {
@@ -2010,6 +2102,7 @@ static int build_program(int nreg, const qs_circuit* const* circs, const qs_obse
     R.cost = cost;
   }
   for (TOp& f : fops) f.var = fwd_variant(f);
+  for (TOp& b : bops) b.var = bwd_variant(b);
   // decreasing cost order
   std::vector<int32_t> order(nreg);
   std::iota(order.begin(), order.end(), 0);
