@@ -36,10 +36,53 @@ struct AdjMat {
   uint64_t off[1 << K];
 };
 
+// Where the gradient of a launch goes: grad[param] += scale * (sum of the CTAs'
+// contributions).  Each CTA writes its partial; the CTA that arrives last at
+// the counter folds them pairwise in index order (the order does not depend on
+// which CTA is last), adds the result and resets the counter for the next
+// launch on the stream: no separate fold launch per gate.
+struct AdjOut {
+  double* partials;   // [gridDim.x]
+  unsigned* counter;  // 0 between launches
+  double* grad;
+  int param;
+  double scale;
+};
+
+__device__ __forceinline__ void adj_finish(double acc, const AdjOut& out) {
+  __shared__ double red[kAdjThreads / 32];
+  __shared__ bool last;
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < kAdjThreads / 32; ++w) v += red[w];
+    out.partials[blockIdx.x] = v;
+    __threadfence();
+    last = atomicAdd(out.counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  __shared__ double buf[2048];
+  static_assert(kAdjMaxBlocks <= 2048, "one fold buffer");
+  for (int i = threadIdx.x; i < 2048; i += blockDim.x) buf[i] = i < (int)gridDim.x ? __ldcg(out.partials + i) : 0.0;
+  __syncthreads();
+  for (int w = 1024; w > 0; w >>= 1) {
+    for (int i = threadIdx.x; i < w; i += blockDim.x) buf[i] += buf[i + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out.grad[out.param] += out.scale * buf[0];
+    *out.counter = 0u;
+  }
+}
+
 template <int K>
 __global__ void __launch_bounds__(kAdjThreads)
 k_adjoint_param(double2* __restrict__ psi, double2* __restrict__ lam, uint64_t nitems, IdxSpec s,
-                const __grid_constant__ AdjMat<K> M, double* __restrict__ partials) {
+                const __grid_constant__ AdjMat<K> M, const AdjOut out) {
   constexpr int D = 1 << K;
   double acc = 0.0;
   for (uint64_t it = (uint64_t)blockIdx.x * kAdjThreads + threadIdx.x; it < nitems;
@@ -71,15 +114,7 @@ k_adjoint_param(double2* __restrict__ psi, double2* __restrict__ lam, uint64_t n
       lam[base + M.off[m]] = pl;
     }
   }
-  __shared__ double red[kAdjThreads / 32];
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double v = 0.0;
-    for (int w = 0; w < kAdjThreads / 32; ++w) v += red[w];
-    partials[blockIdx.x] = v;
-  }
+  adj_finish(acc, out);
 }
 
 // Single-target parameterised gates in structured forms (FP64 is scarce on
@@ -99,7 +134,7 @@ struct AdjForm1 {
 template <int FORM>
 __global__ void __launch_bounds__(kAdjThreads)
 k_adjoint_param1(double2* __restrict__ psi, double2* __restrict__ lam, uint64_t nitems, IdxSpec s,
-                 const __grid_constant__ AdjForm1 F, double* __restrict__ partials) {
+                 const __grid_constant__ AdjForm1 F, const AdjOut out) {
   double acc = 0.0;
   for (uint64_t it = (uint64_t)blockIdx.x * kAdjThreads + threadIdx.x; it < nitems;
        it += (uint64_t)gridDim.x * kAdjThreads) {
@@ -128,28 +163,7 @@ k_adjoint_param1(double2* __restrict__ psi, double2* __restrict__ lam, uint64_t 
     lam[b0] = l0;
     lam[b1] = l1;
   }
-  __shared__ double red[kAdjThreads / 32];
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double v = 0.0;
-    for (int w = 0; w < kAdjThreads / 32; ++w) v += red[w];
-    partials[blockIdx.x] = v;
-  }
-}
-
-// grad[param] += scale * (pairwise fold of partials[0..n))
-__global__ void k_fold_into(const double* __restrict__ partials, int n, double scale, double* __restrict__ grad,
-                            int param) {
-  __shared__ double buf[2048];
-  for (int i = threadIdx.x; i < 2048; i += blockDim.x) buf[i] = i < n ? partials[i] : 0.0;
-  __syncthreads();
-  for (int w = 1024; w > 0; w >>= 1) {
-    for (int i = threadIdx.x; i < w; i += blockDim.x) buf[i] += buf[i + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) grad[param] += scale * buf[0];
+  adj_finish(acc, out);
 }
 
 // the structured form of a single-target gate, or -1
@@ -174,7 +188,8 @@ static int adj_form1(const std::vector<cd>& G, const std::vector<cd>& Ud, AdjFor
 template <int K>
 static int launch_adjoint_param(double2* psi, double2* lam, int n, const qs_gate_desc& g,
                                 const std::vector<cd>& G, const std::vector<cd>& Ud, double* partials,
-                                double* dgrad, double cfac, cudaStream_t st) {
+                                unsigned* counter, double* dgrad, double cfac, cudaStream_t st) {
+  const AdjOut out{partials, counter, dgrad, g.param, 2.0 * cfac};
   if constexpr (K == 1) {
     AdjForm1 F;
     memset(&F, 0, sizeof(F));
@@ -186,11 +201,9 @@ static int launch_adjoint_param(double2* psi, double2* lam, int n, const qs_gate
       const uint64_t items = 1ull << s.item_log2;
       const int nblk = (int)std::min<uint64_t>(kAdjMaxBlocks, std::max<uint64_t>(1, (items + kAdjThreads * 4 - 1) / (kAdjThreads * 4)));
       if (form == ADJ_DIAG)
-        k_adjoint_param1<ADJ_DIAG><<<nblk, kAdjThreads, 0, st>>>(psi, lam, items, s, F, partials);
+        k_adjoint_param1<ADJ_DIAG><<<nblk, kAdjThreads, 0, st>>>(psi, lam, items, s, F, out);
       else
-        k_adjoint_param1<ADJ_RX><<<nblk, kAdjThreads, 0, st>>>(psi, lam, items, s, F, partials);
-      QS_LAUNCHED();
-      k_fold_into<<<1, 256, 0, st>>>(partials, nblk, 2.0 * cfac, dgrad, g.param);
+        k_adjoint_param1<ADJ_RX><<<nblk, kAdjThreads, 0, st>>>(psi, lam, items, s, F, out);
       QS_LAUNCHED();
       return QS_OK;
     }
@@ -214,9 +227,7 @@ static int launch_adjoint_param(double2* psi, double2* lam, int n, const qs_gate
   QS_TRY(make_idx(n, locmask | g.ctrl_mask, g.ctrl_vals & g.ctrl_mask, &s));
   const uint64_t items = 1ull << s.item_log2;
   const int nblk = (int)std::min<uint64_t>(kAdjMaxBlocks, std::max<uint64_t>(1, (items + kAdjThreads * 4 - 1) / (kAdjThreads * 4)));
-  k_adjoint_param<K><<<nblk, kAdjThreads, 0, st>>>(psi, lam, items, s, M, partials);
-  QS_LAUNCHED();
-  k_fold_into<<<1, 256, 0, st>>>(partials, nblk, 2.0 * cfac, dgrad, g.param);
+  k_adjoint_param<K><<<nblk, kAdjThreads, 0, st>>>(psi, lam, items, s, M, out);
   QS_LAUNCHED();
   return QS_OK;
 }
@@ -256,7 +267,9 @@ int backward(qs_state* s, const qs_circuit* c, const double* params, const qs_ob
   QS_TRY(ensure_ws(s, s->ws, sizeof(double) * (np + kAdjMaxBlocks) + 256));
   double* dgrad = (double*)s->ws.ptr;
   double* partials = dgrad + np;
+  unsigned* counter = reinterpret_cast<unsigned*>(partials + kAdjMaxBlocks);
   QS_CUDA(cudaMemsetAsync(dgrad, 0, sizeof(double) * np, st));
+  QS_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
   QS_TRY(promote_to_c128(s->data, s->dtype, psi, dim, st));
   QS_TRY(apply_observable_c128(psi, lam, n, o, st));
   const size_t ab = amp_bytes(s->dtype);
@@ -274,9 +287,9 @@ int backward(qs_state* s, const qs_circuit* c, const double* params, const qs_ob
       QS_TRY(gate_generator(g, G, &cfac));
       int rc;
       switch (g.nlocs) {
-        case 1: rc = launch_adjoint_param<1>(psi, lam, n, g, G, U, partials, dgrad, cfac, st); break;
-        case 2: rc = launch_adjoint_param<2>(psi, lam, n, g, G, U, partials, dgrad, cfac, st); break;
-        case 3: rc = launch_adjoint_param<3>(psi, lam, n, g, G, U, partials, dgrad, cfac, st); break;
+        case 1: rc = launch_adjoint_param<1>(psi, lam, n, g, G, U, partials, counter, dgrad, cfac, st); break;
+        case 2: rc = launch_adjoint_param<2>(psi, lam, n, g, G, U, partials, counter, dgrad, cfac, st); break;
+        case 3: rc = launch_adjoint_param<3>(psi, lam, n, g, G, U, partials, counter, dgrad, cfac, st); break;
         default: rc = fail(QS_EUNSUPPORTED, "parameterised gate on %d targets", g.nlocs);
       }
       QS_TRY(rc);
@@ -382,12 +395,14 @@ int qs_adjoint_step(qs_state* psi, qs_state* lam, const qs_gate_desc* g, const d
   std::vector<cd> G;
   double cfac = 0.0;
   QS_TRY(gate_generator(*g, G, &cfac));
-  QS_TRY(ensure_ws(psi, psi->ws, sizeof(double) * kAdjMaxBlocks));
+  QS_TRY(ensure_ws(psi, psi->ws, sizeof(double) * kAdjMaxBlocks + 256));
   double* partials = (double*)psi->ws.ptr;
+  unsigned* counter = reinterpret_cast<unsigned*>(partials + kAdjMaxBlocks);
+  QS_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
   switch (g->nlocs) {
-    case 1: return launch_adjoint_param<1>(x, l, n, *g, G, U, partials, dev_grad, cfac, st);
-    case 2: return launch_adjoint_param<2>(x, l, n, *g, G, U, partials, dev_grad, cfac, st);
-    case 3: return launch_adjoint_param<3>(x, l, n, *g, G, U, partials, dev_grad, cfac, st);
+    case 1: return launch_adjoint_param<1>(x, l, n, *g, G, U, partials, counter, dev_grad, cfac, st);
+    case 2: return launch_adjoint_param<2>(x, l, n, *g, G, U, partials, counter, dev_grad, cfac, st);
+    case 3: return launch_adjoint_param<3>(x, l, n, *g, G, U, partials, counter, dev_grad, cfac, st);
   }
   return fail(QS_EUNSUPPORTED, "parameterised gate on %d targets", g->nlocs);
 }
