@@ -294,10 +294,11 @@ int backward(qs_state* s, const qs_circuit* c, const double* params, const qs_ob
       }
       QS_TRY(rc);
     } else {
+      // psi and lambda are adjacent in the work buffer: one launch over both as
+      // a batch of two registers
       Plan p;
       QS_TRY(plan_gate(U.data(), g.nlocs, g.locs, g.ctrl_mask, g.ctrl_vals, &p));
-      QS_TRY(launch_plan_on(psi, QS_C128, n, 1, dim, p, s));
-      QS_TRY(launch_plan_on(lam, QS_C128, n, 1, dim, p, s));
+      QS_TRY(launch_plan_on(psi, QS_C128, n, 2, dim, p, s));
     }
   }
   QS_CUDA(cudaMemcpyAsync(host_grad, dgrad, sizeof(double) * c->nparams, cudaMemcpyDeviceToHost, st));
