@@ -1056,8 +1056,9 @@ __device__ __forceinline__ void fold_phase_grad(const TPhase& ph, const TOp* bop
 template <int RB>
 __device__ __forceinline__ void phase_bwd_body(float2* sx, float2* sl, const TPhase* php, const TOp* bops, int m,
                                                float* red, double* gacc, uint32_t tbase) {
-  // the phase record stays in memory (L1): with 2 x 2^RB live amplitudes per
-  // thread there are no registers to spare for a copy of it
+  // the phase record is read where it lies (the pass's shared-memory copy when
+  // staged): with 2 x 2^RB live amplitudes per thread there are no registers
+  // to spare for a copy of it
   constexpr int A = 1 << RB;
   const TPhase& ph = *php;
   const int ntb = m - RB;
