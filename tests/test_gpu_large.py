@@ -180,7 +180,7 @@ def test_large_pipeline_blocks_n32_light_cone_oracle(qs, record_property):
 
 @pytest.mark.parametrize("tc", [1, 0])
 def test_large_pipeline_n22_fp64_block_backward(qs, tc, record_property):
-    # the benchmark spec's split: complex64 forward (QFT on tiles, brickwork as 5-qubit blocks),
+    # the mixed-precision split: complex64 forward (QFT on tiles, brickwork as 5-qubit blocks),
     # then the reversible backward over the same blocks with psi and lambda in FP64 (the final
     # state widened to complex128, FP64 block adjoints and Grams)
     n = 22
